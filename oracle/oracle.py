@@ -1,0 +1,191 @@
+"""ctypes wrapper of the C oracle (ipm_oracle.c).
+
+Test infrastructure: plain double-precision CPU code written from the paper
+(Sections 3-4), used to check the GPU library.  Nothing in the product path
+imports this module.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ipm_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "libipm_oracle.so")
+
+FORM_AS = 1
+FORM_NE = 2
+
+_lib = None
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/_build (portable flags only)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-w", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ct.CDLL(build_oracle())
+    P = ct.c_void_p
+    i64p = np.ctypeslib.ndpointer(np.int64, flags="C")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C")
+    f64p = np.ctypeslib.ndpointer(np.float64, flags="C")
+    lib.orc_create.restype = P
+    lib.orc_create.argtypes = [ct.c_int, ct.c_int, i64p, i32p, f64p, ct.c_int]
+    lib.orc_destroy.argtypes = [P]
+    lib.orc_N.argtypes = [P]
+    lib.orc_N.restype = ct.c_int
+    lib.orc_analyse.argtypes = [P, P, ct.c_int, ct.c_int, ct.c_double]
+    lib.orc_analyse.restype = ct.c_int
+    lib.orc_nsuper.argtypes = [P]
+    lib.orc_nsuper.restype = ct.c_int
+    lib.orc_nrows_total.argtypes = [P]
+    lib.orc_nrows_total.restype = ct.c_int64
+    lib.orc_nnzL_stored.argtypes = [P]
+    lib.orc_nnzL_stored.restype = ct.c_int64
+    lib.orc_get_symbolic.argtypes = [P, i32p, i32p, i64p, i32p, i32p, i64p, i32p]
+    lib.orc_factorise.argtypes = [P, f64p, ct.c_double, ct.c_double, ct.c_double]
+    lib.orc_factorise.restype = ct.c_int
+    lib.orc_get_factor.argtypes = [P, f64p, f64p, f64p, i64p]
+    lib.orc_get_stats.argtypes = [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                                  ct.POINTER(ct.c_double)]
+    lib.orc_solve.argtypes = [P, f64p, f64p, f64p, f64p, f64p, ct.c_double, ct.c_int]
+    lib.orc_solve.restype = ct.c_int
+    lib.orc_refine_record.argtypes = [P, f64p, ct.POINTER(ct.c_double)]
+    lib.orc_refine_record.restype = ct.c_int
+    lib.orc_omega_K.argtypes = [P, f64p, ct.c_double, ct.c_double, f64p, f64p, f64p, f64p]
+    lib.orc_omega_K.restype = ct.c_double
+    lib.orc_front_factor.argtypes = [ct.c_int, ct.c_int, ct.c_int, f64p, i32p, f64p, ct.c_double, f64p, f64p]
+    lib.orc_front_factor.restype = ct.c_int
+    lib.orc_backward_error.argtypes = [ct.c_int, f64p, f64p, f64p, f64p, f64p]
+    lib.orc_backward_error.restype = ct.c_double
+    lib.orc_get_matrix.argtypes = [P, i64p, i32p, f64p]
+    lib.orc_nnzM.argtypes = [P]
+    lib.orc_nnzM.restype = ct.c_int64
+    _lib = lib
+    return lib
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class Oracle:
+    """One matrix pattern: analyse once, factorise and solve many times."""
+
+    def __init__(self, m, n, colptr, rowidx, vals, form=FORM_AS):
+        lib = _load()
+        self.m, self.n, self.form = int(m), int(n), int(form)
+        self._keep = (_c(colptr, np.int64), _c(rowidx, np.int32), _c(vals, np.float64))
+        self.h = lib.orc_create(self.m, self.n, *self._keep, self.form)
+        if not self.h:
+            raise ValueError("oracle rejected the matrix")
+        self.N = lib.orc_N(self.h)
+        self.lib = lib
+
+    @classmethod
+    def from_lp(cls, lp, form=FORM_AS):
+        return cls(lp.m, lp.n, lp.colptr, lp.rowidx, lp.vals, form)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.orc_destroy(self.h)
+            self.h = None
+
+    def analyse(self, perm=None, nb=32, amalg_width=16, amalg_zero_frac=0.05):
+        p = None
+        if perm is not None:
+            self._perm_in = _c(perm, np.int32)
+            if self._perm_in.size != self.N:
+                raise ValueError("permutation size")
+            p = self._perm_in.ctypes.data_as(ct.c_void_p)
+        rc = self.lib.orc_analyse(self.h, p, int(nb), int(amalg_width), float(amalg_zero_frac))
+        if rc:
+            raise ValueError(f"oracle analyse failed ({rc})")
+        return self.symbolic()
+
+    def symbolic(self):
+        N, ns = self.N, self.lib.orc_nsuper(self.h)
+        nr = self.lib.orc_nrows_total(self.h)
+        out = dict(perm=np.empty(N, np.int32), parent=np.empty(N, np.int32), colcount=np.empty(N, np.int64),
+                   sn_start=np.empty(ns + 1, np.int32), sn_parent=np.empty(ns, np.int32),
+                   sn_rptr=np.empty(ns + 1, np.int64), sn_rows=np.empty(nr, np.int32))
+        self.lib.orc_get_symbolic(self.h, out["perm"], out["parent"], out["colcount"], out["sn_start"],
+                                  out["sn_parent"], out["sn_rptr"], out["sn_rows"])
+        return out
+
+    def factorise(self, theta, rho, delta, eps_piv=1e-14):
+        rc = self.lib.orc_factorise(self.h, _c(theta, np.float64), float(rho), float(delta), float(eps_piv))
+        self.theta = _c(theta, np.float64)
+        self.rho, self.delta = float(rho), float(delta)
+        return rc
+
+    def factor(self):
+        ns = self.lib.orc_nsuper(self.h)
+        nl = self.lib.orc_nnzL_stored(self.h)
+        L = np.empty(nl, np.float64)
+        D = np.empty(self.N, np.float64)
+        dyn = np.empty(self.N, np.float64)
+        lptr = np.empty(ns + 1, np.int64)
+        self.lib.orc_get_factor(self.h, L, D, dyn, lptr)
+        return dict(L=L, D=D, dynreg=dyn, lptr=lptr)
+
+    def stats(self):
+        a, b, c = ct.c_int(), ct.c_int(), ct.c_int()
+        d = ct.c_double()
+        self.lib.orc_get_stats(self.h, ct.byref(a), ct.byref(b), ct.byref(c), ct.byref(d))
+        return dict(ndyn=a.value, npos=b.value, nneg=c.value, normM1=d.value)
+
+    def solve(self, r7, r1, omega_target=1e-12, max_steps=2):
+        dx = np.empty(self.n, np.float64)
+        dy = np.empty(self.m, np.float64)
+        self.lib.orc_solve(self.h, self.theta, _c(r7, np.float64), _c(r1, np.float64), dx, dy,
+                           float(omega_target), int(max_steps))
+        hist = np.empty(65, np.float64)
+        wk = ct.c_double()
+        steps = self.lib.orc_refine_record(self.h, hist, ct.byref(wk))
+        return dx, dy, dict(steps=steps, omega_hist=hist[: steps + 1].copy(), omega_K=wk.value)
+
+    def omega_K(self, theta, rho, delta, r7, r1, dx, dy):
+        return self.lib.orc_omega_K(self.h, _c(theta, np.float64), float(rho), float(delta), _c(r7, np.float64),
+                                    _c(r1, np.float64), _c(dx, np.float64), _c(dy, np.float64))
+
+    def matrix(self):
+        nz = self.lib.orc_nnzM(self.h)
+        cp = np.empty(self.N + 1, np.int64)
+        ri = np.empty(nz, np.int32)
+        x = np.empty(nz, np.float64)
+        self.lib.orc_get_matrix(self.h, cp, ri, x)
+        return cp, ri, x
+
+
+def front_factor(F, k, signs, sreg, b1, nb=32):
+    """Run the oracle's dense front factorisation (Sec. 4.4-4.5) on a full
+    symmetric matrix F (f x f).  Returns (F_out, D, dynreg, rc)."""
+    lib = _load()
+    F = np.array(F, dtype=np.float64, order="F")
+    f = F.shape[0]
+    buf = np.ascontiguousarray(F.T.reshape(-1))  # column-major flat
+    D = np.zeros(max(k, 1), np.float64)
+    dyn = np.zeros(max(k, 1), np.float64)
+    rc = lib.orc_front_factor(int(f), int(k), int(nb), buf, _c(signs, np.int32), _c(sreg, np.float64),
+                              float(b1), D, dyn)
+    out = buf.reshape(f, f).T.copy()
+    return out, D[:k], dyn[:k], rc
+
+
+def backward_error(r, ad, ae, f, d):
+    lib = _load()
+    return lib.orc_backward_error(int(len(r)), _c(r, np.float64), _c(ad, np.float64), _c(ae, np.float64),
+                                  _c(f, np.float64), _c(d, np.float64))

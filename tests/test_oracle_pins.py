@@ -1,0 +1,460 @@
+"""Pins for the CPU oracle: facts fixed by the paper and by mathematics,
+independent of the oracle's own code.
+
+* hand-worked pivot-rule cases (Sec. 4.5, Prop. 3)         -> golden/pivot_rule_cases.json
+* hand-worked symbolic cases (Sec. 4.1-4.3)                -> golden/symbolic_cases.json
+* hand-worked backward-error cases (Sec. 4.5)              -> golden/backward_error_cases.json
+* closed forms for A = I (Eq. augsys / Eq. normeq with Eq. regul_matrix)
+* exact rational LDL^T on tiny systems (Python fractions)
+* symbolic structure from a numpy Cholesky of a random SPD matrix on the pattern
+* dense reconstruction, dense solve, inertia (Props. 1-2) against numpy / LAPACK
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+from oracle import FORM_AS, FORM_NE, Oracle, backward_error, front_factor
+
+
+# ----------------------------------------------------------------- helpers
+
+def lp_from_dense(A):
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    C = sp.csc_matrix(A)
+    C.sort_indices()
+    return m, n, C.indptr.astype(np.int64), C.indices.astype(np.int32), C.data.astype(np.float64)
+
+
+def K_dense(A, theta, rho, delta):
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    K = np.zeros((n + m, n + m))
+    K[:n, :n] = np.diag(-(1.0 / theta + rho))
+    K[n:, :n] = A
+    K[:n, n:] = A.T
+    K[n:, n:] = delta * np.eye(m)
+    return K
+
+
+def dense_L(orc_sym, fac, N):
+    L = np.zeros((N, N))
+    ns = len(orc_sym["sn_parent"])
+    for s in range(ns):
+        c0, c1 = orc_sym["sn_start"][s], orc_sym["sn_start"][s + 1]
+        k = c1 - c0
+        R = orc_sym["sn_rows"][orc_sym["sn_rptr"][s]:orc_sym["sn_rptr"][s + 1]]
+        f = len(R)
+        blk = fac["L"][fac["lptr"][s]:fac["lptr"][s + 1]].reshape(k, f).T
+        for jj in range(k):
+            L[R, c0 + jj] = blk[:, jj]
+    return L
+
+
+def load(golden_dir, name):
+    with open(os.path.join(golden_dir, name)) as fh:
+        return json.load(fh)
+
+
+# ------------------------------------------------------- pivot rule cases
+
+def test_pivot_rule_hand_cases(golden_dir):
+    data = load(golden_dir, "pivot_rule_cases.json")
+    for case in data["cases"]:
+        F = np.array(case["F"])
+        Fo, D, dyn, rc = front_factor(F, case["k"], case["signs"], case["sreg"], case["b1"])
+        assert rc == 0, case["name"]
+        np.testing.assert_allclose(D, case["D"], rtol=1e-13, atol=0, err_msg=case["name"])
+        np.testing.assert_allclose(dyn, case["dynreg"], rtol=1e-12, atol=1e-15, err_msg=case["name"])
+        L = np.tril(Fo, -1) + np.eye(F.shape[0])
+        np.testing.assert_allclose(L, np.array(case["L"], dtype=float), rtol=1e-13, atol=1e-15,
+                                   err_msg=case["name"])
+
+
+def test_prop3_bound_holds_for_every_accepted_pivot():
+    """Prop. 3: after a pivot is accepted, every later same-sign diagonal in
+    its block that was correctly signed keeps its sign.  Checked on random
+    symmetric blocks by recomputing the partially eliminated matrix densely."""
+    rng = np.random.default_rng(5)
+    fired = 0
+    for trial in range(40):
+        f = 12
+        signs = rng.choice([-1, 1], size=f)
+        B = rng.standard_normal((f, f))
+        F = 0.6 * (B + B.T) / 2
+        F[np.arange(f), np.arange(f)] = signs * rng.uniform(0.05, 1.5, size=f)
+        # a few diagonals pushed towards zero or past it
+        bad = rng.choice(f, size=3, replace=False)
+        F[bad, bad] = signs[bad] * rng.uniform(-0.2, 0.01, size=3)
+        sreg = np.full(f, 1e-3)
+        Fo, D, dyn, rc = front_factor(F, f, signs, sreg, 0.05, nb=4)
+        L = np.tril(Fo, -1) + np.eye(f)
+        # reconstruct the matrix actually factorised: F + diag(s*sreg + dyn)
+        Freg = F + np.diag(signs * sreg + dyn)
+        scale = np.abs(L) @ np.diag(np.abs(D)) @ np.abs(L).T
+        scale += np.diag(np.abs(np.diag(F)) + sreg + np.abs(dyn))  # rounding of F_pp + s*sreg + dyn
+        assert np.all(np.abs(L @ np.diag(D) @ L.T - Freg) <= 1e-13 * scale + 1e-300)
+        # signs of the pivots are the expected ones
+        assert np.all(np.sign(D) == signs)
+        fired += int(np.count_nonzero(dyn))
+        # Prop. 3 inside each block of 4: after eliminating p, diagonal j>p of the
+        # same block with the same sign and correct sign before keeps it
+        S = F.copy()
+        acc = np.abs(np.diag(F)).copy()  # magnitude of everything summed into each diagonal
+        for p in range(f):
+            blk_end = (p // 4 + 1) * 4
+            S[p, p] += signs[p] * sreg[p] + dyn[p]  # both terms enter at pivot time
+            before = np.diag(S).copy()
+            col = S[:, p].copy()
+            upd = np.outer(col, col) / S[p, p]
+            S = S - upd
+            acc += np.abs(np.diag(upd))
+            for j in range(p + 1, min(blk_end, f)):
+                # only diagonals that are clearly correctly signed (not a rounding-level
+                # zero left by an earlier pivot lifted exactly to its bound)
+                if signs[j] == signs[p] and signs[j] * before[j] > 1e-8 * acc[j]:
+                    tol = 1e-8 * acc[j]
+                    assert signs[j] * S[j, j] >= -tol, (trial, p, j)
+    assert fired > 10
+
+
+# ---------------------------------------------------------- backward error
+
+def test_backward_error_hand_cases(golden_dir):
+    data = load(golden_dir, "backward_error_cases.json")
+    for case in data["cases"]:
+        M = np.array(case["M"], dtype=float)
+        d = np.array(case["d"], dtype=float)
+        f = np.array(case["f"], dtype=float)
+        r = f - M @ d
+        ad = np.abs(M) @ np.abs(d)
+        ae = np.abs(M).sum(axis=1)
+        w = backward_error(r, ad, ae, f, d)
+        assert w == pytest.approx(case["omega"], rel=1e-12, abs=1e-300), case["name"]
+
+
+# -------------------------------------------------------------- symbolic
+
+def _tridiag_ne(m):
+    A = np.zeros((m, m - 1))
+    for i in range(m - 1):
+        A[i, i] = 1.0
+        A[i + 1, i] = 1.0
+    return A
+
+
+def _arrow_ne(m):
+    A = np.zeros((m, m - 1))
+    for i in range(m - 1):
+        A[i, i] = 1.0
+        A[m - 1, i] = 1.0
+    return A
+
+
+def test_symbolic_hand_cases(golden_dir):
+    data = load(golden_dir, "symbolic_cases.json")
+    cases = {c["kind"]: c for c in data["cases"]}
+    # tridiagonal: chain
+    m = cases["ne_path"]["m"]
+    o = Oracle(*lp_from_dense(_tridiag_ne(m)), form=FORM_NE)
+    s = o.analyse(np.arange(m))
+    assert list(s["parent"]) == list(range(1, m)) + [-1]
+    assert list(s["colcount"]) == [2] * (m - 1) + [1]
+    assert list(s["sn_start"]) == cases["ne_path"]["sn_start"]
+    o2 = Oracle(*lp_from_dense(_tridiag_ne(m)), form=FORM_NE)
+    s2 = o2.analyse(np.arange(m), amalg_width=1, amalg_zero_frac=0.0)
+    assert list(s2["sn_start"]) == list(range(0, m - 1)) + [m]
+    # arrowhead: star
+    m = cases["ne_arrow"]["m"]
+    o = Oracle(*lp_from_dense(_arrow_ne(m)), form=FORM_NE)
+    s = o.analyse(np.arange(m))
+    assert list(s["parent"]) == [m - 1] * (m - 1) + [-1]
+    assert list(s["colcount"]) == [2] * (m - 1) + [1]
+    assert list(s["sn_start"]) == cases["ne_arrow"]["sn_start"]
+    # identity A, interleaved
+    n = cases["as_identity"]["n"]
+    o = Oracle(*lp_from_dense(np.eye(n)), form=FORM_AS)
+    perm = np.ravel(np.column_stack([np.arange(n), n + np.arange(n)])).astype(np.int32)
+    s = o.analyse(perm)
+    assert list(s["perm"]) == list(perm)
+    assert list(s["parent"]) == [v for j in range(n) for v in (2 * j + 1, -1)]
+    assert list(s["colcount"]) == [2, 1] * n
+    assert list(s["sn_start"]) == list(range(0, 2 * n + 1, 2))
+    # two overlapping dense columns: the zero-fraction rule decides the merge
+    c = cases["ne_two_blocks"]
+    m = c["m"]
+    A = np.zeros((m, 2))
+    A[:19, 0] = 1.0
+    A[10:, 1] = 1.0
+    o = Oracle(*lp_from_dense(A), form=FORM_NE)
+    s = o.analyse(np.arange(m))
+    assert list(s["colcount"]) == [19 - j for j in range(10)] + [20 - j for j in range(10, 20)]
+    assert list(s["sn_start"]) == c["sn_start"]
+    o = Oracle(*lp_from_dense(A), form=FORM_NE)
+    s = o.analyse(np.arange(m), amalg_zero_frac=0.04)
+    assert list(s["sn_start"]) == c["sn_start_4pct"]
+
+
+def _structure_from_cholesky(Mpat_dense, rng):
+    """Structure of L from a numeric Cholesky of an SPD matrix with the given
+    pattern (no cancellation for generic random values)."""
+    N = Mpat_dense.shape[0]
+    V = rng.uniform(0.5, 1.0, size=(N, N))
+    V = (V + V.T) / 2 * Mpat_dense
+    np.fill_diagonal(V, 0.0)
+    V += np.diag(np.abs(V).sum(axis=1) + 1.0)
+    L = np.linalg.cholesky(V)
+    nzL = L != 0.0
+    parent = np.full(N, -1)
+    colcount = np.zeros(N, dtype=int)
+    for j in range(N):
+        rows = np.flatnonzero(nzL[j + 1:, j]) + j + 1
+        parent[j] = rows[0] if rows.size else -1
+        colcount[j] = rows.size + 1
+    return parent, colcount, nzL
+
+
+@pytest.mark.parametrize("form", [FORM_AS, FORM_NE])
+def test_symbolic_against_numeric_cholesky(form):
+    rng = np.random.default_rng(11)
+    for trial in range(6):
+        lp = synth.random_lp(14 + trial, 30 + 2 * trial, 3, seed=100 + trial)
+        o = Oracle.from_lp(lp, form=form)
+        N = o.N
+        s = o.analyse(synth.random_perm(N, trial))
+        cp, ri, _ = o.matrix()
+        pat = np.zeros((N, N), dtype=bool)
+        for j in range(N):
+            for p in range(cp[j], cp[j + 1]):
+                pat[ri[p], j] = pat[j, ri[p]] = True
+        P = s["perm"]
+        parent, colcount, nzL = _structure_from_cholesky(pat[np.ix_(P, P)].astype(float), rng)
+        assert np.array_equal(s["parent"], parent)
+        assert np.array_equal(s["colcount"], colcount)
+        # postorder: every parent comes after its children, and subtrees are contiguous
+        assert np.all((s["parent"] == -1) | (s["parent"] > np.arange(N)))
+        # supernodes: contiguous columns, rows sorted, first k rows are the columns
+        for t in range(len(s["sn_parent"])):
+            c0, c1 = s["sn_start"][t], s["sn_start"][t + 1]
+            R = s["sn_rows"][s["sn_rptr"][t]:s["sn_rptr"][t + 1]]
+            assert list(R[: c1 - c0]) == list(range(c0, c1))
+            assert np.all(np.diff(R) > 0)
+            # the front rows are exactly the union of its columns' structures
+            union = set()
+            for j in range(c0, c1):
+                union |= set(np.flatnonzero(nzL[:, j]).tolist())
+            assert set(R.tolist()) == union
+
+
+# ----------------------------------------------------------- closed forms
+
+def test_closed_form_identity_augmented():
+    n = 10
+    theta = 10.0 ** np.linspace(-3, 3, n)
+    rho, delta = 1e-6, 2e-6
+    o = Oracle(*lp_from_dense(np.eye(n)), form=FORM_AS)
+    perm = np.ravel(np.column_stack([np.arange(n), n + np.arange(n)])).astype(np.int32)
+    s = o.analyse(perm)
+    assert o.factorise(theta, rho, delta, eps_piv=0.0) == 0
+    fac = o.factor()
+    D = fac["D"]
+    dx = -(1.0 / theta + rho)
+    dy = delta + 1.0 / (1.0 / theta + rho)
+    np.testing.assert_allclose(D[0::2], dx, rtol=4e-16)
+    np.testing.assert_allclose(D[1::2], dy, rtol=4e-16)
+    L = dense_L(s, fac, 2 * n)
+    for j in range(n):
+        assert L[2 * j + 1, 2 * j] == pytest.approx(1.0 / dx[j], rel=4e-16)
+    assert np.all(fac["dynreg"] == 0.0)
+
+
+def test_closed_form_identity_normal_equations():
+    n = 10
+    theta = 10.0 ** np.linspace(-4, 4, n)
+    rho, delta = 1e-6, 3e-6
+    o = Oracle(*lp_from_dense(np.eye(n)), form=FORM_NE)
+    o.analyse(None)
+    assert o.factorise(theta, rho, delta, eps_piv=0.0) == 0
+    D = o.factor()["D"]
+    np.testing.assert_allclose(D, 1.0 / (1.0 / theta + rho) + delta, rtol=4e-16)
+
+
+# ------------------------------------------------------- exact arithmetic
+
+def _exact_ldlt(M):
+    N = len(M)
+    A = [row[:] for row in M]
+    L = [[Fraction(int(i == j)) for j in range(N)] for i in range(N)]
+    D = [Fraction(0)] * N
+    for p in range(N):
+        D[p] = A[p][p]
+        for i in range(p + 1, N):
+            L[i][p] = A[i][p] / D[p]
+        for i in range(p + 1, N):
+            for j in range(p + 1, i + 1):
+                A[i][j] -= L[i][p] * D[p] * L[j][p]
+                A[j][i] = A[i][j]
+    return L, D
+
+
+def test_exact_rational_ldlt():
+    rng = np.random.default_rng(3)
+    for trial in range(5):
+        m, n = 3, 5
+        Aint = rng.integers(-3, 4, size=(m, n))
+        Aint[rng.random((m, n)) < 0.4] = 0
+        for j in range(n):
+            if not Aint[:, j].any():
+                Aint[rng.integers(m), j] = 1
+        for i in range(m):
+            if not Aint[i].any():
+                Aint[i, rng.integers(n)] = 2
+        theta_fr = [Fraction(2) ** int(e) for e in rng.integers(-6, 7, size=n)]
+        rho = Fraction(1, 2 ** 10)
+        delta = Fraction(1, 2 ** 11)
+        N = n + m
+        K = [[Fraction(0)] * N for _ in range(N)]
+        for j in range(n):
+            K[j][j] = -(1 / theta_fr[j] + rho)
+        for i in range(m):
+            K[n + i][n + i] = delta
+            for j in range(n):
+                K[n + i][j] = K[j][n + i] = Fraction(int(Aint[i, j]))
+        o = Oracle(*lp_from_dense(Aint.astype(float)), form=FORM_AS)
+        s = o.analyse(synth.random_perm(N, 50 + trial))
+        P = s["perm"]
+        KP = [[K[P[i]][P[j]] for j in range(N)] for i in range(N)]
+        Le, De = _exact_ldlt(KP)
+        theta = np.array([float(t) for t in theta_fr])
+        assert o.factorise(theta, float(rho), float(delta), eps_piv=0.0) == 0
+        fac = o.factor()
+        assert np.all(fac["dynreg"] == 0.0)
+        Lx = np.array([[float(v) for v in row] for row in Le])
+        Dx = np.array([float(v) for v in De])
+        eps = 2.220446049250313e-16
+        Lo = dense_L(s, fac, N)
+        Do = fac["D"]
+        # (1) backward stability against the exact matrix: |L D L^T - P K P^T| <= c eps |L||D||L^T|
+        KPx = np.array([[float(v) for v in row] for row in KP])
+        So = np.abs(Lo) @ np.diag(np.abs(Do)) @ np.abs(Lo).T
+        assert np.all(np.abs(Lo @ np.diag(Do) @ Lo.T - KPx) <= 32 * eps * So), trial
+        # (2) forward agreement with the exact factors; the leading blocks have
+        # condition numbers up to ~1e5 here, so 1e-8 of the |L||D||L^T| scale
+        # still fails on any dropped term or sign
+        S = np.abs(Lx) @ np.diag(np.abs(Dx)) @ np.abs(Lx).T
+        assert np.all(np.abs(Do - Dx) <= 1e-8 * np.diag(S)), trial
+        tolL = 1e-8 * (S / np.abs(Dx)[None, :] + np.abs(Lx))
+        assert np.all(np.abs(Lo - Lx) <= tolL), trial
+        # structural zeros are exact zeros
+        assert np.all(Lo[Lx == 0] == 0.0)
+
+
+# ---------------------------------------------- dense brute force, inertia
+
+@pytest.mark.parametrize("form", [FORM_AS, FORM_NE])
+def test_dense_reconstruction_and_solve(form):
+    for trial in range(3):
+        lp = synth.random_lp(40, 100, 4, seed=200 + trial)
+        theta = synth.theta_loguniform(lp.n, trial, -1.0, 1.0)
+        rho, delta = 1e-8, 1e-8
+        o = Oracle.from_lp(lp, form=form)
+        s = o.analyse(synth.random_perm(o.N, trial))
+        assert o.factorise(theta, rho, delta, eps_piv=1e-14) == 0
+        fac = o.factor()
+        N = o.N
+        A = sp.csc_matrix((lp.vals, lp.rowidx, lp.colptr), shape=(lp.m, lp.n)).toarray()
+        K = K_dense(A, theta, rho, delta)
+        if form == FORM_AS:
+            M = K.copy()
+        else:
+            tt = 1.0 / (1.0 / theta + rho)
+            M = A @ np.diag(tt) @ A.T + delta * np.eye(lp.m)
+        P = s["perm"]
+        Mp = M[np.ix_(P, P)] + np.diag(fac["dynreg"])
+        L = dense_L(s, fac, N)
+        R = L @ np.diag(fac["D"]) @ L.T
+        scale = np.abs(L) @ np.diag(np.abs(fac["D"])) @ np.abs(L).T
+        assert np.all(np.abs(R - Mp) <= 1e-13 * scale + 1e-300)
+        # inertia: n negative and m positive pivots (AS), m positive (NE)
+        if form == FORM_AS:
+            assert (fac["D"] < 0).sum() == lp.n and (fac["D"] > 0).sum() == lp.m
+            ev = np.linalg.eigvalsh(K)
+            assert (ev < 0).sum() == lp.n
+        else:
+            assert (fac["D"] > 0).sum() == lp.m
+        # solve against LAPACK on the well-conditioned system
+        r7 = synth.rhs_normal(lp.n, trial)
+        r1 = synth.rhs_normal(lp.m, trial + 9)
+        dx, dy, info = o.solve(r7, r1, omega_target=1e-14, max_steps=5)
+        x = np.linalg.solve(K, np.concatenate([r7, r1]))
+        np.testing.assert_allclose(np.concatenate([dx, dy]), x, rtol=1e-9, atol=1e-9 * np.abs(x).max())
+        assert info["omega_K"] < 1e-13
+
+
+def test_refinement_reaches_target_on_ill_conditioned_theta():
+    lp = synth.by_name("random_300x800", 1)
+    theta = synth.theta_loguniform(lp.n, 1)
+    o = Oracle.from_lp(lp)
+    o.analyse(synth.random_perm(o.N, 1))
+    o.factorise(theta, 1e-8, 1e-8, eps_piv=1e-14)
+    r7 = synth.rhs_normal(lp.n, 1)
+    r1 = synth.rhs_normal(lp.m, 2)
+    dx, dy, info = o.solve(r7, r1, omega_target=1e-12, max_steps=10)
+    assert info["omega_hist"][-1] <= 1e-12
+    assert info["omega_K"] <= 1e-12
+    # every accepted refinement step at least halves omega
+    h = info["omega_hist"]
+    assert np.all(h[1:] <= 0.5 * h[:-1])
+    # the oracle's omega equals a direct evaluation of the formula
+    w = o.omega_K(theta, 1e-8, 1e-8, r7, r1, dx, dy)
+    assert w == info["omega_K"]
+
+
+def test_normal_equations_match_augmented_system():
+    lp = synth.random_lp(60, 150, 4, seed=7)
+    theta = synth.theta_loguniform(lp.n, 7, -2.0, 2.0)
+    r7 = synth.rhs_normal(lp.n, 3)
+    r1 = synth.rhs_normal(lp.m, 4)
+    res = {}
+    for form in (FORM_AS, FORM_NE):
+        o = Oracle.from_lp(lp, form=form)
+        o.analyse(synth.random_perm(o.N, 1))
+        o.factorise(theta, 1e-8, 1e-8, eps_piv=1e-14)
+        res[form] = o.solve(r7, r1, omega_target=1e-14, max_steps=5)
+        assert res[form][2]["omega_K"] < 1e-12
+    x1 = np.concatenate(res[FORM_AS][:2])
+    x2 = np.concatenate(res[FORM_NE][:2])
+    np.testing.assert_allclose(x1, x2, rtol=1e-8, atol=1e-8 * np.abs(x1).max())
+
+
+def test_deterministic_bitwise():
+    lp = synth.by_name("random_300x800", 2)
+    theta = synth.theta_loguniform(lp.n, 2)
+    outs = []
+    for _ in range(2):
+        o = Oracle.from_lp(lp)
+        o.analyse(synth.random_perm(o.N, 2))
+        o.factorise(theta, 1e-8, 1e-8)
+        outs.append(o.factor())
+    for key in ("L", "D", "dynreg"):
+        assert np.array_equal(outs[0][key], outs[1][key])
+
+
+def test_rejects_bad_input():
+    lp = synth.random_lp(5, 8, 2, seed=1)
+    o = Oracle.from_lp(lp)
+    with pytest.raises(ValueError):
+        o.analyse(np.zeros(o.N, dtype=np.int32))  # not a permutation
+    o.analyse(None)
+    theta = np.ones(lp.n)
+    theta[3] = np.nan
+    assert o.factorise(theta, 1e-8, 1e-8) != 0
+    bad = lp.rowidx.copy()
+    bad[0] = lp.m + 3
+    with pytest.raises(ValueError):
+        Oracle(lp.m, lp.n, lp.colptr, bad, lp.vals)
