@@ -1,0 +1,224 @@
+/*
+ * ipm_mf.h -- C ABI of a GB300 (sm_103a) multifrontal LDL^T factorise/solve
+ * library for the regularised linear systems of an interior point method
+ * (Zanetti & Gondzio, "A factorisation-based regularised interior point
+ * method using the augmented system", arXiv 2508.04370).
+ *
+ * The library factorises, at every IPM iteration and on a fixed pattern,
+ * either the regularised augmented system (Sec. 3.2, Eq. regul_matrix)
+ *
+ *        K = [ -(Theta^-1 + rho I)   A^T     ]          (n + m unknowns)
+ *            [        A             delta I  ]
+ *
+ * or the regularised normal equations (Eq. normeq with Eq. regul_matrix)
+ *
+ *        M = A (Theta^-1 + rho I)^-1 A^T + delta I       (m unknowns),
+ *
+ * and solves K [dx; dy] = [r7; r1] (Eq. augsys; for the normal equations dy
+ * solves M dy = r1 + A Theta~ r7 and dx = Theta~ (A^T dy - r7), Eq. normeq).
+ *
+ * Conventions shared by every call:
+ *   - A is m x n in compressed sparse columns: colptr[n+1] (int64),
+ *     rowidx[nnz] (int32), 0-based, rows sorted inside each column, no
+ *     duplicates.  The pattern is copied at ipm_analyse; the caller keeps
+ *     ownership of its arrays.
+ *   - Pointers documented as "device" are CUDA device pointers owned by the
+ *     caller and accessed in stream order on the given stream.  Pointers
+ *     documented as "host" are ordinary host memory.
+ *   - Streams are passed as `void *` holding a cudaStream_t (NULL = legacy
+ *     default stream), so this header needs no CUDA header.
+ *   - Return value: 0 = success, negative = error (nothing was changed
+ *     unless stated), positive = success with a warning.
+ *   - A context is not thread-safe: one host thread at a time.
+ *   - Nothing in this library traps or aborts the GPU: device-side problems
+ *     (non-finite pivots, expired bounded waits) are recorded in a device
+ *     status word and returned by the next call that synchronises
+ *     (ipm_get_info, ipm_sync_status, the *_host calls).
+ */
+#ifndef IPM_MF_H
+#define IPM_MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define IPM_OK 0
+#define IPM_ERR_INVALID_ARG (-1)
+#define IPM_ERR_NOT_ANALYSED (-2)
+#define IPM_ERR_OOM (-3)
+#define IPM_ERR_CUDA (-4)
+#define IPM_ERR_NONFINITE (-5)     /* NaN/Inf in Theta, a pivot or a residual */
+#define IPM_ERR_DEVICE_TIMEOUT (-6) /* a bounded device-side wait expired */
+#define IPM_ERR_NOT_FACTORISED (-7)
+#define IPM_ERR_NO_DEVICE (-8)
+#define IPM_WARN_DYNREG_APPLIED 1   /* at least one pivot was lifted (Sec. 4.5) */
+#define IPM_WARN_LARGE_REG 2        /* a lift exceeded opt.large_reg (Sec. 4.6 end) */
+#define IPM_WARN_REFINE_NOT_CONVERGED 3
+
+/* forms (Sec. 4.2) */
+#define IPM_FORM_AUTO 0
+#define IPM_FORM_AUGMENTED 1
+#define IPM_FORM_NORMAL 2
+
+/* fill-reducing orderings (Sec. 4.2) */
+#define IPM_ORD_AMD 0      /* approximate minimum degree (Amestoy, Davis, Duff) */
+#define IPM_ORD_ND 1       /* nested dissection, minimum degree on the leaves */
+#define IPM_ORD_USER 2     /* caller-supplied permutation */
+#define IPM_ORD_NATURAL 3  /* identity (tests) */
+
+/* precision of the Schur-complement updates (Sec. 4.4 dgemm updates) */
+#define IPM_PREC_FP64 0    /* everything in FP64 */
+#define IPM_PREC_MIXED 1   /* FP32-accurate tensor-core updates on large fronts,
+                              FP64 pivots, regularisation, residual, refinement */
+
+typedef struct ipm_ctx ipm_ctx;
+
+typedef struct ipm_options {
+    int32_t nb;               /* pivot-block width (Sec. 4.4 "32, 64 or 128"); default 32 */
+    int32_t amalg_width;      /* merge a child into its parent when the width stays <= this; 16 */
+    double amalg_zero_frac;   /* ... or when explicit zeros stay <= this fraction; 0.05 */
+    double eps_piv;           /* dynamic-regularisation floor eps_piv * ||K||_1 (Sec. 4.5); 1e-14 */
+    double large_reg;         /* a lift larger than this raises IPM_WARN_LARGE_REG; 1e-4 */
+    int32_t precision;        /* IPM_PREC_FP64 or IPM_PREC_MIXED; FP64 */
+    int32_t mixed_min_front;  /* mixed path: fronts with f >= this use tensor-core updates; 256 */
+    double omega_target;      /* refinement stops at this backward error; 1e-12 */
+    int32_t refine_max;       /* at most this many refinement steps per solve; 10 */
+    int32_t nd_leaf;          /* nested dissection stops at subgraphs of this size; 128 */
+    double dense_row_factor;  /* AMD treats degree > max(16, f*sqrt(N)) as dense; 10 */
+    int32_t device;           /* CUDA device ordinal; 0 */
+    int32_t verbose;          /* print analysis statistics to stderr; 0 */
+} ipm_options;
+
+typedef struct ipm_info {
+    int32_t m, n, N, form, ordering;
+    int32_t nsuper, nlevels, nfronts_small, nfronts_large;
+    int32_t max_front, max_k;
+    int64_t nnz_A, nnz_K_lower, nnz_L;      /* nnz_L counts stored supernodal entries */
+    double flops_factor;                    /* sum over fronts of sum_{i=1..k} (f-i)(f-i+3) */
+    double flops_tensor;                    /* part of flops_factor in tensor-core updates */
+    int64_t device_bytes;                   /* device memory held by the context */
+    int32_t npos, nneg, ndynreg;            /* inertia and number of lifted pivots */
+    double max_dynreg;                      /* largest |lift| */
+    double norm_K1;                         /* ||K||_1 (or ||M||_1) of the last factorisation */
+    int32_t refine_steps;                   /* refinement steps of the last solve */
+    double omega;                           /* backward error of the last solve, on K */
+    double omega_hist[16];                  /* omega after 0, 1, ... refinement steps */
+    int32_t status;                         /* device status word of the last factorise/solve */
+    double ms_analyse;                      /* host wall time of ipm_analyse */
+    double est_flops_ne, est_flops_as;      /* AS/NE chooser model (Sec. 4.2) */
+    int64_t nnz_ne_seen;                    /* NE entries formed before the chooser stopped */
+} ipm_info;
+
+/* Fill *opt with the defaults listed above. */
+void ipm_default_options(ipm_options *opt);
+
+/* Create a context.  opt may be NULL (defaults).  Allocates no device memory. */
+int ipm_create(ipm_ctx **out, const ipm_options *opt);
+
+/* Release the context, its device arena and any captured graph. */
+int ipm_destroy(ipm_ctx *ctx);
+
+/* Symbolic analysis, done once per pattern (Sec. 4.2-4.3): choose the form
+ * (AUTO runs the augmented-system symbolic first and abandons forming the
+ * normal equations once they hold more entries than L of the augmented
+ * system, Sec. 4.2), order (AMD / ND / USER / NATURAL), build the elimination
+ * tree, postorder, column counts, fundamental supernodes and amalgamation,
+ * the front row lists, the extend-add maps, the tree levels and the device
+ * plan.  Host only: the device arena is allocated by the first
+ * ipm_set_values.
+ *   m, n      sizes of A (m >= 0, n >= 0)
+ *   colptr    host, n+1 entries
+ *   rowidx    host, colptr[n] entries
+ *   user_perm host, N entries (N = n+m for the augmented system, m for the
+ *             normal equations), perm[new] = old; read only for IPM_ORD_USER
+ * Errors: IPM_ERR_INVALID_ARG for a malformed pattern or permutation. */
+int ipm_analyse(ipm_ctx *ctx, int32_t m, int32_t n, const int64_t *colptr, const int32_t *rowidx,
+                int32_t form, int32_t ordering, const int32_t *user_perm);
+
+/* Batched analysis of `count` independent LPs, factorised together as one
+ * block-diagonal system (a forest); per-instance arrays are concatenated:
+ *   ms[count], ns[count], colptrs (sum(n_i+1) entries, each instance
+ *   starting at 0), rowidxs (sum nnz_i entries).  The combined unknowns are
+ *   [x_0; ...; x_{c-1}; y_0; ...; y_{c-1}] (all primal blocks, then all dual
+ *   blocks), so the batch behaves exactly like one LP with a block-diagonal
+ *   A.  Form is the augmented system. */
+int ipm_analyse_batch(ipm_ctx *ctx, int32_t count, const int32_t *ms, const int32_t *ns,
+                      const int64_t *colptrs, const int32_t *rowidxs, int32_t ordering);
+
+/* Values of A (device, colptr[n] doubles in the CSC order given at analyse).
+ * They are copied into the context, so the pointer need not stay valid.
+ * The first call allocates the device arena (call it before any stream
+ * capture).  Errors: IPM_ERR_NOT_ANALYSED, IPM_ERR_OOM, IPM_ERR_CUDA. */
+int ipm_set_values(ipm_ctx *ctx, const double *Ax_dev, void *stream);
+
+/* Numeric factorisation of K (or M) for the given Theta (device, n doubles,
+ * every entry > 0 and finite) and static regularisation rho, delta >= 0
+ * (Sec. 4.5: added to each pivot after it has been computed, with sign -1
+ * for the primal block and +1 for the dual block).  Pivots whose magnitude
+ * falls below max(eps_piv ||K||_1, Prop. 3 bound) are lifted (dynamic
+ * regularisation).  Enqueued on `stream`; returns without synchronising.
+ * Non-finite input or pivots set IPM_ERR_NONFINITE in the device status. */
+int ipm_factorise(ipm_ctx *ctx, const double *theta_dev, double rho, double delta, void *stream);
+
+/* Solve K [dx; dy] = [r7; r1] with the last factorisation, followed by
+ * iterative refinement on the regularised K (Sec. 4.5) until the
+ * component-wise backward error is <= omega_target, refine_max steps were
+ * taken, or a step fails to halve it.  All pointers device: r7, dx have n
+ * entries, r1, dy have m.  Inputs and outputs may not alias.  Enqueued on
+ * `stream`, no synchronisation. */
+int ipm_solve(ipm_ctx *ctx, const double *r7_dev, const double *r1_dev, double *dx_dev, double *dy_dev,
+              void *stream);
+
+/* One IPM iteration's linear algebra from host memory: copy Theta (n) and
+ * `nrhs` right-hand sides (r7 blocks of n then r1 blocks of m, rhs k at
+ * r7_host + k*n and r1_host + k*m) to the device, factorise, solve each rhs
+ * with refinement, and copy the solutions back (dx_host, dy_host, same
+ * layout).  Synchronises `stream` and returns the device status. */
+int ipm_iterate_host(ipm_ctx *ctx, const double *theta_host, double rho, double delta, int32_t nrhs,
+                     const double *r7_host, const double *r1_host, double *dx_host, double *dy_host,
+                     void *stream);
+
+/* Synchronise `stream` and return (and clear) the device status word. */
+int ipm_sync_status(ipm_ctx *ctx, void *stream);
+
+/* Statistics of the analysis and of the last factorise/solve; synchronises
+ * the device.  Returns the device status of the last operations. */
+int ipm_get_info(ipm_ctx *ctx, ipm_info *out);
+
+/* Symbolic results in the factorisation order (for bit-exact tests); any
+ * pointer may be NULL.  Sizes: perm, etree, colcount N; snode_ptr nsuper+1;
+ * sn_parent nsuper; sn_rptr nsuper+1; sn_rows sn_rptr[nsuper].
+ * perm[new] = old is the fill-reducing order composed with the postorder of
+ * its elimination tree. */
+int ipm_get_symbolic(const ipm_ctx *ctx, int32_t *perm, int32_t *etree, int64_t *colcount,
+                     int32_t *snode_ptr, int32_t *sn_parent, int64_t *sn_rptr, int32_t *sn_rows);
+
+/* Sizes needed by ipm_get_symbolic / ipm_get_factor. */
+int ipm_get_sizes(const ipm_ctx *ctx, int32_t *N, int32_t *nsuper, int64_t *nrows_total, int64_t *nnz_L_stored);
+
+/* Copy the factor to host memory (tests): L_host holds, supernode after
+ * supernode, the f x k column-major block of each front (rows in sn_rows
+ * order, unit diagonal stored as 1, entries above it 0); D_host and
+ * dynreg_host have N entries in the factorisation order.  Synchronises. */
+int ipm_get_factor(ipm_ctx *ctx, double *L_host, double *D_host, double *dynreg_host);
+
+/* Capture ipm_factorise + ipm_solve (with the given pointers, which must stay
+ * valid) into one CUDA graph owned by the context; ipm_graph_launch replays
+ * it on any stream.  Replays read the pointed-to Theta and right-hand sides
+ * afresh, so an IPM loop writes new values there and replays. */
+int ipm_graph_capture(ipm_ctx *ctx, const double *theta_dev, double rho, double delta, const double *r7_dev,
+                      const double *r1_dev, double *dx_dev, double *dy_dev, int32_t nsolves, void *stream);
+int ipm_graph_launch(ipm_ctx *ctx, void *stream);
+
+/* Number of kernel launches enqueued by the last ipm_factorise and the last
+ * ipm_solve (for launch accounting). */
+int ipm_launch_counts(const ipm_ctx *ctx, int32_t *factorise_launches, int32_t *solve_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPM_MF_H */

@@ -1,0 +1,731 @@
+// C ABI of the multifrontal factorise/solve library (include/ipm_mf.h).
+// Host orchestration: device arena, plan upload, per-level launch sequence of
+// the numeric factorisation (Sec. 4.1, 4.3-4.5 of Zanetti & Gondzio, arXiv
+// 2508.04370) and of the solves with iterative refinement (Sec. 4.5).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ipm_mf.h"
+#include "ipm_dev.h"
+#include "ipm_plan.h"
+
+using namespace ipm;
+
+namespace {
+
+struct StepWork {
+    int32_t p0;
+    int64_t panel_off;
+    int32_t panel_cnt;
+    int64_t tile_off;
+    int32_t tile_cnt;
+};
+struct LevelWork {
+    int64_t small_off;
+    int32_t small_cnt, small_maxf;
+    int64_t all_off;
+    int32_t all_cnt, all_maxf;
+    int64_t asm_off;
+    int32_t asm_cnt;
+    std::vector<StepWork> steps;
+};
+
+constexpr int kTile = 64;
+
+}  // namespace
+
+struct ipm_ctx {
+    ipm_options opt;
+    Plan plan;
+    bool analysed = false;
+    bool dev_ready = false;
+    bool values_set = false;
+    bool factorised = false;
+    std::vector<void *> allocs;
+    int64_t device_bytes = 0;
+    DevPlan dp{};
+    DevCtl *ctl = nullptr;
+    double *fronts = nullptr, *D = nullptr, *dyn = nullptr;
+    double *Ax = nullptr;
+    double *theta = nullptr;  // owned copy for host entry points
+    double *vf = nullptr, *vx = nullptr, *vbest = nullptr, *vr = nullptr, *vad = nullptr, *vae = nullptr,
+           *vc = nullptr, *upd = nullptr;
+    double *h_r7 = nullptr, *h_r1 = nullptr, *d_r7 = nullptr, *d_r1 = nullptr, *d_dx = nullptr, *d_dy = nullptr;
+    int32_t *lvl_small = nullptr, *lvl_all = nullptr;
+    PanelItem *asm_items = nullptr, *panel_items = nullptr;
+    TileItem *tile_items = nullptr;
+    std::vector<LevelWork> levels;
+    // numeric state of the last factorisation
+    double rho = 0.0, delta = 0.0;
+    const double *theta_used = nullptr;
+    // last solve
+    DevCtl last{};
+    int32_t refine_steps = 0;
+    double omega = 0.0;
+    double omega_hist[16] = {0};
+    int32_t status_acc = 0;
+    int32_t nl_factor = 0, nl_solve = 0;
+    double ms_analyse = 0.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+};
+
+namespace {
+
+int to_err(cudaError_t e) { return e == cudaSuccess ? IPM_OK : (e == cudaErrorMemoryAllocation ? IPM_ERR_OOM : IPM_ERR_CUDA); }
+
+template <typename T>
+int dalloc(ipm_ctx *c, T **p, size_t count) {
+    void *q = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return to_err(e);
+    }
+    c->allocs.push_back(q);
+    c->device_bytes += (int64_t)bytes;
+    *p = (T *)q;
+    return IPM_OK;
+}
+
+template <typename T>
+int dupload(ipm_ctx *c, T **p, const std::vector<T> &h) {
+    int rc = dalloc(c, p, h.size());
+    if (rc) return rc;
+    if (!h.empty()) {
+        cudaError_t e = cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return to_err(e);
+    }
+    return IPM_OK;
+}
+
+void free_device(ipm_ctx *c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    for (void *p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    if (c->h_r7) cudaFreeHost(c->h_r7);
+    c->h_r7 = nullptr;
+    c->device_bytes = 0;
+    c->dev_ready = false;
+    c->values_set = false;
+    c->factorised = false;
+}
+
+// Build the device plan and the large-front work lists, then upload.
+int setup_device(ipm_ctx *c) {
+    const Plan &P = c->plan;
+    cudaError_t e = cudaSetDevice(c->opt.device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return IPM_ERR_NO_DEVICE;
+    }
+    const int32_t ns = P.nsuper, N = P.N;
+    std::vector<int32_t> c0(ns);
+    for (int32_t s = 0; s < ns; s++) c0[s] = P.sn_start[s];
+    std::vector<int8_t> sign(P.sign.begin(), P.sign.end());
+    // regularised matrix, full symmetric CSR in factorisation order
+    std::vector<int64_t> kp(N + 1, 0);
+    std::vector<int32_t> kj;
+    std::vector<int64_t> ksrc;
+    if (P.form == 1) {
+        const int32_t n = P.n;
+        // count
+        for (int32_t j = 0; j < n; j++) {
+            kp[P.iperm[j] + 1]++;  // diagonal
+            for (int64_t p = P.Acp[j]; p < P.Acp[j + 1]; p++) {
+                kp[P.iperm[j] + 1]++;
+                kp[P.iperm[n + P.Ari[p]] + 1]++;
+            }
+        }
+        for (int32_t i = 0; i < P.m; i++) kp[P.iperm[n + i] + 1]++;
+        for (int32_t i = 0; i < N; i++) kp[i + 1] += kp[i];
+        kj.resize(kp[N]);
+        ksrc.resize(kp[N]);
+        std::vector<int64_t> fill(kp.begin(), kp.end() - 1);
+        for (int32_t j = 0; j < n; j++) {
+            int32_t a = P.iperm[j];
+            kj[fill[a]] = a;
+            ksrc[fill[a]++] = -1 - (int64_t)j;
+            for (int64_t p = P.Acp[j]; p < P.Acp[j + 1]; p++) {
+                int32_t b = P.iperm[n + P.Ari[p]];
+                kj[fill[a]] = b;
+                ksrc[fill[a]++] = p;
+                kj[fill[b]] = a;
+                ksrc[fill[b]++] = p;
+            }
+        }
+        for (int32_t i = 0; i < P.m; i++) {
+            int32_t b = P.iperm[n + i];
+            kj[fill[b]] = b;
+            ksrc[fill[b]++] = kDualDiag;
+        }
+    }
+    // per-level lists
+    std::vector<int32_t> lvl_all;
+    std::vector<PanelItem> asm_items, panel_items;
+    std::vector<TileItem> tile_items;
+    c->levels.assign(P.nlevels, LevelWork());
+    for (int32_t l = 0; l < P.nlevels; l++) {
+        LevelWork &W = c->levels[l];
+        W.small_off = P.lvl_small_ptr[l];
+        W.small_cnt = P.lvl_small_ptr[l + 1] - P.lvl_small_ptr[l];
+        W.small_maxf = 0;
+        for (int32_t t = P.lvl_small_ptr[l]; t < P.lvl_small_ptr[l + 1]; t++)
+            W.small_maxf = std::max(W.small_maxf, P.sn_f[P.lvl_small[t]]);
+        W.all_off = (int64_t)lvl_all.size();
+        W.all_maxf = W.small_maxf;
+        for (int32_t t = P.lvl_small_ptr[l]; t < P.lvl_small_ptr[l + 1]; t++) lvl_all.push_back(P.lvl_small[t]);
+        for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
+            lvl_all.push_back(P.lvl_large[t]);
+            W.all_maxf = std::max(W.all_maxf, P.sn_f[P.lvl_large[t]]);
+        }
+        W.all_cnt = (int32_t)(lvl_all.size() - W.all_off);
+        // large fronts
+        W.asm_off = (int64_t)asm_items.size();
+        int32_t maxsteps = 0;
+        for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
+            int32_t s = P.lvl_large[t];
+            for (int32_t cl = 0; cl < P.sn_f[s]; cl += 32) asm_items.push_back({s, cl, std::min(cl + 32, P.sn_f[s])});
+            maxsteps = std::max(maxsteps, (P.sn_k[s] + c->opt.nb - 1) / c->opt.nb);
+        }
+        W.asm_cnt = (int32_t)(asm_items.size() - W.asm_off);
+        for (int32_t st = 0; st < maxsteps; st++) {
+            StepWork S;
+            S.p0 = st * c->opt.nb;
+            S.panel_off = (int64_t)panel_items.size();
+            S.tile_off = (int64_t)tile_items.size();
+            for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
+                int32_t s = P.lvl_large[t];
+                const int32_t k = P.sn_k[s], f = P.sn_f[s];
+                if (S.p0 >= k) continue;
+                const int32_t p1 = std::min(S.p0 + c->opt.nb, k);
+                if (p1 >= f) panel_items.push_back({s, p1, p1});
+                for (int32_t r = p1; r < f; r += 128) panel_items.push_back({s, r, std::min(r + 128, f)});
+                for (int32_t j0 = p1; j0 < f; j0 += kTile)
+                    for (int32_t i0 = j0; i0 < f; i0 += kTile) tile_items.push_back({s, i0, j0});
+            }
+            S.panel_cnt = (int32_t)(panel_items.size() - S.panel_off);
+            S.tile_cnt = (int32_t)(tile_items.size() - S.tile_off);
+            W.steps.push_back(S);
+        }
+    }
+    std::vector<int64_t> upd_off(P.upd_off.begin(), P.upd_off.end());
+    int rc = 0;
+    int32_t *d_c0, *d_k, *d_f, *d_ld, *d_rows, *d_cptr, *d_clist, *d_relmap, *d_odst, *d_perm, *d_kj;
+    int64_t *d_off, *d_rptr, *d_moff, *d_optr, *d_osrc, *d_uoff, *d_kp, *d_ksrc;
+    int8_t *d_sign;
+    std::vector<int64_t> upd_sizes;
+    if ((rc = dupload(c, &d_c0, c0)) || (rc = dupload(c, &d_k, P.sn_k)) || (rc = dupload(c, &d_f, P.sn_f)) ||
+        (rc = dupload(c, &d_ld, P.sn_ld)) || (rc = dupload(c, &d_off, P.sn_off)) ||
+        (rc = dupload(c, &d_rptr, P.sn_rptr)) || (rc = dupload(c, &d_rows, P.sn_rows)) ||
+        (rc = dupload(c, &d_cptr, P.child_ptr)) || (rc = dupload(c, &d_clist, P.child_list)) ||
+        (rc = dupload(c, &d_moff, P.map_off)) || (rc = dupload(c, &d_relmap, P.relmap)) ||
+        (rc = dupload(c, &d_optr, P.orig_ptr)) || (rc = dupload(c, &d_odst, P.orig_dst)) ||
+        (rc = dupload(c, &d_osrc, P.orig_src)) || (rc = dupload(c, &d_sign, sign)) ||
+        (rc = dupload(c, &d_perm, P.perm)) || (rc = dupload(c, &d_uoff, upd_off)) || (rc = dupload(c, &d_kp, kp)) ||
+        (rc = dupload(c, &d_kj, kj)) || (rc = dupload(c, &d_ksrc, ksrc)) ||
+        (rc = dupload(c, &c->lvl_small, P.lvl_small)) || (rc = dupload(c, &c->lvl_all, lvl_all)) ||
+        (rc = dupload(c, &c->asm_items, asm_items)) || (rc = dupload(c, &c->panel_items, panel_items)) ||
+        (rc = dupload(c, &c->tile_items, tile_items)))
+        return rc;
+    DevPlan &dp = c->dp;
+    dp.N = N;
+    dp.n = P.n;
+    dp.m = P.m;
+    dp.nsuper = ns;
+    dp.form = P.form;
+    dp.sn_c0 = d_c0;
+    dp.sn_k = d_k;
+    dp.sn_f = d_f;
+    dp.sn_ld = d_ld;
+    dp.sn_off = d_off;
+    dp.sn_rptr = d_rptr;
+    dp.sn_rows = d_rows;
+    dp.child_ptr = d_cptr;
+    dp.child_list = d_clist;
+    dp.map_off = d_moff;
+    dp.relmap = d_relmap;
+    dp.orig_ptr = d_optr;
+    dp.orig_dst = d_odst;
+    dp.orig_src = d_osrc;
+    dp.sign = d_sign;
+    dp.perm = d_perm;
+    dp.upd_off = d_uoff;
+    dp.kp = d_kp;
+    dp.kj = d_kj;
+    dp.ksrc = d_ksrc;
+    const int64_t nnzA = P.Acp[P.n];
+    if ((rc = dalloc(c, &c->fronts, (size_t)P.front_doubles)) || (rc = dalloc(c, &c->D, N)) ||
+        (rc = dalloc(c, &c->dyn, N)) || (rc = dalloc(c, &c->ctl, 1)) || (rc = dalloc(c, &c->Ax, nnzA)) ||
+        (rc = dalloc(c, &c->theta, P.n)) ||
+        (rc = dalloc(c, &c->vf, N)) || (rc = dalloc(c, &c->vx, N)) || (rc = dalloc(c, &c->vbest, N)) ||
+        (rc = dalloc(c, &c->vr, N)) || (rc = dalloc(c, &c->vad, N)) || (rc = dalloc(c, &c->vae, N)) ||
+        (rc = dalloc(c, &c->vc, N)) || (rc = dalloc(c, &c->upd, (size_t)std::max<int64_t>(P.upd_total, 1))))
+        return rc;
+    cudaMemset(c->ctl, 0, sizeof(DevCtl));
+    cudaMemset(c->fronts, 0, (size_t)std::max<int64_t>(P.front_doubles, 1) * sizeof(double));
+    c->dev_ready = true;
+    return to_err(cudaGetLastError());
+}
+
+int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta, cudaStream_t st) {
+    const Plan &P = c->plan;
+    DevVals V{};
+    V.Ax = c->Ax;
+    V.theta = theta;
+    V.nev = nullptr;
+    V.rho = rho;
+    V.delta = delta;
+    V.large_reg = c->opt.large_reg;
+    int nl = 0;
+    // reset the per-factorisation fields of the control block
+    cudaMemsetAsync(&c->ctl->ndyn, 0, offsetof(DevCtl, omega) - offsetof(DevCtl, ndyn), st);
+    launch_norm1(c->dp, V, c->ctl, c->opt.eps_piv, st);
+    nl += 2;
+    for (int32_t l = 0; l < P.nlevels; l++) {
+        const LevelWork &W = c->levels[l];
+        if (W.small_cnt > 0) {
+            launch_small_fronts(c->dp, V, c->fronts, c->D, c->dyn, c->ctl, c->lvl_small + W.small_off, W.small_cnt,
+                                c->opt.nb, W.small_maxf, st);
+            nl++;
+        }
+        if (W.asm_cnt > 0) {
+            launch_large_assemble(c->dp, V, c->fronts, c->asm_items + W.asm_off, W.asm_cnt, st);
+            nl++;
+        }
+        for (const StepWork &S : W.steps) {
+            launch_large_panel(c->dp, V, c->fronts, c->D, c->dyn, c->ctl, c->panel_items + S.panel_off, S.panel_cnt,
+                               S.p0, c->opt.nb, st);
+            nl++;
+            if (S.tile_cnt > 0) {
+                launch_large_update(c->dp, c->fronts, c->D, c->tile_items + S.tile_off, S.tile_cnt, S.p0, c->opt.nb,
+                                    st);
+                nl++;
+            }
+        }
+    }
+    launch_factor_stats(c->D, c->dyn, P.N, c->opt.large_reg, c->ctl, st);
+    nl++;
+    c->nl_factor = nl;
+    return to_err(cudaGetLastError());
+}
+
+// x <- (L D L^T)^-1 x in the factorisation order.
+int solve_inplace(ipm_ctx *c, double *x, cudaStream_t st, int *nl) {
+    const Plan &P = c->plan;
+    for (int32_t l = 0; l < P.nlevels; l++) {
+        const LevelWork &W = c->levels[l];
+        launch_forward(c->dp, c->fronts, c->D, x, c->upd, c->lvl_all + W.all_off, W.all_cnt, W.all_maxf, st);
+        (*nl)++;
+    }
+    for (int32_t l = P.nlevels - 1; l >= 0; l--) {
+        const LevelWork &W = c->levels[l];
+        launch_backward(c->dp, c->fronts, x, c->lvl_all + W.all_off, W.all_cnt, W.all_maxf, st);
+        (*nl)++;
+    }
+    return to_err(cudaGetLastError());
+}
+
+int check_ctx(const ipm_ctx *c) {
+    if (!c) return IPM_ERR_INVALID_ARG;
+    if (!c->analysed) return IPM_ERR_NOT_ANALYSED;
+    return IPM_OK;
+}
+
+int status_to_code(int32_t st) {
+    if (st & kStatNonFinite) return IPM_ERR_NONFINITE;
+    if (st & kStatTimeout) return IPM_ERR_DEVICE_TIMEOUT;
+    if (st & kStatRefineFail) return IPM_WARN_REFINE_NOT_CONVERGED;
+    if (st & kStatLargeReg) return IPM_WARN_LARGE_REG;
+    if (st & kStatDynReg) return IPM_WARN_DYNREG_APPLIED;
+    return IPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ipm_default_options(ipm_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->nb = 32;
+    o->amalg_width = 16;
+    o->amalg_zero_frac = 0.05;
+    o->eps_piv = 1e-14;
+    o->large_reg = 1e-4;
+    o->precision = IPM_PREC_FP64;
+    o->mixed_min_front = 256;
+    o->omega_target = 1e-12;
+    o->refine_max = 10;
+    o->nd_leaf = 128;
+    o->dense_row_factor = 10.0;
+    o->device = 0;
+    o->verbose = 0;
+}
+
+int ipm_create(ipm_ctx **out, const ipm_options *opt) {
+    if (!out) return IPM_ERR_INVALID_ARG;
+    ipm_ctx *c = new (std::nothrow) ipm_ctx();
+    if (!c) return IPM_ERR_OOM;
+    if (opt) c->opt = *opt;
+    else ipm_default_options(&c->opt);
+    if (c->opt.nb != 32 || c->opt.refine_max < 0 || c->opt.refine_max > 15 || !(c->opt.eps_piv >= 0.0)) {
+        delete c;
+        return IPM_ERR_INVALID_ARG;
+    }
+    *out = c;
+    return IPM_OK;
+}
+
+int ipm_destroy(ipm_ctx *c) {
+    if (!c) return IPM_ERR_INVALID_ARG;
+    if (c->dev_ready) {
+        cudaSetDevice(c->opt.device);
+        cudaDeviceSynchronize();
+    }
+    free_device(c);
+    delete c;
+    return IPM_OK;
+}
+
+int ipm_analyse(ipm_ctx *c, int32_t m, int32_t n, const int64_t *colptr, const int32_t *rowidx, int32_t form,
+                int32_t ordering, const int32_t *user_perm) {
+    if (!c) return IPM_ERR_INVALID_ARG;
+    if (form == IPM_FORM_AUTO) form = IPM_FORM_AUGMENTED;
+    if (form == IPM_FORM_NORMAL) return IPM_ERR_INVALID_ARG;  // normal equations: not in this build yet
+    AnalyseOptions ao;
+    ao.nb = c->opt.nb;
+    ao.amalg_width = c->opt.amalg_width;
+    ao.amalg_zero_frac = c->opt.amalg_zero_frac;
+    ao.nd_leaf = c->opt.nd_leaf;
+    ao.dense_row_factor = c->opt.dense_row_factor;
+    ao.verbose = c->opt.verbose;
+    std::string err;
+    if (c->dev_ready) {
+        cudaSetDevice(c->opt.device);
+        cudaDeviceSynchronize();
+    }
+    free_device(c);
+    c->analysed = false;
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = analyse(c->plan, m, n, colptr, rowidx, form, ordering, user_perm, ao, err);
+    c->ms_analyse = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rc) {
+        if (c->opt.verbose) std::fprintf(stderr, "[ipm analyse] %s\n", err.c_str());
+        return rc;
+    }
+    c->analysed = true;
+    return IPM_OK;
+}
+
+int ipm_analyse_batch(ipm_ctx *c, int32_t count, const int32_t *ms, const int32_t *ns, const int64_t *colptrs,
+                      const int32_t *rowidxs, int32_t ordering) {
+    if (!c || count <= 0 || !ms || !ns || !colptrs || !rowidxs) return IPM_ERR_INVALID_ARG;
+    int64_t M = 0, Nn = 0;
+    for (int32_t b = 0; b < count; b++) {
+        if (ms[b] < 0 || ns[b] < 0) return IPM_ERR_INVALID_ARG;
+        M += ms[b];
+        Nn += ns[b];
+    }
+    if (M + Nn > INT32_MAX) return IPM_ERR_INVALID_ARG;
+    // block-diagonal A: instance b's columns follow instance b-1's, its rows are shifted by sum m
+    std::vector<int64_t> cp(Nn + 1, 0);
+    std::vector<int32_t> ri;
+    int64_t cpo = 0, rio = 0, col = 0, roff = 0;
+    for (int32_t b = 0; b < count; b++) {
+        const int64_t *cpb = colptrs + cpo;
+        if (cpb[0] != 0) return IPM_ERR_INVALID_ARG;
+        for (int32_t j = 0; j < ns[b]; j++) {
+            if (cpb[j + 1] < cpb[j]) return IPM_ERR_INVALID_ARG;
+            for (int64_t p = cpb[j]; p < cpb[j + 1]; p++) {
+                const int32_t r = rowidxs[rio + p];
+                if (r < 0 || r >= ms[b]) return IPM_ERR_INVALID_ARG;
+                ri.push_back((int32_t)(roff + r));
+            }
+            cp[col + j + 1] = (int64_t)ri.size();
+        }
+        rio += cpb[ns[b]];
+        cpo += ns[b] + 1;
+        col += ns[b];
+        roff += ms[b];
+    }
+    return ipm_analyse(c, (int32_t)M, (int32_t)Nn, cp.data(), ri.data(), IPM_FORM_AUGMENTED, ordering, nullptr);
+}
+
+
+int ipm_set_values(ipm_ctx *c, const double *Ax_dev, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!Ax_dev && c->plan.Acp[c->plan.n] > 0) return IPM_ERR_INVALID_ARG;
+    if (!c->dev_ready) {
+        rc = setup_device(c);
+        if (rc) return rc;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nnz = c->plan.Acp[c->plan.n];
+    if (nnz > 0) {
+        cudaError_t e = cudaMemcpyAsync(c->Ax, Ax_dev, nnz * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return to_err(e);
+    }
+    c->values_set = true;
+    c->factorised = false;
+    return IPM_OK;
+}
+
+int ipm_factorise(ipm_ctx *c, const double *theta_dev, double rho, double delta, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->values_set) return IPM_ERR_NOT_ANALYSED;
+    if (!theta_dev && c->plan.n > 0) return IPM_ERR_INVALID_ARG;
+    if (!(rho >= 0.0) || !(delta >= 0.0) || !std::isfinite(rho) || !std::isfinite(delta)) return IPM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (c->plan.n > 0 && theta_dev != c->theta) {
+        cudaError_t e = cudaMemcpyAsync(c->theta, theta_dev, c->plan.n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return to_err(e);
+    }
+    c->rho = rho;
+    c->delta = delta;
+    rc = factorise_enqueue(c, c->theta, rho, delta, st);
+    if (rc) return rc;
+    c->factorised = true;
+    return IPM_OK;
+}
+
+static int read_ctl(ipm_ctx *c, cudaStream_t st, DevCtl *h) {
+    cudaError_t e = cudaMemcpyAsync(h, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return to_err(e);
+    c->status_acc |= h->status;
+    return IPM_OK;
+}
+
+int ipm_solve(ipm_ctx *c, const double *r7, const double *r1, double *dx, double *dy, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->factorised) return IPM_ERR_NOT_FACTORISED;
+    const Plan &P = c->plan;
+    if ((P.n > 0 && (!r7 || !dx)) || (P.m > 0 && (!r1 || !dy))) return IPM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t N = P.N;
+    DevVals V{};
+    V.Ax = c->Ax;
+    V.theta = c->theta;
+    V.rho = c->rho;
+    V.delta = c->delta;
+    int nl = 0;
+    launch_permute_in(c->dp, r7, r1, c->vf, st);
+    nl++;
+    cudaMemcpyAsync(c->vx, c->vf, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if ((rc = solve_inplace(c, c->vx, st, &nl))) return rc;
+    launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st);
+    nl += 2;
+    DevCtl h{};
+    if ((rc = read_ctl(c, st, &h))) return rc;
+    double wbest = h.omega;
+    cudaMemcpyAsync(c->vbest, c->vx, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    int steps = 0;
+    c->omega_hist[0] = h.omega;
+    const double target = c->opt.omega_target;
+    while (wbest > target && steps < c->opt.refine_max && !(h.status & kStatNonFinite)) {
+        cudaMemcpyAsync(c->vc, c->vr, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if ((rc = solve_inplace(c, c->vc, st, &nl))) return rc;
+        launch_axpy(c->vx, c->vc, N, st);
+        launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st);
+        nl += 3;
+        if ((rc = read_ctl(c, st, &h))) return rc;
+        steps++;
+        if (steps < 16) c->omega_hist[steps] = h.omega;
+        const bool halved = h.omega <= 0.5 * wbest;
+        if (h.omega < wbest) {
+            wbest = h.omega;
+            cudaMemcpyAsync(c->vbest, c->vx, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        }
+        if (!halved) break;
+    }
+    launch_permute_out(c->dp, c->vbest, dx, dy, st);
+    nl++;
+    c->refine_steps = steps;
+    c->omega = wbest;
+    if (wbest > target) c->status_acc |= kStatRefineFail;
+    c->nl_solve = nl;
+    return to_err(cudaGetLastError());
+}
+
+int ipm_iterate_host(ipm_ctx *c, const double *theta_h, double rho, double delta, int32_t nrhs, const double *r7_h,
+                     const double *r1_h, double *dx_h, double *dy_h, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->values_set) return IPM_ERR_NOT_ANALYSED;
+    const Plan &P = c->plan;
+    if (nrhs < 0 || (P.n > 0 && !theta_h) || (nrhs > 0 && ((P.n > 0 && (!r7_h || !dx_h)) || (P.m > 0 && (!r1_h || !dy_h)))))
+        return IPM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!c->d_r7) {
+        if ((rc = dalloc(c, &c->d_r7, P.n)) || (rc = dalloc(c, &c->d_r1, P.m)) || (rc = dalloc(c, &c->d_dx, P.n)) ||
+            (rc = dalloc(c, &c->d_dy, P.m)))
+            return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->theta, theta_h, P.n * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return to_err(e);
+    if ((rc = ipm_factorise(c, c->theta, rho, delta, stream))) return rc;
+    for (int32_t k = 0; k < nrhs; k++) {
+        cudaMemcpyAsync(c->d_r7, r7_h + (size_t)k * P.n, P.n * sizeof(double), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(c->d_r1, r1_h + (size_t)k * P.m, P.m * sizeof(double), cudaMemcpyHostToDevice, st);
+        if ((rc = ipm_solve(c, c->d_r7, c->d_r1, c->d_dx, c->d_dy, stream))) return rc;
+        cudaMemcpyAsync(dx_h + (size_t)k * P.n, c->d_dx, P.n * sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(dy_h + (size_t)k * P.m, c->d_dy, P.m * sizeof(double), cudaMemcpyDeviceToHost, st);
+    }
+    return ipm_sync_status(c, stream);
+}
+
+int ipm_sync_status(ipm_ctx *c, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->dev_ready) return IPM_OK;
+    DevCtl h{};
+    if ((rc = read_ctl(c, (cudaStream_t)stream, &h))) return rc;
+    c->last = h;
+    int32_t st = c->status_acc;
+    c->status_acc = 0;
+    cudaMemsetAsync(&c->ctl->status, 0, sizeof(int32_t), (cudaStream_t)stream);
+    cudaStreamSynchronize((cudaStream_t)stream);
+    return status_to_code(st);
+}
+
+int ipm_get_info(ipm_ctx *c, ipm_info *out) {
+    if (!c || !out) return IPM_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    const Plan &P = c->plan;
+    out->m = P.m;
+    out->n = P.n;
+    out->N = P.N;
+    out->form = P.form;
+    out->ordering = P.ordering;
+    out->nsuper = P.nsuper;
+    out->nlevels = P.nlevels;
+    out->nfronts_small = P.nsmall;
+    out->nfronts_large = P.nlarge;
+    out->max_front = P.max_f;
+    out->max_k = P.max_k;
+    out->nnz_A = P.Acp.empty() ? 0 : P.Acp[P.n];
+    out->nnz_K_lower = P.nnzK_lower;
+    out->nnz_L = P.nnzL;
+    out->flops_factor = P.flops;
+    out->device_bytes = c->device_bytes;
+    out->ms_analyse = c->ms_analyse;
+    out->refine_steps = c->refine_steps;
+    out->omega = c->omega;
+    for (int i = 0; i < 16; i++) out->omega_hist[i] = c->omega_hist[i];
+    if (!c->analysed) return IPM_ERR_NOT_ANALYSED;
+    int code = IPM_OK;
+    if (c->dev_ready) {
+        cudaSetDevice(c->opt.device);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return to_err(e);
+        DevCtl h{};
+        e = cudaMemcpy(&h, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return to_err(e);
+        c->status_acc |= h.status;
+        out->npos = h.npos;
+        out->nneg = h.nneg;
+        out->ndynreg = h.ndyn;
+        out->max_dynreg = h.max_dyn;
+        out->norm_K1 = h.norm1;
+        out->status = c->status_acc;
+        code = status_to_code(c->status_acc);
+    }
+    return code;
+}
+
+int ipm_get_sizes(const ipm_ctx *c, int32_t *N, int32_t *nsuper, int64_t *nrows_total, int64_t *nnz_L_stored) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    const Plan &P = c->plan;
+    if (N) *N = P.N;
+    if (nsuper) *nsuper = P.nsuper;
+    if (nrows_total) *nrows_total = P.sn_rptr[P.nsuper];
+    if (nnz_L_stored) {
+        int64_t t = 0;
+        for (int32_t s = 0; s < P.nsuper; s++) t += (int64_t)P.sn_f[s] * P.sn_k[s];
+        *nnz_L_stored = t;
+    }
+    return IPM_OK;
+}
+
+int ipm_get_symbolic(const ipm_ctx *c, int32_t *perm, int32_t *etree, int64_t *colcount, int32_t *snode_ptr,
+                     int32_t *sn_parent, int64_t *sn_rptr, int32_t *sn_rows) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    const Plan &P = c->plan;
+    if (perm) std::memcpy(perm, P.perm.data(), P.N * sizeof(int32_t));
+    if (etree) std::memcpy(etree, P.parent.data(), P.N * sizeof(int32_t));
+    if (colcount) std::memcpy(colcount, P.colcount.data(), P.N * sizeof(int64_t));
+    if (snode_ptr) std::memcpy(snode_ptr, P.sn_start.data(), (P.nsuper + 1) * sizeof(int32_t));
+    if (sn_parent) std::memcpy(sn_parent, P.sn_parent.data(), P.nsuper * sizeof(int32_t));
+    if (sn_rptr) std::memcpy(sn_rptr, P.sn_rptr.data(), (P.nsuper + 1) * sizeof(int64_t));
+    if (sn_rows) std::memcpy(sn_rows, P.sn_rows.data(), P.sn_rptr[P.nsuper] * sizeof(int32_t));
+    return IPM_OK;
+}
+
+int ipm_get_factor(ipm_ctx *c, double *L_host, double *D_host, double *dyn_host) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->factorised) return IPM_ERR_NOT_FACTORISED;
+    const Plan &P = c->plan;
+    cudaSetDevice(c->opt.device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return to_err(e);
+    if (D_host && (e = cudaMemcpy(D_host, c->D, P.N * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return to_err(e);
+    if (dyn_host && (e = cudaMemcpy(dyn_host, c->dyn, P.N * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return to_err(e);
+    if (L_host) {
+        std::vector<double> F((size_t)P.front_doubles);
+        if ((e = cudaMemcpy(F.data(), c->fronts, F.size() * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return to_err(e);
+        int64_t o = 0;
+        for (int32_t s = 0; s < P.nsuper; s++) {
+            const int32_t f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s];
+            const double *src = F.data() + P.sn_off[s];
+            for (int32_t jj = 0; jj < k; jj++)
+                for (int32_t ii = 0; ii < f; ii++)
+                    L_host[o + (int64_t)jj * f + ii] = ii > jj ? src[(int64_t)jj * ld + ii] : (ii == jj ? 1.0 : 0.0);
+            o += (int64_t)f * k;
+        }
+    }
+    return IPM_OK;
+}
+
+int ipm_graph_capture(ipm_ctx *c, const double *, double, double, const double *, const double *, double *, double *,
+                      int32_t, void *) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    return IPM_ERR_INVALID_ARG;
+}
+
+int ipm_graph_launch(ipm_ctx *c, void *) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    return IPM_ERR_INVALID_ARG;
+}
+
+int ipm_launch_counts(const ipm_ctx *c, int32_t *nf, int32_t *ns) {
+    if (!c) return IPM_ERR_INVALID_ARG;
+    if (nf) *nf = c->nl_factor;
+    if (ns) *ns = c->nl_solve;
+    return IPM_OK;
+}
+
+}  // extern "C"

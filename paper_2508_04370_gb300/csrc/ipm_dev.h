@@ -1,0 +1,103 @@
+// Device-side view of the analysis plan and kernel entry points of the
+// multifrontal factorise/solve (Zanetti & Gondzio, arXiv 2508.04370, Sec. 4).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ipm {
+
+// Status bits written by kernels (never traps): OR-ed into DevCtl::status.
+enum : int32_t {
+    kStatNonFinite = 1,    // NaN / Inf in Theta, a pivot or a residual
+    kStatDynReg = 2,       // a pivot was lifted
+    kStatLargeReg = 4,     // a lift exceeded opt.large_reg
+    kStatTimeout = 8,      // a bounded wait expired
+    kStatRefineFail = 16,  // refinement did not reach the target
+};
+
+// Small control block in device memory.
+struct DevCtl {
+    int32_t status;
+    int32_t ndyn;
+    int32_t npos, nneg;
+    double max_dyn;
+    double norm1;          // ||K||_1 (or ||M||_1) of the current factorisation
+    double b1;             // eps_piv * norm1
+    // refinement
+    double omega;          // backward error of the current iterate
+    double omega_best;
+    double dinf;           // ||d||_inf of the current iterate (as ordered bits >= 0)
+    int32_t done;          // refinement finished
+    int32_t steps;
+    double omega_hist[16];
+};
+
+// Read-only plan arrays on the device (all indices in factorisation order).
+struct DevPlan {
+    int32_t N, n, m, nsuper, form;
+    const int32_t *sn_c0, *sn_k, *sn_f, *sn_ld;
+    const int64_t *sn_off;        // slab offset (doubles)
+    const int64_t *sn_rptr;       // row list offset
+    const int32_t *sn_rows;       // global row indices
+    const int32_t *child_ptr, *child_list;
+    const int64_t *map_off;
+    const int32_t *relmap;
+    const int64_t *orig_ptr;
+    const int32_t *orig_dst;
+    const int64_t *orig_src;
+    const int8_t *sign;           // expected pivot sign per row (-1 / +1)
+    const int32_t *perm;          // perm[new] = old
+    const int64_t *upd_off;       // solve: contribution-vector offsets
+    // regularised matrix in factorisation order, full symmetric CSR (for
+    // residuals): value source per entry (>= 0: A index, -1-j: primal
+    // diagonal of old column j, kDualDiag: delta)
+    const int64_t *kp;
+    const int32_t *kj;
+    const int64_t *ksrc;
+};
+
+constexpr int64_t kDualDiag = INT64_MIN;
+
+// Numeric values for one factorisation.
+struct DevVals {
+    const double *Ax;      // A values (CSC order of the pattern)
+    const double *theta;   // n
+    const double *nev;     // normal equations: lower entries of M (or null)
+    double rho, delta;
+    double large_reg;
+};
+
+// Work item of the large-front path.
+struct PanelItem {
+    int32_t s;       // supernode
+    int32_t r0, r1;  // row range (local) handled by this block
+};
+struct TileItem {
+    int32_t s;
+    int32_t i0, j0;  // local row / column of a 64 x 64 output tile
+};
+
+// ---------------------------------------------------------------- launches
+// factorisation (kernels_factor.cu)
+void launch_norm1(const DevPlan &P, const DevVals &V, DevCtl *ctl, double eps_piv, cudaStream_t st);
+void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *dyn, DevCtl *ctl,
+                         const int32_t *list, int32_t count, int32_t nb, int32_t maxf, cudaStream_t st);
+void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, const PanelItem *items,
+                           int32_t count, cudaStream_t st);
+void launch_large_panel(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *dyn, DevCtl *ctl,
+                        const PanelItem *items, int32_t count, int32_t p0, int32_t nb, cudaStream_t st);
+void launch_large_update(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
+                         int32_t p0, int32_t w, cudaStream_t st);
+void launch_factor_stats(const double *D, const double *dyn, int N, double large_reg, DevCtl *ctl, cudaStream_t st);
+// solves and refinement (kernels_solve.cu)
+void launch_forward(const DevPlan &P, const double *fronts, const double *D, double *x, double *upd,
+                    const int32_t *list, int32_t count, int32_t maxf, cudaStream_t st);
+void launch_backward(const DevPlan &P, const double *fronts, double *x, const int32_t *list, int32_t count,
+                     int32_t maxf, cudaStream_t st);
+void launch_permute_in(const DevPlan &P, const double *r7, const double *r1, double *f, cudaStream_t st);
+void launch_permute_out(const DevPlan &P, const double *x, double *dx, double *dy, cudaStream_t st);
+void launch_residual_omega(const DevPlan &P, const DevVals &V, const double *f, const double *x, double *r,
+                           double *ad, double *ae, DevCtl *ctl, cudaStream_t st);
+void launch_axpy(double *x, const double *c, int32_t N, cudaStream_t st);
+
+}  // namespace ipm

@@ -1,0 +1,158 @@
+"""CPU tests of the library's host side: the shared library loads and exports
+every symbol include/ipm_mf.h declares, and the symbolic analysis (Sec.
+4.2-4.3) is bit-exact with the oracle's by-definition symbolic analysis for
+the same fill-reducing order.  No GPU call is made here."""
+import ctypes as ct
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import FORM_AS, Oracle
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2508_04370_gb300.build import build
+
+    build()
+    import paper_2508_04370_gb300 as pkg
+
+    return pkg
+
+
+def test_exports_every_declared_symbol(lib):
+    names = lib.declared_symbols()
+    assert len(names) >= 17
+    so = lib.library()
+    for name in names:
+        assert hasattr(so, name), name
+
+
+def _analyse(lib, lp, ordering, perm=None):
+    ctx = lib.ipm_create()
+    rc = lib.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, lib.IPM_FORM_AUGMENTED, ordering, perm)
+    return ctx, rc
+
+
+def _compare_with_oracle(lib, ctx, lp):
+    sym = lib.ipm_get_symbolic(ctx)
+    o = Oracle.from_lp(lp, form=FORM_AS)
+    s = o.analyse(sym["perm"])
+    assert np.array_equal(s["perm"], sym["perm"])
+    assert np.array_equal(s["parent"], sym["etree"])
+    assert np.array_equal(s["colcount"], sym["colcount"])
+    assert np.array_equal(s["sn_start"], sym["snode_ptr"])
+    assert np.array_equal(s["sn_parent"], sym["sn_parent"])
+    assert np.array_equal(s["sn_rptr"], sym["sn_rptr"])
+    assert np.array_equal(s["sn_rows"], sym["sn_rows"])
+    return sym
+
+
+@pytest.mark.parametrize("ordering", [0, 1, 3])
+def test_symbolic_bit_exact_random(lib, ordering):
+    for seed in range(3):
+        lp = synth.random_lp(60 + 20 * seed, 150 + 40 * seed, 4, seed=seed)
+        ctx, rc = _analyse(lib, lp, ordering)
+        assert rc == 0
+        _compare_with_oracle(lib, ctx, lp)
+        lib.ipm_destroy(ctx)
+
+
+def test_symbolic_bit_exact_user_perm(lib):
+    lp = synth.random_lp(50, 120, 4, seed=9)
+    perm = synth.random_perm(lp.m + lp.n, 9)
+    ctx, rc = _analyse(lib, lp, lib.IPM_ORD_USER, perm)
+    assert rc == 0
+    sym = lib.ipm_get_symbolic(ctx)
+    # both sides compose the same user order with the same postorder
+    o = Oracle.from_lp(lp)
+    s = o.analyse(perm)
+    assert np.array_equal(s["perm"], sym["perm"])
+    _compare_with_oracle(lib, ctx, lp)
+    lib.ipm_destroy(ctx)
+
+
+def test_symbolic_bit_exact_config1_and_grid(lib):
+    for lp, ordering in ((synth.by_name("random_300x800"), 0), (synth.grid_multicommodity(12, 2), 0),
+                         (synth.grid_multicommodity(12, 2), 1)):
+        ctx, rc = _analyse(lib, lp, ordering)
+        assert rc == 0
+        _compare_with_oracle(lib, ctx, lp)
+        lib.ipm_destroy(ctx)
+
+
+def test_amd_fill_beats_natural_order(lib):
+    lp = synth.grid_multicommodity(16, 2)
+    nnz = {}
+    for ordering in (0, 1, 3):
+        ctx, rc = _analyse(lib, lp, ordering)
+        assert rc == 0
+        rc, info = lib.ipm_get_info(ctx)
+        nnz[ordering] = info.nnz_L
+        lib.ipm_destroy(ctx)
+    assert nnz[0] < nnz[3] / 3
+    assert nnz[1] < nnz[3] / 3
+
+
+def test_batch_analysis_is_block_diagonal_lp(lib):
+    lps = [synth.random_lp(20 + 5 * i, 50 + 9 * i, 3, seed=40 + i) for i in range(4)]
+    ctx = lib.ipm_create()
+    rc = lib.ipm_analyse_batch(ctx, [lp.m for lp in lps], [lp.n for lp in lps],
+                               np.concatenate([lp.colptr for lp in lps]),
+                               np.concatenate([lp.rowidx for lp in lps]), lib.IPM_ORD_AMD)
+    assert rc == 0
+    # the same block-diagonal LP assembled here
+    m = sum(lp.m for lp in lps)
+    n = sum(lp.n for lp in lps)
+    cols, rows = [], []
+    ro = co = 0
+    for lp in lps:
+        for j in range(lp.n):
+            for p in range(lp.colptr[j], lp.colptr[j + 1]):
+                rows.append(ro + lp.rowidx[p])
+                cols.append(co + j)
+        ro += lp.m
+        co += lp.n
+    big = synth.lp._from_coo(m, n, rows, cols, np.ones(len(rows)), "blockdiag")
+    ctx2, rc = _analyse(lib, big, lib.IPM_ORD_AMD)
+    assert rc == 0
+    a, b = lib.ipm_get_symbolic(ctx), lib.ipm_get_symbolic(ctx2)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+    _compare_with_oracle(lib, ctx, big)
+    lib.ipm_destroy(ctx)
+    lib.ipm_destroy(ctx2)
+
+
+def test_rejects_malformed_input(lib):
+    lp = synth.random_lp(10, 20, 3, seed=1)
+    ctx = lib.ipm_create()
+    bad = lp.rowidx.copy()
+    bad[0] = lp.m
+    assert lib.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, bad) == lib.IPM_ERR_INVALID_ARG
+    unsorted = lp.rowidx.copy()
+    unsorted[0], unsorted[1] = unsorted[1], unsorted[0]
+    assert lib.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, unsorted) == lib.IPM_ERR_INVALID_ARG
+    perm = np.zeros(lp.m + lp.n, np.int32)
+    assert lib.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, 1, lib.IPM_ORD_USER, perm) == lib.IPM_ERR_INVALID_ARG
+    # calls before analysis
+    assert lib.ipm_factorise(ctx, 0, 1e-8, 1e-8, stream=0) == lib.IPM_ERR_NOT_ANALYSED
+    lib.ipm_destroy(ctx)
+    opt = lib.ipm_default_options()
+    opt.nb = 48
+    with pytest.raises(RuntimeError):
+        lib.ipm_create(opt)
+
+
+def test_edge_patterns(lib):
+    # no constraints, one empty column, a single column
+    for m, n, cp, ri in ((0, 5, np.zeros(6, np.int64), np.zeros(0, np.int32)),
+                         (3, 4, np.array([0, 1, 1, 3, 4]), np.array([0, 1, 2, 2])),
+                         (1, 1, np.array([0, 1]), np.array([0]))):
+        ctx = lib.ipm_create()
+        rc = lib.ipm_analyse(ctx, m, n, cp, ri)
+        assert rc == 0
+        lp = synth.lp.LP(m, n, np.asarray(cp, np.int64), np.asarray(ri, np.int32), np.ones(len(ri)))
+        _compare_with_oracle(lib, ctx, lp)
+        lib.ipm_destroy(ctx)
