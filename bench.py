@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the IPM linear-algebra hot path on one GB300.
+
+One step = one IPM iteration's linear algebra on the grid multicommodity LP
+(64 x 64 grid, 4 commodities, m = 24,444, n = 64,512): numeric factorisation
+of the regularised augmented system for a new Theta (nested-dissection
+order), then two solves with iterative refinement (predictor and one
+corrector).  The metric is ms per IPM iteration (lower is better), reported
+for the FP64 path and, when built, the mixed-precision path; the headline
+`value` is the fastest path that reaches its backward-error target.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "grid64_q4"
+RHO = DELTA = 1e-8
+FP64_NOMINAL_TFLOPS = 1.25  # FP64 rate of a GB300 (profiling recipe's nominal table)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_desc(ordering_name):
+    return (f"grid multicommodity LP {WORKLOAD}: 64x64 4-neighbour grid, 4 commodities, m=24444, n=64512, "
+            f"entries +-1; Theta 10^U[-8,8]; rho=delta=1e-8; {ordering_name} ordering; one IPM iteration = "
+            f"factorise + 2 refined solves (predictor + 1 corrector)")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel):
+    """Per-launch DRAM bytes of a kernel class from a committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            table = json.load(fh)
+    except OSError:
+        return None
+    ent = table.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    try:
+        with open(src, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return ent["bytes_per_launch"] if sha == ent["source_sha"] else None
+
+
+def make_inputs(seed=1, nthetas=3):
+    import synth
+
+    lp = synth.by_name(WORKLOAD, seed)
+    thetas = [synth.theta_loguniform(lp.n, seed + t) for t in range(nthetas)]
+    rhs = [(synth.rhs_normal(lp.n, 10 + 2 * t), synth.rhs_normal(lp.m, 11 + 2 * t)) for t in range(2)]
+    return lp, thetas, rhs
+
+
+# ------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2508_04370_gb300 as pkg
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    lp, thetas, rhs = make_inputs()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    results = {}
+    precisions = [("fp64", pkg.IPM_PREC_FP64, 1e-12)]
+    ordering = pkg.IPM_ORD_ND
+    for pname, prec, target in precisions:
+        s = pkg.Solver.from_lp(lp, ordering=ordering, precision=prec, omega_target=target, device=dev.index)
+        th = [torch.as_tensor(t, device=dev) for t in thetas]
+        rr = [(torch.as_tensor(a, device=dev), torch.as_tensor(b, device=dev)) for a, b in rhs]
+        dx = torch.empty(lp.n, dtype=torch.float64, device=dev)
+        dy = torch.empty(lp.m, dtype=torch.float64, device=dev)
+        stream = torch.cuda.current_stream()
+
+        def step(i):
+            pkg.ipm_factorise(s.ctx, th[i % len(th)], RHO, DELTA, stream)
+            for a, b in rr:
+                rc = pkg.ipm_solve(s.ctx, a, b, dx, dy, stream)
+                if rc < 0:
+                    raise RuntimeError(f"ipm_solve failed ({rc})")
+
+        for i in range(args.warmup):
+            step(i)
+        torch.cuda.synchronize()
+        pkg.ipm_kernel_stats(s.ctx, reset=True)
+        pkg.ipm_set_profiling(s.ctx, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        omegas = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[i][0].record(stream)
+            step(i)
+            ev[i][1].record(stream)
+            omegas.append(s.info()["omega"])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop()
+        pkg.ipm_set_profiling(s.ctx, False)
+        kstats = pkg.ipm_kernel_stats(s.ctx, reset=True)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        info = s.info()
+        # end to end through the host-buffer entry point
+        r7h = np.ascontiguousarray(np.concatenate([a for a, _ in rhs]))
+        r1h = np.ascontiguousarray(np.concatenate([b for _, b in rhs]))
+        dxh = np.empty(2 * lp.n)
+        dyh = np.empty(2 * lp.m)
+        thh = [np.ascontiguousarray(t) for t in thetas]
+        for i in range(max(1, args.warmup)):
+            pkg.ipm_iterate_host(s.ctx, thh[i % len(thh)], RHO, DELTA, r7h, r1h, dxh, dyh, nrhs=2, stream=stream)
+        torch.cuda.synchronize()
+        e2e = []
+        for i in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            rc = pkg.ipm_iterate_host(s.ctx, thh[i % len(thh)], RHO, DELTA, r7h, r1h, dxh, dyh, nrhs=2, stream=stream)
+            e2e.append((time.perf_counter() - t1) * 1e3)
+            if rc < 0:
+                raise RuntimeError(f"ipm_iterate_host failed ({rc})")
+        results[pname] = dict(step_ms=step_ms, wall_s=wall, kstats=kstats, info=info, omegas=omegas, clocks=clk,
+                              e2e_ms=e2e, target=target,
+                              h2d=8 * (lp.n + 2 * (lp.n + lp.m)), d2h=8 * 2 * (lp.n + lp.m))
+        s.close()
+    return lp, results
+
+
+def roofline(kstats, peaks, sustained):
+    """Dominant kernel class of the timed region and its achieved rate."""
+    name, st = max(((k, v) for k, v in kstats.items() if v["launches"] > 0), key=lambda kv: kv[1]["ms"])
+    avg_ms = st["ms"] / st["launches"]
+    if name in ("forward", "backward", "residual", "large_assemble", "other"):
+        achieved = st["bytes"] / st["launches"] / (avg_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+               "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    elif name == "large_update_tc":
+        achieved = st["flops"] / st["launches"] / (avg_ms * 1e-3) / 1e12
+        bf16 = peaks.get("bf16_tflops_sustained" if sustained else "bf16_tflops", 1900.0)
+        peak = bf16 / 2.0  # tf32 dense rate is half the bf16 rate (nominal 1.1 vs 2.25 PFLOP/s)
+        out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "peak_source": "measured bf16 x nominal tf32/bf16 ratio"}
+    else:
+        achieved = st["flops"] / st["launches"] / (avg_ms * 1e-3) / 1e12
+        out = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+               "peak_source": "nominal FP64 (152 SMs x 2.07 GHz x 2 FMA/clk/SM x 2)"}
+    out["frac"] = out["achieved"] / out["peak"]
+    out["kernel"] = name
+    out["launches"] = st["launches"]
+    out["avg_launch_ms"] = avg_ms
+    out["share_of_step"] = None
+    out["traffic"] = traffic_for(name)
+    return out
+
+
+def cpu_baseline(lp, thetas, rhs, ordering_perm, budget_s=12.0):
+    """The oracle as it stands, single thread, on the same workload."""
+    from oracle import Oracle
+
+    o = Oracle.from_lp(lp)
+    o.analyse(ordering_perm)
+    times = []
+    t_end = time.perf_counter() + budget_s
+    i = 0
+    while True:
+        t0 = time.perf_counter()
+        o.factorise(thetas[i % len(thetas)], RHO, DELTA)
+        for a, b in rhs:
+            o.solve(a, b, omega_target=1e-12, max_steps=10)
+        times.append((time.perf_counter() - t0) * 1e3)
+        i += 1
+        if time.perf_counter() > t_end or i >= 50:
+            break
+    return float(np.median(times)), i
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    if rank == 0:
+        from paper_2508_04370_gb300.build import build
+
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    lp, results = run_ours(args, rank, world)
+    import paper_2508_04370_gb300 as pkg
+
+    peaks = load_peaks()
+    # the headline: fastest path that met its target
+    best = None
+    per = {}
+    for pname, r in results.items():
+        ms = float(np.sum(r["step_ms"]) / len(r["step_ms"]))
+        ok = max(r["omegas"]) <= r["target"]
+        fl = r["info"]["flops_factor"]
+        fact_ms = r["kstats"]
+        per[pname] = {"ms_per_iter": ms, "met_target": bool(ok), "omega_max": max(r["omegas"]),
+                      "omega_target": r["target"], "refine_steps_last": r["info"]["refine_steps"],
+                      "front_flops": fl, "e2e_ms_per_iter": float(np.median(r["e2e_ms"]))}
+        fms = sum(v["ms"] for k, v in r["kstats"].items()
+                  if k in ("small_fronts", "large_assemble", "large_panel", "large_update", "large_update_tc"))
+        per[pname]["factorise_kernel_ms_per_iter"] = fms / len(r["step_ms"])
+        per[pname]["front_gflops"] = fl / (fms / len(r["step_ms"]) * 1e-3) / 1e9 if fms > 0 else None
+        per[pname]["kernels"] = {k: {"launches": v["launches"], "ms": round(v["ms"], 4)}
+                                 for k, v in r["kstats"].items() if v["launches"]}
+        if ok and (best is None or ms < per[best]["ms_per_iter"]):
+            best = pname
+    if best is None:
+        best = next(iter(results))
+    r = results[best]
+    ms_local = per[best]["ms_per_iter"]
+    if world > 1:
+        t = torch.tensor([ms_local], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    else:
+        ms_max = ms_local
+    value = ms_max / world  # replicas: whole-job ms per IPM iteration
+    launches = sum(v["launches"] for v in r["kstats"].values())
+    rl = roofline(r["kstats"], peaks, sustained=False)
+    step_total = float(np.sum(r["step_ms"]))
+    rl["share_of_step"] = r["kstats"][rl["kernel"]]["ms"] / step_total if step_total > 0 else None
+    out = {
+        "metric": "factorise+solve ms per IPM iteration (front GFLOP/s alongside), mixed vs FP64 at backward error",
+        "value": value,
+        "unit": "ms",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if best == "fp64" else "f64+tf32",
+        "data": "synthetic",
+        "config": {"workload": workload_desc("nested-dissection"), "path": best,
+                   "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "paths": per,
+        "roofline": rl,
+        "gpu_launches": int(launches),
+        "clocks": r["clocks"],
+        "e2e": {"value": float(np.median(r["e2e_ms"])), "unit": "ms",
+                "h2d_bytes_per_step": int(r["h2d"]), "d2h_bytes_per_step": int(r["d2h"])},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, thetas, rhs = make_inputs()
+        s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND)
+        perm = s.symbolic()["perm"]
+        s.close()
+        v, n = cpu_baseline(lp, thetas, rhs, perm)
+        out["cpu_baseline"] = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                               "sample": f"{n} full IPM iterations of the same workload (factorise + 2 refined "
+                                         f"solves), median; symbolic analysis excluded"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    """The oracle (plain C, one host core) timed on this arm's workload."""
+    if rank != 0:
+        return
+    import paper_2508_04370_gb300 as pkg
+    from oracle import Oracle
+
+    lp, thetas, rhs = make_inputs()
+    ctx = pkg.ipm_create()
+    pkg.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, pkg.IPM_FORM_AUGMENTED, pkg.IPM_ORD_ND)
+    perm = pkg.ipm_get_symbolic(ctx)["perm"]
+    pkg.ipm_destroy(ctx)
+    o = Oracle.from_lp(lp)
+    o.analyse(perm)
+
+    def step(i):
+        o.factorise(thetas[i % len(thetas)], RHO, DELTA)
+        for a, b in rhs:
+            o.solve(a, b, omega_target=1e-12, max_steps=10)
+
+    for i in range(args.warmup):
+        step(i)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        step(i)
+        times.append((time.perf_counter() - t0) * 1e3)
+    v = float(np.mean(times))
+    out = {"impl": "reference", "metric": "factorise+solve ms per IPM iteration (front GFLOP/s alongside), mixed vs "
+           "FP64 at backward error", "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_desc("nested-dissection"), "path": "oracle"},
+           "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} full IPM iterations (factorise + 2 refined solves)"},
+           "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

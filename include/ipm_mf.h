@@ -81,7 +81,8 @@ typedef struct ipm_options {
     int32_t nb;               /* pivot-block width (Sec. 4.4 "32, 64 or 128"); default 32 */
     int32_t amalg_width;      /* merge a child into its parent when the width stays <= this; 16 */
     double amalg_zero_frac;   /* ... or when explicit zeros stay <= this fraction; 0.05 */
-    double eps_piv;           /* dynamic-regularisation floor eps_piv * ||K||_1 (Sec. 4.5); 1e-14 */
+    double eps_piv;           /* dynamic-regularisation floor eps_piv * ||K||_1 (Sec. 4.5: "of the order of
+                                 magnitude of machine precision"); 2.220446049250313e-16 */
     double large_reg;         /* a lift larger than this raises IPM_WARN_LARGE_REG; 1e-4 */
     int32_t precision;        /* IPM_PREC_FP64 or IPM_PREC_MIXED; FP64 */
     int32_t mixed_min_front;  /* mixed path: fronts with f >= this use tensor-core updates; 256 */
@@ -217,6 +218,34 @@ int ipm_graph_launch(ipm_ctx *ctx, void *stream);
 /* Number of kernel launches enqueued by the last ipm_factorise and the last
  * ipm_solve (for launch accounting). */
 int ipm_launch_counts(const ipm_ctx *ctx, int32_t *factorise_launches, int32_t *solve_launches);
+
+/* ------------------------------------------------------------ measurement */
+/* Kernel classes reported by ipm_kernel_stats. */
+#define IPM_K_SMALL_FRONTS 0   /* fused assemble+factorise of fronts f <= 128 (shared memory) */
+#define IPM_K_LARGE_ASSEMBLE 1 /* extend-add into large fronts */
+#define IPM_K_LARGE_PANEL 2    /* pivot block + triangular solve of a 32-column panel */
+#define IPM_K_LARGE_UPDATE 3   /* trailing (Schur-complement) update, FP64 */
+#define IPM_K_LARGE_UPDATE_TC 4 /* trailing update on tensor cores (mixed precision) */
+#define IPM_K_FORWARD 5        /* forward + diagonal solve of one tree level */
+#define IPM_K_BACKWARD 6       /* backward solve of one tree level */
+#define IPM_K_RESIDUAL 7       /* residual, |K||x|, |K|e and backward error */
+#define IPM_K_OTHER 8          /* norms, statistics, permutations, vector updates */
+#define IPM_K_COUNT 9
+
+typedef struct ipm_kernel_stat {
+    int64_t launches;  /* launches recorded since the last reset */
+    double ms;         /* summed device time between CUDA events around each launch */
+    double flops;      /* algorithmic floating-point operations of those launches */
+    double bytes;      /* algorithmic HBM bytes of those launches */
+} ipm_kernel_stat;
+
+/* Enable (1) or disable (0) per-launch CUDA events for ipm_kernel_stats.
+ * Events are recorded on the stream each kernel is launched on. */
+int ipm_set_profiling(ipm_ctx *ctx, int32_t enable);
+
+/* Synchronise, fold the recorded events into per-class totals and copy
+ * IPM_K_COUNT entries to out (host array); reset != 0 clears the totals. */
+int ipm_kernel_stats(ipm_ctx *ctx, ipm_kernel_stat *out, int32_t reset);
 
 #ifdef __cplusplus
 }

@@ -125,7 +125,7 @@ class Oracle:
                                   out["sn_parent"], out["sn_rptr"], out["sn_rows"])
         return out
 
-    def factorise(self, theta, rho, delta, eps_piv=1e-14):
+    def factorise(self, theta, rho, delta, eps_piv=2.220446049250313e-16):
         rc = self.lib.orc_factorise(self.h, _c(theta, np.float64), float(rho), float(delta), float(eps_piv))
         self.theta = _c(theta, np.float64)
         self.rho, self.delta = float(rho), float(delta)

@@ -80,6 +80,13 @@ class ipm_info(ct.Structure):
         return d
 
 
+class ipm_kernel_stat(ct.Structure):
+    _fields_ = [("launches", ct.c_int64), ("ms", ct.c_double), ("flops", ct.c_double), ("bytes", ct.c_double)]
+
+
+KERNEL_CLASSES = ["small_fronts", "large_assemble", "large_panel", "large_update", "large_update_tc", "forward",
+                  "backward", "residual", "other"]
+
 _lib = None
 
 
@@ -111,9 +118,12 @@ def _load():
     lib.ipm_graph_capture.argtypes = [P, P, ct.c_double, ct.c_double, P, P, P, P, ct.c_int32, P]
     lib.ipm_graph_launch.argtypes = [P, P]
     lib.ipm_launch_counts.argtypes = [P, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]
+    lib.ipm_set_profiling.argtypes = [P, ct.c_int32]
+    lib.ipm_kernel_stats.argtypes = [P, P, ct.c_int32]
     for name in ("ipm_create", "ipm_destroy", "ipm_analyse", "ipm_analyse_batch", "ipm_set_values", "ipm_factorise",
                  "ipm_solve", "ipm_iterate_host", "ipm_sync_status", "ipm_get_info", "ipm_get_symbolic",
-                 "ipm_get_sizes", "ipm_get_factor", "ipm_graph_capture", "ipm_graph_launch", "ipm_launch_counts"):
+                 "ipm_get_sizes", "ipm_get_factor", "ipm_graph_capture", "ipm_graph_launch", "ipm_launch_counts",
+                 "ipm_set_profiling", "ipm_kernel_stats"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -271,6 +281,20 @@ def ipm_launch_counts(ctx):
     a, b = ct.c_int32(), ct.c_int32()
     _load().ipm_launch_counts(ctx, ct.byref(a), ct.byref(b))
     return a.value, b.value
+
+
+def ipm_set_profiling(ctx, enable=True) -> int:
+    return _load().ipm_set_profiling(ctx, 1 if enable else 0)
+
+
+def ipm_kernel_stats(ctx, reset=False):
+    """Per kernel class: dict(launches, ms, flops, bytes)."""
+    arr = (ipm_kernel_stat * len(KERNEL_CLASSES))()
+    rc = _load().ipm_kernel_stats(ctx, ct.cast(arr, ct.c_void_p), 1 if reset else 0)
+    if rc:
+        raise RuntimeError(f"ipm_kernel_stats failed ({rc})")
+    return {name: dict(launches=a.launches, ms=a.ms, flops=a.flops, bytes=a.bytes)
+            for name, a in zip(KERNEL_CLASSES, arr)}
 
 
 def declared_symbols():

@@ -21,12 +21,17 @@ using namespace ipm;
 
 namespace {
 
+// Algorithmic work of one launch (for the per-kernel roofline).
+struct Work {
+    double flops = 0.0, bytes = 0.0;
+};
 struct StepWork {
     int32_t p0;
     int64_t panel_off;
     int32_t panel_cnt;
     int64_t tile_off;
     int32_t tile_cnt;
+    Work panel_w, tile_w;
 };
 struct LevelWork {
     int64_t small_off;
@@ -36,6 +41,13 @@ struct LevelWork {
     int64_t asm_off;
     int32_t asm_cnt;
     std::vector<StepWork> steps;
+    Work small_w, asm_w, fwd_w, bwd_w;
+};
+
+struct ProfRec {
+    int cls;
+    cudaEvent_t e0, e1;
+    double flops, bytes;
 };
 
 constexpr int kTile = 64;
@@ -60,6 +72,8 @@ struct ipm_ctx {
            *vc = nullptr, *upd = nullptr;
     double *h_r7 = nullptr, *h_r1 = nullptr, *d_r7 = nullptr, *d_r1 = nullptr, *d_dx = nullptr, *d_dy = nullptr;
     int32_t *lvl_small = nullptr, *lvl_all = nullptr;
+    int32_t *bwd_order = nullptr, *solve_sync = nullptr;
+    int32_t solve_maxf = 0, solve_grid = 0;
     PanelItem *asm_items = nullptr, *panel_items = nullptr;
     TileItem *tile_items = nullptr;
     std::vector<LevelWork> levels;
@@ -76,11 +90,67 @@ struct ipm_ctx {
     double ms_analyse = 0.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    // per-kernel-class measurement
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<ProfRec> prof_pending;
+    ipm_kernel_stat prof_tot[IPM_K_COUNT] = {};
+    Work resid_w;
 };
 
 namespace {
 
 int to_err(cudaError_t e) { return e == cudaSuccess ? IPM_OK : (e == cudaErrorMemoryAllocation ? IPM_ERR_OOM : IPM_ERR_CUDA); }
+
+cudaEvent_t next_event(ipm_ctx *c) {
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+// Brackets one launch with events on its stream when profiling is enabled.
+struct Prof {
+    ipm_ctx *c;
+    int cls;
+    double flops, bytes;
+    cudaStream_t st;
+    cudaEvent_t e0 = nullptr;
+    Prof(ipm_ctx *c_, int cls_, const Work &w, cudaStream_t st_) : c(c_), cls(cls_), flops(w.flops), bytes(w.bytes), st(st_) {
+        if (c->prof_on) {
+            e0 = next_event(c);
+            cudaEventRecord(e0, st);
+        }
+    }
+    ~Prof() {
+        if (c->prof_on) {
+            cudaEvent_t e1 = next_event(c);
+            cudaEventRecord(e1, st);
+            c->prof_pending.push_back({cls, e0, e1, flops, bytes});
+        }
+    }
+};
+
+void fold_profile(ipm_ctx *c) {
+    for (const ProfRec &r : c->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        ipm_kernel_stat &t = c->prof_tot[r.cls];
+        t.launches++;
+        t.ms += ms;
+        t.flops += r.flops;
+        t.bytes += r.bytes;
+    }
+    c->prof_pending.clear();
+    c->ev_used = 0;
+}
+
 
 template <typename T>
 int dalloc(ipm_ctx *c, T **p, size_t count) {
@@ -115,6 +185,10 @@ void free_device(ipm_ctx *c) {
     c->graph = nullptr;
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    c->ev_pool.clear();
+    c->ev_used = 0;
+    c->prof_pending.clear();
     if (c->h_r7) cudaFreeHost(c->h_r7);
     c->h_r7 = nullptr;
     c->device_bytes = 0;
@@ -192,6 +266,30 @@ int setup_device(ipm_ctx *c) {
             W.all_maxf = std::max(W.all_maxf, P.sn_f[P.lvl_large[t]]);
         }
         W.all_cnt = (int32_t)(lvl_all.size() - W.all_off);
+        // algorithmic work of the level's launches
+        for (int64_t t = W.all_off; t < (int64_t)lvl_all.size(); t++) {
+            const int32_t s = lvl_all[t];
+            const double f = P.sn_f[s], k = P.sn_k[s];
+            const double lnz = f * k - k * (k - 1) / 2;  // stored entries of L
+            Work fr;
+            for (int32_t i = 1; i <= P.sn_k[s]; i++) fr.flops += (f - i) * (f - i + 3);
+            fr.bytes = 8.0 * f * (f + 1) / 2 + 12.0 * (double)(P.orig_ptr[s + 1] - P.orig_ptr[s]);
+            for (int32_t q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
+                const double cc = P.sn_f[P.child_list[q]] - P.sn_k[P.child_list[q]];
+                fr.bytes += 8.0 * cc * (cc + 1) / 2 + 4.0 * cc;
+                fr.flops += cc * (cc + 1) / 2;
+            }
+            if (P.sn_f[s] <= kSmallFrontMax) {
+                W.small_w.flops += fr.flops;
+                W.small_w.bytes += fr.bytes;
+            } else {
+                W.asm_w.bytes += fr.bytes;
+            }
+            W.fwd_w.flops += 2.0 * (lnz - f);
+            W.fwd_w.bytes += 8.0 * lnz + 8.0 * (f + 2 * k);
+            W.bwd_w.flops += 2.0 * (lnz - f);
+            W.bwd_w.bytes += 8.0 * lnz + 8.0 * (f + k);
+        }
         // large fronts
         W.asm_off = (int64_t)asm_items.size();
         int32_t maxsteps = 0;
@@ -212,9 +310,15 @@ int setup_device(ipm_ctx *c) {
                 if (S.p0 >= k) continue;
                 const int32_t p1 = std::min(S.p0 + c->opt.nb, k);
                 if (p1 >= f) panel_items.push_back({s, p1, p1});
-                for (int32_t r = p1; r < f; r += 128) panel_items.push_back({s, r, std::min(r + 128, f)});
+                for (int32_t r = p1; r < f; r += kPanelRows) panel_items.push_back({s, r, std::min(r + kPanelRows, f)});
                 for (int32_t j0 = p1; j0 < f; j0 += kTile)
                     for (int32_t i0 = j0; i0 < f; i0 += kTile) tile_items.push_back({s, i0, j0});
+                const double w = p1 - S.p0, rest = f - p1;
+                // pivot block (w^3/3) + triangular solve of the rows below; update of the lower trailing part
+                S.panel_w.flops += w * w * w / 3.0 + rest * w * w;
+                S.panel_w.bytes += 16.0 * (f - S.p0) * w;
+                S.tile_w.flops += 2.0 * w * rest * (rest + 1) / 2;
+                S.tile_w.bytes += 16.0 * rest * (rest + 1) / 2 + 8.0 * rest * w;
             }
             S.panel_cnt = (int32_t)(panel_items.size() - S.panel_off);
             S.tile_cnt = (int32_t)(tile_items.size() - S.tile_off);
@@ -222,6 +326,8 @@ int setup_device(ipm_ctx *c) {
         }
     }
     std::vector<int64_t> upd_off(P.upd_off.begin(), P.upd_off.end());
+    std::vector<int32_t> bwd_order(lvl_all.rbegin(), lvl_all.rend());
+    c->solve_maxf = P.max_f;
     int rc = 0;
     int32_t *d_c0, *d_k, *d_f, *d_ld, *d_rows, *d_cptr, *d_clist, *d_relmap, *d_odst, *d_perm, *d_kj;
     int64_t *d_off, *d_rptr, *d_moff, *d_optr, *d_osrc, *d_uoff, *d_kp, *d_ksrc;
@@ -238,8 +344,19 @@ int setup_device(ipm_ctx *c) {
         (rc = dupload(c, &d_kj, kj)) || (rc = dupload(c, &d_ksrc, ksrc)) ||
         (rc = dupload(c, &c->lvl_small, P.lvl_small)) || (rc = dupload(c, &c->lvl_all, lvl_all)) ||
         (rc = dupload(c, &c->asm_items, asm_items)) || (rc = dupload(c, &c->panel_items, panel_items)) ||
-        (rc = dupload(c, &c->tile_items, tile_items)))
+        (rc = dupload(c, &c->tile_items, tile_items)) || (rc = dupload(c, &c->bwd_order, bwd_order)) ||
+        (rc = dalloc(c, &c->solve_sync, (size_t)ns + 1)))
         return rc;
+    int32_t *d_sparent;
+    if ((rc = dupload(c, &d_sparent, P.sn_parent))) return rc;
+    {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_probe_kernel(), 256,
+                                                      (size_t)P.max_f * sizeof(double));
+        c->solve_grid = std::max(1, std::min(ns, sms * std::max(1, per_sm)));
+    }
     DevPlan &dp = c->dp;
     dp.N = N;
     dp.n = P.n;
@@ -255,6 +372,7 @@ int setup_device(ipm_ctx *c) {
     dp.sn_rows = d_rows;
     dp.child_ptr = d_cptr;
     dp.child_list = d_clist;
+    dp.sn_parent = d_sparent;
     dp.map_off = d_moff;
     dp.relmap = d_relmap;
     dp.orig_ptr = d_optr;
@@ -276,6 +394,8 @@ int setup_device(ipm_ctx *c) {
         return rc;
     cudaMemset(c->ctl, 0, sizeof(DevCtl));
     cudaMemset(c->fronts, 0, (size_t)std::max<int64_t>(P.front_doubles, 1) * sizeof(double));
+    c->resid_w.flops = 6.0 * (double)kp[N];
+    c->resid_w.bytes = 20.0 * (double)kp[N] + 48.0 * N;
     c->dev_ready = true;
     return to_err(cudaGetLastError());
 }
@@ -292,49 +412,70 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
     int nl = 0;
     // reset the per-factorisation fields of the control block
     cudaMemsetAsync(&c->ctl->ndyn, 0, offsetof(DevCtl, omega) - offsetof(DevCtl, ndyn), st);
-    launch_norm1(c->dp, V, c->ctl, c->opt.eps_piv, st);
+    {
+        Prof pr(c, IPM_K_OTHER, Work(), st);
+        launch_norm1(c->dp, V, c->ctl, c->opt.eps_piv, st);
+    }
     nl += 2;
     for (int32_t l = 0; l < P.nlevels; l++) {
         const LevelWork &W = c->levels[l];
         if (W.small_cnt > 0) {
+            Prof pr(c, IPM_K_SMALL_FRONTS, W.small_w, st);
             launch_small_fronts(c->dp, V, c->fronts, c->D, c->dyn, c->ctl, c->lvl_small + W.small_off, W.small_cnt,
                                 c->opt.nb, W.small_maxf, st);
             nl++;
         }
         if (W.asm_cnt > 0) {
+            Prof pr(c, IPM_K_LARGE_ASSEMBLE, W.asm_w, st);
             launch_large_assemble(c->dp, V, c->fronts, c->asm_items + W.asm_off, W.asm_cnt, st);
             nl++;
         }
         for (const StepWork &S : W.steps) {
-            launch_large_panel(c->dp, V, c->fronts, c->D, c->dyn, c->ctl, c->panel_items + S.panel_off, S.panel_cnt,
-                               S.p0, c->opt.nb, st);
+            {
+                Prof pr(c, IPM_K_LARGE_PANEL, S.panel_w, st);
+                launch_large_panel(c->dp, V, c->fronts, c->D, c->dyn, c->ctl, c->panel_items + S.panel_off,
+                                   S.panel_cnt, S.p0, c->opt.nb, st);
+            }
             nl++;
             if (S.tile_cnt > 0) {
+                Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w, st);
                 launch_large_update(c->dp, c->fronts, c->D, c->tile_items + S.tile_off, S.tile_cnt, S.p0, c->opt.nb,
                                     st);
                 nl++;
             }
         }
     }
-    launch_factor_stats(c->D, c->dyn, P.N, c->opt.large_reg, c->ctl, st);
+    {
+        Prof pr(c, IPM_K_OTHER, Work(), st);
+        launch_factor_stats(c->D, c->dyn, P.N, c->opt.large_reg, c->ctl, st);
+    }
     nl++;
     c->nl_factor = nl;
     return to_err(cudaGetLastError());
 }
 
-// x <- (L D L^T)^-1 x in the factorisation order.
+// x <- (L D L^T)^-1 x in the factorisation order: one persistent launch per
+// sweep (dependency-driven, see kernels_solve.cu).
 int solve_inplace(ipm_ctx *c, double *x, cudaStream_t st, int *nl) {
     const Plan &P = c->plan;
-    for (int32_t l = 0; l < P.nlevels; l++) {
-        const LevelWork &W = c->levels[l];
-        launch_forward(c->dp, c->fronts, c->D, x, c->upd, c->lvl_all + W.all_off, W.all_cnt, W.all_maxf, st);
-        (*nl)++;
+    Work fw, bw;
+    for (const LevelWork &W : c->levels) {
+        fw.flops += W.fwd_w.flops;
+        fw.bytes += W.fwd_w.bytes;
+        bw.flops += W.bwd_w.flops;
+        bw.bytes += W.bwd_w.bytes;
     }
-    for (int32_t l = P.nlevels - 1; l >= 0; l--) {
-        const LevelWork &W = c->levels[l];
-        launch_backward(c->dp, c->fronts, x, c->lvl_all + W.all_off, W.all_cnt, W.all_maxf, st);
-        (*nl)++;
+    {
+        Prof pr(c, IPM_K_FORWARD, fw, st);
+        launch_forward_persistent(c->dp, c->fronts, c->D, x, c->upd, c->lvl_all, P.nsuper, c->solve_sync,
+                                  c->solve_maxf, c->solve_grid, c->ctl, st);
     }
+    {
+        Prof pr(c, IPM_K_BACKWARD, bw, st);
+        launch_backward_persistent(c->dp, c->fronts, x, c->bwd_order, P.nsuper, c->solve_sync, c->solve_maxf,
+                                   c->solve_grid, c->ctl, st);
+    }
+    *nl += 2;
     return to_err(cudaGetLastError());
 }
 
@@ -363,7 +504,7 @@ void ipm_default_options(ipm_options *o) {
     o->nb = 32;
     o->amalg_width = 16;
     o->amalg_zero_frac = 0.05;
-    o->eps_piv = 1e-14;
+    o->eps_piv = 2.220446049250313e-16;  // machine precision (Sec. 4.5)
     o->large_reg = 1e-4;
     o->precision = IPM_PREC_FP64;
     o->mixed_min_front = 256;
@@ -529,7 +670,10 @@ int ipm_solve(ipm_ctx *c, const double *r7, const double *r1, double *dx, double
     nl++;
     cudaMemcpyAsync(c->vx, c->vf, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if ((rc = solve_inplace(c, c->vx, st, &nl))) return rc;
-    launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st);
+    {
+        Prof pr(c, IPM_K_RESIDUAL, c->resid_w, st);
+        launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st);
+    }
     nl += 2;
     DevCtl h{};
     if ((rc = read_ctl(c, st, &h))) return rc;
@@ -542,7 +686,10 @@ int ipm_solve(ipm_ctx *c, const double *r7, const double *r1, double *dx, double
         cudaMemcpyAsync(c->vc, c->vr, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
         if ((rc = solve_inplace(c, c->vc, st, &nl))) return rc;
         launch_axpy(c->vx, c->vc, N, st);
-        launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st);
+        {
+            Prof pr(c, IPM_K_RESIDUAL, c->resid_w, st);
+            launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st);
+        }
         nl += 3;
         if ((rc = read_ctl(c, st, &h))) return rc;
         steps++;
@@ -727,5 +874,26 @@ int ipm_launch_counts(const ipm_ctx *c, int32_t *nf, int32_t *ns) {
     if (ns) *ns = c->nl_solve;
     return IPM_OK;
 }
+
+
+int ipm_set_profiling(ipm_ctx *c, int32_t enable) {
+    if (!c) return IPM_ERR_INVALID_ARG;
+    c->prof_on = enable != 0;
+    return IPM_OK;
+}
+
+int ipm_kernel_stats(ipm_ctx *c, ipm_kernel_stat *out, int32_t reset) {
+    if (!c) return IPM_ERR_INVALID_ARG;
+    if (c->dev_ready) {
+        cudaSetDevice(c->opt.device);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return to_err(e);
+    }
+    fold_profile(c);
+    if (out) std::memcpy(out, c->prof_tot, sizeof(c->prof_tot));
+    if (reset) std::memset(c->prof_tot, 0, sizeof(c->prof_tot));
+    return IPM_OK;
+}
+
 
 }  // extern "C"

@@ -40,6 +40,7 @@ struct DevPlan {
     const int64_t *sn_rptr;       // row list offset
     const int32_t *sn_rows;       // global row indices
     const int32_t *child_ptr, *child_list;
+    const int32_t *sn_parent;     // parent supernode or -1
     const int64_t *map_off;
     const int32_t *relmap;
     const int64_t *orig_ptr;
@@ -66,6 +67,9 @@ struct DevVals {
     double rho, delta;
     double large_reg;
 };
+
+// Rows of a panel handled by one CTA of the panel kernel (one thread per row).
+constexpr int kPanelRows = 64;
 
 // Work item of the large-front path.
 struct PanelItem {
@@ -94,6 +98,14 @@ void launch_forward(const DevPlan &P, const double *fronts, const double *D, dou
                     const int32_t *list, int32_t count, int32_t maxf, cudaStream_t st);
 void launch_backward(const DevPlan &P, const double *fronts, double *x, const int32_t *list, int32_t count,
                      int32_t maxf, cudaStream_t st);
+void launch_forward_persistent(const DevPlan &P, const double *fronts, const double *D, double *x, double *upd,
+                               const int32_t *order, int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid,
+                               DevCtl *ctl, cudaStream_t st);
+void launch_backward_persistent(const DevPlan &P, const double *fronts, double *x, const int32_t *order,
+                                int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid, DevCtl *ctl,
+                                cudaStream_t st);
+// kernel used to size the persistent sweeps' grid (occupancy query)
+const void *persistent_probe_kernel();
 void launch_permute_in(const DevPlan &P, const double *r7, const double *r1, double *f, cudaStream_t st);
 void launch_permute_out(const DevPlan &P, const double *x, double *dx, double *dy, cudaStream_t st);
 void launch_residual_omega(const DevPlan &P, const DevVals &V, const double *f, const double *x, double *r,

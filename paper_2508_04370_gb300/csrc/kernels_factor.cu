@@ -199,22 +199,22 @@ __global__ void __launch_bounds__(256) k_large_assemble(DevPlan P, DevVals V, do
 
 // Panel [p0, p1) of front s: every CTA factorises the nb x nb diagonal block
 // redundantly in shared memory (deterministic, identical results), then
-// solves its rows [r0, r1) of the panel below it; the CTA whose r0 is the
-// first row below the block writes the factorised diagonal block, D and the
-// lifts.
-constexpr int kPanelRows = 128;
-
+// solves its rows [r0, r1) of the panel below it by forward substitution
+// with L_DD and D (one reciprocal per pivot, W(q, p) = d_q L_pq staged in
+// shared memory); the CTA whose r0 is the first row below the block writes
+// the factorised diagonal block, D and the lifts.
 __global__ void __launch_bounds__(kPanelRows) k_large_panel(DevPlan P, DevVals V, double *__restrict__ fronts,
                                                              double *__restrict__ Dg, double *__restrict__ dyng,
                                                              DevCtl *ctl, const PanelItem *__restrict__ items,
                                                              int p0, int nb) {
     __shared__ double Fd[32 * 33];
+    __shared__ double Wd[32 * 33];
     __shared__ double wv[32];
-    __shared__ double dq[32];
+    __shared__ double dq[32], inv[32];
     __shared__ double Dtmp[32], dyntmp[32];
     const PanelItem it = items[blockIdx.x];
     const int s = it.s;
-    const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
+    const int k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
     const int p1 = min(p0 + nb, k);
     const int w = p1 - p0;
     double *F = fronts + P.sn_off[s];
@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(kPanelRows) k_large_panel(DevPlan P, DevVals V
     __syncthreads();
     const int8_t *sgn = P.sign + c0 + p0;
     const double b1floor = ctl->b1;
-    for (int p = 0; p < w; p++) {
-        if (warp == 0) {
+    if (warp == 0) {
+        for (int p = 0; p < w; p++) {
             double dn = decide_pivot(Fd, LDD, p, w, sgn, V.rho, V.delta, b1floor, lane, &Dtmp[p], &dyntmp[p], ctl);
             if (lane == 0) dq[p] = dn;
             if (lane > p && lane < w) {
@@ -243,18 +243,21 @@ __global__ void __launch_bounds__(kPanelRows) k_large_panel(DevPlan P, DevVals V
         }
     }
     __syncthreads();
-    // rows below the diagonal block: forward substitution with L_DD and D
+    for (int t = tid; t < w * w; t += kPanelRows) {
+        const int q = t / w, p = t % w;
+        Wd[q * LDD + p] = p > q ? dq[q] * Fd[q * LDD + p] : 0.0;
+    }
+    for (int t = tid; t < 32; t += kPanelRows) inv[t] = t < w ? 1.0 / dq[t] : 0.0;
+    __syncthreads();
     for (int i = it.r0 + tid; i < it.r1; i += kPanelRows) {
         double li[32];
 #pragma unroll
-        for (int p = 0; p < 32; p++) {
-            if (p < w) {
-                double acc = F[(int64_t)(p0 + p) * ld + i];
+        for (int p = 0; p < 32; p++) li[p] = p < w ? F[(int64_t)(p0 + p) * ld + i] : 0.0;
 #pragma unroll
-                for (int q = 0; q < 32; q++)
-                    if (q < p) acc -= li[q] * (dq[q] * Fd[q * LDD + p]);
-                li[p] = acc / dq[p];
-            }
+        for (int q = 0; q < 32; q++) {
+            li[q] *= inv[q];
+#pragma unroll
+            for (int p = q + 1; p < 32; p++) li[p] -= li[q] * Wd[q * LDD + p];
         }
 #pragma unroll
         for (int p = 0; p < 32; p++)
@@ -271,7 +274,6 @@ __global__ void __launch_bounds__(kPanelRows) k_large_panel(DevPlan P, DevVals V
             dyng[c0 + p0 + t] = dyntmp[t];
         }
     }
-    (void)f;
 }
 
 // Trailing update of the lower part of columns [p1, f) by the panel

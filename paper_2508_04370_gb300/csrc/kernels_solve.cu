@@ -32,15 +32,19 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // Forward: L y = b on the supernodes of one level, then y <- D^-1 y.
+// Columns are eliminated in blocks of 32: the 32 x 32 diagonal block of L is
+// staged in shared memory for the dependent triangle steps (one warp), then
+// all threads apply the block to the rows below it.
 __global__ void __launch_bounds__(kSolveThreads) k_forward(DevPlan P, const double *__restrict__ fronts,
                                                             const double *__restrict__ D, double *__restrict__ x,
                                                             double *__restrict__ upd,
                                                             const int32_t *__restrict__ list) {
     extern __shared__ double v[];
+    __shared__ double Lb[32 * 33];
     const int s = list[blockIdx.x];
     const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
     const double *L = fronts + P.sn_off[s];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int t = tid; t < f; t += kSolveThreads) v[t] = t < k ? x[c0 + t] : 0.0;
     __syncthreads();
     for (int q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
@@ -51,29 +55,29 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(DevPlan P, const doub
         for (int t = tid; t < cc; t += kSolveThreads) v[map[t]] += u[t];
         __syncthreads();
     }
-    const int lane = tid & 31, warp = tid >> 5;
-    // column-oriented elimination in blocks of 32 columns: warp 0 solves the
-    // 32 x 32 triangle, then all threads update the rows below the block
     for (int b0 = 0; b0 < k; b0 += 32) {
-        const int b1 = min(b0 + 32, k);
+        const int b1 = min(b0 + 32, k), w = b1 - b0;
+        for (int t = tid; t < w * w; t += kSolveThreads) {
+            const int jj = t / w, ii = t - jj * w;
+            if (ii > jj) Lb[jj * 33 + ii] = L[(int64_t)(b0 + jj) * ld + (b0 + ii)];
+        }
+        __syncthreads();
         if (warp == 0) {
-            for (int j = b0; j < b1; j++) {
-                const double yj = v[j];
-                __syncwarp();
-                const int i = j + 1 + lane;
-                if (i < b1) v[i] -= L[(int64_t)j * ld + i] * yj;
-                __syncwarp();
+            double vi = lane < w ? v[b0 + lane] : 0.0;
+            for (int j = 0; j < w; j++) {
+                const double yj = __shfl_sync(0xffffffffu, vi, j);
+                if (lane > j && lane < w) vi -= Lb[j * 33 + lane] * yj;
             }
+            if (lane < w) v[b0 + lane] = vi;
         }
         __syncthreads();
         for (int i = b1 + tid; i < f; i += kSolveThreads) {
             double acc = 0.0;
-            for (int j = b0; j < b1; j++) acc += L[(int64_t)j * ld + i] * v[j];
+            for (int j = 0; j < w; j++) acc += L[(int64_t)(b0 + j) * ld + i] * v[b0 + j];
             v[i] -= acc;
         }
         __syncthreads();
     }
-    (void)warp;
     for (int t = tid; t < f; t += kSolveThreads) {
         if (t < k) x[c0 + t] = v[t] / D[c0 + t];
         else upd[P.upd_off[s] + (t - k)] = v[t];
@@ -81,10 +85,14 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(DevPlan P, const doub
 }
 
 // Backward: L^T z = y on the supernodes of one level (ancestors are final).
+// Blocks of 32 columns from the last: first the contributions of all rows
+// below the block (one warp per column, coalesced), then the triangle with
+// the staged diagonal block, column by column (one warp, no reductions).
 __global__ void __launch_bounds__(kSolveThreads) k_backward(DevPlan P, const double *__restrict__ fronts,
                                                              double *__restrict__ x,
                                                              const int32_t *__restrict__ list) {
     extern __shared__ double z[];
+    __shared__ double Lb[32 * 33];
     const int s = list[blockIdx.x];
     const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
     const double *L = fronts + P.sn_off[s];
@@ -92,11 +100,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward(DevPlan P, const dou
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int t = tid; t < f; t += kSolveThreads) z[t] = t < k ? x[c0 + t] : x[rows[t]];
     __syncthreads();
-    // blocks of 32 columns from the last: the rows below the block are final
     const int nblk = (k + 31) / 32;
     for (int bb = nblk - 1; bb >= 0; bb--) {
-        const int b0 = bb * 32, b1 = min(b0 + 32, k);
-        // z_j -= sum_{i >= b1} L(i, j) z_i  for j in the block (one warp per column)
+        const int b0 = bb * 32, b1 = min(b0 + 32, k), w = b1 - b0;
+        for (int t = tid; t < w * w; t += kSolveThreads) {
+            const int jj = t / w, ii = t - jj * w;
+            if (ii > jj) Lb[jj * 33 + ii] = L[(int64_t)(b0 + jj) * ld + (b0 + ii)];
+        }
         for (int j = b0 + warp; j < b1; j += kSolveThreads / 32) {
             double acc = 0.0;
             for (int i = b1 + lane; i < f; i += 32) acc += L[(int64_t)j * ld + i] * z[i];
@@ -105,18 +115,166 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward(DevPlan P, const dou
         }
         __syncthreads();
         if (warp == 0) {
-            for (int j = b1 - 1; j >= b0; j--) {
-                double acc = 0.0;
-                const int i = j + 1 + lane;
-                if (i < b1) acc = L[(int64_t)j * ld + i] * z[i];
-                acc = warp_sum(acc);
-                if (lane == 0) z[j] -= acc;
-                __syncwarp();
+            double zi = lane < w ? z[b0 + lane] : 0.0;
+            for (int j = w - 1; j > 0; j--) {
+                const double zj = __shfl_sync(0xffffffffu, zi, j);
+                if (lane < j) zi -= Lb[lane * 33 + j] * zj;
             }
+            if (lane < w) z[b0 + lane] = zi;
         }
         __syncthreads();
     }
     for (int t = tid; t < k; t += kSolveThreads) x[c0 + t] = z[t];
+}
+
+// --------------------------------------------------------------------------
+// Persistent dependency-driven sweeps: one launch per forward or backward
+// pass instead of one per tree level.  CTAs take supernodes from an atomic
+// ticket in a topological order (forward: children before parents;
+// backward: parents before children).  Every dependency of a ticket holds a
+// smaller ticket, taken earlier by a running CTA, so waiting can always make
+// progress.  Waits are bounded: after kSpinLimit polls the CTA records
+// kStatTimeout and carries on, so the launch always terminates.
+// Values produced by other CTAs of the same launch are read with ld.global.cg
+// (L2, bypassing the non-coherent L1).
+constexpr long long kSpinLimit = 1ll << 24;
+
+__device__ __forceinline__ int ld_acquire(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void wait_count(const int32_t *cnt, int need, DevCtl *ctl) {
+    if (need <= 0) return;
+    long long spins = 0;
+    while (ld_acquire(cnt) < need) {
+        if (++spins > kSpinLimit) {
+            atomicOr(&ctl->status, kStatTimeout);
+            break;
+        }
+        __nanosleep(64);
+    }
+}
+
+__global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(DevPlan P, const double *__restrict__ fronts,
+                                                                       const double *__restrict__ D,
+                                                                       double *__restrict__ x, double *upd,
+                                                                       const int32_t *__restrict__ order, int nitems,
+                                                                       int32_t *ticket, int32_t *cnt, DevCtl *ctl) {
+    extern __shared__ double v[];
+    __shared__ double Lb[32 * 33];
+    __shared__ int item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (;;) {
+        if (tid == 0) item = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int t = item;
+        __syncthreads();
+        if (t >= nitems) break;
+        const int s = order[t];
+        const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
+        const double *L = fronts + P.sn_off[s];
+        if (tid == 0) wait_count(&cnt[s], P.child_ptr[s + 1] - P.child_ptr[s], ctl);
+        __syncthreads();
+        for (int q = tid; q < f; q += kSolveThreads) v[q] = q < k ? x[c0 + q] : 0.0;
+        __syncthreads();
+        for (int q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
+            const int c = P.child_list[q];
+            const int cc = P.sn_f[c] - P.sn_k[c];
+            const double *u = upd + P.upd_off[c];
+            const int32_t *map = P.relmap + P.map_off[c];
+            for (int r = tid; r < cc; r += kSolveThreads) v[map[r]] += __ldcg(u + r);
+            __syncthreads();
+        }
+        for (int b0 = 0; b0 < k; b0 += 32) {
+            const int b1 = min(b0 + 32, k), w = b1 - b0;
+            for (int q = tid; q < w * w; q += kSolveThreads) {
+                const int jj = q / w, ii = q - jj * w;
+                if (ii > jj) Lb[jj * 33 + ii] = L[(int64_t)(b0 + jj) * ld + (b0 + ii)];
+            }
+            __syncthreads();
+            if (warp == 0) {
+                double vi = lane < w ? v[b0 + lane] : 0.0;
+                for (int j = 0; j < w; j++) {
+                    const double yj = __shfl_sync(0xffffffffu, vi, j);
+                    if (lane > j && lane < w) vi -= Lb[j * 33 + lane] * yj;
+                }
+                if (lane < w) v[b0 + lane] = vi;
+            }
+            __syncthreads();
+            for (int i = b1 + tid; i < f; i += kSolveThreads) {
+                double acc = 0.0;
+                for (int j = 0; j < w; j++) acc += L[(int64_t)(b0 + j) * ld + i] * v[b0 + j];
+                v[i] -= acc;
+            }
+            __syncthreads();
+        }
+        for (int q = tid; q < f; q += kSolveThreads) {
+            if (q < k) x[c0 + q] = v[q] / D[c0 + q];
+            else __stcg(upd + P.upd_off[s] + (q - k), v[q]);
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const int pa = P.sn_parent[s];
+            if (pa >= 0) atomicAdd(&cnt[pa], 1);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(DevPlan P, const double *__restrict__ fronts,
+                                                                        double *x, const int32_t *__restrict__ order,
+                                                                        int nitems, int32_t *ticket, int32_t *flag,
+                                                                        DevCtl *ctl) {
+    extern __shared__ double z[];
+    __shared__ double Lb[32 * 33];
+    __shared__ int item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (;;) {
+        if (tid == 0) item = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int t = item;
+        __syncthreads();
+        if (t >= nitems) break;
+        const int s = order[t];
+        const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
+        const double *L = fronts + P.sn_off[s];
+        const int32_t *rows = P.sn_rows + P.sn_rptr[s];
+        const int pa = P.sn_parent[s];
+        if (tid == 0 && pa >= 0) wait_count(&flag[pa], 1, ctl);
+        __syncthreads();
+        for (int q = tid; q < f; q += kSolveThreads) z[q] = q < k ? __ldcg(x + c0 + q) : __ldcg(x + rows[q]);
+        __syncthreads();
+        const int nblk = (k + 31) / 32;
+        for (int bb = nblk - 1; bb >= 0; bb--) {
+            const int b0 = bb * 32, b1 = min(b0 + 32, k), w = b1 - b0;
+            for (int q = tid; q < w * w; q += kSolveThreads) {
+                const int jj = q / w, ii = q - jj * w;
+                if (ii > jj) Lb[jj * 33 + ii] = L[(int64_t)(b0 + jj) * ld + (b0 + ii)];
+            }
+            for (int j = b0 + warp; j < b1; j += kSolveThreads / 32) {
+                double acc = 0.0;
+                for (int i = b1 + lane; i < f; i += 32) acc += L[(int64_t)j * ld + i] * z[i];
+                acc = warp_sum(acc);
+                if (lane == 0) z[j] -= acc;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                double zi = lane < w ? z[b0 + lane] : 0.0;
+                for (int j = w - 1; j > 0; j--) {
+                    const double zj = __shfl_sync(0xffffffffu, zi, j);
+                    if (lane < j) zi -= Lb[lane * 33 + j] * zj;
+                }
+                if (lane < w) z[b0 + lane] = zi;
+            }
+            __syncthreads();
+        }
+        for (int q = tid; q < k; q += kSolveThreads) __stcg(x + c0 + q, z[q]);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicExch(&flag[s], 1);
+    }
 }
 
 // f (factorisation order) from [r7; r1] (original order).
@@ -209,6 +367,31 @@ void launch_backward(const DevPlan &P, const double *fronts, double *x, const in
                      int32_t maxf, cudaStream_t st) {
     if (count <= 0) return;
     k_backward<<<count, kSolveThreads, (size_t)maxf * sizeof(double), st>>>(P, fronts, x, list);
+}
+
+const void *persistent_probe_kernel() { return (const void *)k_forward_persistent; }
+
+void launch_forward_persistent(const DevPlan &P, const double *fronts, const double *D, double *x, double *upd,
+                               const int32_t *order, int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid,
+                               DevCtl *ctl, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_forward_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_backward_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    // sync[0] = ticket, sync[1 .. nsuper] = finished-children counters
+    cudaMemsetAsync(sync, 0, (size_t)(P.nsuper + 1) * sizeof(int32_t), st);
+    k_forward_persistent<<<grid, kSolveThreads, (size_t)maxf * sizeof(double), st>>>(P, fronts, D, x, upd, order,
+                                                                                      nitems, sync, sync + 1, ctl);
+}
+
+void launch_backward_persistent(const DevPlan &P, const double *fronts, double *x, const int32_t *order,
+                                int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid, DevCtl *ctl,
+                                cudaStream_t st) {
+    cudaMemsetAsync(sync, 0, (size_t)(P.nsuper + 1) * sizeof(int32_t), st);
+    k_backward_persistent<<<grid, kSolveThreads, (size_t)maxf * sizeof(double), st>>>(P, fronts, x, order, nitems,
+                                                                                       sync, sync + 1, ctl);
 }
 
 void launch_permute_in(const DevPlan &P, const double *r7, const double *r1, double *f, cudaStream_t st) {
