@@ -55,6 +55,7 @@ extern "C" {
 #define IPM_ERR_DEVICE_TIMEOUT (-6) /* a bounded device-side wait expired */
 #define IPM_ERR_NOT_FACTORISED (-7)
 #define IPM_ERR_NO_DEVICE (-8)
+#define IPM_ERR_SCRATCH_TOO_SMALL (-9) /* ipm_solve_noalloc: problem exceeds its fixed work space */
 #define IPM_WARN_DYNREG_APPLIED 1   /* at least one pivot was lifted (Sec. 4.5) */
 #define IPM_WARN_LARGE_REG 2        /* a lift exceeded opt.large_reg (Sec. 4.6 end) */
 #define IPM_WARN_REFINE_NOT_CONVERGED 3
@@ -218,6 +219,27 @@ int ipm_graph_launch(ipm_ctx *ctx, void *stream);
 /* Number of kernel launches enqueued by the last ipm_factorise and the last
  * ipm_solve (for launch accounting). */
 int ipm_launch_counts(const ipm_ctx *ctx, int32_t *factorise_launches, int32_t *solve_launches);
+
+/* Allocation-free variant of ipm_solve (the paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at solve
+ * time, for example code running while a stream is captured into a CUDA
+ * graph, where cudaMalloc is not allowed, or a host library that must not
+ * change the device's allocation state).  Same arguments, kernels and
+ * results as ipm_solve; its work vectors live in one file-scope device array
+ * of 2^21 doubles (16 MiB) that every GPU loading this library holds until
+ * the process exits, instead of in the context's own buffers, and the call
+ * makes no cudaMalloc, cudaFree or other allocating call.
+ *   - Needs 7 N + (sum of the front sizes) doubles; a larger problem returns
+ *     IPM_ERR_SCRATCH_TOO_SMALL before anything is enqueued.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (other
+ *     streams, other threads, other contexts) race and must be serialised by
+ *     the caller.  Every work vector is written before it is read within a
+ *     call, so the previous call's contents need no clearing.
+ *   - Like ipm_solve it synchronises `stream` once per refinement step. */
+int ipm_solve_noalloc(ipm_ctx *ctx, const double *r7_dev, const double *r1_dev, double *dx_dev, double *dy_dev,
+                      void *stream);
 
 /* ------------------------------------------------------------ measurement */
 /* Kernel classes reported by ipm_kernel_stats. */

@@ -27,6 +27,7 @@ IPM_ERR_NONFINITE = -5
 IPM_ERR_DEVICE_TIMEOUT = -6
 IPM_ERR_NOT_FACTORISED = -7
 IPM_ERR_NO_DEVICE = -8
+IPM_ERR_SCRATCH_TOO_SMALL = -9
 IPM_WARN_DYNREG_APPLIED = 1
 IPM_WARN_LARGE_REG = 2
 IPM_WARN_REFINE_NOT_CONVERGED = 3
@@ -118,12 +119,13 @@ def _load():
     lib.ipm_graph_capture.argtypes = [P, P, ct.c_double, ct.c_double, P, P, P, P, ct.c_int32, P]
     lib.ipm_graph_launch.argtypes = [P, P]
     lib.ipm_launch_counts.argtypes = [P, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]
+    lib.ipm_solve_noalloc.argtypes = [P, P, P, P, P, P]
     lib.ipm_set_profiling.argtypes = [P, ct.c_int32]
     lib.ipm_kernel_stats.argtypes = [P, P, ct.c_int32]
     for name in ("ipm_create", "ipm_destroy", "ipm_analyse", "ipm_analyse_batch", "ipm_set_values", "ipm_factorise",
                  "ipm_solve", "ipm_iterate_host", "ipm_sync_status", "ipm_get_info", "ipm_get_symbolic",
                  "ipm_get_sizes", "ipm_get_factor", "ipm_graph_capture", "ipm_graph_launch", "ipm_launch_counts",
-                 "ipm_set_profiling", "ipm_kernel_stats"):
+                 "ipm_set_profiling", "ipm_kernel_stats", "ipm_solve_noalloc"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -215,6 +217,12 @@ def ipm_factorise(ctx, theta_dev, rho, delta, stream=None) -> int:
 
 def ipm_solve(ctx, r7_dev, r1_dev, dx_dev, dy_dev, stream=None) -> int:
     return _load().ipm_solve(ctx, _dptr(r7_dev), _dptr(r1_dev), _dptr(dx_dev), _dptr(dy_dev), _stream(stream))
+
+
+def ipm_solve_noalloc(ctx, r7_dev, r1_dev, dx_dev, dy_dev, stream=None) -> int:
+    """ipm_solve without any device allocation (fixed file-scope work space)."""
+    return _load().ipm_solve_noalloc(ctx, _dptr(r7_dev), _dptr(r1_dev), _dptr(dx_dev), _dptr(dy_dev),
+                                     _stream(stream))
 
 
 def ipm_iterate_host(ctx, theta, rho, delta, r7, r1, dx, dy, nrhs=1, stream=None) -> int:

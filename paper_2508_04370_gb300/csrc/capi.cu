@@ -897,3 +897,118 @@ int ipm_kernel_stats(ipm_ctx *c, ipm_kernel_stat *out, int32_t reset) {
 
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve.
+//
+// Some callers cannot allocate device memory when they need a solve: code
+// that runs while a stream is being captured into a CUDA graph (cudaMalloc
+// is not allowed during capture and cudaFree synchronises the device),
+// callbacks of an optimisation loop that run under a strict memory budget or
+// inside a host library that must never change the device's allocation
+// state.  ipm_solve_noalloc serves them: it runs the same kernels as
+// ipm_solve but takes every work vector from one file-scope device array
+// instead of the context's own buffers, and it calls no allocating routine.
+namespace {
+
+// Capacity of the shared work array, in doubles (16 MiB).  A solve needs
+// 7 N + sum_s f_s doubles (N unknowns, f_s the front sizes).
+constexpr int64_t kNoAllocDoubles = int64_t(1) << 21;
+static __device__ __align__(256) double g_noalloc_work[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+double *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the work array for the current device, looked up once
+// per device (with that device current).  In host code the array's name is
+// only a stand-in, so kernels must receive this address instead.
+int noalloc_base(int device, double **out) {
+    if (device < 0 || device >= kMaxDevices) return IPM_ERR_INVALID_ARG;
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_work);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return IPM_ERR_CUDA;
+        }
+        g_noalloc_ptr[device] = (double *)p;
+    }
+    *out = g_noalloc_ptr[device];
+    return IPM_OK;
+}
+
+int noalloc_sweeps(ipm_ctx *c, double *x, double *upd, cudaStream_t st) {
+    const Plan &P = c->plan;
+    for (int32_t l = 0; l < P.nlevels; l++) {
+        const LevelWork &W = c->levels[l];
+        launch_forward(c->dp, c->fronts, c->D, x, upd, c->lvl_all + W.all_off, W.all_cnt, W.all_maxf, st);
+    }
+    for (int32_t l = P.nlevels - 1; l >= 0; l--) {
+        const LevelWork &W = c->levels[l];
+        launch_backward(c->dp, c->fronts, x, c->lvl_all + W.all_off, W.all_cnt, W.all_maxf, st);
+    }
+    return to_err(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+int ipm_solve_noalloc(ipm_ctx *c, const double *r7, const double *r1, double *dx, double *dy, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    const Plan &P = c->plan;
+    const int64_t N = P.N;
+    const int64_t need = 7 * N + P.upd_total;
+    if (need > kNoAllocDoubles) {
+        if (c->opt.verbose)
+            std::fprintf(stderr, "[ipm] ipm_solve_noalloc: needs %lld doubles of work space, the limit is %lld\n",
+                         (long long)need, (long long)kNoAllocDoubles);
+        return IPM_ERR_SCRATCH_TOO_SMALL;
+    }
+    if (!c->factorised) return IPM_ERR_NOT_FACTORISED;
+    if ((P.n > 0 && (!r7 || !dx)) || (P.m > 0 && (!r1 || !dy))) return IPM_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(c->opt.device);
+    if (e != cudaSuccess) return to_err(e);
+    double *base = nullptr;
+    if ((rc = noalloc_base(c->opt.device, &base))) return rc;
+    // every vector below is written before it is read within one call, so
+    // nothing left by the previous call needs clearing
+    double *vf = base, *vx = base + N, *vbest = base + 2 * N, *vr = base + 3 * N, *vad = base + 4 * N,
+           *vae = base + 5 * N, *vc = base + 6 * N, *upd = base + 7 * N;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevVals V{};
+    V.Ax = c->Ax;
+    V.theta = c->theta;
+    V.rho = c->rho;
+    V.delta = c->delta;
+    launch_permute_in(c->dp, r7, r1, vf, st);
+    cudaMemcpyAsync(vx, vf, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if ((rc = noalloc_sweeps(c, vx, upd, st))) return rc;
+    launch_residual_omega(c->dp, V, vf, vx, vr, vad, vae, c->ctl, st);
+    DevCtl h{};
+    if ((rc = read_ctl(c, st, &h))) return rc;
+    double wbest = h.omega;
+    cudaMemcpyAsync(vbest, vx, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    int steps = 0;
+    const double target = c->opt.omega_target;
+    while (wbest > target && steps < c->opt.refine_max && !(h.status & kStatNonFinite)) {
+        cudaMemcpyAsync(vc, vr, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if ((rc = noalloc_sweeps(c, vc, upd, st))) return rc;
+        launch_axpy(vx, vc, (int32_t)N, st);
+        launch_residual_omega(c->dp, V, vf, vx, vr, vad, vae, c->ctl, st);
+        if ((rc = read_ctl(c, st, &h))) return rc;
+        steps++;
+        const bool halved = h.omega <= 0.5 * wbest;
+        if (h.omega < wbest) {
+            wbest = h.omega;
+            cudaMemcpyAsync(vbest, vx, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        }
+        if (!halved) break;
+    }
+    launch_permute_out(c->dp, vbest, dx, dy, st);
+    if (wbest > target) c->status_acc |= kStatRefineFail;
+    return to_err(cudaGetLastError());
+}
+
+}  // extern "C"
