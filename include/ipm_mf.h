@@ -74,7 +74,12 @@ extern "C" {
 /* precision of the Schur-complement updates (Sec. 4.4 dgemm updates) */
 #define IPM_PREC_FP64 0    /* everything in FP64 */
 #define IPM_PREC_MIXED 1   /* FP32-accurate tensor-core updates on large fronts,
-                              FP64 pivots, regularisation, residual, refinement */
+                              FP64 pivots, regularisation, residual, refinement.
+                              If refinement cannot reach omega_target from such a
+                              factorisation (very wide Theta spreads), ipm_solve
+                              factorises again in FP64, solves again, and later
+                              factorisations stay in FP64 (an IPM's Theta spread
+                              only widens); ipm_info counts these fallbacks. */
 
 typedef struct ipm_ctx ipm_ctx;
 
@@ -113,6 +118,8 @@ typedef struct ipm_info {
     double ms_analyse;                      /* host wall time of ipm_analyse */
     double est_flops_ne, est_flops_as;      /* AS/NE chooser model (Sec. 4.2) */
     int64_t nnz_ne_seen;                    /* NE entries formed before the chooser stopped */
+    int32_t precision_fallbacks;            /* mixed path: refactorisations in FP64 so far */
+    int32_t mixed_active;                   /* 1 while tensor-core updates are in use */
 } ipm_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -208,10 +215,21 @@ int ipm_get_sizes(const ipm_ctx *ctx, int32_t *N, int32_t *nsuper, int64_t *nrow
  * dynreg_host have N entries in the factorisation order.  Synchronises. */
 int ipm_get_factor(ipm_ctx *ctx, double *L_host, double *D_host, double *dynreg_host);
 
-/* Capture ipm_factorise + ipm_solve (with the given pointers, which must stay
- * valid) into one CUDA graph owned by the context; ipm_graph_launch replays
- * it on any stream.  Replays read the pointed-to Theta and right-hand sides
- * afresh, so an IPM loop writes new values there and replays. */
+/* Capture one IPM iteration's linear algebra into one CUDA graph owned by the
+ * context (Sec. 4.2: the pattern and the symbolic analysis are reused by
+ * every iteration): a copy of Theta (device, n) into the context, the
+ * factorisation, then `nsolves` refined solves with right-hand side k at
+ * r7_dev + k*n, r1_dev + k*m and solution k at dx_dev + k*n, dy_dev + k*m
+ * (all device).  The pointers must stay valid; every replay reads Theta and
+ * the right-hand sides afresh, so an IPM loop writes new values there and
+ * calls ipm_graph_launch.  Inside the graph the refinement decisions are
+ * taken on the device: refine_max steps are captured and the kernels of a
+ * step exit at entry once omega <= omega_target, omega failed to halve or
+ * the step limit is reached.  A mixed-precision factorisation that cannot be
+ * refined to the target sets IPM_WARN_REFINE_NOT_CONVERGED (no fallback
+ * inside a graph).  Call after ipm_set_values.  The capture runs on a
+ * stream private to the context (`stream` is unused and may be NULL); the
+ * graph can then be launched on any stream. */
 int ipm_graph_capture(ipm_ctx *ctx, const double *theta_dev, double rho, double delta, const double *r7_dev,
                       const double *r1_dev, double *dx_dev, double *dy_dev, int32_t nsolves, void *stream);
 int ipm_graph_launch(ipm_ctx *ctx, void *stream);

@@ -27,21 +27,31 @@ struct Work {
 };
 struct StepWork {
     int32_t p0;
-    int64_t panel_off;
+    int64_t panel_off;  // diagonal-block items (one per front)
     int32_t panel_cnt;
+    int64_t trsm_off;   // row-chunk items below the diagonal blocks
+    int32_t trsm_cnt;
     int64_t tile_off;
     int32_t tile_cnt;
-    Work panel_w, tile_w;
+    int64_t tc_off;   // tensor-core tiles (mixed precision, large fronts)
+    int32_t tc_cnt;
+    int64_t alt_off;  // FP64 tiles of the same fronts, used after a precision fallback
+    int32_t alt_cnt;
+    Work panel_w, trsm_w, tile_w, tc_w;
+};
+struct SmallClass {
+    int64_t off;
+    int32_t cnt, maxf;
+    Work w;
 };
 struct LevelWork {
-    int64_t small_off;
-    int32_t small_cnt, small_maxf;
+    std::vector<SmallClass> small;  // small fronts of the level by size class
     int64_t all_off;
     int32_t all_cnt, all_maxf;
     int64_t asm_off;
     int32_t asm_cnt;
     std::vector<StepWork> steps;
-    Work small_w, asm_w, fwd_w, bwd_w;
+    Work asm_w, fwd_w, bwd_w;
 };
 
 struct ProfRec {
@@ -50,7 +60,6 @@ struct ProfRec {
     double flops, bytes;
 };
 
-constexpr int kTile = 64;
 
 }  // namespace
 
@@ -74,8 +83,13 @@ struct ipm_ctx {
     int32_t *lvl_small = nullptr, *lvl_all = nullptr;
     int32_t *bwd_order = nullptr, *solve_sync = nullptr;
     int32_t solve_maxf = 0, solve_grid = 0;
-    PanelItem *asm_items = nullptr, *panel_items = nullptr;
-    TileItem *tile_items = nullptr;
+    PanelItem *asm_items = nullptr, *panel_items = nullptr, *trsm_items = nullptr;
+    int32_t *trsm_slots = nullptr;
+    double *panel_ws = nullptr;
+    TileItem *tile_items = nullptr, *tc_items = nullptr, *alt_items = nullptr;
+    bool mixed_active = false;  // tensor-core updates in use (mixed precision, no fallback yet)
+    int32_t fallbacks = 0;
+    double flops_tensor = 0.0;
     std::vector<LevelWork> levels;
     // numeric state of the last factorisation
     double rho = 0.0, delta = 0.0;
@@ -90,6 +104,8 @@ struct ipm_ctx {
     double ms_analyse = 0.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    bool graph_solved = false;  // the last solve ran inside a graph (info comes from the device)
+    cudaStream_t cap_stream = nullptr;  // private stream used only for capturing
     // per-kernel-class measurement
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -183,6 +199,8 @@ void free_device(ipm_ctx *c) {
     if (c->graph) cudaGraphDestroy(c->graph);
     c->graph_exec = nullptr;
     c->graph = nullptr;
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    c->cap_stream = nullptr;
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -247,44 +265,67 @@ int setup_device(ipm_ctx *c) {
         }
     }
     // per-level lists
-    std::vector<int32_t> lvl_all;
-    std::vector<PanelItem> asm_items, panel_items;
-    std::vector<TileItem> tile_items;
+    std::vector<int32_t> lvl_all, small_lists;
+    std::vector<PanelItem> asm_items, panel_items, trsm_items;
+    std::vector<int32_t> trsm_slots, slot_of(P.nsuper, -1);
+    int32_t nslots = 0;
+    for (int32_t s = 0; s < P.nsuper; s++)
+        if (P.sn_f[s] > kSmallFrontMax) slot_of[s] = nslots++;
+    std::vector<TileItem> tile_items, tc_items, alt_items;
     c->levels.assign(P.nlevels, LevelWork());
+    c->flops_tensor = 0.0;
+    // algorithmic work of assembling and factorising one front
+    auto front_work = [&](int32_t s) {
+        const double f = P.sn_f[s];
+        Work fr;
+        for (int32_t i = 1; i <= P.sn_k[s]; i++) fr.flops += (f - i) * (f - i + 3);
+        fr.bytes = 8.0 * f * (f + 1) / 2 + 12.0 * (double)(P.orig_ptr[s + 1] - P.orig_ptr[s]);
+        for (int32_t q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
+            const double cc = P.sn_f[P.child_list[q]] - P.sn_k[P.child_list[q]];
+            fr.bytes += 8.0 * cc * (cc + 1) / 2 + 4.0 * cc;
+            fr.flops += cc * (cc + 1) / 2;
+        }
+        return fr;
+    };
     for (int32_t l = 0; l < P.nlevels; l++) {
         LevelWork &W = c->levels[l];
-        W.small_off = P.lvl_small_ptr[l];
-        W.small_cnt = P.lvl_small_ptr[l + 1] - P.lvl_small_ptr[l];
-        W.small_maxf = 0;
-        for (int32_t t = P.lvl_small_ptr[l]; t < P.lvl_small_ptr[l + 1]; t++)
-            W.small_maxf = std::max(W.small_maxf, P.sn_f[P.lvl_small[t]]);
+        // small fronts of the level, by size class (shared memory per launch
+        // is sized by the class maximum)
+        const int32_t bounds[3] = {32, 64, kSmallFrontMax};
+        int32_t lo = 0, maxsmall = 0;
+        for (int32_t b = 0; b < 3; b++) {
+            SmallClass C;
+            C.off = (int64_t)small_lists.size();
+            C.maxf = 0;
+            for (int32_t t = P.lvl_small_ptr[l]; t < P.lvl_small_ptr[l + 1]; t++) {
+                const int32_t s = P.lvl_small[t], f = P.sn_f[s];
+                if (f > lo && f <= bounds[b]) {
+                    small_lists.push_back(s);
+                    C.maxf = std::max(C.maxf, f);
+                    const Work fr = front_work(s);
+                    C.w.flops += fr.flops;
+                    C.w.bytes += fr.bytes;
+                }
+            }
+            C.cnt = (int32_t)(small_lists.size() - C.off);
+            lo = bounds[b];
+            maxsmall = std::max(maxsmall, C.maxf);
+            if (C.cnt > 0) W.small.push_back(C);
+        }
         W.all_off = (int64_t)lvl_all.size();
-        W.all_maxf = W.small_maxf;
+        W.all_maxf = maxsmall;
         for (int32_t t = P.lvl_small_ptr[l]; t < P.lvl_small_ptr[l + 1]; t++) lvl_all.push_back(P.lvl_small[t]);
         for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
             lvl_all.push_back(P.lvl_large[t]);
             W.all_maxf = std::max(W.all_maxf, P.sn_f[P.lvl_large[t]]);
         }
         W.all_cnt = (int32_t)(lvl_all.size() - W.all_off);
-        // algorithmic work of the level's launches
+        // algorithmic work of the level's assembly and solve launches
         for (int64_t t = W.all_off; t < (int64_t)lvl_all.size(); t++) {
             const int32_t s = lvl_all[t];
             const double f = P.sn_f[s], k = P.sn_k[s];
             const double lnz = f * k - k * (k - 1) / 2;  // stored entries of L
-            Work fr;
-            for (int32_t i = 1; i <= P.sn_k[s]; i++) fr.flops += (f - i) * (f - i + 3);
-            fr.bytes = 8.0 * f * (f + 1) / 2 + 12.0 * (double)(P.orig_ptr[s + 1] - P.orig_ptr[s]);
-            for (int32_t q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
-                const double cc = P.sn_f[P.child_list[q]] - P.sn_k[P.child_list[q]];
-                fr.bytes += 8.0 * cc * (cc + 1) / 2 + 4.0 * cc;
-                fr.flops += cc * (cc + 1) / 2;
-            }
-            if (P.sn_f[s] <= kSmallFrontMax) {
-                W.small_w.flops += fr.flops;
-                W.small_w.bytes += fr.bytes;
-            } else {
-                W.asm_w.bytes += fr.bytes;
-            }
+            if (P.sn_f[s] > kSmallFrontMax) W.asm_w.bytes += front_work(s).bytes;
             W.fwd_w.flops += 2.0 * (lnz - f);
             W.fwd_w.bytes += 8.0 * lnz + 8.0 * (f + 2 * k);
             W.bwd_w.flops += 2.0 * (lnz - f);
@@ -303,25 +344,46 @@ int setup_device(ipm_ctx *c) {
             StepWork S;
             S.p0 = st * c->opt.nb;
             S.panel_off = (int64_t)panel_items.size();
+            S.trsm_off = (int64_t)trsm_items.size();
             S.tile_off = (int64_t)tile_items.size();
+            S.tc_off = (int64_t)tc_items.size();
+            S.alt_off = (int64_t)alt_items.size();
             for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
                 int32_t s = P.lvl_large[t];
                 const int32_t k = P.sn_k[s], f = P.sn_f[s];
                 if (S.p0 >= k) continue;
                 const int32_t p1 = std::min(S.p0 + c->opt.nb, k);
-                if (p1 >= f) panel_items.push_back({s, p1, p1});
-                for (int32_t r = p1; r < f; r += kPanelRows) panel_items.push_back({s, r, std::min(r + kPanelRows, f)});
-                for (int32_t j0 = p1; j0 < f; j0 += kTile)
-                    for (int32_t i0 = j0; i0 < f; i0 += kTile) tile_items.push_back({s, i0, j0});
+                panel_items.push_back({s, 0, slot_of[s]});
+                for (int32_t r = p1; r < f; r += kTrsmRowsHost) {
+                    trsm_items.push_back({s, r, std::min(r + kTrsmRowsHost, f)});
+                    trsm_slots.push_back(slot_of[s]);
+                }
+                const bool tc = c->opt.precision == IPM_PREC_MIXED && f >= c->opt.mixed_min_front;
+                if (tc) {
+                    for (int32_t j0 = p1; j0 < f; j0 += kTcTile)
+                        for (int32_t i0 = j0; i0 < f; i0 += kTcTile) tc_items.push_back({s, i0, j0});
+                    for (int32_t j0 = p1; j0 < f; j0 += kUpdTile)
+                        for (int32_t i0 = j0; i0 < f; i0 += kUpdTile) alt_items.push_back({s, i0, j0});
+                } else {
+                    for (int32_t j0 = p1; j0 < f; j0 += kUpdTile)
+                        for (int32_t i0 = j0; i0 < f; i0 += kUpdTile) tile_items.push_back({s, i0, j0});
+                }
                 const double w = p1 - S.p0, rest = f - p1;
                 // pivot block (w^3/3) + triangular solve of the rows below; update of the lower trailing part
-                S.panel_w.flops += w * w * w / 3.0 + rest * w * w;
-                S.panel_w.bytes += 16.0 * (f - S.p0) * w;
-                S.tile_w.flops += 2.0 * w * rest * (rest + 1) / 2;
-                S.tile_w.bytes += 16.0 * rest * (rest + 1) / 2 + 8.0 * rest * w;
+                S.panel_w.flops += w * w * w / 3.0;
+                S.panel_w.bytes += 16.0 * w * w;
+                S.trsm_w.flops += rest * w * w;
+                S.trsm_w.bytes += 16.0 * rest * w;
+                Work &uw = tc ? S.tc_w : S.tile_w;
+                uw.flops += 2.0 * w * rest * (rest + 1) / 2;
+                uw.bytes += 16.0 * rest * (rest + 1) / 2 + 8.0 * rest * w;
+                if (tc) c->flops_tensor += 2.0 * w * rest * (rest + 1) / 2;
             }
             S.panel_cnt = (int32_t)(panel_items.size() - S.panel_off);
+            S.trsm_cnt = (int32_t)(trsm_items.size() - S.trsm_off);
             S.tile_cnt = (int32_t)(tile_items.size() - S.tile_off);
+            S.tc_cnt = (int32_t)(tc_items.size() - S.tc_off);
+            S.alt_cnt = (int32_t)(alt_items.size() - S.alt_off);
             W.steps.push_back(S);
         }
     }
@@ -342,9 +404,12 @@ int setup_device(ipm_ctx *c) {
         (rc = dupload(c, &d_osrc, P.orig_src)) || (rc = dupload(c, &d_sign, sign)) ||
         (rc = dupload(c, &d_perm, P.perm)) || (rc = dupload(c, &d_uoff, upd_off)) || (rc = dupload(c, &d_kp, kp)) ||
         (rc = dupload(c, &d_kj, kj)) || (rc = dupload(c, &d_ksrc, ksrc)) ||
-        (rc = dupload(c, &c->lvl_small, P.lvl_small)) || (rc = dupload(c, &c->lvl_all, lvl_all)) ||
+        (rc = dupload(c, &c->lvl_small, small_lists)) || (rc = dupload(c, &c->lvl_all, lvl_all)) ||
         (rc = dupload(c, &c->asm_items, asm_items)) || (rc = dupload(c, &c->panel_items, panel_items)) ||
-        (rc = dupload(c, &c->tile_items, tile_items)) || (rc = dupload(c, &c->bwd_order, bwd_order)) ||
+        (rc = dupload(c, &c->trsm_items, trsm_items)) || (rc = dupload(c, &c->trsm_slots, trsm_slots)) ||
+        (rc = dalloc(c, &c->panel_ws, (size_t)std::max(nslots, 1) * kPanelWsHost)) ||
+        (rc = dupload(c, &c->tile_items, tile_items)) || (rc = dupload(c, &c->tc_items, tc_items)) ||
+        (rc = dupload(c, &c->alt_items, alt_items)) || (rc = dupload(c, &c->bwd_order, bwd_order)) ||
         (rc = dalloc(c, &c->solve_sync, (size_t)ns + 1)))
         return rc;
     int32_t *d_sparent;
@@ -394,6 +459,8 @@ int setup_device(ipm_ctx *c) {
         return rc;
     cudaMemset(c->ctl, 0, sizeof(DevCtl));
     cudaMemset(c->fronts, 0, (size_t)std::max<int64_t>(P.front_doubles, 1) * sizeof(double));
+    c->mixed_active = c->opt.precision == IPM_PREC_MIXED;
+    c->fallbacks = 0;
     c->resid_w.flops = 6.0 * (double)kp[N];
     c->resid_w.bytes = 20.0 * (double)kp[N] + 48.0 * N;
     c->dev_ready = true;
@@ -419,10 +486,10 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
     nl += 2;
     for (int32_t l = 0; l < P.nlevels; l++) {
         const LevelWork &W = c->levels[l];
-        if (W.small_cnt > 0) {
-            Prof pr(c, IPM_K_SMALL_FRONTS, W.small_w, st);
-            launch_small_fronts(c->dp, V, c->fronts, c->D, c->dyn, c->ctl, c->lvl_small + W.small_off, W.small_cnt,
-                                c->opt.nb, W.small_maxf, st);
+        for (const SmallClass &C : W.small) {
+            Prof pr(c, IPM_K_SMALL_FRONTS, C.w, st);
+            launch_small_fronts(c->dp, V, c->fronts, c->D, c->dyn, c->ctl, c->lvl_small + C.off, C.cnt, c->opt.nb,
+                                C.maxf, st);
             nl++;
         }
         if (W.asm_cnt > 0) {
@@ -433,14 +500,31 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         for (const StepWork &S : W.steps) {
             {
                 Prof pr(c, IPM_K_LARGE_PANEL, S.panel_w, st);
-                launch_large_panel(c->dp, V, c->fronts, c->D, c->dyn, c->ctl, c->panel_items + S.panel_off,
-                                   S.panel_cnt, S.p0, c->opt.nb, st);
+                launch_panel_diag(c->dp, V, c->fronts, c->D, c->dyn, c->ctl, c->panel_items + S.panel_off,
+                                  S.panel_cnt, S.p0, c->opt.nb, c->panel_ws, st);
             }
             nl++;
+            if (S.trsm_cnt > 0) {
+                Prof pr(c, IPM_K_LARGE_PANEL, S.trsm_w, st);
+                launch_panel_trsm(c->dp, c->fronts, c->trsm_items + S.trsm_off, c->trsm_slots + S.trsm_off,
+                                  S.trsm_cnt, S.p0, c->opt.nb, c->panel_ws, st);
+                nl++;
+            }
             if (S.tile_cnt > 0) {
                 Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w, st);
                 launch_large_update(c->dp, c->fronts, c->D, c->tile_items + S.tile_off, S.tile_cnt, S.p0, c->opt.nb,
                                     st);
+                nl++;
+            }
+            if (S.tc_cnt > 0 && !c->mixed_active) {
+                Prof pr(c, IPM_K_LARGE_UPDATE, S.tc_w, st);
+                launch_large_update(c->dp, c->fronts, c->D, c->alt_items + S.alt_off, S.alt_cnt, S.p0, c->opt.nb,
+                                    st);
+                nl++;
+            } else if (S.tc_cnt > 0) {
+                Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.tc_w, st);
+                launch_large_update_tc(c->dp, c->fronts, c->D, c->tc_items + S.tc_off, S.tc_cnt, S.p0, c->opt.nb,
+                                       c->ctl, st);
                 nl++;
             }
         }
@@ -476,6 +560,47 @@ int solve_inplace(ipm_ctx *c, double *x, cudaStream_t st, int *nl) {
                                    c->solve_grid, c->ctl, st);
     }
     *nl += 2;
+    return to_err(cudaGetLastError());
+}
+
+// Refined solve with all decisions taken on the device, so it can be
+// captured into a CUDA graph: refine_max steps are enqueued and every kernel
+// of a step exits at entry once the control block says the refinement is
+// done (omega <= target, omega failed to halve, or the step limit).
+int solve_device_driven(ipm_ctx *c, const double *r7, const double *r1, double *dx, double *dy, cudaStream_t st) {
+    const Plan &P = c->plan;
+    const int32_t N = P.N;
+    DevVals V{};
+    V.Ax = c->Ax;
+    V.theta = c->theta;
+    V.rho = c->rho;
+    V.delta = c->delta;
+    const int32_t *done = &c->ctl->done;
+    const int32_t *improved = &c->ctl->improved;
+    const double target = c->opt.omega_target;
+    const int32_t rmax = c->opt.refine_max;
+    launch_permute_in(c->dp, r7, r1, c->vf, st);
+    launch_copy_if(c->vx, c->vf, N, nullptr, 0, st);
+    launch_forward_persistent(c->dp, c->fronts, c->D, c->vx, c->upd, c->lvl_all, P.nsuper, c->solve_sync, c->solve_maxf,
+                              c->solve_grid, c->ctl, st);
+    launch_backward_persistent(c->dp, c->fronts, c->vx, c->bwd_order, P.nsuper, c->solve_sync, c->solve_maxf,
+                               c->solve_grid, c->ctl, st);
+    launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st);
+    launch_refine_init(c->ctl, target, rmax, st);
+    launch_copy_if(c->vbest, c->vx, N, nullptr, 0, st);
+    for (int32_t step = 1; step <= rmax; step++) {
+        launch_copy_if(c->vc, c->vr, N, done, 1, st);
+        launch_forward_persistent(c->dp, c->fronts, c->D, c->vc, c->upd, c->lvl_all, P.nsuper, c->solve_sync,
+                                  c->solve_maxf, c->solve_grid, c->ctl, st, done);
+        launch_backward_persistent(c->dp, c->fronts, c->vc, c->bwd_order, P.nsuper, c->solve_sync, c->solve_maxf,
+                                   c->solve_grid, c->ctl, st, done);
+        launch_axpy(c->vx, c->vc, N, st, done);
+        launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st, done);
+        launch_refine_step(c->ctl, target, step, rmax, st);
+        launch_copy_if(c->vbest, c->vx, N, improved, 0, st);
+    }
+    launch_refine_finish(c->ctl, target, st);
+    launch_permute_out(c->dp, c->vbest, dx, dy, st);
     return to_err(cudaGetLastError());
 }
 
@@ -522,7 +647,8 @@ int ipm_create(ipm_ctx **out, const ipm_options *opt) {
     if (!c) return IPM_ERR_OOM;
     if (opt) c->opt = *opt;
     else ipm_default_options(&c->opt);
-    if (c->opt.nb != 32 || c->opt.refine_max < 0 || c->opt.refine_max > 15 || !(c->opt.eps_piv >= 0.0)) {
+    if (c->opt.nb != 32 || c->opt.refine_max < 0 || c->opt.refine_max > 15 || !(c->opt.eps_piv >= 0.0) ||
+        (c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED) || c->opt.mixed_min_front < 1) {
         delete c;
         return IPM_ERR_INVALID_ARG;
     }
@@ -652,7 +778,7 @@ static int read_ctl(ipm_ctx *c, cudaStream_t st, DevCtl *h) {
     return IPM_OK;
 }
 
-int ipm_solve(ipm_ctx *c, const double *r7, const double *r1, double *dx, double *dy, void *stream) {
+static int solve_once(ipm_ctx *c, const double *r7, const double *r1, double *dx, double *dy, void *stream) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!c->factorised) return IPM_ERR_NOT_FACTORISED;
@@ -705,9 +831,25 @@ int ipm_solve(ipm_ctx *c, const double *r7, const double *r1, double *dx, double
     nl++;
     c->refine_steps = steps;
     c->omega = wbest;
+    c->graph_solved = false;
     if (wbest > target) c->status_acc |= kStatRefineFail;
     c->nl_solve = nl;
     return to_err(cudaGetLastError());
+}
+
+int ipm_solve(ipm_ctx *c, const double *r7, const double *r1, double *dx, double *dy, void *stream) {
+    int rc = solve_once(c, r7, r1, dx, dy, stream);
+    if (rc) return rc;
+    // mixed precision: when refinement stalls above the target, factorise
+    // again in FP64 and solve again; later factorisations stay in FP64
+    if (c->mixed_active && c->omega > c->opt.omega_target) {
+        c->mixed_active = false;
+        c->fallbacks++;
+        c->status_acc &= ~kStatRefineFail;
+        if ((rc = factorise_enqueue(c, c->theta, c->rho, c->delta, (cudaStream_t)stream))) return rc;
+        rc = solve_once(c, r7, r1, dx, dy, stream);
+    }
+    return rc;
 }
 
 int ipm_iterate_host(ipm_ctx *c, const double *theta_h, double rho, double delta, int32_t nrhs, const double *r7_h,
@@ -770,6 +912,9 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
     out->nnz_K_lower = P.nnzK_lower;
     out->nnz_L = P.nnzL;
     out->flops_factor = P.flops;
+    out->flops_tensor = c->flops_tensor;
+    out->precision_fallbacks = c->fallbacks;
+    out->mixed_active = c->mixed_active ? 1 : 0;
     out->device_bytes = c->device_bytes;
     out->ms_analyse = c->ms_analyse;
     out->refine_steps = c->refine_steps;
@@ -785,6 +930,11 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
         e = cudaMemcpy(&h, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return to_err(e);
         c->status_acc |= h.status;
+        if (c->graph_solved) {
+            out->refine_steps = h.steps;
+            out->omega = h.omega_best;
+            for (int i = 0; i < 16; i++) out->omega_hist[i] = i <= h.steps ? h.omega_hist[i] : 0.0;
+        }
         out->npos = h.npos;
         out->nneg = h.nneg;
         out->ndynreg = h.ndyn;
@@ -855,17 +1005,75 @@ int ipm_get_factor(ipm_ctx *c, double *L_host, double *D_host, double *dyn_host)
     return IPM_OK;
 }
 
-int ipm_graph_capture(ipm_ctx *c, const double *, double, double, const double *, const double *, double *, double *,
-                      int32_t, void *) {
+int ipm_graph_capture(ipm_ctx *c, const double *theta_dev, double rho, double delta, const double *r7_dev,
+                      const double *r1_dev, double *dx_dev, double *dy_dev, int32_t nsolves, void *stream) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    return IPM_ERR_INVALID_ARG;
+    if (!c->values_set) return IPM_ERR_NOT_ANALYSED;
+    const Plan &P = c->plan;
+    if (nsolves < 0 || (P.n > 0 && !theta_dev) || !(rho >= 0.0) || !(delta >= 0.0) ||
+        (nsolves > 0 && ((P.n > 0 && (!r7_dev || !dx_dev)) || (P.m > 0 && (!r1_dev || !dy_dev)))))
+        return IPM_ERR_INVALID_ARG;
+    (void)stream;
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    // capture on a private stream (the legacy default stream cannot be
+    // captured); the graph is later launched on any stream
+    if (!c->cap_stream) {
+        cudaError_t e0 = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e0 != cudaSuccess) {
+            cudaGetLastError();
+            c->cap_stream = nullptr;
+            return to_err(e0);
+        }
+    }
+    cudaStream_t st = c->cap_stream;
+    const bool prof = c->prof_on;
+    c->prof_on = false;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->prof_on = prof;
+        return to_err(e);
+    }
+    c->rho = rho;
+    c->delta = delta;
+    if (P.n > 0 && theta_dev != c->theta)
+        cudaMemcpyAsync(c->theta, theta_dev, P.n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    rc = factorise_enqueue(c, c->theta, rho, delta, st);
+    for (int32_t k = 0; k < nsolves && rc == IPM_OK; k++)
+        rc = solve_device_driven(c, r7_dev + (size_t)k * P.n, r1_dev + (size_t)k * P.m, dx_dev + (size_t)k * P.n,
+                                 dy_dev + (size_t)k * P.m, st);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    c->prof_on = prof;
+    if (rc || e != cudaSuccess) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : to_err(e);
+    }
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        c->graph_exec = nullptr;
+        return to_err(e);
+    }
+    c->graph = g;
+    return IPM_OK;
 }
 
-int ipm_graph_launch(ipm_ctx *c, void *) {
+int ipm_graph_launch(ipm_ctx *c, void *stream) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    return IPM_ERR_INVALID_ARG;
+    if (!c->graph_exec) return IPM_ERR_INVALID_ARG;
+    cudaError_t e = cudaGraphLaunch(c->graph_exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return to_err(e);
+    c->factorised = true;
+    c->graph_solved = true;
+    return IPM_OK;
 }
 
 int ipm_launch_counts(const ipm_ctx *c, int32_t *nf, int32_t *ns) {

@@ -29,6 +29,7 @@ struct DevCtl {
     double dinf;           // ||d||_inf of the current iterate (as ordered bits >= 0)
     int32_t done;          // refinement finished
     int32_t steps;
+    int32_t improved;      // the last step improved omega_best
     double omega_hist[16];
 };
 
@@ -69,7 +70,11 @@ struct DevVals {
 };
 
 // Rows of a panel handled by one CTA of the panel kernel (one thread per row).
-constexpr int kPanelRows = 64;
+constexpr int kPanelRows = 128;
+// Output tile of the FP64 trailing-update kernel.
+constexpr int kUpdTile = 32;
+// Output tile of the tensor-core trailing update (M = N).
+constexpr int kTcTile = 128;
 
 // Work item of the large-front path.
 struct PanelItem {
@@ -88,10 +93,18 @@ void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, dou
                          const int32_t *list, int32_t count, int32_t nb, int32_t maxf, cudaStream_t st);
 void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, const PanelItem *items,
                            int32_t count, cudaStream_t st);
-void launch_large_panel(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *dyn, DevCtl *ctl,
-                        const PanelItem *items, int32_t count, int32_t p0, int32_t nb, cudaStream_t st);
+// panel step 1 (diagonal block, one item per front; item.r1 = workspace slot)
+void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *dyn, DevCtl *ctl,
+                       const PanelItem *items, int32_t count, int32_t p0, int32_t nb, double *pws, cudaStream_t st);
+// panel step 2 (rows below, kTrsmRowsHost rows per item; slots[i] = workspace slot of item i)
+void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,
+                       int32_t p0, int32_t nb, const double *pws, cudaStream_t st);
+constexpr int kTrsmRowsHost = 32;
+constexpr int kPanelWsHost = 32 * 33 + 32;
 void launch_large_update(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
                          int32_t p0, int32_t w, cudaStream_t st);
+void launch_large_update_tc(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
+                            int32_t p0, int32_t w, DevCtl *ctl, cudaStream_t st);
 void launch_factor_stats(const double *D, const double *dyn, int N, double large_reg, DevCtl *ctl, cudaStream_t st);
 // solves and refinement (kernels_solve.cu)
 void launch_forward(const DevPlan &P, const double *fronts, const double *D, double *x, double *upd,
@@ -100,16 +113,22 @@ void launch_backward(const DevPlan &P, const double *fronts, double *x, const in
                      int32_t maxf, cudaStream_t st);
 void launch_forward_persistent(const DevPlan &P, const double *fronts, const double *D, double *x, double *upd,
                                const int32_t *order, int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid,
-                               DevCtl *ctl, cudaStream_t st);
+                               DevCtl *ctl, cudaStream_t st, const int32_t *skip = nullptr);
 void launch_backward_persistent(const DevPlan &P, const double *fronts, double *x, const int32_t *order,
                                 int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid, DevCtl *ctl,
-                                cudaStream_t st);
+                                cudaStream_t st, const int32_t *skip = nullptr);
 // kernel used to size the persistent sweeps' grid (occupancy query)
 const void *persistent_probe_kernel();
 void launch_permute_in(const DevPlan &P, const double *r7, const double *r1, double *f, cudaStream_t st);
 void launch_permute_out(const DevPlan &P, const double *x, double *dx, double *dy, cudaStream_t st);
+// skip != nullptr: the kernels return at entry while *skip != 0 (graph-captured refinement)
 void launch_residual_omega(const DevPlan &P, const DevVals &V, const double *f, const double *x, double *r,
-                           double *ad, double *ae, DevCtl *ctl, cudaStream_t st);
-void launch_axpy(double *x, const double *c, int32_t N, cudaStream_t st);
+                           double *ad, double *ae, DevCtl *ctl, cudaStream_t st, const int32_t *skip = nullptr);
+void launch_axpy(double *x, const double *c, int32_t N, cudaStream_t st, const int32_t *skip = nullptr);
+void launch_refine_init(DevCtl *ctl, double target, int32_t max_steps, cudaStream_t st);
+void launch_refine_step(DevCtl *ctl, double target, int32_t step, int32_t max_steps, cudaStream_t st);
+void launch_refine_finish(DevCtl *ctl, double target, cudaStream_t st);
+// dst = src when flag == nullptr or (*flag != 0) != invert
+void launch_copy_if(double *dst, const double *src, int32_t N, const int32_t *flag, int32_t invert, cudaStream_t st);
 
 }  // namespace ipm

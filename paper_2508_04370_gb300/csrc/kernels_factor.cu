@@ -37,48 +37,75 @@ __device__ __forceinline__ double orig_value(const DevPlan &P, const DevVals &V,
     return -1.0 / V.theta[j];
 }
 
-// Pivot decision for pivot p of block [p, b1) held in a column-major array
-// Fm with leading dimension ld; executed by one full warp.  Returns the
-// accepted pivot on every lane.
-__device__ __forceinline__ double decide_pivot(const double *Fm, int ld, int p, int b1, const int8_t *sgn,
-                                               double rho, double delta, double b1floor, int lane, double *D_out,
-                                               double *dyn_out, DevCtl *ctl) {
+// Pivot decision of Sec. 4.5 / Prop. 3 for pivot p of the block [0, w) held
+// column-major in shared memory (one full warp):
+//   d   = F_pp + s_p sigma_p          (static term after the pivot is computed)
+//   b2  = max over j in (p, w) with s_j = s_p and s_j F_jj > 0 of F_jp^2 / |F_jj|
+//   d  <- s_p max(s_p d, max(eps_piv ||K||_1, b2)).
+// The maximum of the quotients is found by cross-multiplication, so only the
+// winning quotient is divided.  Lane 0 records D, the lift and the status and
+// returns the pivot and its reciprocal through shared memory.
+__device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int w, const int8_t *sgn, double rho,
+                                           double delta, double b1floor, double *Dout, double *dynout, DevCtl *ctl,
+                                           double *piv_out) {
+    const int lane = threadIdx.x & 31;
     const int sp = sgn[p];
-    const double fpp = Fm[(int64_t)p * ld + p];
-    const double d = fpp + (sp < 0 ? -rho : delta);
-    double b2 = 0.0;
-    for (int j = p + 1 + lane; j < b1; j += 32) {
+    double num = 0.0, den = 1.0;  // candidate F_jp^2 / |F_jj|
+    for (int j = p + 1 + lane; j < w; j += 32) {
         if (sgn[j] != sp) continue;
-        const double fjj = Fm[(int64_t)j * ld + j];
+        const double fjj = Fd[j * LDD + j];
         if (!(sp * fjj > 0.0)) continue;
-        const double fjp = Fm[(int64_t)p * ld + j];
-        b2 = fmax(b2, fjp * fjp / fabs(fjj));
+        const double fjp = Fd[p * LDD + j];
+        const double n2 = fjp * fjp, d2 = fabs(fjj);
+        if (n2 * den > num * d2) {
+            num = n2;
+            den = d2;
+        }
     }
-    b2 = warp_max(b2);
-    const double bnd = b1floor > b2 ? b1floor : b2;
-    const double sd = sp * d;
-    const double dn = sp * (sd > bnd ? sd : bnd);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double on = __shfl_xor_sync(0xffffffffu, num, o), od = __shfl_xor_sync(0xffffffffu, den, o);
+        if (on * den > num * od) {
+            num = on;
+            den = od;
+        }
+    }
     if (lane == 0) {
-        *D_out = dn;
-        *dyn_out = dn - d;
+        const double b2 = num > 0.0 ? num / den : 0.0;
+        const double d = Fd[p * LDD + p] + (sp < 0 ? -rho : delta);
+        const double bnd = b1floor > b2 ? b1floor : b2;
+        const double sd = sp * d;
+        const double dn = sp * (sd > bnd ? sd : bnd);
+        Dout[p] = dn;
+        dynout[p] = dn - d;
         if (!isfinite(d) || !isfinite(dn) || dn == 0.0) atomicOr(&ctl->status, kStatNonFinite);
+        piv_out[0] = dn;
+        piv_out[1] = 1.0 / dn;
     }
-    return dn;
 }
 
 // ------------------------------------------------------------ small fronts
-// One CTA per front, the whole front in shared memory.
+// One CTA per front, the whole front in shared memory.  FP64 is scarce on
+// this GPU (about 0.4 FP64 FMA per clock per SM sub-partition), so every
+// pivot's work is spread over all warps: warp 0 decides the pivot
+// (pivot_warp), all threads scale the pivot column with one reciprocal and
+// apply the rank-1 update to the rest of the pivot block's columns (all rows
+// below, which also performs the triangular solve of the rows under the
+// block); after each block of 32 pivots all threads apply the block to the
+// trailing lower part.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, double *__restrict__ fronts,
                                                       double *__restrict__ Dg, double *__restrict__ dyng,
                                                       DevCtl *ctl, const int32_t *__restrict__ list, int nb) {
     extern __shared__ double smem[];
+    __shared__ double wcol[128];  // fronts up to 128 rows use this kernel
+    __shared__ double dq[32];
+    __shared__ double piv[2];
     const int s = list[blockIdx.x];
     const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
-    double *F = smem;                 // ld * f
-    double *w = smem + (size_t)ld * f;  // f   (unscaled pivot column)
-    double *dq = w + f;               // nb  (pivots of the current block)
+    double *F = smem;  // ld * f
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = NT / 32;
     const int sz = ld * f;
     for (int t = tid; t < sz; t += NT) F[t] = 0.0;
     __syncthreads();
@@ -100,34 +127,36 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
     const int8_t *sgn = P.sign + c0;
     const double b1floor = ctl->b1;
     for (int b0 = 0; b0 < k; b0 += nb) {
-        const int b1 = min(b0 + nb, k);
-        for (int p = b0; p < b1; p++) {
-            if (warp == 0) {
-                double dn = decide_pivot(F, ld, p, b1, sgn, V.rho, V.delta, b1floor, lane, &Dg[c0 + p],
-                                         &dyng[c0 + p], ctl);
-                if (lane == 0) dq[p - b0] = dn;
+        const int b1 = min(b0 + nb, k), w = b1 - b0;
+        double *Fb = F + b0 * ld + b0;
+        for (int p = 0; p < w; p++) {
+            if (warp == 0) pivot_warp(Fb, ld, p, w, sgn + b0, V.rho, V.delta, b1floor, Dg + c0 + b0, dyng + c0 + b0,
+                                      ctl, piv);
+            __syncthreads();
+            const double dn = piv[0], rinv = piv[1];
+            const int pc = b0 + p;  // front column of the pivot
+            for (int i = pc + 1 + tid; i < f; i += NT) {
+                const double v = F[pc * ld + i];
+                wcol[i] = v;
+                F[pc * ld + i] = v * rinv;
+            }
+            if (tid == 0) {
+                F[pc * ld + pc] = dn;
+                dq[p] = dn;
             }
             __syncthreads();
-            const double dp = dq[p - b0];
-            for (int i = p + 1 + tid; i < f; i += NT) {
-                const double v = F[p * ld + i];
-                w[i] = v;
-                F[p * ld + i] = v / dp;
-            }
-            if (tid == 0) F[p * ld + p] = dp;
-            __syncthreads();
-            // rank-1 update of the remaining columns of the block, all rows
-            for (int j = p + 1 + warp; j < b1; j += NT / 32) {
-                const double wj = w[j];
-                for (int i = j + lane; i < f; i += 32) F[j * ld + i] -= F[p * ld + i] * wj;
+            // rank-1 update of the block's remaining columns, all rows below
+            for (int j = pc + 1 + warp; j < b0 + w; j += NW) {
+                const double wj = wcol[j];
+                for (int i = j + lane; i < f; i += 32) F[j * ld + i] -= F[pc * ld + i] * wj;
             }
             __syncthreads();
         }
         // trailing update of columns [b1, f) by the block's pivots
-        for (int j = b1 + warp; j < f; j += NT / 32) {
+        for (int j = b1 + warp; j < f; j += NW) {
             for (int i = j + lane; i < f; i += 32) {
                 double acc = 0.0;
-                for (int q = b0; q < b1; q++) acc += F[q * ld + i] * (F[q * ld + j] * dq[q - b0]);
+                for (int q = 0; q < w; q++) acc += F[(b0 + q) * ld + i] * (F[(b0 + q) * ld + j] * dq[q]);
                 F[j * ld + i] -= acc;
             }
         }
@@ -197,129 +226,149 @@ __global__ void __launch_bounds__(256) k_large_assemble(DevPlan P, DevVals V, do
     (void)f;
 }
 
-// Panel [p0, p1) of front s: every CTA factorises the nb x nb diagonal block
-// redundantly in shared memory (deterministic, identical results), then
-// solves its rows [r0, r1) of the panel below it by forward substitution
-// with L_DD and D (one reciprocal per pivot, W(q, p) = d_q L_pq staged in
-// shared memory); the CTA whose r0 is the first row below the block writes
-// the factorised diagonal block, D and the lifts.
-__global__ void __launch_bounds__(kPanelRows) k_large_panel(DevPlan P, DevVals V, double *__restrict__ fronts,
-                                                             double *__restrict__ Dg, double *__restrict__ dyng,
-                                                             DevCtl *ctl, const PanelItem *__restrict__ items,
-                                                             int p0, int nb) {
+// Panel [p0, p1) of a large front, step 1: the nb x nb diagonal block,
+// one CTA per front.  Warp 0 decides each pivot (pivot_warp); all threads
+// scale the pivot column inside the block and apply the rank-1 update to the
+// block's remaining columns.  The factorised block goes back to the slab (L
+// strictly below the diagonal, D on it) together with D and the lifts, and
+// the panel workspace of the front receives W(q, p) = d_q L_pq (p > q) and
+// 1 / d_q for the triangular solve of the rows below.
+constexpr int kPanelWs = 32 * 33 + 32;  // doubles of panel workspace per large front
+
+__global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double *__restrict__ fronts,
+                                                     double *__restrict__ Dg, double *__restrict__ dyng, DevCtl *ctl,
+                                                     const PanelItem *__restrict__ items, int p0, int nb,
+                                                     double *__restrict__ pws) {
     __shared__ double Fd[32 * 33];
-    __shared__ double Wd[32 * 33];
-    __shared__ double wv[32];
-    __shared__ double dq[32], inv[32];
     __shared__ double Dtmp[32], dyntmp[32];
+    __shared__ double piv[2];
+    constexpr int LDD = 33, NT = 128;
     const PanelItem it = items[blockIdx.x];
     const int s = it.s;
     const int k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
-    const int p1 = min(p0 + nb, k);
-    const int w = p1 - p0;
+    const int w = min(p0 + nb, k) - p0;
     double *F = fronts + P.sn_off[s];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int LDD = 33;
-    for (int t = tid; t < w * w; t += kPanelRows) {
-        const int jj = t / w, ii = t % w;
-        Fd[jj * LDD + ii] = (ii >= jj) ? F[(int64_t)(p0 + jj) * ld + (p0 + ii)] : 0.0;
+    double *ws = pws + (int64_t)it.r1 * kPanelWs;  // r1 carries the workspace slot
+    const int tid = threadIdx.x, warp = tid >> 5;
+#pragma unroll
+    for (int u = 0; u < 1024 / NT; u++) {
+        const int t = tid + u * NT;
+        const int jj = t >> 5, ii = t & 31;
+        Fd[jj * LDD + ii] = (jj < w && ii < w && ii >= jj) ? F[(int64_t)(p0 + jj) * ld + (p0 + ii)] : 0.0;
     }
     __syncthreads();
     const int8_t *sgn = P.sign + c0 + p0;
     const double b1floor = ctl->b1;
-    if (warp == 0) {
-        for (int p = 0; p < w; p++) {
-            double dn = decide_pivot(Fd, LDD, p, w, sgn, V.rho, V.delta, b1floor, lane, &Dtmp[p], &dyntmp[p], ctl);
-            if (lane == 0) dq[p] = dn;
-            if (lane > p && lane < w) {
-                const double v = Fd[p * LDD + lane];
-                wv[lane] = v;
-                Fd[p * LDD + lane] = v / dn;
-            }
-            __syncwarp();
-            for (int j = p + 1; j < w; j++)
-                if (lane >= j && lane < w) Fd[j * LDD + lane] -= Fd[p * LDD + lane] * wv[j];
-            __syncwarp();
+    for (int p = 0; p < w; p++) {
+        if (warp == 0) pivot_warp(Fd, LDD, p, w, sgn, V.rho, V.delta, b1floor, Dtmp, dyntmp, ctl, piv);
+        __syncthreads();
+        const double rinv = piv[1];
+        // all threads: scale the column, then the rank-1 update of the block
+        double wv = 0.0;
+        const int i = p + 1 + (tid & 31);
+        if (tid < 32 && i < w) {
+            wv = Fd[p * LDD + i];
         }
-    }
-    __syncthreads();
-    for (int t = tid; t < w * w; t += kPanelRows) {
-        const int q = t / w, p = t % w;
-        Wd[q * LDD + p] = p > q ? dq[q] * Fd[q * LDD + p] : 0.0;
-    }
-    for (int t = tid; t < 32; t += kPanelRows) inv[t] = t < w ? 1.0 / dq[t] : 0.0;
-    __syncthreads();
-    for (int i = it.r0 + tid; i < it.r1; i += kPanelRows) {
-        double li[32];
-#pragma unroll
-        for (int p = 0; p < 32; p++) li[p] = p < w ? F[(int64_t)(p0 + p) * ld + i] : 0.0;
-#pragma unroll
-        for (int q = 0; q < 32; q++) {
-            li[q] *= inv[q];
-#pragma unroll
-            for (int p = q + 1; p < 32; p++) li[p] -= li[q] * Wd[q * LDD + p];
+        __syncthreads();
+        if (tid < 32 && i < w) Fd[p * LDD + i] = wv * rinv;
+        if (tid == 0) Fd[p * LDD + p] = piv[0];
+        __syncthreads();
+        for (int t = tid; t < 32 * 32; t += NT) {
+            const int jj = t >> 5, ii = t & 31;
+            if (jj > p && jj < w && ii >= jj && ii < w)
+                Fd[jj * LDD + ii] -= Fd[p * LDD + ii] * (Fd[p * LDD + jj] * piv[0]);
         }
-#pragma unroll
-        for (int p = 0; p < 32; p++)
-            if (p < w) F[(int64_t)(p0 + p) * ld + i] = li[p];
+        __syncthreads();
     }
-    if (it.r0 == p1) {  // exactly one item per (front, panel) starts at p1
-        for (int t = tid; t < w * w; t += kPanelRows) {
-            const int jj = t / w, ii = t % w;
-            if (ii > jj) F[(int64_t)(p0 + jj) * ld + (p0 + ii)] = Fd[jj * LDD + ii];
-            else if (ii == jj) F[(int64_t)(p0 + jj) * ld + (p0 + ii)] = dq[jj];
-        }
-        for (int t = tid; t < w; t += kPanelRows) {
+    for (int t = tid; t < 32 * 32; t += NT) {
+        const int jj = t >> 5, ii = t & 31;
+        const bool in = jj < w && ii < w;
+        if (in && ii >= jj) F[(int64_t)(p0 + jj) * ld + (p0 + ii)] = Fd[jj * LDD + ii];
+        ws[jj * 33 + ii] = (in && ii > jj) ? Dtmp[jj] * Fd[jj * LDD + ii] : 0.0;  // W(q = jj, p = ii)
+    }
+    for (int t = tid; t < 32; t += NT) {
+        ws[32 * 33 + t] = t < w ? 1.0 / Dtmp[t] : 0.0;
+        if (t < w) {
             Dg[c0 + p0 + t] = Dtmp[t];
             dyng[c0 + p0 + t] = dyntmp[t];
         }
     }
 }
 
+// Panel step 2: rows [r0, r1) below the diagonal block, one row per thread
+// (all lanes do useful FP64 work):  l_iq = (F_iq - sum_{q' < q} l_iq' W(q', q)) / d_q.
+constexpr int kTrsmRows = 32;
+
+__global__ void __launch_bounds__(kTrsmRows) k_panel_trsm(DevPlan P, double *__restrict__ fronts,
+                                                           const PanelItem *__restrict__ items, const int32_t *slots,
+                                                           int p0, int nb, const double *__restrict__ pws) {
+    __shared__ double Wd[32 * 33 + 32];
+    const PanelItem it = items[blockIdx.x];
+    const int s = it.s;
+    const int k = P.sn_k[s], ld = P.sn_ld[s];
+    const int w = min(p0 + nb, k) - p0;
+    double *F = fronts + P.sn_off[s];
+    const double *ws = pws + (int64_t)slots[blockIdx.x] * kPanelWs;
+    const int tid = threadIdx.x;
+    for (int t = tid; t < 32 * 33 + 32; t += kTrsmRows) Wd[t] = ws[t];
+    __syncthreads();
+    const int i = it.r0 + tid;
+    if (i < it.r1) {
+        double li[32];
+#pragma unroll
+        for (int q = 0; q < 32; q++) li[q] = q < w ? F[(int64_t)(p0 + q) * ld + i] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 32; q++) {
+            li[q] *= Wd[32 * 33 + q];
+#pragma unroll
+            for (int p = q + 1; p < 32; p++) li[p] -= li[q] * Wd[q * 33 + p];
+        }
+#pragma unroll
+        for (int q = 0; q < 32; q++)
+            if (q < w) F[(int64_t)(p0 + q) * ld + i] = li[q];
+    }
+}
+
 // Trailing update of the lower part of columns [p1, f) by the panel
-// [p0, p0+w): C(i, j) -= sum_q L(i,q) d_q L(j,q), one 64 x 64 tile per CTA.
+// [p0, p0+w): C(i, j) -= sum_q L(i,q) d_q L(j,q), one kUpdTile x kUpdTile
+// tile per CTA.  FP64 runs at ~6.6 GFLOP/s per SM on this part, so tiles are
+// small (32 x 32) to put every SM to work on each launch.
 __global__ void __launch_bounds__(256) k_large_update(DevPlan P, double *__restrict__ fronts,
                                                       const double *__restrict__ Dg,
                                                       const TileItem *__restrict__ items, int p0, int w) {
-    __shared__ double As[32][65];
-    __shared__ double Bs[32][65];
+    constexpr int T = kUpdTile;
+    __shared__ double As[32][T + 1];
+    __shared__ double Bs[32][T + 1];
     const TileItem it = items[blockIdx.x];
     const int s = it.s;
     const int f = P.sn_f[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
     w = min(w, P.sn_k[s] - p0);  // ragged last panel
     double *F = fronts + P.sn_off[s];
     const int tid = threadIdx.x;
-    for (int t = tid; t < 32 * 64; t += 256) {
-        const int q = t / 64, r = t % 64;
+    for (int t = tid; t < 32 * T; t += 256) {
+        const int q = t / T, r = t % T;
         const int i = it.i0 + r, j = it.j0 + r;
         const bool qa = q < w;
         As[q][r] = (qa && i < f) ? F[(int64_t)(p0 + q) * ld + i] : 0.0;
         Bs[q][r] = (qa && j < f) ? F[(int64_t)(p0 + q) * ld + j] * Dg[c0 + p0 + q] : 0.0;
     }
     __syncthreads();
-    const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads, 4 x 4 each
-    double acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; a++)
-#pragma unroll
-        for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+    const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads, 2 x 2 outputs each
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
     for (int q = 0; q < w; q++) {
-        double av[4], bv[4];
-#pragma unroll
-        for (int a = 0; a < 4; a++) av[a] = As[q][tx + 16 * a];
-#pragma unroll
-        for (int b = 0; b < 4; b++) bv[b] = Bs[q][ty + 16 * b];
-#pragma unroll
-        for (int a = 0; a < 4; a++)
-#pragma unroll
-            for (int b = 0; b < 4; b++) acc[a][b] += av[a] * bv[b];
+        const double a0 = As[q][tx], a1 = As[q][tx + 16];
+        const double b0 = Bs[q][ty], b1 = Bs[q][ty + 16];
+        acc[0][0] += a0 * b0;
+        acc[1][0] += a1 * b0;
+        acc[0][1] += a0 * b1;
+        acc[1][1] += a1 * b1;
     }
 #pragma unroll
-    for (int b = 0; b < 4; b++) {
+    for (int b = 0; b < 2; b++) {
         const int j = it.j0 + ty + 16 * b;
         if (j >= f) continue;
 #pragma unroll
-        for (int a = 0; a < 4; a++) {
+        for (int a = 0; a < 2; a++) {
             const int i = it.i0 + tx + 16 * a;
             if (i < f && i >= j) F[(int64_t)j * ld + i] -= acc[a][b];
         }
@@ -391,13 +440,17 @@ void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, dou
                          const int32_t *list, int32_t count, int32_t nb, int32_t maxf, cudaStream_t st) {
     if (count <= 0) return;
     const int ldmax = (maxf + 3) & ~3;
-    const size_t smem = ((size_t)ldmax * maxf + maxf + 32) * sizeof(double);
+    const size_t smem = (size_t)ldmax * maxf * sizeof(double);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_small_fronts<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        cudaFuncSetAttribute(k_small_fronts<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_small_fronts<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    k_small_fronts<256><<<count, 256, smem, st>>>(P, V, fronts, D, dyn, ctl, list, nb);
+    // one warp per front up to f = 32, two up to 64, four beyond
+    if (maxf <= 32) k_small_fronts<32><<<count, 32, smem, st>>>(P, V, fronts, D, dyn, ctl, list, nb);
+    else if (maxf <= 64) k_small_fronts<64><<<count, 64, smem, st>>>(P, V, fronts, D, dyn, ctl, list, nb);
+    else k_small_fronts<128><<<count, 128, smem, st>>>(P, V, fronts, D, dyn, ctl, list, nb);
 }
 
 void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, const PanelItem *items,
@@ -406,10 +459,16 @@ void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, c
     k_large_assemble<<<count, 256, 0, st>>>(P, V, fronts, items);
 }
 
-void launch_large_panel(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *dyn, DevCtl *ctl,
-                        const PanelItem *items, int32_t count, int32_t p0, int32_t nb, cudaStream_t st) {
+void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *dyn, DevCtl *ctl,
+                       const PanelItem *items, int32_t count, int32_t p0, int32_t nb, double *pws, cudaStream_t st) {
     if (count <= 0) return;
-    k_large_panel<<<count, kPanelRows, 0, st>>>(P, V, fronts, D, dyn, ctl, items, p0, nb);
+    k_panel_diag<<<count, 128, 0, st>>>(P, V, fronts, D, dyn, ctl, items, p0, nb, pws);
+}
+
+void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,
+                       int32_t p0, int32_t nb, const double *pws, cudaStream_t st) {
+    if (count <= 0) return;
+    k_panel_trsm<<<count, kTrsmRows, 0, st>>>(P, fronts, items, slots, p0, nb, pws);
 }
 
 void launch_large_update(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,

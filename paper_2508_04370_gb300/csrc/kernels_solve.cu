@@ -161,11 +161,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(DevPlan P,
                                                                        const double *__restrict__ D,
                                                                        double *__restrict__ x, double *upd,
                                                                        const int32_t *__restrict__ order, int nitems,
-                                                                       int32_t *ticket, int32_t *cnt, DevCtl *ctl) {
+                                                                       int32_t *ticket, int32_t *cnt, DevCtl *ctl,
+                                                                       const int32_t *skip) {
     extern __shared__ double v[];
     __shared__ double Lb[32 * 33];
     __shared__ int item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (skip && *skip) return;
     for (;;) {
         if (tid == 0) item = atomicAdd(ticket, 1);
         __syncthreads();
@@ -226,11 +228,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(DevPlan P,
 __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(DevPlan P, const double *__restrict__ fronts,
                                                                         double *x, const int32_t *__restrict__ order,
                                                                         int nitems, int32_t *ticket, int32_t *flag,
-                                                                        DevCtl *ctl) {
+                                                                        DevCtl *ctl, const int32_t *skip) {
     extern __shared__ double z[];
     __shared__ double Lb[32 * 33];
     __shared__ int item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (skip && *skip) return;
     for (;;) {
         if (tid == 0) item = atomicAdd(ticket, 1);
         __syncthreads();
@@ -297,7 +300,9 @@ __global__ void k_permute_out(const int32_t *__restrict__ perm, int N, int n, co
 // r = f - K x, ad = |K||x|, ae = |K|e in the factorisation order; also the
 // running max of |x| (ctl->dinf, as ordered bits of a non-negative double).
 __global__ void k_residual(DevPlan P, DevVals V, const double *__restrict__ f, const double *__restrict__ x,
-                           double *__restrict__ r, double *__restrict__ ad, double *__restrict__ ae, DevCtl *ctl) {
+                           double *__restrict__ r, double *__restrict__ ad, double *__restrict__ ae, DevCtl *ctl,
+                           const int32_t *skip) {
+    if (skip && *skip) return;
     double xm = 0.0;
     bool bad = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
@@ -328,7 +333,9 @@ __global__ void k_residual(DevPlan P, DevVals V, const double *__restrict__ f, c
 // omega = max_i |r_i| / den_i, den_i = (|K||x| + |f|)_i, replaced by
 // (|K||x| + ||x||_inf |K|e)_i when den_i <= 1000 N eps (ae_i ||x||_inf + |f_i|).
 __global__ void k_omega(int N, const double *__restrict__ r, const double *__restrict__ ad,
-                        const double *__restrict__ ae, const double *__restrict__ f, DevCtl *ctl) {
+                        const double *__restrict__ ae, const double *__restrict__ f, DevCtl *ctl,
+                        const int32_t *skip) {
+    if (skip && *skip) return;
     const double dinf = ctl->dinf;
     const double eps = 2.220446049250313e-16;
     double w = 0.0;
@@ -345,8 +352,54 @@ __global__ void k_omega(int N, const double *__restrict__ r, const double *__res
     if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long *)&ctl->omega, (unsigned long long)__double_as_longlong(w));
 }
 
-__global__ void k_axpy(double *__restrict__ x, const double *__restrict__ c, int N) {
+__global__ void k_axpy(double *__restrict__ x, const double *__restrict__ c, int N, const int32_t *skip) {
+    if (skip && *skip) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) x[i] += c[i];
+}
+
+// Device-side refinement control (used when the solve is captured in a CUDA
+// graph and no host decision is possible).  After the first residual:
+// best = x, omega_best = omega, done = omega <= target.  After step k:
+// keep x as best if omega improved; done once omega <= target, omega failed
+// to halve, or k = max_steps.  Kernels of later steps exit at entry when done.
+__global__ void k_refine_init(DevCtl *ctl, double target, int max_steps) {
+    const double w = ctl->omega;
+    ctl->omega_best = w;
+    ctl->omega_hist[0] = w;
+    ctl->steps = 0;
+    ctl->improved = 1;
+    ctl->done = (w <= target || max_steps <= 0) ? 1 : 0;
+}
+
+__global__ void k_refine_step(DevCtl *ctl, double target, int step, int max_steps) {
+    if (ctl->done) {
+        ctl->improved = 0;
+        return;
+    }
+    const double w = ctl->omega;
+    ctl->steps = step;
+    if (step < 16) ctl->omega_hist[step] = w;
+    const bool halved = w <= 0.5 * ctl->omega_best;
+    ctl->improved = w < ctl->omega_best ? 1 : 0;
+    if (ctl->improved) ctl->omega_best = w;
+    ctl->done = (!halved || ctl->omega_best <= target || step >= max_steps) ? 1 : 0;
+}
+
+__global__ void k_refine_finish(DevCtl *ctl, double target) {
+    if (ctl->omega_best > target) atomicOr(&ctl->status, kStatRefineFail);
+}
+
+// dst = src when flag == nullptr or (*flag != 0) != invert
+__global__ void k_copy_if(double *__restrict__ dst, const double *__restrict__ src, int N, const int32_t *flag,
+                          int invert) {
+    if (flag && ((*flag != 0) == (invert != 0))) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+__global__ void k_clear_norms(DevCtl *ctl, const int32_t *skip) {
+    if (skip && *skip) return;
+    ctl->dinf = 0.0;
+    ctl->omega = 0.0;
 }
 
 }  // namespace
@@ -373,7 +426,7 @@ const void *persistent_probe_kernel() { return (const void *)k_forward_persisten
 
 void launch_forward_persistent(const DevPlan &P, const double *fronts, const double *D, double *x, double *upd,
                                const int32_t *order, int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid,
-                               DevCtl *ctl, cudaStream_t st) {
+                               DevCtl *ctl, cudaStream_t st, const int32_t *skip) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_forward_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -383,15 +436,16 @@ void launch_forward_persistent(const DevPlan &P, const double *fronts, const dou
     // sync[0] = ticket, sync[1 .. nsuper] = finished-children counters
     cudaMemsetAsync(sync, 0, (size_t)(P.nsuper + 1) * sizeof(int32_t), st);
     k_forward_persistent<<<grid, kSolveThreads, (size_t)maxf * sizeof(double), st>>>(P, fronts, D, x, upd, order,
-                                                                                      nitems, sync, sync + 1, ctl);
+                                                                                      nitems, sync, sync + 1, ctl,
+                                                                                      skip);
 }
 
 void launch_backward_persistent(const DevPlan &P, const double *fronts, double *x, const int32_t *order,
                                 int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid, DevCtl *ctl,
-                                cudaStream_t st) {
+                                cudaStream_t st, const int32_t *skip) {
     cudaMemsetAsync(sync, 0, (size_t)(P.nsuper + 1) * sizeof(int32_t), st);
     k_backward_persistent<<<grid, kSolveThreads, (size_t)maxf * sizeof(double), st>>>(P, fronts, x, order, nitems,
-                                                                                       sync, sync + 1, ctl);
+                                                                                       sync, sync + 1, ctl, skip);
 }
 
 void launch_permute_in(const DevPlan &P, const double *r7, const double *r1, double *f, cudaStream_t st) {
@@ -403,16 +457,34 @@ void launch_permute_out(const DevPlan &P, const double *x, double *dx, double *d
 }
 
 void launch_residual_omega(const DevPlan &P, const DevVals &V, const double *f, const double *x, double *r,
-                           double *ad, double *ae, DevCtl *ctl, cudaStream_t st) {
+                           double *ad, double *ae, DevCtl *ctl, cudaStream_t st, const int32_t *skip) {
     const int grid = (P.N + 255) / 256 < 608 ? (P.N + 255) / 256 : 608;
-    cudaMemsetAsync(&ctl->dinf, 0, sizeof(double), st);
-    cudaMemsetAsync(&ctl->omega, 0, sizeof(double), st);
-    k_residual<<<grid, 256, 0, st>>>(P, V, f, x, r, ad, ae, ctl);
-    k_omega<<<grid, 256, 0, st>>>(P.N, r, ad, ae, f, ctl);
+    if (!skip) {
+        cudaMemsetAsync(&ctl->dinf, 0, sizeof(double), st);
+        cudaMemsetAsync(&ctl->omega, 0, sizeof(double), st);
+    } else {
+        k_clear_norms<<<1, 1, 0, st>>>(ctl, skip);
+    }
+    k_residual<<<grid, 256, 0, st>>>(P, V, f, x, r, ad, ae, ctl, skip);
+    k_omega<<<grid, 256, 0, st>>>(P.N, r, ad, ae, f, ctl, skip);
 }
 
-void launch_axpy(double *x, const double *c, int32_t N, cudaStream_t st) {
-    k_axpy<<<(N + 255) / 256 < 608 ? (N + 255) / 256 : 608, 256, 0, st>>>(x, c, N);
+void launch_axpy(double *x, const double *c, int32_t N, cudaStream_t st, const int32_t *skip) {
+    k_axpy<<<(N + 255) / 256 < 608 ? (N + 255) / 256 : 608, 256, 0, st>>>(x, c, N, skip);
+}
+
+void launch_refine_init(DevCtl *ctl, double target, int32_t max_steps, cudaStream_t st) {
+    k_refine_init<<<1, 1, 0, st>>>(ctl, target, max_steps);
+}
+
+void launch_refine_step(DevCtl *ctl, double target, int32_t step, int32_t max_steps, cudaStream_t st) {
+    k_refine_step<<<1, 1, 0, st>>>(ctl, target, step, max_steps);
+}
+
+void launch_refine_finish(DevCtl *ctl, double target, cudaStream_t st) { k_refine_finish<<<1, 1, 0, st>>>(ctl, target); }
+
+void launch_copy_if(double *dst, const double *src, int32_t N, const int32_t *flag, int32_t invert, cudaStream_t st) {
+    k_copy_if<<<(N + 255) / 256 < 608 ? (N + 255) / 256 : 608, 256, 0, st>>>(dst, src, N, flag, invert);
 }
 
 }  // namespace ipm
