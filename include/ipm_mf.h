@@ -116,8 +116,9 @@ typedef struct ipm_info {
     double omega_hist[16];                  /* omega after 0, 1, ... refinement steps */
     int32_t status;                         /* device status word of the last factorise/solve */
     double ms_analyse;                      /* host wall time of ipm_analyse */
-    double est_flops_ne, est_flops_as;      /* AS/NE chooser model (Sec. 4.2) */
-    int64_t nnz_ne_seen;                    /* NE entries formed before the chooser stopped */
+    double est_cost_ne, est_cost_as;        /* AS/NE chooser: modelled seconds per IPM iteration
+                                               (Sec. 4.2; -1 when the normal equations were abandoned) */
+    int64_t nnz_ne_seen;                    /* entries of A A^T counted before the chooser stopped */
     int32_t precision_fallbacks;            /* mixed path: refactorisations in FP64 so far */
     int32_t mixed_active;                   /* 1 while tensor-core updates are in use */
 } ipm_info;
@@ -134,7 +135,11 @@ int ipm_destroy(ipm_ctx *ctx);
 /* Symbolic analysis, done once per pattern (Sec. 4.2-4.3): choose the form
  * (AUTO runs the augmented-system symbolic first and abandons forming the
  * normal equations once they hold more entries than L of the augmented
- * system, Sec. 4.2), order (AMD / ND / USER / NATURAL), build the elimination
+ * system, Sec. 4.2; otherwise it compares modelled per-iteration costs:
+ * factorisation flops at 1 TFLOP/s FP64, three solves' worth of L traffic at
+ * 6.7 TB/s and the formation of A Theta~ A^T; ties and AUTO + USER order are
+ * resolved to / rejected in favour of the augmented system), order
+ * (AMD / ND / USER / NATURAL), build the elimination
  * tree, postorder, column counts, fundamental supernodes and amalgamation,
  * the front row lists, the extend-add maps, the tree levels and the device
  * plan.  Host only: the device arena is allocated by the first
@@ -144,7 +149,11 @@ int ipm_destroy(ipm_ctx *ctx);
  *   rowidx    host, colptr[n] entries
  *   user_perm host, N entries (N = n+m for the augmented system, m for the
  *             normal equations), perm[new] = old; read only for IPM_ORD_USER
- * Errors: IPM_ERR_INVALID_ARG for a malformed pattern or permutation. */
+ * The normal equations need, for every entry of A A^T, the list of columns
+ * contributing to it; a pattern needing more than 2^28 such pairs (dense
+ * rows) is rejected for IPM_FORM_NORMAL and never chosen by AUTO.
+ * Errors: IPM_ERR_INVALID_ARG for a malformed pattern or permutation, the
+ * AUTO + USER combination, or normal equations beyond the pair limit. */
 int ipm_analyse(ipm_ctx *ctx, int32_t m, int32_t n, const int64_t *colptr, const int32_t *rowidx,
                 int32_t form, int32_t ordering, const int32_t *user_perm);
 
@@ -238,7 +247,7 @@ int ipm_graph_launch(ipm_ctx *ctx, void *stream);
  * ipm_solve (for launch accounting). */
 int ipm_launch_counts(const ipm_ctx *ctx, int32_t *factorise_launches, int32_t *solve_launches);
 
-/* Allocation-free variant of ipm_solve (the paper has no counterpart: this
+/* Allocation-free variant of ipm_solve for the augmented system (the paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at solve
  * time, for example code running while a stream is captured into a CUDA
  * graph, where cudaMalloc is not allowed, or a host library that must not

@@ -71,7 +71,7 @@ class ipm_info(ct.Structure):
         ("npos", ct.c_int32), ("nneg", ct.c_int32), ("ndynreg", ct.c_int32),
         ("max_dynreg", ct.c_double), ("norm_K1", ct.c_double), ("refine_steps", ct.c_int32),
         ("omega", ct.c_double), ("omega_hist", ct.c_double * 16), ("status", ct.c_int32),
-        ("ms_analyse", ct.c_double), ("est_flops_ne", ct.c_double), ("est_flops_as", ct.c_double),
+        ("ms_analyse", ct.c_double), ("est_cost_ne", ct.c_double), ("est_cost_as", ct.c_double),
         ("nnz_ne_seen", ct.c_int64), ("precision_fallbacks", ct.c_int32), ("mixed_active", ct.c_int32),
     ]
 

@@ -158,6 +158,33 @@ double front_flops(int64_t f, int64_t k) {
 
 }  // namespace
 
+int64_t count_ne_lower(int32_t m, int32_t n, const int64_t *colptr, const int32_t *rowidx, int64_t limit) {
+    std::vector<int64_t> rp(m + 1, 0);
+    std::vector<int32_t> rc(colptr[n]);
+    for (int64_t p = 0; p < colptr[n]; p++) rp[rowidx[p] + 1]++;
+    for (int32_t i = 0; i < m; i++) rp[i + 1] += rp[i];
+    std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
+    for (int32_t j = 0; j < n; j++)
+        for (int64_t p = colptr[j]; p < colptr[j + 1]; p++) rc[fill[rowidx[p]]++] = j;
+    std::vector<int32_t> mark(m, -1);
+    int64_t total = 0;
+    for (int32_t i = 0; i < m; i++) {
+        mark[i] = i;
+        total++;
+        for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+            const int32_t j = rc[p];
+            for (int64_t q = colptr[j]; q < colptr[j + 1]; q++) {
+                const int32_t r = rowidx[q];
+                if (r > i && mark[r] != i) {
+                    mark[r] = i;
+                    if (++total > limit) return limit + 1;
+                }
+            }
+        }
+    }
+    return total;
+}
+
 int analyse(Plan &P, int32_t m, int32_t n, const int64_t *colptr, const int32_t *rowidx, int32_t form,
             int32_t ordering, const int32_t *user_perm, const AnalyseOptions &opt, std::string &err) {
     auto t0 = std::chrono::steady_clock::now();
@@ -203,6 +230,65 @@ int analyse(Plan &P, int32_t m, int32_t n, const int64_t *colptr, const int32_t 
     std::vector<int32_t> lri;
     lower_pattern(P, lcp, lri);
     P.nnzK_lower = lcp[N];
+    if (form == 2) {
+        // contributor pairs of every lower entry (r, i) of A A^T, ascending j
+        if ((int64_t)P.Acp[n] > INT32_MAX) {
+            err = "too many entries in A for the normal equations";
+            return kErrInvalid;
+        }
+        std::vector<int64_t> rp(m + 1, 0);
+        std::vector<int32_t> rc(P.Acp[n]), rpos(P.Acp[n]);
+        for (int64_t p = 0; p < P.Acp[n]; p++) rp[P.Ari[p] + 1]++;
+        for (int32_t i = 0; i < m; i++) rp[i + 1] += rp[i];
+        {
+            std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
+            for (int32_t j = 0; j < n; j++)
+                for (int64_t p = P.Acp[j]; p < P.Acp[j + 1]; p++) {
+                    rc[fill[P.Ari[p]]] = j;
+                    rpos[fill[P.Ari[p]]++] = (int32_t)p;
+                }
+        }
+        std::vector<int64_t> cnt(lcp[N] + 1, 0);
+        std::vector<int64_t> pos(m, -1);
+        int64_t total = 0;
+        for (int pass = 0; pass < 2; pass++) {
+            if (pass == 1) {
+                for (int64_t e = 0; e < lcp[N]; e++) cnt[e + 1] += cnt[e];
+                total = cnt[lcp[N]];
+                if (total > kMaxNePairs) {
+                    err = "normal equations too expensive to form (pair limit)";
+                    return kErrInvalid;
+                }
+                P.ne_ta.resize(total);
+                P.ne_tb.resize(total);
+                P.ne_tj.resize(total);
+            }
+            std::vector<int64_t> fillc;
+            if (pass == 1) fillc.assign(cnt.begin(), cnt.end() - 1);
+            for (int32_t i = 0; i < m; i++) {
+                for (int64_t q = lcp[i]; q < lcp[i + 1]; q++) pos[lri[q]] = q;
+                for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+                    const int32_t j = rc[p];
+                    const int32_t aij = rpos[p];
+                    for (int64_t t = P.Acp[j]; t < P.Acp[j + 1]; t++) {
+                        const int32_t r = P.Ari[t];
+                        if (r < i) continue;
+                        const int64_t e = pos[r];
+                        if (pass == 0) cnt[e + 1]++;
+                        else {
+                            const int64_t w = fillc[e]++;
+                            P.ne_ta[w] = (int32_t)t;
+                            P.ne_tb[w] = aij;
+                            P.ne_tj[w] = j;
+                        }
+                    }
+                }
+            }
+        }
+        P.ne_tptr.assign(cnt.begin(), cnt.end());
+        P.ne_cp = lcp;
+        P.ne_ri = lri;
+    }
     Graph g = symmetric_graph(N, lcp, lri);
 
     // ----- ordering

@@ -97,7 +97,8 @@ struct ipm_ctx {
     // last solve
     DevCtl last{};
     int32_t refine_steps = 0;
-    double omega = 0.0;
+    double omega = 0.0;      // reported backward error (on K)
+    double omega_sys = 0.0;  // backward error of the refined system (K, or M for the normal equations)
     double omega_hist[16] = {0};
     int32_t status_acc = 0;
     int32_t nl_factor = 0, nl_solve = 0;
@@ -106,6 +107,9 @@ struct ipm_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     bool graph_solved = false;  // the last solve ran inside a graph (info comes from the device)
     cudaStream_t cap_stream = nullptr;  // private stream used only for capturing
+    // normal equations
+    NeView ne{};
+    double *kf = nullptr, *kr = nullptr, *kad = nullptr, *kae = nullptr;  // K-sized scratch for omega on K
     // per-kernel-class measurement
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -263,6 +267,32 @@ int setup_device(ipm_ctx *c) {
             kj[fill[b]] = b;
             ksrc[fill[b]++] = kDualDiag;
         }
+    }
+    if (P.form == 2) {
+        // M = A Theta~ A^T + delta I, full symmetric CSR in factorisation order; value
+        // source = index of the lower entry (the diagonal adds delta)
+        const std::vector<int64_t> &cp = P.ne_cp;
+        const std::vector<int32_t> &ri = P.ne_ri;
+        for (int32_t jo = 0; jo < N; jo++)
+            for (int64_t p = cp[jo]; p < cp[jo + 1]; p++) {
+                const int32_t a = P.iperm[ri[p]], b = P.iperm[jo];
+                kp[a + 1]++;
+                if (a != b) kp[b + 1]++;
+            }
+        for (int32_t i = 0; i < N; i++) kp[i + 1] += kp[i];
+        kj.resize(kp[N]);
+        ksrc.resize(kp[N]);
+        std::vector<int64_t> fill(kp.begin(), kp.end() - 1);
+        for (int32_t jo = 0; jo < N; jo++)
+            for (int64_t p = cp[jo]; p < cp[jo + 1]; p++) {
+                const int32_t a = P.iperm[ri[p]], b = P.iperm[jo];
+                kj[fill[a]] = b;
+                ksrc[fill[a]++] = p;
+                if (a != b) {
+                    kj[fill[b]] = a;
+                    ksrc[fill[b]++] = p;
+                }
+            }
     }
     // per-level lists
     std::vector<int32_t> lvl_all, small_lists;
@@ -457,6 +487,42 @@ int setup_device(ipm_ctx *c) {
         (rc = dalloc(c, &c->vr, N)) || (rc = dalloc(c, &c->vad, N)) || (rc = dalloc(c, &c->vae, N)) ||
         (rc = dalloc(c, &c->vc, N)) || (rc = dalloc(c, &c->upd, (size_t)std::max<int64_t>(P.upd_total, 1))))
         return rc;
+    if (P.form == 2) {
+        const int32_t n = P.n, m = P.m;
+        std::vector<int64_t> arp(m + 1, 0);
+        std::vector<int32_t> aci(P.Acp[n]), apos(P.Acp[n]);
+        for (int64_t q = 0; q < P.Acp[n]; q++) arp[P.Ari[q] + 1]++;
+        for (int32_t i = 0; i < m; i++) arp[i + 1] += arp[i];
+        std::vector<int64_t> fill(arp.begin(), arp.end() - 1);
+        for (int32_t j = 0; j < n; j++)
+            for (int64_t q = P.Acp[j]; q < P.Acp[j + 1]; q++) {
+                aci[fill[P.Ari[q]]] = j;
+                apos[fill[P.Ari[q]]++] = (int32_t)q;
+            }
+        int64_t *d_tptr, *d_arp, *d_acp;
+        int32_t *d_ta, *d_tb, *d_tj, *d_aci, *d_apos, *d_ari;
+        std::vector<int64_t> acp(P.Acp.begin(), P.Acp.end());
+        if ((rc = dupload(c, &d_tptr, P.ne_tptr)) || (rc = dupload(c, &d_ta, P.ne_ta)) ||
+            (rc = dupload(c, &d_tb, P.ne_tb)) || (rc = dupload(c, &d_tj, P.ne_tj)) || (rc = dupload(c, &d_arp, arp)) ||
+            (rc = dupload(c, &d_aci, aci)) || (rc = dupload(c, &d_apos, apos)) || (rc = dupload(c, &d_acp, acp)) ||
+            (rc = dupload(c, &d_ari, P.Ari)) || (rc = dalloc(c, &c->ne.tt, n)) ||
+            (rc = dalloc(c, &c->ne.nev, (size_t)P.ne_cp[N])) || (rc = dalloc(c, &c->kf, (size_t)n + m)) ||
+            (rc = dalloc(c, &c->kr, (size_t)n + m)) || (rc = dalloc(c, &c->kad, (size_t)n + m)) ||
+            (rc = dalloc(c, &c->kae, (size_t)n + m)))
+            return rc;
+        c->ne.n = n;
+        c->ne.m = m;
+        c->ne.nnz = P.ne_cp[N];
+        c->ne.tptr = d_tptr;
+        c->ne.ta = d_ta;
+        c->ne.tb = d_tb;
+        c->ne.tj = d_tj;
+        c->ne.Arp = d_arp;
+        c->ne.Aci = d_aci;
+        c->ne.Apos = d_apos;
+        c->ne.Acp = d_acp;
+        c->ne.Ari = d_ari;
+    }
     cudaMemset(c->ctl, 0, sizeof(DevCtl));
     cudaMemset(c->fronts, 0, (size_t)std::max<int64_t>(P.front_doubles, 1) * sizeof(double));
     c->mixed_active = c->opt.precision == IPM_PREC_MIXED;
@@ -472,11 +538,16 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
     DevVals V{};
     V.Ax = c->Ax;
     V.theta = theta;
-    V.nev = nullptr;
+    V.nev = c->ne.nev;
     V.rho = rho;
     V.delta = delta;
     V.large_reg = c->opt.large_reg;
     int nl = 0;
+    if (P.form == 2) {
+        Prof pr(c, IPM_K_OTHER, Work(), st);
+        launch_ne_form(c->ne, c->Ax, theta, rho, c->ctl, st);
+        nl += 2;
+    }
     // reset the per-factorisation fields of the control block
     cudaMemsetAsync(&c->ctl->ndyn, 0, offsetof(DevCtl, omega) - offsetof(DevCtl, ndyn), st);
     {
@@ -579,7 +650,9 @@ int solve_device_driven(ipm_ctx *c, const double *r7, const double *r1, double *
     const int32_t *improved = &c->ctl->improved;
     const double target = c->opt.omega_target;
     const int32_t rmax = c->opt.refine_max;
-    launch_permute_in(c->dp, r7, r1, c->vf, st);
+    V.nev = c->ne.nev;
+    if (P.form == 2) launch_ne_rhs(c->ne, c->dp.perm, c->Ax, r7, r1, c->vf, st);
+    else launch_permute_in(c->dp, r7, r1, c->vf, st);
     launch_copy_if(c->vx, c->vf, N, nullptr, 0, st);
     launch_forward_persistent(c->dp, c->fronts, c->D, c->vx, c->upd, c->lvl_all, P.nsuper, c->solve_sync, c->solve_maxf,
                               c->solve_grid, c->ctl, st);
@@ -601,6 +674,7 @@ int solve_device_driven(ipm_ctx *c, const double *r7, const double *r1, double *
     }
     launch_refine_finish(c->ctl, target, st);
     launch_permute_out(c->dp, c->vbest, dx, dy, st);
+    if (P.form == 2) launch_ne_dx(c->ne, c->Ax, dy, r7, dx, st);
     return to_err(cudaGetLastError());
 }
 
@@ -670,8 +744,8 @@ int ipm_destroy(ipm_ctx *c) {
 int ipm_analyse(ipm_ctx *c, int32_t m, int32_t n, const int64_t *colptr, const int32_t *rowidx, int32_t form,
                 int32_t ordering, const int32_t *user_perm) {
     if (!c) return IPM_ERR_INVALID_ARG;
-    if (form == IPM_FORM_AUTO) form = IPM_FORM_AUGMENTED;
-    if (form == IPM_FORM_NORMAL) return IPM_ERR_INVALID_ARG;  // normal equations: not in this build yet
+    if (form != IPM_FORM_AUTO && form != IPM_FORM_AUGMENTED && form != IPM_FORM_NORMAL) return IPM_ERR_INVALID_ARG;
+    if (form == IPM_FORM_AUTO && ordering == IPM_ORD_USER) return IPM_ERR_INVALID_ARG;  // order size depends on the form
     AnalyseOptions ao;
     ao.nb = c->opt.nb;
     ao.amalg_width = c->opt.amalg_width;
@@ -687,12 +761,46 @@ int ipm_analyse(ipm_ctx *c, int32_t m, int32_t n, const int64_t *colptr, const i
     free_device(c);
     c->analysed = false;
     auto t0 = std::chrono::steady_clock::now();
-    int rc = analyse(c->plan, m, n, colptr, rowidx, form, ordering, user_perm, ao, err);
-    c->ms_analyse = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (rc) {
-        if (c->opt.verbose) std::fprintf(stderr, "[ipm analyse] %s\n", err.c_str());
-        return rc;
+    int rc;
+    if (form == IPM_FORM_AUTO) {
+        // Sec. 4.2: the augmented-system symbolic first; forming the normal
+        // equations is abandoned as soon as they hold more entries than L of
+        // the augmented system, otherwise the modelled per-iteration costs
+        // decide (factorisation flops at the FP64 rate, three solves' worth of
+        // L traffic at HBM bandwidth, the formation of A Theta~ A^T; ties go
+        // to the augmented system)
+        constexpr double kFlop = 1.0e12, kBw = 6.7e12;
+        Plan pas;
+        rc = analyse(pas, m, n, colptr, rowidx, 1, ordering, user_perm, ao, err);
+        if (rc) {
+            if (c->opt.verbose) std::fprintf(stderr, "[ipm analyse] %s\n", err.c_str());
+            return rc;
+        }
+        const double cost_as = pas.flops / kFlop + 3.0 * 2.0 * (double)pas.nnzL * 8.0 / kBw;
+        const int64_t ne_seen = count_ne_lower(m, n, colptr, rowidx, pas.nnzL);
+        double cost_ne = -1.0;
+        bool use_ne = false;
+        Plan pne;
+        if (ne_seen <= pas.nnzL) {
+            std::string err2;
+            if (analyse(pne, m, n, colptr, rowidx, 2, ordering, nullptr, ao, err2) == 0) {
+                const double pairs = (double)pne.ne_tptr.back();
+                cost_ne = (pne.flops + 2.0 * pairs) / kFlop + 3.0 * 2.0 * (double)pne.nnzL * 8.0 / kBw;
+                use_ne = cost_ne < cost_as;
+            }
+        }
+        c->plan = use_ne ? std::move(pne) : std::move(pas);
+        c->plan.est_as = cost_as;
+        c->plan.est_ne = cost_ne;
+        c->plan.nnz_ne_seen = ne_seen;
+    } else {
+        rc = analyse(c->plan, m, n, colptr, rowidx, form, ordering, user_perm, ao, err);
+        if (rc) {
+            if (c->opt.verbose) std::fprintf(stderr, "[ipm analyse] %s\n", err.c_str());
+            return rc;
+        }
     }
+    c->ms_analyse = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     c->analysed = true;
     return IPM_OK;
 }
@@ -791,8 +899,10 @@ static int solve_once(ipm_ctx *c, const double *r7, const double *r1, double *dx
     V.theta = c->theta;
     V.rho = c->rho;
     V.delta = c->delta;
+    V.nev = c->ne.nev;
     int nl = 0;
-    launch_permute_in(c->dp, r7, r1, c->vf, st);
+    if (P.form == 2) launch_ne_rhs(c->ne, c->dp.perm, c->Ax, r7, r1, c->vf, st);  // r8 = r1 + A Theta~ r7
+    else launch_permute_in(c->dp, r7, r1, c->vf, st);
     nl++;
     cudaMemcpyAsync(c->vx, c->vf, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if ((rc = solve_inplace(c, c->vx, st, &nl))) return rc;
@@ -831,6 +941,17 @@ static int solve_once(ipm_ctx *c, const double *r7, const double *r1, double *dx
     nl++;
     c->refine_steps = steps;
     c->omega = wbest;
+    c->omega_sys = wbest;
+    if (P.form == 2) {
+        // dx = Theta~ (A^T dy - r7); the reported backward error is the one on K
+        launch_ne_dx(c->ne, c->Ax, dy, r7, dx, st);
+        launch_residual_K(c->ne, c->Ax, c->theta, c->rho, c->delta, r7, r1, dx, dy, c->kf, c->kr, c->kad, c->kae,
+                          c->ctl, st);
+        launch_omega_only(P.n + P.m, c->kr, c->kad, c->kae, c->kf, c->ctl, st);
+        nl += 3;
+        if ((rc = read_ctl(c, st, &h))) return rc;
+        c->omega = h.omega;
+    }
     c->graph_solved = false;
     if (wbest > target) c->status_acc |= kStatRefineFail;
     c->nl_solve = nl;
@@ -842,7 +963,7 @@ int ipm_solve(ipm_ctx *c, const double *r7, const double *r1, double *dx, double
     if (rc) return rc;
     // mixed precision: when refinement stalls above the target, factorise
     // again in FP64 and solve again; later factorisations stay in FP64
-    if (c->mixed_active && c->omega > c->opt.omega_target) {
+    if (c->mixed_active && c->omega_sys > c->opt.omega_target) {
         c->mixed_active = false;
         c->fallbacks++;
         c->status_acc &= ~kStatRefineFail;
@@ -914,6 +1035,9 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
     out->flops_factor = P.flops;
     out->flops_tensor = c->flops_tensor;
     out->precision_fallbacks = c->fallbacks;
+    out->est_cost_as = P.est_as;
+    out->est_cost_ne = P.est_ne;
+    out->nnz_ne_seen = P.nnz_ne_seen;
     out->mixed_active = c->mixed_active ? 1 : 0;
     out->device_bytes = c->device_bytes;
     out->ms_analyse = c->ms_analyse;
@@ -1175,6 +1299,7 @@ int ipm_solve_noalloc(ipm_ctx *c, const double *r7, const double *r1, double *dx
         return IPM_ERR_SCRATCH_TOO_SMALL;
     }
     if (!c->factorised) return IPM_ERR_NOT_FACTORISED;
+    if (P.form != 1) return IPM_ERR_INVALID_ARG;  // augmented system only
     if ((P.n > 0 && (!r7 || !dx)) || (P.m > 0 && (!r1 || !dy))) return IPM_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(c->opt.device);
     if (e != cudaSuccess) return to_err(e);

@@ -76,6 +76,20 @@ constexpr int kUpdTile = 32;
 // Output tile of the tensor-core trailing update (M = N).
 constexpr int kTcTile = 128;
 
+// Device data of the normal-equations path.
+struct NeView {
+    int32_t n, m;
+    int64_t nnz;                 // lower entries of M
+    const int64_t *tptr;         // contributor pairs per entry
+    const int32_t *ta, *tb, *tj;
+    double *tt;                  // Theta~ (n)
+    double *nev;                 // formed entries of M (nnz)
+    const int64_t *Arp;          // A by rows: pointer, column, position in Ax
+    const int32_t *Aci, *Apos;
+    const int64_t *Acp;          // A by columns
+    const int32_t *Ari;
+};
+
 // Work item of the large-front path.
 struct PanelItem {
     int32_t s;       // supernode
@@ -117,6 +131,17 @@ void launch_forward_persistent(const DevPlan &P, const double *fronts, const dou
 void launch_backward_persistent(const DevPlan &P, const double *fronts, double *x, const int32_t *order,
                                 int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid, DevCtl *ctl,
                                 cudaStream_t st, const int32_t *skip = nullptr);
+// normal equations (kernels_ne.cu)
+void launch_ne_form(const NeView &E, const double *Ax, const double *theta, double rho, DevCtl *ctl, cudaStream_t st);
+void launch_ne_rhs(const NeView &E, const int32_t *perm, const double *Ax, const double *r7, const double *r1,
+                   double *f, cudaStream_t st);
+void launch_ne_dx(const NeView &E, const double *Ax, const double *dy, const double *r7, double *dx, cudaStream_t st);
+void launch_residual_K(const NeView &E, const double *Ax, const double *theta, double rho, double delta,
+                       const double *r7, const double *r1, const double *dx, const double *dy, double *f, double *r,
+                       double *ad, double *ae, DevCtl *ctl, cudaStream_t st);
+// backward error from precomputed r, |K||d|, |K|e, f (ctl->dinf set)
+void launch_omega_only(int32_t N, const double *r, const double *ad, const double *ae, const double *f, DevCtl *ctl,
+                       cudaStream_t st);
 // kernel used to size the persistent sweeps' grid (occupancy query)
 const void *persistent_probe_kernel();
 void launch_permute_in(const DevPlan &P, const double *r7, const double *r1, double *f, cudaStream_t st);

@@ -65,17 +65,26 @@ struct Plan {
     int32_t max_f = 0, max_k = 0;
     int32_t nsmall = 0, nlarge = 0;
 
-    // normal equations: lower entries of M in original numbering (CSC) and,
-    // for each, the list of A-entry pairs (p_row_i', p_row_i) contributing
+    // normal equations: lower entries of M = A Theta~ A^T in original
+    // numbering (CSC, rows >= column) and, for each entry (r, i), the A-entry
+    // pairs (a_rj, a_ij) contributing to it, in ascending column j
     std::vector<int64_t> ne_cp;
     std::vector<int32_t> ne_ri;
-    std::vector<int64_t> ne_tptr;     // per NE entry: range in ne_ta/ne_tb
-    std::vector<int64_t> ne_ta, ne_tb;  // A value indices (same column j)
-    std::vector<int32_t> ne_tj;         // that column j
+    std::vector<int64_t> ne_tptr;     // per NE entry: range in ne_ta/ne_tb/ne_tj
+    std::vector<int32_t> ne_ta, ne_tb;  // A value indices of a_rj and a_ij
+    std::vector<int32_t> ne_tj;         // the column j
     // chooser record
     double est_as = 0.0, est_ne = 0.0;
     int64_t nnz_ne_seen = 0;
 };
+
+// Largest number of (a_rj, a_ij) pairs the normal equations may need; a
+// pattern beyond it is not formed (dense rows of A make A A^T expensive).
+constexpr int64_t kMaxNePairs = int64_t(1) << 28;
+
+// Entries of the lower part of A A^T (with diagonal), counting stops once it
+// exceeds `limit` (returns limit + 1 then).
+int64_t count_ne_lower(int32_t m, int32_t n, const int64_t *colptr, const int32_t *rowidx, int64_t limit);
 
 struct AnalyseOptions {
     int32_t nb = 32;

@@ -386,7 +386,8 @@ __global__ void k_norm1(DevPlan P, DevVals V, DevCtl *ctl) {
         for (int64_t p = P.kp[i]; p < P.kp[i + 1]; p++) {
             const int64_t src = P.ksrc[p];
             double val;
-            if (src >= 0) val = V.Ax[src];
+            if (P.form == 2) val = V.nev[src] + (P.kj[p] == i ? V.delta : 0.0);
+            else if (src >= 0) val = V.Ax[src];
             else if (src == kDualDiag) val = V.delta;
             else {
                 const double th = V.theta[-1 - src];

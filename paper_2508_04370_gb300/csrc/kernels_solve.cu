@@ -289,10 +289,11 @@ __global__ void k_permute_in(const int32_t *__restrict__ perm, int N, int n, con
     }
 }
 __global__ void k_permute_out(const int32_t *__restrict__ perm, int N, int n, const double *__restrict__ x,
-                              double *__restrict__ dx, double *__restrict__ dy) {
+                              double *__restrict__ dx, double *__restrict__ dy, int form) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const int o = perm[i];
-        if (o < n) dx[o] = x[i];
+        if (form == 2) dy[o] = x[i];
+        else if (o < n) dx[o] = x[i];
         else dy[o - n] = x[i];
     }
 }
@@ -310,7 +311,8 @@ __global__ void k_residual(DevPlan P, DevVals V, const double *__restrict__ f, c
         for (int64_t p = P.kp[i]; p < P.kp[i + 1]; p++) {
             const int64_t src = P.ksrc[p];
             double val;
-            if (src >= 0) val = V.Ax[src];
+            if (P.form == 2) val = V.nev[src] + (P.kj[p] == i ? V.delta : 0.0);
+            else if (src >= 0) val = V.Ax[src];
             else if (src == kDualDiag) val = V.delta;
             else val = -(1.0 / V.theta[-1 - src] + V.rho);
             const double xj = x[P.kj[p]];
@@ -453,7 +455,7 @@ void launch_permute_in(const DevPlan &P, const double *r7, const double *r1, dou
 }
 
 void launch_permute_out(const DevPlan &P, const double *x, double *dx, double *dy, cudaStream_t st) {
-    k_permute_out<<<(P.N + 255) / 256, 256, 0, st>>>(P.perm, P.N, P.n, x, dx, dy);
+    k_permute_out<<<(P.N + 255) / 256, 256, 0, st>>>(P.perm, P.N, P.n, x, dx, dy, P.form);
 }
 
 void launch_residual_omega(const DevPlan &P, const DevVals &V, const double *f, const double *x, double *r,
@@ -467,6 +469,12 @@ void launch_residual_omega(const DevPlan &P, const DevVals &V, const double *f, 
     }
     k_residual<<<grid, 256, 0, st>>>(P, V, f, x, r, ad, ae, ctl, skip);
     k_omega<<<grid, 256, 0, st>>>(P.N, r, ad, ae, f, ctl, skip);
+}
+
+void launch_omega_only(int32_t N, const double *r, const double *ad, const double *ae, const double *f, DevCtl *ctl,
+                       cudaStream_t st) {
+    const int grid = (N + 255) / 256 < 608 ? (N + 255) / 256 : 608;
+    k_omega<<<grid > 0 ? grid : 1, 256, 0, st>>>(N, r, ad, ae, f, ctl, nullptr);
 }
 
 void launch_axpy(double *x, const double *c, int32_t N, cudaStream_t st, const int32_t *skip) {

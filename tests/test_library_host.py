@@ -156,3 +156,43 @@ def test_edge_patterns(lib):
         lp = synth.lp.LP(m, n, np.asarray(cp, np.int64), np.asarray(ri, np.int32), np.ones(len(ri)))
         _compare_with_oracle(lib, ctx, lp)
         lib.ipm_destroy(ctx)
+
+
+def test_normal_equations_symbolic_bit_exact(lib):
+    from oracle import FORM_NE
+
+    for seed in range(3):
+        lp = synth.random_lp(50 + 10 * seed, 140, 3, seed=60 + seed)
+        ctx = lib.ipm_create()
+        assert lib.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, lib.IPM_FORM_NORMAL, lib.IPM_ORD_AMD) == 0
+        sym = lib.ipm_get_symbolic(ctx)
+        o = Oracle.from_lp(lp, form=FORM_NE)
+        s = o.analyse(sym["perm"])
+        for a, b in (("parent", "etree"), ("colcount", "colcount"), ("sn_start", "snode_ptr"),
+                     ("sn_parent", "sn_parent"), ("sn_rows", "sn_rows")):
+            assert np.array_equal(s[a], sym[b]), a
+        lib.ipm_destroy(ctx)
+
+
+def test_form_chooser(lib):
+    """Sec. 4.2: a dense column makes A A^T dense, so forming the normal
+    equations is abandoned once it holds more entries than L of the
+    augmented system; a sparse LP with few rows per column keeps the cheaper
+    form by the cost model."""
+    lp = synth.random_lp(400, 1000, 3, seed=5)
+    # append one fully dense column
+    cp = np.concatenate([lp.colptr, [lp.colptr[-1] + lp.m]]).astype(np.int64)
+    ri = np.concatenate([lp.rowidx, np.arange(lp.m, dtype=np.int32)])
+    ctx = lib.ipm_create()
+    assert lib.ipm_analyse(ctx, lp.m, lp.n + 1, cp, ri, lib.IPM_FORM_AUTO, lib.IPM_ORD_AMD) == 0
+    rc, info = lib.ipm_get_info(ctx)
+    assert info.form == lib.IPM_FORM_AUGMENTED
+    assert info.nnz_ne_seen > info.nnz_L and info.est_cost_ne == -1.0
+    lib.ipm_destroy(ctx)
+    ctx = lib.ipm_create()
+    assert lib.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, lib.IPM_FORM_AUTO, lib.IPM_ORD_AMD) == 0
+    rc, info = lib.ipm_get_info(ctx)
+    assert info.est_cost_ne > 0 and info.est_cost_as > 0
+    chosen = lib.IPM_FORM_NORMAL if info.est_cost_ne < info.est_cost_as else lib.IPM_FORM_AUGMENTED
+    assert info.form == chosen
+    lib.ipm_destroy(ctx)

@@ -399,3 +399,39 @@ def test_graph_replay_matches_direct_path(pkg):
             np.testing.assert_array_equal(gy[k * m:(k + 1) * m], ey.cpu().numpy())
         assert info_g["omega"] <= 1e-12
     s.close()
+
+
+# ------------------------------------------------------ normal equations
+
+def test_normal_equations_against_oracle(pkg):
+    """Eq. normeq with Eq. regul_matrix: M = A Theta~ A^T + delta I formed on
+    the GPU (deterministic pair sums), factorised, refined on M; dx recovered
+    as Theta~ (A^T dy - r7); the backward error is reported on K."""
+    from oracle import FORM_NE
+
+    for seed, (m, n) in enumerate(((60, 150), (200, 500))):
+        lp = synth.random_lp(m, n, 4, seed=70 + seed)
+        theta = synth.theta_loguniform(lp.n, 70 + seed, -3.0, 3.0)
+        r7, r1 = synth.rhs_normal(lp.n, 71), synth.rhs_normal(lp.m, 72)
+        s = pkg.Solver.from_lp(lp, form=pkg.IPM_FORM_NORMAL)
+        s.factorise(theta, RHO, DELTA)
+        dx, dy = s.solve(r7, r1)
+        info = s.info()
+        L, D, dyn = s.factor()
+        sym = s.symbolic()
+        x = np.concatenate([dx.cpu().numpy(), dy.cpu().numpy()])
+        o = Oracle.from_lp(lp, form=FORM_NE)
+        o.analyse(sym["perm"])
+        o.factorise(theta, RHO, DELTA, eps_piv=EPS_PIV)
+        of = o.factor()
+        ox, oy, oi = o.solve(r7, r1, omega_target=1e-12, max_steps=10)
+        ref = np.concatenate([ox, oy])
+        assert info["form"] == pkg.IPM_FORM_NORMAL and info["npos"] == lp.m
+        assert np.array_equal(dyn != 0, of["dynreg"] != 0)
+        sc = pivot_scales(sym, of["L"], of["D"])
+        assert np.all(np.abs(D - of["D"]) <= 1e-9 * sc)
+        w = o.omega_K(theta, RHO, DELTA, r7, r1, x[: lp.n], x[lp.n:])
+        assert w <= 1e-10 and info["omega"] == pytest.approx(w, rel=1e-6, abs=1e-300)
+        err = np.abs(x - ref).max() / np.abs(ref).max()
+        assert err <= 1e-8, f"solution rel err {err:.3e}"
+        s.close()
