@@ -315,3 +315,4 @@ def declared_symbols():
 
 
 from .solver import Solver  # noqa: E402,F401
+from .batch import BatchSolver, lpt_partition, shard  # noqa: E402,F401

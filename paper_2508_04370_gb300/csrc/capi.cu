@@ -479,6 +479,20 @@ int setup_device(ipm_ctx *c) {
     dp.kp = d_kp;
     dp.kj = d_kj;
     dp.ksrc = d_ksrc;
+    dp.batch_count = 0;
+    dp.inst = nullptr;
+    dp.inst_norm1 = dp.inst_b1 = nullptr;
+    if (P.batch_count > 0) {
+        int32_t *d_inst;
+        double *d_in, *d_ib;
+        if ((rc = dupload(c, &d_inst, P.inst)) || (rc = dalloc(c, &d_in, (size_t)P.batch_count)) ||
+            (rc = dalloc(c, &d_ib, (size_t)P.batch_count)))
+            return rc;
+        dp.batch_count = P.batch_count;
+        dp.inst = d_inst;
+        dp.inst_norm1 = d_in;
+        dp.inst_b1 = d_ib;
+    }
     const int64_t nnzA = P.Acp[P.n];
     if ((rc = dalloc(c, &c->fronts, (size_t)P.front_doubles)) || (rc = dalloc(c, &c->D, N)) ||
         (rc = dalloc(c, &c->dyn, N)) || (rc = dalloc(c, &c->ctl, 1)) || (rc = dalloc(c, &c->Ax, nnzA)) ||
@@ -800,6 +814,8 @@ int ipm_analyse(ipm_ctx *c, int32_t m, int32_t n, const int64_t *colptr, const i
             return rc;
         }
     }
+    c->plan.batch_count = 0;
+    c->plan.inst.clear();
     c->ms_analyse = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     c->analysed = true;
     return IPM_OK;
@@ -836,7 +852,23 @@ int ipm_analyse_batch(ipm_ctx *c, int32_t count, const int32_t *ms, const int32_
         col += ns[b];
         roff += ms[b];
     }
-    return ipm_analyse(c, (int32_t)M, (int32_t)Nn, cp.data(), ri.data(), IPM_FORM_AUGMENTED, ordering, nullptr);
+    const int rc = ipm_analyse(c, (int32_t)M, (int32_t)Nn, cp.data(), ri.data(), IPM_FORM_AUGMENTED, ordering,
+                               nullptr);
+    if (rc) return rc;
+    // instance of every unknown, in the factorisation order: the pivot floor
+    // eps_piv ||K||_1 of Sec. 4.5 is taken per instance, so that each problem
+    // is factorised exactly as it would be on its own
+    Plan &P = c->plan;
+    P.batch_count = count;
+    P.inst.assign(P.N, 0);
+    int64_t co = 0, ro = 0;
+    for (int32_t b = 0; b < count; b++) {
+        for (int32_t j = 0; j < ns[b]; j++) P.inst[P.iperm[co + j]] = b;
+        for (int32_t i = 0; i < ms[b]; i++) P.inst[P.iperm[Nn + ro + i]] = b;
+        co += ns[b];
+        ro += ms[b];
+    }
+    return IPM_OK;
 }
 
 

@@ -56,7 +56,18 @@ struct DevPlan {
     const int64_t *kp;
     const int32_t *kj;
     const int64_t *ksrc;
+    // batches of independent problems: instance of each unknown (factorisation
+    // order) and, per instance, ||K_b||_1 and eps_piv ||K_b||_1; null otherwise
+    int32_t batch_count;
+    const int32_t *inst;
+    double *inst_norm1, *inst_b1;
 };
+
+// eps_piv ||K||_1 of the problem that owns column c (Sec. 4.5); the norm is
+// per instance when independent problems are factorised together.
+__device__ __forceinline__ double pivot_floor(const DevPlan &P, const DevCtl *ctl, int c) {
+    return P.inst ? P.inst_b1[P.inst[c]] : ctl->b1;
+}
 
 constexpr int64_t kDualDiag = INT64_MIN;
 
@@ -113,7 +124,7 @@ void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, doubl
 // panel step 2 (rows below, kTrsmRowsHost rows per item; slots[i] = workspace slot of item i)
 void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,
                        int32_t p0, int32_t nb, const double *pws, cudaStream_t st);
-constexpr int kTrsmRowsHost = 32;
+constexpr int kTrsmRowsHost = 8;
 constexpr int kPanelWsHost = 32 * 33 + 32;
 void launch_large_update(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
                          int32_t p0, int32_t w, cudaStream_t st);

@@ -27,8 +27,10 @@ struct Plan {
     int32_t m = 0, n = 0, N = 0, form = 1, ordering = 0;
     std::vector<int64_t> Acp;  // CSC of A as given
     std::vector<int32_t> Ari;
-    // batch bookkeeping (empty for a single LP)
+    // batch bookkeeping (empty for a single LP): instance of every unknown,
+    // indexed in the factorisation order
     int32_t batch_count = 0;
+    std::vector<int32_t> inst;
 
     // symbolic, factorisation order
     std::vector<int32_t> perm, iperm, parent;

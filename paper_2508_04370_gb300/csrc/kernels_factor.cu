@@ -38,47 +38,93 @@ __device__ __forceinline__ double orig_value(const DevPlan &P, const DevVals &V,
 }
 
 // Pivot decision of Sec. 4.5 / Prop. 3 for pivot p of the block [0, w) held
-// column-major in shared memory (one full warp):
+// column-major in shared memory (one full warp, w <= 32):
 //   d   = F_pp + s_p sigma_p          (static term after the pivot is computed)
 //   b2  = max over j in (p, w) with s_j = s_p and s_j F_jj > 0 of F_jp^2 / |F_jj|
 //   d  <- s_p max(s_p d, max(eps_piv ||K||_1, b2)).
-// The maximum of the quotients is found by cross-multiplication, so only the
-// winning quotient is divided.  Lane 0 records D, the lift and the status and
-// returns the pivot and its reciprocal through shared memory.
+// Every FP64 instruction costs this GPU about 64 cycles per warp whatever
+// the number of active lanes, while integer instructions cost a few, so the
+// common case is decided with integer arithmetic on the IEEE bit patterns:
+// for non-negative doubles the bit pattern orders like the value, and
+// bits(x) / 2^52 - 1023 is a lower bound of log2(x) that is within 0.0861 of
+// it for normal x (and an upper-bound-preserving one for subnormal x).  A
+// candidate j is screened out when 2 log2|F_jp| < log2|F_jj| + log2(t) - 0.0278
+// with t = max(s_p d, eps_piv ||K||_1), which proves F_jp^2 / |F_jj| < t even
+// after rounding, so b2 cannot change the pivot.  If any candidate survives
+// the screen (rare: in exact arithmetic the same-sign block is definite and
+// b2 <= |d|), the bound is evaluated exactly as written above.  Either way the
+// result equals the plain evaluation of the rule.  Lane 0 records D, the
+// lift and the status and returns the pivot and its reciprocal through
+// shared memory.
+constexpr long long kSignBit = (long long)0x8000000000000000ull;
+constexpr long long kAbsMask = 0x7fffffffffffffffll;
+constexpr long long kInfBits = 0x7ff0000000000000ll;
+constexpr long long kBias = 0x3ff0000000000000ll;    // bits(1.0)
+constexpr long long kScreen = 0x0003333333333333ll;  // 0.2 * 2^52
+constexpr long long kTiny = 0x2000000000000000ll;    // bits(2^-511): squares stay normal above it
+constexpr long long kHuge = 0x5fe0000000000000ll;    // bits(2^511): squares stay finite below it
+
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// x > b for a non-negative, non-NaN b, with IEEE semantics (NaN > b is false).
+__device__ __forceinline__ bool gt_nonneg(long long xb, long long bb) {
+    return xb >= 0 && xb <= kInfBits && xb > bb;
+}
+
 __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int w, const int8_t *sgn, double rho,
                                            double delta, double b1floor, double *Dout, double *dynout, DevCtl *ctl,
                                            double *piv_out) {
     const int lane = threadIdx.x & 31;
     const int sp = sgn[p];
-    double num = 0.0, den = 1.0;  // candidate F_jp^2 / |F_jj|
-    for (int j = p + 1 + lane; j < w; j += 32) {
-        if (sgn[j] != sp) continue;
-        const double fjj = Fd[j * LDD + j];
-        if (!(sp * fjj > 0.0)) continue;
-        const double fjp = Fd[p * LDD + j];
-        const double n2 = fjp * fjp, d2 = fabs(fjj);
-        if (n2 * den > num * d2) {
-            num = n2;
-            den = d2;
+    const double d = Fd[p * LDD + p] + (sp < 0 ? -rho : delta);
+    const long long db = dbits(d);
+    const long long sdb = sp < 0 ? db ^ kSignBit : db;  // bits of s_p d
+    const long long b1b = dbits(b1floor);
+    const long long tb = gt_nonneg(sdb, b1b) ? sdb : b1b;  // bits of t = max(s_p d, b1)
+    const bool t_ok = tb > 0x000fffffffffffffll && tb < kInfBits;  // t normal and finite
+    bool maybe = false;
+    const int j = p + 1 + lane;
+    if (j < w && sgn[j] == sp) {
+        const long long jb = dbits(Fd[j * LDD + j]);
+        const long long ja = jb & kAbsMask;
+        const bool cand = ja != 0 && ja <= kInfBits && ((jb < 0) == (sp < 0));  // s_j F_jj > 0
+        if (cand) {
+            const long long ab = dbits(Fd[p * LDD + j]) & kAbsMask;
+            if (ab != 0) {
+                const bool screenable = t_ok && ab >= kTiny && ab < kHuge && ja > 0x000fffffffffffffll && ja < kInfBits;
+                maybe = !screenable || 2 * (ab - kBias) >= (ja - kBias) + (tb - kBias) - kScreen;
+            }
         }
     }
+    long long dnb;
+    if (__any_sync(0xffffffffu, maybe)) {
+        // exact evaluation of b2 and of the rule, as written
+        double b2 = 0.0;
+        if (j < w && sgn[j] == sp) {
+            const double fjj = Fd[j * LDD + j];
+            if (sp * fjj > 0.0) {
+                const double fjp = Fd[p * LDD + j];
+                const double v = fjp * fjp / fabs(fjj);
+                if (v > b2) b2 = v;
+            }
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double on = __shfl_xor_sync(0xffffffffu, num, o), od = __shfl_xor_sync(0xffffffffu, den, o);
-        if (on * den > num * od) {
-            num = on;
-            den = od;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, b2, o);
+            if (ov > b2) b2 = ov;
         }
-    }
-    if (lane == 0) {
-        const double b2 = num > 0.0 ? num / den : 0.0;
-        const double d = Fd[p * LDD + p] + (sp < 0 ? -rho : delta);
         const double bnd = b1floor > b2 ? b1floor : b2;
         const double sd = sp * d;
-        const double dn = sp * (sd > bnd ? sd : bnd);
+        dnb = dbits(sp * (sd > bnd ? sd : bnd));
+    } else {
+        dnb = sp < 0 ? tb ^ kSignBit : tb;
+    }
+    if (lane == 0) {
+        const double dn = __longlong_as_double(dnb);
         Dout[p] = dn;
-        dynout[p] = dn - d;
-        if (!isfinite(d) || !isfinite(dn) || dn == 0.0) atomicOr(&ctl->status, kStatNonFinite);
+        dynout[p] = dnb == db ? 0.0 : dn - d;
+        const bool fin = (db & kAbsMask) < kInfBits && (dnb & kAbsMask) < kInfBits && (dnb & kAbsMask) != 0;
+        if (!fin) atomicOr(&ctl->status, kStatNonFinite);
         piv_out[0] = dn;
         piv_out[1] = 1.0 / dn;
     }
@@ -125,7 +171,7 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
         __syncthreads();
     }
     const int8_t *sgn = P.sign + c0;
-    const double b1floor = ctl->b1;
+    const double b1floor = pivot_floor(P, ctl, c0);
     for (int b0 = 0; b0 < k; b0 += nb) {
         const int b1 = min(b0 + nb, k), w = b1 - b0;
         double *Fb = F + b0 * ld + b0;
@@ -227,12 +273,15 @@ __global__ void __launch_bounds__(256) k_large_assemble(DevPlan P, DevVals V, do
 }
 
 // Panel [p0, p1) of a large front, step 1: the nb x nb diagonal block,
-// one CTA per front.  Warp 0 decides each pivot (pivot_warp); all threads
-// scale the pivot column inside the block and apply the rank-1 update to the
-// block's remaining columns.  The factorised block goes back to the slab (L
-// strictly below the diagonal, D on it) together with D and the lifts, and
-// the panel workspace of the front receives W(q, p) = d_q L_pq (p > q) and
-// 1 / d_q for the triangular solve of the rows below.
+// one CTA per front.  Warp 0 decides each pivot (pivot_warp) and scales the
+// pivot column, keeping its unscaled copy w_j = F_jp; then all threads apply
+// the rank-1 update F_ij -= l_i w_j to the block's remaining lower triangle,
+// whose entries are enumerated densely (last column first) so that each warp
+// issues as few FP64 instructions as possible.  The factorised block goes
+// back to the slab (L strictly below the diagonal, D on it) together with D
+// and the lifts, and the panel workspace of the front receives the rows of
+// L_11 (row-major, ws[q * 33 + q'] = L_qq') and 1 / d_q for the triangular
+// solve of the rows below.
 constexpr int kPanelWs = 32 * 33 + 32;  // doubles of panel workspace per large front
 
 __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double *__restrict__ fronts,
@@ -240,8 +289,9 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
                                                      const PanelItem *__restrict__ items, int p0, int nb,
                                                      double *__restrict__ pws) {
     __shared__ double Fd[32 * 33];
-    __shared__ double Dtmp[32], dyntmp[32];
+    __shared__ double Dtmp[32], dyntmp[32], rtmp[32], wsave[32];
     __shared__ double piv[2];
+    __shared__ uint16_t tri[496];  // (column << 8 | row) of the strictly trailing triangle
     constexpr int LDD = 33, NT = 128;
     const PanelItem it = items[blockIdx.x];
     const int s = it.s;
@@ -249,34 +299,45 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
     const int w = min(p0 + nb, k) - p0;
     double *F = fronts + P.sn_off[s];
     double *ws = pws + (int64_t)it.r1 * kPanelWs;  // r1 carries the workspace slot
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 #pragma unroll
     for (int u = 0; u < 1024 / NT; u++) {
         const int t = tid + u * NT;
         const int jj = t >> 5, ii = t & 31;
         Fd[jj * LDD + ii] = (jj < w && ii < w && ii >= jj) ? F[(int64_t)(p0 + jj) * ld + (p0 + ii)] : 0.0;
     }
+    // entry e = r (r + 1) / 2 + c  ->  column w-1-r, row w-1-r+c  (0 <= c <= r)
+    for (int e = tid; e < (w - 1) * w / 2; e += NT) {
+        int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+        while ((r + 1) * (r + 2) / 2 <= e) r++;
+        while (r * (r + 1) / 2 > e) r--;
+        const int jj = w - 1 - r, ii = jj + (e - r * (r + 1) / 2);
+        tri[e] = (uint16_t)((jj << 8) | ii);
+    }
     __syncthreads();
     const int8_t *sgn = P.sign + c0 + p0;
-    const double b1floor = ctl->b1;
+    const double b1floor = pivot_floor(P, ctl, c0);
     for (int p = 0; p < w; p++) {
-        if (warp == 0) pivot_warp(Fd, LDD, p, w, sgn, V.rho, V.delta, b1floor, Dtmp, dyntmp, ctl, piv);
-        __syncthreads();
-        const double rinv = piv[1];
-        // all threads: scale the column, then the rank-1 update of the block
-        double wv = 0.0;
-        const int i = p + 1 + (tid & 31);
-        if (tid < 32 && i < w) {
-            wv = Fd[p * LDD + i];
+        if (warp == 0) {
+            pivot_warp(Fd, LDD, p, w, sgn, V.rho, V.delta, b1floor, Dtmp, dyntmp, ctl, piv);
+            __syncwarp();
+            const double rinv = piv[1];
+            const int i = p + 1 + lane;
+            if (i < w) {
+                const double v = Fd[p * LDD + i];
+                wsave[i] = v;
+                Fd[p * LDD + i] = v * rinv;
+            }
+            if (lane == 0) {
+                Fd[p * LDD + p] = piv[0];
+                rtmp[p] = rinv;
+            }
         }
         __syncthreads();
-        if (tid < 32 && i < w) Fd[p * LDD + i] = wv * rinv;
-        if (tid == 0) Fd[p * LDD + p] = piv[0];
-        __syncthreads();
-        for (int t = tid; t < 32 * 32; t += NT) {
-            const int jj = t >> 5, ii = t & 31;
-            if (jj > p && jj < w && ii >= jj && ii < w)
-                Fd[jj * LDD + ii] -= Fd[p * LDD + ii] * (Fd[p * LDD + jj] * piv[0]);
+        const int ne = (w - 1 - p) * (w - p) / 2;  // entries with column > p
+        for (int e = tid; e < ne; e += NT) {
+            const int code = tri[e], jj = code >> 8, ii = code & 255;
+            Fd[jj * LDD + ii] -= Fd[p * LDD + ii] * wsave[jj];
         }
         __syncthreads();
     }
@@ -284,10 +345,10 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
         const int jj = t >> 5, ii = t & 31;
         const bool in = jj < w && ii < w;
         if (in && ii >= jj) F[(int64_t)(p0 + jj) * ld + (p0 + ii)] = Fd[jj * LDD + ii];
-        ws[jj * 33 + ii] = (in && ii > jj) ? Dtmp[jj] * Fd[jj * LDD + ii] : 0.0;  // W(q = jj, p = ii)
+        ws[ii * 33 + jj] = (in && ii > jj) ? Fd[jj * LDD + ii] : 0.0;  // L(row ii, column jj), row-major
     }
     for (int t = tid; t < 32; t += NT) {
-        ws[32 * 33 + t] = t < w ? 1.0 / Dtmp[t] : 0.0;
+        ws[32 * 33 + t] = t < w ? rtmp[t] : 0.0;
         if (t < w) {
             Dg[c0 + p0 + t] = Dtmp[t];
             dyng[c0 + p0 + t] = dyntmp[t];
@@ -295,37 +356,51 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
     }
 }
 
-// Panel step 2: rows [r0, r1) below the diagonal block, one row per thread
-// (all lanes do useful FP64 work):  l_iq = (F_iq - sum_{q' < q} l_iq' W(q', q)) / d_q.
-constexpr int kTrsmRows = 32;
+// Panel step 2: rows [r0, r1) below the diagonal block, one warp per row
+// with one lane per pivot column q.  With u_iq = l_iq d_q the rows satisfy
+//   u_iq = F_iq - sum_{q' < q} u_iq' L_qq',   l_iq = u_iq / d_q,
+// so step q' broadcasts the finished u_iq' and every lane q > q' applies one
+// FMA: 32 dependent steps per row instead of 528 per thread when a thread
+// owns a whole row.
+constexpr int kTrsmRows = 8;
+static_assert(kTrsmRows == kTrsmRowsHost, "host and device row chunks differ");
 
-__global__ void __launch_bounds__(kTrsmRows) k_panel_trsm(DevPlan P, double *__restrict__ fronts,
-                                                           const PanelItem *__restrict__ items, const int32_t *slots,
-                                                           int p0, int nb, const double *__restrict__ pws) {
+__global__ void __launch_bounds__(32 * kTrsmRows) k_panel_trsm(DevPlan P, double *__restrict__ fronts,
+                                                                const PanelItem *__restrict__ items,
+                                                                const int32_t *slots, int p0, int nb,
+                                                                const double *__restrict__ pws) {
     __shared__ double Wd[32 * 33 + 32];
+    __shared__ double T[32][kTrsmRows + 1];
     const PanelItem it = items[blockIdx.x];
     const int s = it.s;
     const int k = P.sn_k[s], ld = P.sn_ld[s];
     const int w = min(p0 + nb, k) - p0;
+    const int nr = it.r1 - it.r0;
     double *F = fronts + P.sn_off[s];
     const double *ws = pws + (int64_t)slots[blockIdx.x] * kPanelWs;
-    const int tid = threadIdx.x;
-    for (int t = tid; t < 32 * 33 + 32; t += kTrsmRows) Wd[t] = ws[t];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int t = tid; t < 32 * 33 + 32; t += 32 * kTrsmRows) Wd[t] = ws[t];
+    {
+        const int q = tid / kTrsmRows, r = tid % kTrsmRows;
+        T[q][r] = (q < w && r < nr) ? F[(int64_t)(p0 + q) * ld + it.r0 + r] : 0.0;
+    }
     __syncthreads();
-    const int i = it.r0 + tid;
-    if (i < it.r1) {
-        double li[32];
+    if (warp < nr) {
+        double Lr[32];
 #pragma unroll
-        for (int q = 0; q < 32; q++) li[q] = q < w ? F[(int64_t)(p0 + q) * ld + i] : 0.0;
+        for (int q = 0; q < 32; q++) Lr[q] = Wd[lane * 33 + q];
+        double t = T[lane][warp];
 #pragma unroll
-        for (int q = 0; q < 32; q++) {
-            li[q] *= Wd[32 * 33 + q];
-#pragma unroll
-            for (int p = q + 1; p < 32; p++) li[p] -= li[q] * Wd[q * 33 + p];
+        for (int q = 0; q < 31; q++) {
+            const double u = __shfl_sync(0xffffffffu, t, q);
+            if (lane > q) t -= u * Lr[q];
         }
-#pragma unroll
-        for (int q = 0; q < 32; q++)
-            if (q < w) F[(int64_t)(p0 + q) * ld + i] = li[q];
+        T[lane][warp] = t * Wd[32 * 33 + lane];
+    }
+    __syncthreads();
+    {
+        const int q = tid / kTrsmRows, r = tid % kTrsmRows;
+        if (q < w && r < nr) F[(int64_t)(p0 + q) * ld + it.r0 + r] = T[q][r];
     }
 }
 
@@ -397,13 +472,19 @@ __global__ void k_norm1(DevPlan P, DevVals V, DevCtl *ctl) {
             sum += fabs(val);
         }
         mx = fmax(mx, sum);
+        if (P.inst) atomicMax((unsigned long long *)&P.inst_norm1[P.inst[i]], (unsigned long long)__double_as_longlong(sum));
     }
     mx = warp_max(mx);
     if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long *)&ctl->norm1, (unsigned long long)__double_as_longlong(mx));
     if (bad) atomicOr(&ctl->status, kStatNonFinite);
 }
 
-__global__ void k_set_b1(DevCtl *ctl, double eps_piv) { ctl->b1 = eps_piv * ctl->norm1; }
+__global__ void k_set_b1(DevPlan P, DevCtl *ctl, double eps_piv) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->b1 = eps_piv * ctl->norm1;
+    if (P.inst)
+        for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.batch_count; b += gridDim.x * blockDim.x)
+            P.inst_b1[b] = eps_piv * P.inst_norm1[b];
+}
 
 // Statistics of the factorisation: inertia, number and size of lifts.
 __global__ void k_factor_stats(const double *__restrict__ D, const double *__restrict__ dyn, int N, double large_reg,
@@ -469,7 +550,7 @@ void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, doubl
 void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,
                        int32_t p0, int32_t nb, const double *pws, cudaStream_t st) {
     if (count <= 0) return;
-    k_panel_trsm<<<count, kTrsmRows, 0, st>>>(P, fronts, items, slots, p0, nb, pws);
+    k_panel_trsm<<<count, 32 * kTrsmRows, 0, st>>>(P, fronts, items, slots, p0, nb, pws);
 }
 
 void launch_large_update(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
@@ -480,8 +561,9 @@ void launch_large_update(const DevPlan &P, double *fronts, const double *D, cons
 
 void launch_norm1(const DevPlan &P, const DevVals &V, DevCtl *ctl, double eps_piv, cudaStream_t st) {
     const int grid = (P.N + 255) / 256 < 608 ? (P.N + 255) / 256 : 608;
+    if (P.inst) cudaMemsetAsync(P.inst_norm1, 0, sizeof(double) * P.batch_count, st);
     k_norm1<<<grid > 0 ? grid : 1, 256, 0, st>>>(P, V, ctl);
-    k_set_b1<<<1, 1, 0, st>>>(ctl, eps_piv);
+    k_set_b1<<<P.inst ? (P.batch_count + 255) / 256 : 1, 256, 0, st>>>(P, ctl, eps_piv);
 }
 
 void launch_factor_stats(const double *D, const double *dyn, int N, double large_reg, DevCtl *ctl, cudaStream_t st) {

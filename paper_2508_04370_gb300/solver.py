@@ -29,7 +29,7 @@ class Solver:
                 raise KeyError(k)
             setattr(self.opt, k, v)
         self.ctx = ipm_create(self.opt)
-        rc = ipm_analyse(self.ctx, m, n, colptr, rowidx, form, ordering, user_perm)
+        rc = self._analyse(m, n, colptr, rowidx, form, ordering, user_perm)
         if rc:
             ipm_destroy(self.ctx)
             self.ctx = None
@@ -40,6 +40,9 @@ class Solver:
         if rc:
             raise RuntimeError(f"ipm_set_values failed ({rc})")
         self.N = self.n + self.m
+
+    def _analyse(self, m, n, colptr, rowidx, form, ordering, user_perm):
+        return ipm_analyse(self.ctx, m, n, colptr, rowidx, form, ordering, user_perm)
 
     @classmethod
     def from_lp(cls, lp, **kw):
