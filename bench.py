@@ -1,15 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the IPM linear-algebra hot path on one GB300.
 
-One step = one IPM iteration's linear algebra on the grid multicommodity LP
-(64 x 64 grid, 4 commodities, m = 24,444, n = 64,512): numeric factorisation
-of the regularised augmented system for a new Theta (nested-dissection
-order), then two solves with iterative refinement (predictor and one
-corrector).  The metric is ms per IPM iteration (lower is better), reported
-for the FP64 path and, when built, the mixed-precision path; the headline
-`value` is the fastest path that reaches its backward-error target.
+One step = one IPM iteration's linear algebra: numeric factorisation of the
+regularised augmented system for a new Theta, then two solves with
+iterative refinement (predictor and one corrector).  The metric is ms per IPM
+iteration (lower is better), reported for the FP64 path and the
+mixed-precision path; the headline `value` is the fastest path that reaches
+its backward-error target.
+
+The default workload is the grid multicommodity LP (64 x 64 grid,
+4 commodities, m = 24,444, n = 64,512, nested-dissection order).  Other
+workloads (--workload): random_300x800 (AMD), staircase (50 periods,
+m = 100,000, n = 250,000, Theta moving along a 40-iteration schedule) and
+batch512 (512 independent random LPs per GPU as one forest; with N GPUs the
+512 N instances are sharded over the ranks, no data exchange).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload NAME] [--paths fp64,mixed] [--no-cpu-baseline]
 Prints one JSON line on rank 0.
 """
 from __future__ import annotations
@@ -28,16 +35,77 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "grid64_q4"
 RHO = DELTA = 1e-8
 FP64_NOMINAL_TFLOPS = 1.25  # FP64 rate of a GB300 (profiling recipe's nominal table)
 L2_FLUSH_BYTES = 256 << 20
+BATCH_PER_GPU = 512
 
 
-def workload_desc(ordering_name):
-    return (f"grid multicommodity LP {WORKLOAD}: 64x64 4-neighbour grid, 4 commodities, m=24444, n=64512, "
-            f"entries +-1; Theta 10^U[-8,8]; rho=delta=1e-8; {ordering_name} ordering; one IPM iteration = "
-            f"factorise + 2 refined solves (predictor + 1 corrector)")
+class Workload:
+    """Inputs of one benchmark workload on one rank: the problem (an LP, or a
+    list of LPs factorised as one forest), three Theta vectors the timed steps
+    cycle through (a 40-entry schedule for the staircase), two right-hand
+    sides, the ordering and the FP64 path's backward-error target."""
+
+    def __init__(self, name, rank=0, world=1):
+        import synth
+
+        self.name = name
+        self.lps = None
+        self.fp64_target = 1e-12
+        if name == "batch512":
+            import paper_2508_04370_gb300.batch as B
+
+            sizes = synth.batched_sizes(count=BATCH_PER_GPU * world, seed=1)
+            self.ids = B.shard_sizes(sizes, rank, world)
+            self.lps = [synth.batched_instance(i, *sizes[i]) for i in self.ids]
+            self.ordering_name = "AMD"
+            self.thetas = [np.concatenate([synth.theta_loguniform(lp.n, 1000 * t + i)
+                                           for i, lp in zip(self.ids, self.lps)]) for t in range(3)]
+            n = sum(lp.n for lp in self.lps)
+            m = sum(lp.m for lp in self.lps)
+            self.desc = (f"{BATCH_PER_GPU * world} independent random LPs ({BATCH_PER_GPU} per GPU): m_i log-uniform "
+                         f"in [100, 5000], n_i = 2.5 m_i, 5 nonzeros per column, N(0,1); own Theta_i = 10^U[-8,8]; "
+                         f"one block-diagonal forest per GPU, AMD ordering; rank {rank}: {len(self.lps)} instances, "
+                         f"m={m}, n={n}; one IPM iteration = factorise + 2 refined solves")
+        else:
+            lp = synth.by_name(name, 1)
+            self.lp = lp
+            n, m = lp.n, lp.m
+            if name == "grid64_q4":
+                self.ordering_name = "nested-dissection"
+                self.desc = ("grid multicommodity LP grid64_q4: 64x64 4-neighbour grid, 4 commodities, m=24444, "
+                             "n=64512, entries +-1; Theta 10^U[-8,8]; rho=delta=1e-8; nested-dissection ordering; "
+                             "one IPM iteration = factorise + 2 refined solves (predictor + 1 corrector)")
+            elif name == "random_300x800":
+                self.ordering_name = "AMD"
+                self.desc = ("random sparse LP m=300, n=800, 6 nonzeros per column, N(0,1); Theta 10^U[-8,8]; "
+                             "rho=delta=1e-8; AMD ordering; factorise + 2 refined solves")
+            elif name == "staircase":
+                self.ordering_name = "nested-dissection"
+                self.fp64_target = 1e-10
+                self.desc = ("staircase LP: 50 periods of 2000 x 5000, density 0.002, 500 identity links to the next "
+                             "period (m=100000, n=250000); Theta_j = exp(s g_j) along a 40-iteration schedule "
+                             "(spread 1 to 1e-8..1e8); nested-dissection ordering; factorise + 2 solves refined to "
+                             "omega <= 1e-10 on both paths")
+            else:
+                raise SystemExit(f"unknown workload {name}")
+            if name == "staircase":
+                self.thetas = synth.theta_schedule(n, 40, 1)
+            else:
+                self.thetas = [synth.theta_loguniform(n, 1 + t) for t in range(3)]
+        n = len(self.thetas[0])
+        m = sum(lp.m for lp in self.lps) if self.lps else self.lp.m
+        self.n, self.m = n, m
+        self.rhs = [(synth.rhs_normal(n, 10 + 2 * t), synth.rhs_normal(m, 11 + 2 * t)) for t in range(2)]
+
+    def ordering(self, pkg):
+        return pkg.IPM_ORD_AMD if self.ordering_name == "AMD" else pkg.IPM_ORD_ND
+
+    def solver(self, pkg, **opts):
+        if self.lps is not None:
+            return pkg.BatchSolver(self.lps, ordering=self.ordering(pkg), **opts)
+        return pkg.Solver.from_lp(self.lp, ordering=self.ordering(pkg), **opts)
 
 
 def load_peaks():
@@ -118,35 +186,26 @@ def traffic_for(kernel):
     return ent["bytes_per_launch"] if sha == ent["source_sha"] else None
 
 
-def make_inputs(seed=1, nthetas=3):
-    import synth
-
-    lp = synth.by_name(WORKLOAD, seed)
-    thetas = [synth.theta_loguniform(lp.n, seed + t) for t in range(nthetas)]
-    rhs = [(synth.rhs_normal(lp.n, 10 + 2 * t), synth.rhs_normal(lp.m, 11 + 2 * t)) for t in range(2)]
-    return lp, thetas, rhs
-
-
 # ------------------------------------------------------------- our arm
 
-def run_ours(args, rank, world):
+def run_ours(args, W, rank, world):
     import torch
 
     import paper_2508_04370_gb300 as pkg
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    lp, thetas, rhs = make_inputs()
+    n, m = W.n, W.m
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     results = {}
-    precisions = [("fp64", pkg.IPM_PREC_FP64, 1e-12), ("mixed", pkg.IPM_PREC_MIXED, 1e-10)]
-    ordering = pkg.IPM_ORD_ND
+    precisions = [("fp64", pkg.IPM_PREC_FP64, W.fp64_target), ("mixed", pkg.IPM_PREC_MIXED, 1e-10)]
+    precisions = [p for p in precisions if p[0] in args.paths.split(",")]
     for pname, prec, target in precisions:
-        s = pkg.Solver.from_lp(lp, ordering=ordering, precision=prec, omega_target=target, device=dev.index)
-        th = [torch.as_tensor(t, device=dev) for t in thetas]
-        rr = [(torch.as_tensor(a, device=dev), torch.as_tensor(b, device=dev)) for a, b in rhs]
-        dx = torch.empty(lp.n, dtype=torch.float64, device=dev)
-        dy = torch.empty(lp.m, dtype=torch.float64, device=dev)
+        s = W.solver(pkg, precision=prec, omega_target=target, device=dev.index)
+        th = [torch.as_tensor(t, device=dev) for t in W.thetas]
+        rr = [(torch.as_tensor(a, device=dev), torch.as_tensor(b, device=dev)) for a, b in W.rhs]
+        dx = torch.empty(n, dtype=torch.float64, device=dev)
+        dy = torch.empty(m, dtype=torch.float64, device=dev)
         stream = torch.cuda.current_stream()
 
         def step(i):
@@ -185,11 +244,11 @@ def run_ours(args, rank, world):
         step_ms = [a.elapsed_time(b) for a, b in ev]
         info = s.info()
         # end to end through the host-buffer entry point
-        r7h = np.ascontiguousarray(np.concatenate([a for a, _ in rhs]))
-        r1h = np.ascontiguousarray(np.concatenate([b for _, b in rhs]))
-        dxh = np.empty(2 * lp.n)
-        dyh = np.empty(2 * lp.m)
-        thh = [np.ascontiguousarray(t) for t in thetas]
+        r7h = np.ascontiguousarray(np.concatenate([a for a, _ in W.rhs]))
+        r1h = np.ascontiguousarray(np.concatenate([b for _, b in W.rhs]))
+        dxh = np.empty(2 * n)
+        dyh = np.empty(2 * m)
+        thh = [np.ascontiguousarray(t) for t in W.thetas]
         for i in range(max(1, args.warmup)):
             pkg.ipm_iterate_host(s.ctx, thh[i % len(thh)], RHO, DELTA, r7h, r1h, dxh, dyh, nrhs=2, stream=stream)
         torch.cuda.synchronize()
@@ -203,15 +262,14 @@ def run_ours(args, rank, world):
             if rc < 0:
                 raise RuntimeError(f"ipm_iterate_host failed ({rc})")
         results[pname] = dict(step_ms=step_ms, wall_s=wall, kstats=kstats, info=info, omegas=omegas, clocks=clk,
-                              e2e_ms=e2e, target=target,
-                              h2d=8 * (lp.n + 2 * (lp.n + lp.m)), d2h=8 * 2 * (lp.n + lp.m))
+                              e2e_ms=e2e, target=target, h2d=8 * (n + 2 * (n + m)), d2h=8 * 2 * (n + m))
         # the same iteration captured once as a CUDA graph and replayed
-        th_buf = torch.empty(lp.n, dtype=torch.float64, device=dev)
+        th_buf = torch.empty(n, dtype=torch.float64, device=dev)
         th_buf.copy_(th[0])
         r7d = torch.cat([a for a, _ in rr])
         r1d = torch.cat([b for _, b in rr])
-        gdx = torch.empty(2 * lp.n, dtype=torch.float64, device=dev)
-        gdy = torch.empty(2 * lp.m, dtype=torch.float64, device=dev)
+        gdx = torch.empty(2 * n, dtype=torch.float64, device=dev)
+        gdy = torch.empty(2 * m, dtype=torch.float64, device=dev)
         rc = pkg.ipm_graph_capture(s.ctx, th_buf, RHO, DELTA, r7d, r1d, gdx, gdy, nsolves=2, stream=stream)
         if rc == 0:
             for i in range(args.warmup):
@@ -233,7 +291,7 @@ def run_ours(args, rank, world):
                                              info=s.info(), omegas=gom, clocks=clk, e2e_ms=e2e, target=target,
                                              h2d=results[pname]["h2d"], d2h=results[pname]["d2h"])
         s.close()
-    return lp, results
+    return results
 
 
 def roofline(kstats, peaks, sustained):
@@ -264,25 +322,91 @@ def roofline(kstats, peaks, sustained):
     return out
 
 
-def cpu_baseline(lp, thetas, rhs, ordering_perm, budget_s=12.0):
-    """The oracle as it stands, single thread, on the same workload."""
-    from oracle import Oracle
+class _OracleProblem:
+    """One problem of the workload for the oracle, analysed on first use."""
 
-    o = Oracle.from_lp(lp)
-    o.analyse(ordering_perm)
+    def __init__(self, lp, perm, thetas, rhs, weight):
+        self.lp, self.perm, self.thetas, self.rhs, self.weight = lp, perm, thetas, rhs, weight
+        self.o = None
+
+    def oracle(self):
+        from oracle import Oracle
+
+        if self.o is None:
+            self.o = Oracle.from_lp(self.lp)
+            self.o.analyse(self.perm)
+        return self.o
+
+
+def oracle_problems(W, pkg):
+    """The workload's problems for the oracle, in the library's order
+    (batches: per instance, the batch order restricted to it)."""
+    s = W.solver(pkg)
+    perm = s.symbolic()["perm"]
+    s.close()
+    if W.lps is None:
+        return [_OracleProblem(W.lp, perm, W.thetas, W.rhs, 1.0)]
+    out = []
+    nof = np.concatenate([[0], np.cumsum([lp.n for lp in W.lps])])
+    mof = np.concatenate([[0], np.cumsum([lp.m for lp in W.lps])])
+    Nn = int(nof[-1])
+    inst = np.empty(len(perm), dtype=np.int64)
+    loc = np.empty(len(perm), dtype=np.int64)
+    for b, lp in enumerate(W.lps):
+        inst[nof[b]:nof[b + 1]] = b
+        loc[nof[b]:nof[b + 1]] = np.arange(lp.n)
+        inst[Nn + mof[b]:Nn + mof[b + 1]] = b
+        loc[Nn + mof[b]:Nn + mof[b + 1]] = lp.n + np.arange(lp.m)
+    pi, pl = inst[perm], loc[perm]
+    import paper_2508_04370_gb300.batch as B
+
+    total = sum(B.instance_cost(lp.m, lp.n, int(lp.colptr[-1])) for lp in W.lps)
+    for b, lp in enumerate(W.lps):
+        th = [t[nof[b]:nof[b + 1]] for t in W.thetas]
+        rhs = [(a[nof[b]:nof[b + 1]], c[mof[b]:mof[b + 1]]) for a, c in W.rhs]
+        out.append(_OracleProblem(lp, pl[pi == b].astype(np.int32), th, rhs,
+                                  B.instance_cost(lp.m, lp.n, int(lp.colptr[-1])) / total))
+    return out
+
+
+def oracle_iteration(probs, i, target, budget_end=None):
+    """One IPM iteration of the oracle over the problems (or as many as fit
+    before budget_end); returns (ms, fraction of the workload's work done).
+    The symbolic analysis of a problem is not timed."""
+    ms = 0.0
+    frac = 0.0
+    for pb in probs:
+        o = pb.oracle()
+        t0 = time.perf_counter()
+        o.factorise(pb.thetas[i % len(pb.thetas)], RHO, DELTA)
+        for a, b in pb.rhs:
+            o.solve(a, b, omega_target=target, max_steps=10)
+        ms += (time.perf_counter() - t0) * 1e3
+        frac += pb.weight
+        if budget_end is not None and time.perf_counter() > budget_end:
+            break
+    return ms, frac
+
+
+def cpu_baseline(W, pkg, budget_s=12.0):
+    """The oracle as it stands, single thread, on a bounded sample of the
+    same workload, scaled to one full IPM iteration."""
+    probs = oracle_problems(W, pkg)
     times = []
     t_end = time.perf_counter() + budget_s
     i = 0
     while True:
-        t0 = time.perf_counter()
-        o.factorise(thetas[i % len(thetas)], RHO, DELTA)
-        for a, b in rhs:
-            o.solve(a, b, omega_target=1e-12, max_steps=10)
-        times.append((time.perf_counter() - t0) * 1e3)
+        ms, frac = oracle_iteration(probs, i, W.fp64_target, t_end if len(probs) > 1 else None)
+        times.append(ms / frac)
         i += 1
         if time.perf_counter() > t_end or i >= 50:
             break
-    return float(np.median(times)), i
+    if len(probs) > 1:
+        sample = (f"instances of the batch in order until {budget_s:.0f} s (factorise + 2 refined solves each), "
+                  f"time scaled by their share of the nnz(A) sqrt(m) work estimate")
+    else:
+        sample = f"{i} full IPM iterations of the same workload (factorise + 2 refined solves), median"
+    return float(np.median(times)), sample + "; symbolic analysis excluded"
 
 
 def main():
@@ -292,6 +416,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="grid64_q4",
+                    choices=["grid64_q4", "random_300x800", "staircase", "batch512"])
+    ap.add_argument("--paths", default="fp64,mixed", help="comma-separated subset of fp64,mixed")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -309,7 +436,8 @@ def main():
         build()
     if world > 1:
         torch.distributed.barrier()
-    lp, results = run_ours(args, rank, world)
+    W = Workload(args.workload, rank, world)
+    results = run_ours(args, W, rank, world)
     import paper_2508_04370_gb300 as pkg
 
     peaks = load_peaks()
@@ -320,7 +448,6 @@ def main():
         ms = float(np.sum(r["step_ms"]) / len(r["step_ms"]))
         ok = max(r["omegas"]) <= r["target"]
         fl = r["info"]["flops_factor"]
-        fact_ms = r["kstats"]
         per[pname] = {"ms_per_iter": ms, "met_target": bool(ok), "omega_max": max(r["omegas"]),
                       "omega_target": r["target"], "refine_steps_last": r["info"]["refine_steps"],
                       "front_flops": fl, "e2e_ms_per_iter": float(np.median(r["e2e_ms"])),
@@ -347,7 +474,9 @@ def main():
         ms_max = float(t.item())
     else:
         ms_max = ms_local
-    value = ms_max / world  # replicas: whole-job ms per IPM iteration
+    # whole-job ms per IPM iteration of the workload: every rank runs its own
+    # problem (a replica of the single LP, or its shard of the batch) at once
+    value = ms_max / world
     launches = sum(v["launches"] for v in r["kstats"].values())
     rl = roofline(r["kstats"], peaks, sustained=False)
     step_total = float(np.sum(r["step_ms"]))
@@ -365,9 +494,10 @@ def main():
         "vs_baseline": None,
         "dtype": "f64+tf32" if per[best]["tensor_cores_in_use"] else "f64",
         "data": "synthetic",
-        "config": {"workload": workload_desc("nested-dissection"), "path": best,
+        "config": {"workload": W.desc, "path": best,
                    "l2": "flushed between timed steps (256 MiB write outside the step events)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                   "parallelism": (f"batch sharded over {world} GPUs (no collective)" if W.lps is not None
+                                   else f"replicas x{world}") if world > 1 else "1 GPU"},
         "paths": per,
         "roofline": rl,
         "gpu_launches": int(launches),
@@ -376,14 +506,8 @@ def main():
                 "h2d_bytes_per_step": int(r["h2d"]), "d2h_bytes_per_step": int(r["d2h"])},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        _, thetas, rhs = make_inputs()
-        s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND)
-        perm = s.symbolic()["perm"]
-        s.close()
-        v, n = cpu_baseline(lp, thetas, rhs, perm)
-        out["cpu_baseline"] = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
-                               "sample": f"{n} full IPM iterations of the same workload (factorise + 2 refined "
-                                         f"solves), median; symbolic analysis excluded"}
+        v, sample = cpu_baseline(W, pkg)
+        out["cpu_baseline"] = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -395,36 +519,31 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import paper_2508_04370_gb300 as pkg
-    from oracle import Oracle
 
-    lp, thetas, rhs = make_inputs()
-    ctx = pkg.ipm_create()
-    pkg.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, pkg.IPM_FORM_AUGMENTED, pkg.IPM_ORD_ND)
-    perm = pkg.ipm_get_symbolic(ctx)["perm"]
-    pkg.ipm_destroy(ctx)
-    o = Oracle.from_lp(lp)
-    o.analyse(perm)
+    W = Workload(args.workload, 0, 1)
+    probs = oracle_problems(W, pkg)
+    budget = 20.0  # seconds of oracle work per timed step at most (batches: a sample of the instances)
 
     def step(i):
-        o.factorise(thetas[i % len(thetas)], RHO, DELTA)
-        for a, b in rhs:
-            o.solve(a, b, omega_target=1e-12, max_steps=10)
+        end = time.perf_counter() + budget if len(probs) > 1 else None
+        ms, frac = oracle_iteration(probs, i, W.fp64_target, end)
+        return ms / frac
 
     for i in range(args.warmup):
         step(i)
-    times = []
-    for i in range(args.steps):
-        t0 = time.perf_counter()
-        step(i)
-        times.append((time.perf_counter() - t0) * 1e3)
+    times = [step(i) for i in range(args.steps)]
     v = float(np.mean(times))
+    if len(probs) > 1:
+        sample = ("each step: instances of the batch in order until 20 s, time scaled by their share of the "
+                  "nnz(A) sqrt(m) work estimate")
+    else:
+        sample = f"{args.steps} full IPM iterations (factorise + 2 refined solves)"
     out = {"impl": "reference", "metric": "factorise+solve ms per IPM iteration (front GFLOP/s alongside), mixed vs "
            "FP64 at backward error", "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_desc("nested-dissection"), "path": "oracle"},
-           "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
-                            "sample": f"{args.steps} full IPM iterations (factorise + 2 refined solves)"},
+           "config": {"workload": W.desc, "path": "oracle"},
+           "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -892,7 +892,8 @@ static void ne_products(const orc *o, const double *d, const double *f, double *
 /* Component-wise backward error of Arioli, Demmel and Duff (Sec. 4.5):
  *   omega = max_i |f - M d|_i / (|M||d| + |f|)_i,
  * where a denominator not larger than tau_i = 1000 N eps (||M_i||_1 ||d||_inf
- * + |f_i|) is replaced by (|M||d| + ||d||_inf |M| e)_i. */
+ * + |f_i|) is replaced by (|M||d| + ||d||_inf |M| e)_i.  A component whose
+ * residual or denominator is NaN makes omega infinite. */
 double orc_backward_error(int N, const double *r, const double *ad, const double *ae,
                           const double *f, const double *d) {
     double dinf = 0.0;
@@ -905,7 +906,8 @@ double orc_backward_error(int N, const double *r, const double *ad, const double
         if (den <= tau) den = ad[i] + dinf * ae[i];
         double num = fabs(r[i]);
         double wi;
-        if (den > 0.0) wi = num / den;
+        if (isnan(num) || isnan(den)) wi = INFINITY; /* a non-finite residual is no backward error */
+        else if (den > 0.0) wi = num / den;
         else wi = (num > 0.0) ? INFINITY : 0.0;
         if (wi > w || isnan(wi)) w = wi;
     }

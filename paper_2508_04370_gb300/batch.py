@@ -46,6 +46,14 @@ def shard(lps, rank: int, world: int) -> list[int]:
     return lpt_partition(costs, world)[rank]
 
 
+def shard_sizes(sizes, rank: int, world: int, per_col: int = 5) -> list[int]:
+    """The same partition from the instance sizes alone ((m_i, n_i) with
+    per_col nonzeros per column), so that a rank generates only its own
+    instances."""
+    costs = [instance_cost(m, n, per_col * n) for m, n in sizes]
+    return lpt_partition(costs, world)[rank]
+
+
 class BatchSolver(Solver):
     """One context for a list of independent LPs (block-diagonal forest)."""
 

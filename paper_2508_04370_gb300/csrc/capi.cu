@@ -74,7 +74,7 @@ struct ipm_ctx {
     int64_t device_bytes = 0;
     DevPlan dp{};
     DevCtl *ctl = nullptr;
-    double *fronts = nullptr, *D = nullptr, *dyn = nullptr;
+    double *fronts = nullptr, *D = nullptr, *Dinv = nullptr, *dyn = nullptr;
     double *Ax = nullptr;
     double *theta = nullptr;  // owned copy for host entry points
     double *vf = nullptr, *vx = nullptr, *vbest = nullptr, *vr = nullptr, *vad = nullptr, *vae = nullptr,
@@ -82,6 +82,7 @@ struct ipm_ctx {
     double *h_r7 = nullptr, *h_r1 = nullptr, *d_r7 = nullptr, *d_r1 = nullptr, *d_dx = nullptr, *d_dy = nullptr;
     int32_t *lvl_small = nullptr, *lvl_all = nullptr;
     int32_t *bwd_order = nullptr, *solve_sync = nullptr;
+    SolveSched sched{};  // dependency-driven solve schedule (device pointers)
     int32_t solve_maxf = 0, solve_grid = 0;
     PanelItem *asm_items = nullptr, *panel_items = nullptr, *trsm_items = nullptr;
     int32_t *trsm_slots = nullptr;
@@ -220,6 +221,106 @@ void free_device(ipm_ctx *c) {
 }
 
 // Build the device plan and the large-front work lists, then upload.
+// Solve schedule: per-supernode descriptors, per-row gather lists of the
+// children's contributions (children ascending, so every row sums in the
+// same order as a child-by-child scatter), and the forward / backward item
+// lists in topological order.
+int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, const std::vector<int32_t> &bwd_order,
+                         const int32_t *d_rows) {
+    const Plan &P = c->plan;
+    const int32_t ns = P.nsuper;
+    std::vector<SolveNode> nodes(ns);
+    int64_t bp = 0;
+    for (int32_t s = 0; s < ns; s++) {
+        SolveNode &nd = nodes[s];
+        nd.off = P.sn_off[s];
+        nd.upd = P.upd_off[s];
+        nd.rptr = P.sn_rptr[s];
+        nd.f = P.sn_f[s];
+        nd.k = P.sn_k[s];
+        nd.ld = P.sn_ld[s];
+        nd.c0 = P.sn_start[s];
+        nd.parent = P.sn_parent[s];
+        nd.nchild = P.child_ptr[s + 1] - P.child_ptr[s];
+        const int64_t rect = (int64_t)nd.k * (nd.f - nd.k);
+        nd.nblk = (nd.k + 31) / 32;
+        nd.nrect = (nd.f > nd.k && (rect >= kRectSplit || nd.nblk > 1)) ? (nd.f - nd.k + kRectRows - 1) / kRectRows : 0;
+        nd.bpart = bp;
+        bp += (int64_t)nd.nrect * nd.k;
+    }
+    const int64_t nrows = P.sn_rptr[ns];
+    std::vector<int64_t> grp(nrows + 1, 0);
+    for (int32_t s = 0; s < ns; s++)
+        for (int32_t q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
+            const int32_t ch = P.child_list[q];
+            const int32_t cc = P.sn_f[ch] - P.sn_k[ch];
+            for (int32_t r = 0; r < cc; r++) grp[P.sn_rptr[s] + P.relmap[P.map_off[ch] + r] + 1]++;
+        }
+    for (int64_t i = 0; i < nrows; i++) grp[i + 1] += grp[i];
+    std::vector<int64_t> gsrc(std::max<int64_t>(grp[nrows], 1));
+    {
+        std::vector<int64_t> fill(grp.begin(), grp.end() - 1);
+        for (int32_t s = 0; s < ns; s++)
+            for (int32_t q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
+                const int32_t ch = P.child_list[q];
+                const int32_t cc = P.sn_f[ch] - P.sn_k[ch];
+                for (int32_t r = 0; r < cc; r++)
+                    gsrc[fill[P.sn_rptr[s] + P.relmap[P.map_off[ch] + r]]++] = P.upd_off[ch] + r;
+            }
+    }
+    // Ticket order: critical path first.  With a latency model of one item,
+    // the forward priority of s is the longest path from s to the root and the
+    // backward priority the longest path from s down to a leaf; both orders
+    // sorted by decreasing priority are topological (a child's forward
+    // priority exceeds its parent's, a parent's backward priority exceeds its
+    // children's), and they start the long chains first.
+    std::vector<double> wcost(ns), up(ns, 0.0), down(ns, 0.0);
+    for (int32_t s = 0; s < ns; s++) {
+        const double k = nodes[s].k, f = nodes[s].f;
+        const double rect = nodes[s].nrect > 0 ? 32.0 * k : (f - k) * k;
+        wcost[s] = 4.0 + 3.0 * nodes[s].nblk + rect / 1500.0;  // microseconds, roughly
+    }
+    for (int32_t s = ns - 1; s >= 0; s--) up[s] = wcost[s] + (nodes[s].parent >= 0 ? up[nodes[s].parent] : 0.0);
+    for (int32_t s = 0; s < ns; s++) {
+        down[s] += wcost[s];
+        if (nodes[s].parent >= 0) down[nodes[s].parent] = std::max(down[nodes[s].parent], down[s]);
+    }
+    std::vector<int32_t> of(fwd_order), ob(bwd_order);
+    std::stable_sort(of.begin(), of.end(), [&](int32_t a, int32_t b) { return up[a] > up[b]; });
+    std::stable_sort(ob.begin(), ob.end(), [&](int32_t a, int32_t b) { return down[a] > down[b]; });
+    std::vector<SolveItem> fwd, bwd;
+    for (int32_t s : of) {
+        for (int32_t b = 0; b < nodes[s].nblk; b++) fwd.push_back({s, -1 - b});
+        for (int32_t r = 0; r < nodes[s].nrect; r++) fwd.push_back({s, r});
+    }
+    for (int32_t s : ob) {
+        for (int32_t r = 0; r < nodes[s].nrect; r++) bwd.push_back({s, r});
+        for (int32_t b = nodes[s].nblk - 1; b >= 0; b--) bwd.push_back({s, -1 - b});
+    }
+    SolveNode *d_nodes;
+    int64_t *d_grp, *d_gsrc;
+    SolveItem *d_fwd, *d_bwd;
+    double *d_yv, *d_bp;
+    int rc;
+    if ((rc = dupload(c, &d_nodes, nodes)) || (rc = dupload(c, &d_grp, grp)) || (rc = dupload(c, &d_gsrc, gsrc)) ||
+        (rc = dupload(c, &d_fwd, fwd)) || (rc = dupload(c, &d_bwd, bwd)) || (rc = dalloc(c, &d_yv, (size_t)P.N)) ||
+        (rc = dalloc(c, &d_bp, (size_t)std::max<int64_t>(bp, 1))))
+        return rc;
+    SolveSched &S = c->sched;
+    S.node = d_nodes;
+    S.sn_rows = d_rows;
+    S.gat_rp = d_grp;
+    S.gat_src = d_gsrc;
+    S.fwd = d_fwd;
+    S.bwd = d_bwd;
+    S.nitems = (int32_t)fwd.size();
+    S.nsuper = ns;
+    S.sync = c->solve_sync;
+    S.yv = d_yv;
+    S.bpart = d_bp;
+    return IPM_OK;
+}
+
 int setup_device(ipm_ctx *c) {
     const Plan &P = c->plan;
     cudaError_t e = cudaSetDevice(c->opt.device);
@@ -440,7 +541,7 @@ int setup_device(ipm_ctx *c) {
         (rc = dalloc(c, &c->panel_ws, (size_t)std::max(nslots, 1) * kPanelWsHost)) ||
         (rc = dupload(c, &c->tile_items, tile_items)) || (rc = dupload(c, &c->tc_items, tc_items)) ||
         (rc = dupload(c, &c->alt_items, alt_items)) || (rc = dupload(c, &c->bwd_order, bwd_order)) ||
-        (rc = dalloc(c, &c->solve_sync, (size_t)ns + 1)))
+        (rc = dalloc(c, &c->solve_sync, (size_t)3 * ns + 1)))
         return rc;
     int32_t *d_sparent;
     if ((rc = dupload(c, &d_sparent, P.sn_parent))) return rc;
@@ -449,7 +550,7 @@ int setup_device(ipm_ctx *c) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_probe_kernel(), 256,
-                                                      (size_t)P.max_f * sizeof(double));
+                                                      (size_t)std::max(P.max_f, kRectRows) * sizeof(double));
         c->solve_grid = std::max(1, std::min(ns, sms * std::max(1, per_sm)));
     }
     DevPlan &dp = c->dp;
@@ -493,8 +594,10 @@ int setup_device(ipm_ctx *c) {
         dp.inst_norm1 = d_in;
         dp.inst_b1 = d_ib;
     }
+    if ((rc = build_solve_schedule(c, lvl_all, bwd_order, d_rows))) return rc;
     const int64_t nnzA = P.Acp[P.n];
     if ((rc = dalloc(c, &c->fronts, (size_t)P.front_doubles)) || (rc = dalloc(c, &c->D, N)) ||
+        (rc = dalloc(c, &c->Dinv, N)) ||
         (rc = dalloc(c, &c->dyn, N)) || (rc = dalloc(c, &c->ctl, 1)) || (rc = dalloc(c, &c->Ax, nnzA)) ||
         (rc = dalloc(c, &c->theta, P.n)) ||
         (rc = dalloc(c, &c->vf, N)) || (rc = dalloc(c, &c->vx, N)) || (rc = dalloc(c, &c->vbest, N)) ||
@@ -573,8 +676,8 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         const LevelWork &W = c->levels[l];
         for (const SmallClass &C : W.small) {
             Prof pr(c, IPM_K_SMALL_FRONTS, C.w, st);
-            launch_small_fronts(c->dp, V, c->fronts, c->D, c->dyn, c->ctl, c->lvl_small + C.off, C.cnt, c->opt.nb,
-                                C.maxf, st);
+            launch_small_fronts(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_small + C.off, C.cnt,
+                                c->opt.nb, C.maxf, st);
             nl++;
         }
         if (W.asm_cnt > 0) {
@@ -585,7 +688,7 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         for (const StepWork &S : W.steps) {
             {
                 Prof pr(c, IPM_K_LARGE_PANEL, S.panel_w, st);
-                launch_panel_diag(c->dp, V, c->fronts, c->D, c->dyn, c->ctl, c->panel_items + S.panel_off,
+                launch_panel_diag(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->panel_items + S.panel_off,
                                   S.panel_cnt, S.p0, c->opt.nb, c->panel_ws, st);
             }
             nl++;
@@ -626,7 +729,6 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
 // x <- (L D L^T)^-1 x in the factorisation order: one persistent launch per
 // sweep (dependency-driven, see kernels_solve.cu).
 int solve_inplace(ipm_ctx *c, double *x, cudaStream_t st, int *nl) {
-    const Plan &P = c->plan;
     Work fw, bw;
     for (const LevelWork &W : c->levels) {
         fw.flops += W.fwd_w.flops;
@@ -636,13 +738,11 @@ int solve_inplace(ipm_ctx *c, double *x, cudaStream_t st, int *nl) {
     }
     {
         Prof pr(c, IPM_K_FORWARD, fw, st);
-        launch_forward_persistent(c->dp, c->fronts, c->D, x, c->upd, c->lvl_all, P.nsuper, c->solve_sync,
-                                  c->solve_maxf, c->solve_grid, c->ctl, st);
+        launch_forward_persistent(c->sched, c->fronts, c->Dinv, x, c->upd, c->solve_maxf, c->solve_grid, c->ctl, st);
     }
     {
         Prof pr(c, IPM_K_BACKWARD, bw, st);
-        launch_backward_persistent(c->dp, c->fronts, x, c->bwd_order, P.nsuper, c->solve_sync, c->solve_maxf,
-                                   c->solve_grid, c->ctl, st);
+        launch_backward_persistent(c->sched, c->fronts, x, c->solve_maxf, c->solve_grid, c->ctl, st);
     }
     *nl += 2;
     return to_err(cudaGetLastError());
@@ -668,19 +768,16 @@ int solve_device_driven(ipm_ctx *c, const double *r7, const double *r1, double *
     if (P.form == 2) launch_ne_rhs(c->ne, c->dp.perm, c->Ax, r7, r1, c->vf, st);
     else launch_permute_in(c->dp, r7, r1, c->vf, st);
     launch_copy_if(c->vx, c->vf, N, nullptr, 0, st);
-    launch_forward_persistent(c->dp, c->fronts, c->D, c->vx, c->upd, c->lvl_all, P.nsuper, c->solve_sync, c->solve_maxf,
-                              c->solve_grid, c->ctl, st);
-    launch_backward_persistent(c->dp, c->fronts, c->vx, c->bwd_order, P.nsuper, c->solve_sync, c->solve_maxf,
-                               c->solve_grid, c->ctl, st);
+    launch_forward_persistent(c->sched, c->fronts, c->Dinv, c->vx, c->upd, c->solve_maxf, c->solve_grid, c->ctl, st);
+    launch_backward_persistent(c->sched, c->fronts, c->vx, c->solve_maxf, c->solve_grid, c->ctl, st);
     launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st);
     launch_refine_init(c->ctl, target, rmax, st);
     launch_copy_if(c->vbest, c->vx, N, nullptr, 0, st);
     for (int32_t step = 1; step <= rmax; step++) {
         launch_copy_if(c->vc, c->vr, N, done, 1, st);
-        launch_forward_persistent(c->dp, c->fronts, c->D, c->vc, c->upd, c->lvl_all, P.nsuper, c->solve_sync,
-                                  c->solve_maxf, c->solve_grid, c->ctl, st, done);
-        launch_backward_persistent(c->dp, c->fronts, c->vc, c->bwd_order, P.nsuper, c->solve_sync, c->solve_maxf,
-                                   c->solve_grid, c->ctl, st, done);
+        launch_forward_persistent(c->sched, c->fronts, c->Dinv, c->vc, c->upd, c->solve_maxf, c->solve_grid, c->ctl, st,
+                                  done);
+        launch_backward_persistent(c->sched, c->fronts, c->vc, c->solve_maxf, c->solve_grid, c->ctl, st, done);
         launch_axpy(c->vx, c->vc, N, st, done);
         launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st, done);
         launch_refine_step(c->ctl, target, step, rmax, st);
@@ -993,12 +1090,15 @@ static int solve_once(ipm_ctx *c, const double *r7, const double *r1, double *dx
 int ipm_solve(ipm_ctx *c, const double *r7, const double *r1, double *dx, double *dy, void *stream) {
     int rc = solve_once(c, r7, r1, dx, dy, stream);
     if (rc) return rc;
-    // mixed precision: when refinement stalls above the target, factorise
-    // again in FP64 and solve again; later factorisations stay in FP64
-    if (c->mixed_active && c->omega_sys > c->opt.omega_target) {
+    // mixed precision: when refinement stalls above the target (or the
+    // FP32-accurate updates drove a pivot to overflow), factorise again in
+    // FP64 and solve again; later factorisations stay in FP64.  The status of
+    // the abandoned factorisation is dropped.
+    if (c->mixed_active && !(c->omega_sys <= c->opt.omega_target)) {
         c->mixed_active = false;
         c->fallbacks++;
-        c->status_acc &= ~kStatRefineFail;
+        c->status_acc &= ~(kStatRefineFail | kStatNonFinite | kStatDynReg | kStatLargeReg);
+        cudaMemsetAsync(&c->ctl->status, 0, sizeof(int32_t), (cudaStream_t)stream);
         if ((rc = factorise_enqueue(c, c->theta, c->rho, c->delta, (cudaStream_t)stream))) return rc;
         rc = solve_once(c, r7, r1, dx, dy, stream);
     }

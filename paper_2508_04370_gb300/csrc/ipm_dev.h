@@ -101,6 +101,35 @@ struct NeView {
     const int32_t *Ari;
 };
 
+// Dependency-driven solve schedule, built once per pattern.  A supernode
+// with k > 32 or a large rectangular part L21 is split into one item per
+// 32-column block of L11 and row-chunk items (kRectRows rows of L21 each),
+// which run on other SMs.
+struct SolveNode {
+    int64_t off;    // slab offset (doubles)
+    int64_t upd;    // offset of its contribution vector
+    int64_t rptr;   // first entry in sn_rows and gat_rp
+    int64_t bpart;  // backward partial sums (nrect x k doubles)
+    int32_t f, k, ld, c0;
+    int32_t parent, nchild, nrect, nblk;  // nblk: items of L11 (32-column blocks; 1 when unsplit)
+};
+struct SolveItem {
+    int32_t s, r;  // r < 0: block -1-r of L11; else row chunk r of L21
+};
+struct SolveSched {
+    const SolveNode *node;
+    const int32_t *sn_rows;
+    const int64_t *gat_rp;   // per front row: range in gat_src
+    const int64_t *gat_src;  // contribution-vector positions summed into the row, children ascending
+    const SolveItem *fwd, *bwd;
+    int32_t nitems, nsuper;
+    int32_t *sync;           // ticket + 3 x nsuper counters
+    double *yv;              // forward: y of split supernodes (before D^-1)
+    double *bpart;           // backward: partial sums of split supernodes
+};
+constexpr int kRectRows = 32;
+constexpr int64_t kRectSplit = 8192;  // split when k (f - k) reaches this
+
 // Work item of the large-front path.
 struct PanelItem {
     int32_t s;       // supernode
@@ -114,12 +143,14 @@ struct TileItem {
 // ---------------------------------------------------------------- launches
 // factorisation (kernels_factor.cu)
 void launch_norm1(const DevPlan &P, const DevVals &V, DevCtl *ctl, double eps_piv, cudaStream_t st);
-void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *dyn, DevCtl *ctl,
+void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
+                         DevCtl *ctl,
                          const int32_t *list, int32_t count, int32_t nb, int32_t maxf, cudaStream_t st);
 void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, const PanelItem *items,
                            int32_t count, cudaStream_t st);
 // panel step 1 (diagonal block, one item per front; item.r1 = workspace slot)
-void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *dyn, DevCtl *ctl,
+void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
+                       DevCtl *ctl,
                        const PanelItem *items, int32_t count, int32_t p0, int32_t nb, double *pws, cudaStream_t st);
 // panel step 2 (rows below, kTrsmRowsHost rows per item; slots[i] = workspace slot of item i)
 void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,
@@ -136,12 +167,11 @@ void launch_forward(const DevPlan &P, const double *fronts, const double *D, dou
                     const int32_t *list, int32_t count, int32_t maxf, cudaStream_t st);
 void launch_backward(const DevPlan &P, const double *fronts, double *x, const int32_t *list, int32_t count,
                      int32_t maxf, cudaStream_t st);
-void launch_forward_persistent(const DevPlan &P, const double *fronts, const double *D, double *x, double *upd,
-                               const int32_t *order, int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid,
-                               DevCtl *ctl, cudaStream_t st, const int32_t *skip = nullptr);
-void launch_backward_persistent(const DevPlan &P, const double *fronts, double *x, const int32_t *order,
-                                int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid, DevCtl *ctl,
-                                cudaStream_t st, const int32_t *skip = nullptr);
+void launch_forward_persistent(const SolveSched &S, const double *fronts, const double *Dinv, double *x, double *upd,
+                               int32_t maxf, int32_t grid, DevCtl *ctl, cudaStream_t st,
+                               const int32_t *skip = nullptr);
+void launch_backward_persistent(const SolveSched &S, const double *fronts, double *x, int32_t maxf, int32_t grid,
+                                DevCtl *ctl, cudaStream_t st, const int32_t *skip = nullptr);
 // normal equations (kernels_ne.cu)
 void launch_ne_form(const NeView &E, const double *Ax, const double *theta, double rho, DevCtl *ctl, cudaStream_t st);
 void launch_ne_rhs(const NeView &E, const int32_t *perm, const double *Ax, const double *r7, const double *r1,

@@ -141,7 +141,8 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
 // trailing lower part.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, double *__restrict__ fronts,
-                                                      double *__restrict__ Dg, double *__restrict__ dyng,
+                                                      double *__restrict__ Dg, double *__restrict__ Dig,
+                                                      double *__restrict__ dyng,
                                                       DevCtl *ctl, const int32_t *__restrict__ list, int nb) {
     extern __shared__ double smem[];
     __shared__ double wcol[128];  // fronts up to 128 rows use this kernel
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
             if (tid == 0) {
                 F[pc * ld + pc] = dn;
                 dq[p] = dn;
+                Dig[c0 + pc] = rinv;
             }
             __syncthreads();
             // rank-1 update of the block's remaining columns, all rows below
@@ -285,7 +287,8 @@ __global__ void __launch_bounds__(256) k_large_assemble(DevPlan P, DevVals V, do
 constexpr int kPanelWs = 32 * 33 + 32;  // doubles of panel workspace per large front
 
 __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double *__restrict__ fronts,
-                                                     double *__restrict__ Dg, double *__restrict__ dyng, DevCtl *ctl,
+                                                     double *__restrict__ Dg, double *__restrict__ Dig,
+                                                     double *__restrict__ dyng, DevCtl *ctl,
                                                      const PanelItem *__restrict__ items, int p0, int nb,
                                                      double *__restrict__ pws) {
     __shared__ double Fd[32 * 33];
@@ -351,6 +354,7 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
         ws[32 * 33 + t] = t < w ? rtmp[t] : 0.0;
         if (t < w) {
             Dg[c0 + p0 + t] = Dtmp[t];
+            Dig[c0 + p0 + t] = rtmp[t];
             dyng[c0 + p0 + t] = dyntmp[t];
         }
     }
@@ -518,7 +522,8 @@ __global__ void k_factor_stats(const double *__restrict__ D, const double *__res
 
 }  // namespace
 
-void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *dyn, DevCtl *ctl,
+void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
+                         DevCtl *ctl,
                          const int32_t *list, int32_t count, int32_t nb, int32_t maxf, cudaStream_t st) {
     if (count <= 0) return;
     const int ldmax = (maxf + 3) & ~3;
@@ -530,9 +535,9 @@ void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, dou
         attr = true;
     }
     // one warp per front up to f = 32, two up to 64, four beyond
-    if (maxf <= 32) k_small_fronts<32><<<count, 32, smem, st>>>(P, V, fronts, D, dyn, ctl, list, nb);
-    else if (maxf <= 64) k_small_fronts<64><<<count, 64, smem, st>>>(P, V, fronts, D, dyn, ctl, list, nb);
-    else k_small_fronts<128><<<count, 128, smem, st>>>(P, V, fronts, D, dyn, ctl, list, nb);
+    if (maxf <= 32) k_small_fronts<32><<<count, 32, smem, st>>>(P, V, fronts, D, Dinv, dyn, ctl, list, nb);
+    else if (maxf <= 64) k_small_fronts<64><<<count, 64, smem, st>>>(P, V, fronts, D, Dinv, dyn, ctl, list, nb);
+    else k_small_fronts<128><<<count, 128, smem, st>>>(P, V, fronts, D, Dinv, dyn, ctl, list, nb);
 }
 
 void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, const PanelItem *items,
@@ -541,10 +546,11 @@ void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, c
     k_large_assemble<<<count, 256, 0, st>>>(P, V, fronts, items);
 }
 
-void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *dyn, DevCtl *ctl,
+void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
+                       DevCtl *ctl,
                        const PanelItem *items, int32_t count, int32_t p0, int32_t nb, double *pws, cudaStream_t st) {
     if (count <= 0) return;
-    k_panel_diag<<<count, 128, 0, st>>>(P, V, fronts, D, dyn, ctl, items, p0, nb, pws);
+    k_panel_diag<<<count, 128, 0, st>>>(P, V, fronts, D, Dinv, dyn, ctl, items, p0, nb, pws);
 }
 
 void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,

@@ -129,14 +129,25 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward(DevPlan P, const dou
 
 // --------------------------------------------------------------------------
 // Persistent dependency-driven sweeps: one launch per forward or backward
-// pass instead of one per tree level.  CTAs take supernodes from an atomic
-// ticket in a topological order (forward: children before parents;
-// backward: parents before children).  Every dependency of a ticket holds a
-// smaller ticket, taken earlier by a running CTA, so waiting can always make
-// progress.  Waits are bounded: after kSpinLimit polls the CTA records
-// kStatTimeout and carries on, so the launch always terminates.
+// pass instead of one per tree level.  CTAs take work items from an atomic
+// ticket in a topological order, critical path first.  Every dependency of a
+// ticket holds a smaller ticket, taken earlier by a running CTA, so waiting
+// can always make progress.  Waits are bounded: after kSpinLimit polls the
+// CTA records kStatTimeout and carries on, so the launch always terminates.
 // Values produced by other CTAs of the same launch are read with ld.global.cg
-// (L2, bypassing the non-coherent L1).
+// (L2, bypassing the non-coherent L1) and written with st.global.cg.
+//
+// Forward, supernode s (front rows t, k columns, blocks of 32 columns):
+//   v_t  = b_t (t < k) + sum over children, ascending, of their contributions
+//   y    = L11^-1 v[0:k),   x[c0:c0+k) = D^-1 y
+//   u    = v[k:f) - L21 y   (contribution vector for the parent)
+// Backward: z = x[c0:c0+k) - L21^T x[rows k..f),  z <- L11^-T z.
+// A supernode with k <= 32 and a small L21 is one item.  Otherwise every
+// 32-column block of L11 is an item of its own (fan-in: block b applies the
+// finished y of blocks b' < b as they appear, then solves its diagonal
+// block; backward in the mirror order), and L21 is cut into row chunks of
+// kRectRows rows (forward: u for the chunk; backward: partial sums of
+// L21^T x over the chunk, added in chunk order).
 constexpr long long kSpinLimit = 1ll << 24;
 
 __device__ __forceinline__ int ld_acquire(const int32_t *p) {
@@ -157,126 +168,303 @@ __device__ __forceinline__ void wait_count(const int32_t *cnt, int need, DevCtl 
     }
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(DevPlan P, const double *__restrict__ fronts,
-                                                                       const double *__restrict__ D,
+// Take the next ticket (thread 0) and publish its item and node to the CTA.
+__device__ __forceinline__ bool next_item(const SolveSched &S, const SolveItem *items, SolveItem &it, SolveNode &nd,
+                                          SolveItem *sh_it, SolveNode *sh_nd) {
+    if (threadIdx.x == 0) {
+        const int t = atomicAdd(S.sync, 1);
+        SolveItem a{-1, -1};
+        if (t < S.nitems) {
+            a = items[t];
+            *sh_nd = S.node[a.s];
+        }
+        *sh_it = a;
+    }
+    __syncthreads();
+    it = *sh_it;
+    if (it.s >= 0) nd = *sh_nd;
+    __syncthreads();
+    return it.s >= 0;
+}
+
+// The last finished item of supernode s reports s to its parent.
+__device__ __forceinline__ void finish_forward(const SolveNode &nd, int s, int32_t *done, int32_t *cnt) {
+    const int old = atomicAdd(&done[s], 1);
+    if (old == nd.nblk + nd.nrect - 1) {
+        __threadfence();
+        if (nd.parent >= 0) atomicAdd(&cnt[nd.parent], 1);
+    }
+}
+
+// Row t of the front: its right-hand side (t < k) plus the children's
+// contributions, children ascending.
+__device__ __forceinline__ double gather_row(const SolveSched &S, const SolveNode &nd, const double *x,
+                                             const double *upd, int t) {
+    double a = t < nd.k ? x[nd.c0 + t] : 0.0;
+    const int64_t e1 = S.gat_rp[nd.rptr + t + 1];
+    for (int64_t e = S.gat_rp[nd.rptr + t]; e < e1; e++) a += __ldcg(upd + S.gat_src[e]);
+    return a;
+}
+
+// Stage the strictly lower part of the w x w diagonal block at column b0.
+__device__ __forceinline__ void stage_diag(double *Lb, const double *L, int ld, int b0, int w) {
+    for (int q = threadIdx.x; q < w * w; q += kSolveThreads) {
+        const int jj = q / w, ii = q - jj * w;
+        if (ii > jj) Lb[jj * 33 + ii] = L[(int64_t)(b0 + jj) * ld + (b0 + ii)];
+    }
+}
+
+// Warp 0: forward substitution with the unit lower diagonal block on v[0:w).
+__device__ __forceinline__ void diag_forward(const double *Lb, double *v, int w) {
+    const int lane = threadIdx.x & 31;
+    double vi = lane < w ? v[lane] : 0.0;
+    for (int j = 0; j < w; j++) {
+        const double yj = __shfl_sync(0xffffffffu, vi, j);
+        if (lane > j && lane < w) vi -= Lb[j * 33 + lane] * yj;
+    }
+    if (lane < w) v[lane] = vi;
+}
+
+// Warp 0: backward substitution with the transposed diagonal block on z[0:w).
+__device__ __forceinline__ void diag_backward(const double *Lb, double *z, int w) {
+    const int lane = threadIdx.x & 31;
+    double zi = lane < w ? z[lane] : 0.0;
+    for (int j = w - 1; j > 0; j--) {
+        const double zj = __shfl_sync(0xffffffffu, zi, j);
+        if (lane < j) zi -= Lb[lane * 33 + j] * zj;
+    }
+    if (lane < w) z[lane] = zi;
+}
+
+__global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched S, const double *__restrict__ fronts,
+                                                                       const double *__restrict__ Dinv,
                                                                        double *__restrict__ x, double *upd,
-                                                                       const int32_t *__restrict__ order, int nitems,
-                                                                       int32_t *ticket, int32_t *cnt, DevCtl *ctl,
-                                                                       const int32_t *skip) {
+                                                                       DevCtl *ctl, const int32_t *skip) {
     extern __shared__ double v[];
     __shared__ double Lb[32 * 33];
-    __shared__ int item;
+    __shared__ double part[8][33];
+    __shared__ double ys[2][32];
+    __shared__ SolveItem sh_it;
+    __shared__ SolveNode sh_nd;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (skip && *skip) return;
-    for (;;) {
-        if (tid == 0) item = atomicAdd(ticket, 1);
-        __syncthreads();
-        const int t = item;
-        __syncthreads();
-        if (t >= nitems) break;
-        const int s = order[t];
-        const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
-        const double *L = fronts + P.sn_off[s];
-        if (tid == 0) wait_count(&cnt[s], P.child_ptr[s + 1] - P.child_ptr[s], ctl);
-        __syncthreads();
-        for (int q = tid; q < f; q += kSolveThreads) v[q] = q < k ? x[c0 + q] : 0.0;
-        __syncthreads();
-        for (int q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
-            const int c = P.child_list[q];
-            const int cc = P.sn_f[c] - P.sn_k[c];
-            const double *u = upd + P.upd_off[c];
-            const int32_t *map = P.relmap + P.map_off[c];
-            for (int r = tid; r < cc; r += kSolveThreads) v[map[r]] += __ldcg(u + r);
-            __syncthreads();
-        }
-        for (int b0 = 0; b0 < k; b0 += 32) {
-            const int b1 = min(b0 + 32, k), w = b1 - b0;
-            for (int q = tid; q < w * w; q += kSolveThreads) {
-                const int jj = q / w, ii = q - jj * w;
-                if (ii > jj) Lb[jj * 33 + ii] = L[(int64_t)(b0 + jj) * ld + (b0 + ii)];
+    int32_t *cnt = S.sync + 1, *done = cnt + S.nsuper, *tcnt = done + S.nsuper;
+    SolveItem it;
+    SolveNode nd;
+    while (next_item(S, S.fwd, it, nd, &sh_it, &sh_nd)) {
+        const int s = it.s;
+        const int f = nd.f, k = nd.k, ld = nd.ld, c0 = nd.c0;
+        const double *L = fronts + nd.off;
+        const bool single = nd.nblk == 1 && nd.nrect == 0;
+        if (it.r < 0) {
+            const int b = -1 - it.r, b0 = 32 * b, w = min(32, k - b0);
+            // loads that do not depend on other items go out before the wait
+            stage_diag(Lb, L, ld, b0, w);
+            const int nr = single ? f : w;  // rows this item gathers
+            int64_t e0 = 0, e1 = 0, g[4] = {0, 0, 0, 0};
+            double a0 = 0.0;
+            if (tid < nr) {
+                e0 = S.gat_rp[nd.rptr + b0 + tid];
+                e1 = S.gat_rp[nd.rptr + b0 + tid + 1];
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (e0 + q < e1) g[q] = S.gat_src[e0 + q];
+                if (b0 + tid < k) a0 = x[c0 + b0 + tid];
             }
+            if (tid == 0) wait_count(&cnt[s], nd.nchild, ctl);
             __syncthreads();
-            if (warp == 0) {
-                double vi = lane < w ? v[b0 + lane] : 0.0;
-                for (int j = 0; j < w; j++) {
-                    const double yj = __shfl_sync(0xffffffffu, vi, j);
-                    if (lane > j && lane < w) vi -= Lb[j * 33 + lane] * yj;
-                }
-                if (lane < w) v[b0 + lane] = vi;
+            if (tid < nr) {
+                double a = a0;
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (e0 + q < e1) a += __ldcg(upd + g[q]);
+                for (int64_t e = e0 + 4; e < e1; e++) a += __ldcg(upd + S.gat_src[e]);
+                v[tid] = a;
             }
-            __syncthreads();
-            for (int i = b1 + tid; i < f; i += kSolveThreads) {
+            for (int t = tid + kSolveThreads; t < nr; t += kSolveThreads) v[t] = gather_row(S, nd, x, upd, t);
+            if (b > 0) {
+                // fan-in of the finished blocks b' < b: warp w applies columns 4w..4w+3 of each
                 double acc = 0.0;
-                for (int j = 0; j < w; j++) acc += L[(int64_t)(b0 + j) * ld + i] * v[b0 + j];
-                v[i] -= acc;
+                for (int bp = 0; bp < b; bp++) {
+                    if (tid == 0) wait_count(&tcnt[s], bp + 1, ctl);
+                    __syncthreads();
+                    if (tid < 32) ys[bp & 1][tid] = __ldcg(S.yv + c0 + 32 * bp + tid);
+                    __syncthreads();
+                    if (lane < w) {
+#pragma unroll
+                        for (int c = 0; c < 4; c++) {
+                            const int j = 4 * warp + c;
+                            acc += L[(int64_t)(32 * bp + j) * ld + b0 + lane] * ys[bp & 1][j];
+                        }
+                    }
+                }
+                part[warp][lane] = acc;
+                __syncthreads();
+                if (warp == 0 && lane < w) {
+                    double sum = part[0][lane];
+#pragma unroll
+                    for (int q = 1; q < kSolveThreads / 32; q++) sum += part[q][lane];
+                    v[lane] -= sum;
+                }
             }
             __syncthreads();
-        }
-        for (int q = tid; q < f; q += kSolveThreads) {
-            if (q < k) x[c0 + q] = v[q] / D[c0 + q];
-            else __stcg(upd + P.upd_off[s] + (q - k), v[q]);
-        }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            const int pa = P.sn_parent[s];
-            if (pa >= 0) atomicAdd(&cnt[pa], 1);
+            if (warp == 0) diag_forward(Lb, v, w);
+            __syncthreads();
+            if (single) {
+                for (int i = w + tid; i < f; i += kSolveThreads) {
+                    double acc = 0.0;
+                    for (int j = 0; j < w; j++) acc += L[(int64_t)j * ld + i] * v[j];
+                    v[i] -= acc;
+                }
+                __syncthreads();
+            }
+            for (int q = tid; q < nr; q += kSolveThreads) {
+                if (q < w) {
+                    const double y = v[q];
+                    if (!single) __stcg(S.yv + c0 + b0 + q, y);
+                    x[c0 + b0 + q] = y * Dinv[c0 + b0 + q];
+                } else {
+                    __stcg(upd + nd.upd + (q - k), v[q]);
+                }
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                if (!single) atomicAdd(&tcnt[s], 1);
+                finish_forward(nd, s, done, cnt);
+            }
+        } else {
+            // rows [i0, i0 + 32) of L21: u_i = contributions_i - sum_j L_ij y_j,
+            // columns split over the warps
+            const int i = k + it.r * kRectRows + lane;
+            const bool ok = i < f;
+            if (tid == 0) {
+                wait_count(&cnt[s], nd.nchild, ctl);
+                wait_count(&tcnt[s], nd.nblk, ctl);
+            }
+            __syncthreads();
+            for (int j = tid; j < k; j += kSolveThreads) v[j] = __ldcg(S.yv + c0 + j);
+            double u0 = 0.0;
+            if (warp == 0 && ok) u0 = gather_row(S, nd, x, upd, i);
+            __syncthreads();
+            double acc = 0.0;
+            if (ok)
+                for (int j = warp; j < k; j += kSolveThreads / 32) acc += L[(int64_t)j * ld + i] * v[j];
+            part[warp][lane] = acc;
+            __syncthreads();
+            if (warp == 0 && ok) {
+                double sum = part[0][lane];
+#pragma unroll
+                for (int q = 1; q < kSolveThreads / 32; q++) sum += part[q][lane];
+                __stcg(upd + nd.upd + (i - k), u0 - sum);
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) finish_forward(nd, s, done, cnt);
         }
     }
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(DevPlan P, const double *__restrict__ fronts,
-                                                                        double *x, const int32_t *__restrict__ order,
-                                                                        int nitems, int32_t *ticket, int32_t *flag,
-                                                                        DevCtl *ctl, const int32_t *skip) {
+__global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSched S, const double *__restrict__ fronts,
+                                                                        double *x, DevCtl *ctl, const int32_t *skip) {
     extern __shared__ double z[];
     __shared__ double Lb[32 * 33];
-    __shared__ int item;
+    __shared__ double part[8][33];
+    __shared__ double zs[2][32];
+    __shared__ SolveItem sh_it;
+    __shared__ SolveNode sh_nd;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (skip && *skip) return;
-    for (;;) {
-        if (tid == 0) item = atomicAdd(ticket, 1);
-        __syncthreads();
-        const int t = item;
-        __syncthreads();
-        if (t >= nitems) break;
-        const int s = order[t];
-        const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
-        const double *L = fronts + P.sn_off[s];
-        const int32_t *rows = P.sn_rows + P.sn_rptr[s];
-        const int pa = P.sn_parent[s];
-        if (tid == 0 && pa >= 0) wait_count(&flag[pa], 1, ctl);
-        __syncthreads();
-        for (int q = tid; q < f; q += kSolveThreads) z[q] = q < k ? __ldcg(x + c0 + q) : __ldcg(x + rows[q]);
-        __syncthreads();
-        const int nblk = (k + 31) / 32;
-        for (int bb = nblk - 1; bb >= 0; bb--) {
-            const int b0 = bb * 32, b1 = min(b0 + 32, k), w = b1 - b0;
-            for (int q = tid; q < w * w; q += kSolveThreads) {
-                const int jj = q / w, ii = q - jj * w;
-                if (ii > jj) Lb[jj * 33 + ii] = L[(int64_t)(b0 + jj) * ld + (b0 + ii)];
-            }
-            for (int j = b0 + warp; j < b1; j += kSolveThreads / 32) {
+    int32_t *rcnt = S.sync + 1, *flag = rcnt + S.nsuper, *tcnt = flag + S.nsuper;
+    SolveItem it;
+    SolveNode nd;
+    while (next_item(S, S.bwd, it, nd, &sh_it, &sh_nd)) {
+        const int s = it.s;
+        const int f = nd.f, k = nd.k, ld = nd.ld, c0 = nd.c0;
+        const double *L = fronts + nd.off;
+        const int32_t *rows = S.sn_rows + nd.rptr;
+        const bool single = nd.nblk == 1 && nd.nrect == 0;
+        if (it.r >= 0) {
+            // partial sums over rows [i0, i0 + nr) of L21: p_j = sum_i L_ij x_rows[i]
+            if (tid == 0) wait_count(&flag[nd.parent], 1, ctl);
+            __syncthreads();
+            const int i0 = k + it.r * kRectRows, nr = min(kRectRows, f - i0);
+            if (tid < nr) z[tid] = __ldcg(x + rows[i0 + tid]);
+            __syncthreads();
+            double *pr = S.bpart + nd.bpart + (int64_t)it.r * k;
+            for (int j = tid; j < k; j += kSolveThreads) {
+                const double *Lc = L + (int64_t)j * ld + i0;
                 double acc = 0.0;
-                for (int i = b1 + lane; i < f; i += 32) acc += L[(int64_t)j * ld + i] * z[i];
+                for (int t = 0; t < nr; t++) acc += Lc[t] * z[t];
+                __stcg(pr + j, acc);
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicAdd(&rcnt[s], 1);
+            continue;
+        }
+        const int b = -1 - it.r, b0 = 32 * b, w = min(32, k - b0);
+        stage_diag(Lb, L, ld, b0, w);
+        if (tid == 0) {
+            if (nd.nrect > 0) wait_count(&rcnt[s], nd.nrect, ctl);
+            else if (single && nd.parent >= 0) wait_count(&flag[nd.parent], 1, ctl);
+        }
+        __syncthreads();
+        const int nz = single ? f : w;
+        for (int q = tid; q < nz; q += kSolveThreads) {
+            double zq;
+            if (q < w) {
+                zq = __ldcg(x + c0 + b0 + q);
+                for (int r = 0; r < nd.nrect; r++) zq -= __ldcg(S.bpart + nd.bpart + (int64_t)r * k + b0 + q);
+            } else {
+                zq = __ldcg(x + rows[q]);
+            }
+            z[q] = zq;
+        }
+        if (b < nd.nblk - 1) {
+            // fan-in of the finished blocks b' > b: warp w applies rows 4w..4w+3 of each
+            double acc = 0.0;
+            for (int bp = nd.nblk - 1; bp > b; bp--) {
+                if (tid == 0) wait_count(&tcnt[s], nd.nblk - bp, ctl);
+                __syncthreads();
+                const int wp = min(32, k - 32 * bp);
+                if (tid < 32) zs[bp & 1][tid] = tid < wp ? __ldcg(x + c0 + 32 * bp + tid) : 0.0;
+                __syncthreads();
+                if (lane < w) {
+                    const double *Lc = L + (int64_t)(b0 + lane) * ld + 32 * bp + 4 * warp;
+#pragma unroll
+                    for (int c = 0; c < 4; c++)
+                        if (4 * warp + c < wp) acc += Lc[c] * zs[bp & 1][4 * warp + c];
+                }
+            }
+            part[warp][lane] = acc;
+            __syncthreads();
+            if (warp == 0 && lane < w) {
+                double sum = part[0][lane];
+#pragma unroll
+                for (int q = 1; q < kSolveThreads / 32; q++) sum += part[q][lane];
+                z[lane] -= sum;
+            }
+        }
+        __syncthreads();
+        if (single) {
+            for (int j = warp; j < w; j += kSolveThreads / 32) {
+                double acc = 0.0;
+                for (int i = w + lane; i < f; i += 32) acc += L[(int64_t)j * ld + i] * z[i];
                 acc = warp_sum(acc);
                 if (lane == 0) z[j] -= acc;
             }
             __syncthreads();
-            if (warp == 0) {
-                double zi = lane < w ? z[b0 + lane] : 0.0;
-                for (int j = w - 1; j > 0; j--) {
-                    const double zj = __shfl_sync(0xffffffffu, zi, j);
-                    if (lane < j) zi -= Lb[lane * 33 + j] * zj;
-                }
-                if (lane < w) z[b0 + lane] = zi;
-            }
-            __syncthreads();
         }
-        for (int q = tid; q < k; q += kSolveThreads) __stcg(x + c0 + q, z[q]);
+        if (warp == 0) diag_backward(Lb, z, w);
+        __syncthreads();
+        for (int q = tid; q < w; q += kSolveThreads) __stcg(x + c0 + b0 + q, z[q]);
         __threadfence();
         __syncthreads();
-        if (tid == 0) atomicExch(&flag[s], 1);
+        if (tid == 0) {
+            if (!single) atomicAdd(&tcnt[s], 1);
+            if (b == 0) atomicExch(&flag[s], 1);
+        }
     }
 }
 
@@ -333,7 +521,8 @@ __global__ void k_residual(DevPlan P, DevVals V, const double *__restrict__ f, c
 }
 
 // omega = max_i |r_i| / den_i, den_i = (|K||x| + |f|)_i, replaced by
-// (|K||x| + ||x||_inf |K|e)_i when den_i <= 1000 N eps (ae_i ||x||_inf + |f_i|).
+// (|K||x| + ||x||_inf |K|e)_i when den_i <= 1000 N eps (ae_i ||x||_inf + |f_i|);
+// a NaN residual or denominator makes omega infinite.
 __global__ void k_omega(int N, const double *__restrict__ r, const double *__restrict__ ad,
                         const double *__restrict__ ae, const double *__restrict__ f, DevCtl *ctl,
                         const int32_t *skip) {
@@ -347,7 +536,7 @@ __global__ void k_omega(int N, const double *__restrict__ r, const double *__res
         if (den <= tau) den = ad[i] + dinf * ae[i];
         const double num = fabs(r[i]);
         double wi = den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0);
-        if (isnan(wi)) wi = INFINITY;
+        if (isnan(num) || isnan(den) || isnan(wi)) wi = INFINITY;  // a non-finite residual is no backward error
         w = fmax(w, wi);
     }
     w = warp_max(w);
@@ -426,28 +615,26 @@ void launch_backward(const DevPlan &P, const double *fronts, double *x, const in
 
 const void *persistent_probe_kernel() { return (const void *)k_forward_persistent; }
 
-void launch_forward_persistent(const DevPlan &P, const double *fronts, const double *D, double *x, double *upd,
-                               const int32_t *order, int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid,
-                               DevCtl *ctl, cudaStream_t st, const int32_t *skip) {
+void launch_forward_persistent(const SolveSched &S, const double *fronts, const double *Dinv, double *x, double *upd,
+                               int32_t maxf, int32_t grid, DevCtl *ctl, cudaStream_t st, const int32_t *skip) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_forward_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_backward_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    // sync[0] = ticket, sync[1 .. nsuper] = finished-children counters
-    cudaMemsetAsync(sync, 0, (size_t)(P.nsuper + 1) * sizeof(int32_t), st);
-    k_forward_persistent<<<grid, kSolveThreads, (size_t)maxf * sizeof(double), st>>>(P, fronts, D, x, upd, order,
-                                                                                      nitems, sync, sync + 1, ctl,
-                                                                                      skip);
+    // sync[0] = ticket; then per supernode: finished children, finished items, finished blocks
+    cudaMemsetAsync(S.sync, 0, (size_t)(3 * S.nsuper + 1) * sizeof(int32_t), st);
+    const size_t smem = (size_t)(maxf > kRectRows ? maxf : kRectRows) * sizeof(double);
+    k_forward_persistent<<<grid, kSolveThreads, smem, st>>>(S, fronts, Dinv, x, upd, ctl, skip);
 }
 
-void launch_backward_persistent(const DevPlan &P, const double *fronts, double *x, const int32_t *order,
-                                int32_t nitems, int32_t *sync, int32_t maxf, int32_t grid, DevCtl *ctl,
-                                cudaStream_t st, const int32_t *skip) {
-    cudaMemsetAsync(sync, 0, (size_t)(P.nsuper + 1) * sizeof(int32_t), st);
-    k_backward_persistent<<<grid, kSolveThreads, (size_t)maxf * sizeof(double), st>>>(P, fronts, x, order, nitems,
-                                                                                       sync, sync + 1, ctl, skip);
+void launch_backward_persistent(const SolveSched &S, const double *fronts, double *x, int32_t maxf, int32_t grid,
+                                DevCtl *ctl, cudaStream_t st, const int32_t *skip) {
+    // sync[0] = ticket; then per supernode: finished row chunks, done flag, finished blocks
+    cudaMemsetAsync(S.sync, 0, (size_t)(3 * S.nsuper + 1) * sizeof(int32_t), st);
+    const size_t smem = (size_t)(maxf > kRectRows ? maxf : kRectRows) * sizeof(double);
+    k_backward_persistent<<<grid, kSolveThreads, smem, st>>>(S, fronts, x, ctl, skip);
 }
 
 void launch_permute_in(const DevPlan &P, const double *r7, const double *r1, double *f, cudaStream_t st) {

@@ -9,6 +9,8 @@ from .lp import (  # noqa: F401
     grid_multicommodity,
     block_angular,
     batched_random,
+    batched_sizes,
+    batched_instance,
     staircase,
     theta_loguniform,
     theta_schedule,

@@ -152,17 +152,26 @@ def block_angular(blocks: int = 200, bm: int = 150, bn: int = 400, density: floa
                      {"blocks": blocks, "bm": bm, "bn": bn, "linking": linking, "seed": seed})
 
 
+def batched_sizes(count: int = 512, m_lo: int = 100, m_hi: int = 5000, ratio: float = 2.5,
+                  seed: int = 1) -> list[tuple[int, int]]:
+    """(m_i, n_i) of the instances of ``batched_random``: m log-uniform in
+    [m_lo, m_hi], n = round(ratio*m)."""
+    rng = np.random.default_rng(seed)
+    ms = np.rint(10.0 ** rng.uniform(np.log10(m_lo), np.log10(m_hi), size=count)).astype(int)
+    return [(int(mi), int(round(ratio * mi))) for mi in ms]
+
+
+def batched_instance(i: int, mi: int, ni: int, per_col: int = 5, seed: int = 1) -> LP:
+    """Instance i of ``batched_random`` (its own seed, seed+1+i)."""
+    return random_lp(mi, ni, per_col, seed + 1 + i, name=f"batch{i}")
+
+
 def batched_random(count: int = 512, m_lo: int = 100, m_hi: int = 5000, ratio: float = 2.5,
                    per_col: int = 5, seed: int = 1) -> list[LP]:
     """``count`` independent random LPs with m log-uniform in [m_lo, m_hi],
-    n = round(ratio*m), ``per_col`` rows per column; instance i uses seed+i."""
-    rng = np.random.default_rng(seed)
-    ms = np.rint(10.0 ** rng.uniform(np.log10(m_lo), np.log10(m_hi), size=count)).astype(int)
-    out = []
-    for i, mi in enumerate(ms):
-        ni = int(round(ratio * mi))
-        out.append(random_lp(int(mi), ni, per_col, seed + 1 + i, name=f"batch{i}"))
-    return out
+    n = round(ratio*m), ``per_col`` rows per column; instance i uses seed+1+i."""
+    return [batched_instance(i, mi, ni, per_col, seed)
+            for i, (mi, ni) in enumerate(batched_sizes(count, m_lo, m_hi, ratio, seed))]
 
 
 def staircase(periods: int = 50, pm: int = 2000, pn: int = 5000, density: float = 0.002,

@@ -138,6 +138,20 @@ def test_backward_error_hand_cases(golden_dir):
         assert w == pytest.approx(case["omega"], rel=1e-12, abs=1e-300), case["name"]
 
 
+def test_backward_error_nonfinite_solution():
+    # a solution with a NaN component has no finite backward error, whichever
+    # component it poisons (Sec. 4.5: omega bounds the relative perturbation)
+    M = np.array([[2.0, 1.0, 0.0], [1.0, 3.0, 1.0], [0.0, 1.0, 4.0]])
+    f = np.array([1.0, -2.0, 0.5])
+    for bad in range(3):
+        d = np.linalg.solve(M, f)
+        assert backward_error(f - M @ d, np.abs(M) @ np.abs(d), np.abs(M).sum(axis=1), f, d) < 1e-15
+        d[bad] = np.nan
+        r = f - M @ d
+        w = backward_error(r, np.abs(M) @ np.abs(d), np.abs(M).sum(axis=1), f, d)
+        assert w == np.inf
+
+
 # -------------------------------------------------------------- symbolic
 
 def _tridiag_ne(m):
