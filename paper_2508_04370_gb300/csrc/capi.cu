@@ -230,7 +230,6 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
     const Plan &P = c->plan;
     const int32_t ns = P.nsuper;
     std::vector<SolveNode> nodes(ns);
-    int64_t bp = 0;
     for (int32_t s = 0; s < ns; s++) {
         SolveNode &nd = nodes[s];
         nd.off = P.sn_off[s];
@@ -245,8 +244,6 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
         const int64_t rect = (int64_t)nd.k * (nd.f - nd.k);
         nd.nblk = (nd.k + 31) / 32;
         nd.nrect = (nd.f > nd.k && (rect >= kRectSplit || nd.nblk > 1)) ? (nd.f - nd.k + kRectRows - 1) / kRectRows : 0;
-        nd.bpart = bp;
-        bp += (int64_t)nd.nrect * nd.k;
     }
     const int64_t nrows = P.sn_rptr[ns];
     std::vector<int64_t> grp(nrows + 1, 0);
@@ -293,18 +290,15 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
         for (int32_t b = 0; b < nodes[s].nblk; b++) fwd.push_back({s, -1 - b});
         for (int32_t r = 0; r < nodes[s].nrect; r++) fwd.push_back({s, r});
     }
-    for (int32_t s : ob) {
-        for (int32_t r = 0; r < nodes[s].nrect; r++) bwd.push_back({s, r});
+    for (int32_t s : ob)
         for (int32_t b = nodes[s].nblk - 1; b >= 0; b--) bwd.push_back({s, -1 - b});
-    }
     SolveNode *d_nodes;
     int64_t *d_grp, *d_gsrc;
     SolveItem *d_fwd, *d_bwd;
-    double *d_yv, *d_bp;
+    double *d_yv;
     int rc;
     if ((rc = dupload(c, &d_nodes, nodes)) || (rc = dupload(c, &d_grp, grp)) || (rc = dupload(c, &d_gsrc, gsrc)) ||
-        (rc = dupload(c, &d_fwd, fwd)) || (rc = dupload(c, &d_bwd, bwd)) || (rc = dalloc(c, &d_yv, (size_t)P.N)) ||
-        (rc = dalloc(c, &d_bp, (size_t)std::max<int64_t>(bp, 1))))
+        (rc = dupload(c, &d_fwd, fwd)) || (rc = dupload(c, &d_bwd, bwd)) || (rc = dalloc(c, &d_yv, (size_t)P.N)))
         return rc;
     SolveSched &S = c->sched;
     S.node = d_nodes;
@@ -313,11 +307,11 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
     S.gat_src = d_gsrc;
     S.fwd = d_fwd;
     S.bwd = d_bwd;
-    S.nitems = (int32_t)fwd.size();
+    S.nfwd = (int32_t)fwd.size();
+    S.nbwd = (int32_t)bwd.size();
     S.nsuper = ns;
     S.sync = c->solve_sync;
     S.yv = d_yv;
-    S.bpart = d_bp;
     return IPM_OK;
 }
 

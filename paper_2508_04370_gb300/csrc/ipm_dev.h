@@ -109,7 +109,6 @@ struct SolveNode {
     int64_t off;    // slab offset (doubles)
     int64_t upd;    // offset of its contribution vector
     int64_t rptr;   // first entry in sn_rows and gat_rp
-    int64_t bpart;  // backward partial sums (nrect x k doubles)
     int32_t f, k, ld, c0;
     int32_t parent, nchild, nrect, nblk;  // nblk: items of L11 (32-column blocks; 1 when unsplit)
 };
@@ -122,10 +121,9 @@ struct SolveSched {
     const int64_t *gat_rp;   // per front row: range in gat_src
     const int64_t *gat_src;  // contribution-vector positions summed into the row, children ascending
     const SolveItem *fwd, *bwd;
-    int32_t nitems, nsuper;
-    int32_t *sync;           // ticket + 3 x nsuper counters
+    int32_t nfwd, nbwd, nsuper;
+    int32_t *sync;           // ticket + 3 x nsuper counters (forward), ticket + 2 x nsuper (backward)
     double *yv;              // forward: y of split supernodes (before D^-1)
-    double *bpart;           // backward: partial sums of split supernodes
 };
 constexpr int kRectRows = 32;
 constexpr int64_t kRectSplit = 8192;  // split when k (f - k) reaches this

@@ -145,9 +145,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward(DevPlan P, const dou
 // A supernode with k <= 32 and a small L21 is one item.  Otherwise every
 // 32-column block of L11 is an item of its own (fan-in: block b applies the
 // finished y of blocks b' < b as they appear, then solves its diagonal
-// block; backward in the mirror order), and L21 is cut into row chunks of
-// kRectRows rows (forward: u for the chunk; backward: partial sums of
-// L21^T x over the chunk, added in chunk order).
+// block; backward in the mirror order, each block also forming its own
+// columns of L21^T x), and in the forward L21 is cut into row chunks of
+// kRectRows rows that apply the blocks of y as they appear.
 constexpr long long kSpinLimit = 1ll << 24;
 
 __device__ __forceinline__ int ld_acquire(const int32_t *p) {
@@ -169,12 +169,12 @@ __device__ __forceinline__ void wait_count(const int32_t *cnt, int need, DevCtl 
 }
 
 // Take the next ticket (thread 0) and publish its item and node to the CTA.
-__device__ __forceinline__ bool next_item(const SolveSched &S, const SolveItem *items, SolveItem &it, SolveNode &nd,
-                                          SolveItem *sh_it, SolveNode *sh_nd) {
+__device__ __forceinline__ bool next_item(const SolveSched &S, const SolveItem *items, int nitems, SolveItem &it,
+                                          SolveNode &nd, SolveItem *sh_it, SolveNode *sh_nd) {
     if (threadIdx.x == 0) {
         const int t = atomicAdd(S.sync, 1);
         SolveItem a{-1, -1};
-        if (t < S.nitems) {
+        if (t < nitems) {
             a = items[t];
             *sh_nd = S.node[a.s];
         }
@@ -187,8 +187,13 @@ __device__ __forceinline__ bool next_item(const SolveSched &S, const SolveItem *
     return it.s >= 0;
 }
 
-// The last finished item of supernode s reports s to its parent.
+// The last finished item of supernode s reports s to its parent (a
+// supernode of one item reports directly).
 __device__ __forceinline__ void finish_forward(const SolveNode &nd, int s, int32_t *done, int32_t *cnt) {
+    if (nd.nblk + nd.nrect == 1) {
+        if (nd.parent >= 0) atomicAdd(&cnt[nd.parent], 1);
+        return;
+    }
     const int old = atomicAdd(&done[s], 1);
     if (old == nd.nblk + nd.nrect - 1) {
         __threadfence();
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
     int32_t *cnt = S.sync + 1, *done = cnt + S.nsuper, *tcnt = done + S.nsuper;
     SolveItem it;
     SolveNode nd;
-    while (next_item(S, S.fwd, it, nd, &sh_it, &sh_nd)) {
+    while (next_item(S, S.fwd, S.nfwd, it, nd, &sh_it, &sh_nd)) {
         const int s = it.s;
         const int f = nd.f, k = nd.k, ld = nd.ld, c0 = nd.c0;
         const double *L = fronts + nd.off;
@@ -262,14 +267,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
             stage_diag(Lb, L, ld, b0, w);
             const int nr = single ? f : w;  // rows this item gathers
             int64_t e0 = 0, e1 = 0, g[4] = {0, 0, 0, 0};
-            double a0 = 0.0;
+            double a0 = 0.0, dinv = 0.0;
             if (tid < nr) {
                 e0 = S.gat_rp[nd.rptr + b0 + tid];
                 e1 = S.gat_rp[nd.rptr + b0 + tid + 1];
 #pragma unroll
                 for (int q = 0; q < 4; q++)
                     if (e0 + q < e1) g[q] = S.gat_src[e0 + q];
-                if (b0 + tid < k) a0 = x[c0 + b0 + tid];
+                if (tid < w) {
+                    a0 = x[c0 + b0 + tid];
+                    dinv = Dinv[c0 + b0 + tid];
+                }
             }
             if (tid == 0) wait_count(&cnt[s], nd.nchild, ctl);
             __syncthreads();
@@ -322,7 +330,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
                 if (q < w) {
                     const double y = v[q];
                     if (!single) __stcg(S.yv + c0 + b0 + q, y);
-                    x[c0 + b0 + q] = y * Dinv[c0 + b0 + q];
+                    x[c0 + b0 + q] = y * dinv;  // q == tid here
                 } else {
                     __stcg(upd + nd.upd + (q - k), v[q]);
                 }
@@ -335,21 +343,29 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
             }
         } else {
             // rows [i0, i0 + 32) of L21: u_i = contributions_i - sum_j L_ij y_j,
-            // columns split over the warps
+            // applied block by block as the blocks of y finish; warp w takes
+            // columns 4w..4w+3 of every block
             const int i = k + it.r * kRectRows + lane;
             const bool ok = i < f;
-            if (tid == 0) {
-                wait_count(&cnt[s], nd.nchild, ctl);
-                wait_count(&tcnt[s], nd.nblk, ctl);
-            }
+            if (tid == 0) wait_count(&cnt[s], nd.nchild, ctl);
             __syncthreads();
-            for (int j = tid; j < k; j += kSolveThreads) v[j] = __ldcg(S.yv + c0 + j);
             double u0 = 0.0;
             if (warp == 0 && ok) u0 = gather_row(S, nd, x, upd, i);
-            __syncthreads();
             double acc = 0.0;
-            if (ok)
-                for (int j = warp; j < k; j += kSolveThreads / 32) acc += L[(int64_t)j * ld + i] * v[j];
+            for (int bp = 0; bp < nd.nblk; bp++) {
+                if (tid == 0) wait_count(&tcnt[s], bp + 1, ctl);
+                __syncthreads();
+                const int wp = min(32, k - 32 * bp);
+                if (tid < 32) ys[bp & 1][tid] = tid < wp ? __ldcg(S.yv + c0 + 32 * bp + tid) : 0.0;
+                __syncthreads();
+                if (ok) {
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        const int j = 4 * warp + c;
+                        if (j < wp) acc += L[(int64_t)(32 * bp + j) * ld + i] * ys[bp & 1][j];
+                    }
+                }
+            }
             part[warp][lane] = acc;
             __syncthreads();
             if (warp == 0 && ok) {
@@ -367,7 +383,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
 
 __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSched S, const double *__restrict__ fronts,
                                                                         double *x, DevCtl *ctl, const int32_t *skip) {
-    extern __shared__ double z[];
+    extern __shared__ double z[];  // [0, 32): the block; [32, 32 + f - k): x of the rows below
     __shared__ double Lb[32 * 33];
     __shared__ double part[8][33];
     __shared__ double zs[2][32];
@@ -375,94 +391,62 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
     __shared__ SolveNode sh_nd;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (skip && *skip) return;
-    int32_t *rcnt = S.sync + 1, *flag = rcnt + S.nsuper, *tcnt = flag + S.nsuper;
+    int32_t *flag = S.sync + 1, *tcnt = flag + S.nsuper;
     SolveItem it;
     SolveNode nd;
-    while (next_item(S, S.bwd, it, nd, &sh_it, &sh_nd)) {
+    while (next_item(S, S.bwd, S.nbwd, it, nd, &sh_it, &sh_nd)) {
         const int s = it.s;
         const int f = nd.f, k = nd.k, ld = nd.ld, c0 = nd.c0;
         const double *L = fronts + nd.off;
         const int32_t *rows = S.sn_rows + nd.rptr;
-        const bool single = nd.nblk == 1 && nd.nrect == 0;
-        if (it.r >= 0) {
-            // partial sums over rows [i0, i0 + nr) of L21: p_j = sum_i L_ij x_rows[i]
-            if (tid == 0) wait_count(&flag[nd.parent], 1, ctl);
-            __syncthreads();
-            const int i0 = k + it.r * kRectRows, nr = min(kRectRows, f - i0);
-            if (tid < nr) z[tid] = __ldcg(x + rows[i0 + tid]);
-            __syncthreads();
-            double *pr = S.bpart + nd.bpart + (int64_t)it.r * k;
-            for (int j = tid; j < k; j += kSolveThreads) {
-                const double *Lc = L + (int64_t)j * ld + i0;
-                double acc = 0.0;
-                for (int t = 0; t < nr; t++) acc += Lc[t] * z[t];
-                __stcg(pr + j, acc);
-            }
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) atomicAdd(&rcnt[s], 1);
-            continue;
-        }
         const int b = -1 - it.r, b0 = 32 * b, w = min(32, k - b0);
+        const int nrr = f - k;  // rows below the supernode's columns
+        // independent of other items: the diagonal block and this block's
+        // values after the forward sweep
         stage_diag(Lb, L, ld, b0, w);
-        if (tid == 0) {
-            if (nd.nrect > 0) wait_count(&rcnt[s], nd.nrect, ctl);
-            else if (single && nd.parent >= 0) wait_count(&flag[nd.parent], 1, ctl);
+        const double xb = (tid < w) ? __ldcg(x + c0 + b0 + tid) : 0.0;
+        if (tid == 0 && nrr > 0) wait_count(&flag[nd.parent], 1, ctl);
+        __syncthreads();
+        for (int t = tid; t < nrr; t += kSolveThreads) z[32 + t] = __ldcg(x + rows[k + t]);
+        __syncthreads();
+        // z_q = x_q - sum_{i >= k} L_iq x_rows[i] - sum_{later blocks} L_iq z_i:
+        // lane = column q of the block, warp g takes a slice of the rows below
+        // and rows 4g..4g+3 of every later block
+        double acc = 0.0;
+        if (lane < w && nrr > 0) {
+            const int chunk = (nrr + 7) / 8, t0 = warp * chunk, t1 = min(nrr, t0 + chunk);
+            const double *Lc = L + (int64_t)(b0 + lane) * ld + k;
+            for (int t = t0; t < t1; t++) acc += Lc[t] * z[32 + t];
+        }
+        for (int bp = nd.nblk - 1; bp > b; bp--) {
+            if (tid == 0) wait_count(&tcnt[s], nd.nblk - bp, ctl);
+            __syncthreads();
+            const int wp = min(32, k - 32 * bp);
+            if (tid < 32) zs[bp & 1][tid] = tid < wp ? __ldcg(x + c0 + 32 * bp + tid) : 0.0;
+            __syncthreads();
+            if (lane < w) {
+                const double *Lc = L + (int64_t)(b0 + lane) * ld + 32 * bp + 4 * warp;
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if (4 * warp + c < wp) acc += Lc[c] * zs[bp & 1][4 * warp + c];
+            }
+        }
+        part[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0 && lane < w) {
+            double sum = part[0][lane];
+#pragma unroll
+            for (int q = 1; q < kSolveThreads / 32; q++) sum += part[q][lane];
+            z[lane] = xb - sum;
         }
         __syncthreads();
-        const int nz = single ? f : w;
-        for (int q = tid; q < nz; q += kSolveThreads) {
-            double zq;
-            if (q < w) {
-                zq = __ldcg(x + c0 + b0 + q);
-                for (int r = 0; r < nd.nrect; r++) zq -= __ldcg(S.bpart + nd.bpart + (int64_t)r * k + b0 + q);
-            } else {
-                zq = __ldcg(x + rows[q]);
-            }
-            z[q] = zq;
-        }
-        if (b < nd.nblk - 1) {
-            // fan-in of the finished blocks b' > b: warp w applies rows 4w..4w+3 of each
-            double acc = 0.0;
-            for (int bp = nd.nblk - 1; bp > b; bp--) {
-                if (tid == 0) wait_count(&tcnt[s], nd.nblk - bp, ctl);
-                __syncthreads();
-                const int wp = min(32, k - 32 * bp);
-                if (tid < 32) zs[bp & 1][tid] = tid < wp ? __ldcg(x + c0 + 32 * bp + tid) : 0.0;
-                __syncthreads();
-                if (lane < w) {
-                    const double *Lc = L + (int64_t)(b0 + lane) * ld + 32 * bp + 4 * warp;
-#pragma unroll
-                    for (int c = 0; c < 4; c++)
-                        if (4 * warp + c < wp) acc += Lc[c] * zs[bp & 1][4 * warp + c];
-                }
-            }
-            part[warp][lane] = acc;
-            __syncthreads();
-            if (warp == 0 && lane < w) {
-                double sum = part[0][lane];
-#pragma unroll
-                for (int q = 1; q < kSolveThreads / 32; q++) sum += part[q][lane];
-                z[lane] -= sum;
-            }
-        }
-        __syncthreads();
-        if (single) {
-            for (int j = warp; j < w; j += kSolveThreads / 32) {
-                double acc = 0.0;
-                for (int i = w + lane; i < f; i += 32) acc += L[(int64_t)j * ld + i] * z[i];
-                acc = warp_sum(acc);
-                if (lane == 0) z[j] -= acc;
-            }
-            __syncthreads();
-        }
         if (warp == 0) diag_backward(Lb, z, w);
         __syncthreads();
         for (int q = tid; q < w; q += kSolveThreads) __stcg(x + c0 + b0 + q, z[q]);
         __threadfence();
         __syncthreads();
         if (tid == 0) {
-            if (!single) atomicAdd(&tcnt[s], 1);
+            if (nd.nblk > 1) atomicAdd(&tcnt[s], 1);
             if (b == 0) atomicExch(&flag[s], 1);
         }
     }
@@ -631,9 +615,9 @@ void launch_forward_persistent(const SolveSched &S, const double *fronts, const 
 
 void launch_backward_persistent(const SolveSched &S, const double *fronts, double *x, int32_t maxf, int32_t grid,
                                 DevCtl *ctl, cudaStream_t st, const int32_t *skip) {
-    // sync[0] = ticket; then per supernode: finished row chunks, done flag, finished blocks
-    cudaMemsetAsync(S.sync, 0, (size_t)(3 * S.nsuper + 1) * sizeof(int32_t), st);
-    const size_t smem = (size_t)(maxf > kRectRows ? maxf : kRectRows) * sizeof(double);
+    // sync[0] = ticket; then per supernode: done flag, finished blocks
+    cudaMemsetAsync(S.sync, 0, (size_t)(2 * S.nsuper + 1) * sizeof(int32_t), st);
+    const size_t smem = (size_t)(maxf + 32) * sizeof(double);
     k_backward_persistent<<<grid, kSolveThreads, smem, st>>>(S, fronts, x, ctl, skip);
 }
 
