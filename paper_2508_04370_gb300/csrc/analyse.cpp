@@ -584,6 +584,18 @@ int analyse(Plan &P, int32_t m, int32_t n, const int64_t *colptr, const int32_t 
             P.orig_dst[t] = (int32_t)dst;
             P.orig_src[t] = e.src;
         }
+        // each supernode's entries by destination (column-major), so that a
+        // range of front columns owns a contiguous range of entries
+        std::vector<std::pair<int32_t, int64_t>> tmp;
+        for (int32_t s = 0; s < ns; s++) {
+            tmp.clear();
+            for (int64_t t = P.orig_ptr[s]; t < P.orig_ptr[s + 1]; t++) tmp.emplace_back(P.orig_dst[t], P.orig_src[t]);
+            std::sort(tmp.begin(), tmp.end());
+            for (size_t u = 0; u < tmp.size(); u++) {
+                P.orig_dst[P.orig_ptr[s] + u] = tmp[u].first;
+                P.orig_src[P.orig_ptr[s] + u] = tmp[u].second;
+            }
+        }
     }
 
     // ----- levels and size classes

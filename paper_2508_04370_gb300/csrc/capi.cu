@@ -85,6 +85,8 @@ struct ipm_ctx {
     SolveSched sched{};  // dependency-driven solve schedule (device pointers)
     int32_t solve_maxf = 0, solve_grid = 0;
     PanelItem *asm_items = nullptr, *panel_items = nullptr, *trsm_items = nullptr;
+    AsmItem *asm_info = nullptr;
+    int32_t *asm_cr = nullptr;
     int32_t *trsm_slots = nullptr;
     double *panel_ws = nullptr;
     TileItem *tile_items = nullptr, *tc_items = nullptr, *alt_items = nullptr;
@@ -108,6 +110,8 @@ struct ipm_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     bool graph_solved = false;  // the last solve ran inside a graph (info comes from the device)
     cudaStream_t cap_stream = nullptr;  // private stream used only for capturing
+    cudaStream_t side = nullptr;        // large fronts of a level run here, beside the small fronts
+    std::vector<cudaEvent_t> dep_ev;    // level-to-level dependencies between the two streams
     // normal equations
     NeView ne{};
     double *kf = nullptr, *kr = nullptr, *kad = nullptr, *kae = nullptr;  // K-sized scratch for omega on K
@@ -206,6 +210,10 @@ void free_device(ipm_ctx *c) {
     c->graph = nullptr;
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     c->cap_stream = nullptr;
+    if (c->side) cudaStreamDestroy(c->side);
+    c->side = nullptr;
+    for (cudaEvent_t e : c->dep_ev) cudaEventDestroy(e);
+    c->dep_ev.clear();
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -392,6 +400,8 @@ int setup_device(ipm_ctx *c) {
     // per-level lists
     std::vector<int32_t> lvl_all, small_lists;
     std::vector<PanelItem> asm_items, panel_items, trsm_items;
+    std::vector<AsmItem> asm_info;
+    std::vector<int32_t> asm_cr;
     std::vector<int32_t> trsm_slots, slot_of(P.nsuper, -1);
     int32_t nslots = 0;
     for (int32_t s = 0; s < P.nsuper; s++)
@@ -461,7 +471,25 @@ int setup_device(ipm_ctx *c) {
         int32_t maxsteps = 0;
         for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
             int32_t s = P.lvl_large[t];
-            for (int32_t cl = 0; cl < P.sn_f[s]; cl += 32) asm_items.push_back({s, cl, std::min(cl + 32, P.sn_f[s])});
+            const int32_t ld = P.sn_ld[s];
+            for (int32_t cl = 0; cl < P.sn_f[s]; cl += 32) {
+                const int32_t ce = std::min(cl + 32, P.sn_f[s]);
+                asm_items.push_back({s, cl, ce});
+                // original entries of columns [cl, ce) and, per child, the
+                // contribution-block columns mapping into them
+                const int32_t *d0 = P.orig_dst.data() + P.orig_ptr[s], *d1 = P.orig_dst.data() + P.orig_ptr[s + 1];
+                AsmItem ai;
+                ai.o0 = std::lower_bound(d0, d1, (int64_t)cl * ld) - P.orig_dst.data();
+                ai.o1 = std::lower_bound(d0, d1, (int64_t)ce * ld) - P.orig_dst.data();
+                ai.cr = (int64_t)(asm_cr.size() / 2);
+                for (int32_t q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
+                    const int32_t ch = P.child_list[q];
+                    const int32_t *m0 = P.relmap.data() + P.map_off[ch], *m1 = m0 + (P.sn_f[ch] - P.sn_k[ch]);
+                    asm_cr.push_back((int32_t)(std::lower_bound(m0, m1, cl) - m0));
+                    asm_cr.push_back((int32_t)(std::lower_bound(m0, m1, ce) - m0));
+                }
+                asm_info.push_back(ai);
+            }
             maxsteps = std::max(maxsteps, (P.sn_k[s] + c->opt.nb - 1) / c->opt.nb);
         }
         W.asm_cnt = (int32_t)(asm_items.size() - W.asm_off);
@@ -530,7 +558,8 @@ int setup_device(ipm_ctx *c) {
         (rc = dupload(c, &d_perm, P.perm)) || (rc = dupload(c, &d_uoff, upd_off)) || (rc = dupload(c, &d_kp, kp)) ||
         (rc = dupload(c, &d_kj, kj)) || (rc = dupload(c, &d_ksrc, ksrc)) ||
         (rc = dupload(c, &c->lvl_small, small_lists)) || (rc = dupload(c, &c->lvl_all, lvl_all)) ||
-        (rc = dupload(c, &c->asm_items, asm_items)) || (rc = dupload(c, &c->panel_items, panel_items)) ||
+        (rc = dupload(c, &c->asm_items, asm_items)) || (rc = dupload(c, &c->asm_info, asm_info)) ||
+        (rc = dupload(c, &c->asm_cr, asm_cr)) || (rc = dupload(c, &c->panel_items, panel_items)) ||
         (rc = dupload(c, &c->trsm_items, trsm_items)) || (rc = dupload(c, &c->trsm_slots, trsm_slots)) ||
         (rc = dalloc(c, &c->panel_ws, (size_t)std::max(nslots, 1) * kPanelWsHost)) ||
         (rc = dupload(c, &c->tile_items, tile_items)) || (rc = dupload(c, &c->tc_items, tc_items)) ||
@@ -666,51 +695,92 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         launch_norm1(c->dp, V, c->ctl, c->opt.eps_piv, st);
     }
     nl += 2;
+    // Small fronts run on the caller's stream and the large fronts of the
+    // same level on a second stream: fronts of one level are independent
+    // (Sec. 4.3, tree-level parallelism), so a level costs the longer of the
+    // two instead of their sum.  Level l's small fronts wait for the large
+    // fronts of level l-1 and vice versa (events; a captured graph keeps them
+    // as edges).
+    if (!c->side) {
+        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            c->side = nullptr;
+            return IPM_ERR_CUDA;
+        }
+    }
+    const size_t nev = 2 * (size_t)P.nlevels + 2;
+    while (c->dep_ev.size() < nev) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return IPM_ERR_CUDA;
+        }
+        c->dep_ev.push_back(e);
+    }
+    cudaStream_t sd = c->side;
+    cudaEventRecord(c->dep_ev[0], st);
+    cudaStreamWaitEvent(sd, c->dep_ev[0], 0);
+    cudaEvent_t last_small = nullptr, last_large = nullptr;
     for (int32_t l = 0; l < P.nlevels; l++) {
         const LevelWork &W = c->levels[l];
-        for (const SmallClass &C : W.small) {
-            Prof pr(c, IPM_K_SMALL_FRONTS, C.w, st);
-            launch_small_fronts(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_small + C.off, C.cnt,
-                                c->opt.nb, C.maxf, st);
-            nl++;
+        cudaEvent_t small_before = last_small, large_before = last_large;
+        if (!W.small.empty()) {
+            if (large_before) cudaStreamWaitEvent(st, large_before, 0);
+            for (const SmallClass &C : W.small) {
+                Prof pr(c, IPM_K_SMALL_FRONTS, C.w, st);
+                launch_small_fronts(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_small + C.off, C.cnt,
+                                    c->opt.nb, C.maxf, st);
+                nl++;
+            }
+            last_small = c->dep_ev[1 + 2 * l];
+            cudaEventRecord(last_small, st);
         }
+        if (W.asm_cnt == 0 && W.steps.empty()) continue;
+        if (small_before) cudaStreamWaitEvent(sd, small_before, 0);
         if (W.asm_cnt > 0) {
-            Prof pr(c, IPM_K_LARGE_ASSEMBLE, W.asm_w, st);
-            launch_large_assemble(c->dp, V, c->fronts, c->asm_items + W.asm_off, W.asm_cnt, st);
+            Prof pr(c, IPM_K_LARGE_ASSEMBLE, W.asm_w, sd);
+            launch_large_assemble(c->dp, V, c->fronts, c->asm_items + W.asm_off, c->asm_info + W.asm_off, c->asm_cr,
+                                  W.asm_cnt, sd);
             nl++;
         }
         for (const StepWork &S : W.steps) {
             {
-                Prof pr(c, IPM_K_LARGE_PANEL, S.panel_w, st);
+                Prof pr(c, IPM_K_LARGE_PANEL, S.panel_w, sd);
                 launch_panel_diag(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->panel_items + S.panel_off,
-                                  S.panel_cnt, S.p0, c->opt.nb, c->panel_ws, st);
+                                  S.panel_cnt, S.p0, c->opt.nb, c->panel_ws, sd);
             }
             nl++;
             if (S.trsm_cnt > 0) {
-                Prof pr(c, IPM_K_LARGE_PANEL, S.trsm_w, st);
+                Prof pr(c, IPM_K_LARGE_PANEL, S.trsm_w, sd);
                 launch_panel_trsm(c->dp, c->fronts, c->trsm_items + S.trsm_off, c->trsm_slots + S.trsm_off,
-                                  S.trsm_cnt, S.p0, c->opt.nb, c->panel_ws, st);
+                                  S.trsm_cnt, S.p0, c->opt.nb, c->panel_ws, sd);
                 nl++;
             }
             if (S.tile_cnt > 0) {
-                Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w, st);
+                Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w, sd);
                 launch_large_update(c->dp, c->fronts, c->D, c->tile_items + S.tile_off, S.tile_cnt, S.p0, c->opt.nb,
-                                    st);
+                                    sd);
                 nl++;
             }
             if (S.tc_cnt > 0 && !c->mixed_active) {
-                Prof pr(c, IPM_K_LARGE_UPDATE, S.tc_w, st);
+                Prof pr(c, IPM_K_LARGE_UPDATE, S.tc_w, sd);
                 launch_large_update(c->dp, c->fronts, c->D, c->alt_items + S.alt_off, S.alt_cnt, S.p0, c->opt.nb,
-                                    st);
+                                    sd);
                 nl++;
             } else if (S.tc_cnt > 0) {
-                Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.tc_w, st);
+                Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.tc_w, sd);
                 launch_large_update_tc(c->dp, c->fronts, c->D, c->tc_items + S.tc_off, S.tc_cnt, S.p0, c->opt.nb,
-                                       c->ctl, st);
+                                       c->ctl, sd);
                 nl++;
             }
         }
+        last_large = c->dep_ev[2 + 2 * l];
+        cudaEventRecord(last_large, sd);
     }
+    // join: the second stream always rejoins the caller's stream (a capture
+    // needs every forked stream joined back)
+    cudaEventRecord(c->dep_ev[nev - 1], sd);
+    cudaStreamWaitEvent(st, c->dep_ev[nev - 1], 0);
     {
         Prof pr(c, IPM_K_OTHER, Work(), st);
         launch_factor_stats(c->D, c->dyn, P.N, c->opt.large_reg, c->ctl, st);

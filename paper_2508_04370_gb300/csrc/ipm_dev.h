@@ -133,6 +133,12 @@ struct PanelItem {
     int32_t s;       // supernode
     int32_t r0, r1;  // row range (local) handled by this block
 };
+// Precomputed ranges of an assembly item (front columns [r0, r1) of a large
+// front): its original entries [o0, o1) and, at acr[2 * cr ...], one
+// [a, b) range of contribution-block columns per child (children ascending).
+struct AsmItem {
+    int64_t o0, o1, cr;
+};
 struct TileItem {
     int32_t s;
     int32_t i0, j0;  // local row / column of a 64 x 64 output tile
@@ -145,7 +151,7 @@ void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, dou
                          DevCtl *ctl,
                          const int32_t *list, int32_t count, int32_t nb, int32_t maxf, cudaStream_t st);
 void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, const PanelItem *items,
-                           int32_t count, cudaStream_t st);
+                           const AsmItem *ainfo, const int32_t *acr, int32_t count, cudaStream_t st);
 // panel step 1 (diagonal block, one item per front; item.r1 = workspace slot)
 void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
                        DevCtl *ctl,

@@ -215,63 +215,55 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
 }
 
 // -------------------------------------------------------------- large fronts
-// Assembly of columns [r0, r1) of front s into its slab in global memory.
+// Assembly of columns [r0, r1) of front s into its slab in global memory:
+// zero the columns, place the original entries (a precomputed contiguous
+// range), then add the children's contribution-block columns that land in
+// the range (precomputed per child), children in ascending order.  Child
+// descriptors are staged in shared memory 64 at a time.
 __global__ void __launch_bounds__(256) k_large_assemble(DevPlan P, DevVals V, double *__restrict__ fronts,
-                                                         const PanelItem *__restrict__ items) {
+                                                         const PanelItem *__restrict__ items,
+                                                         const AsmItem *__restrict__ ainfo,
+                                                         const int32_t *__restrict__ acr) {
+    __shared__ int32_t ch_a[64], ch_b[64], ch_cc[64], ch_ldc[64];
+    __shared__ int64_t ch_cb[64], ch_map[64];
     const PanelItem it = items[blockIdx.x];
+    const AsmItem ai = ainfo[blockIdx.x];
     const int s = it.s, c_lo = it.r0, c_hi = it.r1;
-    const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s];
+    const int ld = P.sn_ld[s];
     double *F = fronts + P.sn_off[s];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ncol = c_hi - c_lo;
-    for (int t = tid; t < ncol * ld; t += 256) {
-        const int jj = c_lo + t / ld, ii = t % ld;
-        F[(int64_t)jj * ld + ii] = 0.0;
-    }
+    for (int t = tid; t < ncol * ld; t += 256) F[(int64_t)c_lo * ld + t] = 0.0;
     __syncthreads();
-    if (c_lo < k) {
-        const int64_t lo = (int64_t)c_lo * ld, hi = (int64_t)c_hi * ld;
-        for (int64_t q = P.orig_ptr[s] + tid; q < P.orig_ptr[s + 1]; q += 256) {
-            const int32_t dst = P.orig_dst[q];
-            if (dst >= lo && dst < hi) F[dst] = orig_value(P, V, P.orig_src[q]);
+    for (int64_t q = ai.o0 + tid; q < ai.o1; q += 256) F[P.orig_dst[q]] = orig_value(P, V, P.orig_src[q]);
+    const int q0 = P.child_ptr[s], nch = P.child_ptr[s + 1] - q0;
+    for (int base = 0; base < nch; base += 64) {
+        __syncthreads();
+        if (tid < 64 && base + tid < nch) {
+            const int c = P.child_list[q0 + base + tid];
+            const int kc = P.sn_k[c], ldc = P.sn_ld[c];
+            ch_a[tid] = acr[2 * (ai.cr + base + tid)];
+            ch_b[tid] = acr[2 * (ai.cr + base + tid) + 1];
+            ch_cc[tid] = P.sn_f[c] - kc;
+            ch_ldc[tid] = ldc;
+            ch_cb[tid] = P.sn_off[c] + (int64_t)kc * ldc + kc;
+            ch_map[tid] = P.map_off[c];
         }
-    }
-    __syncthreads();
-    for (int q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
-        const int c = P.child_list[q];
-        const int kc = P.sn_k[c], ldc = P.sn_ld[c];
-        const int cc = P.sn_f[c] - kc;
-        const int32_t *map = P.relmap + P.map_off[c];
-        // child columns whose parent column lies in [c_lo, c_hi): map is increasing
-        int a = 0, b = cc;
-        {
-            int lo = 0, hi = cc;
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (map[mid] < c_lo) lo = mid + 1;
-                else hi = mid;
-            }
-            a = lo;
-            lo = a;
-            hi = cc;
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (map[mid] < c_hi) lo = mid + 1;
-                else hi = mid;
-            }
-            b = lo;
-        }
-        if (a < b) {
-            const double *CB = fronts + P.sn_off[c] + (int64_t)kc * ldc + kc;
-            const int warp = tid >> 5, lane = tid & 31;
+        __syncthreads();
+        const int nu = min(64, nch - base);
+        for (int u = 0; u < nu; u++) {
+            const int a = ch_a[u], b = ch_b[u];
+            if (a >= b) continue;  // uniform over the CTA
+            const int cc = ch_cc[u], ldc = ch_ldc[u];
+            const double *CB = fronts + ch_cb[u];
+            const int32_t *map = P.relmap + ch_map[u];
             for (int jj = a + warp; jj < b; jj += 8) {
                 const int pj = map[jj];
                 for (int ii = jj + lane; ii < cc; ii += 32) F[(int64_t)pj * ld + map[ii]] += CB[(int64_t)jj * ldc + ii];
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
-    (void)f;
 }
 
 // Panel [p0, p1) of a large front, step 1: the nb x nb diagonal block,
@@ -541,9 +533,9 @@ void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, dou
 }
 
 void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, const PanelItem *items,
-                           int32_t count, cudaStream_t st) {
+                           const AsmItem *ainfo, const int32_t *acr, int32_t count, cudaStream_t st) {
     if (count <= 0) return;
-    k_large_assemble<<<count, 256, 0, st>>>(P, V, fronts, items);
+    k_large_assemble<<<count, 256, 0, st>>>(P, V, fronts, items, ainfo, acr);
 }
 
 void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
