@@ -31,13 +31,15 @@ struct StepWork {
     int32_t panel_cnt;
     int64_t trsm_off;   // row-chunk items below the diagonal blocks
     int32_t trsm_cnt;
-    int64_t tile_off;
-    int32_t tile_cnt;
+    int64_t tile_off;   // FP64 update tiles: the first tile_cnt1 cover the next panel's
+    int32_t tile_cnt;   // columns (lookahead, on the critical path), the rest the
+    int32_t tile_cnt1;  // remaining trailing columns (a third stream)
     int64_t tc_off;   // tensor-core tiles (mixed precision, large fronts)
     int32_t tc_cnt;
     int64_t alt_off;  // FP64 tiles of the same fronts, used after a precision fallback
     int32_t alt_cnt;
-    Work panel_w, trsm_w, tile_w, tc_w;
+    int32_t alt_cnt1;  // lookahead tiles among them
+    Work panel_w, trsm_w, tile_w, tile_w1, tc_w, alt_w1;
 };
 struct SmallClass {
     int64_t off;
@@ -111,7 +113,9 @@ struct ipm_ctx {
     bool graph_solved = false;  // the last solve ran inside a graph (info comes from the device)
     cudaStream_t cap_stream = nullptr;  // private stream used only for capturing
     cudaStream_t side = nullptr;        // large fronts of a level run here, beside the small fronts
-    std::vector<cudaEvent_t> dep_ev;    // level-to-level dependencies between the two streams
+    cudaStream_t side2 = nullptr;       // trailing updates beside the next panel (lookahead)
+    std::vector<cudaEvent_t> dep_ev;    // level-to-level dependencies between the streams
+    std::vector<cudaEvent_t> step_ev;   // per-step fork/join of the trailing updates
     // normal equations
     NeView ne{};
     double *kf = nullptr, *kr = nullptr, *kad = nullptr, *kae = nullptr;  // K-sized scratch for omega on K
@@ -212,8 +216,12 @@ void free_device(ipm_ctx *c) {
     c->cap_stream = nullptr;
     if (c->side) cudaStreamDestroy(c->side);
     c->side = nullptr;
+    if (c->side2) cudaStreamDestroy(c->side2);
+    c->side2 = nullptr;
     for (cudaEvent_t e : c->dep_ev) cudaEventDestroy(e);
     c->dep_ev.clear();
+    for (cudaEvent_t e : c->step_ev) cudaEventDestroy(e);
+    c->step_ev.clear();
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -501,6 +509,16 @@ int setup_device(ipm_ctx *c) {
             S.tile_off = (int64_t)tile_items.size();
             S.tc_off = (int64_t)tc_items.size();
             S.alt_off = (int64_t)alt_items.size();
+            std::vector<TileItem> u1, u2, a1, a2;  // lookahead / remaining tiles of this step
+            Work w1, w2, wa1, wa2;
+            // lower entries of a kUpdTile tile times 2 w flops (and its bytes)
+            auto tile_work = [](Work &acc, int32_t f, int32_t i0, int32_t j0, double w) {
+                double e = 0.0;
+                for (int32_t j = j0; j < std::min(j0 + kUpdTile, f); j++)
+                    e += std::max(0, std::min(i0 + kUpdTile, f) - std::max(i0, j));
+                acc.flops += 2.0 * w * e;
+                acc.bytes += 16.0 * e + 8.0 * w * (2.0 * kUpdTile);
+            };
             for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
                 int32_t s = P.lvl_large[t];
                 const int32_t k = P.sn_k[s], f = P.sn_f[s];
@@ -512,26 +530,43 @@ int setup_device(ipm_ctx *c) {
                     trsm_slots.push_back(slot_of[s]);
                 }
                 const bool tc = c->opt.precision == IPM_PREC_MIXED && f >= c->opt.mixed_min_front;
-                if (tc) {
+                const double w = p1 - S.p0, rest = f - p1;
+                // tiles of the next panel's columns (when the front has one) go first
+                const bool next_panel = p1 < k;
+                if (tc)
                     for (int32_t j0 = p1; j0 < f; j0 += kTcTile)
                         for (int32_t i0 = j0; i0 < f; i0 += kTcTile) tc_items.push_back({s, i0, j0});
-                    for (int32_t j0 = p1; j0 < f; j0 += kUpdTile)
-                        for (int32_t i0 = j0; i0 < f; i0 += kUpdTile) alt_items.push_back({s, i0, j0});
-                } else {
-                    for (int32_t j0 = p1; j0 < f; j0 += kUpdTile)
-                        for (int32_t i0 = j0; i0 < f; i0 += kUpdTile) tile_items.push_back({s, i0, j0});
-                }
-                const double w = p1 - S.p0, rest = f - p1;
+                for (int32_t j0 = p1; j0 < f; j0 += kUpdTile)
+                    for (int32_t i0 = j0; i0 < f; i0 += kUpdTile) {
+                        const bool la = next_panel && j0 == p1;
+                        if (tc) {
+                            (la ? a1 : a2).push_back({s, i0, j0});
+                            tile_work(la ? wa1 : wa2, f, i0, j0, w);
+                        } else {
+                            (la ? u1 : u2).push_back({s, i0, j0});
+                            tile_work(la ? w1 : w2, f, i0, j0, w);
+                        }
+                    }
                 // pivot block (w^3/3) + triangular solve of the rows below; update of the lower trailing part
                 S.panel_w.flops += w * w * w / 3.0;
                 S.panel_w.bytes += 16.0 * w * w;
                 S.trsm_w.flops += rest * w * w;
                 S.trsm_w.bytes += 16.0 * rest * w;
-                Work &uw = tc ? S.tc_w : S.tile_w;
-                uw.flops += 2.0 * w * rest * (rest + 1) / 2;
-                uw.bytes += 16.0 * rest * (rest + 1) / 2 + 8.0 * rest * w;
-                if (tc) c->flops_tensor += 2.0 * w * rest * (rest + 1) / 2;
+                if (tc) {
+                    S.tc_w.flops += 2.0 * w * rest * (rest + 1) / 2;
+                    S.tc_w.bytes += 16.0 * rest * (rest + 1) / 2 + 8.0 * rest * w;
+                    c->flops_tensor += 2.0 * w * rest * (rest + 1) / 2;
+                }
             }
+            tile_items.insert(tile_items.end(), u1.begin(), u1.end());
+            tile_items.insert(tile_items.end(), u2.begin(), u2.end());
+            alt_items.insert(alt_items.end(), a1.begin(), a1.end());
+            alt_items.insert(alt_items.end(), a2.begin(), a2.end());
+            S.tile_cnt1 = (int32_t)u1.size();
+            S.alt_cnt1 = (int32_t)a1.size();
+            S.tile_w1 = w1;
+            S.tile_w = w2;
+            S.alt_w1 = wa1;
             S.panel_cnt = (int32_t)(panel_items.size() - S.panel_off);
             S.trsm_cnt = (int32_t)(trsm_items.size() - S.trsm_off);
             S.tile_cnt = (int32_t)(tile_items.size() - S.tile_off);
@@ -717,7 +752,25 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         }
         c->dep_ev.push_back(e);
     }
-    cudaStream_t sd = c->side;
+    if (!c->side2) {
+        if (cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            c->side2 = nullptr;
+            return IPM_ERR_CUDA;
+        }
+    }
+    size_t nsteps = 0;
+    for (const LevelWork &W : c->levels) nsteps += W.steps.size();
+    while (c->step_ev.size() < 2 * nsteps) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return IPM_ERR_CUDA;
+        }
+        c->step_ev.push_back(e);
+    }
+    cudaStream_t sd = c->side, sd2 = c->side2;
+    size_t sidx = 0;
     cudaEventRecord(c->dep_ev[0], st);
     cudaStreamWaitEvent(sd, c->dep_ev[0], 0);
     cudaEvent_t last_small = nullptr, last_large = nullptr;
@@ -743,6 +796,13 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                                   W.asm_cnt, sd);
             nl++;
         }
+        // Per 32-column step: diagonal block and TRSM, then the update split
+        // in two.  The tiles of the next panel's columns (lookahead) stay on
+        // the critical path; the remaining trailing tiles run on a third
+        // stream beside the next step's diagonal block.  Every entry still
+        // receives the panels' updates in panel order: the lookahead tiles of
+        // step s wait for the remaining tiles of step s-1.
+        cudaEvent_t prev_rest = nullptr;
         for (const StepWork &S : W.steps) {
             {
                 Prof pr(c, IPM_K_LARGE_PANEL, S.panel_w, sd);
@@ -756,24 +816,51 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                                   S.trsm_cnt, S.p0, c->opt.nb, c->panel_ws, sd);
                 nl++;
             }
-            if (S.tile_cnt > 0) {
-                Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w, sd);
-                launch_large_update(c->dp, c->fronts, c->D, c->tile_items + S.tile_off, S.tile_cnt, S.p0, c->opt.nb,
+            const bool use_tc = S.tc_cnt > 0 && c->mixed_active;
+            const int32_t rest_tiles = S.tile_cnt - S.tile_cnt1;
+            const int32_t rest_alt = (S.tc_cnt > 0 && !c->mixed_active) ? S.alt_cnt - S.alt_cnt1 : 0;
+            cudaEvent_t this_rest = nullptr;
+            if (rest_tiles > 0 || rest_alt > 0) {
+                cudaEvent_t ev_in = c->step_ev[2 * sidx], ev_out = c->step_ev[2 * sidx + 1];
+                cudaEventRecord(ev_in, sd);
+                cudaStreamWaitEvent(sd2, ev_in, 0);
+                if (rest_tiles > 0) {
+                    Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w, sd2);
+                    launch_large_update(c->dp, c->fronts, c->D, c->tile_items + S.tile_off + S.tile_cnt1, rest_tiles,
+                                        S.p0, c->opt.nb, sd2);
+                    nl++;
+                }
+                if (rest_alt > 0) {
+                    Prof pr(c, IPM_K_LARGE_UPDATE, Work(), sd2);
+                    launch_large_update(c->dp, c->fronts, c->D, c->alt_items + S.alt_off + S.alt_cnt1, rest_alt, S.p0,
+                                        c->opt.nb, sd2);
+                    nl++;
+                }
+                cudaEventRecord(ev_out, sd2);
+                this_rest = ev_out;
+            }
+            sidx++;
+            if (prev_rest) cudaStreamWaitEvent(sd, prev_rest, 0);
+            if (S.tile_cnt1 > 0) {
+                Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w1, sd);
+                launch_large_update(c->dp, c->fronts, c->D, c->tile_items + S.tile_off, S.tile_cnt1, S.p0, c->opt.nb,
                                     sd);
                 nl++;
             }
-            if (S.tc_cnt > 0 && !c->mixed_active) {
-                Prof pr(c, IPM_K_LARGE_UPDATE, S.tc_w, sd);
-                launch_large_update(c->dp, c->fronts, c->D, c->alt_items + S.alt_off, S.alt_cnt, S.p0, c->opt.nb,
+            if (S.tc_cnt > 0 && !c->mixed_active && S.alt_cnt1 > 0) {
+                Prof pr(c, IPM_K_LARGE_UPDATE, S.alt_w1, sd);
+                launch_large_update(c->dp, c->fronts, c->D, c->alt_items + S.alt_off, S.alt_cnt1, S.p0, c->opt.nb,
                                     sd);
                 nl++;
-            } else if (S.tc_cnt > 0) {
+            } else if (use_tc) {
                 Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.tc_w, sd);
                 launch_large_update_tc(c->dp, c->fronts, c->D, c->tc_items + S.tc_off, S.tc_cnt, S.p0, c->opt.nb,
                                        c->ctl, sd);
                 nl++;
             }
+            prev_rest = this_rest;
         }
+        if (prev_rest) cudaStreamWaitEvent(sd, prev_rest, 0);
         last_large = c->dep_ev[2 + 2 * l];
         cudaEventRecord(last_large, sd);
     }

@@ -96,8 +96,14 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
             }
         }
     }
+    // the common-case pivot and its reciprocal, started before the vote so
+    // that the reciprocal's latency overlaps the screen
+    const long long dnb_fast = sp < 0 ? tb ^ kSignBit : tb;
+    const double rinv_fast = 1.0 / __longlong_as_double(dnb_fast);
     long long dnb;
+    bool exact = false;
     if (__any_sync(0xffffffffu, maybe)) {
+        exact = true;
         // exact evaluation of b2 and of the rule, as written
         double b2 = 0.0;
         if (j < w && sgn[j] == sp) {
@@ -117,7 +123,7 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
         const double sd = sp * d;
         dnb = dbits(sp * (sd > bnd ? sd : bnd));
     } else {
-        dnb = sp < 0 ? tb ^ kSignBit : tb;
+        dnb = dnb_fast;
     }
     if (lane == 0) {
         const double dn = __longlong_as_double(dnb);
@@ -126,7 +132,7 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
         const bool fin = (db & kAbsMask) < kInfBits && (dnb & kAbsMask) < kInfBits && (dnb & kAbsMask) != 0;
         if (!fin) atomicOr(&ctl->status, kStatNonFinite);
         piv_out[0] = dn;
-        piv_out[1] = 1.0 / dn;
+        piv_out[1] = exact ? 1.0 / dn : rinv_fast;
     }
 }
 
@@ -148,6 +154,7 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
     __shared__ double wcol[128];  // fronts up to 128 rows use this kernel
     __shared__ double dq[32];
     __shared__ double piv[2];
+    __shared__ int8_t sg[128];
     const int s = list[blockIdx.x];
     const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
     double *F = smem;  // ld * f
@@ -171,7 +178,9 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
         }
         __syncthreads();
     }
-    const int8_t *sgn = P.sign + c0;
+    for (int t = tid; t < k; t += NT) sg[t] = P.sign[c0 + t];
+    __syncthreads();
+    const int8_t *sgn = sg;
     const double b1floor = pivot_floor(P, ctl, c0);
     for (int b0 = 0; b0 < k; b0 += nb) {
         const int b1 = min(b0 + nb, k), w = b1 - b0;
@@ -287,6 +296,7 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
     __shared__ double Dtmp[32], dyntmp[32], rtmp[32], wsave[32];
     __shared__ double piv[2];
     __shared__ uint16_t tri[496];  // (column << 8 | row) of the strictly trailing triangle
+    __shared__ int8_t sg[32];
     constexpr int LDD = 33, NT = 128;
     const PanelItem it = items[blockIdx.x];
     const int s = it.s;
@@ -309,12 +319,12 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
         const int jj = w - 1 - r, ii = jj + (e - r * (r + 1) / 2);
         tri[e] = (uint16_t)((jj << 8) | ii);
     }
+    if (tid < 32) sg[tid] = tid < w ? P.sign[c0 + p0 + tid] : (int8_t)0;
     __syncthreads();
-    const int8_t *sgn = P.sign + c0 + p0;
     const double b1floor = pivot_floor(P, ctl, c0);
     for (int p = 0; p < w; p++) {
         if (warp == 0) {
-            pivot_warp(Fd, LDD, p, w, sgn, V.rho, V.delta, b1floor, Dtmp, dyntmp, ctl, piv);
+            pivot_warp(Fd, LDD, p, w, sg, V.rho, V.delta, b1floor, Dtmp, dyntmp, ctl, piv);
             __syncwarp();
             const double rinv = piv[1];
             const int i = p + 1 + lane;
