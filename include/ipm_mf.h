@@ -94,6 +94,10 @@ typedef struct ipm_options {
     int32_t mixed_min_front;  /* mixed path: fronts with f >= this use tensor-core updates; 256 */
     double omega_target;      /* refinement stops at this backward error; 1e-12 */
     int32_t refine_max;       /* at most this many refinement steps per solve; 10 */
+    int32_t gmres_restarts;   /* when classical refinement of an FP64 factor stalls above omega_target, up to
+                                 this many restarts of GMRES(8) on K c = r preconditioned by the factor follow
+                                 (an extension of Sec. 4.5; 0 = the paper's classical refinement only; a
+                                 stalled tensor-core factor falls back to FP64 instead); 3 */
     int32_t nd_leaf;          /* nested dissection stops at subgraphs of this size; 128 */
     double dense_row_factor;  /* AMD treats degree > max(16, f*sqrt(N)) as dense; 10 */
     int32_t device;           /* CUDA device ordinal; 0 */
@@ -111,7 +115,8 @@ typedef struct ipm_info {
     int32_t npos, nneg, ndynreg;            /* inertia and number of lifted pivots */
     double max_dynreg;                      /* largest |lift| */
     double norm_K1;                         /* ||K||_1 (or ||M||_1) of the last factorisation */
-    int32_t refine_steps;                   /* refinement steps of the last solve */
+    int32_t refine_steps;                   /* refinement steps of the last solve (GMRES iterations included) */
+    int32_t gmres_iters;                    /* GMRES iterations of the last solve (0: classical refinement sufficed) */
     double omega;                           /* backward error of the last solve, on K */
     double omega_hist[16];                  /* omega after 0, 1, ... refinement steps */
     int32_t status;                         /* device status word of the last factorise/solve */

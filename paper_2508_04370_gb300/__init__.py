@@ -54,6 +54,7 @@ class ipm_options(ct.Structure):
         ("mixed_min_front", ct.c_int32),
         ("omega_target", ct.c_double),
         ("refine_max", ct.c_int32),
+        ("gmres_restarts", ct.c_int32),
         ("nd_leaf", ct.c_int32),
         ("dense_row_factor", ct.c_double),
         ("device", ct.c_int32),
@@ -70,14 +71,14 @@ class ipm_info(ct.Structure):
         ("flops_factor", ct.c_double), ("flops_tensor", ct.c_double), ("device_bytes", ct.c_int64),
         ("npos", ct.c_int32), ("nneg", ct.c_int32), ("ndynreg", ct.c_int32),
         ("max_dynreg", ct.c_double), ("norm_K1", ct.c_double), ("refine_steps", ct.c_int32),
-        ("omega", ct.c_double), ("omega_hist", ct.c_double * 16), ("status", ct.c_int32),
+        ("gmres_iters", ct.c_int32), ("omega", ct.c_double), ("omega_hist", ct.c_double * 16), ("status", ct.c_int32),
         ("ms_analyse", ct.c_double), ("est_cost_ne", ct.c_double), ("est_cost_as", ct.c_double),
         ("nnz_ne_seen", ct.c_int64), ("precision_fallbacks", ct.c_int32), ("mixed_active", ct.c_int32),
     ]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
-        d["omega_hist"] = list(self.omega_hist)[: max(self.refine_steps + 1, 1)]
+        d["omega_hist"] = list(self.omega_hist)[: min(16, max(self.refine_steps - self.gmres_iters + 1, 1))]
         return d
 
 

@@ -102,6 +102,9 @@ struct ipm_ctx {
     // last solve
     DevCtl last{};
     int32_t refine_steps = 0;
+    int32_t gmres_iters = 0;  // GMRES iterations of the last solve
+    double *gm_V = nullptr, *gm_Z = nullptr, *gm_zero = nullptr, *gm_w = nullptr, *gm_part = nullptr,
+           *gm_h = nullptr;
     double omega = 0.0;      // reported backward error (on K)
     double omega_sys = 0.0;  // backward error of the refined system (K, or M for the normal equations)
     double omega_hist[16] = {0};
@@ -971,6 +974,7 @@ void ipm_default_options(ipm_options *o) {
     o->mixed_min_front = 256;
     o->omega_target = 1e-12;
     o->refine_max = 10;
+    o->gmres_restarts = 3;
     o->nd_leaf = 128;
     o->dense_row_factor = 10.0;
     o->device = 0;
@@ -983,7 +987,8 @@ int ipm_create(ipm_ctx **out, const ipm_options *opt) {
     if (!c) return IPM_ERR_OOM;
     if (opt) c->opt = *opt;
     else ipm_default_options(&c->opt);
-    if (c->opt.nb != 32 || c->opt.refine_max < 0 || c->opt.refine_max > 15 || !(c->opt.eps_piv >= 0.0) ||
+    if (c->opt.nb != 32 || c->opt.refine_max < 0 || c->opt.refine_max > 15 ||
+        c->opt.gmres_restarts < 0 || c->opt.gmres_restarts > 16 || !(c->opt.eps_piv >= 0.0) ||
         (c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED) || c->opt.mixed_min_front < 1) {
         delete c;
         return IPM_ERR_INVALID_ARG;
@@ -1166,6 +1171,112 @@ static int read_ctl(ipm_ctx *c, cudaStream_t st, DevCtl *h) {
     return IPM_OK;
 }
 
+// GMRES refinement, an extension of the refinement of Sec. 4.5 for systems
+// where classical refinement stalls above the target (lifted pivots make the
+// factor a poor enough preconditioner that r -> K^-1 r steps stop halving
+// omega): restarted GMRES(m) on K c = r, right-preconditioned by the
+// regularised LDL^T factor (c = M^-1 u), classical Gram-Schmidt with one
+// re-orthogonalisation, Givens rotations on the host; every restart updates
+// x and measures omega with the true residual, and the best iterate is kept.
+// Starts from c->vbest (omega wbest); returns the improved wbest.
+constexpr int kGmresRestart = 8;
+
+static int gmres_refine(ipm_ctx *c, const DevVals &V, cudaStream_t st, double &wbest, int *nl) {
+    const Plan &P = c->plan;
+    const int64_t N = P.N;
+    const int m = kGmresRestart;
+    int rc;
+    if (!c->gm_V) {
+        if ((rc = dalloc(c, &c->gm_V, (size_t)(m + 1) * N)) || (rc = dalloc(c, &c->gm_Z, (size_t)m * N)) ||
+            (rc = dalloc(c, &c->gm_zero, (size_t)N)) || (rc = dalloc(c, &c->gm_w, (size_t)N)) ||
+            (rc = dalloc(c, &c->gm_part, (size_t)dots_partial_size())) || (rc = dalloc(c, &c->gm_h, kMaxDots)))
+            return rc;
+        cudaMemsetAsync(c->gm_zero, 0, sizeof(double) * N, st);
+    }
+    const double target = c->opt.omega_target;
+    double hbuf[kMaxDots];
+    auto read_h = [&](int cnt) -> int {
+        cudaError_t e = cudaMemcpyAsync(hbuf, c->gm_h, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        return to_err(e);
+    };
+    cudaMemcpyAsync(c->vx, c->vbest, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    for (int restart = 0; restart <= c->opt.gmres_restarts; restart++) {
+        // r = f - K x and omega of the current x
+        launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st);
+        *nl += 2;
+        DevCtl h{};
+        if ((rc = read_ctl(c, st, &h))) return rc;
+        if (h.status & kStatNonFinite) break;
+        if (restart > 0) {
+            if (h.omega < wbest) {
+                wbest = h.omega;
+                cudaMemcpyAsync(c->vbest, c->vx, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            } else {
+                break;  // no progress
+            }
+        }
+        if (wbest <= target || restart == c->opt.gmres_restarts) break;
+        launch_dots(c->vr, c->vr, N, 1, c->gm_part, c->gm_h, st);
+        if ((rc = read_h(1))) return rc;
+        const double beta = std::sqrt(hbuf[0]);
+        if (!(beta > 0.0) || !std::isfinite(beta)) break;
+        launch_scale(c->gm_V, c->vr, 1.0 / beta, N, st);
+        double H[kGmresRestart + 1][kGmresRestart] = {};
+        double cs[kGmresRestart], sn[kGmresRestart], g[kGmresRestart + 1] = {};
+        g[0] = beta;
+        // relative residual reduction that brings omega under the target, with margin
+        const double eta = std::min(0.5, std::max(1e-14, 0.1 * target / std::max(h.omega, 1e-300)));
+        int jdone = 0;
+        for (int j = 0; j < m; j++) {
+            double *vj = c->gm_V + (int64_t)j * N, *zj = c->gm_Z + (int64_t)j * N, *vn = vj + N;
+            cudaMemcpyAsync(zj, vj, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            if ((rc = solve_inplace(c, zj, st, nl))) return rc;
+            launch_residual_omega(c->dp, V, c->gm_zero, zj, c->gm_w, c->vad, c->vae, c->ctl, st);  // -K z
+            launch_scale(vn, c->gm_w, -1.0, N, st);
+            *nl += 3;
+            for (int pass = 0; pass < 2; pass++) {
+                launch_dots(vn, c->gm_V, N, j + 1, c->gm_part, c->gm_h, st);
+                launch_gs_update(vn, c->gm_V, c->gm_h, N, j + 1, st);
+                *nl += 3;
+                if ((rc = read_h(j + 1))) return rc;
+                for (int i = 0; i <= j; i++) H[i][j] += hbuf[i];
+            }
+            launch_dots(vn, vn, N, 1, c->gm_part, c->gm_h, st);
+            if ((rc = read_h(1))) return rc;
+            const double hn = std::sqrt(hbuf[0]);
+            H[j + 1][j] = hn;
+            if (hn > 0.0) launch_scale(vn, vn, 1.0 / hn, N, st);
+            // Givens rotations: apply the earlier ones, then annihilate H[j+1][j]
+            for (int i = 0; i < j; i++) {
+                const double a = H[i][j], b = H[i + 1][j];
+                H[i][j] = cs[i] * a + sn[i] * b;
+                H[i + 1][j] = -sn[i] * a + cs[i] * b;
+            }
+            const double a = H[j][j], b = H[j + 1][j], r = std::hypot(a, b);
+            cs[j] = r > 0.0 ? a / r : 1.0;
+            sn[j] = r > 0.0 ? b / r : 0.0;
+            H[j][j] = r;
+            H[j + 1][j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            jdone = j + 1;
+            c->gmres_iters++;
+            if (std::fabs(g[j + 1]) <= eta * beta || !(hn > 0.0)) break;
+        }
+        // y = R^-1 g, x += Z y
+        GmresCoef y{};
+        for (int i = jdone - 1; i >= 0; i--) {
+            double t = g[i];
+            for (int q = i + 1; q < jdone; q++) t -= H[i][q] * y.c[q];
+            y.c[i] = H[i][i] != 0.0 ? t / H[i][i] : 0.0;
+        }
+        launch_combine(c->vx, c->gm_Z, y, N, jdone, st);
+        *nl += 1;
+    }
+    return IPM_OK;
+}
+
 static int solve_once(ipm_ctx *c, const double *r7, const double *r1, double *dx, double *dy, void *stream) {
     int rc = check_ctx(c);
     if (rc) return rc;
@@ -1216,6 +1327,14 @@ static int solve_once(ipm_ctx *c, const double *r7, const double *r1, double *dx
             cudaMemcpyAsync(c->vbest, c->vx, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
         }
         if (!halved) break;
+    }
+    // GMRES refinement of an FP64 factor; a tensor-core factor whose classical
+    // refinement stalls is replaced by an FP64 one instead (ipm_solve), which
+    // later iterations keep, rather than paying GMRES iterations every solve
+    c->gmres_iters = 0;
+    if (wbest > target && c->opt.gmres_restarts > 0 && !c->mixed_active && !(h.status & kStatNonFinite)) {
+        if ((rc = gmres_refine(c, V, st, wbest, &nl))) return rc;
+        steps += c->gmres_iters;
     }
     launch_permute_out(c->dp, c->vbest, dx, dy, st);
     nl++;
@@ -1325,6 +1444,7 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
     out->device_bytes = c->device_bytes;
     out->ms_analyse = c->ms_analyse;
     out->refine_steps = c->refine_steps;
+    out->gmres_iters = c->gmres_iters;
     out->omega = c->omega;
     for (int i = 0; i < 16; i++) out->omega_hist[i] = c->omega_hist[i];
     if (!c->analysed) return IPM_ERR_NOT_ANALYSED;
@@ -1339,6 +1459,7 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
         c->status_acc |= h.status;
         if (c->graph_solved) {
             out->refine_steps = h.steps;
+            out->gmres_iters = 0;
             out->omega = h.omega_best;
             for (int i = 0; i < 16; i++) out->omega_hist[i] = i <= h.steps ? h.omega_hist[i] : 0.0;
         }

@@ -176,6 +176,17 @@ void launch_forward_persistent(const SolveSched &S, const double *fronts, const 
                                const int32_t *skip = nullptr);
 void launch_backward_persistent(const SolveSched &S, const double *fronts, double *x, int32_t maxf, int32_t grid,
                                 DevCtl *ctl, cudaStream_t st, const int32_t *skip = nullptr);
+// GMRES refinement vectors (kernels_krylov.cu)
+constexpr int kMaxDots = 16;  // vectors per dot-product launch (restart length + 1 at most)
+struct GmresCoef {
+    double c[kMaxDots];
+};
+void launch_dots(const double *w, const double *V, int64_t N, int32_t cnt, double *part, double *out,
+                 cudaStream_t st);
+void launch_gs_update(double *w, const double *V, const double *h, int64_t N, int32_t cnt, cudaStream_t st);
+void launch_scale(double *dst, const double *src, double alpha, int64_t N, cudaStream_t st);
+void launch_combine(double *x, const double *Z, const GmresCoef &y, int64_t N, int32_t cnt, cudaStream_t st);
+int32_t dots_partial_size();
 // normal equations (kernels_ne.cu)
 void launch_ne_form(const NeView &E, const double *Ax, const double *theta, double rho, DevCtl *ctl, cudaStream_t st);
 void launch_ne_rhs(const NeView &E, const int32_t *perm, const double *Ax, const double *r7, const double *r1,

@@ -45,14 +45,15 @@ def test_staircase_schedule_fp64_against_oracle(pkg):
 
 def test_staircase_schedule_end_stalls_like_oracle(pkg):
     """At the end of the schedule (Theta spread 1e16) classical refinement of
-    the regularised factorisation stalls above the target for the oracle too;
-    the library must stall at the same level, flag REFINE_NOT_CONVERGED, keep
-    the inertia, and lift the same pivots."""
+    the regularised factorisation (Sec. 4.5) stalls above the target for the
+    oracle too; with GMRES refinement off, the library must stall at the same
+    level, flag REFINE_NOT_CONVERGED, keep the inertia and lift the same
+    pivots."""
     lp = small_staircase()
     th = synth.theta_schedule(lp.n, 40, 3)[39]
-    r = run_pair(pkg, lp, th, synth.rhs_normal(lp.n, 39), synth.rhs_normal(lp.m, 40), ordering=pkg.IPM_ORD_ND)
-    w_orc = r["o"].omega_K(th, RHO, DELTA, synth.rhs_normal(lp.n, 39), synth.rhs_normal(lp.m, 40),
-                           r["ref"][: lp.n], r["ref"][lp.n:])
+    r7, r1 = synth.rhs_normal(lp.n, 39), synth.rhs_normal(lp.m, 40)
+    r = run_pair(pkg, lp, th, r7, r1, ordering=pkg.IPM_ORD_ND, gmres_restarts=0)
+    w_orc = r["o"].omega_K(th, RHO, DELTA, r7, r1, r["ref"][: lp.n], r["ref"][lp.n:])
     assert w_orc > 1e-12  # the oracle stalls
     assert r["w_gpu"] <= 10.0 * w_orc, f"omega {r['w_gpu']:.3e} vs oracle {w_orc:.3e}"
     assert r["info"]["nneg"] == lp.n and r["info"]["npos"] == lp.m
@@ -60,6 +61,29 @@ def test_staircase_schedule_end_stalls_like_oracle(pkg):
     assert mismatch.size <= max(2, 0.002 * (lp.n + lp.m))
     assert r["s"].status() == pkg.IPM_WARN_REFINE_NOT_CONVERGED
     r["s"].close()
+
+
+def test_staircase_schedule_end_gmres_reaches_target(pkg):
+    """Same system with the GMRES refinement (restarted GMRES(8) on K c = r,
+    preconditioned by the same regularised factor): the backward error on K
+    reaches 1e-12, and the solution agrees with the oracle's (stalled) one to
+    the accuracy the oracle's backward error allows."""
+    lp = small_staircase()
+    th = synth.theta_schedule(lp.n, 40, 3)[39]
+    r7, r1 = synth.rhs_normal(lp.n, 39), synth.rhs_normal(lp.m, 40)
+    s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND)
+    s.factorise(th, RHO, DELTA)
+    dx, dy = s.solve(r7, r1)
+    info = s.info()
+    assert info["gmres_iters"] > 0
+    o = Oracle.from_lp(lp)
+    w = o.omega_K(th, RHO, DELTA, r7, r1, dx.cpu().numpy(), dy.cpu().numpy())
+    assert w <= 1e-12, f"omega {w:.3e}"
+    assert info["omega"] == pytest.approx(w, rel=1e-6, abs=1e-300)
+    assert s.status() >= 0 and s.status() != pkg.IPM_WARN_REFINE_NOT_CONVERGED
+    print(f"staircase end with GMRES: omega {w:.2e}, {info['gmres_iters']} GMRES iterations, "
+          f"{info['refine_steps']} steps in all")
+    s.close()
 
 
 def test_staircase_schedule_mixed_matches_fp64(pkg):

@@ -307,9 +307,9 @@ def test_full_size_grid64_q4(pkg):
 
 # ---------------------------------------------------------------- mixed path
 
-def run_mixed(pkg, lp, theta, r7, r1, ordering, min_front):
+def run_mixed(pkg, lp, theta, r7, r1, ordering, min_front, **opts):
     s = pkg.Solver.from_lp(lp, ordering=ordering, precision=pkg.IPM_PREC_MIXED, mixed_min_front=min_front,
-                           omega_target=1e-10)
+                           omega_target=1e-10, **opts)
     pkg.ipm_set_profiling(s.ctx, True)
     s.factorise(theta, RHO, DELTA)
     dx, dy = s.solve(r7, r1)
@@ -347,20 +347,23 @@ def test_mixed_tensor_core_updates_small_grid(pkg):
 
 
 def test_mixed_full_size_grid64_q4(pkg):
-    """Theta 10^U[-8,8] (a 1e16 spread): FP32-accurate updates cannot be
-    refined to 1e-10 here, so the mixed path must fall back to FP64 and still
-    meet the target."""
+    """Theta 10^U[-8,8] (a 1e16 spread): FP32-accurate updates cannot be refined
+    to 1e-10 here, so the mixed path must fall back to FP64 and still meet the
+    target, with or without GMRES refinement (which refines FP64 factors
+    only)."""
     lp = synth.by_name("grid64_q4", 1)
     theta = synth.theta_loguniform(lp.n, 1)
     r7, r1 = synth.rhs_normal(lp.n, 1), synth.rhs_normal(lp.m, 2)
-    info, stats, x, ref, w = run_mixed(pkg, lp, theta, r7, r1, pkg.IPM_ORD_ND, 256)
-    assert info["flops_tensor"] > 0
-    assert info["precision_fallbacks"] == 1 and info["mixed_active"] == 0
-    assert info["nneg"] == lp.n and info["npos"] == lp.m
-    assert w <= 1e-10, f"omega {w:.3e}"
-    err = np.abs(x - ref).max() / np.abs(ref).max()
-    assert err <= 1e-6, f"solution rel err {err:.3e}"
-    print(f"mixed grid64: omega {w:.2e} rel err {err:.2e} steps {info['refine_steps']}")
+    for g in (0, 3):
+        info, stats, x, ref, w = run_mixed(pkg, lp, theta, r7, r1, pkg.IPM_ORD_ND, 256, gmres_restarts=g)
+        assert info["flops_tensor"] > 0
+        assert info["precision_fallbacks"] == 1 and info["mixed_active"] == 0
+        assert info["nneg"] == lp.n and info["npos"] == lp.m
+        assert w <= 1e-10, f"omega {w:.3e}"
+        err = np.abs(x - ref).max() / np.abs(ref).max()
+        assert err <= 1e-6, f"solution rel err {err:.3e}"
+        print(f"mixed grid64 (gmres restarts {g}): omega {w:.2e} rel err {err:.2e} steps {info['refine_steps']} "
+              f"gmres {info['gmres_iters']} fallbacks {info['precision_fallbacks']}")
 
 
 # ------------------------------------------------------------- CUDA graph
