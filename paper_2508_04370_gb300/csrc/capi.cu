@@ -117,6 +117,7 @@ struct ipm_ctx {
     cudaStream_t cap_stream = nullptr;  // private stream used only for capturing
     cudaStream_t side = nullptr;        // large fronts of a level run here, beside the small fronts
     cudaStream_t side2 = nullptr;       // trailing updates beside the next panel (lookahead)
+    cudaStream_t cls[2] = {nullptr, nullptr};  // the 2nd and 3rd small-front size classes of a level
     std::vector<cudaEvent_t> dep_ev;    // level-to-level dependencies between the streams
     std::vector<cudaEvent_t> step_ev;   // per-step fork/join of the trailing updates
     // normal equations
@@ -221,6 +222,10 @@ void free_device(ipm_ctx *c) {
     c->side = nullptr;
     if (c->side2) cudaStreamDestroy(c->side2);
     c->side2 = nullptr;
+    for (cudaStream_t &q : c->cls) {
+        if (q) cudaStreamDestroy(q);
+        q = nullptr;
+    }
     for (cudaEvent_t e : c->dep_ev) cudaEventDestroy(e);
     c->dep_ev.clear();
     for (cudaEvent_t e : c->step_ev) cudaEventDestroy(e);
@@ -746,7 +751,7 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
             return IPM_ERR_CUDA;
         }
     }
-    const size_t nev = 2 * (size_t)P.nlevels + 2;
+    const size_t nev = 5 * (size_t)P.nlevels + 2;  // per level: fork, two joins, small done, large done
     while (c->dep_ev.size() < nev) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
@@ -755,10 +760,10 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         }
         c->dep_ev.push_back(e);
     }
-    if (!c->side2) {
-        if (cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess) {
+    for (cudaStream_t *q : {&c->side2, &c->cls[0], &c->cls[1]}) {
+        if (!*q && cudaStreamCreateWithFlags(q, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
-            c->side2 = nullptr;
+            *q = nullptr;
             return IPM_ERR_CUDA;
         }
     }
@@ -781,14 +786,25 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         const LevelWork &W = c->levels[l];
         cudaEvent_t small_before = last_small, large_before = last_large;
         if (!W.small.empty()) {
+            // the size classes of a level are independent: each on its own stream
             if (large_before) cudaStreamWaitEvent(st, large_before, 0);
-            for (const SmallClass &C : W.small) {
-                Prof pr(c, IPM_K_SMALL_FRONTS, C.w, st);
+            cudaEvent_t fork = c->dep_ev[1 + 5 * l];
+            if (W.small.size() > 1) cudaEventRecord(fork, st);
+            for (size_t q = 0; q < W.small.size(); q++) {
+                const SmallClass &C = W.small[q];
+                cudaStream_t sq = q == 0 ? st : c->cls[(q - 1) & 1];
+                if (q > 0) cudaStreamWaitEvent(sq, fork, 0);
+                Prof pr(c, IPM_K_SMALL_FRONTS, C.w, sq);
                 launch_small_fronts(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_small + C.off, C.cnt,
-                                    c->opt.nb, C.maxf, st);
+                                    c->opt.nb, C.maxf, sq);
                 nl++;
+                if (q > 0) {
+                    cudaEvent_t join = c->dep_ev[2 + 5 * l + (q - 1)];
+                    cudaEventRecord(join, sq);
+                    cudaStreamWaitEvent(st, join, 0);
+                }
             }
-            last_small = c->dep_ev[1 + 2 * l];
+            last_small = c->dep_ev[4 + 5 * l];
             cudaEventRecord(last_small, st);
         }
         if (W.asm_cnt == 0 && W.steps.empty()) continue;
@@ -864,7 +880,7 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
             prev_rest = this_rest;
         }
         if (prev_rest) cudaStreamWaitEvent(sd, prev_rest, 0);
-        last_large = c->dep_ev[2 + 2 * l];
+        last_large = c->dep_ev[5 + 5 * l];
         cudaEventRecord(last_large, sd);
     }
     // join: the second stream always rejoins the caller's stream (a capture
