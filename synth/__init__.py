@@ -12,6 +12,7 @@ from .lp import (  # noqa: F401
     batched_sizes,
     batched_instance,
     staircase,
+    feasible_rhs,
     theta_loguniform,
     theta_schedule,
     rhs_normal,

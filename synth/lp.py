@@ -208,6 +208,22 @@ def staircase(periods: int = 50, pm: int = 2000, pn: int = 5000, density: float 
                      "staircase", {"periods": periods, "seed": seed})
 
 
+def feasible_rhs(lp: LP, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """(b, c) making min c^T x, A x = b, x >= 0 feasible and bounded: b = A x0
+    and c = A^T y0 + z0 with x0, z0 ~ U[0.5, 2] and y0 ~ N(0, 1), so x0 is
+    primal feasible and (y0, z0) dual feasible."""
+    rng = np.random.default_rng(seed + 611953)
+    x0 = rng.uniform(0.5, 2.0, size=lp.n)
+    y0 = rng.standard_normal(lp.m)
+    z0 = rng.uniform(0.5, 2.0, size=lp.n)
+    cols = np.repeat(np.arange(lp.n), np.diff(lp.colptr))
+    b = np.zeros(lp.m)
+    np.add.at(b, lp.rowidx, lp.vals * x0[cols])
+    c = z0.copy()
+    np.add.at(c, cols, lp.vals * y0[lp.rowidx])
+    return b, c
+
+
 def theta_loguniform(n: int, seed: int, lo: float = -8.0, hi: float = 8.0) -> np.ndarray:
     """Theta_j = 10**U[lo, hi]."""
     rng = np.random.default_rng(seed + 7919)
