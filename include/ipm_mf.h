@@ -101,6 +101,9 @@ typedef struct ipm_options {
     int32_t nd_leaf;          /* nested dissection stops at subgraphs of this size; 128 */
     double dense_row_factor;  /* AMD treats degree > max(16, f*sqrt(N)) as dense; 10 */
     int32_t device;           /* CUDA device ordinal; 0 */
+    int32_t spin_limit_log2;  /* dependency waits of the persistent solve give up after 2^this polls (each
+                                 >= 64 ns) and report IPM_ERR_DEVICE_TIMEOUT; -1 = give up at once (tests
+                                 of the failure path); 24 */
     int32_t verbose;          /* print analysis statistics to stderr; 0 */
 } ipm_options;
 
@@ -171,6 +174,17 @@ int ipm_analyse(ipm_ctx *ctx, int32_t m, int32_t n, const int64_t *colptr, const
  *   A.  Form is the augmented system. */
 int ipm_analyse_batch(ipm_ctx *ctx, int32_t count, const int32_t *ms, const int32_t *ns,
                       const int64_t *colptrs, const int32_t *rowidxs, int32_t ordering);
+
+/* Checkpoint of the symbolic analysis (Sec. 4.2: the symbolic phase runs once
+ * per sparsity pattern).  ipm_save_analysis writes everything ipm_analyse (or
+ * ipm_analyse_batch) computed to the file at `path` (host string);
+ * ipm_load_analysis reads such a file into a context instead of calling
+ * ipm_analyse, releasing any device state the context held.  The file is
+ * self-contained (the pattern of A included) and checked on reading: a
+ * missing, truncated or foreign file gives IPM_ERR_INVALID_ARG and leaves the
+ * context unchanged.  Saving before any analysis gives IPM_ERR_NOT_ANALYSED. */
+int ipm_save_analysis(const ipm_ctx *ctx, const char *path);
+int ipm_load_analysis(ipm_ctx *ctx, const char *path);
 
 /* Values of A (device, colptr[n] doubles in the CSC order given at analyse).
  * They are copied into the context, so the pointer need not stay valid.

@@ -58,6 +58,7 @@ class ipm_options(ct.Structure):
         ("nd_leaf", ct.c_int32),
         ("dense_row_factor", ct.c_double),
         ("device", ct.c_int32),
+        ("spin_limit_log2", ct.c_int32),
         ("verbose", ct.c_int32),
     ]
 
@@ -108,6 +109,8 @@ def _load():
     lib.ipm_analyse.argtypes = [P, ct.c_int32, ct.c_int32, P, P, ct.c_int32, ct.c_int32, P]
     lib.ipm_analyse_batch.argtypes = [P, ct.c_int32, P, P, P, P, ct.c_int32]
     lib.ipm_set_values.argtypes = [P, P, P]
+    lib.ipm_save_analysis.argtypes = [P, ct.c_char_p]
+    lib.ipm_load_analysis.argtypes = [P, ct.c_char_p]
     lib.ipm_factorise.argtypes = [P, P, ct.c_double, ct.c_double, P]
     lib.ipm_solve.argtypes = [P, P, P, P, P, P]
     lib.ipm_iterate_host.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_int32, P, P, P, P, P]
@@ -206,6 +209,14 @@ def ipm_analyse_batch(ctx, ms, ns, colptrs, rowidxs, ordering=IPM_ORD_AMD) -> in
     ris = np.ascontiguousarray(rowidxs, dtype=np.int32)
     return _load().ipm_analyse_batch(ctx, int(ms.size), _hptr(ms, np.int32), _hptr(ns, np.int32),
                                      _hptr(cps, np.int64), _hptr(ris, np.int32), int(ordering))
+
+
+def ipm_save_analysis(ctx, path) -> int:
+    return _load().ipm_save_analysis(ctx, os.fsencode(path))
+
+
+def ipm_load_analysis(ctx, path) -> int:
+    return _load().ipm_load_analysis(ctx, os.fsencode(path))
 
 
 def ipm_set_values(ctx, Ax_dev, stream=None) -> int:

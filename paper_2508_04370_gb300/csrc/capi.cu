@@ -331,6 +331,7 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
     S.gat_src = d_gsrc;
     S.fwd = d_fwd;
     S.bwd = d_bwd;
+    S.spin_limit = c->opt.spin_limit_log2 < 0 ? 0 : (1ll << c->opt.spin_limit_log2);
     S.nfwd = (int32_t)fwd.size();
     S.nbwd = (int32_t)bwd.size();
     S.nsuper = ns;
@@ -994,6 +995,7 @@ void ipm_default_options(ipm_options *o) {
     o->nd_leaf = 128;
     o->dense_row_factor = 10.0;
     o->device = 0;
+    o->spin_limit_log2 = 24;
     o->verbose = 0;
 }
 
@@ -1004,7 +1006,8 @@ int ipm_create(ipm_ctx **out, const ipm_options *opt) {
     if (opt) c->opt = *opt;
     else ipm_default_options(&c->opt);
     if (c->opt.nb != 32 || c->opt.refine_max < 0 || c->opt.refine_max > 15 ||
-        c->opt.gmres_restarts < 0 || c->opt.gmres_restarts > 16 || !(c->opt.eps_piv >= 0.0) ||
+        c->opt.gmres_restarts < 0 || c->opt.gmres_restarts > 16 ||
+        c->opt.spin_limit_log2 < -1 || c->opt.spin_limit_log2 > 40 || !(c->opt.eps_piv >= 0.0) ||
         (c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED) || c->opt.mixed_min_front < 1) {
         delete c;
         return IPM_ERR_INVALID_ARG;
@@ -1086,6 +1089,36 @@ int ipm_analyse(ipm_ctx *c, int32_t m, int32_t n, const int64_t *colptr, const i
     c->plan.batch_count = 0;
     c->plan.inst.clear();
     c->ms_analyse = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    c->analysed = true;
+    return IPM_OK;
+}
+
+int ipm_save_analysis(const ipm_ctx *c, const char *path) {
+    if (!c || !path) return IPM_ERR_INVALID_ARG;
+    if (!c->analysed) return IPM_ERR_NOT_ANALYSED;
+    std::string err;
+    if (plan_save(c->plan, path, err)) {
+        if (c->opt.verbose) std::fprintf(stderr, "[ipm save] %s\n", err.c_str());
+        return IPM_ERR_INVALID_ARG;
+    }
+    return IPM_OK;
+}
+
+int ipm_load_analysis(ipm_ctx *c, const char *path) {
+    if (!c || !path) return IPM_ERR_INVALID_ARG;
+    Plan Q;
+    std::string err;
+    if (plan_load(Q, path, err)) {
+        if (c->opt.verbose) std::fprintf(stderr, "[ipm load] %s\n", err.c_str());
+        return IPM_ERR_INVALID_ARG;
+    }
+    if (c->dev_ready) {
+        cudaSetDevice(c->opt.device);
+        cudaDeviceSynchronize();
+    }
+    free_device(c);
+    c->plan = std::move(Q);
+    c->ms_analyse = 0.0;
     c->analysed = true;
     return IPM_OK;
 }

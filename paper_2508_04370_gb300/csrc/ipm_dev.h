@@ -122,6 +122,7 @@ struct SolveSched {
     const int64_t *gat_src;  // contribution-vector positions summed into the row, children ascending
     const SolveItem *fwd, *bwd;
     int32_t nfwd, nbwd, nsuper;
+    long long spin_limit;    // polls before a dependency wait gives up (kStatTimeout)
     int32_t *sync;           // ticket + 3 x nsuper counters (forward), ticket + 2 x nsuper (backward)
     double *yv;              // forward: y of split supernodes (before D^-1)
 };

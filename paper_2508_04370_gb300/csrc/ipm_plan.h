@@ -97,6 +97,10 @@ struct AnalyseOptions {
     int32_t verbose = 0;
 };
 
+// Analysis checkpoint (analysis_io.cpp): 0 on success, -1 with err set.
+int plan_save(const Plan &plan, const std::string &path, std::string &err);
+int plan_load(Plan &plan, const std::string &path, std::string &err);
+
 // Returns 0 or a negative IPM error code; fills plan.
 int analyse(Plan &plan, int32_t m, int32_t n, const int64_t *colptr, const int32_t *rowidx, int32_t form,
             int32_t ordering, const int32_t *user_perm, const AnalyseOptions &opt, std::string &err);

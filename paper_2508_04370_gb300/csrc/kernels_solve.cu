@@ -132,8 +132,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward(DevPlan P, const dou
 // pass instead of one per tree level.  CTAs take work items from an atomic
 // ticket in a topological order, critical path first.  Every dependency of a
 // ticket holds a smaller ticket, taken earlier by a running CTA, so waiting
-// can always make progress.  Waits are bounded: after kSpinLimit polls the
-// CTA records kStatTimeout and carries on, so the launch always terminates.
+// can always make progress.  Waits are bounded: after S.spin_limit polls
+// the CTA records kStatTimeout and carries on, so the launch always
+// terminates (with a wrong result and the status set).
 // Values produced by other CTAs of the same launch are read with ld.global.cg
 // (L2, bypassing the non-coherent L1) and written with st.global.cg.
 //
@@ -148,19 +149,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward(DevPlan P, const dou
 // block; backward in the mirror order, each block also forming its own
 // columns of L21^T x), and in the forward L21 is cut into row chunks of
 // kRectRows rows that apply the blocks of y as they appear.
-constexpr long long kSpinLimit = 1ll << 24;
-
 __device__ __forceinline__ int ld_acquire(const int32_t *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void wait_count(const int32_t *cnt, int need, DevCtl *ctl) {
+__device__ __forceinline__ void wait_count(const int32_t *cnt, int need, DevCtl *ctl, long long limit) {
     if (need <= 0) return;
     long long spins = 0;
     while (ld_acquire(cnt) < need) {
-        if (++spins > kSpinLimit) {
+        if (++spins > limit) {
             atomicOr(&ctl->status, kStatTimeout);
             break;
         }
@@ -279,7 +278,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
                     dinv = Dinv[c0 + b0 + tid];
                 }
             }
-            if (tid == 0) wait_count(&cnt[s], nd.nchild, ctl);
+            if (tid == 0) wait_count(&cnt[s], nd.nchild, ctl, S.spin_limit);
             __syncthreads();
             if (tid < nr) {
                 double a = a0;
@@ -294,7 +293,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
                 // fan-in of the finished blocks b' < b: warp w applies columns 4w..4w+3 of each
                 double acc = 0.0;
                 for (int bp = 0; bp < b; bp++) {
-                    if (tid == 0) wait_count(&tcnt[s], bp + 1, ctl);
+                    if (tid == 0) wait_count(&tcnt[s], bp + 1, ctl, S.spin_limit);
                     __syncthreads();
                     if (tid < 32) ys[bp & 1][tid] = __ldcg(S.yv + c0 + 32 * bp + tid);
                     __syncthreads();
@@ -347,13 +346,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
             // columns 4w..4w+3 of every block
             const int i = k + it.r * kRectRows + lane;
             const bool ok = i < f;
-            if (tid == 0) wait_count(&cnt[s], nd.nchild, ctl);
+            if (tid == 0) wait_count(&cnt[s], nd.nchild, ctl, S.spin_limit);
             __syncthreads();
             double u0 = 0.0;
             if (warp == 0 && ok) u0 = gather_row(S, nd, x, upd, i);
             double acc = 0.0;
             for (int bp = 0; bp < nd.nblk; bp++) {
-                if (tid == 0) wait_count(&tcnt[s], bp + 1, ctl);
+                if (tid == 0) wait_count(&tcnt[s], bp + 1, ctl, S.spin_limit);
                 __syncthreads();
                 const int wp = min(32, k - 32 * bp);
                 if (tid < 32) ys[bp & 1][tid] = tid < wp ? __ldcg(S.yv + c0 + 32 * bp + tid) : 0.0;
@@ -405,7 +404,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
         // values after the forward sweep
         stage_diag(Lb, L, ld, b0, w);
         const double xb = (tid < w) ? __ldcg(x + c0 + b0 + tid) : 0.0;
-        if (tid == 0 && nrr > 0) wait_count(&flag[nd.parent], 1, ctl);
+        if (tid == 0 && nrr > 0) wait_count(&flag[nd.parent], 1, ctl, S.spin_limit);
         __syncthreads();
         for (int t = tid; t < nrr; t += kSolveThreads) z[32 + t] = __ldcg(x + rows[k + t]);
         __syncthreads();
@@ -419,7 +418,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
             for (int t = t0; t < t1; t++) acc += Lc[t] * z[32 + t];
         }
         for (int bp = nd.nblk - 1; bp > b; bp--) {
-            if (tid == 0) wait_count(&tcnt[s], nd.nblk - bp, ctl);
+            if (tid == 0) wait_count(&tcnt[s], nd.nblk - bp, ctl, S.spin_limit);
             __syncthreads();
             const int wp = min(32, k - 32 * bp);
             if (tid < 32) zs[bp & 1][tid] = tid < wp ? __ldcg(x + c0 + 32 * bp + tid) : 0.0;

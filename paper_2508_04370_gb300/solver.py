@@ -8,8 +8,8 @@ from __future__ import annotations
 import numpy as np
 
 from . import (IPM_FORM_AUGMENTED, IPM_ORD_AMD, ipm_analyse, ipm_create, ipm_default_options, ipm_destroy,
-               ipm_factorise, ipm_get_factor, ipm_get_info, ipm_get_symbolic, ipm_iterate_host, ipm_set_values,
-               ipm_solve, ipm_sync_status)
+               ipm_factorise, ipm_get_factor, ipm_get_info, ipm_get_symbolic, ipm_iterate_host, ipm_load_analysis,
+               ipm_save_analysis, ipm_set_values, ipm_solve, ipm_sync_status)
 
 
 class Solver:
@@ -42,11 +42,33 @@ class Solver:
         self.N = self.n + self.m
 
     def _analyse(self, m, n, colptr, rowidx, form, ordering, user_perm):
+        path = getattr(self, "_load_path", None)
+        if path is not None:
+            rc = ipm_load_analysis(self.ctx, path)
+            if rc == 0:
+                _, info = ipm_get_info(self.ctx)
+                self.m, self.n = int(info.m), int(info.n)
+            return rc
         return ipm_analyse(self.ctx, m, n, colptr, rowidx, form, ordering, user_perm)
 
     @classmethod
     def from_lp(cls, lp, **kw):
         return cls(lp.m, lp.n, lp.colptr, lp.rowidx, lp.vals, **kw)
+
+    @classmethod
+    def from_analysis(cls, path, vals, device=0, **options):
+        """A solver whose analysis is read from a file written by
+        save_analysis (the pattern of A is in the file; vals are A's values
+        in its CSC order)."""
+        s = cls.__new__(cls)
+        s._load_path = str(path)
+        s.__init__(0, 0, None, None, vals, device=device, **options)
+        return s
+
+    def save_analysis(self, path):
+        rc = ipm_save_analysis(self.ctx, str(path))
+        if rc:
+            raise RuntimeError(f"ipm_save_analysis failed ({rc})")
 
     def factorise(self, theta, rho, delta):
         theta = self._dev(theta)

@@ -196,3 +196,36 @@ def test_form_chooser(lib):
     chosen = lib.IPM_FORM_NORMAL if info.est_cost_ne < info.est_cost_as else lib.IPM_FORM_AUGMENTED
     assert info.form == chosen
     lib.ipm_destroy(ctx)
+
+
+def test_analysis_checkpoint_roundtrip(tmp_path):
+    """The analysis written by ipm_save_analysis and read back into a fresh
+    context gives the same symbolic results and statistics; truncated or
+    foreign files are rejected and leave the context unchanged."""
+    import paper_2508_04370_gb300 as L
+
+    for name, form, ordering in (("grid", L.IPM_FORM_AUGMENTED, L.IPM_ORD_ND),
+                                 ("ne", L.IPM_FORM_NORMAL, L.IPM_ORD_AMD)):
+        lp = synth.grid_multicommodity(12, 3) if name == "grid" else synth.random_lp(80, 200, 4, seed=3)
+        a = L.ipm_create(L.ipm_default_options())
+        assert L.ipm_save_analysis(a, str(tmp_path / "none.plan")) == L.IPM_ERR_NOT_ANALYSED
+        assert L.ipm_analyse(a, lp.m, lp.n, lp.colptr, lp.rowidx, form, ordering) == 0
+        path = tmp_path / f"{name}.plan"
+        assert L.ipm_save_analysis(a, str(path)) == 0
+        b = L.ipm_create(L.ipm_default_options())
+        assert L.ipm_load_analysis(b, str(path)) == 0
+        sa, sb = L.ipm_get_symbolic(a), L.ipm_get_symbolic(b)
+        for k in sa:
+            assert np.array_equal(sa[k], sb[k]), k
+        ia, ib = L.ipm_get_info(a)[1].as_dict(), L.ipm_get_info(b)[1].as_dict()
+        for k in ("form", "nsuper", "nlevels", "max_front", "nnz_L", "flops_factor", "nnz_K_lower"):
+            assert ia[k] == ib[k], k
+        data = path.read_bytes()
+        bad = tmp_path / "bad.plan"
+        for blob in (data[: len(data) // 2], b"NOTAPLAN" + data[8:], data + b"x"):
+            bad.write_bytes(blob)
+            assert L.ipm_load_analysis(b, str(bad)) == L.IPM_ERR_INVALID_ARG
+        assert L.ipm_get_info(b)[1].as_dict()["nsuper"] == ia["nsuper"]  # unchanged
+        assert L.ipm_load_analysis(b, str(tmp_path / "missing.plan")) == L.IPM_ERR_INVALID_ARG
+        L.ipm_destroy(a)
+        L.ipm_destroy(b)

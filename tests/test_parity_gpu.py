@@ -438,3 +438,52 @@ def test_normal_equations_against_oracle(pkg):
         err = np.abs(x - ref).max() / np.abs(ref).max()
         assert err <= 1e-8, f"solution rel err {err:.3e}"
         s.close()
+
+
+# ------------------------------------------------------ failure detection
+
+def test_dependency_wait_timeout_reports_status(pkg):
+    """A dependency wait of the persistent solve that runs out (here forced:
+    every wait gives up at its first poll) must end the launch with the
+    timeout bit in the status word and an error from the next synchronising
+    call, never hang; the context and the GPU stay usable."""
+    lp = synth.grid_multicommodity(12, 3)
+    theta = synth.theta_loguniform(lp.n, 31)
+    r7, r1 = synth.rhs_normal(lp.n, 31), synth.rhs_normal(lp.m, 32)
+    s = pkg.Solver.from_lp(lp, spin_limit_log2=-1, refine_max=0, gmres_restarts=0)
+    s.factorise(theta, RHO, DELTA)
+    assert s.status() >= 0  # the factorisation has no dependency waits
+    s.solve(r7, r1)
+    assert s.info()["status"] & 8, "timeout bit not set"
+    assert s.status() in (pkg.IPM_ERR_DEVICE_TIMEOUT, pkg.IPM_ERR_NONFINITE)
+    s.factorise(theta, RHO, DELTA)
+    assert s.status() >= 0
+    s.close()
+    s2 = pkg.Solver.from_lp(lp)
+    s2.factorise(theta, RHO, DELTA)
+    s2.solve(r7, r1)
+    assert s2.status() >= 0 and s2.info()["omega"] <= 1e-12
+    s2.close()
+
+
+def test_loaded_analysis_factorises_identically(pkg, tmp_path):
+    """A context built from a saved analysis (no ordering, no symbolic work)
+    produces the same factor, bit for bit, and the same solution."""
+    lp = synth.grid_multicommodity(16, 4)
+    theta = synth.theta_loguniform(lp.n, 51)
+    r7, r1 = synth.rhs_normal(lp.n, 51), synth.rhs_normal(lp.m, 52)
+    a = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND)
+    path = tmp_path / "grid16.plan"
+    a.save_analysis(path)
+    b = pkg.Solver.from_analysis(path, lp.vals)
+    assert (b.m, b.n) == (lp.m, lp.n)
+    outs = []
+    for s in (a, b):
+        s.factorise(theta, RHO, DELTA)
+        dx, dy = s.solve(r7, r1)
+        outs.append((s.factor(), dx.cpu().numpy(), dy.cpu().numpy()))
+    for fa, fb in zip(outs[0][0], outs[1][0]):
+        assert np.array_equal(fa, fb)
+    assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][2], outs[1][2])
+    a.close()
+    b.close()
