@@ -603,8 +603,19 @@ int analyse(Plan &P, int32_t m, int32_t n, const int64_t *colptr, const int32_t 
     for (int32_t s = 0; s < ns; s++) P.nlevels = std::max(P.nlevels, P.sn_level[s] + 1);
     P.lvl_small_ptr.assign(P.nlevels + 1, 0);
     P.lvl_large_ptr.assign(P.nlevels + 1, 0);
+    // small or large path per front (see kPromoteBelow)
+    P.sn_large.assign(ns, 0);
+    {
+        std::vector<int32_t> mid(P.nlevels, 0);
+        for (int32_t s = 0; s < ns; s++)
+            if (P.sn_f[s] > kPromoteMin && P.sn_f[s] <= kSmallFrontMax) mid[P.sn_level[s]]++;
+        for (int32_t s = 0; s < ns; s++) {
+            const int32_t f = P.sn_f[s];
+            P.sn_large[s] = (f > kSmallFrontMax || (f > kPromoteMin && mid[P.sn_level[s]] < kPromoteBelow)) ? 1 : 0;
+        }
+    }
     for (int32_t s = 0; s < ns; s++) {
-        if (P.sn_f[s] <= kSmallFrontMax) P.lvl_small_ptr[P.sn_level[s] + 1]++;
+        if (!P.sn_large[s]) P.lvl_small_ptr[P.sn_level[s] + 1]++;
         else P.lvl_large_ptr[P.sn_level[s] + 1]++;
     }
     for (int32_t l = 0; l < P.nlevels; l++) {
@@ -617,7 +628,7 @@ int analyse(Plan &P, int32_t m, int32_t n, const int64_t *colptr, const int32_t 
         std::vector<int32_t> fs(P.lvl_small_ptr.begin(), P.lvl_small_ptr.end() - 1);
         std::vector<int32_t> fl(P.lvl_large_ptr.begin(), P.lvl_large_ptr.end() - 1);
         for (int32_t s = 0; s < ns; s++) {
-            if (P.sn_f[s] <= kSmallFrontMax) P.lvl_small[fs[P.sn_level[s]]++] = s;
+            if (!P.sn_large[s]) P.lvl_small[fs[P.sn_level[s]]++] = s;
             else P.lvl_large[fl[P.sn_level[s]]++] = s;
         }
     }

@@ -20,7 +20,7 @@ namespace ipm {
 namespace {
 
 constexpr char kMagic[8] = {'I', 'P', 'M', 'P', 'L', 'A', 'N', '1'};
-constexpr uint64_t kVersion = 1;
+constexpr uint64_t kVersion = 2;
 
 struct Writer {
     FILE *f;
@@ -100,6 +100,7 @@ void visit(Plan &P, IO &io) {
     io.scalar(P.front_doubles), io.vec(P.child_ptr), io.vec(P.child_list), io.vec(P.map_off), io.vec(P.relmap);
     io.vec(P.orig_ptr), io.vec(P.orig_dst), io.vec(P.orig_src), io.vec(P.sign);
     io.scalar(P.nlevels), io.vec(P.lvl_small_ptr), io.vec(P.lvl_small), io.vec(P.lvl_large_ptr), io.vec(P.lvl_large);
+    io.vec(P.sn_large);
     io.vec(P.upd_off), io.scalar(P.upd_total);
     io.scalar(P.nnzL), io.scalar(P.nnzK_lower), io.scalar(P.flops);
     io.scalar(P.max_f), io.scalar(P.max_k), io.scalar(P.nsmall), io.scalar(P.nlarge);
@@ -115,7 +116,7 @@ bool consistent(const Plan &P) {
     if (P.sn_start.size() != ns + 1 || P.sn_rptr.size() != ns + 1 || P.sn_k.size() != ns || P.sn_f.size() != ns ||
         P.sn_ld.size() != ns || P.sn_off.size() != ns + 1 || P.sn_parent.size() != ns ||
         P.child_ptr.size() != ns + 1 || P.map_off.size() != ns + 1 || P.orig_ptr.size() != ns + 1 ||
-        P.upd_off.size() != ns + 1)
+        P.upd_off.size() != ns + 1 || P.sn_large.size() != ns)
         return false;
     if (P.sn_rows.size() != (size_t)P.sn_rptr[ns] || P.orig_dst.size() != (size_t)P.orig_ptr[ns] ||
         P.orig_src.size() != P.orig_dst.size() || P.Acp.size() != (size_t)P.n + 1 ||

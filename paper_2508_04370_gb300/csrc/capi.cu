@@ -422,7 +422,7 @@ int setup_device(ipm_ctx *c) {
     std::vector<int32_t> trsm_slots, slot_of(P.nsuper, -1);
     int32_t nslots = 0;
     for (int32_t s = 0; s < P.nsuper; s++)
-        if (P.sn_f[s] > kSmallFrontMax) slot_of[s] = nslots++;
+        if (P.sn_large[s]) slot_of[s] = nslots++;
     std::vector<TileItem> tile_items, tc_items, alt_items;
     c->levels.assign(P.nlevels, LevelWork());
     c->flops_tensor = 0.0;
@@ -477,7 +477,7 @@ int setup_device(ipm_ctx *c) {
             const int32_t s = lvl_all[t];
             const double f = P.sn_f[s], k = P.sn_k[s];
             const double lnz = f * k - k * (k - 1) / 2;  // stored entries of L
-            if (P.sn_f[s] > kSmallFrontMax) W.asm_w.bytes += front_work(s).bytes;
+            if (P.sn_large[s]) W.asm_w.bytes += front_work(s).bytes;
             W.fwd_w.flops += 2.0 * (lnz - f);
             W.fwd_w.bytes += 8.0 * lnz + 8.0 * (f + 2 * k);
             W.bwd_w.flops += 2.0 * (lnz - f);

@@ -20,7 +20,12 @@ std::vector<int32_t> order_amd(const Graph &g, double dense_factor);
 std::vector<int32_t> order_nd(const Graph &g, int32_t leaf, double dense_factor);
 
 // Front size classes.
-constexpr int32_t kSmallFrontMax = 128;  // fronts with f <= this run fully in shared memory
+constexpr int32_t kSmallFrontMax = 128;  // fronts with f <= this can run fully in shared memory
+// A level with fewer than kPromoteBelow fronts of f in (kPromoteMin, kSmallFrontMax]
+// sends them to the multi-CTA large-front path: one SM per such front would
+// leave most of the GPU idle while it works through the front's flops.
+constexpr int32_t kPromoteMin = 64;
+constexpr int32_t kPromoteBelow = 152;
 
 struct Plan {
     // problem
@@ -56,6 +61,7 @@ struct Plan {
     int32_t nlevels = 0;
     std::vector<int32_t> lvl_small_ptr, lvl_small;  // small fronts per level
     std::vector<int32_t> lvl_large_ptr, lvl_large;  // large fronts per level
+    std::vector<int8_t> sn_large;                    // 1: the front runs on the large-front path
 
     // solve buffers: per supernode offset of its contribution vector (length f-k)
     std::vector<int64_t> upd_off;
