@@ -7,9 +7,10 @@
 //   aggressive element absorption (|L_e \ L_p| = 0), supervariable detection
 //   by hashing, and dense rows (degree > max(16, f*sqrt(N))) ordered last.
 // order_nd: nested dissection by recursive vertex separators taken from
-//   breadth-first level structures rooted at a pseudo-peripheral vertex;
-//   subgraphs below the leaf size are ordered with order_amd.  The paper uses
-//   Metis (Sec. 4.2); this is a self-contained replacement.
+//   breadth-first level structures rooted at a pseudo-peripheral vertex and
+//   improved by vertex Fiduccia-Mattheyses refinement; subgraphs below the
+//   leaf size are ordered with order_amd.  The paper uses Metis (Sec. 4.2);
+//   this is a self-contained replacement.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -295,6 +296,193 @@ int32_t bfs_levels(const Graph &h, int32_t root, std::vector<int32_t> &level, st
     return maxl;
 }
 
+// Smallest vertex separator for a given edge cut: the cut edges form a
+// bipartite graph between the boundary vertices of the two sides, and its
+// minimum vertex cover (Konig's theorem: from a maximum matching, the
+// unmatched low-side vertices and everything reachable from them by
+// alternating paths, Z; cover = (low \ Z) + (high intersect Z)) separates
+// the sides with the fewest vertices.  side[v]: 1 or 2 for every vertex.
+// Returns the cover as part[] (0 for cover vertices, else the side).
+int64_t cover_separator(const Graph &h, const std::vector<int8_t> &side, std::vector<int8_t> &part) {
+    const int32_t n = h.N;
+    part.assign(side.begin(), side.end());
+    // boundary vertices and their cut edges
+    std::vector<int32_t> lows, idx(n, -1);
+    for (int32_t v = 0; v < n; v++) {
+        if (side[v] != 1) continue;
+        for (int64_t p = h.ptr[v]; p < h.ptr[v + 1]; p++)
+            if (side[h.adj[p]] == 2) {
+                idx[v] = (int32_t)lows.size();
+                lows.push_back(v);
+                break;
+            }
+    }
+    std::vector<int32_t> mate_hi(n, -1), mate_lo(lows.size(), -1), seen(n, -1);
+    // augmenting paths by iterative depth-first search (Kuhn): frame t holds a
+    // low vertex and its next edge; via[t] is the high vertex leading from
+    // frame t to frame t+1 (matched to frame t+1's low vertex)
+    struct Frame {
+        int32_t li;
+        int64_t pos;
+    };
+    std::vector<Frame> frames;
+    std::vector<int32_t> via;
+    for (int32_t i = 0; i < (int32_t)lows.size(); i++) {
+        frames.assign(1, {i, h.ptr[lows[i]]});
+        via.clear();
+        while (!frames.empty()) {
+            Frame &fr = frames.back();
+            const int32_t v = lows[fr.li];
+            if (fr.pos >= h.ptr[v + 1]) {  // dead end
+                frames.pop_back();
+                if (!via.empty()) via.pop_back();
+                continue;
+            }
+            const int32_t u = h.adj[fr.pos++];
+            if (side[u] != 2 || seen[u] == i) continue;
+            seen[u] = i;
+            if (mate_hi[u] < 0) {  // free: flip the path
+                via.push_back(u);
+                for (size_t t = 0; t < frames.size(); t++) {
+                    mate_lo[frames[t].li] = via[t];
+                    mate_hi[via[t]] = frames[t].li;
+                }
+                break;
+            }
+            via.push_back(u);
+            frames.push_back({mate_hi[u], h.ptr[lows[mate_hi[u]]]});
+        }
+    }
+    // Konig: alternating reachability from unmatched low vertices
+    std::vector<char> zl(lows.size(), 0), zh(n, 0);
+    std::vector<int32_t> q;
+    for (int32_t i = 0; i < (int32_t)lows.size(); i++)
+        if (mate_lo[i] < 0) {
+            zl[i] = 1;
+            q.push_back(i);
+        }
+    for (size_t t = 0; t < q.size(); t++) {
+        const int32_t v = lows[q[t]];
+        for (int64_t p = h.ptr[v]; p < h.ptr[v + 1]; p++) {
+            const int32_t u = h.adj[p];
+            if (side[u] != 2 || zh[u]) continue;
+            zh[u] = 1;
+            const int32_t m = mate_hi[u];
+            if (m >= 0 && !zl[m]) {
+                zl[m] = 1;
+                q.push_back(m);
+            }
+        }
+    }
+    int64_t size = 0;
+    for (int32_t i = 0; i < (int32_t)lows.size(); i++)
+        if (!zl[i]) {
+            part[lows[i]] = 0;
+            size++;
+        }
+    for (int32_t u = 0; u < n; u++)
+        if (zh[u] && side[u] == 2) {
+            part[u] = 0;
+            size++;
+        }
+    return size;
+}
+
+// Vertex-separator refinement (Fiduccia-Mattheyses moves on a vertex
+// separator, the node-based refinement of multilevel nested dissection):
+// moving a separator vertex v into side a pulls its neighbours on the other
+// side into the separator, so the separator changes by
+// |N(v) on the other side| - 1.  A pass repeatedly makes the best admissible
+// move (each vertex moves out of the separator at most once per pass; moves
+// that do not shrink the separator are allowed), then rolls back to the
+// smallest separator it saw.  part[v]: 0 separator, 1 or 2 a side.  The
+// larger side stays within max(its initial share, 60%) of both sides.
+void refine_separator(const Graph &h, std::vector<int8_t> &part, int max_passes) {
+    const int32_t n = h.N;
+    int64_t cnt[3] = {0, 0, 0};
+    for (int32_t v = 0; v < n; v++) cnt[part[v]]++;
+    const double share = std::max(0.6, (double)std::max(cnt[1], cnt[2]) / (double)std::max<int64_t>(1, cnt[1] + cnt[2]));
+    struct Mv {
+        int32_t v;
+        int8_t from, to;
+    };
+    struct Cand {
+        int32_t gain, v;
+        int8_t side;
+        bool operator<(const Cand &o) const { return gain < o.gain || (gain == o.gain && v > o.v); }
+    };
+    std::vector<char> locked(n);
+    std::vector<Mv> log;
+    std::vector<Cand> heap;
+    auto gain_of = [&](int32_t v, int8_t a) {
+        const int8_t b = (int8_t)(3 - a);
+        int32_t k = 0;
+        for (int64_t p = h.ptr[v]; p < h.ptr[v + 1]; p++) k += part[h.adj[p]] == b;
+        return 1 - k;
+    };
+    auto push = [&](int32_t v) {
+        if (part[v] != 0 || locked[v]) return;
+        for (int8_t a = 1; a <= 2; a++) {
+            heap.push_back({gain_of(v, a), v, a});
+            std::push_heap(heap.begin(), heap.end());
+        }
+    };
+    for (int pass = 0; pass < max_passes; pass++) {
+        std::fill(locked.begin(), locked.end(), 0);
+        log.clear();
+        heap.clear();
+        for (int32_t v = 0; v < n; v++)
+            if (part[v] == 0) push(v);
+        const int64_t start_sep = cnt[0];
+        int64_t best_sep = cnt[0];
+        size_t best_len = 0;
+        while (!heap.empty()) {
+            std::pop_heap(heap.begin(), heap.end());
+            const Cand c = heap.back();
+            heap.pop_back();
+            if (part[c.v] != 0 || locked[c.v] || gain_of(c.v, c.side) != c.gain) continue;  // stale
+            const int8_t a = c.side, b = (int8_t)(3 - a);
+            int64_t pulled = 0;
+            for (int64_t p = h.ptr[c.v]; p < h.ptr[c.v + 1]; p++) pulled += part[h.adj[p]] == b;
+            const int64_t ca = cnt[a] + 1, cb = cnt[b] - pulled;
+            if (cb <= 0 || (double)std::max(ca, cb) > share * (double)(ca + cb)) continue;
+            part[c.v] = a;
+            locked[c.v] = 1;
+            cnt[0]--;
+            cnt[a]++;
+            log.push_back({c.v, 0, a});
+            for (int64_t p = h.ptr[c.v]; p < h.ptr[c.v + 1]; p++) {
+                const int32_t u = h.adj[p];
+                if (part[u] == b) {
+                    part[u] = 0;
+                    cnt[b]--;
+                    cnt[0]++;
+                    log.push_back({u, b, 0});
+                }
+            }
+            // gains change for separator vertices next to v or to the pulled ones
+            for (int64_t p = h.ptr[c.v]; p < h.ptr[c.v + 1]; p++) {
+                const int32_t u = h.adj[p];
+                push(u);
+                if (part[u] == 0)
+                    for (int64_t q = h.ptr[u]; q < h.ptr[u + 1]; q++) push(h.adj[q]);
+            }
+            if (cnt[0] < best_sep) {
+                best_sep = cnt[0];
+                best_len = log.size();
+            }
+            if (log.size() > best_len + 4 * 64) break;  // long enough without improvement
+        }
+        for (size_t t = log.size(); t > best_len; t--) {
+            const Mv &m = log[t - 1];
+            cnt[m.to]--;
+            cnt[m.from]++;
+            part[m.v] = m.from;
+        }
+        if (best_sep >= start_sep) break;
+    }
+}
+
 }  // namespace
 
 std::vector<int32_t> order_nd(const Graph &g, int32_t leaf, double dense_factor) {
@@ -407,49 +595,52 @@ std::vector<int32_t> order_nd(const Graph &g, int32_t leaf, double dense_factor)
                 if (adj_dn[v] && level[v] >= 1) hi_sep[level[v] - 1]++;
             }
         }
-        double best_score = 1e300;
-        int32_t best_l = -1, best_side = 0;
+        // candidate cuts between level l and l+1 with both sides at least 20% of
+        // the vertices; the cheap one-sided separator estimates rank them and
+        // the best few get their optimal vertex separator (minimum cover of
+        // the cut edges)
+        std::vector<std::pair<double, int32_t>> cands;
         int64_t below = 0;
         for (int32_t l = 0; l < ecc; l++) {
-            // split between level l and l+1
-            int64_t left = below + cnt[l];  // levels <= l
-            int64_t right = n - left;
+            const int64_t left = below + cnt[l], right = n - left;
             below += cnt[l];
-            for (int side = 0; side < 2; side++) {
-                int64_t sep = side == 0 ? lo_sep[l] : hi_sep[l];
-                int64_t a = side == 0 ? left - sep : left;
-                int64_t b = side == 0 ? right : right - sep;
-                if (a <= 0 || b <= 0) continue;
-                double mn = (double)std::min(a, b), mx = (double)std::max(a, b);
-                if (mn < 0.2 * (double)n) continue;
-                double score = (double)sep * (1.0 + 0.5 * (mx - mn) / (double)n);
-                if (score < best_score) {
-                    best_score = score;
-                    best_l = l;
-                    best_side = side;
-                }
-            }
+            const int64_t sep = std::min(lo_sep[l], hi_sep[l]);
+            if (std::min(left, right) - sep < (int64_t)(0.2 * n)) continue;
+            const double mn = (double)std::min(left, right), mx = (double)std::max(left, right);
+            cands.push_back({(double)sep * (1.0 + 0.5 * (mx - mn) / (double)n), l});
         }
-        if (best_l < 0) {
+        if (cands.empty()) {
             std::vector<int32_t> o = order_amd(h, 0.0);
             for (int32_t t : o) order.push_back(vs[t]);
             continue;
         }
-        std::vector<int32_t> P1, P2, S;
-        for (int32_t v = 0; v < n; v++) {
-            int32_t lv = level[v];
-            bool in_sep = false;
-            if (best_side == 0 && lv == best_l) {
-                for (int64_t p = h.ptr[v]; p < h.ptr[v + 1]; p++)
-                    if (level[h.adj[p]] == lv + 1) { in_sep = true; break; }
-            } else if (best_side == 1 && lv == best_l + 1) {
-                for (int64_t p = h.ptr[v]; p < h.ptr[v + 1]; p++)
-                    if (level[h.adj[p]] == lv - 1) { in_sep = true; break; }
+        std::sort(cands.begin(), cands.end());
+        if (cands.size() > 6) cands.resize(6);
+        std::vector<int8_t> part, trial, sidev(n);
+        double best_score = 1e300;
+        for (const auto &cd : cands) {
+            const int32_t l = cd.second;
+            for (int32_t v = 0; v < n; v++) sidev[v] = level[v] <= l ? 1 : 2;
+            const int64_t sep = cover_separator(h, sidev, trial);
+            int64_t c1 = 0;
+            for (int32_t v = 0; v < n; v++) c1 += trial[v] == 1;
+            const int64_t c2 = n - sep - c1;
+            if (c1 <= 0 || c2 <= 0) continue;
+            const double mn = (double)std::min(c1, c2), mx = (double)std::max(c1, c2);
+            const double score = (double)sep * (1.0 + 0.5 * (mx - mn) / (double)n);
+            if (score < best_score) {
+                best_score = score;
+                part.swap(trial);
             }
-            if (in_sep) S.push_back(vs[v]);
-            else if (lv <= best_l) P1.push_back(vs[v]);
-            else P2.push_back(vs[v]);
         }
+        if (part.empty()) {
+            std::vector<int32_t> o = order_amd(h, 0.0);
+            for (int32_t t : o) order.push_back(vs[t]);
+            continue;
+        }
+        refine_separator(h, part, 8);
+        std::vector<int32_t> P1, P2, S;
+        for (int32_t v = 0; v < n; v++) (part[v] == 0 ? S : part[v] == 1 ? P1 : P2).push_back(vs[v]);
         // order: P1, P2, then the separator
         stack.push_back({std::move(S), true});
         stack.push_back({std::move(P2), false});
