@@ -31,7 +31,7 @@ struct StepWork {
     int32_t panel_cnt;
     int64_t trsm_off;   // row-chunk items below the diagonal blocks
     int32_t trsm_cnt;
-    int64_t tile_off;   // FP64 update tiles: the first tile_cnt1 cover the next panel's
+    int64_t tile_off;   // FP64 update tiles: the first tile_cnt1 (strips) cover the next panel's
     int32_t tile_cnt;   // columns (lookahead, on the critical path), the rest the
     int32_t tile_cnt1;  // remaining trailing columns (a third stream)
     int64_t tc_off;   // tensor-core tiles (mixed precision, large fronts)
@@ -547,14 +547,16 @@ int setup_device(ipm_ctx *c) {
                         for (int32_t i0 = j0; i0 < f; i0 += kTcTile) tc_items.push_back({s, i0, j0});
                 for (int32_t j0 = p1; j0 < f; j0 += kUpdTile)
                     for (int32_t i0 = j0; i0 < f; i0 += kUpdTile) {
+                        // lookahead tiles become strips of kStripCols columns
                         const bool la = next_panel && j0 == p1;
-                        if (tc) {
-                            (la ? a1 : a2).push_back({s, i0, j0});
-                            tile_work(la ? wa1 : wa2, f, i0, j0, w);
+                        std::vector<TileItem> &dst = tc ? (la ? a1 : a2) : (la ? u1 : u2);
+                        if (la) {
+                            for (int32_t jj = j0; jj < std::min(j0 + kUpdTile, f); jj += kStripCols)
+                                dst.push_back({s, i0, jj});
                         } else {
-                            (la ? u1 : u2).push_back({s, i0, j0});
-                            tile_work(la ? w1 : w2, f, i0, j0, w);
+                            dst.push_back({s, i0, j0});
                         }
+                        tile_work(tc ? (la ? wa1 : wa2) : (la ? w1 : w2), f, i0, j0, w);
                     }
                 // pivot block (w^3/3) + triangular solve of the rows below; update of the lower trailing part
                 S.panel_w.flops += w * w * w / 3.0;
@@ -863,14 +865,14 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
             if (prev_rest) cudaStreamWaitEvent(sd, prev_rest, 0);
             if (S.tile_cnt1 > 0) {
                 Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w1, sd);
-                launch_large_update(c->dp, c->fronts, c->D, c->tile_items + S.tile_off, S.tile_cnt1, S.p0, c->opt.nb,
-                                    sd);
+                launch_large_update_strip(c->dp, c->fronts, c->D, c->tile_items + S.tile_off, S.tile_cnt1, S.p0,
+                                          c->opt.nb, sd);
                 nl++;
             }
             if (S.tc_cnt > 0 && !c->mixed_active && S.alt_cnt1 > 0) {
                 Prof pr(c, IPM_K_LARGE_UPDATE, S.alt_w1, sd);
-                launch_large_update(c->dp, c->fronts, c->D, c->alt_items + S.alt_off, S.alt_cnt1, S.p0, c->opt.nb,
-                                    sd);
+                launch_large_update_strip(c->dp, c->fronts, c->D, c->alt_items + S.alt_off, S.alt_cnt1, S.p0,
+                                          c->opt.nb, sd);
                 nl++;
             } else if (use_tc) {
                 Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.tc_w, sd);

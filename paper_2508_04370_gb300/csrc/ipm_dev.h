@@ -84,6 +84,9 @@ struct DevVals {
 constexpr int kPanelRows = 128;
 // Output tile of the FP64 trailing-update kernel.
 constexpr int kUpdTile = 32;
+// Lookahead (next panel) columns of the trailing update are cut into strips
+// of kUpdTile rows x kStripCols columns, one output per thread.
+constexpr int kStripCols = 4;
 // Output tile of the tensor-core trailing update (M = N).
 constexpr int kTcTile = 128;
 
@@ -142,7 +145,8 @@ struct AsmItem {
 };
 struct TileItem {
     int32_t s;
-    int32_t i0, j0;  // local row / column of a 64 x 64 output tile
+    int32_t i0, j0;  // first local row / column of a kUpdTile x kUpdTile output tile
+                     // (kUpdTile x kStripCols for the lookahead strips)
 };
 
 // ---------------------------------------------------------------- launches
@@ -162,6 +166,8 @@ void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items,
                        int32_t p0, int32_t nb, const double *pws, cudaStream_t st);
 constexpr int kTrsmRowsHost = 8;
 constexpr int kPanelWsHost = 32 * 33 + 32;
+void launch_large_update_strip(const DevPlan &P, double *fronts, const double *D, const TileItem *items,
+                               int32_t count, int32_t p0, int32_t w, cudaStream_t st);
 void launch_large_update(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
                          int32_t p0, int32_t w, cudaStream_t st);
 void launch_large_update_tc(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,

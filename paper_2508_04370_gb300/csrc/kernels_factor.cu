@@ -66,6 +66,23 @@ constexpr long long kHuge = 0x5fe0000000000000ll;    // bits(2^511): squares sta
 
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
+// 1 / x for a pivot: the hardware estimate (relative error below 2^-20 for
+// normal x) refined by one third-order Newton-Raphson step for the
+// reciprocal, r' = r (1 + e + e^2) with e = 1 - x r, whose error is about
+// e^3 < 2^-60, below the rounding of the final fused multiply-add (so the
+// result is within about half an ulp).  Three dependent FMAs instead of a
+// full division on the pivot chain.  Outside [2^-1000, 2^1000] in magnitude
+// (never the case for a pivot above the floor eps ||K||_1 of a sensible K)
+// it divides.
+__device__ __forceinline__ double recip_pivot(double x) {
+    const long long a = __double_as_longlong(x) & 0x7fffffffffffffffll;
+    if (a < 0x0170000000000000ll || a > 0x7e70000000000000ll) return 1.0 / x;
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    const double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+
 // x > b for a non-negative, non-NaN b, with IEEE semantics (NaN > b is false).
 __device__ __forceinline__ bool gt_nonneg(long long xb, long long bb) {
     return xb >= 0 && xb <= kInfBits && xb > bb;
@@ -99,7 +116,7 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
     // the common-case pivot and its reciprocal, started before the vote so
     // that the reciprocal's latency overlaps the screen
     const long long dnb_fast = sp < 0 ? tb ^ kSignBit : tb;
-    const double rinv_fast = 1.0 / __longlong_as_double(dnb_fast);
+    const double rinv_fast = recip_pivot(__longlong_as_double(dnb_fast));
     long long dnb;
     bool exact = false;
     if (__any_sync(0xffffffffu, maybe)) {
@@ -134,6 +151,78 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
         piv_out[0] = dn;
         piv_out[1] = exact ? 1.0 / dn : rinv_fast;
     }
+}
+
+// The same decision with the pivot column held one row per lane: lane j
+// holds c = F_jp and g = F_jj (rows j > p of the block [0, w) take part),
+// sl = s_j; d is the pivot after the static term.  Returns the pivot in
+// every lane and its reciprocal through *rinv; lane 0 records D, the
+// statically regularised pivot d (the lift D - d is formed later, off the
+// pivot chain) and the status.
+__device__ __forceinline__ double pivot_lanes(double c, double g, int sl, int p, int w, int sp, double d,
+                                              double b1floor, double *Dout, double *dout, DevCtl *ctl,
+                                              double *rinv) {
+    const int lane = threadIdx.x & 31;
+    const long long db = dbits(d);
+    const long long sdb = sp < 0 ? db ^ kSignBit : db;
+    const long long b1b = dbits(b1floor);
+    const long long tb = gt_nonneg(sdb, b1b) ? sdb : b1b;
+    const bool t_ok = tb > 0x000fffffffffffffll && tb < kInfBits;
+    const bool take = lane > p && lane < w && sl == sp;
+    bool maybe = false;
+    if (take) {
+        const long long jb = dbits(g);
+        const long long ja = jb & kAbsMask;
+        const bool cand = ja != 0 && ja <= kInfBits && ((jb < 0) == (sp < 0));
+        if (cand) {
+            const long long ab = dbits(c) & kAbsMask;
+            if (ab != 0) {
+                const bool screenable = t_ok && ab >= kTiny && ab < kHuge && ja > 0x000fffffffffffffll && ja < kInfBits;
+                maybe = !screenable || 2 * (ab - kBias) >= (ja - kBias) + (tb - kBias) - kScreen;
+            }
+        }
+    }
+    const long long dnb_fast = sp < 0 ? tb ^ kSignBit : tb;
+    double r = recip_pivot(__longlong_as_double(dnb_fast));
+    long long dnb = dnb_fast;
+    if (__any_sync(0xffffffffu, maybe)) {
+        double b2 = 0.0;
+        if (take && sp * g > 0.0) {
+            const double v = c * c / fabs(g);
+            if (v > b2) b2 = v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, b2, o);
+            if (ov > b2) b2 = ov;
+        }
+        const double bnd = b1floor > b2 ? b1floor : b2;
+        const double sd = sp * d;
+        dnb = dbits(sp * (sd > bnd ? sd : bnd));
+        r = 1.0 / __longlong_as_double(dnb);
+    }
+    const double dn = __longlong_as_double(dnb);
+    if (lane == 0) {
+        Dout[p] = dn;
+        dout[p] = d;
+        const bool fin = (db & kAbsMask) < kInfBits && (dnb & kAbsMask) < kInfBits && (dnb & kAbsMask) != 0;
+        if (!fin) atomicOr(&ctl->status, kStatNonFinite);
+    }
+    *rinv = r;
+    return dn;
+}
+
+// Named barriers 1-4 of a 128-thread CTA, the id chosen by parity so that it
+// stays an immediate: sync/arrive on barrier base + (parity & 1).
+template <int kBase>
+__device__ __forceinline__ void bar_sync_parity(int parity) {
+    if (parity & 1) asm volatile("bar.sync %0, 128;" ::"n"(kBase + 1) : "memory");
+    else asm volatile("bar.sync %0, 128;" ::"n"(kBase) : "memory");
+}
+template <int kBase>
+__device__ __forceinline__ void bar_arrive_parity(int parity) {
+    if (parity & 1) asm volatile("bar.arrive %0, 128;" ::"n"(kBase + 1) : "memory");
+    else asm volatile("bar.arrive %0, 128;" ::"n"(kBase) : "memory");
 }
 
 // ------------------------------------------------------------ small fronts
@@ -276,15 +365,21 @@ __global__ void __launch_bounds__(256) k_large_assemble(DevPlan P, DevVals V, do
 }
 
 // Panel [p0, p1) of a large front, step 1: the nb x nb diagonal block,
-// one CTA per front.  Warp 0 decides each pivot (pivot_warp) and scales the
-// pivot column, keeping its unscaled copy w_j = F_jp; then all threads apply
-// the rank-1 update F_ij -= l_i w_j to the block's remaining lower triangle,
-// whose entries are enumerated densely (last column first) so that each warp
-// issues as few FP64 instructions as possible.  The factorised block goes
-// back to the slab (L strictly below the diagonal, D on it) together with D
-// and the lifts, and the panel workspace of the front receives the rows of
-// L_11 (row-major, ws[q * 33 + q'] = L_qq') and 1 / d_q for the triangular
-// solve of the rows below.
+// one CTA per front, as a two-stage pipeline over the pivots.  Warp 0 owns
+// the pivot chain: for pivot p it applies pivot p-1 to column p, decides p
+// (pivot_lanes), scales the column (l_jp = F_jp / d_p, keeping the unscaled
+// w_jp = F_jp) and applies p to the diagonal entries it keeps in registers;
+// then it publishes p.  Warps 1-3 apply pivot p to the strictly lower
+// entries of columns >= p + 2 while warp 0 already works on pivot p + 1,
+// which needs only column p + 1 and the diagonal; each of their threads
+// holds up to five of these entries in registers for the whole panel.  Named barriers 1-2 (pivot published) and 3-4 (columns updated)
+// alternate by pivot parity, so neither side runs more than one pivot
+// ahead.  Every entry receives the updates of all earlier pivots in pivot
+// order, as in the sequential elimination.  The factorised block goes back
+// to the slab (L strictly below the diagonal, D on it) together with D and
+// the lifts, and the panel workspace of the front receives the rows of L_11
+// (row-major, ws[q * 33 + q'] = L_qq') and 1 / d_q for the triangular solve
+// of the rows below.
 constexpr int kPanelWs = 32 * 33 + 32;  // doubles of panel workspace per large front
 
 __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double *__restrict__ fronts,
@@ -293,15 +388,16 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
                                                      const PanelItem *__restrict__ items, int p0, int nb,
                                                      double *__restrict__ pws) {
     __shared__ double Fd[32 * 33];
-    __shared__ double Dtmp[32], dyntmp[32], rtmp[32], wsave[32];
-    __shared__ double piv[2];
-    __shared__ uint16_t tri[496];  // (column << 8 | row) of the strictly trailing triangle
+    __shared__ double wsv[2][32];
+    __shared__ double Dtmp[32], dstat[32], rtmp[32];
     __shared__ int8_t sg[32];
-    constexpr int LDD = 33, NT = 128;
+    constexpr int LDD = 33, NT = 128, NU = NT - 32, kOwn = 5;  // 5 x 96 >= 435 entries
+    constexpr int kBarPub = 1, kBarUpd = 3;
     const PanelItem it = items[blockIdx.x];
     const int s = it.s;
     const int k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
     const int w = min(p0 + nb, k) - p0;
+    if (w <= 0) return;
     double *F = fronts + P.sn_off[s];
     double *ws = pws + (int64_t)it.r1 * kPanelWs;  // r1 carries the workspace slot
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -311,41 +407,92 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
         const int jj = t >> 5, ii = t & 31;
         Fd[jj * LDD + ii] = (jj < w && ii < w && ii >= jj) ? F[(int64_t)(p0 + jj) * ld + (p0 + ii)] : 0.0;
     }
-    // entry e = r (r + 1) / 2 + c  ->  column w-1-r, row w-1-r+c  (0 <= c <= r)
-    for (int e = tid; e < (w - 1) * w / 2; e += NT) {
-        int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-        while ((r + 1) * (r + 2) / 2 <= e) r++;
-        while (r * (r + 1) / 2 > e) r--;
-        const int jj = w - 1 - r, ii = jj + (e - r * (r + 1) / 2);
-        tri[e] = (uint16_t)((jj << 8) | ii);
-    }
     if (tid < 32) sg[tid] = tid < w ? P.sign[c0 + p0 + tid] : (int8_t)0;
     __syncthreads();
-    const double b1floor = pivot_floor(P, ctl, c0);
-    for (int p = 0; p < w; p++) {
-        if (warp == 0) {
-            pivot_warp(Fd, LDD, p, w, sg, V.rho, V.delta, b1floor, Dtmp, dyntmp, ctl, piv);
-            __syncwarp();
-            const double rinv = piv[1];
-            const int i = p + 1 + lane;
-            if (i < w) {
-                const double v = Fd[p * LDD + i];
-                wsave[i] = v;
-                Fd[p * LDD + i] = v * rinv;
+    if (warp == 0) {
+        // lane j keeps c = F_jp of the current pivot column, g = F_jj and
+        // gs = F_jj + s_j sigma_j (the static term) up to date; per pivot the
+        // chain is the reciprocal, the scaling l = c / d and three
+        // independent FMAs that bring c, g and gs to the next pivot
+        const double b1floor = pivot_floor(P, ctl, c0);
+        const int sl = sg[lane];
+        double g = lane < w ? Fd[lane * LDD + lane] : 0.0;   // F_jj of row j = lane
+        double gs = g + (sl < 0 ? -V.rho : V.delta);
+        double c = (lane > 0 && lane < w) ? Fd[lane] : 0.0;  // column 0
+        for (int p = 0; p < w; p++) {
+            const int sp = __shfl_sync(0xffffffffu, sl, p);
+            const double d = __shfl_sync(0xffffffffu, gs, p);
+            double rinv;
+            const double dn = pivot_lanes(c, g, sl, p, w, sp, d, b1floor, Dtmp, dstat, ctl, &rinv);
+            const bool below = lane > p && lane < w;
+            const double l = below ? c * rinv : 0.0;
+            if (below) {
+                Fd[p * LDD + lane] = l;
+                wsv[p & 1][lane] = c;
             }
             if (lane == 0) {
-                Fd[p * LDD + p] = piv[0];
+                Fd[p * LDD + p] = dn;
                 rtmp[p] = rinv;
             }
+            __syncwarp();
+            bar_arrive_parity<kBarPub>(p);
+            if (p + 1 < w) {
+                if (p >= 1) bar_sync_parity<kBarUpd>(p + 1);  // pivot p-1 applied to columns >= p+1
+                const double wn = __shfl_sync(0xffffffffu, c, p + 1);  // w_{p+1,p}, unscaled
+                const double f = (lane > p + 1 && lane < w) ? Fd[(p + 1) * LDD + lane] : 0.0;
+                const double cn = f - l * wn;
+                g -= l * c;
+                gs -= l * c;
+                c = lane > p + 1 ? cn : 0.0;
+            }
         }
-        __syncthreads();
-        const int ne = (w - 1 - p) * (w - p) / 2;  // entries with column > p
-        for (int e = tid; e < ne; e += NT) {
-            const int code = tri[e], jj = code >> 8, ii = code & 255;
-            Fd[jj * LDD + ii] -= Fd[p * LDD + ii] * wsave[jj];
+    } else {
+        // this thread owns the strictly lower entries e = ut + 96 t of columns
+        // >= 2, enumerated last column first: e = r (r + 1) / 2 + c  ->
+        // column w-2-r, row w-1-r+c (0 <= c <= r); it keeps them in registers
+        // and stores an entry when its column has received its last update
+        // here (pivot column - 2)
+        const int ut = tid - 32;
+        const int nall = w >= 3 ? (w - 3) * (w - 2) / 2 : 0;
+        int jo[kOwn], io[kOwn];
+        double vo[kOwn];
+#pragma unroll
+        for (int t = 0; t < kOwn; t++) {
+            const int e = ut + NU * t;
+            jo[t] = 0;
+            io[t] = 0;
+            vo[t] = 0.0;
+            if (e < nall) {
+                int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+                while ((r + 1) * (r + 2) / 2 <= e) r++;
+                while (r * (r + 1) / 2 > e) r--;
+                jo[t] = w - 2 - r;
+                io[t] = w - 1 - r + (e - r * (r + 1) / 2);
+                vo[t] = Fd[jo[t] * LDD + io[t]];
+            }
         }
-        __syncthreads();
+        for (int q = 0; q < w; q++) {
+            bar_sync_parity<kBarPub>(q);
+            const int m = w - 3 - q;  // columns >= q + 2 have m (m + 1) / 2 such entries
+            const int ne = m > 0 ? m * (m + 1) / 2 : 0;
+            double lq[kOwn], wq[kOwn];
+#pragma unroll
+            for (int t = 0; t < kOwn; t++) {
+                const bool on = ut + NU * t < ne;
+                lq[t] = on ? Fd[q * LDD + io[t]] : 0.0;
+                wq[t] = on ? wsv[q & 1][jo[t]] : 0.0;
+            }
+#pragma unroll
+            for (int t = 0; t < kOwn; t++) {
+                if (ut + NU * t < ne) {
+                    vo[t] -= lq[t] * wq[t];
+                    if (jo[t] == q + 2) Fd[jo[t] * LDD + io[t]] = vo[t];
+                }
+            }
+            if (q <= w - 3) bar_arrive_parity<kBarUpd>(q);
+        }
     }
+    __syncthreads();
     for (int t = tid; t < 32 * 32; t += NT) {
         const int jj = t >> 5, ii = t & 31;
         const bool in = jj < w && ii < w;
@@ -355,9 +502,10 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
     for (int t = tid; t < 32; t += NT) {
         ws[32 * 33 + t] = t < w ? rtmp[t] : 0.0;
         if (t < w) {
-            Dg[c0 + p0 + t] = Dtmp[t];
+            const double dn = Dtmp[t], d = dstat[t];
+            Dg[c0 + p0 + t] = dn;
             Dig[c0 + p0 + t] = rtmp[t];
-            dyng[c0 + p0 + t] = dyntmp[t];
+            dyng[c0 + p0 + t] = dbits(dn) == dbits(d) ? 0.0 : dn - d;
         }
     }
 }
@@ -453,6 +601,46 @@ __global__ void __launch_bounds__(256) k_large_update(DevPlan P, double *__restr
             const int i = it.i0 + tx + 16 * a;
             if (i < f && i >= j) F[(int64_t)j * ld + i] -= acc[a][b];
         }
+    }
+}
+
+// The same update for the next panel's columns, which lie on the critical
+// path: strips of kUpdTile rows x kStripCols columns, one output per thread,
+// summed over the panel's pivots in the same order as k_large_update (so
+// the results are identical).  A whole 32 x 32 tile is 32k FP64 FMAs, about
+// 8 us on one SM of this GPU; the strips spread those few tiles over eight
+// times as many SMs.
+__global__ void __launch_bounds__(32 * kStripCols) k_large_update_strip(DevPlan P, double *__restrict__ fronts,
+                                                                        const double *__restrict__ Dg,
+                                                                        const TileItem *__restrict__ items, int p0,
+                                                                        int w) {
+    constexpr int T = kUpdTile, C = kStripCols, NT = 32 * kStripCols;
+    static_assert(T == 32, "one row per lane");
+    __shared__ double As[32][T + 1];
+    __shared__ double Bs[32][C];
+    const TileItem it = items[blockIdx.x];
+    const int s = it.s;
+    const int f = P.sn_f[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
+    w = min(w, P.sn_k[s] - p0);  // ragged last panel
+    const double *Fc = fronts + P.sn_off[s];
+    const int tid = threadIdx.x;
+    for (int t = tid; t < 32 * T; t += NT) {
+        const int q = t / T, r = t % T;
+        const int i = it.i0 + r;
+        As[q][r] = (q < w && i < f) ? Fc[(int64_t)(p0 + q) * ld + i] : 0.0;
+    }
+    {
+        const int q = tid / C, cc = tid % C;  // NT == 32 * C: one entry each
+        const int j = it.j0 + cc;
+        Bs[q][cc] = (q < w && j < f) ? Fc[(int64_t)(p0 + q) * ld + j] * Dg[c0 + p0 + q] : 0.0;
+    }
+    __syncthreads();
+    const int r = tid & 31, cc = tid >> 5;
+    const int i = it.i0 + r, j = it.j0 + cc;
+    if (i < f && j < f && i >= j) {
+        double acc = 0.0;
+        for (int q = 0; q < w; q++) acc += As[q][r] * Bs[q][cc];
+        fronts[P.sn_off[s] + (int64_t)j * ld + i] -= acc;
     }
 }
 
@@ -565,6 +753,12 @@ void launch_large_update(const DevPlan &P, double *fronts, const double *D, cons
                          int32_t p0, int32_t w, cudaStream_t st) {
     if (count <= 0) return;
     k_large_update<<<count, 256, 0, st>>>(P, fronts, D, items, p0, w);
+}
+
+void launch_large_update_strip(const DevPlan &P, double *fronts, const double *D, const TileItem *items,
+                               int32_t count, int32_t p0, int32_t w, cudaStream_t st) {
+    if (count <= 0) return;
+    k_large_update_strip<<<count, 32 * kStripCols, 0, st>>>(P, fronts, D, items, p0, w);
 }
 
 void launch_norm1(const DevPlan &P, const DevVals &V, DevCtl *ctl, double eps_piv, cudaStream_t st) {

@@ -606,8 +606,7 @@ std::vector<int32_t> order_nd(const Graph &g, int32_t leaf, double dense_factor)
             below += cnt[l];
             const int64_t sep = std::min(lo_sep[l], hi_sep[l]);
             if (std::min(left, right) - sep < (int64_t)(0.2 * n)) continue;
-            const double mn = (double)std::min(left, right), mx = (double)std::max(left, right);
-            cands.push_back({(double)sep * (1.0 + 0.5 * (mx - mn) / (double)n), l});
+            cands.push_back({(double)sep / ((double)(left - sep) * (double)(right - sep) + 1.0), l});
         }
         if (cands.empty()) {
             std::vector<int32_t> o = order_amd(h, 0.0);
@@ -626,8 +625,7 @@ std::vector<int32_t> order_nd(const Graph &g, int32_t leaf, double dense_factor)
             for (int32_t v = 0; v < n; v++) c1 += trial[v] == 1;
             const int64_t c2 = n - sep - c1;
             if (c1 <= 0 || c2 <= 0) continue;
-            const double mn = (double)std::min(c1, c2), mx = (double)std::max(c1, c2);
-            const double score = (double)sep * (1.0 + 0.5 * (mx - mn) / (double)n);
+            const double score = (double)sep / ((double)c1 * (double)c2);
             if (score < best_score) {
                 best_score = score;
                 part.swap(trial);
