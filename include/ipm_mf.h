@@ -101,10 +101,13 @@ typedef struct ipm_options {
     int32_t nd_leaf;          /* nested dissection stops at subgraphs of this size; 128 */
     double dense_row_factor;  /* AMD treats degree > max(16, f*sqrt(N)) as dense; 10 */
     int32_t device;           /* CUDA device ordinal; 0 */
-    int32_t spin_limit_log2;  /* dependency waits of the persistent solve give up after 2^this polls (each
-                                 >= 64 ns) and report IPM_ERR_DEVICE_TIMEOUT; -1 = give up at once (tests
-                                 of the failure path); 24 */
+    int32_t spin_limit_log2;  /* dependency waits of the persistent solve and of the level kernel give up
+                                 after 2^this polls (each >= 64 ns) and report IPM_ERR_DEVICE_TIMEOUT;
+                                 -1 = give up at once (tests of the failure path); 24 */
     int32_t verbose;          /* print analysis statistics to stderr; 0 */
+    int32_t level_kernel;     /* FP64 large fronts: 1 = one persistent, dependency-driven launch per tree
+                                 level (diagonal blocks, triangular solves and trailing updates of all the
+                                 level's large fronts); 0 = one launch per kernel and pivot block; 1 */
 } ipm_options;
 
 typedef struct ipm_info {

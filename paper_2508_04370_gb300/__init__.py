@@ -60,6 +60,7 @@ class ipm_options(ct.Structure):
         ("device", ct.c_int32),
         ("spin_limit_log2", ct.c_int32),
         ("verbose", ct.c_int32),
+        ("level_kernel", ct.c_int32),
     ]
 
 

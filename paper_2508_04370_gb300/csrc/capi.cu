@@ -54,6 +54,10 @@ struct LevelWork {
     int32_t asm_cnt;
     std::vector<StepWork> steps;
     Work asm_w, fwd_w, bwd_w;
+    int64_t lvl_off = 0;   // items of the persistent level kernel (FP64 large fronts)
+    int32_t lvl_cnt = 0;
+    int32_t lvl_ncnt = 0;  // its dependency counters
+    bool has_tc = false;   // some front of the level has tensor-core update tiles
 };
 
 struct ProfRec {
@@ -92,6 +96,9 @@ struct ipm_ctx {
     int32_t *trsm_slots = nullptr;
     double *panel_ws = nullptr;
     TileItem *tile_items = nullptr, *tc_items = nullptr, *alt_items = nullptr;
+    FactorItem *lvl_items = nullptr;  // persistent level kernel: items of all levels
+    int32_t *lvl_sync = nullptr;      // its ticket and counters (1 + max counters of a level)
+    int32_t lvl_grid = 1;
     bool mixed_active = false;  // tensor-core updates in use (mixed precision, no fallback yet)
     int32_t fallbacks = 0;
     double flops_tensor = 0.0;
@@ -209,6 +216,182 @@ int dupload(ipm_ctx *c, T **p, const std::vector<T> &h) {
         if (e != cudaSuccess) return to_err(e);
     }
     return IPM_OK;
+}
+
+// Items of the persistent level kernel for the large fronts of level l, in
+// ticket order: all assembly items, then per pivot block t the diagonal
+// blocks, the triangular solves, the remaining trailing tiles of block t-1
+// and the lookahead strips of block t (after the last block, the remaining
+// tiles of the last block).  Counters per front (base b): b+0 assembly
+// items done, b+1 diagonal blocks done, b+2 triangular-solve chunks done,
+// then one counter per 32 x 32 tile (ib >= jb) of the front that grows by 8
+// per pivot block applied to the tile (a whole tile adds 8, the strips of a
+// tile add 8 between them).  Every wait refers to items placed earlier:
+//   diagonal block t:     tile (t, t) >= 8 t (assembly done for t = 0),
+//   solve chunk (t, r):   diagonal block t done, tile (r / 32, t) >= 8 t,
+//   update (t, ib, jb):   all solve chunks of blocks <= t, tile >= 8 t.
+// Tiles lie on the front's 32-grid; updates skip the columns < p1 (the
+// panel's own columns) of a grid tile that a partial last panel cuts.
+void build_level_items(const Plan &P, int32_t l, LevelWork &W, const std::vector<int32_t> &slot_of,
+                       std::vector<FactorItem> &items, std::vector<int32_t> &cbase) {
+    constexpr int32_t B = kUpdTile;  // == nb == 32
+    W.lvl_off = (int64_t)items.size();
+    const int32_t t0 = P.lvl_large_ptr[l], t1 = P.lvl_large_ptr[l + 1];
+    int32_t ncnt = 0, maxsteps = 0;
+    for (int32_t q = t0; q < t1; q++) {
+        const int32_t s = P.lvl_large[q], nblk = (P.sn_f[s] + B - 1) / B;
+        cbase[s] = ncnt;
+        ncnt += 3 + nblk * (nblk + 1) / 2;
+        maxsteps = std::max(maxsteps, (P.sn_k[s] + B - 1) / B);
+    }
+    auto tidx = [&](int32_t s, int32_t ib, int32_t jb) { return cbase[s] + 3 + ib * (ib + 1) / 2 + jb; };
+    auto item = [](int32_t kind, int32_t s, int32_t t, int32_t a, int32_t b, int32_t aux) {
+        FactorItem it;
+        it.kind = kind;
+        it.s = s;
+        it.t = t;
+        it.a = a;
+        it.b = b;
+        it.aux = aux;
+        it.wait0 = it.wait1 = -1;
+        it.need0 = it.need1 = 0;
+        it.sig = -1;
+        it.add = 0;
+        return it;
+    };
+    // assembly, in the order of the level's AsmItems
+    int64_t ai = W.asm_off;
+    for (int32_t q = t0; q < t1; q++) {
+        const int32_t s = P.lvl_large[q];
+        for (int32_t cl = 0; cl < P.sn_f[s]; cl += B) {
+            FactorItem it = item(kItemAssemble, s, 0, cl, std::min(cl + B, P.sn_f[s]), (int32_t)ai++);
+            it.sig = cbase[s];
+            it.add = 1;
+            items.push_back(it);
+        }
+    }
+    // triangular-solve chunks of rows [p1, f): the first ends at the next
+    // multiple of kTrsmRowsHost, so that no chunk crosses a 32-row tile
+    // (each chunk waits on the one tile it lies in)
+    auto chunk_end = [](int32_t r, int32_t f) { return std::min(f, (r / kTrsmRowsHost + 1) * kTrsmRowsHost); };
+    auto nchunks = [&](int32_t p1, int32_t f) {
+        int32_t n = 0;
+        for (int32_t r = p1; r < f; r = chunk_end(r, f)) n++;
+        return n;
+    };
+    // solve chunks of blocks <= t of front s
+    auto cum_chunks = [&](int32_t s, int32_t t) {
+        const int32_t k = P.sn_k[s], f = P.sn_f[s];
+        int32_t n = 0;
+        for (int32_t u = 0; u <= t && u * B < k; u++) n += nchunks(std::min((u + 1) * B, k), f);
+        return n;
+    };
+    // updates of block t of front s: tiles (ib, jb >= first) with the
+    // lookahead column block as strips when la
+    auto updates = [&](int32_t q, int32_t t, bool lookahead) {
+        const int32_t s = P.lvl_large[q], k = P.sn_k[s], f = P.sn_f[s];
+        if (t * B >= k) return;
+        const int32_t p1 = std::min((t + 1) * B, k);
+        if (p1 >= f) return;
+        const bool next_panel = p1 < k;
+        const int32_t jb0 = p1 / B, nblk = (f + B - 1) / B, nchunk = cum_chunks(s, t);
+        for (int32_t jb = jb0; jb < nblk; jb++) {
+            const bool la = next_panel && jb == t + 1;
+            if (la != lookahead) continue;
+            for (int32_t ib = jb; ib < nblk; ib++) {
+                const int32_t need = 8 * t;
+                if (la) {
+                    const int32_t c1 = std::min((jb + 1) * B, f), nstrip = (c1 - jb * B + kStripCols - 1) / kStripCols;
+                    for (int32_t u = 0; u < nstrip; u++) {
+                        FactorItem it = item(kItemStrip, s, t, ib * B, jb * B + u * kStripCols, 0);
+                        it.wait0 = cbase[s] + 2;
+                        it.need0 = nchunk;
+                        if (t > 0) {
+                            it.wait1 = tidx(s, ib, jb);
+                            it.need1 = need;
+                        }
+                        it.sig = tidx(s, ib, jb);
+                        it.add = u + 1 < nstrip ? 1 : 8 - (nstrip - 1);
+                        items.push_back(it);
+                    }
+                } else {
+                    FactorItem it = item(kItemTile, s, t, ib * B, jb * B, 0);
+                    it.wait0 = cbase[s] + 2;
+                    it.need0 = nchunk;
+                    if (t > 0) {
+                        it.wait1 = tidx(s, ib, jb);
+                        it.need1 = need;
+                    }
+                    it.sig = tidx(s, ib, jb);
+                    it.add = 8;
+                    items.push_back(it);
+                }
+            }
+        }
+    };
+    for (int32_t t = 0; t <= maxsteps; t++) {
+        if (t < maxsteps) {
+            for (int32_t q = t0; q < t1; q++) {
+                const int32_t s = P.lvl_large[q];
+                if (t * B >= P.sn_k[s]) continue;
+                FactorItem it = item(kItemDiag, s, t, 0, 0, slot_of[s]);
+                if (t == 0) {
+                    it.wait0 = cbase[s];
+                    it.need0 = (P.sn_f[s] + B - 1) / B;
+                } else {
+                    it.wait0 = tidx(s, t, t);
+                    it.need0 = 8 * t;
+                }
+                it.sig = cbase[s] + 1;
+                it.add = 1;
+                items.push_back(it);
+            }
+            for (int32_t q = t0; q < t1; q++) {
+                const int32_t s = P.lvl_large[q], k = P.sn_k[s], f = P.sn_f[s];
+                if (t * B >= k) continue;
+                const int32_t p1 = std::min((t + 1) * B, k);
+                for (int32_t r = p1; r < f; r = chunk_end(r, f)) {
+                    FactorItem it = item(kItemTrsm, s, t, r, chunk_end(r, f), slot_of[s]);
+                    it.wait0 = cbase[s] + 1;
+                    it.need0 = t + 1;
+                    if (t > 0) {
+                        it.wait1 = tidx(s, r / B, t);
+                        it.need1 = 8 * t;
+                    }
+                    it.sig = cbase[s] + 2;
+                    it.add = 1;
+                    items.push_back(it);
+                }
+            }
+        }
+        if (t > 0)
+            for (int32_t q = t0; q < t1; q++) updates(q, t - 1, false);
+        if (t < maxsteps)
+            for (int32_t q = t0; q < t1; q++) updates(q, t, true);
+    }
+    W.lvl_cnt = (int32_t)(items.size() - W.lvl_off);
+    W.lvl_ncnt = ncnt;
+    // Deadlock freedom, checked: running the items one at a time in ticket
+    // order must meet every wait (then every wait of the parallel run is met
+    // by items with smaller tickets, all of which complete by induction).
+    // A level that fails the check keeps the one-launch-per-step path.
+    std::vector<int32_t> sim(ncnt, 0);
+    bool ok = true;
+    for (int64_t i = W.lvl_off; i < (int64_t)items.size() && ok; i++) {
+        const FactorItem &it = items[i];
+        for (int u = 0; u < 2; u++) {
+            const int32_t wi = u ? it.wait1 : it.wait0, need = u ? it.need1 : it.need0;
+            if (wi >= ncnt || (wi >= 0 && sim[wi] < need)) ok = false;
+        }
+        if (it.sig >= ncnt) ok = false;
+        if (it.kind == kItemTrsm && (it.a / B != (it.b - 1) / B || it.b - it.a > kTrsmRowsHost)) ok = false;
+        if (ok && it.sig >= 0) sim[it.sig] += it.add;
+    }
+    if (!ok) {
+        items.resize(W.lvl_off);
+        W.lvl_cnt = 0;
+        W.lvl_ncnt = 0;
+    }
 }
 
 void free_device(ipm_ctx *c) {
@@ -424,6 +607,9 @@ int setup_device(ipm_ctx *c) {
     for (int32_t s = 0; s < P.nsuper; s++)
         if (P.sn_large[s]) slot_of[s] = nslots++;
     std::vector<TileItem> tile_items, tc_items, alt_items;
+    std::vector<FactorItem> lvl_items;
+    std::vector<int32_t> cbase(P.nsuper, -1);
+    int32_t max_ncnt = 0;
     c->levels.assign(P.nlevels, LevelWork());
     c->flops_tensor = 0.0;
     // algorithmic work of assembling and factorising one front
@@ -584,7 +770,10 @@ int setup_device(ipm_ctx *c) {
             S.tc_cnt = (int32_t)(tc_items.size() - S.tc_off);
             S.alt_cnt = (int32_t)(alt_items.size() - S.alt_off);
             W.steps.push_back(S);
+            if (S.tc_cnt > 0) W.has_tc = true;
         }
+        build_level_items(P, l, W, slot_of, lvl_items, cbase);
+        max_ncnt = std::max(max_ncnt, W.lvl_ncnt);
     }
     std::vector<int64_t> upd_off(P.upd_off.begin(), P.upd_off.end());
     std::vector<int32_t> bwd_order(lvl_all.rbegin(), lvl_all.rend());
@@ -610,6 +799,7 @@ int setup_device(ipm_ctx *c) {
         (rc = dalloc(c, &c->panel_ws, (size_t)std::max(nslots, 1) * kPanelWsHost)) ||
         (rc = dupload(c, &c->tile_items, tile_items)) || (rc = dupload(c, &c->tc_items, tc_items)) ||
         (rc = dupload(c, &c->alt_items, alt_items)) || (rc = dupload(c, &c->bwd_order, bwd_order)) ||
+        (rc = dupload(c, &c->lvl_items, lvl_items)) || (rc = dalloc(c, &c->lvl_sync, (size_t)max_ncnt + 1)) ||
         (rc = dalloc(c, &c->solve_sync, (size_t)3 * ns + 1)))
         return rc;
     int32_t *d_sparent;
@@ -621,6 +811,9 @@ int setup_device(ipm_ctx *c) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_probe_kernel(), 256,
                                                       (size_t)std::max(P.max_f, kRectRows) * sizeof(double));
         c->solve_grid = std::max(1, std::min(ns, sms * std::max(1, per_sm)));
+        int lvl_per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lvl_per_sm, large_level_kernel(), 256, 0);
+        c->lvl_grid = sms * std::max(1, lvl_per_sm);
     }
     DevPlan &dp = c->dp;
     dp.N = N;
@@ -812,6 +1005,26 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         }
         if (W.asm_cnt == 0 && W.steps.empty()) continue;
         if (small_before) cudaStreamWaitEvent(sd, small_before, 0);
+        if (c->opt.level_kernel && W.lvl_cnt > 0 && !(W.has_tc && c->mixed_active)) {
+            // FP64: all large-front work of the level in one dependency-driven launch
+            Work lw = W.asm_w;
+            for (const StepWork &S : W.steps)
+                for (const Work *x : {&S.panel_w, &S.trsm_w, &S.tile_w, &S.tile_w1}) {
+                    lw.flops += x->flops;
+                    lw.bytes += x->bytes;
+                }
+            {
+                Prof pr(c, IPM_K_LARGE_PANEL, lw, sd);
+                launch_large_level(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_items + W.lvl_off,
+                                   W.lvl_cnt, c->lvl_sync, W.lvl_ncnt, c->asm_info, c->asm_cr, c->panel_ws,
+                                   c->opt.nb, c->lvl_grid,
+                                   c->opt.spin_limit_log2 < 0 ? 0 : (1ll << c->opt.spin_limit_log2), sd);
+            }
+            nl++;
+            last_large = c->dep_ev[5 + 5 * l];
+            cudaEventRecord(last_large, sd);
+            continue;
+        }
         if (W.asm_cnt > 0) {
             Prof pr(c, IPM_K_LARGE_ASSEMBLE, W.asm_w, sd);
             launch_large_assemble(c->dp, V, c->fronts, c->asm_items + W.asm_off, c->asm_info + W.asm_off, c->asm_cr,
@@ -998,6 +1211,7 @@ void ipm_default_options(ipm_options *o) {
     o->dense_row_factor = 10.0;
     o->device = 0;
     o->spin_limit_log2 = 24;
+    o->level_kernel = 1;
     o->verbose = 0;
 }
 
@@ -1010,6 +1224,7 @@ int ipm_create(ipm_ctx **out, const ipm_options *opt) {
     if (c->opt.nb != 32 || c->opt.refine_max < 0 || c->opt.refine_max > 15 ||
         c->opt.gmres_restarts < 0 || c->opt.gmres_restarts > 16 ||
         c->opt.spin_limit_log2 < -1 || c->opt.spin_limit_log2 > 40 || !(c->opt.eps_piv >= 0.0) ||
+        c->opt.level_kernel < 0 || c->opt.level_kernel > 1 ||
         (c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED) || c->opt.mixed_min_front < 1) {
         delete c;
         return IPM_ERR_INVALID_ARG;

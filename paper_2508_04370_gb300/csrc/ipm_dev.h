@@ -149,6 +149,21 @@ struct TileItem {
                      // (kUpdTile x kStripCols for the lookahead strips)
 };
 
+// One item of the persistent level kernel (large fronts of one tree level):
+// it waits until counter wait0 >= need0 and counter wait1 >= need1 (-1: no
+// wait), runs, then adds `add` to counter sig.  Counters are per level,
+// zeroed before the launch; the host orders the items so that every wait
+// refers to items with smaller positions.
+enum : int32_t { kItemAssemble = 0, kItemDiag = 1, kItemTrsm = 2, kItemStrip = 3, kItemTile = 4 };
+struct FactorItem {
+    int32_t kind;
+    int32_t s, t;  // front, pivot block (panel) index
+    int32_t a, b;  // assemble: columns [a, b); trsm: rows [a, b); strip / tile: first row, first column
+    int32_t aux;   // assemble: AsmItem index; diag / trsm: panel workspace slot
+    int32_t wait0, need0, wait1, need1;
+    int32_t sig, add;
+};
+
 // ---------------------------------------------------------------- launches
 // factorisation (kernels_factor.cu)
 void launch_norm1(const DevPlan &P, const DevVals &V, DevCtl *ctl, double eps_piv, cudaStream_t st);
@@ -168,6 +183,11 @@ constexpr int kTrsmRowsHost = 8;
 constexpr int kPanelWsHost = 32 * 33 + 32;
 void launch_large_update_strip(const DevPlan &P, double *fronts, const double *D, const TileItem *items,
                                int32_t count, int32_t p0, int32_t w, cudaStream_t st);
+void launch_large_level(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
+                        DevCtl *ctl, const FactorItem *items, int32_t count, int32_t *sync, int32_t ncounters,
+                        const AsmItem *ainfo, const int32_t *acr, double *pws, int32_t nb, int32_t grid,
+                        long long spin_limit, cudaStream_t st);
+const void *large_level_kernel();
 void launch_large_update(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
                          int32_t p0, int32_t w, cudaStream_t st);
 void launch_large_update_tc(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,

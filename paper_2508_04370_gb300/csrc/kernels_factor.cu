@@ -88,6 +88,40 @@ __device__ __forceinline__ bool gt_nonneg(long long xb, long long bb) {
     return xb >= 0 && xb <= kInfBits && xb > bb;
 }
 
+// The exact evaluation of the rule for the lanes the integer screen could
+// not settle (maybe).  For non-negative values the rule only takes maxima,
+// so it runs on bit patterns: the result is max(s_p d, b1, b2) and a lane
+// can change it only if its F_jp^2 / |F_jj| exceeds t = max(s_p d, b1).  A
+// second screen decides that without dividing: with a = fl(F_jp^2) and
+// b = fl(t |F_jj|), bits(a) < bits(b) - 16 gives a < b (1 - 2^-49) and so
+// fl(a / |F_jj|) < t (for lanes inside the first screen's ranges, where no
+// product over- or underflows in a way that could mislead it).  Only the
+// lanes left over divide, as the rule is written.  Returns the bits of the
+// signed pivot.
+__device__ __forceinline__ long long pivot_exact_bits(bool maybe, bool screenable, double c, double g, long long tb,
+                                                      long long sdb, long long b1b, int sp) {
+    bool need = false;
+    if (maybe) {
+        need = true;
+        if (screenable) {
+            const long long a = dbits(c * c), b = dbits(__longlong_as_double(tb) * fabs(g));
+            need = !(a < b - 16);
+        }
+    }
+    long long b2b = 0;
+    if (__any_sync(0xffffffffu, need)) {
+        if (need) b2b = dbits(c * c / fabs(g));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ov = __shfl_xor_sync(0xffffffffu, b2b, o);
+            if (ov > b2b) b2b = ov;
+        }
+    }
+    const long long bndb = b1b > b2b ? b1b : b2b;            // max(b1, b2), both >= 0
+    const long long res = gt_nonneg(sdb, bndb) ? sdb : bndb;  // s_p d > bnd ? s_p d : bnd
+    return sp < 0 ? res ^ kSignBit : res;
+}
+
 __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int w, const int8_t *sgn, double rho,
                                            double delta, double b1floor, double *Dout, double *dynout, DevCtl *ctl,
                                            double *piv_out) {
@@ -99,16 +133,19 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
     const long long b1b = dbits(b1floor);
     const long long tb = gt_nonneg(sdb, b1b) ? sdb : b1b;  // bits of t = max(s_p d, b1)
     const bool t_ok = tb > 0x000fffffffffffffll && tb < kInfBits;  // t normal and finite
-    bool maybe = false;
+    bool maybe = false, screenable = false;
+    double c = 0.0, g = 0.0;
     const int j = p + 1 + lane;
     if (j < w && sgn[j] == sp) {
-        const long long jb = dbits(Fd[j * LDD + j]);
+        g = Fd[j * LDD + j];
+        const long long jb = dbits(g);
         const long long ja = jb & kAbsMask;
         const bool cand = ja != 0 && ja <= kInfBits && ((jb < 0) == (sp < 0));  // s_j F_jj > 0
         if (cand) {
-            const long long ab = dbits(Fd[p * LDD + j]) & kAbsMask;
+            c = Fd[p * LDD + j];
+            const long long ab = dbits(c) & kAbsMask;
             if (ab != 0) {
-                const bool screenable = t_ok && ab >= kTiny && ab < kHuge && ja > 0x000fffffffffffffll && ja < kInfBits;
+                screenable = t_ok && ab >= kTiny && ab < kHuge && ja > 0x000fffffffffffffll && ja < kInfBits;
                 maybe = !screenable || 2 * (ab - kBias) >= (ja - kBias) + (tb - kBias) - kScreen;
             }
         }
@@ -117,31 +154,8 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
     // that the reciprocal's latency overlaps the screen
     const long long dnb_fast = sp < 0 ? tb ^ kSignBit : tb;
     const double rinv_fast = recip_pivot(__longlong_as_double(dnb_fast));
-    long long dnb;
-    bool exact = false;
-    if (__any_sync(0xffffffffu, maybe)) {
-        exact = true;
-        // exact evaluation of b2 and of the rule, as written
-        double b2 = 0.0;
-        if (j < w && sgn[j] == sp) {
-            const double fjj = Fd[j * LDD + j];
-            if (sp * fjj > 0.0) {
-                const double fjp = Fd[p * LDD + j];
-                const double v = fjp * fjp / fabs(fjj);
-                if (v > b2) b2 = v;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, b2, o);
-            if (ov > b2) b2 = ov;
-        }
-        const double bnd = b1floor > b2 ? b1floor : b2;
-        const double sd = sp * d;
-        dnb = dbits(sp * (sd > bnd ? sd : bnd));
-    } else {
-        dnb = dnb_fast;
-    }
+    long long dnb = dnb_fast;
+    if (__any_sync(0xffffffffu, maybe)) dnb = pivot_exact_bits(maybe, screenable, c, g, tb, sdb, b1b, sp);
     if (lane == 0) {
         const double dn = __longlong_as_double(dnb);
         Dout[p] = dn;
@@ -149,7 +163,7 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
         const bool fin = (db & kAbsMask) < kInfBits && (dnb & kAbsMask) < kInfBits && (dnb & kAbsMask) != 0;
         if (!fin) atomicOr(&ctl->status, kStatNonFinite);
         piv_out[0] = dn;
-        piv_out[1] = exact ? 1.0 / dn : rinv_fast;
+        piv_out[1] = dnb == dnb_fast ? rinv_fast : recip_pivot(dn);
     }
 }
 
@@ -169,7 +183,7 @@ __device__ __forceinline__ double pivot_lanes(double c, double g, int sl, int p,
     const long long tb = gt_nonneg(sdb, b1b) ? sdb : b1b;
     const bool t_ok = tb > 0x000fffffffffffffll && tb < kInfBits;
     const bool take = lane > p && lane < w && sl == sp;
-    bool maybe = false;
+    bool maybe = false, screenable = false;
     if (take) {
         const long long jb = dbits(g);
         const long long ja = jb & kAbsMask;
@@ -177,7 +191,7 @@ __device__ __forceinline__ double pivot_lanes(double c, double g, int sl, int p,
         if (cand) {
             const long long ab = dbits(c) & kAbsMask;
             if (ab != 0) {
-                const bool screenable = t_ok && ab >= kTiny && ab < kHuge && ja > 0x000fffffffffffffll && ja < kInfBits;
+                screenable = t_ok && ab >= kTiny && ab < kHuge && ja > 0x000fffffffffffffll && ja < kInfBits;
                 maybe = !screenable || 2 * (ab - kBias) >= (ja - kBias) + (tb - kBias) - kScreen;
             }
         }
@@ -186,20 +200,8 @@ __device__ __forceinline__ double pivot_lanes(double c, double g, int sl, int p,
     double r = recip_pivot(__longlong_as_double(dnb_fast));
     long long dnb = dnb_fast;
     if (__any_sync(0xffffffffu, maybe)) {
-        double b2 = 0.0;
-        if (take && sp * g > 0.0) {
-            const double v = c * c / fabs(g);
-            if (v > b2) b2 = v;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, b2, o);
-            if (ov > b2) b2 = ov;
-        }
-        const double bnd = b1floor > b2 ? b1floor : b2;
-        const double sd = sp * d;
-        dnb = dbits(sp * (sd > bnd ? sd : bnd));
-        r = 1.0 / __longlong_as_double(dnb);
+        dnb = pivot_exact_bits(maybe, screenable, c, g, tb, sdb, b1b, sp);
+        if (dnb != dnb_fast) r = recip_pivot(__longlong_as_double(dnb));
     }
     const double dn = __longlong_as_double(dnb);
     if (lane == 0) {
@@ -313,27 +315,35 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
 }
 
 // -------------------------------------------------------------- large fronts
-// Assembly of columns [r0, r1) of front s into its slab in global memory:
+// The work on a large front is cut into items (Sec. 4.4: per pivot block of
+// nb = 32 columns, the diagonal block, the triangular solve of the rows below
+// it and the trailing update), each written once as a CTA-wide body (256
+// threads call it; bodies that need fewer leave the others idle).  The
+// bodies serve both the one-launch-per-step kernels and the persistent
+// level kernel below.  Front data are read through L2 (ld.global.cg)
+// because in the persistent kernel other CTAs of the same launch wrote
+// them.  All bodies share one shared-memory pool sized for the largest.
+constexpr int kBodyThreads = 256;
+constexpr int kPoolDoubles = 2 * 32 * 33;  // a 32 x 32 update tile's two operands
+
+// Assembly of columns [c_lo, c_hi) of front s into its slab in global memory:
 // zero the columns, place the original entries (a precomputed contiguous
 // range), then add the children's contribution-block columns that land in
 // the range (precomputed per child), children in ascending order.  Child
 // descriptors are staged in shared memory 64 at a time.
-__global__ void __launch_bounds__(256) k_large_assemble(DevPlan P, DevVals V, double *__restrict__ fronts,
-                                                         const PanelItem *__restrict__ items,
-                                                         const AsmItem *__restrict__ ainfo,
-                                                         const int32_t *__restrict__ acr) {
-    __shared__ int32_t ch_a[64], ch_b[64], ch_cc[64], ch_ldc[64];
-    __shared__ int64_t ch_cb[64], ch_map[64];
-    const PanelItem it = items[blockIdx.x];
-    const AsmItem ai = ainfo[blockIdx.x];
-    const int s = it.s, c_lo = it.r0, c_hi = it.r1;
+__device__ __forceinline__ void body_assemble(const DevPlan &P, const DevVals &V, double *__restrict__ fronts, int s,
+                                              int c_lo, int c_hi, const AsmItem &ai, const int32_t *__restrict__ acr,
+                                              double *pool) {
+    constexpr int NT = kBodyThreads;
+    int32_t *ch_a = reinterpret_cast<int32_t *>(pool), *ch_b = ch_a + 64, *ch_cc = ch_b + 64, *ch_ldc = ch_cc + 64;
+    int64_t *ch_cb = reinterpret_cast<int64_t *>(ch_ldc + 64), *ch_map = ch_cb + 64;
     const int ld = P.sn_ld[s];
     double *F = fronts + P.sn_off[s];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ncol = c_hi - c_lo;
-    for (int t = tid; t < ncol * ld; t += 256) F[(int64_t)c_lo * ld + t] = 0.0;
+    for (int t = tid; t < ncol * ld; t += NT) F[(int64_t)c_lo * ld + t] = 0.0;
     __syncthreads();
-    for (int64_t q = ai.o0 + tid; q < ai.o1; q += 256) F[P.orig_dst[q]] = orig_value(P, V, P.orig_src[q]);
+    for (int64_t q = ai.o0 + tid; q < ai.o1; q += NT) F[P.orig_dst[q]] = orig_value(P, V, P.orig_src[q]);
     const int q0 = P.child_ptr[s], nch = P.child_ptr[s + 1] - q0;
     for (int base = 0; base < nch; base += 64) {
         __syncthreads();
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(256) k_large_assemble(DevPlan P, DevVals V, do
             const int cc = ch_cc[u], ldc = ch_ldc[u];
             const double *CB = fronts + ch_cb[u];
             const int32_t *map = P.relmap + ch_map[u];
-            for (int jj = a + warp; jj < b; jj += 8) {
+            for (int jj = a + warp; jj < b; jj += NT / 32) {
                 const int pj = map[jj];
                 for (int ii = jj + lane; ii < cc; ii += 32) F[(int64_t)pj * ld + map[ii]] += CB[(int64_t)jj * ldc + ii];
             }
@@ -364,56 +374,59 @@ __global__ void __launch_bounds__(256) k_large_assemble(DevPlan P, DevVals V, do
     }
 }
 
-// Panel [p0, p1) of a large front, step 1: the nb x nb diagonal block,
-// one CTA per front, as a two-stage pipeline over the pivots.  Warp 0 owns
-// the pivot chain: for pivot p it applies pivot p-1 to column p, decides p
-// (pivot_lanes), scales the column (l_jp = F_jp / d_p, keeping the unscaled
-// w_jp = F_jp) and applies p to the diagonal entries it keeps in registers;
-// then it publishes p.  Warps 1-3 apply pivot p to the strictly lower
-// entries of columns >= p + 2 while warp 0 already works on pivot p + 1,
-// which needs only column p + 1 and the diagonal; each of their threads
-// holds up to five of these entries in registers for the whole panel.  Named barriers 1-2 (pivot published) and 3-4 (columns updated)
-// alternate by pivot parity, so neither side runs more than one pivot
-// ahead.  Every entry receives the updates of all earlier pivots in pivot
-// order, as in the sequential elimination.  The factorised block goes back
-// to the slab (L strictly below the diagonal, D on it) together with D and
-// the lifts, and the panel workspace of the front receives the rows of L_11
-// (row-major, ws[q * 33 + q'] = L_qq') and 1 / d_q for the triangular solve
-// of the rows below.
+// The nb x nb diagonal block of panel [p0, p0 + nb) of front s as a
+// two-stage pipeline over the pivots, on threads 0-127.  Warp 0 owns the
+// pivot chain: lane j keeps c = F_jp of the current pivot column, g = F_jj
+// and gs = F_jj + s_j sigma_j (the static term) up to date; per pivot it
+// decides (pivot_lanes), scales the column (l_jp = F_jp / d_p, keeping the
+// unscaled w_jp = F_jp), publishes p, and brings c, g and gs to pivot p + 1
+// with three independent FMAs.  Warps 1-3 apply pivot p to the strictly
+// lower entries of columns >= p + 2 while warp 0 already works on pivot
+// p + 1, which needs only column p + 1 and the diagonal; each of their
+// threads holds up to five of these entries in registers for the whole
+// block and stores one when its column has received its last update here.
+// Named barriers 1-2 (pivot published) and 3-4 (columns updated) alternate
+// by pivot parity, so neither side runs more than one pivot ahead.  Every
+// entry receives the updates of all earlier pivots in pivot order, as in the
+// sequential elimination.  The factorised block goes back to the slab (L
+// strictly below the diagonal, D on it) together with D, 1/D and the lifts,
+// and the panel workspace ws receives the rows of L_11 (row-major,
+// ws[q * 33 + q'] = L_qq') and 1 / d_q for the triangular solve below.
 constexpr int kPanelWs = 32 * 33 + 32;  // doubles of panel workspace per large front
 
-__global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double *__restrict__ fronts,
-                                                     double *__restrict__ Dg, double *__restrict__ Dig,
-                                                     double *__restrict__ dyng, DevCtl *ctl,
-                                                     const PanelItem *__restrict__ items, int p0, int nb,
-                                                     double *__restrict__ pws) {
-    __shared__ double Fd[32 * 33];
-    __shared__ double wsv[2][32];
-    __shared__ double Dtmp[32], dstat[32], rtmp[32];
-    __shared__ int8_t sg[32];
+__device__ __forceinline__ void body_diag(const DevPlan &P, const DevVals &V, double *__restrict__ fronts,
+                                          double *__restrict__ Dg, double *__restrict__ Dig,
+                                          double *__restrict__ dyng, DevCtl *ctl, int s, int p0, int nb,
+                                          double *__restrict__ ws, double *pool) {
     constexpr int LDD = 33, NT = 128, NU = NT - 32, kOwn = 5;  // 5 x 96 >= 435 entries
     constexpr int kBarPub = 1, kBarUpd = 3;
-    const PanelItem it = items[blockIdx.x];
-    const int s = it.s;
+    double *Fd = pool;                          // 32 x 33, column-major
+    double(*wsv)[32] = reinterpret_cast<double(*)[32]>(pool + 32 * 33);  // [2][32]
+    double *Dtmp = pool + 32 * 33 + 64, *dstat = Dtmp + 32, *rtmp = dstat + 32;
+    int8_t *sg = reinterpret_cast<int8_t *>(rtmp + 32);
     const int k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
     const int w = min(p0 + nb, k) - p0;
-    if (w <= 0) return;
+    if (w <= 0) return;  // uniform over the CTA
     double *F = fronts + P.sn_off[s];
-    double *ws = pws + (int64_t)it.r1 * kPanelWs;  // r1 carries the workspace slot
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    {
+        // all loads in flight before the shared-memory stores
+        constexpr int U = 32 * 32 / kBodyThreads;
+        double v[U];
 #pragma unroll
-    for (int u = 0; u < 1024 / NT; u++) {
-        const int t = tid + u * NT;
-        const int jj = t >> 5, ii = t & 31;
-        Fd[jj * LDD + ii] = (jj < w && ii < w && ii >= jj) ? F[(int64_t)(p0 + jj) * ld + (p0 + ii)] : 0.0;
+        for (int u = 0; u < U; u++) {
+            const int t = tid + u * kBodyThreads, jj = t >> 5, ii = t & 31;
+            v[u] = (jj < w && ii < w && ii >= jj) ? __ldcg(F + (int64_t)(p0 + jj) * ld + (p0 + ii)) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int t = tid + u * kBodyThreads;
+            Fd[(t >> 5) * LDD + (t & 31)] = v[u];
+        }
     }
     if (tid < 32) sg[tid] = tid < w ? P.sign[c0 + p0 + tid] : (int8_t)0;
     __syncthreads();
     if (warp == 0) {
-        // lane j keeps c = F_jp of the current pivot column, g = F_jj and
-        // gs = F_jj + s_j sigma_j (the static term) up to date; per pivot the
-        // chain is the reciprocal, the scaling l = c / d and three
-        // independent FMAs that bring c, g and gs to the next pivot
         const double b1floor = pivot_floor(P, ctl, c0);
         const int sl = sg[lane];
         double g = lane < w ? Fd[lane * LDD + lane] : 0.0;   // F_jj of row j = lane
@@ -439,19 +452,17 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
             if (p + 1 < w) {
                 if (p >= 1) bar_sync_parity<kBarUpd>(p + 1);  // pivot p-1 applied to columns >= p+1
                 const double wn = __shfl_sync(0xffffffffu, c, p + 1);  // w_{p+1,p}, unscaled
-                const double f = (lane > p + 1 && lane < w) ? Fd[(p + 1) * LDD + lane] : 0.0;
-                const double cn = f - l * wn;
+                const double fv = (lane > p + 1 && lane < w) ? Fd[(p + 1) * LDD + lane] : 0.0;
+                const double cn = fv - l * wn;
                 g -= l * c;
                 gs -= l * c;
                 c = lane > p + 1 ? cn : 0.0;
             }
         }
-    } else {
+    } else if (warp < NT / 32) {
         // this thread owns the strictly lower entries e = ut + 96 t of columns
         // >= 2, enumerated last column first: e = r (r + 1) / 2 + c  ->
-        // column w-2-r, row w-1-r+c (0 <= c <= r); it keeps them in registers
-        // and stores an entry when its column has received its last update
-        // here (pivot column - 2)
+        // column w-2-r, row w-1-r+c (0 <= c <= r)
         const int ut = tid - 32;
         const int nall = w >= 3 ? (w - 3) * (w - 2) / 2 : 0;
         int jo[kOwn], io[kOwn];
@@ -493,13 +504,14 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
         }
     }
     __syncthreads();
-    for (int t = tid; t < 32 * 32; t += NT) {
+    for (int t = tid; t < 32 * 32; t += kBodyThreads) {
         const int jj = t >> 5, ii = t & 31;
         const bool in = jj < w && ii < w;
         if (in && ii >= jj) F[(int64_t)(p0 + jj) * ld + (p0 + ii)] = Fd[jj * LDD + ii];
         ws[ii * 33 + jj] = (in && ii > jj) ? Fd[jj * LDD + ii] : 0.0;  // L(row ii, column jj), row-major
     }
-    for (int t = tid; t < 32; t += NT) {
+    if (tid < 32) {
+        const int t = tid;
         ws[32 * 33 + t] = t < w ? rtmp[t] : 0.0;
         if (t < w) {
             const double dn = Dtmp[t], d = dstat[t];
@@ -510,33 +522,43 @@ __global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevVals V, double
     }
 }
 
-// Panel step 2: rows [r0, r1) below the diagonal block, one warp per row
-// with one lane per pivot column q.  With u_iq = l_iq d_q the rows satisfy
+// Rows [r0, r1) below the diagonal block of panel [p0, p0 + nb), one warp
+// per row with one lane per pivot column q.  With u_iq = l_iq d_q the rows
+// satisfy
 //   u_iq = F_iq - sum_{q' < q} u_iq' L_qq',   l_iq = u_iq / d_q,
 // so step q' broadcasts the finished u_iq' and every lane q > q' applies one
 // FMA: 32 dependent steps per row instead of 528 per thread when a thread
 // owns a whole row.
 constexpr int kTrsmRows = 8;
 static_assert(kTrsmRows == kTrsmRowsHost, "host and device row chunks differ");
+static_assert(32 * kTrsmRows == kBodyThreads, "one warp per row");
 
-__global__ void __launch_bounds__(32 * kTrsmRows) k_panel_trsm(DevPlan P, double *__restrict__ fronts,
-                                                                const PanelItem *__restrict__ items,
-                                                                const int32_t *slots, int p0, int nb,
-                                                                const double *__restrict__ pws) {
-    __shared__ double Wd[32 * 33 + 32];
-    __shared__ double T[32][kTrsmRows + 1];
-    const PanelItem it = items[blockIdx.x];
-    const int s = it.s;
+__device__ __forceinline__ void body_trsm(const DevPlan &P, double *__restrict__ fronts, int s, int r0, int r1,
+                                          int p0, int nb, const double *__restrict__ ws, double *pool) {
+    double *Wd = pool;                                                     // 32 x 33 + 32
+    double(*T)[kTrsmRows + 1] = reinterpret_cast<double(*)[kTrsmRows + 1]>(pool + 32 * 33 + 32);  // [32][9]
     const int k = P.sn_k[s], ld = P.sn_ld[s];
     const int w = min(p0 + nb, k) - p0;
-    const int nr = it.r1 - it.r0;
+    const int nr = r1 - r0;
     double *F = fronts + P.sn_off[s];
-    const double *ws = pws + (int64_t)slots[blockIdx.x] * kPanelWs;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int t = tid; t < 32 * 33 + 32; t += 32 * kTrsmRows) Wd[t] = ws[t];
     {
+        // all loads in flight before the shared-memory stores
+        constexpr int U = (32 * 33 + 32 + kBodyThreads - 1) / kBodyThreads;
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int t = tid + u * kBodyThreads;
+            v[u] = t < 32 * 33 + 32 ? __ldcg(ws + t) : 0.0;
+        }
         const int q = tid / kTrsmRows, r = tid % kTrsmRows;
-        T[q][r] = (q < w && r < nr) ? F[(int64_t)(p0 + q) * ld + it.r0 + r] : 0.0;
+        const double tv = (q < w && r < nr) ? __ldcg(F + (int64_t)(p0 + q) * ld + r0 + r) : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int t = tid + u * kBodyThreads;
+            if (t < 32 * 33 + 32) Wd[t] = v[u];
+        }
+        T[q][r] = tv;
     }
     __syncthreads();
     if (warp < nr) {
@@ -554,35 +576,48 @@ __global__ void __launch_bounds__(32 * kTrsmRows) k_panel_trsm(DevPlan P, double
     __syncthreads();
     {
         const int q = tid / kTrsmRows, r = tid % kTrsmRows;
-        if (q < w && r < nr) F[(int64_t)(p0 + q) * ld + it.r0 + r] = T[q][r];
+        if (q < w && r < nr) F[(int64_t)(p0 + q) * ld + r0 + r] = T[q][r];
     }
 }
 
 // Trailing update of the lower part of columns [p1, f) by the panel
 // [p0, p0+w): C(i, j) -= sum_q L(i,q) d_q L(j,q), one kUpdTile x kUpdTile
-// tile per CTA.  FP64 runs at ~6.6 GFLOP/s per SM on this part, so tiles are
-// small (32 x 32) to put every SM to work on each launch.
-__global__ void __launch_bounds__(256) k_large_update(DevPlan P, double *__restrict__ fronts,
-                                                      const double *__restrict__ Dg,
-                                                      const TileItem *__restrict__ items, int p0, int w) {
+// tile at (i0, j0), 16 x 16 threads with 2 x 2 outputs each.  FP64 runs at
+// about 2 FMA per clock per SM on this GPU, so tiles are small (32 x 32) to
+// put every SM to work.
+__device__ __forceinline__ void body_tile(const DevPlan &P, double *__restrict__ fronts,
+                                          const double *__restrict__ Dg, int s, int i0, int j0, int p0, int w,
+                                          double *pool) {
     constexpr int T = kUpdTile;
-    __shared__ double As[32][T + 1];
-    __shared__ double Bs[32][T + 1];
-    const TileItem it = items[blockIdx.x];
-    const int s = it.s;
+    static_assert(T == 32, "16 x 16 threads, 2 x 2 outputs");
+    double(*As)[T + 1] = reinterpret_cast<double(*)[T + 1]>(pool);
+    double(*Bs)[T + 1] = reinterpret_cast<double(*)[T + 1]>(pool + 32 * (T + 1));
     const int f = P.sn_f[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
     w = min(w, P.sn_k[s] - p0);  // ragged last panel
     double *F = fronts + P.sn_off[s];
     const int tid = threadIdx.x;
-    for (int t = tid; t < 32 * T; t += 256) {
-        const int q = t / T, r = t % T;
-        const int i = it.i0 + r, j = it.j0 + r;
-        const bool qa = q < w;
-        As[q][r] = (qa && i < f) ? F[(int64_t)(p0 + q) * ld + i] : 0.0;
-        Bs[q][r] = (qa && j < f) ? F[(int64_t)(p0 + q) * ld + j] * Dg[c0 + p0 + q] : 0.0;
+    {
+        // all loads in flight before the shared-memory stores
+        constexpr int U = 32 * T / kBodyThreads;
+        double va[U], vb[U], vd[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int t = tid + u * kBodyThreads, q = t / T, r = t % T;
+            const int i = i0 + r, j = j0 + r;
+            const bool qa = q < w;
+            va[u] = (qa && i < f) ? __ldcg(F + (int64_t)(p0 + q) * ld + i) : 0.0;
+            vb[u] = (qa && j < f) ? __ldcg(F + (int64_t)(p0 + q) * ld + j) : 0.0;
+            vd[u] = qa ? __ldcg(Dg + c0 + p0 + q) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int t = tid + u * kBodyThreads, q = t / T, r = t % T;
+            As[q][r] = va[u];
+            Bs[q][r] = vb[u] * vd[u];
+        }
     }
     __syncthreads();
-    const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads, 2 x 2 outputs each
+    const int tx = tid & 15, ty = tid >> 4;
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
     for (int q = 0; q < w; q++) {
         const double a0 = As[q][tx], a1 = As[q][tx + 16];
@@ -594,53 +629,187 @@ __global__ void __launch_bounds__(256) k_large_update(DevPlan P, double *__restr
     }
 #pragma unroll
     for (int b = 0; b < 2; b++) {
-        const int j = it.j0 + ty + 16 * b;
-        if (j >= f) continue;
+        const int j = j0 + ty + 16 * b;
+        if (j >= f || j < p0 + w) continue;  // a grid tile cut by a partial last panel
 #pragma unroll
         for (int a = 0; a < 2; a++) {
-            const int i = it.i0 + tx + 16 * a;
-            if (i < f && i >= j) F[(int64_t)j * ld + i] -= acc[a][b];
+            const int i = i0 + tx + 16 * a;
+            if (i < f && i >= j) {
+                double *e = F + (int64_t)j * ld + i;
+                *e = __ldcg(e) - acc[a][b];
+            }
         }
     }
 }
 
 // The same update for the next panel's columns, which lie on the critical
-// path: strips of kUpdTile rows x kStripCols columns, one output per thread,
-// summed over the panel's pivots in the same order as k_large_update (so
-// the results are identical).  A whole 32 x 32 tile is 32k FP64 FMAs, about
-// 8 us on one SM of this GPU; the strips spread those few tiles over eight
-// times as many SMs.
-__global__ void __launch_bounds__(32 * kStripCols) k_large_update_strip(DevPlan P, double *__restrict__ fronts,
-                                                                        const double *__restrict__ Dg,
-                                                                        const TileItem *__restrict__ items, int p0,
-                                                                        int w) {
-    constexpr int T = kUpdTile, C = kStripCols, NT = 32 * kStripCols;
-    static_assert(T == 32, "one row per lane");
-    __shared__ double As[32][T + 1];
-    __shared__ double Bs[32][C];
-    const TileItem it = items[blockIdx.x];
-    const int s = it.s;
+// path: a strip of kUpdTile rows x kStripCols columns at (i0, j0), one
+// output per thread on threads 0..32 kStripCols - 1, summed over the panel's
+// pivots in the same order as body_tile (so the results are identical).  A
+// whole 32 x 32 tile is 32k FP64 FMAs, about 8 us on one SM of this GPU;
+// strips spread those few tiles over eight times as many SMs.
+__device__ __forceinline__ void body_strip(const DevPlan &P, double *__restrict__ fronts,
+                                           const double *__restrict__ Dg, int s, int i0, int j0, int p0, int w,
+                                           double *pool) {
+    constexpr int T = kUpdTile, C = kStripCols;
+    static_assert(T == 32 && 32 * C <= kBodyThreads, "one row per lane, one column per warp");
+    double(*As)[T + 1] = reinterpret_cast<double(*)[T + 1]>(pool);
+    double(*Bs)[C] = reinterpret_cast<double(*)[C]>(pool + 32 * (T + 1));
     const int f = P.sn_f[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
-    w = min(w, P.sn_k[s] - p0);  // ragged last panel
-    const double *Fc = fronts + P.sn_off[s];
+    w = min(w, P.sn_k[s] - p0);
+    double *F = fronts + P.sn_off[s];
     const int tid = threadIdx.x;
-    for (int t = tid; t < 32 * T; t += NT) {
-        const int q = t / T, r = t % T;
-        const int i = it.i0 + r;
-        As[q][r] = (q < w && i < f) ? Fc[(int64_t)(p0 + q) * ld + i] : 0.0;
-    }
     {
-        const int q = tid / C, cc = tid % C;  // NT == 32 * C: one entry each
-        const int j = it.j0 + cc;
-        Bs[q][cc] = (q < w && j < f) ? Fc[(int64_t)(p0 + q) * ld + j] * Dg[c0 + p0 + q] : 0.0;
+        // all loads in flight before the shared-memory stores
+        constexpr int U = 32 * T / kBodyThreads;
+        double va[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int t = tid + u * kBodyThreads, q = t / T, r = t % T;
+            va[u] = (q < w && i0 + r < f) ? __ldcg(F + (int64_t)(p0 + q) * ld + i0 + r) : 0.0;
+        }
+        double vb = 0.0, vd = 0.0;
+        const int q = tid / C, cc = tid % C, j = j0 + cc;
+        if (tid < 32 * C && q < w && j < f) {
+            vb = __ldcg(F + (int64_t)(p0 + q) * ld + j);
+            vd = __ldcg(Dg + c0 + p0 + q);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int t = tid + u * kBodyThreads;
+            As[t / T][t % T] = va[u];
+        }
+        if (tid < 32 * C) Bs[q][cc] = vb * vd;
     }
     __syncthreads();
     const int r = tid & 31, cc = tid >> 5;
-    const int i = it.i0 + r, j = it.j0 + cc;
-    if (i < f && j < f && i >= j) {
+    const int i = i0 + r, j = j0 + cc;
+    if (cc < C && i < f && j < f && i >= j && j >= p0 + w) {
         double acc = 0.0;
         for (int q = 0; q < w; q++) acc += As[q][r] * Bs[q][cc];
-        fronts[P.sn_off[s] + (int64_t)j * ld + i] -= acc;
+        double *e = F + (int64_t)j * ld + i;
+        *e = __ldcg(e) - acc;
+    }
+}
+
+// One launch per step: one item per CTA.
+__global__ void __launch_bounds__(kBodyThreads) k_large_assemble(DevPlan P, DevVals V, double *__restrict__ fronts,
+                                                                  const PanelItem *__restrict__ items,
+                                                                  const AsmItem *__restrict__ ainfo,
+                                                                  const int32_t *__restrict__ acr) {
+    __shared__ double pool[kPoolDoubles];
+    const PanelItem it = items[blockIdx.x];
+    body_assemble(P, V, fronts, it.s, it.r0, it.r1, ainfo[blockIdx.x], acr, pool);
+}
+
+__global__ void __launch_bounds__(kBodyThreads) k_panel_diag(DevPlan P, DevVals V, double *__restrict__ fronts,
+                                                              double *__restrict__ Dg, double *__restrict__ Dig,
+                                                              double *__restrict__ dyng, DevCtl *ctl,
+                                                              const PanelItem *__restrict__ items, int p0, int nb,
+                                                              double *__restrict__ pws) {
+    __shared__ double pool[kPoolDoubles];
+    const PanelItem it = items[blockIdx.x];
+    body_diag(P, V, fronts, Dg, Dig, dyng, ctl, it.s, p0, nb, pws + (int64_t)it.r1 * kPanelWs, pool);
+}
+
+__global__ void __launch_bounds__(kBodyThreads) k_panel_trsm(DevPlan P, double *__restrict__ fronts,
+                                                              const PanelItem *__restrict__ items,
+                                                              const int32_t *slots, int p0, int nb,
+                                                              const double *__restrict__ pws) {
+    __shared__ double pool[kPoolDoubles];
+    const PanelItem it = items[blockIdx.x];
+    body_trsm(P, fronts, it.s, it.r0, it.r1, p0, nb, pws + (int64_t)slots[blockIdx.x] * kPanelWs, pool);
+}
+
+__global__ void __launch_bounds__(kBodyThreads) k_large_update(DevPlan P, double *__restrict__ fronts,
+                                                                const double *__restrict__ Dg,
+                                                                const TileItem *__restrict__ items, int p0, int w) {
+    __shared__ double pool[kPoolDoubles];
+    const TileItem it = items[blockIdx.x];
+    body_tile(P, fronts, Dg, it.s, it.i0, it.j0, p0, w, pool);
+}
+
+__global__ void __launch_bounds__(kBodyThreads) k_large_update_strip(DevPlan P, double *__restrict__ fronts,
+                                                                        const double *__restrict__ Dg,
+                                                                        const TileItem *__restrict__ items, int p0,
+                                                                        int w) {
+    __shared__ double pool[kPoolDoubles];
+    const TileItem it = items[blockIdx.x];
+    body_strip(P, fronts, Dg, it.s, it.i0, it.j0, p0, w, pool);
+}
+
+// Persistent level kernel: all large-front items of one tree level in one
+// launch.  CTAs take tickets in the host's order, wait (thread 0, bounded
+// spin on acquire loads) until the item's counters reach their thresholds,
+// run the item's body, and add the item's increment to its completion
+// counter (release: every thread fences its writes before the barrier).
+// Every item waits only on items with smaller tickets, which were taken by
+// running CTAs, so the launch completes whatever the grid size.  A wait
+// that runs out sets kStatTimeout and the item proceeds (its results are
+// then wrong, but the launch still ends).
+__device__ __forceinline__ int ld_acquire_i32(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Once some wait of the launch has given up, the others stop at their next
+// check of the status word, so a failed launch ends after one wait limit.
+__device__ __forceinline__ void wait_counter(const int32_t *cnt, int need, DevCtl *ctl, long long limit) {
+    long long spins = 0;
+    while (ld_acquire_i32(cnt) < need) {
+        if (++spins > limit) {
+            atomicOr(&ctl->status, kStatTimeout);
+            break;
+        }
+        if ((spins & 1023) == 0 && (*(volatile int32_t *)&ctl->status & kStatTimeout)) break;
+        __nanosleep(64);
+    }
+}
+
+__global__ void __launch_bounds__(kBodyThreads) k_large_level(DevPlan P, DevVals V, double *__restrict__ fronts,
+                                                               double *__restrict__ Dg, double *__restrict__ Dig,
+                                                               double *__restrict__ dyng, DevCtl *ctl,
+                                                               const FactorItem *__restrict__ items, int nitems,
+                                                               int32_t *sync, const AsmItem *__restrict__ ainfo,
+                                                               const int32_t *__restrict__ acr,
+                                                               double *__restrict__ pws, int nb, long long limit) {
+    __shared__ double pool[kPoolDoubles];
+    __shared__ FactorItem sh_it;
+    int32_t *cnt = sync + 1;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            const int t = atomicAdd(sync, 1);
+            FactorItem a;
+            a.kind = -1;
+            if (t < nitems) a = items[t];
+            sh_it = a;
+        }
+        __syncthreads();
+        const FactorItem it = sh_it;
+        __syncthreads();
+        if (it.kind < 0) break;
+        if (tid == 0) {
+            if (it.wait0 >= 0) wait_counter(cnt + it.wait0, it.need0, ctl, limit);
+            if (it.wait1 >= 0) wait_counter(cnt + it.wait1, it.need1, ctl, limit);
+        }
+        __syncthreads();
+        switch (it.kind) {
+            case kItemAssemble: body_assemble(P, V, fronts, it.s, it.a, it.b, ainfo[it.aux], acr, pool); break;
+            case kItemDiag:
+                body_diag(P, V, fronts, Dg, Dig, dyng, ctl, it.s, it.t * nb, nb, pws + (int64_t)it.aux * kPanelWs,
+                          pool);
+                break;
+            case kItemTrsm:
+                body_trsm(P, fronts, it.s, it.a, it.b, it.t * nb, nb, pws + (int64_t)it.aux * kPanelWs, pool);
+                break;
+            case kItemStrip: body_strip(P, fronts, Dg, it.s, it.a, it.b, it.t * nb, nb, pool); break;
+            default: body_tile(P, fronts, Dg, it.s, it.a, it.b, it.t * nb, nb, pool); break;
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0 && it.sig >= 0) atomicAdd(cnt + it.sig, it.add);
     }
 }
 
@@ -733,33 +902,45 @@ void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, dou
 void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, const PanelItem *items,
                            const AsmItem *ainfo, const int32_t *acr, int32_t count, cudaStream_t st) {
     if (count <= 0) return;
-    k_large_assemble<<<count, 256, 0, st>>>(P, V, fronts, items, ainfo, acr);
+    k_large_assemble<<<count, kBodyThreads, 0, st>>>(P, V, fronts, items, ainfo, acr);
 }
 
 void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
                        DevCtl *ctl,
                        const PanelItem *items, int32_t count, int32_t p0, int32_t nb, double *pws, cudaStream_t st) {
     if (count <= 0) return;
-    k_panel_diag<<<count, 128, 0, st>>>(P, V, fronts, D, Dinv, dyn, ctl, items, p0, nb, pws);
+    k_panel_diag<<<count, kBodyThreads, 0, st>>>(P, V, fronts, D, Dinv, dyn, ctl, items, p0, nb, pws);
 }
 
 void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,
                        int32_t p0, int32_t nb, const double *pws, cudaStream_t st) {
     if (count <= 0) return;
-    k_panel_trsm<<<count, 32 * kTrsmRows, 0, st>>>(P, fronts, items, slots, p0, nb, pws);
+    k_panel_trsm<<<count, kBodyThreads, 0, st>>>(P, fronts, items, slots, p0, nb, pws);
 }
 
 void launch_large_update(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
                          int32_t p0, int32_t w, cudaStream_t st) {
     if (count <= 0) return;
-    k_large_update<<<count, 256, 0, st>>>(P, fronts, D, items, p0, w);
+    k_large_update<<<count, kBodyThreads, 0, st>>>(P, fronts, D, items, p0, w);
 }
 
 void launch_large_update_strip(const DevPlan &P, double *fronts, const double *D, const TileItem *items,
                                int32_t count, int32_t p0, int32_t w, cudaStream_t st) {
     if (count <= 0) return;
-    k_large_update_strip<<<count, 32 * kStripCols, 0, st>>>(P, fronts, D, items, p0, w);
+    k_large_update_strip<<<count, kBodyThreads, 0, st>>>(P, fronts, D, items, p0, w);
 }
+
+void launch_large_level(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
+                        DevCtl *ctl, const FactorItem *items, int32_t count, int32_t *sync, int32_t ncounters,
+                        const AsmItem *ainfo, const int32_t *acr, double *pws, int32_t nb, int32_t grid,
+                        long long spin_limit, cudaStream_t st) {
+    if (count <= 0) return;
+    cudaMemsetAsync(sync, 0, sizeof(int32_t) * (size_t)(ncounters + 1), st);
+    k_large_level<<<grid < count ? grid : count, kBodyThreads, 0, st>>>(P, V, fronts, D, Dinv, dyn, ctl, items, count,
+                                                                        sync, ainfo, acr, pws, nb, spin_limit);
+}
+
+const void *large_level_kernel() { return reinterpret_cast<const void *>(k_large_level); }
 
 void launch_norm1(const DevPlan &P, const DevVals &V, DevCtl *ctl, double eps_piv, cudaStream_t st) {
     const int grid = (P.N + 255) / 256 < 608 ? (P.N + 255) / 256 : 608;

@@ -450,9 +450,9 @@ def test_dependency_wait_timeout_reports_status(pkg):
     lp = synth.grid_multicommodity(12, 3)
     theta = synth.theta_loguniform(lp.n, 31)
     r7, r1 = synth.rhs_normal(lp.n, 31), synth.rhs_normal(lp.m, 32)
-    s = pkg.Solver.from_lp(lp, spin_limit_log2=-1, refine_max=0, gmres_restarts=0)
+    s = pkg.Solver.from_lp(lp, spin_limit_log2=-1, refine_max=0, gmres_restarts=0, level_kernel=0)
     s.factorise(theta, RHO, DELTA)
-    assert s.status() >= 0  # the factorisation has no dependency waits
+    assert s.status() >= 0  # one launch per step: the factorisation has no dependency waits
     s.solve(r7, r1)
     assert s.info()["status"] & 8, "timeout bit not set"
     assert s.status() in (pkg.IPM_ERR_DEVICE_TIMEOUT, pkg.IPM_ERR_NONFINITE)
@@ -487,3 +487,48 @@ def test_loaded_analysis_factorises_identically(pkg, tmp_path):
     assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][2], outs[1][2])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("grid,order", [(16, "ND"), (24, "ND"), (24, "AMD")])
+def test_level_kernel_matches_per_step_launches(pkg, grid, order):
+    """The persistent level kernel (one dependency-driven launch per tree
+    level) applies the same arithmetic to every entry in the same order as
+    the one-launch-per-step path: the factors agree bit for bit, and so do
+    the refined solutions."""
+    lp = synth.grid_multicommodity(grid, 4)
+    theta = synth.theta_loguniform(lp.n, 61)
+    r7, r1 = synth.rhs_normal(lp.n, 61), synth.rhs_normal(lp.m, 62)
+    ordering = pkg.IPM_ORD_ND if order == "ND" else pkg.IPM_ORD_AMD
+    out = []
+    for lk in (1, 0):
+        s = pkg.Solver.from_lp(lp, ordering=ordering, level_kernel=lk)
+        assert s.info()["nfronts_large"] > 0
+        s.factorise(theta, RHO, DELTA)
+        dx, dy = s.solve(r7, r1)
+        assert s.status() >= 0
+        L, D, dyn = s.factor()
+        out.append((L, D, dyn, dx.cpu().numpy(), dy.cpu().numpy(), s.info()["omega"]))
+        s.close()
+    for a, b in zip(out[0][:5], out[1][:5]):
+        assert np.array_equal(a, b)
+    assert out[0][5] <= 1e-12
+
+
+def test_level_kernel_wait_timeout_reports_status(pkg):
+    """Every dependency wait of the level kernel gives up at its first poll
+    (forced): the launch still ends, the status word carries the timeout
+    bit, and a context with the normal limit factorises correctly after."""
+    lp = synth.grid_multicommodity(16, 4)
+    theta = synth.theta_loguniform(lp.n, 71)
+    r7, r1 = synth.rhs_normal(lp.n, 71), synth.rhs_normal(lp.m, 72)
+    s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND, spin_limit_log2=-1, refine_max=0, gmres_restarts=0)
+    assert s.info()["nfronts_large"] > 0
+    s.factorise(theta, RHO, DELTA)
+    assert s.info()["status"] & 8, "timeout bit not set"
+    assert s.status() in (pkg.IPM_ERR_DEVICE_TIMEOUT, pkg.IPM_ERR_NONFINITE)
+    s.close()
+    s2 = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND)
+    s2.factorise(theta, RHO, DELTA)
+    s2.solve(r7, r1)
+    assert s2.status() >= 0 and s2.info()["omega"] <= 1e-12
+    s2.close()
