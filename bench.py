@@ -494,7 +494,10 @@ def main():
         "vs_baseline": None,
         "dtype": "f64+tf32" if per[best]["tensor_cores_in_use"] else "f64",
         "data": "synthetic",
-        "config": {"workload": W.desc, "path": best,
+        "config": {"workload": W.desc, "path": best, "omega_target": per[best]["omega_target"],
+                   "factors": ("FP64 pivots, tensor-core Schur updates" if per[best]["tensor_cores_in_use"] else
+                               "FP64 throughout" + (" (the mixed path fell back to FP64 factors)"
+                                                    if per[best]["precision_fallbacks"] else "")),
                    "l2": "flushed between timed steps (256 MiB write outside the step events)",
                    "parallelism": (f"batch sharded over {world} GPUs (no collective)" if W.lps is not None
                                    else f"replicas x{world}") if world > 1 else "1 GPU"},

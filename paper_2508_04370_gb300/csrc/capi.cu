@@ -492,20 +492,46 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
     std::vector<int32_t> of(fwd_order), ob(bwd_order);
     std::stable_sort(of.begin(), of.end(), [&](int32_t a, int32_t b) { return up[a] > up[b]; });
     std::stable_sort(ob.begin(), ob.end(), [&](int32_t a, int32_t b) { return down[a] > down[b]; });
+    // Childless single-item supernodes with f <= 32 run one per warp, eight
+    // to a ticket.  A forward group takes the place of its first member (a
+    // leaf waits on nothing); a backward group the place of its last member
+    // (so every member's parent has an earlier ticket).
+    std::vector<char> is_leaf(ns, 0);
+    for (int32_t s = 0; s < ns; s++)
+        is_leaf[s] = nodes[s].nchild == 0 && nodes[s].nblk == 1 && nodes[s].nrect == 0 && nodes[s].f <= 32;
     std::vector<SolveItem> fwd, bwd;
+    std::vector<int32_t> fleaf, bleaf;
     for (int32_t s : of) {
+        if (is_leaf[s]) {
+            if (fleaf.size() % 8 == 0) fwd.push_back({(int32_t)(fleaf.size() / 8), kLeafGroup});
+            fleaf.push_back(s);
+            continue;
+        }
         for (int32_t b = 0; b < nodes[s].nblk; b++) fwd.push_back({s, -1 - b});
         for (int32_t r = 0; r < nodes[s].nrect; r++) fwd.push_back({s, r});
     }
-    for (int32_t s : ob)
+    while (fleaf.size() % 8) fleaf.push_back(-1);
+    for (int32_t s : ob) {
+        if (is_leaf[s]) {
+            bleaf.push_back(s);
+            if (bleaf.size() % 8 == 0) bwd.push_back({(int32_t)(bleaf.size() / 8 - 1), kLeafGroup});
+            continue;
+        }
         for (int32_t b = nodes[s].nblk - 1; b >= 0; b--) bwd.push_back({s, -1 - b});
+    }
+    if (bleaf.size() % 8) {
+        bwd.push_back({(int32_t)(bleaf.size() / 8), kLeafGroup});
+        while (bleaf.size() % 8) bleaf.push_back(-1);
+    }
     SolveNode *d_nodes;
     int64_t *d_grp, *d_gsrc;
     SolveItem *d_fwd, *d_bwd;
     double *d_yv;
+    int32_t *d_fleaf, *d_bleaf;
     int rc;
     if ((rc = dupload(c, &d_nodes, nodes)) || (rc = dupload(c, &d_grp, grp)) || (rc = dupload(c, &d_gsrc, gsrc)) ||
-        (rc = dupload(c, &d_fwd, fwd)) || (rc = dupload(c, &d_bwd, bwd)) || (rc = dalloc(c, &d_yv, (size_t)P.N)))
+        (rc = dupload(c, &d_fwd, fwd)) || (rc = dupload(c, &d_bwd, bwd)) || (rc = dalloc(c, &d_yv, (size_t)P.N)) ||
+        (rc = dupload(c, &d_fleaf, fleaf)) || (rc = dupload(c, &d_bleaf, bleaf)))
         return rc;
     SolveSched &S = c->sched;
     S.node = d_nodes;
@@ -520,6 +546,8 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
     S.nsuper = ns;
     S.sync = c->solve_sync;
     S.yv = d_yv;
+    S.fwd_leaf = d_fleaf;
+    S.bwd_leaf = d_bleaf;
     return IPM_OK;
 }
 

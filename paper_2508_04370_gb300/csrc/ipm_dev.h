@@ -1,6 +1,7 @@
 // Device-side view of the analysis plan and kernel entry points of the
 // multifrontal factorise/solve (Zanetti & Gondzio, arXiv 2508.04370, Sec. 4).
 #pragma once
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -128,7 +129,10 @@ struct SolveSched {
     long long spin_limit;    // polls before a dependency wait gives up (kStatTimeout)
     int32_t *sync;           // ticket + 3 x nsuper counters (forward), ticket + 2 x nsuper (backward)
     double *yv;              // forward: y of split supernodes (before D^-1)
+    const int32_t *fwd_leaf, *bwd_leaf;  // leaf groups: 8 childless single-item supernodes with f <= 32
+                                         // per ticket (-1 pads), one warp each
 };
+constexpr int32_t kLeafGroup = INT32_MIN;  // SolveItem.r of a leaf group (s = group index)
 constexpr int kRectRows = 32;
 constexpr int64_t kRectSplit = 8192;  // split when k (f - k) reaches this
 

@@ -175,13 +175,13 @@ __device__ __forceinline__ bool next_item(const SolveSched &S, const SolveItem *
         SolveItem a{-1, -1};
         if (t < nitems) {
             a = items[t];
-            *sh_nd = S.node[a.s];
+            if (a.r != kLeafGroup) *sh_nd = S.node[a.s];
         }
         *sh_it = a;
     }
     __syncthreads();
     it = *sh_it;
-    if (it.s >= 0) nd = *sh_nd;
+    if (it.s >= 0 && it.r != kLeafGroup) nd = *sh_nd;
     __syncthreads();
     return it.s >= 0;
 }
@@ -240,6 +240,67 @@ __device__ __forceinline__ void diag_backward(const double *Lb, double *z, int w
     if (lane < w) z[lane] = zi;
 }
 
+// Leaves of the elimination tree with one block and f <= 32 (most of the
+// supernodes of a nested-dissection or AMD tree) are processed one per
+// warp, eight to a ticket (a leaf group), lane i = front row i.  Each
+// computes what the single-item path below computes, in the same order of
+// operations.
+__device__ __forceinline__ void leaf_forward(const SolveSched &S, int s, const double *__restrict__ fronts,
+                                             const double *__restrict__ Dinv, double *__restrict__ x, double *upd,
+                                             int32_t *cnt) {
+    const int lane = threadIdx.x & 31;
+    const SolveNode nd = S.node[s];
+    const double *L = fronts + nd.off;
+    const int f = nd.f, k = nd.k, ld = nd.ld, c0 = nd.c0;
+    double v = lane < k ? x[c0 + lane] : 0.0;
+    const double dinv = lane < k ? Dinv[c0 + lane] : 0.0;
+    double acc = 0.0;  // rows below the block: sum_j L_ij y_j, subtracted at the end
+    for (int j = 0; j < k; j++) {
+        const double yj = __shfl_sync(0xffffffffu, v, j);
+        const double l = (lane > j && lane < f) ? L[(int64_t)j * ld + lane] : 0.0;
+        if (lane < k) v -= l * yj;
+        else acc += l * yj;
+    }
+    if (lane < k) x[c0 + lane] = v * dinv;
+    else if (lane < f) __stcg(upd + nd.upd + (lane - k), v - acc);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0 && nd.parent >= 0) atomicAdd(&cnt[nd.parent], 1);
+}
+
+__device__ __forceinline__ void leaf_backward(const SolveSched &S, int s, const double *__restrict__ fronts,
+                                              double *x, const int32_t *flag, DevCtl *ctl) {
+    const int lane = threadIdx.x & 31;
+    const SolveNode nd = S.node[s];
+    const double *L = fronts + nd.off;
+    const int f = nd.f, k = nd.k, ld = nd.ld, c0 = nd.c0;
+    const int nrr = f - k;
+    double z = lane < k ? __ldcg(x + c0 + lane) : 0.0;
+    if (lane == 0 && nrr > 0) wait_count(&flag[nd.parent], 1, ctl, S.spin_limit);
+    __syncwarp();
+    const double xr = lane < nrr ? __ldcg(x + S.sn_rows[nd.rptr + k + lane]) : 0.0;  // x of the rows below
+    // z_q -= sum over the rows below of L_iq x_i, in the single-item path's
+    // eight row chunks (chunk sums added in chunk order)
+    const int chunk = (nrr + 7) / 8;
+    double sum = 0.0;
+    for (int g = 0; g < 8; g++) {
+        double part = 0.0;
+        const int t0 = g * chunk, t1 = min(nrr, t0 + chunk);
+        for (int t = t0; t < t1; t++) {
+            const double xt = __shfl_sync(0xffffffffu, xr, t);
+            if (lane < k) part += L[(int64_t)lane * ld + k + t] * xt;
+        }
+        sum = g == 0 ? part : sum + part;
+    }
+    if (lane < k) z -= sum;
+    for (int j = k - 1; j > 0; j--) {
+        const double zj = __shfl_sync(0xffffffffu, z, j);
+        if (lane < j) z -= L[(int64_t)lane * ld + j] * zj;
+    }
+    if (lane < k) __stcg(x + c0 + lane, z);
+}
+
+
 __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched S, const double *__restrict__ fronts,
                                                                        const double *__restrict__ Dinv,
                                                                        double *__restrict__ x, double *upd,
@@ -256,6 +317,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
     SolveItem it;
     SolveNode nd;
     while (next_item(S, S.fwd, S.nfwd, it, nd, &sh_it, &sh_nd)) {
+        if (it.r == kLeafGroup) {
+            const int ls = S.fwd_leaf[8 * it.s + warp];
+            if (ls >= 0) leaf_forward(S, ls, fronts, Dinv, x, upd, cnt);
+            __syncthreads();
+            continue;
+        }
         const int s = it.s;
         const int f = nd.f, k = nd.k, ld = nd.ld, c0 = nd.c0;
         const double *L = fronts + nd.off;
@@ -394,6 +461,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
     SolveItem it;
     SolveNode nd;
     while (next_item(S, S.bwd, S.nbwd, it, nd, &sh_it, &sh_nd)) {
+        if (it.r == kLeafGroup) {
+            const int ls = S.bwd_leaf[8 * it.s + warp];
+            if (ls >= 0) leaf_backward(S, ls, fronts, x, flag, ctl);
+            __syncthreads();
+            continue;
+        }
         const int s = it.s;
         const int f = nd.f, k = nd.k, ld = nd.ld, c0 = nd.c0;
         const double *L = fronts + nd.off;
