@@ -86,7 +86,7 @@ typedef struct ipm_ctx ipm_ctx;
 typedef struct ipm_options {
     int32_t nb;               /* pivot-block width (Sec. 4.4 "32, 64 or 128"); default 32 */
     int32_t amalg_width;      /* merge a child into its parent when the width stays <= this; 16 */
-    double amalg_zero_frac;   /* ... or when explicit zeros stay <= this fraction; 0.05 */
+    double amalg_zero_frac;   /* ... or when explicit zeros stay <= this fraction; 0.1 */
     double eps_piv;           /* dynamic-regularisation floor eps_piv * ||K||_1 (Sec. 4.5: "of the order of
                                  magnitude of machine precision"); 2.220446049250313e-16 */
     double large_reg;         /* a lift larger than this raises IPM_WARN_LARGE_REG; 1e-4 */

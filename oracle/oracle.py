@@ -103,7 +103,7 @@ class Oracle:
             self.lib.orc_destroy(self.h)
             self.h = None
 
-    def analyse(self, perm=None, nb=32, amalg_width=16, amalg_zero_frac=0.05):
+    def analyse(self, perm=None, nb=32, amalg_width=16, amalg_zero_frac=0.1):
         p = None
         if perm is not None:
             self._perm_in = _c(perm, np.int32)

@@ -1227,7 +1227,7 @@ void ipm_default_options(ipm_options *o) {
     std::memset(o, 0, sizeof(*o));
     o->nb = 32;
     o->amalg_width = 16;
-    o->amalg_zero_frac = 0.05;
+    o->amalg_zero_frac = 0.1;
     o->eps_piv = 2.220446049250313e-16;  // machine precision (Sec. 4.5)
     o->large_reg = 1e-4;
     o->precision = IPM_PREC_FP64;
