@@ -97,6 +97,9 @@ struct ipm_ctx {
     double *panel_ws = nullptr;
     TileItem *tile_items = nullptr, *tc_items = nullptr, *alt_items = nullptr;
     FactorItem *lvl_items = nullptr;  // persistent level kernel: items of all levels
+    InvItem *inv_items = nullptr;     // diagonal blocks inverted after each factorisation
+    double *linv = nullptr;
+    int32_t ninv = 0;
     int32_t *lvl_sync = nullptr;      // its ticket and counters (1 + max counters of a level)
     int32_t lvl_grid = 1;
     bool mixed_active = false;  // tensor-core updates in use (mixed precision, no fallback yet)
@@ -451,6 +454,21 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
         const int64_t rect = (int64_t)nd.k * (nd.f - nd.k);
         nd.nblk = (nd.k + 31) / 32;
         nd.nrect = (nd.f > nd.k && (rect >= kRectSplit || nd.nblk > 1)) ? (nd.f - nd.k + kRectRows - 1) / kRectRows : 0;
+        nd.inv = -1;
+    }
+    // Supernodes whose diagonal blocks the sweeps apply through explicit
+    // inverses (computed once per factorisation): every block of a supernode
+    // with several blocks, and the block of a supernode with children and
+    // k >= 16.  Their substitutions lie on the sweeps' dependency chains;
+    // the leaves, off them, keep the substitution.
+    std::vector<InvItem> inv_items;
+    int64_t ninv = 0;
+    for (int32_t s = 0; s < ns; s++) {
+        SolveNode &nd = nodes[s];
+        if (!(nd.nblk > 1 || (nd.nchild > 0 && nd.k >= 16))) continue;
+        nd.inv = ninv * 1024;
+        for (int32_t b = 0; b < nd.nblk; b++) inv_items.push_back({s, b, (ninv + b) * 1024});
+        ninv += nd.nblk;
     }
     const int64_t nrows = P.sn_rptr[ns];
     std::vector<int64_t> grp(nrows + 1, 0);
@@ -531,8 +549,10 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
     int rc;
     if ((rc = dupload(c, &d_nodes, nodes)) || (rc = dupload(c, &d_grp, grp)) || (rc = dupload(c, &d_gsrc, gsrc)) ||
         (rc = dupload(c, &d_fwd, fwd)) || (rc = dupload(c, &d_bwd, bwd)) || (rc = dalloc(c, &d_yv, (size_t)P.N)) ||
-        (rc = dupload(c, &d_fleaf, fleaf)) || (rc = dupload(c, &d_bleaf, bleaf)))
+        (rc = dupload(c, &d_fleaf, fleaf)) || (rc = dupload(c, &d_bleaf, bleaf)) ||
+        (rc = dupload(c, &c->inv_items, inv_items)) || (rc = dalloc(c, &c->linv, (size_t)ninv * 1024)))
         return rc;
+    c->ninv = (int32_t)inv_items.size();
     SolveSched &S = c->sched;
     S.node = d_nodes;
     S.sn_rows = d_rows;
@@ -548,6 +568,7 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
     S.yv = d_yv;
     S.fwd_leaf = d_fleaf;
     S.bwd_leaf = d_bleaf;
+    S.Linv = c->linv;
     return IPM_OK;
 }
 
@@ -1131,6 +1152,11 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
     // needs every forked stream joined back)
     cudaEventRecord(c->dep_ev[nev - 1], sd);
     cudaStreamWaitEvent(st, c->dep_ev[nev - 1], 0);
+    if (c->ninv > 0) {
+        Prof pr(c, IPM_K_OTHER, Work(), st);
+        launch_diag_inverse(c->sched, c->fronts, c->linv, c->inv_items, c->ninv, st);
+        nl++;
+    }
     {
         Prof pr(c, IPM_K_OTHER, Work(), st);
         launch_factor_stats(c->D, c->dyn, P.N, c->opt.large_reg, c->ctl, st);

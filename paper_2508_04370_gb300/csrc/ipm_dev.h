@@ -113,6 +113,7 @@ struct SolveNode {
     int64_t off;    // slab offset (doubles)
     int64_t upd;    // offset of its contribution vector
     int64_t rptr;   // first entry in sn_rows and gat_rp
+    int64_t inv;    // inverses of its diagonal blocks in SolveSched::Linv (32 x 32 each), -1: none
     int32_t f, k, ld, c0;
     int32_t parent, nchild, nrect, nblk;  // nblk: items of L11 (32-column blocks; 1 when unsplit)
 };
@@ -131,6 +132,13 @@ struct SolveSched {
     double *yv;              // forward: y of split supernodes (before D^-1)
     const int32_t *fwd_leaf, *bwd_leaf;  // leaf groups: 8 childless single-item supernodes with f <= 32
                                          // per ticket (-1 pads), one warp each
+    const double *Linv;                  // inverse unit-lower diagonal blocks, column-major 32 x 32
+};
+// One diagonal block to invert after a factorisation: block b of supernode s
+// into Linv + dst.
+struct InvItem {
+    int32_t s, b;
+    int64_t dst;
 };
 constexpr int32_t kLeafGroup = INT32_MIN;  // SolveItem.r of a leaf group (s = group index)
 constexpr int kRectRows = 32;
@@ -202,6 +210,8 @@ void launch_forward(const DevPlan &P, const double *fronts, const double *D, dou
                     const int32_t *list, int32_t count, int32_t maxf, cudaStream_t st);
 void launch_backward(const DevPlan &P, const double *fronts, double *x, const int32_t *list, int32_t count,
                      int32_t maxf, cudaStream_t st);
+void launch_diag_inverse(const SolveSched &S, const double *fronts, double *Linv, const InvItem *items,
+                         int32_t count, cudaStream_t st);
 void launch_forward_persistent(const SolveSched &S, const double *fronts, const double *Dinv, double *x, double *upd,
                                int32_t maxf, int32_t grid, DevCtl *ctl, cudaStream_t st,
                                const int32_t *skip = nullptr);

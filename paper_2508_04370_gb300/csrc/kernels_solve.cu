@@ -240,6 +240,43 @@ __device__ __forceinline__ void diag_backward(const double *Lb, double *z, int w
     if (lane < w) z[lane] = zi;
 }
 
+// Explicit inverse X = L11^-1 of the unit lower-triangular w x w diagonal
+// block b of supernode s (w <= 32), one warp per block, computed once per
+// factorisation: lane j builds column j by
+//   X_jj = 1,   X_ij = -sum_{j <= t < i} L_it X_tj   (i > j),
+// rows in increasing order.  Stored column-major 32 x 32 (X_ij at 32 j + i),
+// zero above the diagonal, identity outside [0, w).  The sweeps then apply a
+// block as a matrix-vector product spread over four warps instead of a
+// substitution of w dependent steps.
+constexpr int kInvWarps = 2;
+__global__ void __launch_bounds__(32 * kInvWarps) k_diag_inverse(SolveSched S, const double *__restrict__ fronts,
+                                                                 double *__restrict__ Linv,
+                                                                 const InvItem *__restrict__ items, int count) {
+    __shared__ double Ls[kInvWarps][32][33];  // [row i][column t] of the strictly lower block
+    __shared__ double Xs[kInvWarps][32][33];  // [row t][column j] of X
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int idx = blockIdx.x * kInvWarps + wl;
+    if (idx >= count) return;  // whole warps; no CTA barrier below
+    const InvItem it = items[idx];
+    const SolveNode nd = S.node[it.s];
+    const int b0 = 32 * it.b, w = min(32, nd.k - b0), ld = nd.ld;
+    const double *L = fronts + nd.off;
+    for (int t = 0; t < 32; t++) {
+        Ls[wl][lane][t] = (t < w && lane > t && lane < w) ? L[(int64_t)(b0 + t) * ld + b0 + lane] : 0.0;
+        Xs[wl][t][lane] = t == lane ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    for (int i = 1; i < w; i++) {
+        double acc = 0.0;
+        for (int t = 0; t < i; t++) acc += Ls[wl][i][t] * Xs[wl][t][lane];  // Xs[t][lane] = 0 for t < lane
+        __syncwarp();
+        if (lane < i) Xs[wl][i][lane] = -acc;
+        __syncwarp();
+    }
+    double *X = Linv + it.dst;
+    for (int j = 0; j < 32; j++) X[32 * j + lane] = Xs[wl][lane][j];
+}
+
 // Leaves of the elimination tree with one block and f <= 32 (most of the
 // supernodes of a nested-dissection or AMD tree) are processed one per
 // warp, eight to a ticket (a leaf group), lane i = front row i.  Each
@@ -301,6 +338,51 @@ __device__ __forceinline__ void leaf_backward(const SolveSched &S, int s, const 
 }
 
 
+// Stage the w x w inverse of a diagonal block (column-major 32 x 32 in
+// Linv) as Lb[j * 33 + i] = X_ij.
+__device__ __forceinline__ void stage_inverse(double *Lb, const double *X, int w) {
+    for (int q = threadIdx.x; q < 32 * 32; q += kSolveThreads) {
+        const int jj = q >> 5, ii = q & 31;
+        if (ii < w && jj < w) Lb[jj * 33 + ii] = X[q];
+    }
+}
+
+// v[0:w) <- X v with X = L11^-1 staged in Lb: warps 0-3 each sum eight
+// columns for every row (lane = row), then warp 0 adds the four partial sums
+// in warp order.  The caller separates this from the writes of v before it
+// and the reads after it with CTA barriers.
+__device__ __forceinline__ void apply_inverse_forward(const double *Lb, double *v, double (*part)[33], int w) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 4) {
+        double a = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const int j = 8 * warp + c;
+            if (j < w) a += Lb[j * 33 + lane] * v[j];
+        }
+        part[warp][lane] = a;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < w) v[lane] = ((part[0][lane] + part[1][lane]) + part[2][lane]) + part[3][lane];
+}
+
+// z[0:w) <- X^T z: warps 0-3 each sum eight rows for every column (lane =
+// column), then warp 0 adds the partial sums in warp order.
+__device__ __forceinline__ void apply_inverse_backward(const double *Lb, double *z, double (*part)[33], int w) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 4) {
+        double a = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const int i = 8 * warp + c;
+            if (i < w && lane < w) a += Lb[lane * 33 + i] * z[i];
+        }
+        part[warp][lane] = a;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < w) z[lane] = ((part[0][lane] + part[1][lane]) + part[2][lane]) + part[3][lane];
+}
+
 __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched S, const double *__restrict__ fronts,
                                                                        const double *__restrict__ Dinv,
                                                                        double *__restrict__ x, double *upd,
@@ -329,8 +411,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
         const bool single = nd.nblk == 1 && nd.nrect == 0;
         if (it.r < 0) {
             const int b = -1 - it.r, b0 = 32 * b, w = min(32, k - b0);
+            const bool inv = nd.inv >= 0;
             // loads that do not depend on other items go out before the wait
-            stage_diag(Lb, L, ld, b0, w);
+            if (inv) stage_inverse(Lb, S.Linv + nd.inv + 1024 * b, w);
+            else stage_diag(Lb, L, ld, b0, w);
             const int nr = single ? f : w;  // rows this item gathers
             int64_t e0 = 0, e1 = 0, g[4] = {0, 0, 0, 0};
             double a0 = 0.0, dinv = 0.0;
@@ -382,7 +466,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
                 }
             }
             __syncthreads();
-            if (warp == 0) diag_forward(Lb, v, w);
+            if (inv) apply_inverse_forward(Lb, v, part, w);
+            else if (warp == 0) diag_forward(Lb, v, w);
             __syncthreads();
             if (single) {
                 for (int i = w + tid; i < f; i += kSolveThreads) {
@@ -473,9 +558,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
         const int32_t *rows = S.sn_rows + nd.rptr;
         const int b = -1 - it.r, b0 = 32 * b, w = min(32, k - b0);
         const int nrr = f - k;  // rows below the supernode's columns
-        // independent of other items: the diagonal block and this block's
-        // values after the forward sweep
-        stage_diag(Lb, L, ld, b0, w);
+        // independent of other items: the diagonal block (or its inverse) and
+        // this block's values after the forward sweep
+        const bool inv = nd.inv >= 0;
+        if (inv) stage_inverse(Lb, S.Linv + nd.inv + 1024 * b, w);
+        else stage_diag(Lb, L, ld, b0, w);
         const double xb = (tid < w) ? __ldcg(x + c0 + b0 + tid) : 0.0;
         if (tid == 0 && nrr > 0) wait_count(&flag[nd.parent], 1, ctl, S.spin_limit);
         __syncthreads();
@@ -512,7 +599,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
             z[lane] = xb - sum;
         }
         __syncthreads();
-        if (warp == 0) diag_backward(Lb, z, w);
+        if (inv) apply_inverse_backward(Lb, z, part, w);
+        else if (warp == 0) diag_backward(Lb, z, w);
         __syncthreads();
         for (int q = tid; q < w; q += kSolveThreads) __stcg(x + c0 + b0 + q, z[q]);
         __threadfence();
@@ -670,6 +758,12 @@ void launch_backward(const DevPlan &P, const double *fronts, double *x, const in
 }
 
 const void *persistent_probe_kernel() { return (const void *)k_forward_persistent; }
+
+void launch_diag_inverse(const SolveSched &S, const double *fronts, double *Linv, const InvItem *items,
+                         int32_t count, cudaStream_t st) {
+    if (count <= 0) return;
+    k_diag_inverse<<<(count + kInvWarps - 1) / kInvWarps, 32 * kInvWarps, 0, st>>>(S, fronts, Linv, items, count);
+}
 
 void launch_forward_persistent(const SolveSched &S, const double *fronts, const double *Dinv, double *x, double *upd,
                                int32_t maxf, int32_t grid, DevCtl *ctl, cudaStream_t st, const int32_t *skip) {
