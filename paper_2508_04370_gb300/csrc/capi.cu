@@ -101,7 +101,8 @@ struct ipm_ctx {
     double *linv = nullptr;
     int32_t ninv = 0;
     int32_t *lvl_sync = nullptr;      // its ticket and counters (1 + max counters of a level)
-    int32_t lvl_grid = 1;
+    int32_t lvl_grid = 1;         // CTAs of the level kernel: every SM full
+    int32_t lvl_grid_shared = 1;  // one CTA per SM, for levels whose small fronts run beside it
     bool mixed_active = false;  // tensor-core updates in use (mixed precision, no fallback yet)
     int32_t fallbacks = 0;
     double flops_tensor = 0.0;
@@ -863,6 +864,7 @@ int setup_device(ipm_ctx *c) {
         int lvl_per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lvl_per_sm, large_level_kernel(), 256, 0);
         c->lvl_grid = sms * std::max(1, lvl_per_sm);
+        c->lvl_grid_shared = sms;
     }
     DevPlan &dp = c->dp;
     dp.N = N;
@@ -1066,7 +1068,7 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                 Prof pr(c, IPM_K_LARGE_PANEL, lw, sd);
                 launch_large_level(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_items + W.lvl_off,
                                    W.lvl_cnt, c->lvl_sync, W.lvl_ncnt, c->asm_info, c->asm_cr, c->panel_ws,
-                                   c->opt.nb, c->lvl_grid,
+                                   c->opt.nb, W.small.empty() ? c->lvl_grid : c->lvl_grid_shared,
                                    c->opt.spin_limit_log2 < 0 ? 0 : (1ll << c->opt.spin_limit_log2), sd);
             }
             nl++;

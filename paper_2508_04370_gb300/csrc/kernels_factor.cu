@@ -300,11 +300,18 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
             }
             __syncthreads();
         }
-        // trailing update of columns [b1, f) by the block's pivots
+        // trailing update of columns [b1, f) by the block's pivots:
+        // W_jq = L_jq d_q is formed once into the unused upper triangle
+        // (row b0 + q of column j), then each entry takes one FMA per pivot
+        for (int t = tid; t < w * (f - b1); t += NT) {
+            const int q = t % w, j = b1 + t / w;
+            F[j * ld + b0 + q] = F[(b0 + q) * ld + j] * dq[q];
+        }
+        __syncthreads();
         for (int j = b1 + warp; j < f; j += NW) {
             for (int i = j + lane; i < f; i += 32) {
                 double acc = 0.0;
-                for (int q = 0; q < w; q++) acc += F[(b0 + q) * ld + i] * (F[(b0 + q) * ld + j] * dq[q]);
+                for (int q = 0; q < w; q++) acc += F[(b0 + q) * ld + i] * F[j * ld + b0 + q];
                 F[j * ld + i] -= acc;
             }
         }
