@@ -39,7 +39,7 @@ struct StepWork {
     int64_t alt_off;  // FP64 tiles of the same fronts, used after a precision fallback
     int32_t alt_cnt;
     int32_t alt_cnt1;  // lookahead tiles among them
-    Work panel_w, trsm_w, tile_w, tile_w1, tc_w, alt_w1;
+    Work panel_w, trsm_w, tile_w, tile_w1, tc_w, alt_w, alt_w1;
 };
 struct SmallClass {
     int64_t off;
@@ -58,6 +58,12 @@ struct LevelWork {
     int32_t lvl_cnt = 0;
     int32_t lvl_ncnt = 0;  // its dependency counters
     bool has_tc = false;   // some front of the level has tensor-core update tiles
+    // The level kernel pays off where a level's large fronts are bound by
+    // their pivot chains (about 35 us per 32-column panel): when the level's
+    // FP64 front work at ~1 TFLOP/s takes less than half its longest chain.
+    // Levels with more work run one launch per step at full occupancy.
+    bool lvl_latency_bound = true;
+    Work lvl_w;  // algorithmic work of the level's large fronts (assembly and factorisation)
 };
 
 struct ProfRec {
@@ -101,8 +107,7 @@ struct ipm_ctx {
     double *linv = nullptr;
     int32_t ninv = 0;
     int32_t *lvl_sync = nullptr;      // its ticket and counters (1 + max counters of a level)
-    int32_t lvl_grid = 1;         // CTAs of the level kernel: every SM full
-    int32_t lvl_grid_shared = 1;  // one CTA per SM, for levels whose small fronts run beside it
+    int32_t lvl_grid = 1;  // CTAs of the level kernel: every SM full
     bool mixed_active = false;  // tensor-core updates in use (mixed precision, no fallback yet)
     int32_t fallbacks = 0;
     double flops_tensor = 0.0;
@@ -814,6 +819,7 @@ int setup_device(ipm_ctx *c) {
             S.tile_w1 = w1;
             S.tile_w = w2;
             S.alt_w1 = wa1;
+            S.alt_w = wa2;
             S.panel_cnt = (int32_t)(panel_items.size() - S.panel_off);
             S.trsm_cnt = (int32_t)(trsm_items.size() - S.trsm_off);
             S.tile_cnt = (int32_t)(tile_items.size() - S.tile_off);
@@ -823,6 +829,17 @@ int setup_device(ipm_ctx *c) {
             if (S.tc_cnt > 0) W.has_tc = true;
         }
         build_level_items(P, l, W, slot_of, lvl_items, cbase);
+        {
+            int32_t chain = 0;
+            for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
+                const int32_t s = P.lvl_large[t];
+                const Work fr = front_work(s);
+                W.lvl_w.flops += fr.flops;
+                W.lvl_w.bytes += fr.bytes;
+                chain = std::max(chain, (P.sn_k[s] + 31) / 32);
+            }
+            W.lvl_latency_bound = W.lvl_w.flops / 1.0e12 < 0.5 * chain * 35e-6;
+        }
         max_ncnt = std::max(max_ncnt, W.lvl_ncnt);
     }
     std::vector<int64_t> upd_off(P.upd_off.begin(), P.upd_off.end());
@@ -864,7 +881,6 @@ int setup_device(ipm_ctx *c) {
         int lvl_per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lvl_per_sm, large_level_kernel(), 256, 0);
         c->lvl_grid = sms * std::max(1, lvl_per_sm);
-        c->lvl_grid_shared = sms;
     }
     DevPlan &dp = c->dp;
     dp.N = N;
@@ -1056,19 +1072,13 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         }
         if (W.asm_cnt == 0 && W.steps.empty()) continue;
         if (small_before) cudaStreamWaitEvent(sd, small_before, 0);
-        if (c->opt.level_kernel && W.lvl_cnt > 0 && !(W.has_tc && c->mixed_active)) {
+        if (c->opt.level_kernel && W.lvl_cnt > 0 && W.lvl_latency_bound && !(W.has_tc && c->mixed_active)) {
             // FP64: all large-front work of the level in one dependency-driven launch
-            Work lw = W.asm_w;
-            for (const StepWork &S : W.steps)
-                for (const Work *x : {&S.panel_w, &S.trsm_w, &S.tile_w, &S.tile_w1}) {
-                    lw.flops += x->flops;
-                    lw.bytes += x->bytes;
-                }
             {
-                Prof pr(c, IPM_K_LARGE_PANEL, lw, sd);
+                Prof pr(c, IPM_K_LARGE_PANEL, W.lvl_w, sd);
                 launch_large_level(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_items + W.lvl_off,
                                    W.lvl_cnt, c->lvl_sync, W.lvl_ncnt, c->asm_info, c->asm_cr, c->panel_ws,
-                                   c->opt.nb, W.small.empty() ? c->lvl_grid : c->lvl_grid_shared,
+                                   c->opt.nb, c->lvl_grid,
                                    c->opt.spin_limit_log2 < 0 ? 0 : (1ll << c->opt.spin_limit_log2), sd);
             }
             nl++;
@@ -1117,7 +1127,7 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                     nl++;
                 }
                 if (rest_alt > 0) {
-                    Prof pr(c, IPM_K_LARGE_UPDATE, Work(), sd2);
+                    Prof pr(c, IPM_K_LARGE_UPDATE, S.alt_w, sd2);
                     launch_large_update(c->dp, c->fronts, c->D, c->alt_items + S.alt_off + S.alt_cnt1, rest_alt, S.p0,
                                         c->opt.nb, sd2);
                     nl++;
