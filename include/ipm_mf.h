@@ -132,6 +132,9 @@ typedef struct ipm_info {
     int64_t nnz_ne_seen;                    /* entries of A A^T counted before the chooser stopped */
     int32_t precision_fallbacks;            /* mixed path: refactorisations in FP64 so far */
     int32_t mixed_active;                   /* 1 while tensor-core updates are in use */
+    int32_t tune_small_threads[3];          /* threads per small-front CTA, size classes f <= 32, 64, 128 */
+    double tune_level_ratio;                /* level-kernel threshold (see ipm_autotune) */
+    double tune_ms;                         /* best factorisation time the autotuner measured; 0 before */
 } ipm_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -289,6 +292,25 @@ int ipm_launch_counts(const ipm_ctx *ctx, int32_t *factorise_launches, int32_t *
  *   - Like ipm_solve it synchronises `stream` once per refinement step. */
 int ipm_solve_noalloc(ipm_ctx *ctx, const double *r7_dev, const double *r1_dev, double *dx_dev, double *dy_dev,
                       void *stream);
+
+/* Autotuner for the launch shapes of the factorisation (the batching and
+ * tiling the paper's CPU scheme leaves to the implementation, Sec. 4.3):
+ * factorises `reps` + 1 times per candidate on `stream` with the given Theta
+ * (device, n doubles), rho and delta, and keeps, by coordinate descent,
+ *   - the level-kernel threshold: a tree level runs its large fronts in one
+ *     persistent launch when their FP64 work at 1 TFLOP/s is below ratio x
+ *     (35 us per 32-column panel of its widest front); candidates 0 (never),
+ *     0.25, 0.5 (default), 1, 2, 1e30 (always);
+ *   - the threads per small-front CTA of each size class present (f <= 32:
+ *     32 or 64; f <= 64: 64 or 128; f <= 128: 128 or 256).
+ * The choices never change the arithmetic of any entry: the factors are the
+ * same bit for bit.  They are reported by ipm_get_info and kept by the
+ * context; tune before ipm_graph_capture (a captured graph keeps the launch
+ * shapes it was captured with).  Synchronises `stream`.  Leaves the context
+ * factorised with the last candidate's (identical) factors.
+ * Errors: IPM_ERR_NOT_ANALYSED before ipm_set_values, IPM_ERR_INVALID_ARG for
+ * reps outside [1, 20], and those of ipm_factorise. */
+int ipm_autotune(ipm_ctx *ctx, const double *theta_dev, double rho, double delta, int32_t reps, void *stream);
 
 /* ------------------------------------------------------------ measurement */
 /* Kernel classes reported by ipm_kernel_stats. */

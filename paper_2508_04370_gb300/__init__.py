@@ -76,11 +76,13 @@ class ipm_info(ct.Structure):
         ("gmres_iters", ct.c_int32), ("omega", ct.c_double), ("omega_hist", ct.c_double * 16), ("status", ct.c_int32),
         ("ms_analyse", ct.c_double), ("est_cost_ne", ct.c_double), ("est_cost_as", ct.c_double),
         ("nnz_ne_seen", ct.c_int64), ("precision_fallbacks", ct.c_int32), ("mixed_active", ct.c_int32),
+        ("tune_small_threads", ct.c_int32 * 3), ("tune_level_ratio", ct.c_double), ("tune_ms", ct.c_double),
     ]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
         d["omega_hist"] = list(self.omega_hist)[: min(16, max(self.refine_steps - self.gmres_iters + 1, 1))]
+        d["tune_small_threads"] = list(self.tune_small_threads)
         return d
 
 
@@ -113,6 +115,7 @@ def _load():
     lib.ipm_save_analysis.argtypes = [P, ct.c_char_p]
     lib.ipm_load_analysis.argtypes = [P, ct.c_char_p]
     lib.ipm_factorise.argtypes = [P, P, ct.c_double, ct.c_double, P]
+    lib.ipm_autotune.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_int32, P]
     lib.ipm_solve.argtypes = [P, P, P, P, P, P]
     lib.ipm_iterate_host.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_int32, P, P, P, P, P]
     lib.ipm_sync_status.argtypes = [P, P]
@@ -226,6 +229,10 @@ def ipm_set_values(ctx, Ax_dev, stream=None) -> int:
 
 def ipm_factorise(ctx, theta_dev, rho, delta, stream=None) -> int:
     return _load().ipm_factorise(ctx, _dptr(theta_dev), float(rho), float(delta), _stream(stream))
+
+
+def ipm_autotune(ctx, theta_dev, rho, delta, reps=3, stream=None) -> int:
+    return _load().ipm_autotune(ctx, _dptr(theta_dev), float(rho), float(delta), int(reps), _stream(stream))
 
 
 def ipm_solve(ctx, r7_dev, r1_dev, dx_dev, dy_dev, stream=None) -> int:

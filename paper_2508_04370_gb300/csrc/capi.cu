@@ -44,6 +44,7 @@ struct StepWork {
 struct SmallClass {
     int64_t off;
     int32_t cnt, maxf;
+    int32_t cls;  // size class: f <= 32, <= 64, <= 128
     Work w;
 };
 struct LevelWork {
@@ -59,11 +60,12 @@ struct LevelWork {
     int32_t lvl_ncnt = 0;  // its dependency counters
     bool has_tc = false;   // some front of the level has tensor-core update tiles
     // The level kernel pays off where a level's large fronts are bound by
-    // their pivot chains (about 35 us per 32-column panel): when the level's
-    // FP64 front work at ~1 TFLOP/s takes less than half its longest chain.
-    // Levels with more work run one launch per step at full occupancy.
-    bool lvl_latency_bound = true;
-    Work lvl_w;  // algorithmic work of the level's large fronts (assembly and factorisation)
+    // their pivot chains (about 35 us per 32-column panel): a level takes it
+    // when its FP64 front work at ~1 TFLOP/s is below tune_ratio times its
+    // longest chain (0.5 unless ipm_autotune chose otherwise).  Levels with
+    // more work run one launch per step at full occupancy.
+    int32_t lvl_chain = 0;  // 32-column panels of the level's widest large front
+    Work lvl_w;             // algorithmic work of the level's large fronts (assembly and factorisation)
 };
 
 struct ProfRec {
@@ -108,6 +110,11 @@ struct ipm_ctx {
     int32_t ninv = 0;
     int32_t *lvl_sync = nullptr;      // its ticket and counters (1 + max counters of a level)
     int32_t lvl_grid = 1;  // CTAs of the level kernel: every SM full
+    // choices of ipm_autotune: threads per small-front CTA by size class
+    // (0: 32 / 64 / 128) and the level-kernel threshold
+    int32_t tune_threads[3] = {0, 0, 0};
+    double tune_ratio = 0.5;
+    double tune_ms = 0.0;
     bool mixed_active = false;  // tensor-core updates in use (mixed precision, no fallback yet)
     int32_t fallbacks = 0;
     double flops_tensor = 0.0;
@@ -701,6 +708,7 @@ int setup_device(ipm_ctx *c) {
                 }
             }
             C.cnt = (int32_t)(small_lists.size() - C.off);
+            C.cls = b;
             lo = bounds[b];
             maxsmall = std::max(maxsmall, C.maxf);
             if (C.cnt > 0) W.small.push_back(C);
@@ -838,7 +846,7 @@ int setup_device(ipm_ctx *c) {
                 W.lvl_w.bytes += fr.bytes;
                 chain = std::max(chain, (P.sn_k[s] + 31) / 32);
             }
-            W.lvl_latency_bound = W.lvl_w.flops / 1.0e12 < 0.5 * chain * 35e-6;
+            W.lvl_chain = chain;
         }
         max_ncnt = std::max(max_ncnt, W.lvl_ncnt);
     }
@@ -1059,7 +1067,7 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                 if (q > 0) cudaStreamWaitEvent(sq, fork, 0);
                 Prof pr(c, IPM_K_SMALL_FRONTS, C.w, sq);
                 launch_small_fronts(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_small + C.off, C.cnt,
-                                    c->opt.nb, C.maxf, sq);
+                                    c->opt.nb, C.maxf, c->tune_threads[C.cls], sq);
                 nl++;
                 if (q > 0) {
                     cudaEvent_t join = c->dep_ev[2 + 5 * l + (q - 1)];
@@ -1072,7 +1080,8 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         }
         if (W.asm_cnt == 0 && W.steps.empty()) continue;
         if (small_before) cudaStreamWaitEvent(sd, small_before, 0);
-        if (c->opt.level_kernel && W.lvl_cnt > 0 && W.lvl_latency_bound && !(W.has_tc && c->mixed_active)) {
+        const bool latency_bound = W.lvl_w.flops / 1.0e12 < c->tune_ratio * W.lvl_chain * 35e-6;
+        if (c->opt.level_kernel && W.lvl_cnt > 0 && latency_bound && !(W.has_tc && c->mixed_active)) {
             // FP64: all large-front work of the level in one dependency-driven launch
             {
                 Prof pr(c, IPM_K_LARGE_PANEL, W.lvl_w, sd);
@@ -1495,6 +1504,85 @@ int ipm_factorise(ipm_ctx *c, const double *theta_dev, double rho, double delta,
     return IPM_OK;
 }
 
+// Autotuner (the batching of Sec. 4.3 leaves the per-bucket launch shapes
+// open): times factorisations of the context's own problem on the device
+// and keeps, by coordinate descent, the level-kernel threshold and the CTA
+// width of each small-front size class that give the shortest time.  No
+// choice changes the arithmetic of any entry, so the factors stay the same
+// bit for bit.
+int ipm_autotune(ipm_ctx *c, const double *theta_dev, double rho, double delta, int32_t reps, void *stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->values_set) return IPM_ERR_NOT_ANALYSED;
+    if (reps < 1 || reps > 20) return IPM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return IPM_ERR_CUDA;
+    }
+    // median of reps factorisations after one untimed
+    auto measure = [&](double &ms) -> int {
+        std::vector<float> t;
+        for (int r = 0; r <= reps; r++) {
+            cudaEventRecord(e0, st);
+            int q = ipm_factorise(c, theta_dev, rho, delta, st);
+            if (q) return q;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return IPM_ERR_CUDA;
+            float x = 0.f;
+            cudaEventElapsedTime(&x, e0, e1);
+            if (r > 0) t.push_back(x);
+        }
+        std::sort(t.begin(), t.end());
+        ms = t[t.size() / 2];
+        return IPM_OK;
+    };
+    bool present[3] = {false, false, false};
+    for (const LevelWork &W : c->levels)
+        for (const SmallClass &C : W.small) present[C.cls] = true;
+    double best = 0.0;
+    if ((rc = measure(best))) goto done;
+    {
+        const double ratios[] = {0.0, 0.25, 0.5, 1.0, 2.0, 1e30};
+        const double r0 = c->tune_ratio;
+        double pick = r0;
+        for (double r : ratios) {
+            if (r == r0) continue;
+            c->tune_ratio = r;
+            double ms;
+            if ((rc = measure(ms))) goto done;
+            if (ms < best) {
+                best = ms;
+                pick = r;
+            }
+        }
+        c->tune_ratio = pick;
+        const int32_t widths[3][2] = {{32, 64}, {64, 128}, {128, 256}};
+        for (int b = 0; b < 3; b++) {
+            if (!present[b]) continue;
+            const int32_t t0 = c->tune_threads[b];
+            int32_t keep = t0;
+            for (int32_t w : widths[b]) {
+                if (w == t0 || (t0 == 0 && w == widths[b][0])) continue;  // 0 is the first width
+                c->tune_threads[b] = w;
+                double ms;
+                if ((rc = measure(ms))) goto done;
+                if (ms < best) {
+                    best = ms;
+                    keep = w;
+                }
+            }
+            c->tune_threads[b] = keep;
+        }
+        c->tune_ms = best;
+    }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
 static int read_ctl(ipm_ctx *c, cudaStream_t st, DevCtl *h) {
     cudaError_t e = cudaMemcpyAsync(h, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1777,6 +1865,12 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
     out->ms_analyse = c->ms_analyse;
     out->refine_steps = c->refine_steps;
     out->gmres_iters = c->gmres_iters;
+    for (int b = 0; b < 3; b++) {
+        const int32_t dflt = b == 0 ? 32 : b == 1 ? 64 : 128;
+        out->tune_small_threads[b] = c->tune_threads[b] > 0 ? c->tune_threads[b] : dflt;
+    }
+    out->tune_level_ratio = c->tune_ratio;
+    out->tune_ms = c->tune_ms;
     out->omega = c->omega;
     for (int i = 0; i < 16; i++) out->omega_hist[i] = c->omega_hist[i];
     if (!c->analysed) return IPM_ERR_NOT_ANALYSED;

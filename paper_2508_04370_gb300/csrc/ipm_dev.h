@@ -180,8 +180,8 @@ struct FactorItem {
 // factorisation (kernels_factor.cu)
 void launch_norm1(const DevPlan &P, const DevVals &V, DevCtl *ctl, double eps_piv, cudaStream_t st);
 void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
-                         DevCtl *ctl,
-                         const int32_t *list, int32_t count, int32_t nb, int32_t maxf, cudaStream_t st);
+                         DevCtl *ctl, const int32_t *list, int32_t count, int32_t nb, int32_t maxf, int32_t threads,
+                         cudaStream_t st);
 void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, const PanelItem *items,
                            const AsmItem *ainfo, const int32_t *acr, int32_t count, cudaStream_t st);
 // panel step 1 (diagonal block, one item per front; item.r1 = workspace slot)

@@ -889,21 +889,29 @@ __global__ void k_factor_stats(const double *__restrict__ D, const double *__res
 }  // namespace
 
 void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
-                         DevCtl *ctl,
-                         const int32_t *list, int32_t count, int32_t nb, int32_t maxf, cudaStream_t st) {
+                         DevCtl *ctl, const int32_t *list, int32_t count, int32_t nb, int32_t maxf, int32_t threads,
+                         cudaStream_t st) {
     if (count <= 0) return;
     const int ldmax = (maxf + 3) & ~3;
     const size_t smem = (size_t)ldmax * maxf * sizeof(double);
     static bool attr = false;
     if (!attr) {
+        cudaFuncSetAttribute(k_small_fronts<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_small_fronts<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_small_fronts<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_small_fronts<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    // one warp per front up to f = 32, two up to 64, four beyond
-    if (maxf <= 32) k_small_fronts<32><<<count, 32, smem, st>>>(P, V, fronts, D, Dinv, dyn, ctl, list, nb);
-    else if (maxf <= 64) k_small_fronts<64><<<count, 64, smem, st>>>(P, V, fronts, D, Dinv, dyn, ctl, list, nb);
-    else k_small_fronts<128><<<count, 128, smem, st>>>(P, V, fronts, D, Dinv, dyn, ctl, list, nb);
+    // default: one warp per front up to f = 32, two up to 64, four beyond;
+    // the autotuner may choose any of 32, 64, 128, 256 (same arithmetic per
+    // entry whatever the width)
+    if (threads <= 0) threads = maxf <= 32 ? 32 : maxf <= 64 ? 64 : 128;
+    switch (threads) {
+        case 32: k_small_fronts<32><<<count, 32, smem, st>>>(P, V, fronts, D, Dinv, dyn, ctl, list, nb); break;
+        case 64: k_small_fronts<64><<<count, 64, smem, st>>>(P, V, fronts, D, Dinv, dyn, ctl, list, nb); break;
+        case 256: k_small_fronts<256><<<count, 256, smem, st>>>(P, V, fronts, D, Dinv, dyn, ctl, list, nb); break;
+        default: k_small_fronts<128><<<count, 128, smem, st>>>(P, V, fronts, D, Dinv, dyn, ctl, list, nb); break;
+    }
 }
 
 void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, const PanelItem *items,

@@ -7,8 +7,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (IPM_FORM_AUGMENTED, IPM_ORD_AMD, ipm_analyse, ipm_create, ipm_default_options, ipm_destroy,
-               ipm_factorise, ipm_get_factor, ipm_get_info, ipm_get_symbolic, ipm_iterate_host, ipm_load_analysis,
+from . import (IPM_FORM_AUGMENTED, IPM_ORD_AMD, ipm_analyse, ipm_autotune, ipm_create, ipm_default_options,
+               ipm_destroy, ipm_factorise, ipm_get_factor, ipm_get_info, ipm_get_symbolic, ipm_iterate_host, ipm_load_analysis,
                ipm_save_analysis, ipm_set_values, ipm_solve, ipm_sync_status)
 
 
@@ -77,6 +77,17 @@ class Solver:
             raise RuntimeError(f"ipm_factorise failed ({rc})")
         self._theta = theta
         return rc
+
+    def autotune(self, theta, rho, delta, reps=3):
+        """Pick the factorisation's launch shapes by timing this problem
+        (see ipm_autotune); returns the choices."""
+        theta = self._dev(theta)
+        rc = ipm_autotune(self.ctx, theta, rho, delta, reps)
+        if rc < 0:
+            raise RuntimeError(f"ipm_autotune failed ({rc})")
+        self._theta = theta
+        i = self.info()
+        return {"small_threads": i["tune_small_threads"], "level_ratio": i["tune_level_ratio"], "ms": i["tune_ms"]}
 
     def solve(self, r7, r1):
         r7 = self._dev(r7)

@@ -532,3 +532,29 @@ def test_level_kernel_wait_timeout_reports_status(pkg):
     s2.solve(r7, r1)
     assert s2.status() >= 0 and s2.info()["omega"] <= 1e-12
     s2.close()
+
+
+def test_autotune_choices_keep_the_factor(pkg):
+    """The autotuner picks launch shapes only (small-front CTA widths per
+    size class, the level-kernel threshold): its choices are from the
+    documented candidate sets and the factor is the same bit for bit before
+    and after tuning, and matches the oracle's solve accuracy."""
+    lp = synth.grid_multicommodity(24, 4)
+    theta = synth.theta_loguniform(lp.n, 81)
+    r7, r1 = synth.rhs_normal(lp.n, 81), synth.rhs_normal(lp.m, 82)
+    s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND)
+    s.factorise(theta, RHO, DELTA)
+    assert s.status() >= 0
+    before = s.factor()
+    t = s.autotune(theta, RHO, DELTA, reps=1)
+    assert t["level_ratio"] in (0.0, 0.25, 0.5, 1.0, 2.0, 1e30)
+    for b, w in enumerate(t["small_threads"]):
+        assert w in ((32, 64), (64, 128), (128, 256))[b]
+    assert t["ms"] > 0.0
+    s.factorise(theta, RHO, DELTA)
+    after = s.factor()
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    s.solve(r7, r1)
+    assert s.status() >= 0 and s.info()["omega"] <= 1e-12
+    s.close()
