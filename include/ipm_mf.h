@@ -97,7 +97,7 @@ typedef struct ipm_options {
     int32_t gmres_restarts;   /* when classical refinement of an FP64 factor stalls above omega_target, up to
                                  this many restarts of GMRES(8) on K c = r preconditioned by the factor follow
                                  (an extension of Sec. 4.5; 0 = the paper's classical refinement only; a
-                                 stalled tensor-core factor falls back to FP64 instead); 3 */
+                                 stalled tensor-core factor falls back to FP64 instead); 6 */
     int32_t nd_leaf;          /* nested dissection stops at subgraphs of this size; 128 */
     double dense_row_factor;  /* AMD treats degree > max(16, f*sqrt(N)) as dense; 10 */
     int32_t device;           /* CUDA device ordinal; 0 */

@@ -1281,7 +1281,7 @@ void ipm_default_options(ipm_options *o) {
     o->mixed_min_front = 256;
     o->omega_target = 1e-12;
     o->refine_max = 10;
-    o->gmres_restarts = 3;
+    o->gmres_restarts = 6;
     o->nd_leaf = 128;
     o->dense_row_factor = 10.0;
     o->device = 0;
