@@ -53,7 +53,7 @@ class Workload:
         self.name = name
         self.lps = None
         self.fp64_target = 1e-12
-        self.tune_reps = 1 if name in ("batch512", "staircase") else 3  # autotuner repetitions per candidate
+        self.tune_reps = 1 if name in ("batch512", "staircase", "staircase10") else 3  # autotuner repetitions
         if name == "batch512":
             import paper_2508_04370_gb300.batch as B
 
@@ -70,7 +70,7 @@ class Workload:
                          f"one block-diagonal forest per GPU, AMD ordering; rank {rank}: {len(self.lps)} instances, "
                          f"m={m}, n={n}; one IPM iteration = factorise + 2 refined solves")
         else:
-            lp = synth.by_name(name, 1)
+            lp = synth.staircase(periods=10, seed=1) if name == "staircase10" else synth.by_name(name, 1)
             self.lp = lp
             n, m = lp.n, lp.m
             if name == "grid64_q4":
@@ -89,9 +89,15 @@ class Workload:
                              "period (m=100000, n=250000); Theta_j = exp(s g_j) along a 40-iteration schedule "
                              "(spread 1 to 1e-8..1e8); nested-dissection ordering; factorise + 2 solves refined to "
                              "omega <= 1e-10 on both paths")
+            elif name == "staircase10":
+                self.ordering_name = "nested-dissection"
+                self.fp64_target = 1e-10
+                self.desc = ("staircase LP, 10 periods of 2000 x 5000 (a profiling size of the 50-period workload), "
+                             "density 0.002, 500 identity links; Theta along the 40-iteration schedule; "
+                             "nested-dissection ordering; factorise + 2 solves refined to omega <= 1e-10")
             else:
                 raise SystemExit(f"unknown workload {name}")
-            if name == "staircase":
+            if name in ("staircase", "staircase10"):
                 self.thetas = synth.theta_schedule(n, 40, 1)
             else:
                 self.thetas = [synth.theta_loguniform(n, 1 + t) for t in range(3)]
@@ -424,7 +430,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="grid64_q4",
-                    choices=["grid64_q4", "random_300x800", "staircase", "batch512"])
+                    choices=["grid64_q4", "random_300x800", "staircase", "staircase10", "batch512"])
     ap.add_argument("--paths", default="fp64,mixed", help="comma-separated subset of fp64,mixed")
     args = ap.parse_args()
     if args.warmup < 3:
