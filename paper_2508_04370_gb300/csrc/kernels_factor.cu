@@ -5,9 +5,18 @@
 // ld) in one device arena.  After its factorisation the first k columns hold
 // L (strictly lower part; D on the diagonal) and the trailing (f-k) x (f-k)
 // lower block holds the contribution block (Schur complement) that the
-// parent pulls during its own assembly.  Children are always summed in
-// ascending order, original entries first, so results do not depend on
+// parent pulls during its own assembly (the strict upper part of a small
+// front's slab holds scratch and is never read).  Children are always summed
+// in ascending order, original entries first, so results do not depend on
 // scheduling (Sec. 4.3, determinism).
+//
+// Kernels: k_small_fronts (a whole front of f <= 128 in shared memory, one
+// CTA per front); the large-front bodies (assembly, diagonal block,
+// triangular solve, lookahead strip, trailing tile), run either one launch
+// per kind and pivot block or as items of the persistent level kernel
+// k_large_level; k_norm1 / k_set_b1 (||K||_1 and the lift floor) and
+// k_factor_stats (inertia, lifts).  The tensor-core trailing update is in
+// kernels_tc.cu.
 //
 // Pivot rule (Sec. 4.5, Prop. 3), applied to pivot p of the current pivot
 // block [b0, b1) of nb fully-summed columns:
