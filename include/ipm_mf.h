@@ -312,6 +312,16 @@ int ipm_solve_noalloc(ipm_ctx *ctx, const double *r7_dev, const double *r1_dev, 
  * reps outside [1, 20], and those of ipm_factorise. */
 int ipm_autotune(ipm_ctx *ctx, const double *theta_dev, double rho, double delta, int32_t reps, void *stream);
 
+/* Set the launch shapes ipm_autotune would choose, e.g. to reproduce a
+ * configuration: small_threads (host, 3 entries, may be NULL to keep) gives
+ * the threads per small-front CTA of the size classes f <= 32, 64, 128, each
+ * 32, 64, 128, 256 or 0 (the default 32 / 64 / 128); level_ratio >= 0 sets
+ * the level-kernel threshold (a negative value keeps it).  Results are the
+ * same bit for bit whatever the shapes.  Takes effect at the next
+ * factorisation (not in an already captured graph).
+ * Errors: IPM_ERR_INVALID_ARG for another width or a NaN ratio. */
+int ipm_set_launch_shapes(ipm_ctx *ctx, const int32_t *small_threads, double level_ratio);
+
 /* ------------------------------------------------------------ measurement */
 /* Kernel classes reported by ipm_kernel_stats. */
 #define IPM_K_SMALL_FRONTS 0   /* fused assemble+factorise of fronts f <= 128 (shared memory) */

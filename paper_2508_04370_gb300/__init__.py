@@ -116,6 +116,7 @@ def _load():
     lib.ipm_load_analysis.argtypes = [P, ct.c_char_p]
     lib.ipm_factorise.argtypes = [P, P, ct.c_double, ct.c_double, P]
     lib.ipm_autotune.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_int32, P]
+    lib.ipm_set_launch_shapes.argtypes = [P, P, ct.c_double]
     lib.ipm_solve.argtypes = [P, P, P, P, P, P]
     lib.ipm_iterate_host.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_int32, P, P, P, P, P]
     lib.ipm_sync_status.argtypes = [P, P]
@@ -233,6 +234,12 @@ def ipm_factorise(ctx, theta_dev, rho, delta, stream=None) -> int:
 
 def ipm_autotune(ctx, theta_dev, rho, delta, reps=3, stream=None) -> int:
     return _load().ipm_autotune(ctx, _dptr(theta_dev), float(rho), float(delta), int(reps), _stream(stream))
+
+
+def ipm_set_launch_shapes(ctx, small_threads=None, level_ratio=-1.0) -> int:
+    arr = None if small_threads is None else np.ascontiguousarray(small_threads, dtype=np.int32)
+    ptr = None if arr is None else _hptr(arr, np.int32)
+    return _load().ipm_set_launch_shapes(ctx, ptr, float(level_ratio))
 
 
 def ipm_solve(ctx, r7_dev, r1_dev, dx_dev, dy_dev, stream=None) -> int:

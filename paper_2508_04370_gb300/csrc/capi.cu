@@ -1591,6 +1591,20 @@ static int read_ctl(ipm_ctx *c, cudaStream_t st, DevCtl *h) {
     return IPM_OK;
 }
 
+int ipm_set_launch_shapes(ipm_ctx *c, const int32_t *small_threads, double level_ratio) {
+    if (!c) return IPM_ERR_INVALID_ARG;
+    if (small_threads)
+        for (int b = 0; b < 3; b++) {
+            const int32_t w = small_threads[b];
+            if (w != 0 && w != 32 && w != 64 && w != 128 && w != 256) return IPM_ERR_INVALID_ARG;
+        }
+    if (!(level_ratio < 0.0) && !(level_ratio >= 0.0)) return IPM_ERR_INVALID_ARG;  // NaN
+    if (small_threads)
+        for (int b = 0; b < 3; b++) c->tune_threads[b] = small_threads[b];
+    if (level_ratio >= 0.0) c->tune_ratio = level_ratio;
+    return IPM_OK;
+}
+
 // GMRES refinement, an extension of the refinement of Sec. 4.5 for systems
 // where classical refinement stalls above the target (lifted pivots make the
 // factor a poor enough preconditioner that r -> K^-1 r steps stop halving

@@ -229,3 +229,18 @@ def test_analysis_checkpoint_roundtrip(tmp_path):
         assert L.ipm_load_analysis(b, str(tmp_path / "missing.plan")) == L.IPM_ERR_INVALID_ARG
         L.ipm_destroy(a)
         L.ipm_destroy(b)
+
+
+def test_launch_shapes_validation(lib):
+    """ipm_set_launch_shapes accepts the autotuner's widths (or 0 for the
+    default) and a non-negative level ratio, and rejects anything else
+    without touching the GPU; ipm_autotune needs values first."""
+    ctx = lib.ipm_create()
+    assert lib.ipm_set_launch_shapes(ctx, [32, 128, 256], 1.0) == 0
+    assert lib.ipm_set_launch_shapes(ctx, [0, 0, 0]) == 0
+    assert lib.ipm_set_launch_shapes(ctx, None, 0.0) == 0
+    assert lib.ipm_set_launch_shapes(ctx, [48, 64, 128]) == lib.IPM_ERR_INVALID_ARG
+    assert lib.ipm_set_launch_shapes(ctx, [32, 64, 512]) == lib.IPM_ERR_INVALID_ARG
+    assert lib.ipm_set_launch_shapes(ctx, None, float("nan")) == lib.IPM_ERR_INVALID_ARG
+    assert lib.ipm_autotune(ctx, None, 1e-8, 1e-8, 1, stream=0) == lib.IPM_ERR_NOT_ANALYSED
+    lib.ipm_destroy(ctx)

@@ -558,3 +558,24 @@ def test_autotune_choices_keep_the_factor(pkg):
     s.solve(r7, r1)
     assert s.status() >= 0 and s.info()["omega"] <= 1e-12
     s.close()
+
+
+@pytest.mark.parametrize("order", ["ND", "AMD"])
+def test_launch_shapes_give_identical_factors(pkg, order):
+    """Every launch shape the autotuner can choose (small-front CTA widths,
+    level kernel on every level or on none) computes each entry with the same
+    operations in the same order: the factors agree bit for bit."""
+    lp = synth.grid_multicommodity(24, 4)
+    theta = synth.theta_loguniform(lp.n, 91)
+    s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND if order == "ND" else pkg.IPM_ORD_AMD)
+    s.factorise(theta, RHO, DELTA)
+    assert s.status() >= 0
+    ref = s.factor()
+    for widths in ((32, 64, 128), (64, 128, 256), (256, 256, 256), (32, 32, 32)):
+        for ratio in (0.0, 1e30):
+            assert pkg.ipm_set_launch_shapes(s.ctx, widths, ratio) == 0
+            s.factorise(theta, RHO, DELTA)
+            assert s.status() >= 0
+            for a, b in zip(ref, s.factor()):
+                assert np.array_equal(a, b), (widths, ratio)
+    s.close()
