@@ -106,8 +106,9 @@ struct ipm_ctx {
     TileItem *tile_items = nullptr, *tc_items = nullptr, *alt_items = nullptr;
     FactorItem *lvl_items = nullptr;  // persistent level kernel: items of all levels
     InvItem *inv_items = nullptr;     // diagonal blocks inverted after each factorisation
+    InvItem *pair_items = nullptr;    // blocks of multi-block supernodes (neighbour products)
     double *linv = nullptr;
-    int32_t ninv = 0;
+    int32_t ninv = 0, npairs = 0;
     int32_t *lvl_sync = nullptr;      // its ticket and counters (1 + max counters of a level)
     int32_t lvl_grid = 1;  // CTAs of the level kernel: every SM full
     // choices of ipm_autotune: threads per small-front CTA by size class
@@ -474,14 +475,20 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
     // with several blocks, and the block of a supernode with children and
     // k >= 16.  Their substitutions lie on the sweeps' dependency chains;
     // the leaves, off them, keep the substitution.
-    std::vector<InvItem> inv_items;
-    int64_t ninv = 0;
+    // A supernode with several blocks also keeps, per block, the products of
+    // X_b with its neighbouring blocks of L11 (3 x 1024 doubles per block).
+    std::vector<InvItem> inv_items, pair_items;
+    int64_t ninv = 0;  // doubles
     for (int32_t s = 0; s < ns; s++) {
         SolveNode &nd = nodes[s];
         if (!(nd.nblk > 1 || (nd.nchild > 0 && nd.k >= 16))) continue;
-        nd.inv = ninv * 1024;
-        for (int32_t b = 0; b < nd.nblk; b++) inv_items.push_back({s, b, (ninv + b) * 1024});
-        ninv += nd.nblk;
+        const int64_t stride = nd.nblk > 1 ? 3072 : 1024;
+        nd.inv = ninv;
+        for (int32_t b = 0; b < nd.nblk; b++) {
+            inv_items.push_back({s, b, ninv + b * stride});
+            if (nd.nblk > 1) pair_items.push_back({s, b, ninv + b * stride});
+        }
+        ninv += nd.nblk * stride;
     }
     const int64_t nrows = P.sn_rptr[ns];
     std::vector<int64_t> grp(nrows + 1, 0);
@@ -563,9 +570,11 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
     if ((rc = dupload(c, &d_nodes, nodes)) || (rc = dupload(c, &d_grp, grp)) || (rc = dupload(c, &d_gsrc, gsrc)) ||
         (rc = dupload(c, &d_fwd, fwd)) || (rc = dupload(c, &d_bwd, bwd)) || (rc = dalloc(c, &d_yv, (size_t)P.N)) ||
         (rc = dupload(c, &d_fleaf, fleaf)) || (rc = dupload(c, &d_bleaf, bleaf)) ||
-        (rc = dupload(c, &c->inv_items, inv_items)) || (rc = dalloc(c, &c->linv, (size_t)ninv * 1024)))
+        (rc = dupload(c, &c->inv_items, inv_items)) || (rc = dupload(c, &c->pair_items, pair_items)) ||
+        (rc = dalloc(c, &c->linv, (size_t)ninv)))
         return rc;
     c->ninv = (int32_t)inv_items.size();
+    c->npairs = (int32_t)pair_items.size();
     SolveSched &S = c->sched;
     S.node = d_nodes;
     S.sn_rows = d_rows;
@@ -1175,8 +1184,8 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
     cudaStreamWaitEvent(st, c->dep_ev[nev - 1], 0);
     if (c->ninv > 0) {
         Prof pr(c, IPM_K_OTHER, Work(), st);
-        launch_diag_inverse(c->sched, c->fronts, c->linv, c->inv_items, c->ninv, st);
-        nl++;
+        launch_diag_inverse(c->sched, c->fronts, c->linv, c->inv_items, c->ninv, c->pair_items, c->npairs, st);
+        nl += c->npairs > 0 ? 2 : 1;
     }
     {
         Prof pr(c, IPM_K_OTHER, Work(), st);

@@ -113,7 +113,7 @@ struct SolveNode {
     int64_t off;    // slab offset (doubles)
     int64_t upd;    // offset of its contribution vector
     int64_t rptr;   // first entry in sn_rows and gat_rp
-    int64_t inv;    // inverses of its diagonal blocks in SolveSched::Linv (32 x 32 each), -1: none
+    int64_t inv;    // inverses of its diagonal blocks in SolveSched::Linv, -1: none (layout: block_slot)
     int32_t f, k, ld, c0;
     int32_t parent, nchild, nrect, nblk;  // nblk: items of L11 (32-column blocks; 1 when unsplit)
 };
@@ -211,7 +211,7 @@ void launch_forward(const DevPlan &P, const double *fronts, const double *D, dou
 void launch_backward(const DevPlan &P, const double *fronts, double *x, const int32_t *list, int32_t count,
                      int32_t maxf, cudaStream_t st);
 void launch_diag_inverse(const SolveSched &S, const double *fronts, double *Linv, const InvItem *items,
-                         int32_t count, cudaStream_t st);
+                         int32_t count, const InvItem *pairs, int32_t npairs, cudaStream_t st);
 void launch_forward_persistent(const SolveSched &S, const double *fronts, const double *Dinv, double *x, double *upd,
                                int32_t maxf, int32_t grid, DevCtl *ctl, cudaStream_t st,
                                const int32_t *skip = nullptr);

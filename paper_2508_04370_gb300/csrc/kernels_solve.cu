@@ -277,6 +277,59 @@ __global__ void __launch_bounds__(32 * kInvWarps) k_diag_inverse(SolveSched S, c
     for (int j = 0; j < 32; j++) X[32 * j + lane] = Xs[wl][lane][j];
 }
 
+// Diagonal-block storage in Linv: a supernode with one block keeps its X
+// (1024 doubles); one with several keeps, per block b, X_b, then
+// W_b = X_b L_{b,b-1} (b >= 1) and V_b = L_{b+1,b} X_b (b + 1 < nblk), each
+// 32 x 32 column-major, 3072 doubles per block.
+__device__ __forceinline__ int64_t block_slot(const SolveNode &nd, int b) {
+    return nd.inv + (int64_t)b * (nd.nblk > 1 ? 3072 : 1024);
+}
+
+// W_b and V_b of one block of a multi-block supernode (one CTA of 256
+// threads, four outputs of each product per thread, 32 FMAs each), after
+// k_diag_inverse has formed X_b.  With them the sweeps take the last
+// dependency of a block (the neighbouring block finished just before) with
+// one product: forward y_b = X_b v' - W_b y_{b-1}, backward
+// z_b = X_b^T z'' - V_b^T z_{b+1}, where v' and z'' hold everything else.
+__global__ void __launch_bounds__(256) k_pair_products(SolveSched S, const double *__restrict__ fronts,
+                                                       double *__restrict__ Linv, const InvItem *__restrict__ items,
+                                                       int count) {
+    __shared__ double Xs[32][33];  // [row][column] of X_b
+    __shared__ double Ls[32][33];  // [row][column] of the neighbouring L block
+    const int tid = threadIdx.x;
+    const InvItem it = items[blockIdx.x];
+    const SolveNode nd = S.node[it.s];
+    const int b = it.b, k = nd.k, ld = nd.ld;
+    const double *L = fronts + nd.off;
+    double *X = Linv + it.dst;
+    for (int q = tid; q < 1024; q += 256) Xs[q & 31][q >> 5] = X[q];
+    for (int pass = 0; pass < 2; pass++) {
+        // pass 0: W_b = X_b L_{b,b-1} (rows 32b.., columns 32(b-1)..);
+        // pass 1: V_b = L_{b+1,b} X_b (rows 32(b+1).., columns 32b..)
+        if (pass == 0 && b == 0) continue;
+        if (pass == 1 && b + 1 >= nd.nblk) continue;
+        const int r0 = pass == 0 ? 32 * b : 32 * (b + 1), cbase = pass == 0 ? 32 * (b - 1) : 32 * b;
+        __syncthreads();
+        for (int q = tid; q < 1024; q += 256) {
+            const int i = q & 31, j = q >> 5;  // L row r0 + i, column cbase + j
+            Ls[i][j] = r0 + i < k ? L[(int64_t)(cbase + j) * ld + r0 + i] : 0.0;
+        }
+        __syncthreads();
+        double *out = X + (pass == 0 ? 1024 : 2048);
+        const int i = tid & 31;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int j = (tid >> 5) + 8 * c;
+            double a = 0.0;
+            if (pass == 0)
+                for (int t = 0; t < 32; t++) a += Xs[i][t] * Ls[t][j];
+            else
+                for (int t = 0; t < 32; t++) a += Ls[i][t] * Xs[t][j];
+            out[32 * j + i] = a;
+        }
+    }
+}
+
 // Leaves of the elimination tree with one block and f <= 32 (most of the
 // supernodes of a nested-dissection or AMD tree) are processed one per
 // warp, eight to a ticket (a leaf group), lane i = front row i.  Each
@@ -383,12 +436,33 @@ __device__ __forceinline__ void apply_inverse_backward(const double *Lb, double 
     if (warp == 0 && lane < w) z[lane] = ((part[0][lane] + part[1][lane]) + part[2][lane]) + part[3][lane];
 }
 
+// t[0:w) -= M u (transpose = false) or M^T u (transpose = true) for the
+// 32 x 32 product M staged in Mb (Mb[j * 33 + i] = M_ij) and the neighbour
+// block's finished values u[0:32): warps 0-3 each sum eight terms, warp 0
+// adds the four partial sums in warp order.  CTA barriers inside.
+__device__ __forceinline__ void apply_pair(const double *Mb, double *t, const double *u, double (*part)[33], int w,
+                                           bool transpose) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 4) {
+        double a = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const int q = 8 * warp + c;
+            a += (transpose ? Mb[lane * 33 + q] : Mb[q * 33 + lane]) * u[q];
+        }
+        part[warp][lane] = a;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < w) t[lane] -= ((part[0][lane] + part[1][lane]) + part[2][lane]) + part[3][lane];
+}
+
 __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched S, const double *__restrict__ fronts,
                                                                        const double *__restrict__ Dinv,
                                                                        double *__restrict__ x, double *upd,
                                                                        DevCtl *ctl, const int32_t *skip) {
     extern __shared__ double v[];
     __shared__ double Lb[32 * 33];
+    __shared__ double Wb[32 * 33];  // W_b of a multi-block supernode
     __shared__ double part[8][33];
     __shared__ double ys[2][32];
     __shared__ SolveItem sh_it;
@@ -412,9 +486,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
         if (it.r < 0) {
             const int b = -1 - it.r, b0 = 32 * b, w = min(32, k - b0);
             const bool inv = nd.inv >= 0;
+            const bool pair = inv && b > 0 && nd.nblk > 1;  // last dependency through W_b
             // loads that do not depend on other items go out before the wait
-            if (inv) stage_inverse(Lb, S.Linv + nd.inv + 1024 * b, w);
+            if (inv) stage_inverse(Lb, S.Linv + block_slot(nd, b), w);
             else stage_diag(Lb, L, ld, b0, w);
+            if (pair) stage_inverse(Wb, S.Linv + block_slot(nd, b) + 1024, 32);
             const int nr = single ? f : w;  // rows this item gathers
             int64_t e0 = 0, e1 = 0, g[4] = {0, 0, 0, 0};
             double a0 = 0.0, dinv = 0.0;
@@ -440,10 +516,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
                 v[tid] = a;
             }
             for (int t = tid + kSolveThreads; t < nr; t += kSolveThreads) v[t] = gather_row(S, nd, x, upd, t);
-            if (b > 0) {
-                // fan-in of the finished blocks b' < b: warp w applies columns 4w..4w+3 of each
+            if (b > (pair ? 1 : 0)) {
+                // fan-in of the finished blocks b' < b (b' < b - 1 with W_b): warp w
+                // applies columns 4w..4w+3 of each
                 double acc = 0.0;
-                for (int bp = 0; bp < b; bp++) {
+                for (int bp = 0; bp < b - (pair ? 1 : 0); bp++) {
                     if (tid == 0) wait_count(&tcnt[s], bp + 1, ctl, S.spin_limit);
                     __syncthreads();
                     if (tid < 32) ys[bp & 1][tid] = __ldcg(S.yv + c0 + 32 * bp + tid);
@@ -469,6 +546,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
             if (inv) apply_inverse_forward(Lb, v, part, w);
             else if (warp == 0) diag_forward(Lb, v, w);
             __syncthreads();
+            if (pair) {
+                // y_b = X_b v' - W_b y_{b-1}, y_{b-1} being the last block to finish
+                if (tid == 0) wait_count(&tcnt[s], b, ctl, S.spin_limit);
+                __syncthreads();
+                if (tid < 32) ys[0][tid] = __ldcg(S.yv + c0 + 32 * (b - 1) + tid);  // block b - 1 is full
+                __syncthreads();
+                apply_pair(Wb, v, ys[0], part, w, false);
+                __syncthreads();
+            }
             if (single) {
                 for (int i = w + tid; i < f; i += kSolveThreads) {
                     double acc = 0.0;
@@ -536,6 +622,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
                                                                         double *x, DevCtl *ctl, const int32_t *skip) {
     extern __shared__ double z[];  // [0, 32): the block; [32, 32 + f - k): x of the rows below
     __shared__ double Lb[32 * 33];
+    __shared__ double Wb[32 * 33];  // V_b of a multi-block supernode
     __shared__ double part[8][33];
     __shared__ double zs[2][32];
     __shared__ SolveItem sh_it;
@@ -561,8 +648,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
         // independent of other items: the diagonal block (or its inverse) and
         // this block's values after the forward sweep
         const bool inv = nd.inv >= 0;
-        if (inv) stage_inverse(Lb, S.Linv + nd.inv + 1024 * b, w);
+        const bool pair = inv && nd.nblk > 1 && b + 1 < nd.nblk;  // last dependency through V_b
+        if (inv) stage_inverse(Lb, S.Linv + block_slot(nd, b), w);
         else stage_diag(Lb, L, ld, b0, w);
+        if (pair) stage_inverse(Wb, S.Linv + block_slot(nd, b) + 2048, 32);
         const double xb = (tid < w) ? __ldcg(x + c0 + b0 + tid) : 0.0;
         if (tid == 0 && nrr > 0) wait_count(&flag[nd.parent], 1, ctl, S.spin_limit);
         __syncthreads();
@@ -577,7 +666,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
             const double *Lc = L + (int64_t)(b0 + lane) * ld + k;
             for (int t = t0; t < t1; t++) acc += Lc[t] * z[32 + t];
         }
-        for (int bp = nd.nblk - 1; bp > b; bp--) {
+        for (int bp = nd.nblk - 1; bp > b + (pair ? 1 : 0); bp--) {
             if (tid == 0) wait_count(&tcnt[s], nd.nblk - bp, ctl, S.spin_limit);
             __syncthreads();
             const int wp = min(32, k - 32 * bp);
@@ -602,6 +691,16 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
         if (inv) apply_inverse_backward(Lb, z, part, w);
         else if (warp == 0) diag_backward(Lb, z, w);
         __syncthreads();
+        if (pair) {
+            // z_b = X_b^T z'' - V_b^T z_{b+1}, z_{b+1} being the last block to finish
+            if (tid == 0) wait_count(&tcnt[s], nd.nblk - (b + 1), ctl, S.spin_limit);
+            __syncthreads();
+            const int wn = min(32, k - 32 * (b + 1));  // block b + 1 may be the last, partial one
+            if (tid < 32) zs[0][tid] = tid < wn ? __ldcg(x + c0 + 32 * (b + 1) + tid) : 0.0;
+            __syncthreads();
+            apply_pair(Wb, z, zs[0], part, w, true);
+            __syncthreads();
+        }
         for (int q = tid; q < w; q += kSolveThreads) __stcg(x + c0 + b0 + q, z[q]);
         __threadfence();
         __syncthreads();
@@ -760,9 +859,10 @@ void launch_backward(const DevPlan &P, const double *fronts, double *x, const in
 const void *persistent_probe_kernel() { return (const void *)k_forward_persistent; }
 
 void launch_diag_inverse(const SolveSched &S, const double *fronts, double *Linv, const InvItem *items,
-                         int32_t count, cudaStream_t st) {
+                         int32_t count, const InvItem *pairs, int32_t npairs, cudaStream_t st) {
     if (count <= 0) return;
     k_diag_inverse<<<(count + kInvWarps - 1) / kInvWarps, 32 * kInvWarps, 0, st>>>(S, fronts, Linv, items, count);
+    if (npairs > 0) k_pair_products<<<npairs, 256, 0, st>>>(S, fronts, Linv, pairs, npairs);
 }
 
 void launch_forward_persistent(const SolveSched &S, const double *fronts, const double *Dinv, double *x, double *upd,
