@@ -16,7 +16,7 @@ batch512 (512 independent random LPs per GPU as one forest; with N GPUs the
 512 N instances are sharded over the ranks, no data exchange).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload NAME] [--paths fp64,mixed] [--no-cpu-baseline]
+                       [--workload NAME] [--paths fp64,mixed] [--no-cpu-baseline] [--autotune-reps R]
 Prints one JSON line on rank 0.
 """
 from __future__ import annotations
@@ -226,7 +226,8 @@ def run_ours(args, W, rank, world):
         # after one step so that the mixed path tunes the precision it keeps
         # (setup, like the analysis; not timed)
         step(0)
-        tune = s.autotune(th[0], RHO, DELTA, reps=W.tune_reps)
+        reps = W.tune_reps if args.autotune_reps is None else args.autotune_reps
+        tune = s.autotune(th[0], RHO, DELTA, reps=reps) if reps > 0 else {"skipped": True}
 
         for i in range(args.warmup):
             step(i)
@@ -432,6 +433,9 @@ def main():
     ap.add_argument("--workload", default="grid64_q4",
                     choices=["grid64_q4", "random_300x800", "staircase", "staircase10", "batch512"])
     ap.add_argument("--paths", default="fp64,mixed", help="comma-separated subset of fp64,mixed")
+    ap.add_argument("--autotune-reps", type=int, default=None,
+                    help="repetitions per autotuner candidate (0: keep the library's default launch shapes, "
+                         "e.g. for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
