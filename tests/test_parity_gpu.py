@@ -48,8 +48,10 @@ def pkg():
     return p
 
 
-def run_pair(pkg, lp, theta, r7, r1, ordering=0, user_perm=None, **opts):
+def run_pair(pkg, lp, theta, r7, r1, ordering=0, user_perm=None, tune=False, **opts):
     s = pkg.Solver.from_lp(lp, ordering=ordering, user_perm=user_perm, **opts)
+    if tune:
+        s.autotune(theta, RHO, DELTA, reps=1)
     s.factorise(theta, RHO, DELTA)
     dx, dy = s.solve(r7, r1)
     info = s.info()
@@ -296,12 +298,17 @@ def test_host_entry_point_matches_device_path(pkg):
     s.close()
 
 
-def test_full_size_grid64_q4(pkg):
+@pytest.mark.parametrize("order", ["AMD", "ND"])
+def test_full_size_grid64_q4(pkg, order):
+    """The bench's workload at full size (the bench orders it by nested
+    dissection), in the bench's launch configuration: the autotuner's shapes
+    (which change no bit of the factor) and the default solve path."""
     lp = synth.by_name("grid64_q4", 1)
     theta = synth.theta_loguniform(lp.n, 1)
-    r = run_pair(pkg, lp, theta, synth.rhs_normal(lp.n, 1), synth.rhs_normal(lp.m, 2))
+    r = run_pair(pkg, lp, theta, synth.rhs_normal(lp.n, 1), synth.rhs_normal(lp.m, 2),
+                 ordering=pkg.IPM_ORD_AMD if order == "AMD" else pkg.IPM_ORD_ND, tune=True)
     err = check_pair(r, lp)
-    print(f"grid64_q4: rel err {err:.2e} omega {r['w_gpu']:.2e} steps {r['info']['refine_steps']}")
+    print(f"grid64_q4 {order}: rel err {err:.2e} omega {r['w_gpu']:.2e} steps {r['info']['refine_steps']}")
     r["s"].close()
 
 
