@@ -210,9 +210,14 @@ int ipm_factorise(ipm_ctx *ctx, const double *theta_dev, double rho, double delt
 /* Solve K [dx; dy] = [r7; r1] with the last factorisation, followed by
  * iterative refinement on the regularised K (Sec. 4.5) until the
  * component-wise backward error is <= omega_target, refine_max steps were
- * taken, or a step fails to halve it.  All pointers device: r7, dx have n
- * entries, r1, dy have m.  Inputs and outputs may not alias.  Enqueued on
- * `stream`, no synchronisation. */
+ * taken, or a step fails to halve it; then, for an FP64 factor still above
+ * the target, up to gmres_restarts cycles of GMRES(8) preconditioned by the
+ * factor, and for a tensor-core factor an FP64 refactorisation and a second
+ * solve (the mixed path's fallback).  All pointers device: r7, dx have n
+ * entries, r1, dy have m.  Inputs and outputs may not alias.  The decisions
+ * are taken on the host: the call synchronises `stream` once per refinement
+ * step (ipm_graph_capture gives the device-driven version without host
+ * synchronisation). */
 int ipm_solve(ipm_ctx *ctx, const double *r7_dev, const double *r1_dev, double *dx_dev, double *dy_dev,
               void *stream);
 
@@ -326,13 +331,15 @@ int ipm_set_launch_shapes(ipm_ctx *ctx, const int32_t *small_threads, double lev
 /* Kernel classes reported by ipm_kernel_stats. */
 #define IPM_K_SMALL_FRONTS 0   /* fused assemble+factorise of fronts f <= 128 (shared memory) */
 #define IPM_K_LARGE_ASSEMBLE 1 /* extend-add into large fronts */
-#define IPM_K_LARGE_PANEL 2    /* pivot block + triangular solve of a 32-column panel */
+#define IPM_K_LARGE_PANEL 2    /* pivot block + triangular solve of a 32-column panel; the persistent
+                                  level kernel (all large-front work of a level) is counted here */
 #define IPM_K_LARGE_UPDATE 3   /* trailing (Schur-complement) update, FP64 */
 #define IPM_K_LARGE_UPDATE_TC 4 /* trailing update on tensor cores (mixed precision) */
-#define IPM_K_FORWARD 5        /* forward + diagonal solve of one tree level */
-#define IPM_K_BACKWARD 6       /* backward solve of one tree level */
+#define IPM_K_FORWARD 5        /* forward + diagonal solve (one persistent sweep) */
+#define IPM_K_BACKWARD 6       /* backward solve (one persistent sweep) */
 #define IPM_K_RESIDUAL 7       /* residual, |K||x|, |K|e and backward error */
-#define IPM_K_OTHER 8          /* norms, statistics, permutations, vector updates */
+#define IPM_K_OTHER 8          /* norms, statistics, permutations, vector updates, diagonal-block
+                                  inverses for the solves */
 #define IPM_K_COUNT 9
 
 typedef struct ipm_kernel_stat {
