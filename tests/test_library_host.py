@@ -244,3 +244,24 @@ def test_launch_shapes_validation(lib):
     assert lib.ipm_set_launch_shapes(ctx, None, float("nan")) == lib.IPM_ERR_INVALID_ARG
     assert lib.ipm_autotune(ctx, None, 1e-8, 1e-8, 1, stream=0) == lib.IPM_ERR_NOT_ANALYSED
     lib.ipm_destroy(ctx)
+
+
+def test_nested_dissection_deterministic_with_bounded_fill(lib):
+    """Nested dissection (ratio-scored level cuts, minimum vertex covers of
+    the cut edges, vertex Fiduccia-Mattheyses refinement) is deterministic,
+    gives a permutation, and on a grid LP fills within a small factor of AMD
+    and far below the natural order."""
+    lp = synth.grid_multicommodity(24, 3)
+    perms, nnz = [], {}
+    for ordering in (1, 1, 0, 3):
+        ctx, rc = _analyse(lib, lp, ordering)
+        assert rc == 0
+        rc, info = lib.ipm_get_info(ctx)
+        nnz[ordering] = info.nnz_L
+        if ordering == 1:
+            perms.append(lib.ipm_get_symbolic(ctx)["perm"])
+        lib.ipm_destroy(ctx)
+    assert np.array_equal(perms[0], perms[1])
+    assert np.array_equal(np.sort(perms[0]), np.arange(lp.m + lp.n))
+    assert nnz[1] < 2.0 * nnz[0]
+    assert nnz[1] < nnz[3] / 3
