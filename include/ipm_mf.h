@@ -301,7 +301,8 @@ int ipm_solve_noalloc(ipm_ctx *ctx, const double *r7_dev, const double *r1_dev, 
 /* Autotuner for the launch shapes of the factorisation (the batching and
  * tiling the paper's CPU scheme leaves to the implementation, Sec. 4.3):
  * factorises `reps` + 1 times per candidate on `stream` with the given Theta
- * (device, n doubles), rho and delta, and keeps, by coordinate descent,
+ * (device, n doubles), rho and delta, and keeps, by coordinate descent (a
+ * candidate must be at least 2% faster than the incumbent, by the median),
  *   - the level-kernel threshold: a tree level runs its large fronts in one
  *     persistent launch when their FP64 work at 1 TFLOP/s is below ratio x
  *     (35 us per 32-column panel of its widest front); candidates 0 (never),

@@ -1516,9 +1516,11 @@ int ipm_factorise(ipm_ctx *c, const double *theta_dev, double rho, double delta,
 // Autotuner (the batching of Sec. 4.3 leaves the per-bucket launch shapes
 // open): times factorisations of the context's own problem on the device
 // and keeps, by coordinate descent, the level-kernel threshold and the CTA
-// width of each small-front size class that give the shortest time.  No
-// choice changes the arithmetic of any entry, so the factors stay the same
-// bit for bit.
+// width of each small-front size class that give the shortest time; a
+// candidate replaces the incumbent only when at least 2% faster, so that
+// timing noise does not move the choice.  No choice changes the arithmetic
+// of any entry, so the factors stay the same bit for bit.
+constexpr double kTuneMargin = 0.98;
 int ipm_autotune(ipm_ctx *c, const double *theta_dev, double rho, double delta, int32_t reps, void *stream) {
     int rc = check_ctx(c);
     if (rc) return rc;
@@ -1561,7 +1563,7 @@ int ipm_autotune(ipm_ctx *c, const double *theta_dev, double rho, double delta, 
             c->tune_ratio = r;
             double ms;
             if ((rc = measure(ms))) goto done;
-            if (ms < best) {
+            if (ms < best * kTuneMargin) {
                 best = ms;
                 pick = r;
             }
@@ -1577,7 +1579,7 @@ int ipm_autotune(ipm_ctx *c, const double *theta_dev, double rho, double delta, 
                 c->tune_threads[b] = w;
                 double ms;
                 if ((rc = measure(ms))) goto done;
-                if (ms < best) {
+                if (ms < best * kTuneMargin) {
                     best = ms;
                     keep = w;
                 }
