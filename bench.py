@@ -354,10 +354,21 @@ class _OracleProblem:
 
 def oracle_problems(W, pkg):
     """The workload's problems for the oracle, in the library's order
-    (batches: per instance, the batch order restricted to it)."""
-    s = W.solver(pkg)
-    perm = s.symbolic()["perm"]
-    s.close()
+    (batches: per instance, the batch order restricted to it).  The order
+    comes from the library's host-side analysis (no GPU needed)."""
+    ctx = pkg.ipm_create(pkg.ipm_default_options())
+    if W.lps is None:
+        rc = pkg.ipm_analyse(ctx, W.lp.m, W.lp.n, W.lp.colptr, W.lp.rowidx, pkg.IPM_FORM_AUGMENTED, W.ordering(pkg))
+    else:
+        rc = pkg.ipm_analyse_batch(ctx, np.array([lp.m for lp in W.lps], np.int32),
+                                   np.array([lp.n for lp in W.lps], np.int32),
+                                   np.concatenate([np.asarray(lp.colptr, np.int64) for lp in W.lps]),
+                                   np.concatenate([np.asarray(lp.rowidx, np.int32) for lp in W.lps]),
+                                   W.ordering(pkg))
+    if rc:
+        raise RuntimeError(f"analysis failed ({rc})")
+    perm = pkg.ipm_get_symbolic(ctx)["perm"]
+    pkg.ipm_destroy(ctx)
     if W.lps is None:
         return [_OracleProblem(W.lp, perm, W.thetas, W.rhs, 1.0)]
     out = []
