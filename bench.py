@@ -174,7 +174,8 @@ class ClockSampler:
 
 def traffic_for(kernel):
     """Per-launch DRAM bytes of a kernel class from a committed ncu summary,
-    valid only while the kernel source is unchanged."""
+    valid only while every source it depends on (the kernel, and the
+    ordering that shapes the workload's tree) is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -184,13 +185,15 @@ def traffic_for(kernel):
     ent = table.get(kernel)
     if not ent:
         return None
-    src = os.path.join(ROOT, ent["source"])
-    try:
-        with open(src, "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()[:16]
-    except OSError:
-        return None
-    return ent["bytes_per_launch"] if sha == ent["source_sha"] else None
+    for rel, want in ent["sources"].items():
+        try:
+            with open(os.path.join(ROOT, rel), "rb") as fh:
+                sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+        except OSError:
+            return None
+        if sha != want:
+            return None
+    return ent["bytes_per_launch"]
 
 
 # ------------------------------------------------------------- our arm

@@ -32,7 +32,7 @@ def _compile(src: str, extra: list[str]) -> str:
     path = os.path.join(CSRC, src)
     cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3", "-c", path, "-o", out, *extra]
     if src.endswith(".cpp"):
-        cmd = [_nvcc(), "-x", "c++", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O3", "-c", path, "-o", out]
+        cmd = [_nvcc(), "-x", "c++", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-pthread", "-c", path, "-o", out]
     subprocess.run(cmd, check=True)
     return out
 
@@ -56,7 +56,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.run([_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs], check=True)
+    subprocess.run([_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread"], check=True)
     os.replace(tmp, LIB)
     if verbose:
         print(f"built {LIB}")

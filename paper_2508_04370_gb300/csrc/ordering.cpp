@@ -6,15 +6,19 @@
 //       d_i <- min( n_left - |i|,  d_i + |L_p \ i|,  |A_i \ i| + |L_p \ i| + sum_{e in E_i \ p} |L_e \ L_p| ),
 //   aggressive element absorption (|L_e \ L_p| = 0), supervariable detection
 //   by hashing, and dense rows (degree > max(16, f*sqrt(N))) ordered last.
-// order_nd: nested dissection by recursive vertex separators taken from
-//   breadth-first level structures rooted at a pseudo-peripheral vertex and
-//   improved by vertex Fiduccia-Mattheyses refinement; subgraphs below the
-//   leaf size are ordered with order_amd.  The paper uses Metis (Sec. 4.2);
-//   this is a self-contained replacement.
+// order_nd: nested dissection by recursive vertex separators; each subgraph
+//   takes the best (separator / side x side) of a separator from
+//   breadth-first level structures and multilevel separators (heavy-edge
+//   coarsening, separators grown on the coarsest graph, vertex
+//   Fiduccia-Mattheyses refinement on the way back), computed on worker
+//   threads; subgraphs below the leaf size are ordered with order_amd.  The
+//   paper uses Metis (Sec. 4.2); this is a self-contained replacement.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <numeric>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "ipm_plan.h"
@@ -391,35 +395,39 @@ int64_t cover_separator(const Graph &h, const std::vector<int8_t> &side, std::ve
 // Vertex-separator refinement (Fiduccia-Mattheyses moves on a vertex
 // separator, the node-based refinement of multilevel nested dissection):
 // moving a separator vertex v into side a pulls its neighbours on the other
-// side into the separator, so the separator changes by
-// |N(v) on the other side| - 1.  A pass repeatedly makes the best admissible
+// side b into the separator, so the separator changes by w(N(v) on b) - w(v)
+// (w = 1 without vertex weights; with weights vw, the number of vertices a
+// coarse vertex stands for).  A pass repeatedly makes the best admissible
 // move (each vertex moves out of the separator at most once per pass; moves
 // that do not shrink the separator are allowed), then rolls back to the
-// smallest separator it saw.  part[v]: 0 separator, 1 or 2 a side.  The
-// larger side stays within max(its initial share, 60%) of both sides.
-void refine_separator(const Graph &h, std::vector<int8_t> &part, int max_passes) {
+// smallest separator it saw; it gives up after min(max(n/100, 15), 100) moves
+// without a new best.  The weight of each vertex's neighbours on either side
+// is kept up to date, so a move costs its neighbours' degrees.  part[v]: 0
+// separator, 1 or 2 a side.  The larger side stays within max(its initial
+// share, 60%) of both sides.
+void refine_separator(const Graph &h, std::vector<int8_t> &part, int max_passes,
+                      const std::vector<int32_t> *vw = nullptr) {
     const int32_t n = h.N;
+    auto wt = [&](int32_t v) -> int64_t { return vw ? (*vw)[v] : 1; };
     int64_t cnt[3] = {0, 0, 0};
-    for (int32_t v = 0; v < n; v++) cnt[part[v]]++;
+    for (int32_t v = 0; v < n; v++) cnt[part[v]] += wt(v);
     const double share = std::max(0.6, (double)std::max(cnt[1], cnt[2]) / (double)std::max<int64_t>(1, cnt[1] + cnt[2]));
+    const size_t patience = (size_t)std::min<int64_t>(std::max<int64_t>(n / 100, 15), 100);
     struct Mv {
         int32_t v;
         int8_t from, to;
     };
     struct Cand {
-        int32_t gain, v;
+        int64_t gain;
+        int32_t v;
         int8_t side;
         bool operator<(const Cand &o) const { return gain < o.gain || (gain == o.gain && v > o.v); }
     };
     std::vector<char> locked(n);
+    std::vector<int64_t> conn(2 * (size_t)n);  // conn[2v + s - 1]: weight of v's neighbours on side s
     std::vector<Mv> log;
     std::vector<Cand> heap;
-    auto gain_of = [&](int32_t v, int8_t a) {
-        const int8_t b = (int8_t)(3 - a);
-        int32_t k = 0;
-        for (int64_t p = h.ptr[v]; p < h.ptr[v + 1]; p++) k += part[h.adj[p]] == b;
-        return 1 - k;
-    };
+    auto gain_of = [&](int32_t v, int8_t a) { return wt(v) - conn[2 * (size_t)v + (2 - a)]; };
     auto push = [&](int32_t v) {
         if (part[v] != 0 || locked[v]) return;
         for (int8_t a = 1; a <= 2; a++) {
@@ -429,6 +437,12 @@ void refine_separator(const Graph &h, std::vector<int8_t> &part, int max_passes)
     };
     for (int pass = 0; pass < max_passes; pass++) {
         std::fill(locked.begin(), locked.end(), 0);
+        std::fill(conn.begin(), conn.end(), 0);
+        for (int32_t v = 0; v < n; v++)
+            for (int64_t p = h.ptr[v]; p < h.ptr[v + 1]; p++) {
+                const int8_t s = part[h.adj[p]];
+                if (s) conn[2 * (size_t)v + s - 1] += wt(h.adj[p]);
+            }
         log.clear();
         heap.clear();
         for (int32_t v = 0; v < n; v++)
@@ -442,47 +456,295 @@ void refine_separator(const Graph &h, std::vector<int8_t> &part, int max_passes)
             heap.pop_back();
             if (part[c.v] != 0 || locked[c.v] || gain_of(c.v, c.side) != c.gain) continue;  // stale
             const int8_t a = c.side, b = (int8_t)(3 - a);
-            int64_t pulled = 0;
-            for (int64_t p = h.ptr[c.v]; p < h.ptr[c.v + 1]; p++) pulled += part[h.adj[p]] == b;
-            const int64_t ca = cnt[a] + 1, cb = cnt[b] - pulled;
+            const int64_t ca = cnt[a] + wt(c.v), cb = cnt[b] - conn[2 * (size_t)c.v + b - 1];
             if (cb <= 0 || (double)std::max(ca, cb) > share * (double)(ca + cb)) continue;
             part[c.v] = a;
             locked[c.v] = 1;
-            cnt[0]--;
-            cnt[a]++;
+            cnt[0] -= wt(c.v);
+            cnt[a] += wt(c.v);
             log.push_back({c.v, 0, a});
             for (int64_t p = h.ptr[c.v]; p < h.ptr[c.v + 1]; p++) {
                 const int32_t u = h.adj[p];
-                if (part[u] == b) {
-                    part[u] = 0;
-                    cnt[b]--;
-                    cnt[0]++;
-                    log.push_back({u, b, 0});
-                }
+                conn[2 * (size_t)u + a - 1] += wt(c.v);
+                push(u);  // a separator neighbour now pulls more when it moves to b
             }
-            // gains change for separator vertices next to v or to the pulled ones
             for (int64_t p = h.ptr[c.v]; p < h.ptr[c.v + 1]; p++) {
                 const int32_t u = h.adj[p];
+                if (part[u] != b) continue;
+                part[u] = 0;  // pulled into the separator
+                cnt[b] -= wt(u);
+                cnt[0] += wt(u);
+                log.push_back({u, b, 0});
+                for (int64_t q = h.ptr[u]; q < h.ptr[u + 1]; q++) {
+                    const int32_t z = h.adj[q];
+                    conn[2 * (size_t)z + b - 1] -= wt(u);
+                    push(z);
+                }
                 push(u);
-                if (part[u] == 0)
-                    for (int64_t q = h.ptr[u]; q < h.ptr[u + 1]; q++) push(h.adj[q]);
             }
             if (cnt[0] < best_sep) {
                 best_sep = cnt[0];
                 best_len = log.size();
             }
-            if (log.size() > best_len + 4 * 64) break;  // long enough without improvement
+            if (log.size() > best_len + patience) break;  // long enough without improvement
         }
         for (size_t t = log.size(); t > best_len; t--) {
             const Mv &m = log[t - 1];
-            cnt[m.to]--;
-            cnt[m.from]++;
+            cnt[m.to] -= wt(m.v);
+            cnt[m.from] += wt(m.v);
             part[m.v] = m.from;
         }
         if (best_sep >= start_sep) break;
     }
 }
 
+// Level-structure separator: breadth-first levels from a pseudo-peripheral
+// vertex; the few most promising cuts between consecutive levels get their
+// optimal vertex separator (cover_separator), the best by separator /
+// (side x side) is refined.  h must be connected with more than one level.
+bool level_separator(const Graph &h, std::vector<int8_t> &part, std::vector<int32_t> &level,
+                     std::vector<int32_t> &queue) {
+    const int32_t n = h.N;
+    level.assign(n, -1);
+    // pseudo-peripheral root
+    int32_t root = 0;
+    for (int32_t t = 1; t < n; t++)
+        if (h.ptr[t + 1] - h.ptr[t] < h.ptr[root + 1] - h.ptr[root]) root = t;
+    int32_t ecc = bfs_levels(h, root, level, queue);
+    for (int iter = 0; iter < 6; iter++) {
+        int32_t best = -1;
+        for (int32_t t = 0; t < n; t++)
+            if (level[t] == ecc && (best < 0 || h.ptr[t + 1] - h.ptr[t] < h.ptr[best + 1] - h.ptr[best])) best = t;
+        std::vector<int32_t> lv2(n);
+        int32_t e2 = bfs_levels(h, best, lv2, queue);
+        if (e2 <= ecc) break;
+        root = best;
+        ecc = e2;
+        level.swap(lv2);
+    }
+    if (ecc < 2) return false;
+    std::vector<int64_t> cnt(ecc + 2, 0);
+    for (int32_t t = 0; t < n; t++) cnt[level[t]]++;
+    // candidate separators: vertices of level l adjacent to level l+1
+    // ("low side") or of level l+1 adjacent to level l ("high side")
+    std::vector<int64_t> lo_sep(ecc + 1, 0), hi_sep(ecc + 1, 0);
+    {
+        std::vector<int8_t> adj_up(n, 0), adj_dn(n, 0);
+        for (int32_t v = 0; v < n; v++)
+            for (int64_t p = h.ptr[v]; p < h.ptr[v + 1]; p++) {
+                int32_t u = h.adj[p];
+                if (level[u] == level[v] + 1) adj_up[v] = 1;
+                if (level[u] == level[v] - 1) adj_dn[v] = 1;
+            }
+        for (int32_t v = 0; v < n; v++) {
+            if (adj_up[v]) lo_sep[level[v]]++;
+            if (adj_dn[v] && level[v] >= 1) hi_sep[level[v] - 1]++;
+        }
+    }
+    // candidate cuts between level l and l+1 with both sides at least 20% of
+    // the vertices; the cheap one-sided separator estimates rank them and
+    // the best few get their optimal vertex separator (minimum cover of
+    // the cut edges)
+    std::vector<std::pair<double, int32_t>> cands;
+    int64_t below = 0;
+    for (int32_t l = 0; l < ecc; l++) {
+        const int64_t left = below + cnt[l], right = n - left;
+        below += cnt[l];
+        const int64_t sep = std::min(lo_sep[l], hi_sep[l]);
+        if (std::min(left, right) - sep < (int64_t)(0.2 * n)) continue;
+        cands.push_back({(double)sep / ((double)(left - sep) * (double)(right - sep) + 1.0), l});
+    }
+    if (cands.empty()) return false;
+    std::sort(cands.begin(), cands.end());
+    if (cands.size() > 6) cands.resize(6);
+    std::vector<int8_t> trial, sidev(n);
+    part.clear();
+    double best_score = 1e300;
+    for (const auto &cd : cands) {
+        const int32_t l = cd.second;
+        for (int32_t v = 0; v < n; v++) sidev[v] = level[v] <= l ? 1 : 2;
+        const int64_t sep = cover_separator(h, sidev, trial);
+        int64_t c1 = 0;
+        for (int32_t v = 0; v < n; v++) c1 += trial[v] == 1;
+        const int64_t c2 = n - sep - c1;
+        if (c1 <= 0 || c2 <= 0) continue;
+        const double score = (double)sep / ((double)c1 * (double)c2);
+        if (score < best_score) {
+            best_score = score;
+            part.swap(trial);
+        }
+    }
+    if (part.empty()) return false;
+    refine_separator(h, part, 8);
+    return true;
+}
+
+// separator / (side x side) of a partition (0 separator, 1 or 2 a side);
+// +inf when a side is empty
+double separator_ratio(const std::vector<int8_t> &part) {
+    int64_t c[3] = {0, 0, 0};
+    for (int8_t p : part) c[p]++;
+    if (c[1] == 0 || c[2] == 0) return 1e300;
+    return (double)c[0] / ((double)c[1] * (double)c[2]);
+}
+
+// splitmix64: deterministic visit orders and seeds
+uint64_t next_random(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// One level of the multilevel scheme: a graph with edge weights (parallel to
+// g.adj: how many finer edges an edge stands for) and vertex weights (how many
+// original vertices a vertex stands for); cmap sends a vertex to its vertex
+// on the next coarser level.
+struct MLevel {
+    Graph g;
+    std::vector<int32_t> ew, vw, cmap;
+};
+
+// Heavy-edge matching: vertices in a shuffled order are paired with the
+// unmatched neighbour across their heaviest edge (ties: the lighter
+// neighbour), keeping coarse vertex weights <= max_vw; pairs and unmatched
+// vertices become the coarse vertices, parallel edges merge with summed
+// weights.  Returns false when the graph shrinks by less than 10%.
+bool coarsen(MLevel &f, MLevel &c, int64_t max_vw, uint64_t &rng) {
+    const int32_t n = f.g.N;
+    std::vector<int32_t> order(n), mate(n, -1);
+    std::iota(order.begin(), order.end(), 0);
+    for (int32_t i = n - 1; i > 0; i--) std::swap(order[i], order[(int32_t)(next_random(rng) % (uint64_t)(i + 1))]);
+    for (int32_t v : order) {
+        if (mate[v] >= 0) continue;
+        int32_t best = -1;
+        for (int64_t p = f.g.ptr[v]; p < f.g.ptr[v + 1]; p++) {
+            const int32_t u = f.g.adj[p];
+            if (mate[u] >= 0 || u == v || (int64_t)f.vw[v] + f.vw[u] > max_vw) continue;
+            if (best < 0 || f.ew[p] > f.ew[best] || (f.ew[p] == f.ew[best] && f.vw[u] < f.vw[f.g.adj[best]])) best = (int32_t)p;
+        }
+        if (best >= 0) {
+            mate[v] = f.g.adj[best];
+            mate[f.g.adj[best]] = v;
+        } else {
+            mate[v] = v;
+        }
+    }
+    f.cmap.assign(n, -1);
+    int32_t nc = 0;
+    for (int32_t v = 0; v < n; v++)
+        if (f.cmap[v] < 0) {
+            f.cmap[v] = nc;
+            f.cmap[mate[v]] = nc;
+            nc++;
+        }
+    if ((double)nc > 0.9 * (double)n) return false;
+    c.g.N = nc;
+    c.g.ptr.assign(nc + 1, 0);
+    c.g.adj.clear();
+    c.ew.clear();
+    c.vw.assign(nc, 0);
+    std::vector<int64_t> pos(nc, -1);
+    for (int32_t v = 0; v < n; v++) {
+        if (mate[v] < v) continue;  // the pair is built from its lower vertex, in coarse order
+        const int32_t cv = f.cmap[v];
+        const int64_t start = (int64_t)c.g.adj.size();
+        for (int t = 0; t < (mate[v] == v ? 1 : 2); t++) {
+            const int32_t w = t == 0 ? v : mate[v];
+            c.vw[cv] += f.vw[w];
+            for (int64_t p = f.g.ptr[w]; p < f.g.ptr[w + 1]; p++) {
+                const int32_t cu = f.cmap[f.g.adj[p]];
+                if (cu == cv) continue;
+                if (pos[cu] >= start) {
+                    c.ew[pos[cu]] += f.ew[p];
+                } else {
+                    pos[cu] = (int64_t)c.g.adj.size();
+                    c.g.adj.push_back(cu);
+                    c.ew.push_back(f.ew[p]);
+                }
+            }
+        }
+        c.g.ptr[cv + 1] = (int64_t)c.g.adj.size();
+    }
+    return true;
+}
+
+// Multilevel vertex separator of a connected graph h (the scheme of
+// multilevel nested dissection): coarsen by heavy-edge matching to about 100
+// vertices; on the coarsest graph grow breadth-first regions of half the
+// weight from several seeds, take the minimum vertex cover of each region's
+// cut edges and refine it by weighted moves, keeping the best by separator /
+// (side x side); project it back level by level (a coarse separator stays a
+// separator) with weighted refinement at each level.  run seeds the shuffles.
+bool multilevel_separator(const Graph &h, std::vector<int8_t> &part, int run) {
+    const int32_t n = h.N;
+    if (n < 16) return false;
+    std::vector<MLevel> lv(1);
+    lv[0].g = h;
+    lv[0].ew.assign(h.adj.size(), 1);
+    lv[0].vw.assign(n, 1);
+    constexpr int32_t kCoarsest = 100;
+    const int64_t max_vw = std::max<int64_t>(1, (int64_t)(1.5 * (double)n / kCoarsest));
+    uint64_t rng = 0x243F6A8885A308D3ull ^ (uint64_t)n ^ ((uint64_t)run << 40);
+    while (lv.back().g.N > kCoarsest && lv.size() < 40) {
+        MLevel c;
+        if (!coarsen(lv.back(), c, max_vw, rng)) break;
+        lv.push_back(std::move(c));
+    }
+    // initial separators on the coarsest graph
+    const MLevel &C = lv.back();
+    const int32_t nc = C.g.N;
+    int64_t total = 0;
+    for (int32_t w : C.vw) total += w;
+    std::vector<int8_t> best, side(nc), trial;
+    double best_score = 1e300;
+    std::vector<int32_t> level(nc), queue;
+    constexpr int kTrials = 8;
+    for (int t = 0; t < kTrials; t++) {
+        int32_t seed;
+        if (t == 0) {  // far end of a breadth-first search from vertex 0
+            bfs_levels(C.g, 0, level, queue);
+            seed = queue.back();
+        } else {
+            seed = (int32_t)(next_random(rng) % (uint64_t)nc);
+        }
+        std::fill(side.begin(), side.end(), 2);
+        bfs_levels(C.g, seed, level, queue);
+        int64_t w1 = 0;
+        for (size_t q = 0; q < queue.size() && 2 * w1 < total; q++) {
+            side[queue[q]] = 1;
+            w1 += C.vw[queue[q]];
+        }
+        if (w1 == 0 || w1 >= total) continue;
+        cover_separator(C.g, side, trial);
+        refine_separator(C.g, trial, 8, &C.vw);
+        int64_t c[3] = {0, 0, 0};
+        for (int32_t v = 0; v < nc; v++) c[trial[v]] += C.vw[v];
+        if (c[1] == 0 || c[2] == 0) continue;
+        const double score = (double)c[0] / ((double)c[1] * (double)c[2]);
+        if (score < best_score) {
+            best_score = score;
+            best.swap(trial);
+        }
+    }
+    if (best.empty()) return false;
+    // project back with refinement
+    for (int l = (int)lv.size() - 2; l >= 0; l--) {
+        const MLevel &F = lv[l];
+        std::vector<int8_t> fp(F.g.N);
+        for (int32_t v = 0; v < F.g.N; v++) fp[v] = best[F.cmap[v]];
+        refine_separator(F.g, fp, 8, &F.vw);
+        best.swap(fp);
+    }
+    int64_t c1 = 0, c2 = 0;
+    for (int8_t p : best) {
+        c1 += p == 1;
+        c2 += p == 2;
+    }
+    if (c1 == 0 || c2 == 0) return false;
+    part.swap(best);
+    return true;
+}
 }  // namespace
 
 std::vector<int32_t> order_nd(const Graph &g, int32_t leaf, double dense_factor) {
@@ -556,87 +818,39 @@ std::vector<int32_t> order_nd(const Graph &g, int32_t leaf, double dense_factor)
             for (int32_t c = ncomp - 1; c >= 0; c--) stack.push_back({std::move(parts[c]), false});
             continue;
         }
-        // pseudo-peripheral root
-        int32_t root = 0;
-        for (int32_t t = 1; t < n; t++)
-            if (h.ptr[t + 1] - h.ptr[t] < h.ptr[root + 1] - h.ptr[root]) root = t;
-        int32_t ecc = bfs_levels(h, root, level, queue);
-        for (int iter = 0; iter < 6; iter++) {
-            int32_t best = -1;
-            for (int32_t t = 0; t < n; t++)
-                if (level[t] == ecc && (best < 0 || h.ptr[t + 1] - h.ptr[t] < h.ptr[best + 1] - h.ptr[best])) best = t;
-            std::vector<int32_t> lv2(n);
-            int32_t e2 = bfs_levels(h, best, lv2, queue);
-            if (e2 <= ecc) break;
-            root = best;
-            ecc = e2;
-            level.swap(lv2);
-        }
-        if (ecc < 2) {
-            std::vector<int32_t> o = order_amd(h, 0.0);
-            for (int32_t t : o) order.push_back(vs[t]);
-            continue;
-        }
-        std::vector<int64_t> cnt(ecc + 2, 0);
-        for (int32_t t = 0; t < n; t++) cnt[level[t]]++;
-        // candidate separators: vertices of level l adjacent to level l+1
-        // ("low side") or of level l+1 adjacent to level l ("high side")
-        std::vector<int64_t> lo_sep(ecc + 1, 0), hi_sep(ecc + 1, 0);
-        {
-            std::vector<int8_t> adj_up(n, 0), adj_dn(n, 0);
-            for (int32_t v = 0; v < n; v++)
-                for (int64_t p = h.ptr[v]; p < h.ptr[v + 1]; p++) {
-                    int32_t u = h.adj[p];
-                    if (level[u] == level[v] + 1) adj_up[v] = 1;
-                    if (level[u] == level[v] - 1) adj_dn[v] = 1;
-                }
-            for (int32_t v = 0; v < n; v++) {
-                if (adj_up[v]) lo_sep[level[v]]++;
-                if (adj_dn[v] && level[v] >= 1) hi_sep[level[v] - 1]++;
+        // the level-structure separator and multilevel ones from differently
+        // shuffled coarsenings (three above 5000 vertices, on their own
+        // threads): the best ratio wins, ties to the earlier candidate
+        const int runs = n > 5000 ? 3 : 1;
+        std::vector<std::vector<int8_t>> mpart(runs);
+        std::vector<char> mok(runs, 0);
+        std::vector<std::thread> workers;
+        if (runs > 1) {
+            try {
+                for (int r = 0; r < runs; r++)
+                    workers.emplace_back([&h, &mpart, &mok, r] { mok[r] = multilevel_separator(h, mpart[r], r); });
+            } catch (const std::system_error &) {
+                for (auto &t : workers) t.join();
+                workers.clear();
+                std::fill(mok.begin(), mok.end(), 0);
+                for (int r = 0; r < runs; r++) mok[r] = multilevel_separator(h, mpart[r], r);
             }
+        } else {
+            mok[0] = multilevel_separator(h, mpart[0], 0);
         }
-        // candidate cuts between level l and l+1 with both sides at least 20% of
-        // the vertices; the cheap one-sided separator estimates rank them and
-        // the best few get their optimal vertex separator (minimum cover of
-        // the cut edges)
-        std::vector<std::pair<double, int32_t>> cands;
-        int64_t below = 0;
-        for (int32_t l = 0; l < ecc; l++) {
-            const int64_t left = below + cnt[l], right = n - left;
-            below += cnt[l];
-            const int64_t sep = std::min(lo_sep[l], hi_sep[l]);
-            if (std::min(left, right) - sep < (int64_t)(0.2 * n)) continue;
-            cands.push_back({(double)sep / ((double)(left - sep) * (double)(right - sep) + 1.0), l});
-        }
-        if (cands.empty()) {
-            std::vector<int32_t> o = order_amd(h, 0.0);
-            for (int32_t t : o) order.push_back(vs[t]);
-            continue;
-        }
-        std::sort(cands.begin(), cands.end());
-        if (cands.size() > 6) cands.resize(6);
-        std::vector<int8_t> part, trial, sidev(n);
-        double best_score = 1e300;
-        for (const auto &cd : cands) {
-            const int32_t l = cd.second;
-            for (int32_t v = 0; v < n; v++) sidev[v] = level[v] <= l ? 1 : 2;
-            const int64_t sep = cover_separator(h, sidev, trial);
-            int64_t c1 = 0;
-            for (int32_t v = 0; v < n; v++) c1 += trial[v] == 1;
-            const int64_t c2 = n - sep - c1;
-            if (c1 <= 0 || c2 <= 0) continue;
-            const double score = (double)sep / ((double)c1 * (double)c2);
-            if (score < best_score) {
-                best_score = score;
-                part.swap(trial);
+        std::vector<int8_t> part;
+        double best_ratio = level_separator(h, part, level, queue) ? separator_ratio(part) : 1e300;
+        for (auto &t : workers) t.join();
+        for (int r = 0; r < runs; r++)
+            if (mok[r] && separator_ratio(mpart[r]) < best_ratio) {
+                best_ratio = separator_ratio(mpart[r]);
+                part.swap(mpart[r]);
             }
-        }
         if (part.empty()) {
             std::vector<int32_t> o = order_amd(h, 0.0);
             for (int32_t t : o) order.push_back(vs[t]);
             continue;
         }
-        refine_separator(h, part, 8);
         std::vector<int32_t> P1, P2, S;
         for (int32_t v = 0; v < n; v++) (part[v] == 0 ? S : part[v] == 1 ? P1 : P2).push_back(vs[v]);
         // order: P1, P2, then the separator

@@ -247,10 +247,11 @@ def test_launch_shapes_validation(lib):
 
 
 def test_nested_dissection_deterministic_with_bounded_fill(lib):
-    """Nested dissection (ratio-scored level cuts, minimum vertex covers of
-    the cut edges, vertex Fiduccia-Mattheyses refinement) is deterministic,
-    gives a permutation, and on a grid LP fills within a small factor of AMD
-    and far below the natural order."""
+    """Nested dissection (the better of ratio-scored level cuts and
+    multilevel separators, each refined by vertex Fiduccia-Mattheyses moves)
+    is deterministic although its candidates run on worker threads, gives a
+    permutation, and on a grid LP fills within 30% of AMD and far below the
+    natural order."""
     lp = synth.grid_multicommodity(24, 3)
     perms, nnz = [], {}
     for ordering in (1, 1, 0, 3):
@@ -263,5 +264,5 @@ def test_nested_dissection_deterministic_with_bounded_fill(lib):
         lib.ipm_destroy(ctx)
     assert np.array_equal(perms[0], perms[1])
     assert np.array_equal(np.sort(perms[0]), np.arange(lp.m + lp.n))
-    assert nnz[1] < 2.0 * nnz[0]
+    assert nnz[1] < 1.3 * nnz[0]
     assert nnz[1] < nnz[3] / 3
