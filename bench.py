@@ -175,7 +175,7 @@ class ClockSampler:
 def traffic_for(kernel):
     """Per-launch DRAM bytes of a kernel class from a committed ncu summary,
     valid only while every source it depends on (the kernel, and the
-    ordering that shapes the workload's tree) is unchanged."""
+    ordering and analysis that shape the workload's tree) is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -342,8 +342,9 @@ def roofline(kstats, peaks, sustained):
 class _OracleProblem:
     """One problem of the workload for the oracle, analysed on first use."""
 
-    def __init__(self, lp, perm, thetas, rhs, weight):
+    def __init__(self, lp, perm, thetas, rhs, weight, amalg_zero_frac):
         self.lp, self.perm, self.thetas, self.rhs, self.weight = lp, perm, thetas, rhs, weight
+        self.amalg_zero_frac = amalg_zero_frac
         self.o = None
 
     def oracle(self):
@@ -351,7 +352,7 @@ class _OracleProblem:
 
         if self.o is None:
             self.o = Oracle.from_lp(self.lp)
-            self.o.analyse(self.perm)
+            self.o.analyse(self.perm, amalg_zero_frac=self.amalg_zero_frac)
         return self.o
 
 
@@ -370,10 +371,11 @@ def oracle_problems(W, pkg):
                                    W.ordering(pkg))
     if rc:
         raise RuntimeError(f"analysis failed ({rc})")
-    perm = pkg.ipm_get_symbolic(ctx)["perm"]
+    sym = pkg.ipm_get_symbolic(ctx)
+    perm, az = sym["perm"], sym["amalg_zero_frac"]
     pkg.ipm_destroy(ctx)
     if W.lps is None:
-        return [_OracleProblem(W.lp, perm, W.thetas, W.rhs, 1.0)]
+        return [_OracleProblem(W.lp, perm, W.thetas, W.rhs, 1.0, az)]
     out = []
     nof = np.concatenate([[0], np.cumsum([lp.n for lp in W.lps])])
     mof = np.concatenate([[0], np.cumsum([lp.m for lp in W.lps])])
@@ -393,7 +395,7 @@ def oracle_problems(W, pkg):
         th = [t[nof[b]:nof[b + 1]] for t in W.thetas]
         rhs = [(a[nof[b]:nof[b + 1]], c[mof[b]:mof[b + 1]]) for a, c in W.rhs]
         out.append(_OracleProblem(lp, pl[pi == b].astype(np.int32), th, rhs,
-                                  B.instance_cost(lp.m, lp.n, int(lp.colptr[-1])) / total))
+                                  B.instance_cost(lp.m, lp.n, int(lp.colptr[-1])) / total, az))
     return out
 
 

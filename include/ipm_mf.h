@@ -86,7 +86,10 @@ typedef struct ipm_ctx ipm_ctx;
 typedef struct ipm_options {
     int32_t nb;               /* pivot-block width (Sec. 4.4 "32, 64 or 128"); default 32 */
     int32_t amalg_width;      /* merge a child into its parent when the width stays <= this; 16 */
-    double amalg_zero_frac;   /* ... or when explicit zeros stay <= this fraction; 0.1 */
+    double amalg_zero_frac;   /* ... or when explicit zeros stay <= this fraction; < 0 (the default, -1):
+                                 0.1 or 0.2, whichever gives the smaller modelled factorisation time
+                                 (front flops at 1 TFLOP/s + 60 us per tree level); the value used is
+                                 reported in ipm_info.amalg_zero_frac */
     double eps_piv;           /* dynamic-regularisation floor eps_piv * ||K||_1 (Sec. 4.5: "of the order of
                                  magnitude of machine precision"); 2.220446049250313e-16 */
     double large_reg;         /* a lift larger than this raises IPM_WARN_LARGE_REG; 1e-4 */
@@ -135,6 +138,7 @@ typedef struct ipm_info {
     int32_t tune_small_threads[3];          /* threads per small-front CTA, size classes f <= 32, 64, 128 */
     double tune_level_ratio;                /* level-kernel threshold (see ipm_autotune) */
     double tune_ms;                         /* best factorisation time the autotuner measured; 0 before */
+    double amalg_zero_frac;                 /* amalgamation threshold the analysis used */
 } ipm_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -77,6 +77,7 @@ class ipm_info(ct.Structure):
         ("ms_analyse", ct.c_double), ("est_cost_ne", ct.c_double), ("est_cost_as", ct.c_double),
         ("nnz_ne_seen", ct.c_int64), ("precision_fallbacks", ct.c_int32), ("mixed_active", ct.c_int32),
         ("tune_small_threads", ct.c_int32 * 3), ("tune_level_ratio", ct.c_double), ("tune_ms", ct.c_double),
+        ("amalg_zero_frac", ct.c_double),
     ]
 
     def as_dict(self):
@@ -289,6 +290,7 @@ def ipm_get_symbolic(ctx):
     if rc:
         raise RuntimeError(f"ipm_get_symbolic failed ({rc})")
     out["sn_rows"] = out["sn_rows"][:nr]
+    out["amalg_zero_frac"] = ipm_get_info(ctx)[1].amalg_zero_frac
     return out
 
 

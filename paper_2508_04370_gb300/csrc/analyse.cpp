@@ -371,35 +371,78 @@ int analyse(Plan &P, int32_t m, int32_t n, const int64_t *colptr, const int32_t 
 
     // ----- amalgamation: bottom-up; absorb the supernode ending right before
     // p while it is a child of p and (merged width <= amalg_width or its
-    // explicit zeros <= amalg_zero_frac of its stored entries)
+    // explicit zeros <= zero_frac of its stored entries)
     struct Open {
         int32_t s, e;
         int64_t nnz, f;
     };
-    std::vector<Open> st;
-    st.reserve(nf);
-    for (int32_t t = 0; t < nf; t++) {
-        int32_t ps = fstart[t], pe = fstart[t + 1];
-        int64_t pnnz = 0;
-        for (int32_t j = ps; j < pe; j++) pnnz += P.colcount[j];
-        int64_t pf = P.colcount[ps];
-        while (!st.empty()) {
-            const Open &c = st.back();
-            if (c.e != ps) break;
-            int32_t par = P.parent[c.e - 1];
-            if (!(par >= ps && par < pe)) break;
-            int64_t k = (int64_t)(c.e - c.s) + (pe - ps);
-            int64_t f = (int64_t)(c.e - c.s) + pf;
-            int64_t total = k * f - k * (k - 1) / 2;
-            int64_t zeros = total - (c.nnz + pnnz);
-            bool merge = k <= opt.amalg_width || (double)zeros <= opt.amalg_zero_frac * (double)total;
-            if (!merge) break;
-            ps = c.s;
-            pnnz += c.nnz;
-            pf = f;
-            st.pop_back();
+    auto amalgamate = [&](double zero_frac) {
+        std::vector<Open> st;
+        st.reserve(nf);
+        for (int32_t t = 0; t < nf; t++) {
+            int32_t ps = fstart[t], pe = fstart[t + 1];
+            int64_t pnnz = 0;
+            for (int32_t j = ps; j < pe; j++) pnnz += P.colcount[j];
+            int64_t pf = P.colcount[ps];
+            while (!st.empty()) {
+                const Open &c = st.back();
+                if (c.e != ps) break;
+                int32_t par = P.parent[c.e - 1];
+                if (!(par >= ps && par < pe)) break;
+                int64_t k = (int64_t)(c.e - c.s) + (pe - ps);
+                int64_t f = (int64_t)(c.e - c.s) + pf;
+                int64_t total = k * f - k * (k - 1) / 2;
+                int64_t zeros = total - (c.nnz + pnnz);
+                bool merge = k <= opt.amalg_width || (double)zeros <= zero_frac * (double)total;
+                if (!merge) break;
+                ps = c.s;
+                pnnz += c.nnz;
+                pf = f;
+                st.pop_back();
+            }
+            st.push_back({ps, pe, pnnz, pf});
         }
-        st.push_back({ps, pe, pnnz, pf});
+        return st;
+    };
+    // A negative threshold chooses between 0.1 and 0.2 by a model of the
+    // factorisation time: front flops at 1 TFLOP/s (the FP64 update rate)
+    // plus 60 us per tree level (the latency of one level's launches and
+    // pivot chains).  More amalgamation trades flops for fewer, larger
+    // supernodes and fewer levels; the model keeps it where the levels, not
+    // the flops, dominate.
+    std::vector<Open> st;
+    if (opt.amalg_zero_frac >= 0) {
+        st = amalgamate(opt.amalg_zero_frac);
+        P.amalg_zero_frac = opt.amalg_zero_frac;
+    } else {
+        double best_t = 0.0;
+        std::vector<int32_t> c2s(N), height;
+        for (double zf : {0.1, 0.2}) {
+            std::vector<Open> cand = amalgamate(zf);
+            const int32_t nc = (int32_t)cand.size();
+            double flops = 0.0;
+            height.assign(nc, 0);
+            int32_t levels = 0;
+            for (int32_t t = 0; t < nc; t++)
+                for (int32_t j = cand[t].s; j < cand[t].e; j++) c2s[j] = t;
+            for (int32_t t = 0; t < nc; t++) {
+                const double k = cand[t].e - cand[t].s, f = (double)cand[t].f;
+                // sum_{i=1..k} (f-i)(f-i+3) with u = f-i running over f-k .. f-1
+                const double a = f - k, b = f - 1;
+                const double su = (b * (b + 1) - (a - 1) * a) / 2.0;
+                const double su2 = (b * (b + 1) * (2 * b + 1) - (a - 1) * a * (2 * a - 1)) / 6.0;
+                flops += su2 + 3.0 * su;
+                levels = std::max(levels, height[t] + 1);
+                const int32_t pc = P.parent[cand[t].e - 1];
+                if (pc >= 0) height[c2s[pc]] = std::max(height[c2s[pc]], height[t] + 1);
+            }
+            const double tm = flops / 1e12 + 60e-6 * levels;
+            if (st.empty() || tm < best_t) {
+                best_t = tm;
+                st.swap(cand);
+                P.amalg_zero_frac = zf;
+            }
+        }
     }
     const int32_t ns = (int32_t)st.size();
     P.nsuper = ns;

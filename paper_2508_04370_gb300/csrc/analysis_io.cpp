@@ -20,7 +20,7 @@ namespace ipm {
 namespace {
 
 constexpr char kMagic[8] = {'I', 'P', 'M', 'P', 'L', 'A', 'N', '1'};
-constexpr uint64_t kVersion = 2;
+constexpr uint64_t kVersion = 3;
 
 struct Writer {
     FILE *f;
@@ -102,7 +102,7 @@ void visit(Plan &P, IO &io) {
     io.scalar(P.nlevels), io.vec(P.lvl_small_ptr), io.vec(P.lvl_small), io.vec(P.lvl_large_ptr), io.vec(P.lvl_large);
     io.vec(P.sn_large);
     io.vec(P.upd_off), io.scalar(P.upd_total);
-    io.scalar(P.nnzL), io.scalar(P.nnzK_lower), io.scalar(P.flops);
+    io.scalar(P.nnzL), io.scalar(P.nnzK_lower), io.scalar(P.flops), io.scalar(P.amalg_zero_frac);
     io.scalar(P.max_f), io.scalar(P.max_k), io.scalar(P.nsmall), io.scalar(P.nlarge);
     io.vec(P.ne_cp), io.vec(P.ne_ri), io.vec(P.ne_tptr), io.vec(P.ne_ta), io.vec(P.ne_tb), io.vec(P.ne_tj);
     io.scalar(P.est_as), io.scalar(P.est_ne), io.scalar(P.nnz_ne_seen);

@@ -1283,7 +1283,7 @@ void ipm_default_options(ipm_options *o) {
     std::memset(o, 0, sizeof(*o));
     o->nb = 32;
     o->amalg_width = 16;
-    o->amalg_zero_frac = 0.1;
+    o->amalg_zero_frac = -1.0;
     o->eps_piv = 2.220446049250313e-16;  // machine precision (Sec. 4.5)
     o->large_reg = 1e-4;
     o->precision = IPM_PREC_FP64;
@@ -1880,6 +1880,7 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
     out->nnz_K_lower = P.nnzK_lower;
     out->nnz_L = P.nnzL;
     out->flops_factor = P.flops;
+    out->amalg_zero_frac = P.amalg_zero_frac;
     out->flops_tensor = c->flops_tensor;
     out->precision_fallbacks = c->fallbacks;
     out->est_cost_as = P.est_as;

@@ -70,6 +70,7 @@ struct Plan {
     // statistics
     int64_t nnzL = 0, nnzK_lower = 0;
     double flops = 0.0;
+    double amalg_zero_frac = 0.0;  // the amalgamation threshold used (chosen when the option is < 0)
     int32_t max_f = 0, max_k = 0;
     int32_t nsmall = 0, nlarge = 0;
 
@@ -97,7 +98,7 @@ int64_t count_ne_lower(int32_t m, int32_t n, const int64_t *colptr, const int32_
 struct AnalyseOptions {
     int32_t nb = 32;
     int32_t amalg_width = 16;
-    double amalg_zero_frac = 0.05;
+    double amalg_zero_frac = 0.05;  // < 0: choose 0.1 or 0.2 by the modelled factorisation time
     int32_t nd_leaf = 128;
     double dense_row_factor = 10.0;
     int32_t verbose = 0;

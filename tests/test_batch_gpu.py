@@ -70,7 +70,7 @@ def test_batch_against_oracle_per_instance(pkg):
     for b, lp in enumerate(lps):
         rp = restricted_perm(perm, b, bs.n_off, bs.m_off, Nn)
         o = Oracle.from_lp(lp)
-        o.analyse(rp)
+        o.analyse(rp, amalg_zero_frac=sym["amalg_zero_frac"])
         o.factorise(thetas[b], RHO, DELTA, eps_piv=EPS_PIV)
         ofac = o.factor()
         ox, oy, _ = o.solve(r7s[b], r1s[b], omega_target=1e-12, max_steps=10)

@@ -162,7 +162,8 @@ def test_block_angular_forms_against_oracle(pkg):
     assert info["form"] == pkg.IPM_FORM_NORMAL and info["npos"] == lp.m
     x = np.concatenate([dx.cpu().numpy(), dy.cpu().numpy()])
     o = Oracle.from_lp(lp, form=FORM_NE)
-    o.analyse(s.symbolic()["perm"])
+    sym = s.symbolic()
+    o.analyse(sym["perm"], amalg_zero_frac=sym["amalg_zero_frac"])
     o.factorise(theta, RHO, DELTA, eps_piv=EPS_PIV)
     ox, oy, _ = o.solve(r7, r1, omega_target=1e-12, max_steps=10)
     ref = np.concatenate([ox, oy])

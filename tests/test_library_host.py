@@ -38,7 +38,7 @@ def _analyse(lib, lp, ordering, perm=None):
 def _compare_with_oracle(lib, ctx, lp):
     sym = lib.ipm_get_symbolic(ctx)
     o = Oracle.from_lp(lp, form=FORM_AS)
-    s = o.analyse(sym["perm"])
+    s = o.analyse(sym["perm"], amalg_zero_frac=sym["amalg_zero_frac"])
     assert np.array_equal(s["perm"], sym["perm"])
     assert np.array_equal(s["parent"], sym["etree"])
     assert np.array_equal(s["colcount"], sym["colcount"])
@@ -67,7 +67,7 @@ def test_symbolic_bit_exact_user_perm(lib):
     sym = lib.ipm_get_symbolic(ctx)
     # both sides compose the same user order with the same postorder
     o = Oracle.from_lp(lp)
-    s = o.analyse(perm)
+    s = o.analyse(perm, amalg_zero_frac=sym["amalg_zero_frac"])
     assert np.array_equal(s["perm"], sym["perm"])
     _compare_with_oracle(lib, ctx, lp)
     lib.ipm_destroy(ctx)
@@ -167,7 +167,7 @@ def test_normal_equations_symbolic_bit_exact(lib):
         assert lib.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, lib.IPM_FORM_NORMAL, lib.IPM_ORD_AMD) == 0
         sym = lib.ipm_get_symbolic(ctx)
         o = Oracle.from_lp(lp, form=FORM_NE)
-        s = o.analyse(sym["perm"])
+        s = o.analyse(sym["perm"], amalg_zero_frac=sym["amalg_zero_frac"])
         for a, b in (("parent", "etree"), ("colcount", "colcount"), ("sn_start", "snode_ptr"),
                      ("sn_parent", "sn_parent"), ("sn_rows", "sn_rows")):
             assert np.array_equal(s[a], sym[b]), a

@@ -59,7 +59,7 @@ def run_pair(pkg, lp, theta, r7, r1, ordering=0, user_perm=None, tune=False, **o
     L, D, dyn = s.factor()
     x = np.concatenate([dx.cpu().numpy(), dy.cpu().numpy()])
     o = Oracle.from_lp(lp)
-    os_ = o.analyse(sym["perm"])
+    os_ = o.analyse(sym["perm"], amalg_zero_frac=sym["amalg_zero_frac"])
     assert np.array_equal(os_["sn_rows"], sym["sn_rows"])
     o.factorise(theta, RHO, DELTA, eps_piv=EPS_PIV)
     ofac = o.factor()
@@ -323,9 +323,9 @@ def run_mixed(pkg, lp, theta, r7, r1, ordering, min_front, **opts):
     stats = pkg.ipm_kernel_stats(s.ctx, reset=True)
     info = s.info()
     x = np.concatenate([dx.cpu().numpy(), dy.cpu().numpy()])
-    perm = s.symbolic()["perm"]
+    sym = s.symbolic()
     o = Oracle.from_lp(lp)
-    o.analyse(perm)
+    o.analyse(sym["perm"], amalg_zero_frac=sym["amalg_zero_frac"])
     o.factorise(theta, RHO, DELTA, eps_piv=EPS_PIV)
     ox, oy, _ = o.solve(r7, r1, omega_target=1e-12, max_steps=10)
     ref = np.concatenate([ox, oy])
@@ -431,7 +431,7 @@ def test_normal_equations_against_oracle(pkg):
         sym = s.symbolic()
         x = np.concatenate([dx.cpu().numpy(), dy.cpu().numpy()])
         o = Oracle.from_lp(lp, form=FORM_NE)
-        o.analyse(sym["perm"])
+        o.analyse(sym["perm"], amalg_zero_frac=sym["amalg_zero_frac"])
         o.factorise(theta, RHO, DELTA, eps_piv=EPS_PIV)
         of = o.factor()
         ox, oy, oi = o.solve(r7, r1, omega_target=1e-12, max_steps=10)
