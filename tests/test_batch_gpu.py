@@ -107,7 +107,8 @@ def test_batch_matches_instances_alone(pkg):
     nlift = 0
     for b, lp in enumerate(lps):
         rp = restricted_perm(perm, b, bs.n_off, bs.m_off, Nn)
-        s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_USER, user_perm=rp)
+        # the batch's elimination order and amalgamation threshold
+        s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_USER, user_perm=rp, amalg_zero_frac=sym["amalg_zero_frac"])
         s.factorise(thetas[b], RHO, DELTA)
         sa = s.symbolic()
         _, Da, dyna = s.factor()
