@@ -266,3 +266,33 @@ def test_nested_dissection_deterministic_with_bounded_fill(lib):
     assert np.array_equal(np.sort(perms[0]), np.arange(lp.m + lp.n))
     assert nnz[1] < 1.3 * nnz[0]
     assert nnz[1] < nnz[3] / 3
+
+
+def test_amalgamation_threshold_chosen_by_model(lib):
+    """With amalg_zero_frac < 0 (the default) the analysis takes 0.1 or 0.2,
+    whichever gives the smaller modelled factorisation time (front flops at
+    1 TFLOP/s + 60 us per tree level): a grid LP, whose extra levels cost more
+    than the extra flops, gets 0.2; a random LP with equal level counts and a
+    staircase whose flops dominate keep 0.1.  The partition equals the one
+    the explicit threshold gives, and the oracle reproduces it bit for bit
+    with the reported value."""
+    cases = ((synth.grid_multicommodity(24, 3), lib.IPM_ORD_ND, 0.2, True),
+             (synth.random_lp(300, 800, 6, seed=1), lib.IPM_ORD_AMD, 0.1, True),
+             (synth.staircase(periods=2, seed=1), lib.IPM_ORD_ND, 0.1, False))  # oracle analysis: ~10 s
+    for lp, ordering, want, with_oracle in cases:
+        syms = {}
+        for az in (-1.0, want):
+            opt = lib.ipm_default_options()
+            opt.amalg_zero_frac = az
+            ctx = lib.ipm_create(opt)
+            assert lib.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, lib.IPM_FORM_AUGMENTED, ordering) == 0
+            rc, info = lib.ipm_get_info(ctx)
+            assert info.amalg_zero_frac == want
+            syms[az] = lib.ipm_get_symbolic(ctx)
+            lib.ipm_destroy(ctx)
+        for key in ("perm", "snode_ptr", "sn_parent", "sn_rptr", "sn_rows"):
+            assert np.array_equal(syms[-1.0][key], syms[want][key]), key
+        if with_oracle:
+            o = Oracle.from_lp(lp, form=FORM_AS)
+            s = o.analyse(syms[-1.0]["perm"], amalg_zero_frac=syms[-1.0]["amalg_zero_frac"])
+            assert np.array_equal(s["sn_start"], syms[-1.0]["snode_ptr"])
