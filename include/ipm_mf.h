@@ -139,6 +139,7 @@ typedef struct ipm_info {
     double tune_level_ratio;                /* level-kernel threshold (see ipm_autotune) */
     double tune_ms;                         /* best factorisation time the autotuner measured; 0 before */
     double amalg_zero_frac;                 /* amalgamation threshold the analysis used */
+    int32_t tune_level_ctas_per_sm;         /* CTAs per SM of the level kernel (0 before the first factorisation) */
 } ipm_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -312,7 +313,9 @@ int ipm_solve_noalloc(ipm_ctx *ctx, const double *r7_dev, const double *r1_dev, 
  *     (35 us per 32-column panel of its widest front); candidates 0 (never),
  *     0.25, 0.5 (default), 1, 2, 1e30 (always);
  *   - the threads per small-front CTA of each size class present (f <= 32:
- *     32 or 64; f <= 64: 64 or 128; f <= 128: 128 or 256).
+ *     32 or 64; f <= 64: 64 or 128; f <= 128: 128 or 256);
+ *   - the level kernel's CTAs per SM: as many as fit (default) or one (see
+ *     ipm_set_level_ctas).
  * The choices never change the arithmetic of any entry: the factors are the
  * same bit for bit.  They are reported by ipm_get_info and kept by the
  * context; tune before ipm_graph_capture (a captured graph keeps the launch
@@ -331,6 +334,17 @@ int ipm_autotune(ipm_ctx *ctx, const double *theta_dev, double rho, double delta
  * factorisation (not in an already captured graph).
  * Errors: IPM_ERR_INVALID_ARG for another width or a NaN ratio. */
 int ipm_set_launch_shapes(ipm_ctx *ctx, const int32_t *small_threads, double level_ratio);
+
+/* CTAs per SM of the persistent level kernel: 0 (the default) as many as
+ * fit, else per_sm (at most as many as fit).  One CTA per SM gives each SM
+ * sub-partition's FP64 pipe to one CTA's pivot chain, which shortens the
+ * chains of latency-bound levels; more keep more trailing tiles in flight.
+ * ipm_autotune tries one against the default.  Items are taken in ticket
+ * order whatever the grid, so waits still end and the factors are the same
+ * bit for bit.  Takes effect at the next factorisation (not in an already
+ * captured graph).
+ * Errors: IPM_ERR_INVALID_ARG for a negative per_sm or one above 64. */
+int ipm_set_level_ctas(ipm_ctx *ctx, int32_t per_sm);
 
 /* ------------------------------------------------------------ measurement */
 /* Kernel classes reported by ipm_kernel_stats. */

@@ -77,7 +77,7 @@ class ipm_info(ct.Structure):
         ("ms_analyse", ct.c_double), ("est_cost_ne", ct.c_double), ("est_cost_as", ct.c_double),
         ("nnz_ne_seen", ct.c_int64), ("precision_fallbacks", ct.c_int32), ("mixed_active", ct.c_int32),
         ("tune_small_threads", ct.c_int32 * 3), ("tune_level_ratio", ct.c_double), ("tune_ms", ct.c_double),
-        ("amalg_zero_frac", ct.c_double),
+        ("amalg_zero_frac", ct.c_double), ("tune_level_ctas_per_sm", ct.c_int32),
     ]
 
     def as_dict(self):
@@ -118,6 +118,7 @@ def _load():
     lib.ipm_factorise.argtypes = [P, P, ct.c_double, ct.c_double, P]
     lib.ipm_autotune.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_int32, P]
     lib.ipm_set_launch_shapes.argtypes = [P, P, ct.c_double]
+    lib.ipm_set_level_ctas.argtypes = [P, ct.c_int32]
     lib.ipm_solve.argtypes = [P, P, P, P, P, P]
     lib.ipm_iterate_host.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_int32, P, P, P, P, P]
     lib.ipm_sync_status.argtypes = [P, P]
@@ -235,6 +236,10 @@ def ipm_factorise(ctx, theta_dev, rho, delta, stream=None) -> int:
 
 def ipm_autotune(ctx, theta_dev, rho, delta, reps=3, stream=None) -> int:
     return _load().ipm_autotune(ctx, _dptr(theta_dev), float(rho), float(delta), int(reps), _stream(stream))
+
+
+def ipm_set_level_ctas(ctx, per_sm=0) -> int:
+    return _load().ipm_set_level_ctas(ctx, int(per_sm))
 
 
 def ipm_set_launch_shapes(ctx, small_threads=None, level_ratio=-1.0) -> int:

@@ -111,10 +111,15 @@ struct ipm_ctx {
     int32_t ninv = 0, npairs = 0;
     int32_t *lvl_sync = nullptr;      // its ticket and counters (1 + max counters of a level)
     int32_t lvl_grid = 1;  // CTAs of the level kernel: every SM full
+    int32_t sms = 1;       // SMs of the device
     // choices of ipm_autotune: threads per small-front CTA by size class
-    // (0: 32 / 64 / 128) and the level-kernel threshold
+    // (0: 32 / 64 / 128), the level-kernel threshold and the level kernel's
+    // CTAs per SM (0: as many as fit).  One CTA per SM leaves each SM
+    // sub-partition's FP64 pipe to one CTA's pivot chain; two keep more
+    // trailing tiles in flight.
     int32_t tune_threads[3] = {0, 0, 0};
     double tune_ratio = 0.5;
+    int32_t tune_lvl_per_sm = 0;
     double tune_ms = 0.0;
     bool mixed_active = false;  // tensor-core updates in use (mixed precision, no fallback yet)
     int32_t fallbacks = 0;
@@ -898,6 +903,7 @@ int setup_device(ipm_ctx *c) {
         int lvl_per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lvl_per_sm, large_level_kernel(), 256, 0);
         c->lvl_grid = sms * std::max(1, lvl_per_sm);
+        c->sms = std::max(1, sms);
     }
     DevPlan &dp = c->dp;
     dp.N = N;
@@ -994,6 +1000,12 @@ int setup_device(ipm_ctx *c) {
     c->resid_w.bytes = 20.0 * (double)kp[N] + 48.0 * N;
     c->dev_ready = true;
     return to_err(cudaGetLastError());
+}
+
+// CTAs of the level kernel: every SM full, or tune_lvl_per_sm per SM.
+static int32_t level_grid(const ipm_ctx *c) {
+    if (c->tune_lvl_per_sm <= 0) return c->lvl_grid;
+    return std::max(1, std::min(c->lvl_grid, c->sms * c->tune_lvl_per_sm));
 }
 
 int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta, cudaStream_t st) {
@@ -1096,7 +1108,7 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                 Prof pr(c, IPM_K_LARGE_PANEL, W.lvl_w, sd);
                 launch_large_level(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_items + W.lvl_off,
                                    W.lvl_cnt, c->lvl_sync, W.lvl_ncnt, c->asm_info, c->asm_cr, c->panel_ws,
-                                   c->opt.nb, c->lvl_grid,
+                                   c->opt.nb, level_grid(c),
                                    c->opt.spin_limit_log2 < 0 ? 0 : (1ll << c->opt.spin_limit_log2), sd);
             }
             nl++;
@@ -1586,6 +1598,14 @@ int ipm_autotune(ipm_ctx *c, const double *theta_dev, double rho, double delta, 
             }
             c->tune_threads[b] = keep;
         }
+        if (c->lvl_grid > c->sms) {  // more than one level-kernel CTA fits per SM: try one
+            const int32_t l0 = c->tune_lvl_per_sm;
+            c->tune_lvl_per_sm = l0 == 1 ? 0 : 1;
+            double ms;
+            if ((rc = measure(ms))) goto done;
+            if (ms < best * kTuneMargin) best = ms;
+            else c->tune_lvl_per_sm = l0;
+        }
         c->tune_ms = best;
     }
 done:
@@ -1599,6 +1619,12 @@ static int read_ctl(ipm_ctx *c, cudaStream_t st, DevCtl *h) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return to_err(e);
     c->status_acc |= h->status;
+    return IPM_OK;
+}
+
+int ipm_set_level_ctas(ipm_ctx *c, int32_t per_sm) {
+    if (!c || per_sm < 0 || per_sm > 64) return IPM_ERR_INVALID_ARG;
+    c->tune_lvl_per_sm = per_sm;
     return IPM_OK;
 }
 
@@ -1896,6 +1922,7 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
         out->tune_small_threads[b] = c->tune_threads[b] > 0 ? c->tune_threads[b] : dflt;
     }
     out->tune_level_ratio = c->tune_ratio;
+    out->tune_level_ctas_per_sm = c->dev_ready ? level_grid(c) / c->sms : 0;
     out->tune_ms = c->tune_ms;
     out->omega = c->omega;
     for (int i = 0; i < 16; i++) out->omega_hist[i] = c->omega_hist[i];

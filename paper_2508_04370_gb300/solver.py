@@ -87,7 +87,8 @@ class Solver:
             raise RuntimeError(f"ipm_autotune failed ({rc})")
         self._theta = theta
         i = self.info()
-        return {"small_threads": i["tune_small_threads"], "level_ratio": i["tune_level_ratio"], "ms": i["tune_ms"]}
+        return {"small_threads": i["tune_small_threads"], "level_ratio": i["tune_level_ratio"],
+                "level_ctas_per_sm": i["tune_level_ctas_per_sm"], "ms": i["tune_ms"]}
 
     def solve(self, r7, r1):
         r7 = self._dev(r7)

@@ -233,8 +233,9 @@ def test_analysis_checkpoint_roundtrip(tmp_path):
 
 def test_launch_shapes_validation(lib):
     """ipm_set_launch_shapes accepts the autotuner's widths (or 0 for the
-    default) and a non-negative level ratio, and rejects anything else
-    without touching the GPU; ipm_autotune needs values first."""
+    default) and a non-negative level ratio, ipm_set_level_ctas 0 to 64 CTAs
+    per SM, and both reject anything else without touching the GPU;
+    ipm_autotune needs values first."""
     ctx = lib.ipm_create()
     assert lib.ipm_set_launch_shapes(ctx, [32, 128, 256], 1.0) == 0
     assert lib.ipm_set_launch_shapes(ctx, [0, 0, 0]) == 0
@@ -242,6 +243,12 @@ def test_launch_shapes_validation(lib):
     assert lib.ipm_set_launch_shapes(ctx, [48, 64, 128]) == lib.IPM_ERR_INVALID_ARG
     assert lib.ipm_set_launch_shapes(ctx, [32, 64, 512]) == lib.IPM_ERR_INVALID_ARG
     assert lib.ipm_set_launch_shapes(ctx, None, float("nan")) == lib.IPM_ERR_INVALID_ARG
+    for per_sm in (0, 1, 2, 64):
+        assert lib.ipm_set_level_ctas(ctx, per_sm) == 0
+    assert lib.ipm_set_level_ctas(ctx, -1) == lib.IPM_ERR_INVALID_ARG
+    assert lib.ipm_set_level_ctas(ctx, 65) == lib.IPM_ERR_INVALID_ARG
+    rc, info = lib.ipm_get_info(ctx)
+    assert info.tune_level_ctas_per_sm == 0  # no device state yet
     assert lib.ipm_autotune(ctx, None, 1e-8, 1e-8, 1, stream=0) == lib.IPM_ERR_NOT_ANALYSED
     lib.ipm_destroy(ctx)
 

@@ -570,8 +570,9 @@ def test_autotune_choices_keep_the_factor(pkg):
 @pytest.mark.parametrize("order", ["ND", "AMD"])
 def test_launch_shapes_give_identical_factors(pkg, order):
     """Every launch shape the autotuner can choose (small-front CTA widths,
-    level kernel on every level or on none) computes each entry with the same
-    operations in the same order: the factors agree bit for bit."""
+    level kernel on every level or on none, one or all level-kernel CTAs per
+    SM) computes each entry with the same operations in the same order: the
+    factors agree bit for bit."""
     lp = synth.grid_multicommodity(24, 4)
     theta = synth.theta_loguniform(lp.n, 91)
     s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND if order == "ND" else pkg.IPM_ORD_AMD)
@@ -585,4 +586,14 @@ def test_launch_shapes_give_identical_factors(pkg, order):
             assert s.status() >= 0
             for a, b in zip(ref, s.factor()):
                 assert np.array_equal(a, b), (widths, ratio)
+    for per_sm in (1, 0):
+        assert pkg.ipm_set_launch_shapes(s.ctx, (32, 64, 128), 1e30) == 0
+        assert pkg.ipm_set_level_ctas(s.ctx, per_sm) == 0
+        s.factorise(theta, RHO, DELTA)
+        assert s.status() >= 0
+        assert s.info()["tune_level_ctas_per_sm"] >= 1
+        if per_sm == 1:
+            assert s.info()["tune_level_ctas_per_sm"] == 1
+        for a, b in zip(ref, s.factor()):
+            assert np.array_equal(a, b), ("level CTAs per SM", per_sm)
     s.close()
