@@ -132,8 +132,7 @@ __device__ __forceinline__ long long pivot_exact_bits(bool maybe, bool screenabl
 }
 
 __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int w, const int8_t *sgn, double rho,
-                                           double delta, double b1floor, double *Dout, double *dynout, DevCtl *ctl,
-                                           double *piv_out) {
+                                           double delta, double b1floor, double *dstat, double *piv_out) {
     const int lane = threadIdx.x & 31;
     const int sp = sgn[p];
     const double d = Fd[p * LDD + p] + (sp < 0 ? -rho : delta);
@@ -167,10 +166,7 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
     if (__any_sync(0xffffffffu, maybe)) dnb = pivot_exact_bits(maybe, screenable, c, g, tb, sdb, b1b, sp);
     if (lane == 0) {
         const double dn = __longlong_as_double(dnb);
-        Dout[p] = dn;
-        dynout[p] = dnb == db ? 0.0 : dn - d;
-        const bool fin = (db & kAbsMask) < kInfBits && (dnb & kAbsMask) < kInfBits && (dnb & kAbsMask) != 0;
-        if (!fin) atomicOr(&ctl->status, kStatNonFinite);
+        dstat[p] = d;  // the lift dn - d and the status are formed off the chain
         piv_out[0] = dn;
         piv_out[1] = dnb == dnb_fast ? rinv_fast : recip_pivot(dn);
     }
@@ -183,8 +179,7 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
 // statically regularised pivot d (the lift D - d is formed later, off the
 // pivot chain) and the status.
 __device__ __forceinline__ double pivot_lanes(double c, double g, int sl, int p, int w, int sp, double d,
-                                              double b1floor, double *Dout, double *dout, DevCtl *ctl,
-                                              double *rinv) {
+                                              double b1floor, double *rinv) {
     const int lane = threadIdx.x & 31;
     const long long db = dbits(d);
     const long long sdb = sp < 0 ? db ^ kSignBit : db;
@@ -213,12 +208,6 @@ __device__ __forceinline__ double pivot_lanes(double c, double g, int sl, int p,
         if (dnb != dnb_fast) r = recip_pivot(__longlong_as_double(dnb));
     }
     const double dn = __longlong_as_double(dnb);
-    if (lane == 0) {
-        Dout[p] = dn;
-        dout[p] = d;
-        const bool fin = (db & kAbsMask) < kInfBits && (dnb & kAbsMask) < kInfBits && (dnb & kAbsMask) != 0;
-        if (!fin) atomicOr(&ctl->status, kStatNonFinite);
-    }
     *rinv = r;
     return dn;
 }
@@ -253,6 +242,7 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
     extern __shared__ double smem[];
     __shared__ double wcol[128];  // fronts up to 128 rows use this kernel
     __shared__ double dq[32];
+    __shared__ double dsm[32];  // statically regularised pivots of the block, before any lift
     __shared__ double piv[2];
     __shared__ int8_t sg[128];
     const int s = list[blockIdx.x];
@@ -286,8 +276,7 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
         const int b1 = min(b0 + nb, k), w = b1 - b0;
         double *Fb = F + b0 * ld + b0;
         for (int p = 0; p < w; p++) {
-            if (warp == 0) pivot_warp(Fb, ld, p, w, sgn + b0, V.rho, V.delta, b1floor, Dg + c0 + b0, dyng + c0 + b0,
-                                      ctl, piv);
+            if (warp == 0) pivot_warp(Fb, ld, p, w, sgn + b0, V.rho, V.delta, b1floor, dsm, piv);
             __syncthreads();
             const double dn = piv[0], rinv = piv[1];
             const int pc = b0 + p;  // front column of the pivot
@@ -308,6 +297,16 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
                 for (int i = j + lane; i < f; i += 32) F[j * ld + i] -= F[pc * ld + i] * wj;
             }
             __syncthreads();
+        }
+        // the block's pivots, lifts and status (dq and dsm are rewritten only
+        // after the barriers of the trailing update)
+        if (tid < w) {
+            const double dn = dq[tid], d = dsm[tid];
+            const long long db = dbits(d), dnb = dbits(dn);
+            Dg[c0 + b0 + tid] = dn;
+            dyng[c0 + b0 + tid] = dnb == db ? 0.0 : dn - d;
+            const bool fin = (db & kAbsMask) < kInfBits && (dnb & kAbsMask) < kInfBits && (dnb & kAbsMask) != 0;
+            if (!fin) atomicOr(&ctl->status, kStatNonFinite);
         }
         // trailing update of columns [b1, f) by the block's pivots:
         // W_jq = L_jq d_q is formed once into the unused upper triangle
@@ -448,20 +447,22 @@ __device__ __forceinline__ void body_diag(const DevPlan &P, const DevVals &V, do
         double g = lane < w ? Fd[lane * LDD + lane] : 0.0;   // F_jj of row j = lane
         double gs = g + (sl < 0 ? -V.rho : V.delta);
         double c = (lane > 0 && lane < w) ? Fd[lane] : 0.0;  // column 0
+        double my_dn = 0.0, my_d = 0.0, my_r = 0.0;          // lane p keeps pivot p's values
         for (int p = 0; p < w; p++) {
             const int sp = __shfl_sync(0xffffffffu, sl, p);
             const double d = __shfl_sync(0xffffffffu, gs, p);
             double rinv;
-            const double dn = pivot_lanes(c, g, sl, p, w, sp, d, b1floor, Dtmp, dstat, ctl, &rinv);
+            const double dn = pivot_lanes(c, g, sl, p, w, sp, d, b1floor, &rinv);
+            if (lane == p) {
+                my_dn = dn;
+                my_d = d;
+                my_r = rinv;
+            }
             const bool below = lane > p && lane < w;
             const double l = below ? c * rinv : 0.0;
             if (below) {
                 Fd[p * LDD + lane] = l;
                 wsv[p & 1][lane] = c;
-            }
-            if (lane == 0) {
-                Fd[p * LDD + p] = dn;
-                rtmp[p] = rinv;
             }
             __syncwarp();
             bar_arrive_parity<kBarPub>(p);
@@ -474,6 +475,16 @@ __device__ __forceinline__ void body_diag(const DevPlan &P, const DevVals &V, do
                 gs -= l * c;
                 c = lane > p + 1 ? cn : 0.0;
             }
+        }
+        // the pivots' values, off the chain (read only after the CTA barrier)
+        if (lane < w) {
+            Fd[lane * LDD + lane] = my_dn;
+            Dtmp[lane] = my_dn;
+            dstat[lane] = my_d;
+            rtmp[lane] = my_r;
+            const long long db = dbits(my_d), dnb = dbits(my_dn);
+            const bool fin = (db & kAbsMask) < kInfBits && (dnb & kAbsMask) < kInfBits && (dnb & kAbsMask) != 0;
+            if (!fin) atomicOr(&ctl->status, kStatNonFinite);
         }
     } else if (warp < NT / 32) {
         // this thread owns the strictly lower entries e = ut + 96 t of columns
