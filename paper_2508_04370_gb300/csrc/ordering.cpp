@@ -828,7 +828,13 @@ std::vector<int32_t> order_nd(const Graph &g, int32_t leaf, double dense_factor)
         if (runs > 1) {
             try {
                 for (int r = 0; r < runs; r++)
-                    workers.emplace_back([&h, &mpart, &mok, r] { mok[r] = multilevel_separator(h, mpart[r], r); });
+                    workers.emplace_back([&h, &mpart, &mok, r] {
+                        try {  // a run that cannot allocate is dropped, not fatal
+                            mok[r] = multilevel_separator(h, mpart[r], r);
+                        } catch (...) {
+                            mok[r] = 0;
+                        }
+                    });
             } catch (const std::system_error &) {
                 for (auto &t : workers) t.join();
                 workers.clear();
