@@ -12,7 +12,9 @@
 //   coarsening, separators grown on the coarsest graph, vertex
 //   Fiduccia-Mattheyses refinement on the way back), computed on worker
 //   threads; subgraphs below the leaf size are ordered with order_amd.  The
-//   paper uses Metis (Sec. 4.2); this is a self-contained replacement.
+//   subsets left after the first dissection steps are dissected on worker
+//   threads; the order does not depend on them.  The paper uses Metis
+//   (Sec. 4.2); this is a self-contained replacement.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -747,6 +749,162 @@ bool multilevel_separator(const Graph &h, std::vector<int8_t> &part, int run) {
 }
 }  // namespace
 
+namespace {
+
+// Per-thread scratch of the dissection: global -> local maps of the induced
+// subgraphs and the breadth-first buffers.
+struct NdScratch {
+    std::vector<int32_t> loc, stampv, level, queue, comp;
+    int32_t stamp = 0;
+    explicit NdScratch(int32_t N) : loc(N, -1), stampv(N, 0) {}
+};
+
+// One dissection step on the vertex set vs (global ids of g).  Either vs is
+// ordered outright (a leaf, or a subgraph without a separator: order_amd),
+// or it splits into parts to dissect in turn, in order, followed by the
+// separator (connected components have none).
+struct NdStep {
+    bool ordered = false;
+    std::vector<int32_t> order;
+    std::vector<std::vector<int32_t>> parts;
+    bool has_sep = false;
+    std::vector<int32_t> sep;
+};
+
+NdStep nd_step(const Graph &g, const std::vector<int32_t> &vs, int32_t leaf, NdScratch &w) {
+    NdStep out;
+    Graph h = induced(g, vs, w.loc, w.stampv, ++w.stamp);
+    const int32_t n = h.N;
+    auto by_amd = [&]() {
+        out.ordered = true;
+        for (int32_t t : order_amd(h, 0.0)) out.order.push_back(vs[t]);
+        return out;
+    };
+    if (n <= leaf) return by_amd();
+    // connected components: dissected separately, lowest first
+    w.comp.assign(n, -1);
+    int32_t ncomp = 0;
+    for (int32_t r = 0; r < n; r++) {
+        if (w.comp[r] >= 0) continue;
+        w.queue.clear();
+        w.queue.push_back(r);
+        w.comp[r] = ncomp;
+        for (size_t q = 0; q < w.queue.size(); q++) {
+            int32_t v = w.queue[q];
+            for (int64_t p = h.ptr[v]; p < h.ptr[v + 1]; p++)
+                if (w.comp[h.adj[p]] < 0) {
+                    w.comp[h.adj[p]] = ncomp;
+                    w.queue.push_back(h.adj[p]);
+                }
+        }
+        ncomp++;
+    }
+    if (ncomp > 1) {
+        out.parts.assign(ncomp, {});
+        for (int32_t t = 0; t < n; t++) out.parts[w.comp[t]].push_back(vs[t]);
+        return out;
+    }
+    // the level-structure separator and multilevel ones from differently
+    // shuffled coarsenings (three above 5000 vertices, on their own
+    // threads): the best ratio wins, ties to the earlier candidate
+    const int runs = n > 5000 ? 3 : 1;
+    std::vector<std::vector<int8_t>> mpart(runs);
+    std::vector<char> mok(runs, 0);
+    std::vector<std::thread> workers;
+    if (runs > 1) {
+        try {
+            for (int r = 0; r < runs; r++)
+                workers.emplace_back([&h, &mpart, &mok, r] {
+                    try {  // a run that cannot allocate is dropped, not fatal
+                        mok[r] = multilevel_separator(h, mpart[r], r);
+                    } catch (...) {
+                        mok[r] = 0;
+                    }
+                });
+        } catch (const std::system_error &) {
+            for (auto &t : workers) t.join();
+            workers.clear();
+            std::fill(mok.begin(), mok.end(), 0);
+            for (int r = 0; r < runs; r++) mok[r] = multilevel_separator(h, mpart[r], r);
+        }
+    } else {
+        mok[0] = multilevel_separator(h, mpart[0], 0);
+    }
+    w.level.assign(n, -1);
+    std::vector<int8_t> part;
+    double best_ratio = level_separator(h, part, w.level, w.queue) ? separator_ratio(part) : 1e300;
+    for (auto &t : workers) t.join();
+    for (int r = 0; r < runs; r++)
+        if (mok[r] && separator_ratio(mpart[r]) < best_ratio) {
+            best_ratio = separator_ratio(mpart[r]);
+            part.swap(mpart[r]);
+        }
+    if (part.empty()) return by_amd();
+    // order: P1, P2, then the separator
+    out.parts.assign(2, {});
+    out.has_sep = true;
+    for (int32_t v = 0; v < n; v++) (part[v] == 0 ? out.sep : out.parts[part[v] - 1]).push_back(vs[v]);
+    return out;
+}
+
+// Nested dissection of vs, appended to order: depth first with an explicit
+// stack (a part's whole subtree before the next part, each separator after
+// its parts).
+void nd_serial(const Graph &g, std::vector<int32_t> vs, int32_t leaf, NdScratch &w, std::vector<int32_t> &order) {
+    struct Item {
+        std::vector<int32_t> verts;
+        bool emit;
+    };
+    std::vector<Item> stack;
+    stack.push_back({std::move(vs), false});
+    while (!stack.empty()) {
+        Item it = std::move(stack.back());
+        stack.pop_back();
+        if (it.emit) {
+            order.insert(order.end(), it.verts.begin(), it.verts.end());
+            continue;
+        }
+        if (it.verts.empty()) continue;
+        NdStep st = nd_step(g, it.verts, leaf, w);
+        if (st.ordered) {
+            order.insert(order.end(), st.order.begin(), st.order.end());
+            continue;
+        }
+        if (st.has_sep) stack.push_back({std::move(st.sep), true});
+        for (size_t c = st.parts.size(); c-- > 0;) stack.push_back({std::move(st.parts[c]), false});
+    }
+}
+
+// The first kNdTopLevels steps run here and leave a list of tasks in output
+// order (sets still to dissect, or vertices already in their final order);
+// the sets then run on worker threads.  Each set's order is a function of the
+// set alone, so the result is the serial one whatever the threads do.
+constexpr int kNdTopLevels = 3;
+constexpr size_t kNdParallelMin = 20000;
+
+struct NdTask {
+    std::vector<int32_t> verts;
+    bool done;  // verts already ordered (a separator, or a set ordered outright)
+};
+
+void nd_expand(const Graph &g, std::vector<int32_t> vs, int32_t leaf, int depth, NdScratch &w,
+               std::vector<NdTask> &tasks) {
+    if (vs.empty()) return;
+    if (depth == 0 || vs.size() < kNdParallelMin) {
+        tasks.push_back({std::move(vs), false});
+        return;
+    }
+    NdStep st = nd_step(g, vs, leaf, w);
+    if (st.ordered) {
+        tasks.push_back({std::move(st.order), true});
+        return;
+    }
+    for (auto &part : st.parts) nd_expand(g, std::move(part), leaf, depth - 1, w, tasks);
+    if (st.has_sep) tasks.push_back({std::move(st.sep), true});
+}
+
+}  // namespace
+
 std::vector<int32_t> order_nd(const Graph &g, int32_t leaf, double dense_factor) {
     const int32_t N = g.N;
     std::vector<int32_t> order;
@@ -761,108 +919,43 @@ std::vector<int32_t> order_nd(const Graph &g, int32_t leaf, double dense_factor)
         if (dense_factor > 0 && (double)d > thr) dense.push_back(i);
         else rest.push_back(i);
     }
-    std::vector<int32_t> loc(N, -1), stampv(N, 0);
-    int32_t stamp = 0;
-    // explicit work stack: entries are either a vertex set to dissect or a
-    // separator to emit after its two halves
-    struct Item {
-        std::vector<int32_t> verts;
-        bool emit;
-    };
-    std::vector<Item> stack;
-    stack.push_back({rest, false});
-    std::vector<int32_t> level, queue, comp;
-    while (!stack.empty()) {
-        Item it = std::move(stack.back());
-        stack.pop_back();
-        if (it.emit) {
-            for (int32_t v : it.verts) order.push_back(v);
-            continue;
-        }
-        auto &vs = it.verts;
-        if (vs.empty()) continue;
-        ++stamp;
-        Graph h = induced(g, vs, loc, stampv, stamp);
-        const int32_t n = h.N;
-        if (n <= leaf) {
-            std::vector<int32_t> o = order_amd(h, 0.0);
-            for (int32_t t : o) order.push_back(vs[t]);
-            continue;
-        }
-        level.assign(n, -1);
-        // connected components
-        comp.assign(n, -1);
-        int32_t ncomp = 0;
-        std::vector<int32_t> csize;
-        for (int32_t r = 0; r < n; r++) {
-            if (comp[r] >= 0) continue;
-            queue.clear();
-            queue.push_back(r);
-            comp[r] = ncomp;
-            for (size_t q = 0; q < queue.size(); q++) {
-                int32_t v = queue[q];
-                for (int64_t p = h.ptr[v]; p < h.ptr[v + 1]; p++)
-                    if (comp[h.adj[p]] < 0) {
-                        comp[h.adj[p]] = ncomp;
-                        queue.push_back(h.adj[p]);
-                    }
-            }
-            csize.push_back((int32_t)queue.size());
-            ncomp++;
-        }
-        if (ncomp > 1) {
-            // independent components: dissect each separately (pushed in
-            // reverse so that the lowest component is ordered first)
-            std::vector<std::vector<int32_t>> parts(ncomp);
-            for (int32_t t = 0; t < n; t++) parts[comp[t]].push_back(vs[t]);
-            for (int32_t c = ncomp - 1; c >= 0; c--) stack.push_back({std::move(parts[c]), false});
-            continue;
-        }
-        // the level-structure separator and multilevel ones from differently
-        // shuffled coarsenings (three above 5000 vertices, on their own
-        // threads): the best ratio wins, ties to the earlier candidate
-        const int runs = n > 5000 ? 3 : 1;
-        std::vector<std::vector<int8_t>> mpart(runs);
-        std::vector<char> mok(runs, 0);
-        std::vector<std::thread> workers;
-        if (runs > 1) {
+    NdScratch main_w(N);
+    std::vector<NdTask> tasks;
+    nd_expand(g, std::move(rest), leaf, kNdTopLevels, main_w, tasks);
+    std::vector<std::vector<int32_t>> sub(tasks.size());
+    std::vector<std::thread> workers;
+    std::vector<size_t> serial;
+    for (size_t t = 0; t < tasks.size(); t++) {
+        if (tasks[t].done) continue;
+        bool started = false;
+        if (tasks[t].verts.size() >= kNdParallelMin / 4) {
             try {
-                for (int r = 0; r < runs; r++)
-                    workers.emplace_back([&h, &mpart, &mok, r] {
-                        try {  // a run that cannot allocate is dropped, not fatal
-                            mok[r] = multilevel_separator(h, mpart[r], r);
-                        } catch (...) {
-                            mok[r] = 0;
-                        }
-                    });
+                workers.emplace_back([&g, &tasks, &sub, t, leaf, N] {
+                    try {
+                        NdScratch w(N);
+                        nd_serial(g, tasks[t].verts, leaf, w, sub[t]);
+                    } catch (...) {
+                        sub[t].clear();  // redone serially below
+                    }
+                });
+                started = true;
             } catch (const std::system_error &) {
-                for (auto &t : workers) t.join();
-                workers.clear();
-                std::fill(mok.begin(), mok.end(), 0);
-                for (int r = 0; r < runs; r++) mok[r] = multilevel_separator(h, mpart[r], r);
             }
-        } else {
-            mok[0] = multilevel_separator(h, mpart[0], 0);
         }
-        std::vector<int8_t> part;
-        double best_ratio = level_separator(h, part, level, queue) ? separator_ratio(part) : 1e300;
-        for (auto &t : workers) t.join();
-        for (int r = 0; r < runs; r++)
-            if (mok[r] && separator_ratio(mpart[r]) < best_ratio) {
-                best_ratio = separator_ratio(mpart[r]);
-                part.swap(mpart[r]);
-            }
-        if (part.empty()) {
-            std::vector<int32_t> o = order_amd(h, 0.0);
-            for (int32_t t : o) order.push_back(vs[t]);
+        if (!started) serial.push_back(t);
+    }
+    for (size_t t : serial) nd_serial(g, tasks[t].verts, leaf, main_w, sub[t]);
+    for (auto &th : workers) th.join();
+    for (size_t t = 0; t < tasks.size(); t++) {
+        if (tasks[t].done) {
+            order.insert(order.end(), tasks[t].verts.begin(), tasks[t].verts.end());
             continue;
         }
-        std::vector<int32_t> P1, P2, S;
-        for (int32_t v = 0; v < n; v++) (part[v] == 0 ? S : part[v] == 1 ? P1 : P2).push_back(vs[v]);
-        // order: P1, P2, then the separator
-        stack.push_back({std::move(S), true});
-        stack.push_back({std::move(P2), false});
-        stack.push_back({std::move(P1), false});
+        if (sub[t].size() != tasks[t].verts.size()) {  // a worker failed: redo here
+            sub[t].clear();
+            nd_serial(g, tasks[t].verts, leaf, main_w, sub[t]);
+        }
+        order.insert(order.end(), sub[t].begin(), sub[t].end());
     }
     for (int32_t v : dense) order.push_back(v);
     return order;
