@@ -43,6 +43,15 @@
  *   - the small-denominator threshold of the backward error is
  *     tau_i = 1000 N eps (||M_i||_1-row * ||d||_inf + |f_i|).
  *
+ * Pivoting for matrices that are not quasi-definite (Sec. 4.5, the variation
+ * of Bunch-Kaufman pivoting), as a dense kernel of its own
+ * (orc_dense_ldlt_bk); the multifrontal path above does not call it.
+ * Readings: the search covers only the rows and columns of the current pivot
+ * block that are not yet eliminated; gamma_r is the largest off-diagonal
+ * magnitude of row/column r there; the pre-swap puts the remaining block
+ * diagonal of largest magnitude (first on ties) at the pivot position before
+ * each pivot is chosen; a lifted pivot keeps the sign of M_pp (+ for 0).
+ *
  * Parity unpinned: the fill-reducing ordering itself (taken as an input).
  */
 #include <math.h>
@@ -1025,4 +1034,143 @@ void orc_get_matrix(const orc *o, int64_t *Mcp, int32_t *Mri, double *Mx) {
     if (Mcp) memcpy(Mcp, o->Mcp, sizeof(int64_t) * (o->N + 1));
     if (Mri) memcpy(Mri, o->Mri, sizeof(int32_t) * o->Mcp[o->N]);
     if (Mx) memcpy(Mx, o->Mx, sizeof(double) * o->Mcp[o->N]);
+}
+
+/* ------------------------------------------- Bunch-Kaufman pivoting (dense) */
+
+/* Symmetric interchange of rows/columns a and b of the n x n matrix A
+ * (column-major, both triangles kept) and of perm. */
+static void bk_swap(int n, double *A, int32_t *perm, int a, int b) {
+    if (a == b) return;
+#define AE(i, j) A[(int64_t)(j) * n + (i)]
+    for (int i = 0; i < n; i++) {
+        double t = AE(i, a);
+        AE(i, a) = AE(i, b);
+        AE(i, b) = t;
+    }
+    for (int j = 0; j < n; j++) {
+        double t = AE(a, j);
+        AE(a, j) = AE(b, j);
+        AE(b, j) = t;
+    }
+#undef AE
+    int32_t t = perm[a];
+    perm[a] = perm[b];
+    perm[b] = t;
+}
+
+/* LDL^T with the pivoting of Sec. 4.5 of the n x n symmetric matrix A
+ * (column-major, both triangles), in pivot blocks of nb columns; only the
+ * entries of the current block that are not yet eliminated take part in the
+ * pivot search, as the paper restricts it to the diagonal block B_D.  For
+ * each pivot position p of the block:
+ *   pre-swap   the remaining block diagonal of largest magnitude moves to p;
+ *   gamma_p    = |M_rp|, the largest magnitude below the pivot in the block;
+ *   lift       if max(|M_pp|, gamma_p) <= b1, the pivot becomes
+ *              sign(M_pp) b1 (a 1x1 pivot; lift[p] = new - old);
+ *   1x1 at p   if |M_pp| >= alpha gamma_p, or |M_pp| gamma_r >= alpha gamma_p^2
+ *              (gamma_r the largest off-diagonal magnitude of row r);
+ *   1x1 at r   if |M_rr| >= alpha gamma_r (r interchanged with p);
+ *   2x2 (p, r) otherwise (r interchanged with p + 1).
+ * (With the pre-swap, |M_rr| <= |M_pp| < alpha gamma_p <= alpha gamma_r
+ * whenever the third test is reached, so it never fires; it is kept as the
+ * paper states the rule.)
+ * Every pivot eliminates its columns from all rows below (a right-looking
+ * update of the whole trailing matrix).  On return
+ *   P A P^T + diag(lift) = L D L^T,  P e_k = e_{perm[k]} (perm[new] = old),
+ * with L unit lower triangular in the strict lower triangle of A, D[k] the
+ * diagonal of D, Doff[k] = D(k+1, k) for the first column of a 2x2 block
+ * (else 0) and bsize[k] = 1 or 2 for the first column of a block, 0 for the
+ * second.  Returns ORC_OK, ORC_ERR_ARG or ORC_ERR_NONFINITE. */
+int orc_dense_ldlt_bk(int n, int nb, double *A, double b1, double alpha, int32_t *perm, double *D, double *Doff,
+                      int32_t *bsize, double *lift) {
+    if (n < 0 || nb < 1 || !(b1 >= 0.0) || !(alpha > 0.0 && alpha < 1.0)) return ORC_ERR_ARG;
+#define AE(i, j) A[(int64_t)(j) * n + (i)]
+    for (int k = 0; k < n; k++) {
+        perm[k] = k;
+        D[k] = Doff[k] = lift[k] = 0.0;
+        bsize[k] = 0;
+    }
+    int rc = ORC_OK;
+    for (int b0 = 0; b0 < n; b0 += nb) {
+        const int b1c = b0 + nb < n ? b0 + nb : n;
+        int p = b0;
+        while (p < b1c) {
+            /* pre-swap: the largest remaining block diagonal to position p */
+            int q = p;
+            for (int t = p + 1; t < b1c; t++)
+                if (fabs(AE(t, t)) > fabs(AE(q, q))) q = t;
+            bk_swap(n, A, perm, p, q);
+            /* gamma_p and r within the block */
+            int r = -1;
+            double gp = 0.0;
+            for (int i = p + 1; i < b1c; i++)
+                if (fabs(AE(i, p)) > gp) {
+                    gp = fabs(AE(i, p));
+                    r = i;
+                }
+            const double app = AE(p, p);
+            int two = 0;
+            if ((fabs(app) > gp ? fabs(app) : gp) <= b1) {
+                const double dn = app < 0.0 ? -b1 : b1;
+                lift[p] = dn - app;
+                AE(p, p) = dn;
+            } else if (fabs(app) < alpha * gp) {
+                double gr = 0.0;
+                for (int i = p; i < b1c; i++)
+                    if (i != r && fabs(AE(i, r)) > gr) gr = fabs(AE(i, r));
+                if (fabs(app) * gr >= alpha * gp * gp) {
+                    /* 1x1 at p */
+                } else if (fabs(AE(r, r)) >= alpha * gr) {
+                    bk_swap(n, A, perm, p, r);
+                } else {
+                    bk_swap(n, A, perm, p + 1, r);
+                    two = 1;
+                }
+            }
+            if (!two) {
+                const double d = AE(p, p);
+                D[p] = d;
+                bsize[p] = 1;
+                if (!isfinite(d) || d == 0.0) rc = ORC_ERR_NONFINITE;
+                for (int i = p + 1; i < n; i++) AE(i, p) /= d;
+                for (int j = p + 1; j < n; j++)
+                    for (int i = j; i < n; i++) {
+                        AE(i, j) -= AE(i, p) * d * AE(j, p);
+                        AE(j, i) = AE(i, j);
+                    }
+                for (int i = p + 1; i < n; i++) AE(p, i) = 0.0;  /* upper part of L's column: unused */
+                p += 1;
+            } else {
+                const double e11 = AE(p, p), e21 = AE(p + 1, p), e22 = AE(p + 1, p + 1);
+                const double det = e11 * e22 - e21 * e21;
+                D[p] = e11;
+                D[p + 1] = e22;
+                Doff[p] = e21;
+                bsize[p] = 2;
+                if (!isfinite(det) || det == 0.0) rc = ORC_ERR_NONFINITE;
+                /* [l_ip, l_ip+1] = [a_ip, a_ip+1] E^-1 for every row below the block pair */
+                for (int i = p + 2; i < n; i++) {
+                    const double x = AE(i, p), y = AE(i, p + 1);
+                    AE(i, p) = (x * e22 - y * e21) / det;
+                    AE(i, p + 1) = (y * e11 - x * e21) / det;
+                }
+                /* A_ij -= [l_ip l_ip+1] E [l_jp l_jp+1]^T */
+                for (int j = p + 2; j < n; j++) {
+                    const double wj0 = e11 * AE(j, p) + e21 * AE(j, p + 1);
+                    const double wj1 = e21 * AE(j, p) + e22 * AE(j, p + 1);
+                    for (int i = j; i < n; i++) {
+                        AE(i, j) -= AE(i, p) * wj0 + AE(i, p + 1) * wj1;
+                        AE(j, i) = AE(i, j);
+                    }
+                }
+                AE(p + 1, p) = 0.0;  /* L is unit lower triangular: the 2x2 block lives in D */
+                for (int i = p + 1; i < n; i++) AE(p, i) = 0.0;
+                for (int i = p + 2; i < n; i++) AE(p + 1, i) = 0.0;
+                p += 2;
+            }
+        }
+    }
+#undef AE
+    return rc;
 }

@@ -58,6 +58,9 @@ def _load():
     lib.orc_factorise.argtypes = [P, f64p, ct.c_double, ct.c_double, ct.c_double]
     lib.orc_factorise.restype = ct.c_int
     lib.orc_get_factor.argtypes = [P, f64p, f64p, f64p, i64p]
+    lib.orc_dense_ldlt_bk.argtypes = [ct.c_int, ct.c_int, f64p, ct.c_double, ct.c_double, i32p, f64p, f64p, i32p,
+                                      f64p]
+    lib.orc_dense_ldlt_bk.restype = ct.c_int
     lib.orc_get_stats.argtypes = [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
                                   ct.POINTER(ct.c_double)]
     lib.orc_solve.argtypes = [P, f64p, f64p, f64p, f64p, f64p, ct.c_double, ct.c_int]
@@ -189,3 +192,29 @@ def backward_error(r, ad, ae, f, d):
     lib = _load()
     return lib.orc_backward_error(int(len(r)), _c(r, np.float64), _c(ad, np.float64), _c(ae, np.float64),
                                   _c(f, np.float64), _c(d, np.float64))
+
+
+BK_ALPHA = (1.0 + 17.0 ** 0.5) / 8.0  # the usual Bunch-Kaufman threshold (Sec. 4.5)
+
+
+def dense_ldlt_bk(A, nb, b1, alpha=BK_ALPHA):
+    """LDL^T of the dense symmetric matrix A with the pivoting of Sec. 4.5
+    (a Bunch-Kaufman variation restricted to pivot blocks of nb columns, with
+    a pre-swap and pivot lifting to magnitude b1).  Returns a dict with L
+    (unit lower triangular), D and Doff (the block diagonal: Doff[k] =
+    D(k+1, k) of a 2x2 block), bsize (1 or 2 at a block's first column, 0 at
+    the second), perm (perm[new] = old), lift and rc, so that
+    A[perm][:, perm] + diag(lift) = L Dblock L^T."""
+    A = np.array(A, dtype=np.float64)
+    n = A.shape[0]
+    F = np.asfortranarray(A).ravel(order="F").copy()
+    perm = np.zeros(n, np.int32)
+    D = np.zeros(n)
+    Doff = np.zeros(n)
+    bsize = np.zeros(n, np.int32)
+    lift = np.zeros(n)
+    rc = _load().orc_dense_ldlt_bk(n, int(nb), F, float(b1), float(alpha), perm, D, Doff, bsize, lift)
+    M = F.reshape((n, n), order="F")
+    L = np.tril(M, -1) + np.eye(n)
+    Dblock = np.diag(D) + np.diag(Doff[:-1], -1) + np.diag(Doff[:-1], 1) if n > 1 else np.diag(D)
+    return dict(L=L, D=D, Doff=Doff, Dblock=Dblock, bsize=bsize, perm=perm, lift=lift, rc=rc)

@@ -472,3 +472,124 @@ def test_rejects_bad_input():
     bad[0] = lp.m + 3
     with pytest.raises(ValueError):
         Oracle(lp.m, lp.n, lp.colptr, bad, lp.vals)
+
+
+# --------------------------------------------- Bunch-Kaufman pivoting (dense)
+# Sec. 4.5: the variation of Bunch-Kaufman pivoting inside pivot blocks, with a
+# pre-swap and pivot lifting.  Pinned by the factorisation identity (checked by
+# numpy products), Sylvester's law of inertia, the element-growth bound of
+# Bunch-Kaufman, and hand-worked cases.
+
+def _bk_residual(A, r):
+    P = r["perm"]
+    R = r["L"] @ r["Dblock"] @ r["L"].T - (A[np.ix_(P, P)] + np.diag(r["lift"]))
+    return np.abs(R).max() / max(np.abs(A).max(), 1e-300)
+
+
+@pytest.mark.parametrize("n,nb", [(1, 1), (2, 2), (13, 4), (40, 8), (40, 40), (33, 32), (50, 7)])
+def test_bk_factor_identity_and_permutation(n, nb):
+    from oracle.oracle import dense_ldlt_bk
+
+    rng = np.random.default_rng(100 + n + nb)
+    A = rng.standard_normal((n, n))
+    A = A + A.T
+    r = dense_ldlt_bk(A, nb, 0.0)
+    assert r["rc"] == 0
+    assert np.array_equal(np.sort(r["perm"]), np.arange(n))
+    assert _bk_residual(A, r) <= 1e-12
+    # blocks: a 2x2 block's second column carries 0, and the block sizes tile n
+    assert r["bsize"].sum() == n
+    for k in np.flatnonzero(r["bsize"] == 2):
+        assert r["bsize"][k + 1] == 0 and (k // nb) == ((k + 1) // nb)  # a 2x2 block stays inside its pivot block
+    # pivots are exchanged only within their pivot block
+    assert all(r["perm"][k] // nb == k // nb for k in range(n))
+    r2 = dense_ldlt_bk(A, nb, 0.0)
+    assert all(np.array_equal(r[key], r2[key]) for key in ("L", "D", "Doff", "perm", "bsize"))
+
+
+def test_bk_needs_a_2x2_pivot():
+    """[[0, 1], [1, 0]] has no usable 1x1 pivot: the whole matrix is one 2x2
+    block of D and L is the identity."""
+    from oracle.oracle import dense_ldlt_bk
+
+    A = np.array([[0.0, 1.0], [1.0, 0.0]])
+    r = dense_ldlt_bk(A, 2, 0.0)
+    assert r["rc"] == 0 and list(r["bsize"]) == [2, 0]
+    assert np.array_equal(r["Dblock"], A) and np.array_equal(r["L"], np.eye(2))
+
+
+def test_bk_inertia_and_growth():
+    """Sylvester: the block diagonal D has the inertia of A.  With one pivot
+    block (the classical setting) every entry of L is bounded by the
+    Bunch-Kaufman growth bound 1 / (1 - alpha) (1 / alpha for 1x1 pivots)."""
+    from oracle.oracle import BK_ALPHA, dense_ldlt_bk
+
+    rng = np.random.default_rng(7)
+    for trial in range(5):
+        n = 30 + 3 * trial
+        A = rng.standard_normal((n, n))
+        A = A + A.T + np.diag(rng.standard_normal(n) * (10.0 if trial % 2 else 0.01))
+        for nb in (n, 8):
+            r = dense_ldlt_bk(A, nb, 0.0)
+            ev_a = np.linalg.eigvalsh(A)
+            ev_d = np.linalg.eigvalsh(r["Dblock"])
+            assert (ev_a > 0).sum() == (ev_d > 0).sum() and (ev_a < 0).sum() == (ev_d < 0).sum()
+        r = dense_ldlt_bk(A, n, 0.0)
+        assert np.abs(np.tril(r["L"], -1)).max() <= 1.0 / (1.0 - BK_ALPHA) + 1e-12
+
+
+def test_bk_pre_swap_and_no_pivoting_cases():
+    """The pre-swap moves the largest diagonal of the block to the pivot
+    position; a diagonally dominant matrix then needs 1x1 pivots only.  With
+    blocks of one column nothing can be exchanged: plain LDL^T."""
+    from oracle.oracle import dense_ldlt_bk
+
+    rng = np.random.default_rng(3)
+    n = 6
+    A = 0.01 * rng.standard_normal((n, n))
+    A = A + A.T + np.diag([2.0, -3.0, 1.5, 9.0, -4.0, 2.5])
+    r = dense_ldlt_bk(A, n, 0.0)
+    assert r["perm"][0] == 3 and np.all(r["bsize"] == 1)
+    assert _bk_residual(A, r) <= 1e-14
+    B = rng.standard_normal((n, n))
+    B = B + B.T + 6.0 * np.eye(n)
+    r = dense_ldlt_bk(B, 1, 0.0)
+    assert np.array_equal(r["perm"], np.arange(n)) and np.all(r["bsize"] == 1)
+    assert _bk_residual(B, r) <= 1e-13
+
+
+def test_bk_lift_keeps_the_sign():
+    """A pivot whose magnitude and column are below b1 is lifted to
+    magnitude b1 with the sign of M_pp; the larger diagonal goes first."""
+    from oracle.oracle import dense_ldlt_bk
+
+    A = np.array([[-1e-20, 0.0], [0.0, 1.0]])
+    r = dense_ldlt_bk(A, 2, 1e-10)
+    assert list(r["perm"]) == [1, 0]
+    assert r["D"][0] == 1.0 and r["D"][1] == -1e-10
+    assert r["lift"][1] == -1e-10 - (-1e-20) and r["lift"][0] == 0.0
+
+
+def test_bk_decision_rule_hand_cases():
+    """Hand-worked 3 x 3 blocks (alpha = (1 + sqrt 17) / 8 = 0.640):
+    M = [[a, g, 0], [g, b, h], [0, h, c]] with a the largest diagonal, so
+    p = 0, r = 1, gamma_p = |g|, gamma_r = max(|g|, |h|).
+      a = .5, g = 1, h = 2: |a| < alpha |g|, but |a| gamma_r = 1 >= alpha g^2
+        -> 1x1 pivot at p;
+      a = .5, g = 1, h = .5: |a| gamma_r = .5 < alpha, |b| = .1 < alpha gamma_r
+        -> 2x2 pivot (0, 1);
+      a = .7, g = 1: |a| >= alpha |g| -> 1x1 pivot at p."""
+    from oracle.oracle import dense_ldlt_bk
+
+    def block(a, g, h, b=0.1, c=0.1):
+        return np.array([[a, g, 0.0], [g, b, h], [0.0, h, c]])
+
+    r = dense_ldlt_bk(block(0.5, 1.0, 2.0), 3, 0.0)
+    assert r["perm"][0] == 0 and r["bsize"][0] == 1
+    r = dense_ldlt_bk(block(0.5, 1.0, 0.5), 3, 0.0)
+    assert list(r["perm"][:2]) == [0, 1] and r["bsize"][0] == 2
+    assert r["Dblock"][1, 0] == 1.0 and r["D"][0] == 0.5 and r["D"][1] == 0.1
+    r = dense_ldlt_bk(block(0.7, 1.0, 0.5), 3, 0.0)
+    assert r["perm"][0] == 0 and r["bsize"][0] == 1
+    for M in (block(0.5, 1.0, 2.0), block(0.5, 1.0, 0.5), block(0.7, 1.0, 0.5)):
+        assert _bk_residual(M, dense_ldlt_bk(M, 3, 0.0)) <= 1e-15
