@@ -1174,3 +1174,35 @@ int orc_dense_ldlt_bk(int n, int nb, double *A, double b1, double alpha, int32_t
 #undef AE
     return rc;
 }
+
+/* Solve A x = b with a factorisation from orc_dense_ldlt_bk (lift zero, or
+ * the lifted matrix P^T (P A P^T + diag(lift)) P is the one solved):
+ *   y = P b;  L z = y (forward);  D w = z (1x1 divisions, 2x2 blocks by
+ *   their inverse);  L^T v = w (backward);  x = P^T v.
+ * Lf holds L in its strict lower triangle (n x n, column-major). */
+int orc_dense_solve_bk(int n, const double *Lf, const double *D, const double *Doff, const int32_t *bsize,
+                       const int32_t *perm, const double *b, double *x) {
+    if (n < 0) return ORC_ERR_ARG;
+    double *v = (double *)xmalloc(NZ(n) * sizeof(double));
+    for (int k = 0; k < n; k++) v[k] = b[perm[k]];
+    for (int j = 0; j < n; j++)
+        for (int i = j + 1; i < n; i++) v[i] -= Lf[(int64_t)j * n + i] * v[j];
+    for (int k = 0; k < n;) {
+        if (bsize[k] == 2) {
+            const double e11 = D[k], e21 = Doff[k], e22 = D[k + 1];
+            const double det = e11 * e22 - e21 * e21;
+            const double y0 = v[k], y1 = v[k + 1];
+            v[k] = (e22 * y0 - e21 * y1) / det;
+            v[k + 1] = (e11 * y1 - e21 * y0) / det;
+            k += 2;
+        } else {
+            v[k] /= D[k];
+            k += 1;
+        }
+    }
+    for (int j = n - 1; j >= 0; j--)
+        for (int i = j + 1; i < n; i++) v[j] -= Lf[(int64_t)j * n + i] * v[i];
+    for (int k = 0; k < n; k++) x[perm[k]] = v[k];
+    free(v);
+    return ORC_OK;
+}

@@ -61,6 +61,8 @@ def _load():
     lib.orc_dense_ldlt_bk.argtypes = [ct.c_int, ct.c_int, f64p, ct.c_double, ct.c_double, i32p, f64p, f64p, i32p,
                                       f64p]
     lib.orc_dense_ldlt_bk.restype = ct.c_int
+    lib.orc_dense_solve_bk.argtypes = [ct.c_int, f64p, f64p, f64p, i32p, i32p, f64p, f64p]
+    lib.orc_dense_solve_bk.restype = ct.c_int
     lib.orc_get_stats.argtypes = [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
                                   ct.POINTER(ct.c_double)]
     lib.orc_solve.argtypes = [P, f64p, f64p, f64p, f64p, f64p, ct.c_double, ct.c_int]
@@ -218,3 +220,17 @@ def dense_ldlt_bk(A, nb, b1, alpha=BK_ALPHA):
     L = np.tril(M, -1) + np.eye(n)
     Dblock = np.diag(D) + np.diag(Doff[:-1], -1) + np.diag(Doff[:-1], 1) if n > 1 else np.diag(D)
     return dict(L=L, D=D, Doff=Doff, Dblock=Dblock, bsize=bsize, perm=perm, lift=lift, rc=rc)
+
+
+def dense_solve_bk(fac, b):
+    """Solve with a factorisation from dense_ldlt_bk: x with
+    P^T (L D L^T) P x = b, i.e. A x = b when nothing was lifted."""
+    n = fac["L"].shape[0]
+    Lf = np.asfortranarray(fac["L"]).ravel(order="F").copy()
+    x = np.zeros(n)
+    rc = _load().orc_dense_solve_bk(n, Lf, np.ascontiguousarray(fac["D"]), np.ascontiguousarray(fac["Doff"]),
+                                    np.ascontiguousarray(fac["bsize"]), np.ascontiguousarray(fac["perm"]),
+                                    np.ascontiguousarray(b, dtype=np.float64), x)
+    if rc:
+        raise RuntimeError(f"orc_dense_solve_bk failed ({rc})")
+    return x

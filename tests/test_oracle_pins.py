@@ -593,3 +593,26 @@ def test_bk_decision_rule_hand_cases():
     assert r["perm"][0] == 0 and r["bsize"][0] == 1
     for M in (block(0.5, 1.0, 2.0), block(0.5, 1.0, 0.5), block(0.7, 1.0, 0.5)):
         assert _bk_residual(M, dense_ldlt_bk(M, 3, 0.0)) <= 1e-15
+
+
+def test_bk_solve_against_lapack():
+    """The solve with a pivoted factorisation (P b, forward with L, 1x1 and
+    2x2 blocks of D, backward with L^T, P^T) agrees with LAPACK's solve of
+    the original matrix on random indefinite systems, including blocks that
+    force 2x2 pivots."""
+    from oracle.oracle import dense_ldlt_bk, dense_solve_bk
+
+    rng = np.random.default_rng(11)
+    for n, nb in ((2, 2), (25, 8), (40, 40), (37, 5)):
+        A = rng.standard_normal((n, n))
+        A = A + A.T
+        if n == 2:
+            A = np.array([[0.0, 1.0], [1.0, 0.0]])
+        fac = dense_ldlt_bk(A, nb, 0.0)
+        assert np.all(fac["lift"] == 0.0)
+        b = rng.standard_normal(n)
+        x = dense_solve_bk(fac, b)
+        ref = np.linalg.solve(A, b)
+        cond = np.linalg.cond(A)
+        assert np.abs(x - ref).max() <= 1e-13 * cond * max(1.0, np.abs(ref).max()), (n, nb)
+        assert np.abs(A @ x - b).max() <= 1e-12 * np.abs(A).max() * max(1.0, np.abs(x).max())
