@@ -1081,10 +1081,15 @@ static void bk_swap(int n, double *A, int32_t *perm, int a, int b) {
  * with L unit lower triangular in the strict lower triangle of A, D[k] the
  * diagonal of D, Doff[k] = D(k+1, k) for the first column of a 2x2 block
  * (else 0) and bsize[k] = 1 or 2 for the first column of a block, 0 for the
- * second.  Returns ORC_OK, ORC_ERR_ARG or ORC_ERR_NONFINITE. */
-int orc_dense_ldlt_bk(int n, int nb, double *A, double b1, double alpha, int32_t *perm, double *D, double *Doff,
-                      int32_t *bsize, double *lift) {
-    if (n < 0 || nb < 1 || !(b1 >= 0.0) || !(alpha > 0.0 && alpha < 1.0)) return ORC_ERR_ARG;
+ * second.  orc_front_ldlt_bk eliminates only the first k columns, as in a
+ * front with k fully-summed columns: only they are interchanged, and the
+ * trailing (n-k) x (n-k) block ends as the Schur complement (D, bsize, lift
+ * are zero there, the identity holds with L's trailing block and that Schur
+ * complement in D's place).  Returns ORC_OK, ORC_ERR_ARG or
+ * ORC_ERR_NONFINITE. */
+int orc_front_ldlt_bk(int n, int k, int nb, double *A, double b1, double alpha, int32_t *perm, double *D,
+                      double *Doff, int32_t *bsize, double *lift) {
+    if (n < 0 || k < 0 || k > n || nb < 1 || !(b1 >= 0.0) || !(alpha > 0.0 && alpha < 1.0)) return ORC_ERR_ARG;
 #define AE(i, j) A[(int64_t)(j) * n + (i)]
     for (int k = 0; k < n; k++) {
         perm[k] = k;
@@ -1092,8 +1097,8 @@ int orc_dense_ldlt_bk(int n, int nb, double *A, double b1, double alpha, int32_t
         bsize[k] = 0;
     }
     int rc = ORC_OK;
-    for (int b0 = 0; b0 < n; b0 += nb) {
-        const int b1c = b0 + nb < n ? b0 + nb : n;
+    for (int b0 = 0; b0 < k; b0 += nb) {
+        const int b1c = b0 + nb < k ? b0 + nb : k;
         int p = b0;
         while (p < b1c) {
             /* pre-swap: the largest remaining block diagonal to position p */
@@ -1173,6 +1178,11 @@ int orc_dense_ldlt_bk(int n, int nb, double *A, double b1, double alpha, int32_t
     }
 #undef AE
     return rc;
+}
+
+int orc_dense_ldlt_bk(int n, int nb, double *A, double b1, double alpha, int32_t *perm, double *D, double *Doff,
+                      int32_t *bsize, double *lift) {
+    return orc_front_ldlt_bk(n, n, nb, A, b1, alpha, perm, D, Doff, bsize, lift);
 }
 
 /* Solve A x = b with a factorisation from orc_dense_ldlt_bk (lift zero, or

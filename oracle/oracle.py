@@ -61,6 +61,9 @@ def _load():
     lib.orc_dense_ldlt_bk.argtypes = [ct.c_int, ct.c_int, f64p, ct.c_double, ct.c_double, i32p, f64p, f64p, i32p,
                                       f64p]
     lib.orc_dense_ldlt_bk.restype = ct.c_int
+    lib.orc_front_ldlt_bk.argtypes = [ct.c_int, ct.c_int, ct.c_int, f64p, ct.c_double, ct.c_double, i32p, f64p, f64p,
+                                      i32p, f64p]
+    lib.orc_front_ldlt_bk.restype = ct.c_int
     lib.orc_dense_solve_bk.argtypes = [ct.c_int, f64p, f64p, f64p, i32p, i32p, f64p, f64p]
     lib.orc_dense_solve_bk.restype = ct.c_int
     lib.orc_get_stats.argtypes = [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
@@ -234,3 +237,24 @@ def dense_solve_bk(fac, b):
     if rc:
         raise RuntimeError(f"orc_dense_solve_bk failed ({rc})")
     return x
+
+
+def front_ldlt_bk(A, k, nb, b1, alpha=BK_ALPHA):
+    """Partial factorisation of a dense front with k fully-summed columns and
+    the pivoting of Sec. 4.5: as dense_ldlt_bk on the first k columns, with
+    S (the Schur complement of the trailing block) in the result."""
+    A = np.array(A, dtype=np.float64)
+    n = A.shape[0]
+    F = np.asfortranarray(A).ravel(order="F").copy()
+    perm = np.zeros(n, np.int32)
+    D = np.zeros(n)
+    Doff = np.zeros(n)
+    bsize = np.zeros(n, np.int32)
+    lift = np.zeros(n)
+    rc = _load().orc_front_ldlt_bk(n, int(k), int(nb), F, float(b1), float(alpha), perm, D, Doff, bsize, lift)
+    M = F.reshape((n, n), order="F")
+    L = np.tril(M[:, :k], -1)
+    L[np.arange(k), np.arange(k)] = 1.0
+    Dk = np.diag(D[:k]) + (np.diag(Doff[: k - 1], -1) + np.diag(Doff[: k - 1], 1) if k > 1 else 0.0)
+    S = np.tril(M[k:, k:]) + np.tril(M[k:, k:], -1).T
+    return dict(L=L, Dblock=Dk, D=D, Doff=Doff, bsize=bsize, perm=perm, lift=lift, S=S, rc=rc)

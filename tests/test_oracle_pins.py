@@ -616,3 +616,27 @@ def test_bk_solve_against_lapack():
         cond = np.linalg.cond(A)
         assert np.abs(x - ref).max() <= 1e-13 * cond * max(1.0, np.abs(ref).max()), (n, nb)
         assert np.abs(A @ x - b).max() <= 1e-12 * np.abs(A).max() * max(1.0, np.abs(x).max())
+
+
+def test_bk_front_partial_factorisation():
+    """A front with k fully-summed columns: only they are interchanged (the
+    contribution rows keep their order), P A P^T + diag(lift) equals
+    [L1; L2] D [L1; L2]^T plus the Schur complement S in the trailing block,
+    and S equals A22 - A21 A11^-1 A12 of the permuted matrix (LAPACK)."""
+    from oracle.oracle import front_ldlt_bk
+
+    rng = np.random.default_rng(21)
+    for f, k, nb in ((20, 8, 4), (37, 32, 32), (30, 13, 8), (12, 0, 4), (9, 9, 3)):
+        A = rng.standard_normal((f, f))
+        A = A + A.T
+        r = front_ldlt_bk(A, k, nb, 0.0)
+        assert r["rc"] == 0
+        P = r["perm"]
+        assert np.array_equal(P[k:], np.arange(k, f)) and np.array_equal(np.sort(P[:k]), np.arange(k))
+        Ap = A[np.ix_(P, P)] + np.diag(r["lift"])
+        R = r["L"] @ r["Dblock"] @ r["L"].T
+        R[k:, k:] += r["S"]
+        assert np.abs(R - Ap).max() <= 1e-12 * np.abs(A).max()
+        if 0 < k < f:
+            S = Ap[k:, k:] - Ap[k:, :k] @ np.linalg.solve(Ap[:k, :k], Ap[:k, k:])
+            assert np.abs(S - r["S"]).max() <= 1e-10 * max(1.0, np.abs(S).max()) * np.linalg.cond(Ap[:k, :k])
