@@ -117,7 +117,8 @@ typedef struct ipm_info {
     int32_t m, n, N, form, ordering;
     int32_t nsuper, nlevels, nfronts_small, nfronts_large;
     int32_t max_front, max_k;
-    int64_t nnz_A, nnz_K_lower, nnz_L;      /* nnz_L counts stored supernodal entries */
+    int64_t nnz_A, nnz_K_lower, nnz_L;      /* nnz_L: entries of L in the supernodal structure,
+                                               sum of k f - k (k - 1) / 2, unit diagonal included */
     double flops_factor;                    /* sum over fronts of sum_{i=1..k} (f-i)(f-i+3) */
     double flops_tensor;                    /* part of flops_factor in tensor-core updates */
     int64_t device_bytes;                   /* device memory held by the context */
@@ -282,24 +283,34 @@ int ipm_graph_launch(ipm_ctx *ctx, void *stream);
  * ipm_solve (for launch accounting). */
 int ipm_launch_counts(const ipm_ctx *ctx, int32_t *factorise_launches, int32_t *solve_launches);
 
-/* Allocation-free variant of ipm_solve for the augmented system (the paper has no counterpart: this
- * entry point exists for callers that cannot allocate device memory at solve
- * time, for example code running while a stream is captured into a CUDA
- * graph, where cudaMalloc is not allowed, or a host library that must not
- * change the device's allocation state).  Same arguments, kernels and
- * results as ipm_solve; its work vectors live in one file-scope device array
- * of 2^21 doubles (16 MiB) that every GPU loading this library holds until
- * the process exits, instead of in the context's own buffers, and the call
- * makes no cudaMalloc, cudaFree or other allocating call.
- *   - Needs 7 N + (sum of the front sizes) doubles; a larger problem returns
- *     IPM_ERR_SCRATCH_TOO_SMALL before anything is enqueued.
- *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
- *   - All calls share the array: calls that overlap on the GPU (other
- *     streams, other threads, other contexts) race and must be serialised by
- *     the caller.  Every work vector is written before it is read within a
- *     call, so the previous call's contents need no clearing.
- *   - Like ipm_solve it synchronises `stream` once per refinement step. */
+/* Allocation-free solve of the augmented system (the paper has no
+ * counterpart).  It exists for callers that cannot allocate device memory
+ * when they need a solve: a host library or an optimisation callback that
+ * runs under a fixed device-memory budget, or that must not change the
+ * device's allocation state (an allocation there can fail, or make a caching
+ * allocator release and re-reserve memory).  Its work vectors live in one
+ * file-scope device array of 2^21 doubles (16 MiB) that every GPU loading
+ * this library holds until the process exits; the call makes no cudaMalloc,
+ * cudaFree or other allocating call.  Arguments as ipm_solve.
+ * It is a simpler variant, not a copy, of ipm_solve:
+ *   - it runs the per-level triangular sweeps (one launch per tree level)
+ *     instead of the persistent sweeps, so its solution agrees with
+ *     ipm_solve's to the refinement accuracy, not bit for bit;
+ *   - classical refinement only: no GMRES, and a tensor-core factor whose
+ *     refinement stalls is not refactorised in FP64; the call then returns
+ *     IPM_WARN_REFINE_NOT_CONVERGED with the best iterate it reached;
+ *   - its decisions are taken on the host: it synchronises `stream` after
+ *     the first solve and after every refinement step;
+ *   - ipm_get_info reports its backward error and step count afterwards.
+ * Limits, checked before anything is enqueued (IPM_ERR_SCRATCH_TOO_SMALL):
+ * the work needs 7 N + sum over supernodes of (f_s - k_s) doubles (N
+ * unknowns, f_s - k_s the contribution rows of supernode s), and the largest
+ * front must fit the sweeps' shared memory (at most 25,600 rows).
+ * The first call on a device looks up the array's device address with that
+ * device current.  All calls share the array: calls that overlap on the GPU
+ * (other streams, other threads, other contexts) race and must be
+ * serialised by the caller.  Every work vector is written before it is read
+ * within a call, so the previous call's contents need no clearing. */
 int ipm_solve_noalloc(ipm_ctx *ctx, const double *r7_dev, const double *r1_dev, double *dx_dev, double *dy_dev,
                       void *stream);
 
@@ -345,6 +356,15 @@ int ipm_set_launch_shapes(ipm_ctx *ctx, const int32_t *small_threads, double lev
  * captured graph).
  * Errors: IPM_ERR_INVALID_ARG for a negative per_sm or one above 64. */
 int ipm_set_level_ctas(ipm_ctx *ctx, int32_t per_sm);
+
+/* Test hook for the pivot reciprocal (Sec. 4.4-4.5: every column of L is the
+ * pivot column scaled by 1/d).  For n doubles x (device) writes the
+ * reciprocal the factorisation uses (hardware estimate plus one third-order
+ * Newton-Raphson step, division outside [2^-1000, 2^1000] in magnitude) to
+ * rcp and CUDA's correctly rounded 1.0 / x to quo (both device, n doubles),
+ * on `stream` without synchronising.  Errors: IPM_ERR_INVALID_ARG for n < 0
+ * or a null pointer with n > 0. */
+int ipm_test_recip_pivot(const double *x_dev, double *rcp_dev, double *quo_dev, int64_t n, void *stream);
 
 /* ------------------------------------------------------------ measurement */
 /* Kernel classes reported by ipm_kernel_stats. */

@@ -169,6 +169,36 @@ class Oracle:
         return self.lib.orc_omega_K(self.h, _c(theta, np.float64), float(rho), float(delta), _c(r7, np.float64),
                                     _c(r1, np.float64), _c(dx, np.float64), _c(dy, np.float64))
 
+    def nnz_lower(self):
+        """Stored entries of the lower part of the matrix (K, or A A^T for the
+        normal equations), diagonal included."""
+        return int(self.lib.orc_nnzM(self.h))
+
+    def nnzL_stored(self):
+        """Entries of the supernodal L as stored: f_s x k_s per supernode."""
+        return int(self.lib.orc_nnzL_stored(self.h))
+
+    def nnzL(self):
+        """Entries of L in the supernodal structure, unit diagonal included:
+        supernode s holds k_s columns whose j-th (from 0) has f_s - j rows, so
+        sum over s of k f - k (k - 1) / 2."""
+        sym = self.symbolic()
+        k = np.diff(sym["sn_start"]).astype(np.int64)
+        f = np.diff(sym["sn_rptr"]).astype(np.int64)
+        return int(np.sum(k * f - k * (k - 1) // 2))
+
+    def front_flops(self):
+        """sum over supernodes of sum_{i=1..k} (f-i)(f-i+3), from the symbolic
+        result (the flop count of the blocked partial LDL^T of every front)."""
+        sym = self.symbolic()
+        k = np.diff(sym["sn_start"]).astype(np.int64)
+        f = np.diff(sym["sn_rptr"]).astype(np.int64)
+        total = 0.0
+        for fs, ks in zip(f.tolist(), k.tolist()):
+            i = np.arange(1, ks + 1, dtype=np.float64)
+            total += float(np.sum((fs - i) * (fs - i + 3)))
+        return total
+
     def matrix(self):
         nz = self.lib.orc_nnzM(self.h)
         cp = np.empty(self.N + 1, np.int64)
@@ -176,6 +206,38 @@ class Oracle:
         x = np.empty(nz, np.float64)
         self.lib.orc_get_matrix(self.h, cp, ri, x)
         return cp, ri, x
+
+
+def choose_form(lp, perm_as, perm_ne, az_as=0.1, az_ne=0.1, flop_rate=1.0e12, bandwidth=6.7e12, solves=3):
+    """Choice between the augmented system and the normal equations (Sec. 4.2:
+    the augmented system is the default, the normal equations are taken when
+    they are cheaper; the paper leaves the measure open).  Reading: the
+    per-iteration cost of a form is its front flops at flop_rate plus `solves`
+    solves, each reading L twice (8 bytes per entry of the supernodal
+    structure, Oracle.nnzL) at bandwidth;
+    forming A Theta~ A^T adds 2 flops per contributor pair (one pair per column
+    j of A and pair of its rows i <= r).  In order:
+      1. symbolic analysis of K in the order perm_as;
+      2. the normal equations are abandoned, cost -1, when the lower part of
+         A A^T (diagonal included) holds more entries than L of step 1;
+      3. otherwise symbolic analysis of A A^T in the order perm_ne;
+      4. the form with the smaller cost wins, ties to the augmented system.
+    The orders are inputs (ordering parity is not pinned); az_* are the
+    amalgamation thresholds the symbolic analyses use.
+    Returns (form, cost_as, cost_ne, nnz_ne_lower)."""
+    oa = Oracle.from_lp(lp, FORM_AS)
+    oa.analyse(perm_as, amalg_zero_frac=az_as)
+    nnzl_as = oa.nnzL()
+    cost_as = oa.front_flops() / flop_rate + solves * 2.0 * nnzl_as * 8.0 / bandwidth
+    on = Oracle.from_lp(lp, FORM_NE)
+    nnz_ne = on.nnz_lower()
+    if nnz_ne > nnzl_as:
+        return FORM_AS, cost_as, -1.0, nnz_ne
+    on.analyse(perm_ne, amalg_zero_frac=az_ne)
+    counts = np.diff(np.asarray(lp.colptr, dtype=np.int64)).astype(np.float64)
+    pairs = float(np.sum(counts * (counts + 1.0) / 2.0))
+    cost_ne = (on.front_flops() + 2.0 * pairs) / flop_rate + solves * 2.0 * on.nnzL() * 8.0 / bandwidth
+    return (FORM_NE if cost_ne < cost_as else FORM_AS), cost_as, cost_ne, nnz_ne
 
 
 def front_factor(F, k, signs, sreg, b1, nb=32):

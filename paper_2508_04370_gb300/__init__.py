@@ -131,12 +131,13 @@ def _load():
     lib.ipm_graph_launch.argtypes = [P, P]
     lib.ipm_launch_counts.argtypes = [P, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]
     lib.ipm_solve_noalloc.argtypes = [P, P, P, P, P, P]
+    lib.ipm_test_recip_pivot.argtypes = [P, P, P, ct.c_int64, P]
     lib.ipm_set_profiling.argtypes = [P, ct.c_int32]
     lib.ipm_kernel_stats.argtypes = [P, P, ct.c_int32]
     for name in ("ipm_create", "ipm_destroy", "ipm_analyse", "ipm_analyse_batch", "ipm_set_values", "ipm_factorise",
                  "ipm_solve", "ipm_iterate_host", "ipm_sync_status", "ipm_get_info", "ipm_get_symbolic",
                  "ipm_get_sizes", "ipm_get_factor", "ipm_graph_capture", "ipm_graph_launch", "ipm_launch_counts",
-                 "ipm_set_profiling", "ipm_kernel_stats", "ipm_solve_noalloc"):
+                 "ipm_set_profiling", "ipm_kernel_stats", "ipm_solve_noalloc", "ipm_test_recip_pivot"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -323,6 +324,11 @@ def ipm_launch_counts(ctx):
     a, b = ct.c_int32(), ct.c_int32()
     _load().ipm_launch_counts(ctx, ct.byref(a), ct.byref(b))
     return a.value, b.value
+
+
+def ipm_test_recip_pivot(x_dev, rcp_dev, quo_dev, stream=None) -> int:
+    return _load().ipm_test_recip_pivot(_dptr(x_dev), _dptr(rcp_dev), _dptr(quo_dev), int(x_dev.numel()),
+                                        _stream(stream))
 
 
 def ipm_set_profiling(ctx, enable=True) -> int:

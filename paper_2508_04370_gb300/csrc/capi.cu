@@ -2091,6 +2091,12 @@ int ipm_launch_counts(const ipm_ctx *c, int32_t *nf, int32_t *ns) {
 }
 
 
+int ipm_test_recip_pivot(const double *x, double *rcp, double *quo, int64_t n, void *stream) {
+    if (n < 0 || (n > 0 && (!x || !rcp || !quo))) return IPM_ERR_INVALID_ARG;
+    launch_test_recip(x, rcp, quo, n, (cudaStream_t)stream);
+    return to_err(cudaGetLastError());
+}
+
 int ipm_set_profiling(ipm_ctx *c, int32_t enable) {
     if (!c) return IPM_ERR_INVALID_ARG;
     c->prof_on = enable != 0;
@@ -2116,18 +2122,25 @@ int ipm_kernel_stats(ipm_ctx *c, ipm_kernel_stat *out, int32_t reset) {
 // ---------------------------------------------------------------------------
 // Allocation-free solve.
 //
-// Some callers cannot allocate device memory when they need a solve: code
-// that runs while a stream is being captured into a CUDA graph (cudaMalloc
-// is not allowed during capture and cudaFree synchronises the device),
-// callbacks of an optimisation loop that run under a strict memory budget or
-// inside a host library that must never change the device's allocation
-// state.  ipm_solve_noalloc serves them: it runs the same kernels as
-// ipm_solve but takes every work vector from one file-scope device array
+// Some callers cannot allocate device memory when they need a solve:
+// callbacks of an optimisation loop that run under a strict device-memory
+// budget, or a host library that must never change the device's allocation
+// state (an allocation there can fail, or make the caching allocator of the
+// surrounding framework release and re-reserve memory).  ipm_solve_noalloc
+// serves them: it takes every work vector from one file-scope device array
 // instead of the context's own buffers, and it calls no allocating routine.
+// It is a plain variant, not a copy of ipm_solve: it runs the per-level sweeps
+// (k_forward / k_backward, one launch per tree level), which need no
+// dependency counters and no per-context scratch, and classical refinement
+// only (no GMRES, and no FP64 refactorisation of a tensor-core factor that
+// fails to refine: it returns IPM_WARN_REFINE_NOT_CONVERGED instead).  Its
+// refinement decisions are taken on the host (one synchronisation of the
+// stream per step).
 namespace {
 
 // Capacity of the shared work array, in doubles (16 MiB).  A solve needs
-// 7 N + sum_s f_s doubles (N unknowns, f_s the front sizes).
+// 7 N + sum_s (f_s - k_s) doubles (N unknowns; f_s - k_s the contribution
+// rows of supernode s, one update vector entry each).
 constexpr int64_t kNoAllocDoubles = int64_t(1) << 21;
 static __device__ __align__(256) double g_noalloc_work[kNoAllocDoubles];
 
@@ -2181,6 +2194,13 @@ int ipm_solve_noalloc(ipm_ctx *c, const double *r7, const double *r1, double *dx
                          (long long)need, (long long)kNoAllocDoubles);
         return IPM_ERR_SCRATCH_TOO_SMALL;
     }
+    // the per-level sweeps keep one front's gathered vector in shared memory
+    if ((int64_t)P.max_f * (int64_t)sizeof(double) > kSweepSmemLimit) {
+        if (c->opt.verbose)
+            std::fprintf(stderr, "[ipm] ipm_solve_noalloc: a front of %d rows exceeds the sweeps' shared memory\n",
+                         (int)P.max_f);
+        return IPM_ERR_SCRATCH_TOO_SMALL;
+    }
     if (!c->factorised) return IPM_ERR_NOT_FACTORISED;
     if (P.form != 1) return IPM_ERR_INVALID_ARG;  // augmented system only
     if ((P.n > 0 && (!r7 || !dx)) || (P.m > 0 && (!r1 || !dy))) return IPM_ERR_INVALID_ARG;
@@ -2207,6 +2227,7 @@ int ipm_solve_noalloc(ipm_ctx *c, const double *r7, const double *r1, double *dx
     double wbest = h.omega;
     cudaMemcpyAsync(vbest, vx, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
     int steps = 0;
+    c->omega_hist[0] = h.omega;
     const double target = c->opt.omega_target;
     while (wbest > target && steps < c->opt.refine_max && !(h.status & kStatNonFinite)) {
         cudaMemcpyAsync(vc, vr, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -2215,6 +2236,7 @@ int ipm_solve_noalloc(ipm_ctx *c, const double *r7, const double *r1, double *dx
         launch_residual_omega(c->dp, V, vf, vx, vr, vad, vae, c->ctl, st);
         if ((rc = read_ctl(c, st, &h))) return rc;
         steps++;
+        if (steps < 16) c->omega_hist[steps] = h.omega;
         const bool halved = h.omega <= 0.5 * wbest;
         if (h.omega < wbest) {
             wbest = h.omega;
@@ -2223,8 +2245,19 @@ int ipm_solve_noalloc(ipm_ctx *c, const double *r7, const double *r1, double *dx
         if (!halved) break;
     }
     launch_permute_out(c->dp, vbest, dx, dy, st);
-    if (wbest > target) c->status_acc |= kStatRefineFail;
-    return to_err(cudaGetLastError());
+    // what ipm_get_info reports about the last solve
+    c->refine_steps = steps;
+    c->gmres_iters = 0;
+    c->omega = wbest;
+    c->omega_sys = wbest;
+    c->graph_solved = false;
+    if ((rc = to_err(cudaGetLastError()))) return rc;
+    if (h.status & kStatNonFinite) return IPM_ERR_NONFINITE;
+    if (wbest > target) {
+        c->status_acc |= kStatRefineFail;
+        return IPM_WARN_REFINE_NOT_CONVERGED;
+    }
+    return IPM_OK;
 }
 
 }  // extern "C"

@@ -16,6 +16,25 @@ enum : int32_t {
     kStatRefineFail = 16,  // refinement did not reach the target
 };
 
+// Dynamic shared memory the per-level solve sweeps may use (one front's
+// gathered vector, f doubles): fronts above 25,600 rows do not fit.
+constexpr int64_t kSweepSmemLimit = 200 * 1024;
+
+// Kernel attributes such as the dynamic shared-memory limit belong to one
+// device: true the first time it is asked for the current device, so the
+// attribute is set once per device and kernel (mask: one bit per device).
+inline bool first_on_device(uint64_t &mask) {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) {
+        cudaGetLastError();
+        return true;
+    }
+    const uint64_t bit = (uint64_t)1 << d;
+    if (mask & bit) return false;
+    mask |= bit;
+    return true;
+}
+
 // Small control block in device memory.
 struct DevCtl {
     int32_t status;
@@ -204,6 +223,7 @@ void launch_large_update(const DevPlan &P, double *fronts, const double *D, cons
                          int32_t p0, int32_t w, cudaStream_t st);
 void launch_large_update_tc(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
                             int32_t p0, int32_t w, DevCtl *ctl, cudaStream_t st);
+void launch_test_recip(const double *x, double *rcp, double *quo, int64_t n, cudaStream_t st);
 void launch_factor_stats(const double *D, const double *dyn, int N, double large_reg, DevCtl *ctl, cudaStream_t st);
 // solves and refinement (kernels_solve.cu)
 void launch_forward(const DevPlan &P, const double *fronts, const double *D, double *x, double *upd,

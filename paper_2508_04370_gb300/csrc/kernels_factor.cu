@@ -914,13 +914,12 @@ void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, dou
     if (count <= 0) return;
     const int ldmax = (maxf + 3) & ~3;
     const size_t smem = (size_t)ldmax * maxf * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
+    static uint64_t attr = 0;
+    if (first_on_device(attr)) {
         cudaFuncSetAttribute(k_small_fronts<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_small_fronts<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_small_fronts<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_small_fronts<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
     }
     // default: one warp per front up to f = 32, two up to 64, four beyond;
     // the autotuner may choose any of 32, 64, 128, 256 (same arithmetic per
@@ -976,6 +975,24 @@ void launch_large_level(const DevPlan &P, const DevVals &V, double *fronts, doub
 }
 
 const void *large_level_kernel() { return reinterpret_cast<const void *>(k_large_level); }
+
+// The pivot reciprocal of the factorisation beside CUDA's correctly rounded
+// division, element by element (a test hook: the factorisation scales every
+// column of L by this reciprocal, Sec. 4.4-4.5).
+__global__ void k_test_recip(const double *__restrict__ x, double *__restrict__ rcp, double *__restrict__ quo,
+                             int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        rcp[i] = recip_pivot(v);
+        quo[i] = 1.0 / v;
+    }
+}
+
+void launch_test_recip(const double *x, double *rcp, double *quo, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    const int64_t blocks = (n + 255) / 256;
+    k_test_recip<<<(int)(blocks < 1216 ? blocks : 1216), 256, 0, st>>>(x, rcp, quo, n);
+}
 
 void launch_norm1(const DevPlan &P, const DevVals &V, DevCtl *ctl, double eps_piv, cudaStream_t st) {
     const int grid = (P.N + 255) / 256 < 608 ? (P.N + 255) / 256 : 608;

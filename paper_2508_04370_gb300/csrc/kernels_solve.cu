@@ -841,11 +841,10 @@ __global__ void k_clear_norms(DevCtl *ctl, const int32_t *skip) {
 void launch_forward(const DevPlan &P, const double *fronts, const double *D, double *x, double *upd,
                     const int32_t *list, int32_t count, int32_t maxf, cudaStream_t st) {
     if (count <= 0) return;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
+    static uint64_t attr = 0;
+    if (first_on_device(attr)) {
+        cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemLimit);
+        cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemLimit);
     }
     k_forward<<<count, kSolveThreads, (size_t)maxf * sizeof(double), st>>>(P, fronts, D, x, upd, list);
 }
@@ -867,11 +866,10 @@ void launch_diag_inverse(const SolveSched &S, const double *fronts, double *Linv
 
 void launch_forward_persistent(const SolveSched &S, const double *fronts, const double *Dinv, double *x, double *upd,
                                int32_t maxf, int32_t grid, DevCtl *ctl, cudaStream_t st, const int32_t *skip) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_forward_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_backward_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
+    static uint64_t attr = 0;
+    if (first_on_device(attr)) {
+        cudaFuncSetAttribute(k_forward_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemLimit);
+        cudaFuncSetAttribute(k_backward_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemLimit);
     }
     // sync[0] = ticket; then per supernode: finished children, finished items, finished blocks
     cudaMemsetAsync(S.sync, 0, (size_t)(3 * S.nsuper + 1) * sizeof(int32_t), st);

@@ -104,10 +104,9 @@ __global__ void __launch_bounds__(128) k_large_update_tc(DevPlan P, double *__re
 void launch_large_update_tc(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
                             int32_t p0, int32_t w, DevCtl *ctl, cudaStream_t st) {
     if (count <= 0) return;
-    static bool attr = false;
-    if (!attr) {
+    static uint64_t attr = 0;
+    if (first_on_device(attr)) {
         cudaFuncSetAttribute(k_large_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-        attr = true;
     }
     k_large_update_tc<<<count, 128, kTcSmem, st>>>(P, fronts, D, items, p0, w, ctl);
 }

@@ -147,16 +147,39 @@ def small_block_angular():
 
 
 def test_block_angular_forms_against_oracle(pkg):
+    """The block-angular family.  At its full Theta range 10^U[-8,8] the
+    augmented system matches the oracle factor by factor and reaches
+    omega <= 1e-12 on K (GMRES refinement takes over where classical
+    refinement stalls; the oracle, which refines classically, stalls near
+    0.1).  The solution is not compared there: cond(K) eps is far above 1
+    (checked), so no solution agreement follows from any backward error.  The
+    normal equations are compared with the oracle's normal equations at a
+    Theta range of 10^U[-4,4], where A Theta~ A^T still carries the small
+    Theta~ contributions (at the full range both sides lose them: omega on K
+    stays near 5e-8 with GMRES, near 1 without).  AUTO picks the normal
+    equations for this reduced instance (the cost model; the full-size
+    instance keeps the augmented system) and solves at the narrower range."""
     lp = small_block_angular()
-    theta = synth.theta_loguniform(lp.n, 4, -4.0, 4.0)
+    theta = synth.theta_loguniform(lp.n, 4)
     r7, r1 = synth.rhs_normal(lp.n, 4), synth.rhs_normal(lp.m, 5)
     # augmented system, against the oracle factor by factor
     r = run_pair(pkg, lp, theta, r7, r1)
-    check_pair(r, lp)
+    check_pair(r, lp, x_tol=None)
+    K = r["o"].matrix()
+    import scipy.sparse as sp
+
+    Kd = sp.csc_matrix((K[2], K[1], K[0]), shape=(lp.n + lp.m,) * 2).toarray()
+    Kd = np.tril(Kd) + np.tril(Kd, -1).T
+    Kd[np.arange(lp.n), np.arange(lp.n)] -= RHO
+    Kd[lp.n + np.arange(lp.m), lp.n + np.arange(lp.m)] += DELTA
+    assert np.linalg.cond(Kd) * 2.2e-16 > 1.0
+    print(f"block-angular AS, Theta 1e-8..1e8: omega {r['w_gpu']:.2e}, GMRES {r['info']['gmres_iters']}, "
+          f"oracle omega {r['oinfo']['omega_hist'][-1]:.2e}")
     r["s"].close()
+    theta_ne = synth.theta_loguniform(lp.n, 4, -4.0, 4.0)
     # normal equations, against the oracle's normal equations
     s = pkg.Solver.from_lp(lp, form=pkg.IPM_FORM_NORMAL)
-    s.factorise(theta, RHO, DELTA)
+    s.factorise(theta_ne, RHO, DELTA)
     dx, dy = s.solve(r7, r1)
     info = s.info()
     assert info["form"] == pkg.IPM_FORM_NORMAL and info["npos"] == lp.m
@@ -164,10 +187,10 @@ def test_block_angular_forms_against_oracle(pkg):
     o = Oracle.from_lp(lp, form=FORM_NE)
     sym = s.symbolic()
     o.analyse(sym["perm"], amalg_zero_frac=sym["amalg_zero_frac"])
-    o.factorise(theta, RHO, DELTA, eps_piv=EPS_PIV)
+    o.factorise(theta_ne, RHO, DELTA, eps_piv=EPS_PIV)
     ox, oy, _ = o.solve(r7, r1, omega_target=1e-12, max_steps=10)
     ref = np.concatenate([ox, oy])
-    w = o.omega_K(theta, RHO, DELTA, r7, r1, x[: lp.n], x[lp.n:])
+    w = o.omega_K(theta_ne, RHO, DELTA, r7, r1, x[: lp.n], x[lp.n:])
     assert w <= 1e-10, f"omega {w:.3e}"
     assert np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max()
     s.close()
@@ -175,9 +198,9 @@ def test_block_angular_forms_against_oracle(pkg):
     s = pkg.Solver.from_lp(lp, form=pkg.IPM_FORM_AUTO)
     info = s.info()
     assert info["est_cost_as"] > 0
-    s.factorise(theta, RHO, DELTA)
+    s.factorise(theta_ne, RHO, DELTA)
     dx, dy = s.solve(r7, r1)
-    w = o.omega_K(theta, RHO, DELTA, r7, r1, dx.cpu().numpy(), dy.cpu().numpy())
+    w = Oracle.from_lp(lp).omega_K(theta_ne, RHO, DELTA, r7, r1, dx.cpu().numpy(), dy.cpu().numpy())
     assert w <= 1e-10
     print(f"block-angular chooser: form {s.info()['form']} cost AS {info['est_cost_as']:.3e} "
           f"NE {info['est_cost_ne']:.3e}")

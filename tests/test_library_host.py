@@ -174,28 +174,53 @@ def test_normal_equations_symbolic_bit_exact(lib):
         lib.ipm_destroy(ctx)
 
 
+def _chooser_against_oracle(lib, lp, ordering):
+    """The library's AUTO choice and both modelled costs against the oracle's
+    restatement of the chooser (oracle.choose_form), given the orders the
+    library computes for each form (ordering parity is not pinned)."""
+    from oracle import FORM_NE, choose_form
+
+    syms = {}
+    for form in (lib.IPM_FORM_AUGMENTED, lib.IPM_FORM_NORMAL):
+        ctx = lib.ipm_create()
+        rc = lib.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, form, ordering)
+        syms[form] = lib.ipm_get_symbolic(ctx) if rc == 0 else None
+        lib.ipm_destroy(ctx)
+    sa, sn = syms[lib.IPM_FORM_AUGMENTED], syms[lib.IPM_FORM_NORMAL]
+    pn = sn["perm"] if sn is not None else np.arange(lp.m, dtype=np.int32)
+    azn = sn["amalg_zero_frac"] if sn is not None else 0.1
+    oform, ocas, ocne, onne = choose_form(lp, sa["perm"], pn, sa["amalg_zero_frac"], azn)
+    ctx = lib.ipm_create()
+    assert lib.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, lib.IPM_FORM_AUTO, ordering) == 0
+    rc, info = lib.ipm_get_info(ctx)
+    lib.ipm_destroy(ctx)
+    assert info.est_cost_as == pytest.approx(ocas, rel=1e-12)
+    if ocne < 0:
+        assert info.est_cost_ne == -1.0 and info.nnz_ne_seen > info.nnz_L
+    else:
+        assert info.est_cost_ne == pytest.approx(ocne, rel=1e-12)
+        assert info.nnz_ne_seen == onne
+    assert info.form == (lib.IPM_FORM_NORMAL if oform == FORM_NE else lib.IPM_FORM_AUGMENTED)
+    return info
+
+
 def test_form_chooser(lib):
-    """Sec. 4.2: a dense column makes A A^T dense, so forming the normal
-    equations is abandoned once it holds more entries than L of the
-    augmented system; a sparse LP with few rows per column keeps the cheaper
-    form by the cost model."""
+    """Sec. 4.2: the library's choice between the augmented system and the
+    normal equations equals the oracle's restatement of it: a dense column
+    makes A A^T dense, so forming the normal equations is abandoned once they
+    hold more entries than L of the augmented system; sparse LPs compare the
+    two modelled costs; the reduced block-angular LP with dense linking rows
+    (the family where the paper weighs the two forms)."""
     lp = synth.random_lp(400, 1000, 3, seed=5)
-    # append one fully dense column
     cp = np.concatenate([lp.colptr, [lp.colptr[-1] + lp.m]]).astype(np.int64)
     ri = np.concatenate([lp.rowidx, np.arange(lp.m, dtype=np.int32)])
-    ctx = lib.ipm_create()
-    assert lib.ipm_analyse(ctx, lp.m, lp.n + 1, cp, ri, lib.IPM_FORM_AUTO, lib.IPM_ORD_AMD) == 0
-    rc, info = lib.ipm_get_info(ctx)
-    assert info.form == lib.IPM_FORM_AUGMENTED
-    assert info.nnz_ne_seen > info.nnz_L and info.est_cost_ne == -1.0
-    lib.ipm_destroy(ctx)
-    ctx = lib.ipm_create()
-    assert lib.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, lib.IPM_FORM_AUTO, lib.IPM_ORD_AMD) == 0
-    rc, info = lib.ipm_get_info(ctx)
-    assert info.est_cost_ne > 0 and info.est_cost_as > 0
-    chosen = lib.IPM_FORM_NORMAL if info.est_cost_ne < info.est_cost_as else lib.IPM_FORM_AUGMENTED
-    assert info.form == chosen
-    lib.ipm_destroy(ctx)
+    dense = synth.lp.LP(lp.m, lp.n + 1, cp, ri, np.ones(len(ri)))
+    info = _chooser_against_oracle(lib, dense, lib.IPM_ORD_AMD)
+    assert info.form == lib.IPM_FORM_AUGMENTED and info.est_cost_ne == -1.0
+    _chooser_against_oracle(lib, lp, lib.IPM_ORD_AMD)
+    _chooser_against_oracle(lib, synth.random_lp(300, 800, 2, seed=6), lib.IPM_ORD_ND)
+    _chooser_against_oracle(lib, synth.block_angular(blocks=12, bm=30, bn=80, density=0.05, linking=8, seed=4),
+                            lib.IPM_ORD_AMD)
 
 
 def test_analysis_checkpoint_roundtrip(tmp_path):

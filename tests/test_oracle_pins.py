@@ -640,3 +640,88 @@ def test_bk_front_partial_factorisation():
         if 0 < k < f:
             S = Ap[k:, k:] - Ap[k:, :k] @ np.linalg.solve(Ap[:k, :k], Ap[:k, k:])
             assert np.abs(S - r["S"]).max() <= 1e-10 * max(1.0, np.abs(S).max()) * np.linalg.cond(Ap[:k, :k])
+
+
+# ------------------------------------------------- ||K||_1 (lift floor)
+
+def _norm1_cases():
+    rng = np.random.default_rng(17)
+    A = rng.standard_normal((7, 12)) * (rng.random((7, 12)) < 0.4)
+    A[np.arange(7), rng.integers(12, size=7)] = rng.standard_normal(7)
+    A[rng.integers(7, size=12), np.arange(12)] = rng.standard_normal(12)
+    # moderate Theta and more entries per row than per column, so that the
+    # largest column sum is a dual column made of mirrored entries
+    theta = 10.0 ** rng.uniform(0, 1, 12)
+    return A, theta
+
+
+def test_norm1_reg_against_dense_max_column_sum():
+    """The lift floor eps_piv ||K||_1 (Sec. 4.5) uses the maximum absolute
+    column sum of the regularised matrix, K with rho and delta for the
+    augmented system and A Theta~ A^T + delta I for the normal equations.
+    Pinned against numpy's matrix 1-norm of the dense matrices; a planted
+    mistake (a column sum of the stored lower part only, without the mirrored
+    entries, or without the static terms) differs from the pin on these
+    cases."""
+    A, theta = _norm1_cases()
+    m, n = A.shape
+    rho, delta = 0.3, 0.7  # large enough for the static terms to move the norm
+    K = K_dense(A, theta, rho, delta)
+    o = Oracle(*lp_from_dense(A), form=FORM_AS)
+    o.analyse(None)
+    o.factorise(theta, rho, delta)
+    got = o.stats()["normM1"]
+    want = np.linalg.norm(K, 1)
+    assert got == pytest.approx(want, rel=1e-14)
+    # the pin is sensitive to the plausible mistakes
+    assert abs(np.abs(np.tril(K)).sum(0).max() - want) > 1e-6 * want
+    K0 = K_dense(A, theta, 0.0, 0.0)
+    assert abs(np.linalg.norm(K0, 1) - want) > 1e-6 * want
+    # normal equations
+    tt = 1.0 / (1.0 / theta + rho)
+    M = A @ np.diag(tt) @ A.T + delta * np.eye(m)
+    on = Oracle(*lp_from_dense(A), form=FORM_NE)
+    on.analyse(None)
+    on.factorise(theta, rho, delta)
+    assert on.stats()["normM1"] == pytest.approx(np.linalg.norm(M, 1), rel=1e-13)
+    assert abs(np.abs(np.tril(M)).sum(0).max() - np.linalg.norm(M, 1)) > 1e-6 * np.linalg.norm(M, 1)
+
+
+# ------------------------------------------------------ AS / NE chooser
+
+def test_chooser_closed_form_identity():
+    """A = I (m = n): K in the interleaved order (x_j, y_j) gives n separate
+    2 x 2 supernodes (f = k = 2: 3 entries of L and 4 flops each), A A^T is
+    diagonal (1 entry, 0 flops per supernode, one contributor pair per
+    column), so cost_AS = 4n/P + 3*2*3n*8/B and cost_NE = 2n/P + 3*2*n*8/B and
+    the normal equations win."""
+    from oracle import choose_form
+
+    n = 9
+    lp = synth.lp.LP(n, n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.ones(n))
+    perm = np.ravel(np.column_stack([np.arange(n), n + np.arange(n)])).astype(np.int32)
+    P, B = 1.0e12, 6.7e12
+    form, cas, cne, nne = choose_form(lp, perm, np.arange(n, dtype=np.int32), 0.0, 0.0, P, B)
+    assert nne == n
+    assert cas == pytest.approx(4 * n / P + 3 * 2 * 3 * n * 8 / B, rel=1e-14)
+    assert cne == pytest.approx(2 * n / P + 3 * 2 * n * 8 / B, rel=1e-14)
+    assert form == FORM_NE
+
+
+def test_chooser_abandons_dense_normal_equations():
+    """One dense column makes A A^T dense: its lower part (m(m+1)/2 entries)
+    exceeds L of the augmented system in an order that eliminates the dense
+    column last, so the normal equations are abandoned (cost -1) and the
+    augmented system is kept."""
+    from oracle import choose_form
+
+    m, n = 30, 40
+    rows = [np.array([j % m]) for j in range(n)] + [np.arange(m)]
+    cp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    ri = np.concatenate(rows).astype(np.int32)
+    lp = synth.lp.LP(m, n + 1, cp, ri, np.ones(len(ri)))
+    # the sparse columns first, then the rows, the dense column last: no fill
+    perm = np.concatenate([np.arange(n), n + 1 + np.arange(m), [n]]).astype(np.int32)
+    form, cas, cne, nne = choose_form(lp, perm, np.arange(m, dtype=np.int32))
+    assert nne == m * (m + 1) // 2
+    assert form == FORM_AS and cne == -1.0 and cas > 0

@@ -1,9 +1,13 @@
 """ipm_solve_noalloc: the allocation-free solve for callers that cannot
-allocate device memory at solve time (for example while a stream is being
-captured into a CUDA graph).  Its output must match ipm_solve's within the
-parity tolerance of the solution (|x - x_ref|_inf <= 1e-8 |x_ref|_inf), on two
-calls in a row, and a problem that does not fit its fixed work space must be
-rejected before anything runs.  This file is collected last on purpose."""
+allocate device memory at solve time (a host library or callback under a
+fixed device-memory budget, or one that must not change the device's
+allocation state).  Its output must match ipm_solve's within the parity
+tolerance of the solution (|x - x_ref|_inf <= 1e-8 |x_ref|_inf), on two calls
+in a row, and ipm_get_info must then report its own backward error; a
+tensor-core factor whose refinement stalls is returned with a warning (no
+FP64 refactorisation here); a problem that does not fit its fixed work space
+must be rejected before anything runs.  This file is collected last on
+purpose."""
 import numpy as np
 import pytest
 
@@ -47,6 +51,31 @@ def test_noalloc_solve_matches_solve_twice(pkg):
         x = np.concatenate([ox.cpu().numpy(), oy.cpu().numpy()])
         assert np.all(np.isfinite(x))
         assert np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max()
+        info = s.info()
+        assert info["omega"] <= 1e-12 and info["gmres_iters"] == 0
+        assert info["omega_hist"][info["refine_steps"]] == pytest.approx(info["omega"], rel=0, abs=info["omega"])
+    s.close()
+
+
+def test_noalloc_reports_a_stalled_tensor_core_factor(pkg):
+    """FP32-accurate tensor-core updates cannot be refined on this staircase
+    (pivots of size delta make the factor grow by ~1/delta): ipm_solve would
+    factorise again in FP64; the allocation-free solve does not, and says so
+    in its return code (or reports the non-finite pivots)."""
+    import torch
+
+    lp = synth.staircase(periods=3, pm=200, pn=500, density=0.01, links=50, seed=3)
+    theta = synth.theta_schedule(lp.n, 40, 3)[20]
+    s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND, precision=pkg.IPM_PREC_MIXED, mixed_min_front=64,
+                           omega_target=1e-10)
+    s.factorise(theta, 1e-8, 1e-8)
+    ox = torch.empty(lp.n, dtype=torch.float64, device=s.dev)
+    oy = torch.empty(lp.m, dtype=torch.float64, device=s.dev)
+    rc = pkg.ipm_solve_noalloc(s.ctx, s._dev(synth.rhs_normal(lp.n, 1)), s._dev(synth.rhs_normal(lp.m, 2)), ox, oy)
+    assert rc in (pkg.IPM_WARN_REFINE_NOT_CONVERGED, pkg.IPM_ERR_NONFINITE), rc
+    info = s.info()
+    assert info["mixed_active"] == 1 and info["precision_fallbacks"] == 0
+    assert not (info["omega"] <= 1e-10)
     s.close()
 
 
