@@ -73,13 +73,17 @@ extern "C" {
 
 /* precision of the Schur-complement updates (Sec. 4.4 dgemm updates) */
 #define IPM_PREC_FP64 0    /* everything in FP64 */
-#define IPM_PREC_MIXED 1   /* FP32-accurate tensor-core updates on large fronts,
-                              FP64 pivots, regularisation, residual, refinement.
-                              If refinement cannot reach omega_target from such a
-                              factorisation (very wide Theta spreads), ipm_solve
-                              factorises again in FP64, solves again, and later
-                              factorisations stay in FP64 (an IPM's Theta spread
-                              only widens); ipm_info counts these fallbacks. */
+#define IPM_PREC_MIXED 1   /* FP32-accurate tensor-core updates (3xTF32, FP32 accumulation) on large
+                              fronts; FP64 pivots, regularisation, residual, refinement */
+#define IPM_PREC_SLICED 2  /* FP64-accurate tensor-core updates on large fronts: each row of the panel
+                              operands is scaled by a power of two and split into eight 7-bit digits,
+                              the digit products run as exact bf16 MMAs with FP32 accumulation and are
+                              recombined in integers (about 2^-54 of the largest operand entry of a
+                              row, where FP64 GEMM gives 2^-53 of each product); FP64 elsewhere.
+                              For both tensor-core modes: if refinement cannot reach omega_target
+                              from such a factorisation, ipm_solve factorises again in FP64, solves
+                              again, and later factorisations stay in FP64 (an IPM's Theta spread only
+                              widens); ipm_info counts these fallbacks. */
 
 typedef struct ipm_ctx ipm_ctx;
 
@@ -93,8 +97,8 @@ typedef struct ipm_options {
     double eps_piv;           /* dynamic-regularisation floor eps_piv * ||K||_1 (Sec. 4.5: "of the order of
                                  magnitude of machine precision"); 2.220446049250313e-16 */
     double large_reg;         /* a lift larger than this raises IPM_WARN_LARGE_REG; 1e-4 */
-    int32_t precision;        /* IPM_PREC_FP64 or IPM_PREC_MIXED; FP64 */
-    int32_t mixed_min_front;  /* mixed path: fronts with f >= this use tensor-core updates; 256 */
+    int32_t precision;        /* IPM_PREC_FP64, IPM_PREC_MIXED or IPM_PREC_SLICED; FP64 */
+    int32_t mixed_min_front;  /* tensor-core modes: fronts with f >= this use tensor-core updates; 256 */
     double omega_target;      /* refinement stops at this backward error; 1e-12 */
     int32_t refine_max;       /* at most this many refinement steps per solve; 10 */
     int32_t gmres_restarts;   /* when classical refinement of an FP64 factor stalls above omega_target, up to
@@ -373,13 +377,14 @@ int ipm_test_recip_pivot(const double *x_dev, double *rcp_dev, double *quo_dev, 
 #define IPM_K_LARGE_PANEL 2    /* pivot block + triangular solve of a 32-column panel; the persistent
                                   level kernel (all large-front work of a level) is counted here */
 #define IPM_K_LARGE_UPDATE 3   /* trailing (Schur-complement) update, FP64 */
-#define IPM_K_LARGE_UPDATE_TC 4 /* trailing update on tensor cores (mixed precision) */
+#define IPM_K_LARGE_UPDATE_TC 4 /* trailing update on tensor cores (IPM_PREC_MIXED or IPM_PREC_SLICED) */
 #define IPM_K_FORWARD 5        /* forward + diagonal solve (one persistent sweep) */
 #define IPM_K_BACKWARD 6       /* backward solve (one persistent sweep) */
 #define IPM_K_RESIDUAL 7       /* residual, |K||x|, |K|e and backward error */
 #define IPM_K_OTHER 8          /* norms, statistics, permutations, vector updates, diagonal-block
                                   inverses for the solves */
-#define IPM_K_COUNT 9
+#define IPM_K_SLICE 9          /* IPM_PREC_SLICED: splitting the panel operands into digit slices */
+#define IPM_K_COUNT 10
 
 typedef struct ipm_kernel_stat {
     int64_t launches;  /* launches recorded since the last reset */

@@ -41,6 +41,7 @@ IPM_ORD_USER = 2
 IPM_ORD_NATURAL = 3
 IPM_PREC_FP64 = 0
 IPM_PREC_MIXED = 1
+IPM_PREC_SLICED = 2
 
 
 class ipm_options(ct.Structure):
@@ -92,7 +93,7 @@ class ipm_kernel_stat(ct.Structure):
 
 
 KERNEL_CLASSES = ["small_fronts", "large_assemble", "large_panel", "large_update", "large_update_tc", "forward",
-                  "backward", "residual", "other"]
+                  "backward", "residual", "other", "slice"]
 
 _lib = None
 

@@ -39,7 +39,12 @@ struct StepWork {
     int64_t alt_off;  // FP64 tiles of the same fronts, used after a precision fallback
     int32_t alt_cnt;
     int32_t alt_cnt1;  // lookahead tiles among them
-    Work panel_w, trsm_w, tile_w, tile_w1, tc_w, alt_w, alt_w1;
+    int64_t sl_off;   // sliced path: slice blocks of the panel operands (one per 128 trailing rows)
+    int32_t sl_cnt;
+    int64_t st_off;   // sliced path: 128 x 32 output tiles; the first st_cnt1 cover the next panel's
+    int32_t st_cnt;   // columns (critical path), the rest run beside the next panel
+    int32_t st_cnt1;
+    Work panel_w, trsm_w, tile_w, tile_w1, tc_w, alt_w, alt_w1, sl_w, st_w1, st_w2;
 };
 struct SmallClass {
     int64_t off;
@@ -104,6 +109,11 @@ struct ipm_ctx {
     int32_t *trsm_slots = nullptr;
     double *panel_ws = nullptr;
     TileItem *tile_items = nullptr, *tc_items = nullptr, *alt_items = nullptr;
+    SliceItem *slice_items = nullptr;  // sliced tensor-core path: slice blocks and output tiles per step
+    SlicedTile *sliced_tiles = nullptr;
+    uint8_t *slice_ws = nullptr;       // digit images of a step: two halves, used by alternate steps
+    int32_t *slice_exp = nullptr;      // their row scales (two halves)
+    int64_t slice_half_blocks = 0;     // slice blocks per half
     FactorItem *lvl_items = nullptr;  // persistent level kernel: items of all levels
     InvItem *inv_items = nullptr;     // diagonal blocks inverted after each factorisation
     InvItem *pair_items = nullptr;    // blocks of multi-block supernodes (neighbour products)
@@ -683,6 +693,10 @@ int setup_device(ipm_ctx *c) {
     for (int32_t s = 0; s < P.nsuper; s++)
         if (P.sn_large[s]) slot_of[s] = nslots++;
     std::vector<TileItem> tile_items, tc_items, alt_items;
+    std::vector<SliceItem> slice_items;
+    std::vector<SlicedTile> sliced_tiles;
+    int64_t max_slice_blocks = 0;
+    const bool sliced = c->opt.precision == IPM_PREC_SLICED;
     std::vector<FactorItem> lvl_items;
     std::vector<int32_t> cbase(P.nsuper, -1);
     int32_t max_ncnt = 0;
@@ -781,6 +795,10 @@ int setup_device(ipm_ctx *c) {
             S.tile_off = (int64_t)tile_items.size();
             S.tc_off = (int64_t)tc_items.size();
             S.alt_off = (int64_t)alt_items.size();
+            S.sl_off = (int64_t)slice_items.size();
+            S.st_off = (int64_t)sliced_tiles.size();
+            int32_t nblk = 0;  // slice blocks of this step
+            std::vector<SlicedTile> t1, t2;  // sliced tiles: next panel's columns / the rest
             std::vector<TileItem> u1, u2, a1, a2;  // lookahead / remaining tiles of this step
             Work w1, w2, wa1, wa2;
             // lower entries of a kUpdTile tile times 2 w flops (and its bytes)
@@ -801,13 +819,34 @@ int setup_device(ipm_ctx *c) {
                     trsm_items.push_back({s, r, std::min(r + kTrsmRowsHost, f)});
                     trsm_slots.push_back(slot_of[s]);
                 }
-                const bool tc = c->opt.precision == IPM_PREC_MIXED && f >= c->opt.mixed_min_front;
+                const bool tc = c->opt.precision != IPM_PREC_FP64 && f >= c->opt.mixed_min_front;
                 const double w = p1 - S.p0, rest = f - p1;
                 // tiles of the next panel's columns (when the front has one) go first
                 const bool next_panel = p1 < k;
-                if (tc)
+                if (tc && sliced && p1 < f) {
+                    // slice blocks of rows p1.., then every 128 x 32 tile of the
+                    // lower trailing part, row blocks aligned with the slice blocks
+                    const int32_t base = nblk;
+                    for (int32_t r0 = p1; r0 < f; r0 += kSliceRows) slice_items.push_back({s, r0, nblk++});
+                    for (int32_t j0 = p1; j0 < f; j0 += kSliceCols)
+                        for (int32_t b = (j0 - p1) / kSliceRows; p1 + b * kSliceRows < f; b++) {
+                            const int32_t i0 = p1 + b * kSliceRows;
+                            const bool la = next_panel && j0 == p1;
+                            (la ? t1 : t2).push_back({s, i0, j0, base + b, base + (j0 - p1) / kSliceRows,
+                                                      (j0 - p1) % kSliceRows});
+                            // lower entries of the tile times 2 w flops; its C read and write
+                            double e = 0.0;
+                            for (int32_t j = j0; j < std::min(j0 + kSliceCols, f); j++)
+                                e += std::max(0, std::min(i0 + kSliceRows, f) - std::max(i0, j));
+                            Work &tw = la ? S.st_w1 : S.st_w2;
+                            tw.flops += 2.0 * w * e;
+                            tw.bytes += 16.0 * e + 2.0 * kSlices * 2.0 * w * (kSliceRows + kSliceCols);
+                        }
+                    S.sl_w.bytes += 8.0 * 2.0 * rest * w + 2.0 * kSlices * 2.0 * rest * w;
+                } else if (tc) {
                     for (int32_t j0 = p1; j0 < f; j0 += kTcTile)
                         for (int32_t i0 = j0; i0 < f; i0 += kTcTile) tc_items.push_back({s, i0, j0});
+                }
                 for (int32_t j0 = p1; j0 < f; j0 += kUpdTile)
                     for (int32_t i0 = j0; i0 < f; i0 += kUpdTile) {
                         // lookahead tiles become strips of kStripCols columns
@@ -847,8 +886,14 @@ int setup_device(ipm_ctx *c) {
             S.tile_cnt = (int32_t)(tile_items.size() - S.tile_off);
             S.tc_cnt = (int32_t)(tc_items.size() - S.tc_off);
             S.alt_cnt = (int32_t)(alt_items.size() - S.alt_off);
+            sliced_tiles.insert(sliced_tiles.end(), t1.begin(), t1.end());
+            sliced_tiles.insert(sliced_tiles.end(), t2.begin(), t2.end());
+            S.sl_cnt = (int32_t)(slice_items.size() - S.sl_off);
+            S.st_cnt = (int32_t)(sliced_tiles.size() - S.st_off);
+            S.st_cnt1 = (int32_t)t1.size();
+            max_slice_blocks = std::max<int64_t>(max_slice_blocks, nblk);
             W.steps.push_back(S);
-            if (S.tc_cnt > 0) W.has_tc = true;
+            if (S.tc_cnt > 0 || S.st_cnt > 0) W.has_tc = true;
         }
         build_level_items(P, l, W, slot_of, lvl_items, cbase);
         {
@@ -888,9 +933,13 @@ int setup_device(ipm_ctx *c) {
         (rc = dalloc(c, &c->panel_ws, (size_t)std::max(nslots, 1) * kPanelWsHost)) ||
         (rc = dupload(c, &c->tile_items, tile_items)) || (rc = dupload(c, &c->tc_items, tc_items)) ||
         (rc = dupload(c, &c->alt_items, alt_items)) || (rc = dupload(c, &c->bwd_order, bwd_order)) ||
+        (rc = dupload(c, &c->slice_items, slice_items)) || (rc = dupload(c, &c->sliced_tiles, sliced_tiles)) ||
+        (rc = dalloc(c, &c->slice_ws, 2 * (size_t)max_slice_blocks * (size_t)kSliceBlockBytes)) ||
+        (rc = dalloc(c, &c->slice_exp, 2 * (size_t)std::max<int64_t>(max_slice_blocks, 1) * kSliceRows * 2)) ||
         (rc = dupload(c, &c->lvl_items, lvl_items)) || (rc = dalloc(c, &c->lvl_sync, (size_t)max_ncnt + 1)) ||
         (rc = dalloc(c, &c->solve_sync, (size_t)3 * ns + 1)))
         return rc;
+    c->slice_half_blocks = max_slice_blocks;
     int32_t *d_sparent;
     if ((rc = dupload(c, &d_sparent, P.sn_parent))) return rc;
     {
@@ -994,7 +1043,7 @@ int setup_device(ipm_ctx *c) {
     }
     cudaMemset(c->ctl, 0, sizeof(DevCtl));
     cudaMemset(c->fronts, 0, (size_t)std::max<int64_t>(P.front_doubles, 1) * sizeof(double));
-    c->mixed_active = c->opt.precision == IPM_PREC_MIXED;
+    c->mixed_active = c->opt.precision != IPM_PREC_FP64;
     c->fallbacks = 0;
     c->resid_w.flops = 6.0 * (double)kp[N];
     c->resid_w.bytes = 20.0 * (double)kp[N] + 48.0 * N;
@@ -1037,7 +1086,13 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
     // fronts of level l-1 and vice versa (events; a captured graph keeps them
     // as edges).
     if (!c->side) {
-        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
+        // the large fronts' per-step chain (diagonal block, triangular solve,
+        // lookahead update) is the factorisation's critical path: its stream
+        // gets the highest priority, so its CTAs go first when the trailing
+        // updates running beside it on side2 release SMs
+        int prio_lo = 0, prio_hi = 0;
+        cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+        if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
             cudaGetLastError();
             c->side = nullptr;
             return IPM_ERR_CUDA;
@@ -1102,7 +1157,9 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         if (W.asm_cnt == 0 && W.steps.empty()) continue;
         if (small_before) cudaStreamWaitEvent(sd, small_before, 0);
         const bool latency_bound = W.lvl_w.flops / 1.0e12 < c->tune_ratio * W.lvl_chain * 35e-6;
-        if (c->opt.level_kernel && W.lvl_cnt > 0 && latency_bound && !(W.has_tc && c->mixed_active)) {
+        // (a latency-bound level keeps the FP64 level kernel in the tensor-core
+        // modes too: its work is too small for the tensor cores to matter)
+        if (c->opt.level_kernel && W.lvl_cnt > 0 && latency_bound) {
             // FP64: all large-front work of the level in one dependency-driven launch
             {
                 Prof pr(c, IPM_K_LARGE_PANEL, W.lvl_w, sd);
@@ -1142,11 +1199,25 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                                   S.trsm_cnt, S.p0, c->opt.nb, c->panel_ws, sd);
                 nl++;
             }
-            const bool use_tc = S.tc_cnt > 0 && c->mixed_active;
+            const bool use_tc = (S.tc_cnt > 0 || S.st_cnt > 0) && c->mixed_active;
+            const bool use_sliced = use_tc && S.st_cnt > 0;
+            // sliced path: the digit images of this step (alternate halves of the
+            // work space: the rest of step s-1 may still read its half while
+            // step s slices; step s+1 slices only after step s's lookahead,
+            // which waits for the rest of step s-1)
+            uint8_t *ws = c->slice_ws + (sidx & 1) * c->slice_half_blocks * kSliceBlockBytes;
+            int32_t *wexp = c->slice_exp + (sidx & 1) * c->slice_half_blocks * kSliceRows * 2;
+            if (use_sliced) {
+                Prof pr(c, IPM_K_SLICE, S.sl_w, sd);
+                launch_slice_panel(c->dp, c->fronts, c->D, c->slice_items + S.sl_off, S.sl_cnt, S.p0, c->opt.nb, ws,
+                                   wexp, c->ctl, sd);
+                nl++;
+            }
             const int32_t rest_tiles = S.tile_cnt - S.tile_cnt1;
-            const int32_t rest_alt = (S.tc_cnt > 0 && !c->mixed_active) ? S.alt_cnt - S.alt_cnt1 : 0;
+            const int32_t rest_alt = ((S.tc_cnt > 0 || S.st_cnt > 0) && !c->mixed_active) ? S.alt_cnt - S.alt_cnt1 : 0;
+            const int32_t rest_sliced = use_sliced ? S.st_cnt - S.st_cnt1 : 0;
             cudaEvent_t this_rest = nullptr;
-            if (rest_tiles > 0 || rest_alt > 0) {
+            if (rest_tiles > 0 || rest_alt > 0 || rest_sliced > 0) {
                 cudaEvent_t ev_in = c->step_ev[2 * sidx], ev_out = c->step_ev[2 * sidx + 1];
                 cudaEventRecord(ev_in, sd);
                 cudaStreamWaitEvent(sd2, ev_in, 0);
@@ -1162,6 +1233,12 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                                         c->opt.nb, sd2);
                     nl++;
                 }
+                if (rest_sliced > 0) {
+                    Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.st_w2, sd2);
+                    launch_update_sliced(c->dp, c->fronts, c->sliced_tiles + S.st_off + S.st_cnt1, rest_sliced, ws,
+                                         wexp, c->ctl, sd2);
+                    nl++;
+                }
                 cudaEventRecord(ev_out, sd2);
                 this_rest = ev_out;
             }
@@ -1173,11 +1250,18 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                                           c->opt.nb, sd);
                 nl++;
             }
-            if (S.tc_cnt > 0 && !c->mixed_active && S.alt_cnt1 > 0) {
+            if ((S.tc_cnt > 0 || S.st_cnt > 0) && !c->mixed_active && S.alt_cnt1 > 0) {
                 Prof pr(c, IPM_K_LARGE_UPDATE, S.alt_w1, sd);
                 launch_large_update_strip(c->dp, c->fronts, c->D, c->alt_items + S.alt_off, S.alt_cnt1, S.p0,
                                           c->opt.nb, sd);
                 nl++;
+            } else if (use_sliced) {
+                if (S.st_cnt1 > 0) {
+                    Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.st_w1, sd);
+                    launch_update_sliced(c->dp, c->fronts, c->sliced_tiles + S.st_off, S.st_cnt1, ws, wexp, c->ctl,
+                                         sd);
+                    nl++;
+                }
             } else if (use_tc) {
                 Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.tc_w, sd);
                 launch_large_update_tc(c->dp, c->fronts, c->D, c->tc_items + S.tc_off, S.tc_cnt, S.p0, c->opt.nb,
@@ -1321,7 +1405,9 @@ int ipm_create(ipm_ctx **out, const ipm_options *opt) {
         c->opt.gmres_restarts < 0 || c->opt.gmres_restarts > 16 ||
         c->opt.spin_limit_log2 < -1 || c->opt.spin_limit_log2 > 40 || !(c->opt.eps_piv >= 0.0) ||
         c->opt.level_kernel < 0 || c->opt.level_kernel > 1 ||
-        (c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED) || c->opt.mixed_min_front < 1) {
+        (c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED &&
+         c->opt.precision != IPM_PREC_SLICED) ||
+        c->opt.mixed_min_front < 1) {
         delete c;
         return IPM_ERR_INVALID_ARG;
     }

@@ -180,6 +180,32 @@ struct TileItem {
                      // (kUpdTile x kStripCols for the lookahead strips)
 };
 
+// Sliced tensor-core update (FP64-accurate Schur complement on bf16 tensor
+// cores).  After a panel [p0, p1) of a large front, every trailing row r >= p1
+// of both panel operands, L(r, q) and L(r, q) d_q, is scaled by a power of two
+// per row and split into kSlices balanced 7-bit digits; one slice block holds
+// 128 rows.
+constexpr int kSlices = 8;                           // 8 x 7 = 56 bits per operand
+constexpr int kSliceRows = 128;                      // rows per slice block (the MMA's M)
+constexpr int kSliceCols = 32;                       // output columns per tile (the MMA's N)
+constexpr int64_t kSlicePairBytes = 128 * 128;       // two slices of 128 rows x 32 bf16, one swizzled image
+constexpr int64_t kSliceOperandBytes = 4 * kSlicePairBytes;
+constexpr int64_t kSliceBlockBytes = 2 * kSliceOperandBytes;  // operand A (L), then operand B (L d)
+
+struct SliceItem {
+    int32_t s;
+    int32_t r0;   // first local row of the block (rows r0 .. r0+127; rows >= f are zero)
+    int32_t blk;  // slice block in the step's work space
+};
+
+struct SlicedTile {
+    int32_t s;
+    int32_t i0, j0;     // output rows i0 .. i0+127, columns j0 .. j0+31 (lower part only)
+    int32_t blk_a;      // slice block of rows i0 ..
+    int32_t blk_b;      // slice block holding columns j0 .. j0+31 as rows,
+    int32_t roff_b;     // at row offset roff_b (a multiple of 32) inside it
+};
+
 // One item of the persistent level kernel (large fronts of one tree level):
 // it waits until counter wait0 >= need0 and counter wait1 >= need1 (-1: no
 // wait), runs, then adds `add` to counter sig.  Counters are per level,
@@ -223,6 +249,11 @@ void launch_large_update(const DevPlan &P, double *fronts, const double *D, cons
                          int32_t p0, int32_t w, cudaStream_t st);
 void launch_large_update_tc(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
                             int32_t p0, int32_t w, DevCtl *ctl, cudaStream_t st);
+void launch_slice_panel(const DevPlan &P, const double *fronts, const double *D, const SliceItem *items,
+                        int32_t count, int32_t p0, int32_t w, uint8_t *ws, int32_t *ws_exp, DevCtl *ctl,
+                        cudaStream_t st);
+void launch_update_sliced(const DevPlan &P, double *fronts, const SlicedTile *items, int32_t count,
+                          const uint8_t *ws, const int32_t *ws_exp, DevCtl *ctl, cudaStream_t st);
 void launch_test_recip(const double *x, double *rcp, double *quo, int64_t n, cudaStream_t st);
 void launch_factor_stats(const double *D, const double *dyn, int N, double large_reg, DevCtl *ctl, cudaStream_t st);
 // solves and refinement (kernels_solve.cu)

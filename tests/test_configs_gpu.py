@@ -97,7 +97,7 @@ def test_staircase_schedule_mixed_matches_fp64(pkg):
     lp = small_staircase()
     sched = synth.theta_schedule(lp.n, 40, 3)
     sm = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND, precision=pkg.IPM_PREC_MIXED, mixed_min_front=64,
-                            omega_target=1e-10)
+                            omega_target=1e-10, level_kernel=0)
     sf = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND, omega_target=1e-10)
     o = Oracle.from_lp(lp)
     for it in (0, 10, 20, 30, 35):

@@ -67,7 +67,7 @@ def test_noalloc_reports_a_stalled_tensor_core_factor(pkg):
     lp = synth.staircase(periods=3, pm=200, pn=500, density=0.01, links=50, seed=3)
     theta = synth.theta_schedule(lp.n, 40, 3)[20]
     s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND, precision=pkg.IPM_PREC_MIXED, mixed_min_front=64,
-                           omega_target=1e-10)
+                           omega_target=1e-10, level_kernel=0)
     s.factorise(theta, 1e-8, 1e-8)
     ox = torch.empty(lp.n, dtype=torch.float64, device=s.dev)
     oy = torch.empty(lp.m, dtype=torch.float64, device=s.dev)
