@@ -2,21 +2,33 @@
 """Benchmark of the IPM linear-algebra hot path on one GB300.
 
 One step = one IPM iteration's linear algebra: numeric factorisation of the
-regularised augmented system for a new Theta, then two solves with
-iterative refinement (predictor and one corrector).  The metric is ms per IPM
-iteration (lower is better), reported for the FP64 path and the
-mixed-precision path; the headline `value` is the fastest path that reaches
-its backward-error target.
+regularised augmented system for the iteration's Theta, then two refined
+solves (predictor and one corrector).  The metric is ms per IPM iteration
+(lower is better) and front GFLOP/s, per precision path, each at its
+backward-error target:
 
-The default workload is the grid multicommodity LP (64 x 64 grid,
-4 commodities, m = 24,444, n = 64,512, nested-dissection order).  Other
-workloads (--workload): random_300x800 (AMD), staircase (50 periods,
-m = 100,000, n = 250,000, Theta moving along a 40-iteration schedule) and
-batch512 (512 independent random LPs per GPU as one forest; with N GPUs the
-512 N instances are sharded over the ranks, no data exchange).
+  fp64    FP64 throughout;
+  sliced  FP64 pivots, lifts, residuals and refinement; Schur updates of
+          fronts >= 256 rows on the bf16 tensor cores from 7-bit digit slices
+          (FP64-accurate);
+  mixed   the same with FP32-accurate (3xTF32) tensor-core updates, which
+          fall back to FP64 factors when refinement cannot reach the target.
+
+Each path runs the direct calls, the end-to-end host entry point and the
+iteration captured once as a CUDA graph and replayed; the headline `value`
+is the fastest graph path that met its target.
+
+The default workload is the multi-period staircase LP (50 periods of
+2000 x 5000, m = 100,000, n = 250,000) along a 40-iteration Theta schedule
+(spread 1 to 1e-8..1e8), both paths refined to omega <= 1e-10 on K.  The
+timed steps walk the whole schedule (step k of K uses iteration
+round(39 k / (K - 1))).  Other workloads (--workload): grid64_q4 (64 x 64
+grid multicommodity LP, nested dissection), random_300x800, staircase10 (10
+periods, for profiling) and batch512 (512 independent LPs per GPU as one
+forest; with N GPUs the 512 N instances are sharded over the ranks).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload NAME] [--paths fp64,mixed] [--no-cpu-baseline] [--autotune-reps R]
+                       [--workload NAME] [--paths fp64,sliced,mixed] [--no-cpu-baseline] [--autotune-reps R]
 Prints one JSON line on rank 0.
 """
 from __future__ import annotations
@@ -36,16 +48,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 RHO = DELTA = 1e-8
-FP64_NOMINAL_TFLOPS = 1.25  # FP64 rate of a GB300 (profiling recipe's nominal table)
 L2_FLUSH_BYTES = 256 << 20
 BATCH_PER_GPU = 512
+SCHEDULE = 40
+# digit products per FP64-equivalent product in the sliced updates (8 slices, t + u <= 7)
+SLICED_PRODUCTS = 36
+METRIC = "factorise+solve ms per IPM iteration (front GFLOP/s alongside), mixed vs FP64 at backward error"
 
 
 class Workload:
     """Inputs of one benchmark workload on one rank: the problem (an LP, or a
-    list of LPs factorised as one forest), three Theta vectors the timed steps
-    cycle through (a 40-entry schedule for the staircase), two right-hand
-    sides, the ordering and the FP64 path's backward-error target."""
+    list of LPs factorised as one forest), the Theta vectors the steps use (a
+    40-iteration schedule for the staircase), two right-hand sides, the
+    ordering and the backward-error target of the FP64-accurate paths."""
 
     def __init__(self, name, rank=0, world=1):
         import synth
@@ -53,6 +68,7 @@ class Workload:
         self.name = name
         self.lps = None
         self.fp64_target = 1e-12
+        self.schedule = False
         self.tune_reps = 1 if name in ("batch512", "staircase", "staircase10") else 3  # autotuner repetitions
         if name == "batch512":
             import paper_2508_04370_gb300.batch as B
@@ -68,9 +84,12 @@ class Workload:
             self.desc = (f"{BATCH_PER_GPU * world} independent random LPs ({BATCH_PER_GPU} per GPU): m_i log-uniform "
                          f"in [100, 5000], n_i = 2.5 m_i, 5 nonzeros per column, N(0,1); own Theta_i = 10^U[-8,8]; "
                          f"one block-diagonal forest per GPU, AMD ordering; rank {rank}: {len(self.lps)} instances, "
-                         f"m={m}, n={n}; one IPM iteration = factorise + 2 refined solves")
+                         f"m={m}, n={n}; one IPM iteration = factorise + 2 refined solves of every instance")
         else:
-            lp = synth.staircase(periods=10, seed=1) if name == "staircase10" else synth.by_name(name, 1)
+            if name == "staircase10":
+                lp = synth.staircase(periods=10, seed=1)
+            else:
+                lp = synth.by_name(name, 1)
             self.lp = lp
             n, m = lp.n, lp.m
             if name == "grid64_q4":
@@ -82,29 +101,35 @@ class Workload:
                 self.ordering_name = "AMD"
                 self.desc = ("random sparse LP m=300, n=800, 6 nonzeros per column, N(0,1); Theta 10^U[-8,8]; "
                              "rho=delta=1e-8; AMD ordering; factorise + 2 refined solves")
-            elif name == "staircase":
+            elif name in ("staircase", "staircase10"):
+                per = 50 if name == "staircase" else 10
                 self.ordering_name = "nested-dissection"
                 self.fp64_target = 1e-10
-                self.desc = ("staircase LP: 50 periods of 2000 x 5000, density 0.002, 500 identity links to the next "
-                             "period (m=100000, n=250000); Theta_j = exp(s g_j) along a 40-iteration schedule "
-                             "(spread 1 to 1e-8..1e8); nested-dissection ordering; factorise + 2 solves refined to "
-                             "omega <= 1e-10 on both paths")
-            elif name == "staircase10":
-                self.ordering_name = "nested-dissection"
-                self.fp64_target = 1e-10
-                self.desc = ("staircase LP, 10 periods of 2000 x 5000 (a profiling size of the 50-period workload), "
-                             "density 0.002, 500 identity links; Theta along the 40-iteration schedule; "
-                             "nested-dissection ordering; factorise + 2 solves refined to omega <= 1e-10")
+                self.schedule = True
+                self.desc = (f"staircase LP: {per} periods of 2000 x 5000, density 0.002, 500 identity links to the "
+                             f"next period (m={m}, n={n}); Theta_j = exp(s g_j) along a 40-iteration schedule "
+                             f"(spread 1 at iteration 0 to 1e-8..1e8 at 39), timed steps spread over the whole "
+                             f"schedule; nested-dissection ordering; one IPM iteration = factorise + 2 solves "
+                             f"(predictor + corrector) refined to omega <= 1e-10 on K on every path")
             else:
                 raise SystemExit(f"unknown workload {name}")
-            if name in ("staircase", "staircase10"):
-                self.thetas = synth.theta_schedule(n, 40, 1)
+            if self.schedule:
+                self.thetas = synth.theta_schedule(n, SCHEDULE, 1)
             else:
                 self.thetas = [synth.theta_loguniform(n, 1 + t) for t in range(3)]
         n = len(self.thetas[0])
         m = sum(lp.m for lp in self.lps) if self.lps else self.lp.m
         self.n, self.m = n, m
         self.rhs = [(synth.rhs_normal(n, 10 + 2 * t), synth.rhs_normal(m, 11 + 2 * t)) for t in range(2)]
+
+    def theta_index(self, i, steps, timed):
+        """Theta of step i: the timed steps of a schedule walk it from the first
+        to the last iteration; warm-up steps take its first iterations."""
+        if not self.schedule:
+            return i % len(self.thetas)
+        if not timed:
+            return min(i, SCHEDULE - 1)
+        return int(round((SCHEDULE - 1) * i / max(steps - 1, 1)))
 
     def ordering(self, pkg):
         return pkg.IPM_ORD_AMD if self.ordering_name == "AMD" else pkg.IPM_ORD_ND
@@ -172,17 +197,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(kernel):
-    """Per-launch DRAM bytes of a kernel class from a committed ncu summary,
-    valid only while every source it depends on (the kernel, and the
-    ordering and analysis that shape the workload's tree) is unchanged."""
+def traffic_for(kernel, workload, alg_bytes_per_launch):
+    """DRAM bytes per launch of a kernel class on a workload, from a committed
+    ncu summary (DRAM bytes over the algorithmic bytes of a captured launch,
+    scaled by this run's algorithmic bytes per launch); valid only while every
+    source it depends on (the kernel, and the ordering and analysis that shape
+    the workload's tree) is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             table = json.load(fh)
     except OSError:
         return None
-    ent = table.get(kernel)
+    ent = table.get(f"{kernel}@{workload}")
     if not ent:
         return None
     for rel, want in ent["sources"].items():
@@ -193,10 +220,133 @@ def traffic_for(kernel):
             return None
         if sha != want:
             return None
-    return ent["bytes_per_launch"]
+    return ent["dram_over_algorithmic"] * alg_bytes_per_launch
 
 
 # ------------------------------------------------------------- our arm
+
+PATHS = {"fp64": "IPM_PREC_FP64", "sliced": "IPM_PREC_SLICED", "mixed": "IPM_PREC_MIXED"}
+
+
+def run_path(args, W, pkg, torch, dev, pname, world):
+    """Direct calls, end to end through the host entry point, and the CUDA
+    graph, for one precision path."""
+    prec = getattr(pkg, PATHS[pname])
+    target = 1e-10 if pname == "mixed" else W.fp64_target
+    s = W.solver(pkg, precision=prec, omega_target=target, device=dev.index)
+    n, m = W.n, W.m
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    th = [torch.as_tensor(t, device=dev) for t in W.thetas]
+    rr = [(torch.as_tensor(a, device=dev), torch.as_tensor(b, device=dev)) for a, b in W.rhs]
+    dx = torch.empty(n, dtype=torch.float64, device=dev)
+    dy = torch.empty(m, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    K = args.steps
+
+    def step(idx):
+        pkg.ipm_factorise(s.ctx, th[idx], RHO, DELTA, stream)
+        for a, b in rr:
+            rc = pkg.ipm_solve(s.ctx, a, b, dx, dy, stream)
+            if rc < 0:
+                raise RuntimeError(f"ipm_solve failed ({rc})")
+
+    # launch shapes picked by the library's autotuner on this problem, after
+    # one step so that a tensor-core path tunes the precision it keeps (set-up,
+    # like the analysis; not timed)
+    step(0)
+    reps = W.tune_reps if args.autotune_reps is None else args.autotune_reps
+    tune = s.autotune(th[0], RHO, DELTA, reps=reps) if reps > 0 else {"skipped": True}
+    for i in range(args.warmup):
+        step(W.theta_index(i, K, False))
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    omegas = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    for i in range(K):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        ev[i][0].record(stream)
+        step(W.theta_index(i, K, True))
+        ev[i][1].record(stream)
+        omegas.append(s.info()["omega"])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    info = s.info()
+    # per-launch CUDA events (the kernel classes behind the roofline) in a
+    # separate pass over steps spread like the timed ones: recording them
+    # slows the steps down, so the timed region above runs without them
+    nprof = min(K, 4)
+    pkg.ipm_kernel_stats(s.ctx, reset=True)
+    pkg.ipm_set_profiling(s.ctx, True)
+    for i in range(nprof):
+        flush.zero_()
+        step(W.theta_index(i, nprof, True))
+    torch.cuda.synchronize()
+    pkg.ipm_set_profiling(s.ctx, False)
+    kstats = pkg.ipm_kernel_stats(s.ctx, reset=True)
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    r7h = np.ascontiguousarray(np.concatenate([a for a, _ in W.rhs]))
+    r1h = np.ascontiguousarray(np.concatenate([b for _, b in W.rhs]))
+    dxh = np.empty(2 * n)
+    dyh = np.empty(2 * m)
+    thh = [np.ascontiguousarray(t) for t in W.thetas]
+    for i in range(max(1, min(args.warmup, 2))):
+        pkg.ipm_iterate_host(s.ctx, thh[W.theta_index(i, K, False)], RHO, DELTA, r7h, r1h, dxh, dyh, nrhs=2,
+                             stream=stream)
+    torch.cuda.synchronize()
+    e2e = []
+    for i in range(K):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rc = pkg.ipm_iterate_host(s.ctx, thh[W.theta_index(i, K, True)], RHO, DELTA, r7h, r1h, dxh, dyh, nrhs=2,
+                                  stream=stream)
+        e2e.append((time.perf_counter() - t1) * 1e3)
+        if rc < 0:
+            raise RuntimeError(f"ipm_iterate_host failed ({rc})")
+    out = dict(step_ms=step_ms, kstats=kstats, prof_steps=nprof, info=info, omegas=omegas, clocks=clk, e2e_ms=e2e,
+               target=target,
+               h2d=8 * (n + 2 * (n + m)), d2h=8 * 2 * (n + m), tune=tune)
+    # the same iteration captured once as a CUDA graph and replayed
+    th_buf = torch.empty(n, dtype=torch.float64, device=dev)
+    th_buf.copy_(th[0])
+    r7d = torch.cat([a for a, _ in rr])
+    r1d = torch.cat([b for _, b in rr])
+    gdx = torch.empty(2 * n, dtype=torch.float64, device=dev)
+    gdy = torch.empty(2 * m, dtype=torch.float64, device=dev)
+    rc = pkg.ipm_graph_capture(s.ctx, th_buf, RHO, DELTA, r7d, r1d, gdx, gdy, nsolves=2, stream=stream)
+    if rc == 0:
+        for i in range(args.warmup):
+            th_buf.copy_(th[W.theta_index(i, K, False)])
+            pkg.ipm_graph_launch(s.ctx, stream)
+        torch.cuda.synchronize()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        gom = []
+        if world > 1:
+            torch.distributed.barrier()
+        gclocks = ClockSampler(dev.index)
+        gclocks.start()
+        for i in range(K):
+            flush.zero_()
+            gev[i][0].record(stream)
+            th_buf.copy_(th[W.theta_index(i, K, True)])
+            pkg.ipm_graph_launch(s.ctx, stream)
+            gev[i][1].record(stream)
+            gom.append(s.info()["omega"])
+        torch.cuda.synchronize()
+        ginfo = s.info()
+        out["graph"] = dict(step_ms=[a.elapsed_time(b) for a, b in gev], omegas=gom, clocks=gclocks.stop(),
+                            info=ginfo, kernels_per_step=ginfo["graph_kernels"])
+    out["symbolic"] = s.symbolic() if W.lps is None else None
+    s.close()
+    return out
+
 
 def run_ours(args, W, rank, world):
     import torch
@@ -205,238 +355,212 @@ def run_ours(args, W, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    n, m = W.n, W.m
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     results = {}
-    precisions = [("fp64", pkg.IPM_PREC_FP64, W.fp64_target), ("mixed", pkg.IPM_PREC_MIXED, 1e-10)]
-    precisions = [p for p in precisions if p[0] in args.paths.split(",")]
-    for pname, prec, target in precisions:
-        s = W.solver(pkg, precision=prec, omega_target=target, device=dev.index)
-        th = [torch.as_tensor(t, device=dev) for t in W.thetas]
-        rr = [(torch.as_tensor(a, device=dev), torch.as_tensor(b, device=dev)) for a, b in W.rhs]
-        dx = torch.empty(n, dtype=torch.float64, device=dev)
-        dy = torch.empty(m, dtype=torch.float64, device=dev)
-        stream = torch.cuda.current_stream()
-
-        def step(i):
-            pkg.ipm_factorise(s.ctx, th[i % len(th)], RHO, DELTA, stream)
-            for a, b in rr:
-                rc = pkg.ipm_solve(s.ctx, a, b, dx, dy, stream)
-                if rc < 0:
-                    raise RuntimeError(f"ipm_solve failed ({rc})")
-
-        # launch shapes picked by the library's autotuner on this problem,
-        # after one step so that the mixed path tunes the precision it keeps
-        # (setup, like the analysis; not timed)
-        step(0)
-        reps = W.tune_reps if args.autotune_reps is None else args.autotune_reps
-        tune = s.autotune(th[0], RHO, DELTA, reps=reps) if reps > 0 else {"skipped": True}
-
-        for i in range(args.warmup):
-            step(i)
-        torch.cuda.synchronize()
-        pkg.ipm_kernel_stats(s.ctx, reset=True)
-        pkg.ipm_set_profiling(s.ctx, True)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        omegas = []
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        clocks = ClockSampler(dev.index)
-        clocks.start()
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()  # L2 flush between timed steps (outside the events)
-            ev[i][0].record(stream)
-            step(i)
-            ev[i][1].record(stream)
-            omegas.append(s.info()["omega"])
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        if world > 1:
-            torch.distributed.barrier()
-        clk = clocks.stop()
-        pkg.ipm_set_profiling(s.ctx, False)
-        kstats = pkg.ipm_kernel_stats(s.ctx, reset=True)
-        step_ms = [a.elapsed_time(b) for a, b in ev]
-        info = s.info()
-        # end to end through the host-buffer entry point
-        r7h = np.ascontiguousarray(np.concatenate([a for a, _ in W.rhs]))
-        r1h = np.ascontiguousarray(np.concatenate([b for _, b in W.rhs]))
-        dxh = np.empty(2 * n)
-        dyh = np.empty(2 * m)
-        thh = [np.ascontiguousarray(t) for t in W.thetas]
-        for i in range(max(1, args.warmup)):
-            pkg.ipm_iterate_host(s.ctx, thh[i % len(thh)], RHO, DELTA, r7h, r1h, dxh, dyh, nrhs=2, stream=stream)
-        torch.cuda.synchronize()
-        e2e = []
-        for i in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            rc = pkg.ipm_iterate_host(s.ctx, thh[i % len(thh)], RHO, DELTA, r7h, r1h, dxh, dyh, nrhs=2, stream=stream)
-            e2e.append((time.perf_counter() - t1) * 1e3)
-            if rc < 0:
-                raise RuntimeError(f"ipm_iterate_host failed ({rc})")
-        results[pname] = dict(step_ms=step_ms, wall_s=wall, kstats=kstats, info=info, omegas=omegas, clocks=clk,
-                              e2e_ms=e2e, target=target, h2d=8 * (n + 2 * (n + m)), d2h=8 * 2 * (n + m), tune=tune)
-        # the same iteration captured once as a CUDA graph and replayed
-        th_buf = torch.empty(n, dtype=torch.float64, device=dev)
-        th_buf.copy_(th[0])
-        r7d = torch.cat([a for a, _ in rr])
-        r1d = torch.cat([b for _, b in rr])
-        gdx = torch.empty(2 * n, dtype=torch.float64, device=dev)
-        gdy = torch.empty(2 * m, dtype=torch.float64, device=dev)
-        rc = pkg.ipm_graph_capture(s.ctx, th_buf, RHO, DELTA, r7d, r1d, gdx, gdy, nsolves=2, stream=stream)
-        if rc == 0:
-            for i in range(args.warmup):
-                th_buf.copy_(th[i % len(th)])
-                pkg.ipm_graph_launch(s.ctx, stream)
-            torch.cuda.synchronize()
-            gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                   for _ in range(args.steps)]
-            gom = []
-            for i in range(args.steps):
-                flush.zero_()
-                gev[i][0].record(stream)
-                th_buf.copy_(th[i % len(th)])
-                pkg.ipm_graph_launch(s.ctx, stream)
-                gev[i][1].record(stream)
-                gom.append(s.info()["omega"])
-            torch.cuda.synchronize()
-            results[pname + "_graph"] = dict(step_ms=[a.elapsed_time(b) for a, b in gev], kstats=kstats,
-                                             info=s.info(), omegas=gom, clocks=clk, e2e_ms=e2e, target=target,
-                                             h2d=results[pname]["h2d"], d2h=results[pname]["d2h"])
-        s.close()
+    for pname in [p for p in args.paths.split(",") if p]:
+        if pname not in PATHS:
+            raise SystemExit(f"unknown path {pname}")
+        results[pname] = run_path(args, W, pkg, torch, dev, pname, world)
     return results
 
 
-def roofline(kstats, peaks, sustained):
+# ------------------------------------------------------------- rooflines
+
+HBM_CLASSES = ("forward", "backward", "residual", "large_assemble", "other", "slice")
+FP64_CLASSES = ("small_fronts", "large_panel", "large_update", "pivot_block")
+
+
+def class_peak(name, pname, peaks, fp64_peak):
+    """(bound, peak, unit, source, work multiplier) of a kernel class."""
+    if name in HBM_CLASSES:
+        return "hbm", peaks.get("hbm_gbs", 6800.0), "GB/s", "measured HBM copy (MEASURED_PEAKS.json)", 1.0
+    if name == "large_update_tc" and pname == "sliced":
+        # every FP64-equivalent product runs as 36 bf16 digit products on the tensor cores
+        return ("tensor", peaks.get("bf16_tflops_sustained", 1700.0), "TFLOP/s",
+                "measured bf16 GEMM, sustained (MEASURED_PEAKS.json); achieved counts the 36 bf16 digit products "
+                "per FP64-equivalent product", float(SLICED_PRODUCTS))
+    if name == "large_update_tc":
+        # 3xTF32: three tf32 products per FP64-equivalent product, tf32 at half the bf16 rate
+        return ("tensor", peaks.get("bf16_tflops_sustained", 1700.0) / 2.0, "TFLOP/s",
+                "measured bf16 GEMM sustained x nominal tf32/bf16 ratio 1/2; achieved counts 3 tf32 products", 3.0)
+    return ("alu", fp64_peak["tflops"], "TFLOP/s", fp64_peak["source"], 1.0)
+
+
+def roofline(kstats, pname, peaks, fp64_peak, workload):
     """Dominant kernel class of the timed region and its achieved rate."""
     name, st = max(((k, v) for k, v in kstats.items() if v["launches"] > 0), key=lambda kv: kv[1]["ms"])
     avg_ms = st["ms"] / st["launches"]
-    if name in ("forward", "backward", "residual", "large_assemble", "other"):
+    bound, peak, unit, source, mult = class_peak(name, pname, peaks, fp64_peak)
+    if bound == "hbm":
         achieved = st["bytes"] / st["launches"] / (avg_ms * 1e-3) / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-               "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-    elif name == "large_update_tc":
-        achieved = st["flops"] / st["launches"] / (avg_ms * 1e-3) / 1e12
-        bf16 = peaks.get("bf16_tflops_sustained" if sustained else "bf16_tflops", 1900.0)
-        peak = bf16 / 2.0  # tf32 dense rate is half the bf16 rate (nominal 1.1 vs 2.25 PFLOP/s)
-        out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-               "peak_source": "measured bf16 x nominal tf32/bf16 ratio"}
     else:
-        achieved = st["flops"] / st["launches"] / (avg_ms * 1e-3) / 1e12
-        out = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-               "peak_source": "nominal FP64 (152 SMs x 2.07 GHz x 2 FMA/clk/SM x 2)"}
-    out["frac"] = out["achieved"] / out["peak"]
-    out["kernel"] = name
-    out["launches"] = st["launches"]
-    out["avg_launch_ms"] = avg_ms
-    out["share_of_step"] = None
-    out["traffic"] = traffic_for(name)
+        achieved = mult * st["flops"] / st["launches"] / (avg_ms * 1e-3) / 1e12
+    out = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "peak_source": source,
+           "frac": achieved / peak, "kernel": name, "launches": st["launches"], "avg_launch_ms": avg_ms,
+           "traffic": traffic_for(name, workload, st["bytes"] / st["launches"])}
+    if name == "large_update_tc":
+        out["fp64_equivalent_tflops"] = st["flops"] / st["ms"] / 1e9
+        out["fp64_equivalent_frac_of_fp64_peak"] = out["fp64_equivalent_tflops"] / fp64_peak["tflops"]
     return out
 
 
-class _OracleProblem:
-    """One problem of the workload for the oracle, analysed on first use."""
+def phase_bound(kstats, pname, peaks, fp64_peak, steps, step_ms):
+    """T* = sum over kernel classes of max(flops / P, bytes / BW) per step (the
+    classes' algorithmic work), against the measured time per step."""
+    bw = peaks.get("hbm_gbs", 6800.0) * 1e9
+    phases = {}
+    for name, st in kstats.items():
+        if not st["launches"]:
+            continue
+        bound, peak, unit, _, mult = class_peak(name, pname, peaks, fp64_peak)
+        t_flop = 0.0 if bound == "hbm" else mult * st["flops"] / (peak * 1e12)
+        t_byte = st["bytes"] / bw
+        phases[name] = {"t_star_ms": 1e3 * max(t_flop, t_byte) / steps, "measured_ms": st["ms"] / steps}
+    t_star = sum(v["t_star_ms"] for v in phases.values())
+    return {"t_star_ms": t_star, "ms_per_step": step_ms, "t_star_over_measured": t_star / step_ms,
+            "note": "per class: max(algorithmic flops / peak, algorithmic bytes / HBM) per step, summed; measured_ms "
+                    "sums per-launch events (overlapping streams count twice)", "phases": phases}
 
-    def __init__(self, lp, perm, thetas, rhs, weight, amalg_zero_frac):
-        self.lp, self.perm, self.thetas, self.rhs, self.weight = lp, perm, thetas, rhs, weight
-        self.amalg_zero_frac = amalg_zero_frac
-        self.o = None
 
-    def oracle(self):
-        from oracle import Oracle
+def critical_path(sym, kstats):
+    """Latency bound of the elimination tree: the longest leaf-to-root chain of
+    32-column panels of large fronts (every panel's pivot block waits for the
+    previous one), times the measured mean duration of a pivot-block launch."""
+    if sym is None:
+        return None
+    sp, rp, parent = sym["snode_ptr"], sym["sn_rptr"], sym["sn_parent"]
+    k = np.diff(sp)
+    f = np.diff(rp)
+    own = np.where(f > 128, (k + 31) // 32, 0)
+    chain = np.zeros(len(k), dtype=np.int64)
+    below = np.zeros(len(k), dtype=np.int64)
+    for s in range(len(k)):  # children come before their parent
+        chain[s] = below[s] + own[s]
+        if parent[s] >= 0:
+            below[parent[s]] = max(below[parent[s]], chain[s])
+    panels = int(chain.max()) if len(chain) else 0
+    pb = kstats.get("pivot_block", {"launches": 0})
+    us = 1e3 * pb["ms"] / pb["launches"] if pb["launches"] else None
+    return {"chain_panels": panels, "pivot_block_us": us,
+            "bound_ms": panels * us / 1e3 if us else None,
+            "note": "longest leaf-to-root chain of 32-column panels of fronts > 128 rows x mean pivot-block launch"}
 
-        if self.o is None:
-            self.o = Oracle.from_lp(self.lp)
-            self.o.analyse(self.perm, amalg_zero_frac=self.amalg_zero_frac)
-        return self.o
+
+def measure_fp64(pkg, dev):
+    dfma, dmma = pkg.ipm_measure_fp64_peak(dev.index)
+    best = max(dfma, dmma)
+    return {"tflops": best, "dfma_tflops": dfma, "dmma_tflops": dmma,
+            "source": "measured on this GPU by ipm_measure_fp64_peak (DFMA and mma.sync.m8n8k4.f64 chains over every "
+                      "SM, best of 3 timed runs, CUDA events)"}
 
 
-def oracle_problems(W, pkg):
-    """The workload's problems for the oracle, in the library's order
-    (batches: per instance, the batch order restricted to it).  The order
-    comes from the library's host-side analysis (no GPU needed)."""
+# ------------------------------------------------------------- the oracle
+
+def staircase_sample(W):
+    """The staircase's bounded CPU sample: the same generator with 2 periods."""
+    import synth
+
+    return synth.staircase(periods=2, seed=1)
+
+
+def oracle_problem(lp, pkg, ordering, batch=None):
+    """An oracle for lp analysed in the library's order (host-side analysis,
+    no GPU); returns (oracle, library front flops)."""
+    from oracle import Oracle
+
     ctx = pkg.ipm_create(pkg.ipm_default_options())
-    if W.lps is None:
-        rc = pkg.ipm_analyse(ctx, W.lp.m, W.lp.n, W.lp.colptr, W.lp.rowidx, pkg.IPM_FORM_AUGMENTED, W.ordering(pkg))
-    else:
-        rc = pkg.ipm_analyse_batch(ctx, np.array([lp.m for lp in W.lps], np.int32),
-                                   np.array([lp.n for lp in W.lps], np.int32),
-                                   np.concatenate([np.asarray(lp.colptr, np.int64) for lp in W.lps]),
-                                   np.concatenate([np.asarray(lp.rowidx, np.int32) for lp in W.lps]),
-                                   W.ordering(pkg))
+    rc = pkg.ipm_analyse(ctx, lp.m, lp.n, lp.colptr, lp.rowidx, pkg.IPM_FORM_AUGMENTED, ordering)
     if rc:
         raise RuntimeError(f"analysis failed ({rc})")
     sym = pkg.ipm_get_symbolic(ctx)
-    perm, az = sym["perm"], sym["amalg_zero_frac"]
+    _, info = pkg.ipm_get_info(ctx)
     pkg.ipm_destroy(ctx)
-    if W.lps is None:
-        return [_OracleProblem(W.lp, perm, W.thetas, W.rhs, 1.0, az)]
-    out = []
-    nof = np.concatenate([[0], np.cumsum([lp.n for lp in W.lps])])
-    mof = np.concatenate([[0], np.cumsum([lp.m for lp in W.lps])])
-    Nn = int(nof[-1])
-    inst = np.empty(len(perm), dtype=np.int64)
-    loc = np.empty(len(perm), dtype=np.int64)
-    for b, lp in enumerate(W.lps):
-        inst[nof[b]:nof[b + 1]] = b
-        loc[nof[b]:nof[b + 1]] = np.arange(lp.n)
-        inst[Nn + mof[b]:Nn + mof[b + 1]] = b
-        loc[Nn + mof[b]:Nn + mof[b + 1]] = lp.n + np.arange(lp.m)
-    pi, pl = inst[perm], loc[perm]
-    import paper_2508_04370_gb300.batch as B
-
-    total = sum(B.instance_cost(lp.m, lp.n, int(lp.colptr[-1])) for lp in W.lps)
-    for b, lp in enumerate(W.lps):
-        th = [t[nof[b]:nof[b + 1]] for t in W.thetas]
-        rhs = [(a[nof[b]:nof[b + 1]], c[mof[b]:mof[b + 1]]) for a, c in W.rhs]
-        out.append(_OracleProblem(lp, pl[pi == b].astype(np.int32), th, rhs,
-                                  B.instance_cost(lp.m, lp.n, int(lp.colptr[-1])) / total, az))
-    return out
+    o = Oracle.from_lp(lp)
+    o.analyse(sym["perm"], amalg_zero_frac=sym["amalg_zero_frac"])
+    return o, info.flops_factor
 
 
-def oracle_iteration(probs, i, target, budget_end=None):
-    """One IPM iteration of the oracle over the problems (or as many as fit
-    before budget_end); returns (ms, fraction of the workload's work done).
-    The symbolic analysis of a problem is not timed."""
-    ms = 0.0
-    frac = 0.0
-    for pb in probs:
-        o = pb.oracle()
-        t0 = time.perf_counter()
-        o.factorise(pb.thetas[i % len(pb.thetas)], RHO, DELTA)
-        for a, b in pb.rhs:
-            o.solve(a, b, omega_target=target, max_steps=10)
-        ms += (time.perf_counter() - t0) * 1e3
-        frac += pb.weight
-        if budget_end is not None and time.perf_counter() > budget_end:
-            break
-    return ms, frac
+def oracle_iteration(o, theta, rhs, target):
+    t0 = time.perf_counter()
+    o.factorise(theta, RHO, DELTA)
+    for a, b in rhs:
+        o.solve(a, b, omega_target=target, max_steps=10)
+    return (time.perf_counter() - t0) * 1e3
+
+
+class OracleArm:
+    """The oracle (plain C, one host core) on a bounded sample of the
+    workload, scaled to one full IPM iteration."""
+
+    def __init__(self, W, pkg):
+        import synth
+
+        self.W = W
+        if W.schedule:
+            # the full staircase takes minutes per iteration on one core: time
+            # the 2-period staircase along the same schedule and scale by the
+            # front flops (the oracle's time is its dense front work)
+            lp = staircase_sample(W)
+            self.o, flops = oracle_problem(lp, pkg, pkg.IPM_ORD_ND)
+            full = pkg.ipm_create(pkg.ipm_default_options())
+            pkg.ipm_analyse(full, W.lp.m, W.lp.n, W.lp.colptr, W.lp.rowidx, pkg.IPM_FORM_AUGMENTED, pkg.IPM_ORD_ND)
+            _, finfo = pkg.ipm_get_info(full)
+            pkg.ipm_destroy(full)
+            self.scale = finfo.flops_factor / flops
+            self.thetas = synth.theta_schedule(lp.n, SCHEDULE, 1)
+            self.rhs = [(synth.rhs_normal(lp.n, 10 + 2 * t), synth.rhs_normal(lp.m, 11 + 2 * t)) for t in range(2)]
+            self.sample = (f"the same staircase generator with 2 periods (m={lp.m}, n={lp.n}, {flops:.3e} front flops), "
+                           f"one IPM iteration (factorise + 2 solves refined to 1e-10) at schedule iterations spread "
+                           f"like the timed steps, time x {self.scale:.1f} (the full problem's front flops over the "
+                           f"sample's)")
+        elif W.lps is None:
+            self.o, _ = oracle_problem(W.lp, pkg, W.ordering(pkg))
+            self.scale = 1.0
+            self.thetas = W.thetas
+            self.rhs = W.rhs
+            self.sample = "full IPM iterations of the same workload (factorise + 2 refined solves)"
+        else:
+            raise SystemExit("the oracle arm covers the single-LP workloads")
+
+    def step(self, i, steps):
+        idx = self.W.theta_index(i, steps, True)
+        return self.scale * oracle_iteration(self.o, self.thetas[idx], self.rhs, self.W.fp64_target)
 
 
 def cpu_baseline(W, pkg, budget_s=12.0):
-    """The oracle as it stands, single thread, on a bounded sample of the
-    same workload, scaled to one full IPM iteration."""
-    probs = oracle_problems(W, pkg)
+    """The oracle as it stands, single thread, on a bounded sample, scaled to
+    one full IPM iteration (median)."""
+    arm = OracleArm(W, pkg)
+    nmax = 3 if W.schedule else 50
     times = []
     t_end = time.perf_counter() + budget_s
-    i = 0
-    while True:
-        ms, frac = oracle_iteration(probs, i, W.fp64_target, t_end if len(probs) > 1 else None)
-        times.append(ms / frac)
-        i += 1
-        if time.perf_counter() > t_end or i >= 50:
-            break
-    if len(probs) > 1:
-        sample = (f"instances of the batch in order until {budget_s:.0f} s (factorise + 2 refined solves each), "
-                  f"time scaled by their share of the nnz(A) sqrt(m) work estimate")
-    else:
-        sample = f"{i} full IPM iterations of the same workload (factorise + 2 refined solves), median"
-    return float(np.median(times)), sample + "; symbolic analysis excluded"
+    while len(times) < nmax and (not times or time.perf_counter() < t_end):
+        times.append(arm.step(len(times), nmax))
+    return float(np.median(times)), f"{len(times)} samples, median: {arm.sample}; symbolic analysis excluded"
+
+
+# ------------------------------------------------------------------ main
+
+def summarise(pname, r, graph):
+    src = r["graph"] if graph else r
+    ms = float(np.mean(src["step_ms"]))
+    info = src["info"]
+    fl = r["info"]["flops_factor"]
+    return {"ms_per_iter": ms, "met_target": bool(max(src["omegas"]) <= r["target"]),
+            "omega_max": float(max(src["omegas"])), "omega_target": r["target"],
+            "front_flops": fl, "precision_fallbacks": int(info["precision_fallbacks"]),
+            "tensor_cores_in_use": bool(info["mixed_active"]),
+            "e2e_ms_per_iter": float(np.median(r["e2e_ms"])) if not graph else None}
+
+
+def factor_label(pname, per):
+    if pname == "fp64":
+        return "FP64 throughout"
+    if not per["tensor_cores_in_use"]:
+        return "FP64 throughout (the tensor-core path fell back to FP64 factors)"
+    if pname == "sliced":
+        return ("FP64 pivots, lifts and refinement; Schur updates of fronts >= 256 rows from 7-bit digit slices on "
+                "the bf16 tensor cores (FP64-accurate)")
+    return "FP64 pivots and refinement; FP32-accurate (3xTF32) tensor-core Schur updates"
 
 
 def main():
@@ -446,17 +570,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="grid64_q4",
-                    choices=["grid64_q4", "random_300x800", "staircase", "staircase10", "batch512"])
-    ap.add_argument("--paths", default="fp64,mixed", help="comma-separated subset of fp64,mixed")
+    ap.add_argument("--workload", default="staircase",
+                    choices=["staircase", "grid64_q4", "random_300x800", "staircase10", "batch512"])
+    ap.add_argument("--paths", default="fp64,sliced,mixed", help="comma-separated subset of fp64,sliced,mixed")
     ap.add_argument("--autotune-reps", type=int, default=None,
-                    help="repetitions per autotuner candidate (0: keep the library's default launch shapes, "
-                         "e.g. for profiling runs)")
+                    help="repetitions per autotuner candidate (0: keep the library's default launch shapes)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.gpus != world:
+        print(f"bench.py: --gpus {args.gpus} needs one process per GPU (torch.distributed.run with "
+              f"--nproc-per-node {args.gpus}); this run has WORLD_SIZE={world}", file=sys.stderr)
+        return 2
     if args.impl == "reference":
         return run_reference(args, rank, world)
     import torch
@@ -469,38 +596,36 @@ def main():
         build()
     if world > 1:
         torch.distributed.barrier()
-    W = Workload(args.workload, rank, world)
-    results = run_ours(args, W, rank, world)
     import paper_2508_04370_gb300 as pkg
 
+    W = Workload(args.workload, rank, world)
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    fp64_peak = measure_fp64(pkg, dev)
+    results = run_ours(args, W, rank, world)
     peaks = load_peaks()
-    # the headline: fastest path that met its target
-    best = None
     per = {}
+    best = None
     for pname, r in results.items():
-        ms = float(np.sum(r["step_ms"]) / len(r["step_ms"]))
-        ok = max(r["omegas"]) <= r["target"]
-        fl = r["info"]["flops_factor"]
-        per[pname] = {"ms_per_iter": ms, "met_target": bool(ok), "omega_max": max(r["omegas"]),
-                      "omega_target": r["target"], "refine_steps_last": r["info"]["refine_steps"],
-                      "front_flops": fl, "e2e_ms_per_iter": float(np.median(r["e2e_ms"])),
-                      "tensor_flops": r["info"]["flops_tensor"],
-                      "precision_fallbacks": r["info"]["precision_fallbacks"],
-                      "tensor_cores_in_use": bool(r["info"]["mixed_active"]),
-                      "autotune": results[pname.replace("_graph", "")]["tune"]}
+        per[pname] = summarise(pname, r, False)
+        per[pname]["autotune"] = r["tune"]
         fms = sum(v["ms"] for k, v in r["kstats"].items()
-                  if k in ("small_fronts", "large_assemble", "large_panel", "large_update", "large_update_tc"))
-        nst = len(results[pname.replace("_graph", "")]["step_ms"])
-        per[pname]["factorise_kernel_ms_per_iter"] = fms / nst
-        per[pname]["front_gflops"] = fl / (fms / nst * 1e-3) / 1e9 if fms > 0 else None
-        if not pname.endswith("_graph"):
-            per[pname]["kernels"] = {k: {"launches": v["launches"], "ms": round(v["ms"], 4)}
-                                     for k, v in r["kstats"].items() if v["launches"]}
-        if ok and (best is None or ms < per[best]["ms_per_iter"]):
+                  if k in ("small_fronts", "large_assemble", "large_panel", "large_update", "large_update_tc",
+                           "slice", "pivot_block"))
+        per[pname]["factorise_kernel_ms_per_iter"] = fms / r["prof_steps"]
+        per[pname]["kernels"] = {k: {"launches": v["launches"], "ms": round(v["ms"], 4)}
+                                 for k, v in r["kstats"].items() if v["launches"]}
+        if "graph" in r:
+            g = summarise(pname, r, True)
+            per[pname + "_graph"] = g
+            if g["met_target"] and (best is None or g["ms_per_iter"] < per[best]["ms_per_iter"]):
+                best = pname + "_graph"
+        elif per[pname]["met_target"] and (best is None or per[pname]["ms_per_iter"] < per[best]["ms_per_iter"]):
             best = pname
     if best is None:
-        best = next(iter(results))
-    r = results[best]
+        best = next(iter(per))
+    base = best.replace("_graph", "")
+    r = results[base]
     ms_local = per[best]["ms_per_iter"]
     if world > 1:
         t = torch.tensor([ms_local], device="cuda", dtype=torch.float64)
@@ -508,16 +633,22 @@ def main():
         ms_max = float(t.item())
     else:
         ms_max = ms_local
-    # whole-job ms per IPM iteration of the workload: every rank runs its own
-    # problem (a replica of the single LP, or its shard of the batch) at once
-    value = ms_max / world
-    launches = sum(v["launches"] for v in r["kstats"].values())
-    rl = roofline(r["kstats"], peaks, sustained=False)
-    step_total = float(np.sum(r["step_ms"]))
-    rl["share_of_step"] = r["kstats"][rl["kernel"]]["ms"] / step_total if step_total > 0 else None
+    # kernel launches in the timed region: the graph's kernel nodes per replay,
+    # or the direct path's launches per step (counted in the profiled pass)
+    if best.endswith("_graph"):
+        launches = int(r["graph"]["kernels_per_step"]) * args.steps
+    else:
+        launches = int(round(sum(v["launches"] for v in r["kstats"].values()) * args.steps / r["prof_steps"]))
+    rl = roofline(r["kstats"], base, peaks, fp64_peak, W.name)
+    rl["share_of_step"] = (r["kstats"][rl["kernel"]]["ms"] / r["prof_steps"]) / float(np.mean(r["step_ms"]))
+    rl["events"] = (f"per-launch CUDA events on each launch's stream over {r['prof_steps']} profiled steps spread "
+                    f"over the schedule like the timed ones")
+    # front GFLOP/s of the headline path: front flops / (ms per iteration spent factorising)
+    fl = per[best]["front_flops"]
+    clk = (r["graph"]["clocks"] if best.endswith("_graph") else r["clocks"])
     out = {
-        "metric": "factorise+solve ms per IPM iteration (front GFLOP/s alongside), mixed vs FP64 at backward error",
-        "value": value,
+        "metric": METRIC,
+        "value": ms_max,
         "unit": "ms",
         "n_gpus": world,
         "steps": args.steps,
@@ -526,64 +657,66 @@ def main():
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64+tf32" if per[best]["tensor_cores_in_use"] else "f64",
+        "dtype": ("f64+bf16-slices" if base == "sliced" and per[best]["tensor_cores_in_use"] else
+                  "f64+tf32" if base == "mixed" and per[best]["tensor_cores_in_use"] else "f64"),
         "data": "synthetic",
         "config": {"workload": W.desc, "path": best, "omega_target": per[best]["omega_target"],
-                   "factors": ("FP64 pivots, tensor-core Schur updates" if per[best]["tensor_cores_in_use"] else
-                               "FP64 throughout" + (" (the mixed path fell back to FP64 factors)"
-                                                    if per[best]["precision_fallbacks"] else "")),
+                   "factors": factor_label(base, per[best]),
                    "l2": "flushed between timed steps (256 MiB write outside the step events)",
-                   "parallelism": (f"batch sharded over {world} GPUs (no collective)" if W.lps is not None
-                                   else f"replicas x{world}") if world > 1 else "1 GPU"},
+                   "parallelism": (f"batch sharded over {world} GPUs (no collective; each rank one IPM iteration of "
+                                   f"its {BATCH_PER_GPU} instances per step)" if W.lps is not None else
+                                   f"{world} replicas (each GPU its own LP; value = the slowest rank's ms per "
+                                   f"iteration)") if world > 1 else "1 GPU"},
+        "front_gflops": fl / (per[base]["factorise_kernel_ms_per_iter"] * 1e-3) / 1e9
+        if per[base]["factorise_kernel_ms_per_iter"] > 0 else None,
         "paths": per,
         "roofline": rl,
-        "gpu_launches": int(launches),
-        "clocks": r["clocks"],
-        "e2e": {"value": float(np.median(r["e2e_ms"])), "unit": "ms",
+        "phases": phase_bound(r["kstats"], base, peaks, fp64_peak, r["prof_steps"], float(np.mean(r["step_ms"]))),
+        "critical_path": critical_path(r["symbolic"], r["kstats"]),
+        "fp64_peak": fp64_peak,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": {"value": per[base]["e2e_ms_per_iter"], "unit": "ms",
                 "h2d_bytes_per_step": int(r["h2d"]), "d2h_bytes_per_step": int(r["d2h"])},
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if world > 1:
+        out["throughput_iters_per_s"] = world * 1e3 / ms_max
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and W.lps is None:
         v, sample = cpu_baseline(W, pkg)
         out["cpu_baseline"] = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
 
 
 def run_reference(args, rank, world):
-    """The oracle (plain C, one host core) timed on this arm's workload."""
+    """The oracle (plain C, one host core) timed on this arm's workload (a
+    bounded sample per step, scaled to one full IPM iteration)."""
     if rank != 0:
-        return
+        return 0
     import paper_2508_04370_gb300 as pkg
 
     W = Workload(args.workload, 0, 1)
-    probs = oracle_problems(W, pkg)
-    budget = 20.0  # seconds of oracle work per timed step at most (batches: a sample of the instances)
-
-    def step(i):
-        end = time.perf_counter() + budget if len(probs) > 1 else None
-        ms, frac = oracle_iteration(probs, i, W.fp64_target, end)
-        return ms / frac
-
+    if W.lps is not None:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the single-LP workloads"}))
+        return 0
+    arm = OracleArm(W, pkg)
     for i in range(args.warmup):
-        step(i)
-    times = [step(i) for i in range(args.steps)]
+        arm.step(i, args.warmup)
+    times = [arm.step(i, args.steps) for i in range(args.steps)]
     v = float(np.mean(times))
-    if len(probs) > 1:
-        sample = ("each step: instances of the batch in order until 20 s, time scaled by their share of the "
-                  "nnz(A) sqrt(m) work estimate")
-    else:
-        sample = f"{args.steps} full IPM iterations (factorise + 2 refined solves)"
-    out = {"impl": "reference", "metric": "factorise+solve ms per IPM iteration (front GFLOP/s alongside), mixed vs "
-           "FP64 at backward error", "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
+    sample = f"each step: {arm.sample}"
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": W.desc, "path": "oracle"},
            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+    return 0
 
 
 if __name__ == "__main__":
-    main()
+    sys.exit(main())

@@ -145,6 +145,7 @@ typedef struct ipm_info {
     double tune_ms;                         /* best factorisation time the autotuner measured; 0 before */
     double amalg_zero_frac;                 /* amalgamation threshold the analysis used */
     int32_t tune_level_ctas_per_sm;         /* CTAs per SM of the level kernel (0 before the first factorisation) */
+    int32_t graph_kernels;                  /* kernel nodes of the graph ipm_graph_capture built (0: none) */
 } ipm_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -371,11 +372,20 @@ int ipm_set_level_ctas(ipm_ctx *ctx, int32_t per_sm);
 int ipm_test_recip_pivot(const double *x_dev, double *rcp_dev, double *quo_dev, int64_t n, void *stream);
 
 /* ------------------------------------------------------------ measurement */
+/* FP64 peaks of `device`, the denominators of the FP64 rooflines (the pivot
+ * blocks, triangular solves and FP64 updates of Sec. 4.4 run on these
+ * units): DFMA chains and mma.sync.m8n8k4.f64 chains over every SM, best of
+ * three timed runs after one untimed (CUDA events), 2 flops per FMA.
+ * Allocates and frees a small device buffer and synchronises the device's
+ * work it starts; takes about a second.  Outputs (host) in TFLOP/s.
+ * Errors: IPM_ERR_INVALID_ARG for a null output, IPM_ERR_CUDA. */
+int ipm_measure_fp64_peak(int32_t device, double *dfma_tflops, double *dmma_tflops);
+
 /* Kernel classes reported by ipm_kernel_stats. */
 #define IPM_K_SMALL_FRONTS 0   /* fused assemble+factorise of fronts f <= 128 (shared memory) */
 #define IPM_K_LARGE_ASSEMBLE 1 /* extend-add into large fronts */
-#define IPM_K_LARGE_PANEL 2    /* pivot block + triangular solve of a 32-column panel; the persistent
-                                  level kernel (all large-front work of a level) is counted here */
+#define IPM_K_LARGE_PANEL 2    /* triangular solve of a 32-column panel; the persistent level kernel
+                                  (all large-front work of a level) is counted here */
 #define IPM_K_LARGE_UPDATE 3   /* trailing (Schur-complement) update, FP64 */
 #define IPM_K_LARGE_UPDATE_TC 4 /* trailing update on tensor cores (IPM_PREC_MIXED or IPM_PREC_SLICED) */
 #define IPM_K_FORWARD 5        /* forward + diagonal solve (one persistent sweep) */
@@ -384,7 +394,9 @@ int ipm_test_recip_pivot(const double *x_dev, double *rcp_dev, double *quo_dev, 
 #define IPM_K_OTHER 8          /* norms, statistics, permutations, vector updates, diagonal-block
                                   inverses for the solves */
 #define IPM_K_SLICE 9          /* IPM_PREC_SLICED: splitting the panel operands into digit slices */
-#define IPM_K_COUNT 10
+#define IPM_K_PIVOT_BLOCK 10   /* pivot blocks of a 32-column step, launched per step (the level kernel's
+                                  are counted in IPM_K_LARGE_PANEL) */
+#define IPM_K_COUNT 11
 
 typedef struct ipm_kernel_stat {
     int64_t launches;  /* launches recorded since the last reset */

@@ -78,7 +78,7 @@ class ipm_info(ct.Structure):
         ("ms_analyse", ct.c_double), ("est_cost_ne", ct.c_double), ("est_cost_as", ct.c_double),
         ("nnz_ne_seen", ct.c_int64), ("precision_fallbacks", ct.c_int32), ("mixed_active", ct.c_int32),
         ("tune_small_threads", ct.c_int32 * 3), ("tune_level_ratio", ct.c_double), ("tune_ms", ct.c_double),
-        ("amalg_zero_frac", ct.c_double), ("tune_level_ctas_per_sm", ct.c_int32),
+        ("amalg_zero_frac", ct.c_double), ("tune_level_ctas_per_sm", ct.c_int32), ("graph_kernels", ct.c_int32),
     ]
 
     def as_dict(self):
@@ -93,7 +93,7 @@ class ipm_kernel_stat(ct.Structure):
 
 
 KERNEL_CLASSES = ["small_fronts", "large_assemble", "large_panel", "large_update", "large_update_tc", "forward",
-                  "backward", "residual", "other", "slice"]
+                  "backward", "residual", "other", "slice", "pivot_block"]
 
 _lib = None
 
@@ -133,12 +133,14 @@ def _load():
     lib.ipm_launch_counts.argtypes = [P, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]
     lib.ipm_solve_noalloc.argtypes = [P, P, P, P, P, P]
     lib.ipm_test_recip_pivot.argtypes = [P, P, P, ct.c_int64, P]
+    lib.ipm_measure_fp64_peak.argtypes = [ct.c_int32, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
     lib.ipm_set_profiling.argtypes = [P, ct.c_int32]
     lib.ipm_kernel_stats.argtypes = [P, P, ct.c_int32]
     for name in ("ipm_create", "ipm_destroy", "ipm_analyse", "ipm_analyse_batch", "ipm_set_values", "ipm_factorise",
                  "ipm_solve", "ipm_iterate_host", "ipm_sync_status", "ipm_get_info", "ipm_get_symbolic",
                  "ipm_get_sizes", "ipm_get_factor", "ipm_graph_capture", "ipm_graph_launch", "ipm_launch_counts",
-                 "ipm_set_profiling", "ipm_kernel_stats", "ipm_solve_noalloc", "ipm_test_recip_pivot"):
+                 "ipm_set_profiling", "ipm_kernel_stats", "ipm_solve_noalloc", "ipm_test_recip_pivot",
+                 "ipm_measure_fp64_peak"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -330,6 +332,15 @@ def ipm_launch_counts(ctx):
 def ipm_test_recip_pivot(x_dev, rcp_dev, quo_dev, stream=None) -> int:
     return _load().ipm_test_recip_pivot(_dptr(x_dev), _dptr(rcp_dev), _dptr(quo_dev), int(x_dev.numel()),
                                         _stream(stream))
+
+
+def ipm_measure_fp64_peak(device=0):
+    """(dfma_tflops, dmma_tflops) measured on `device`."""
+    a, b = ct.c_double(), ct.c_double()
+    rc = _load().ipm_measure_fp64_peak(int(device), ct.byref(a), ct.byref(b))
+    if rc:
+        raise RuntimeError(f"ipm_measure_fp64_peak failed ({rc})")
+    return a.value, b.value
 
 
 def ipm_set_profiling(ctx, enable=True) -> int:

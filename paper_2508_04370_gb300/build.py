@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libipm_mf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "kernels_factor.cu", "kernels_solve.cu", "kernels_tc.cu", "kernels_sliced.cu", "kernels_ne.cu", "kernels_krylov.cu",
+SOURCES = ["capi.cu", "kernels_factor.cu", "kernels_solve.cu", "kernels_tc.cu", "kernels_sliced.cu", "kernels_peak.cu", "kernels_ne.cu", "kernels_krylov.cu",
            "analyse.cpp", "ordering.cpp", "analysis_io.cpp"]
 
 

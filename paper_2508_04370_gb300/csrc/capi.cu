@@ -153,6 +153,7 @@ struct ipm_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     bool graph_solved = false;  // the last solve ran inside a graph (info comes from the device)
+    int32_t graph_kernels = 0;  // kernel nodes of the captured graph
     cudaStream_t cap_stream = nullptr;  // private stream used only for capturing
     cudaStream_t side = nullptr;        // large fronts of a level run here, beside the small fronts
     cudaStream_t side2 = nullptr;       // trailing updates beside the next panel (lookahead)
@@ -1188,7 +1189,7 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         cudaEvent_t prev_rest = nullptr;
         for (const StepWork &S : W.steps) {
             {
-                Prof pr(c, IPM_K_LARGE_PANEL, S.panel_w, sd);
+                Prof pr(c, IPM_K_PIVOT_BLOCK, S.panel_w, sd);
                 launch_panel_diag(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->panel_items + S.panel_off,
                                   S.panel_cnt, S.p0, c->opt.nb, c->panel_ws, sd);
             }
@@ -2009,6 +2010,7 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
     }
     out->tune_level_ratio = c->tune_ratio;
     out->tune_level_ctas_per_sm = c->dev_ready ? level_grid(c) / c->sms : 0;
+    out->graph_kernels = c->graph_kernels;
     out->tune_ms = c->tune_ms;
     out->omega = c->omega;
     for (int i = 0; i < 16; i++) out->omega_hist[i] = c->omega_hist[i];
@@ -2147,7 +2149,24 @@ int ipm_graph_capture(ipm_ctx *c, const double *theta_dev, double rho, double de
         if (g) cudaGraphDestroy(g);
         return rc ? rc : to_err(e);
     }
-    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    {
+        // kernel nodes of the graph (one launch each per replay)
+        size_t nn = 0;
+        c->graph_kernels = 0;
+        if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+                for (size_t q = 0; q < nn; q++) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nodes[q], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+                        c->graph_kernels++;
+                }
+        }
+        cudaGetLastError();
+    }
+    // keep the priorities the kernels were captured with (the critical
+    // stream's), instead of the priority of the stream the graph is launched on
+    e = cudaGraphInstantiate(&c->graph_exec, g, cudaGraphInstantiateFlagUseNodePriority);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaGraphDestroy(g);
@@ -2176,6 +2195,27 @@ int ipm_launch_counts(const ipm_ctx *c, int32_t *nf, int32_t *ns) {
     return IPM_OK;
 }
 
+
+int ipm_measure_fp64_peak(int32_t device, double *dfma_tflops, double *dmma_tflops) {
+    if (!dfma_tflops || !dmma_tflops) return IPM_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return to_err(e);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int blocks = std::max(sms, 1) * 8;
+    double *buf = nullptr;
+    if ((e = cudaMalloc(&buf, (size_t)blocks * 256 * sizeof(double))) != cudaSuccess) return to_err(e);
+    cudaStream_t st = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) {
+        cudaFree(buf);
+        return to_err(e);
+    }
+    const int rc = measure_fp64_peaks(buf, blocks, 20000, 3, st, dfma_tflops, dmma_tflops);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    cudaFree(buf);
+    return rc ? IPM_ERR_CUDA : to_err(cudaGetLastError());
+}
 
 int ipm_test_recip_pivot(const double *x, double *rcp, double *quo, int64_t n, void *stream) {
     if (n < 0 || (n > 0 && (!x || !rcp || !quo))) return IPM_ERR_INVALID_ARG;

@@ -254,6 +254,8 @@ void launch_slice_panel(const DevPlan &P, const double *fronts, const double *D,
                         cudaStream_t st);
 void launch_update_sliced(const DevPlan &P, double *fronts, const SlicedTile *items, int32_t count,
                           const uint8_t *ws, const int32_t *ws_exp, DevCtl *ctl, cudaStream_t st);
+int measure_fp64_peaks(double *out, int blocks, int iters, int reps, cudaStream_t st, double *dfma_tflops,
+                       double *dmma_tflops);
 void launch_test_recip(const double *x, double *rcp, double *quo, int64_t n, cudaStream_t st);
 void launch_factor_stats(const double *D, const double *dyn, int N, double large_reg, DevCtl *ctl, cudaStream_t st);
 // solves and refinement (kernels_solve.cu)
