@@ -328,3 +328,17 @@ def test_amalgamation_threshold_chosen_by_model(lib):
             o = Oracle.from_lp(lp, form=FORM_AS)
             s = o.analyse(syms[-1.0]["perm"], amalg_zero_frac=syms[-1.0]["amalg_zero_frac"])
             assert np.array_equal(s["sn_start"], syms[-1.0]["snode_ptr"])
+
+
+def test_corrector_count_rule():
+    """Sec. 4.7: (1 + k)(1 + f/2) solves should take about one factorisation;
+    k is lifted to 1 and capped."""
+    from paper_2508_04370_gb300.ipm import corrector_count
+
+    # T_f = 10 solves, f = 2: (1 + k) 2 = 10 -> k = 4
+    assert corrector_count(10.0, 1.0, 2, 6) == 4
+    # f = 0: 1 + k = 10 -> k = 9, capped at 6
+    assert corrector_count(10.0, 1.0, 0, 6) == 6
+    # a factorisation cheaper than two solves: still one corrector
+    assert corrector_count(1.0, 1.0, 1, 6) == 1
+    assert corrector_count(1.0, 0.0, 1, 6) == 1
