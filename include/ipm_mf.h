@@ -275,9 +275,12 @@ int ipm_get_factor(ipm_ctx *ctx, double *L_host, double *D_host, double *dynreg_
  * calls ipm_graph_launch.  Inside the graph the refinement decisions are
  * taken on the device: refine_max steps are captured and the kernels of a
  * step exit at entry once omega <= omega_target, omega failed to halve or
- * the step limit is reached.  A mixed-precision factorisation that cannot be
- * refined to the target sets IPM_WARN_REFINE_NOT_CONVERGED (no fallback
- * inside a graph).  Call after ipm_set_values.  The capture runs on a
+ * the step limit is reached.  When classical refinement ends above the
+ * target, GMRES refinement (gmres_restarts cycles of GMRES(8), as in
+ * ipm_solve) follows inside the graph as a conditional node that the device
+ * enables only then; its kernels return at entry once it is done.  A 3xTF32
+ * factorisation that cannot be refined to the target sets
+ * IPM_WARN_REFINE_NOT_CONVERGED (no FP64 fallback inside a graph).  Call after ipm_set_values.  The capture runs on a
  * stream private to the context (`stream` is unused and may be NULL); the
  * graph can then be launched on any stream. */
 int ipm_graph_capture(ipm_ctx *ctx, const double *theta_dev, double rho, double delta, const double *r7_dev,

@@ -144,6 +144,8 @@ struct ipm_ctx {
     int32_t gmres_iters = 0;  // GMRES iterations of the last solve
     double *gm_V = nullptr, *gm_Z = nullptr, *gm_zero = nullptr, *gm_w = nullptr, *gm_part = nullptr,
            *gm_h = nullptr;
+    GmDev *gm_dev = nullptr;            // device-side GMRES state of captured graphs
+    cudaStream_t gm_stream = nullptr;   // captures the conditional GMRES body of a graph
     double omega = 0.0;      // reported backward error (on K)
     double omega_sys = 0.0;  // backward error of the refined system (K, or M for the normal equations)
     double omega_hist[16] = {0};
@@ -446,8 +448,13 @@ void free_device(ipm_ctx *c) {
     c->dep_ev.clear();
     for (cudaEvent_t e : c->step_ev) cudaEventDestroy(e);
     c->step_ev.clear();
+    if (c->gm_stream) cudaStreamDestroy(c->gm_stream);
+    c->gm_stream = nullptr;
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    // buffers allocated on first use live in allocs too
+    c->gm_V = c->gm_Z = c->gm_zero = c->gm_w = c->gm_part = c->gm_h = nullptr;
+    c->gm_dev = nullptr;
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
     c->ev_used = 0;
@@ -1315,6 +1322,93 @@ int solve_inplace(ipm_ctx *c, double *x, cudaStream_t st, int *nl) {
     return to_err(cudaGetLastError());
 }
 
+// The GMRES refinement of a captured graph: a conditional node whose body
+// (captured on a second stream) runs only when classical refinement ended
+// above the target; inside it every kernel tests the device-side flags of
+// GmDev, so cycles and Arnoldi steps that are not needed return at entry.
+int capture_gmres(ipm_ctx *c, const DevVals &V, cudaStream_t st) {
+    const Plan &P = c->plan;
+    const int64_t N = P.N;
+    const int m = kGmresM;
+    const double target = c->opt.omega_target;
+    const int R = c->opt.gmres_restarts;
+    GmDev *gm = c->gm_dev;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusActive) return IPM_ERR_CUDA;
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, 0)) != cudaSuccess) return to_err(e);
+    launch_gm_begin(c->ctl, gm, target, (unsigned long long)h, st);
+    if ((e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd)) != cudaSuccess) return to_err(e);
+    cudaGraphNodeParams prm{};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeIf;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, ed, nd, &prm)) != cudaSuccess) return to_err(e);
+    cudaGraph_t body = prm.conditional.phGraph_out[0];
+    if ((e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+        return to_err(e);
+    if (!c->gm_stream && (e = cudaStreamCreateWithFlags(&c->gm_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        c->gm_stream = nullptr;
+        return to_err(e);
+    }
+    cudaStream_t s2 = c->gm_stream;
+    if ((e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+        cudaSuccess)
+        return to_err(e);
+    launch_copy_if(c->vx, c->vbest, (int32_t)N, nullptr, 0, s2);
+    for (int r = 0; r <= R; r++) {
+        // r = f - K x and omega of the current x; keep it if it improved
+        launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, s2, &gm->stop);
+        launch_gm_cycle(c->ctl, gm, target, r, R, s2);
+        launch_copy_if(c->vbest, c->vx, (int32_t)N, &gm->improved, 0, s2);
+        if (r == R) break;
+        launch_dots(c->vr, c->vr, N, 1, c->gm_part, gm->h, s2, &gm->stop);
+        launch_gm_init(c->ctl, gm, target, s2);
+        launch_scale_dev(c->gm_V, c->vr, gm, NAN, N, &gm->stop, s2);
+        for (int j = 0; j < m; j++) {
+            double *vj = c->gm_V + (int64_t)j * N, *zj = c->gm_Z + (int64_t)j * N, *vn = vj + N;
+            launch_copy_if(zj, vj, (int32_t)N, &gm->skip_inner, 1, s2);
+            launch_forward_persistent(c->sched, c->fronts, c->Dinv, zj, c->upd, c->solve_maxf, c->solve_grid, c->ctl,
+                                      s2, &gm->skip_inner);
+            launch_backward_persistent(c->sched, c->fronts, zj, c->solve_maxf, c->solve_grid, c->ctl, s2,
+                                       &gm->skip_inner);
+            launch_residual_omega(c->dp, V, c->gm_zero, zj, c->gm_w, c->vad, c->vae, c->ctl, s2, &gm->skip_inner);
+            launch_scale_dev(vn, c->gm_w, gm, -1.0, N, &gm->skip_inner, s2);  // K z
+            for (int pass = 0; pass < 2; pass++) {
+                launch_dots(vn, c->gm_V, N, j + 1, c->gm_part, gm->h, s2, &gm->skip_inner);
+                launch_gs_update_dev(vn, c->gm_V, gm, N, j + 1, s2);
+                launch_gm_hacc(gm, j, s2);
+            }
+            launch_dots(vn, vn, N, 1, c->gm_part, gm->h, s2, &gm->skip_inner);
+            launch_gm_arnoldi(gm, j, s2);
+            launch_scale_dev(vn, vn, gm, NAN, N, &gm->skip_inner, s2);
+        }
+        launch_gm_ls(gm, s2);
+        launch_combine_dev(c->vx, c->gm_Z, gm, N, s2);
+    }
+    launch_gm_end(c->ctl, gm, s2);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e1 = cudaGetLastError();
+    e = cudaStreamEndCapture(s2, &out);
+    if (e1 != cudaSuccess) return to_err(e1);
+    return to_err(e);
+}
+
+
+// GMRES refines an FP64-accurate factor (FP64 or sliced updates); a stalled
+// 3xTF32 factor is replaced by an FP64 one instead
+bool gmres_allowed(const ipm_ctx *c) {
+    return c->opt.gmres_restarts > 0 && !(c->opt.precision == IPM_PREC_MIXED && c->mixed_active);
+}
+
 // Refined solve with all decisions taken on the device, so it can be
 // captured into a CUDA graph: refine_max steps are enqueued and every kernel
 // of a step exits at entry once the control block says the refinement is
@@ -1349,6 +1443,10 @@ int solve_device_driven(ipm_ctx *c, const double *r7, const double *r1, double *
         launch_residual_omega(c->dp, V, c->vf, c->vx, c->vr, c->vad, c->vae, c->ctl, st, done);
         launch_refine_step(c->ctl, target, step, rmax, st);
         launch_copy_if(c->vbest, c->vx, N, improved, 0, st);
+    }
+    if (c->gm_dev && gmres_allowed(c)) {
+        int rc = capture_gmres(c, V, st);
+        if (rc) return rc;
     }
     launch_refine_finish(c->ctl, target, st);
     launch_permute_out(c->dp, c->vbest, dx, dy, st);
@@ -1739,18 +1837,31 @@ int ipm_set_launch_shapes(ipm_ctx *c, const int32_t *small_threads, double level
 // Starts from c->vbest (omega wbest); returns the improved wbest.
 constexpr int kGmresRestart = 8;
 
+static_assert(kGmresRestart == kGmresM, "host and device restart lengths differ");
+
+// Work space of the GMRES refinement (allocated on first use; before any
+// stream capture for the graph-resident version).
+static int gmres_alloc(ipm_ctx *c, cudaStream_t st) {
+    if (c->gm_V) return IPM_OK;
+    const int64_t N = c->plan.N;
+    const int m = kGmresRestart;
+    int rc;
+    if ((rc = dalloc(c, &c->gm_V, (size_t)(m + 1) * N)) || (rc = dalloc(c, &c->gm_Z, (size_t)m * N)) ||
+        (rc = dalloc(c, &c->gm_zero, (size_t)N)) || (rc = dalloc(c, &c->gm_w, (size_t)N)) ||
+        (rc = dalloc(c, &c->gm_part, (size_t)dots_partial_size())) || (rc = dalloc(c, &c->gm_h, kMaxDots)) ||
+        (rc = dalloc(c, &c->gm_dev, 1)))
+        return rc;
+    cudaMemsetAsync(c->gm_zero, 0, sizeof(double) * N, st);
+    cudaMemsetAsync(c->gm_dev, 0, sizeof(GmDev), st);
+    return to_err(cudaGetLastError());
+}
+
 static int gmres_refine(ipm_ctx *c, const DevVals &V, cudaStream_t st, double &wbest, int *nl) {
     const Plan &P = c->plan;
     const int64_t N = P.N;
     const int m = kGmresRestart;
     int rc;
-    if (!c->gm_V) {
-        if ((rc = dalloc(c, &c->gm_V, (size_t)(m + 1) * N)) || (rc = dalloc(c, &c->gm_Z, (size_t)m * N)) ||
-            (rc = dalloc(c, &c->gm_zero, (size_t)N)) || (rc = dalloc(c, &c->gm_w, (size_t)N)) ||
-            (rc = dalloc(c, &c->gm_part, (size_t)dots_partial_size())) || (rc = dalloc(c, &c->gm_h, kMaxDots)))
-            return rc;
-        cudaMemsetAsync(c->gm_zero, 0, sizeof(double) * N, st);
-    }
+    if ((rc = gmres_alloc(c, st))) return rc;
     const double target = c->opt.omega_target;
     double hbuf[kMaxDots];
     auto read_h = [&](int cnt) -> int {
@@ -1890,7 +2001,7 @@ static int solve_once(ipm_ctx *c, const double *r7, const double *r1, double *dx
     // refinement stalls is replaced by an FP64 one instead (ipm_solve), which
     // later iterations keep, rather than paying GMRES iterations every solve
     c->gmres_iters = 0;
-    if (wbest > target && c->opt.gmres_restarts > 0 && !c->mixed_active && !(h.status & kStatNonFinite)) {
+    if (wbest > target && gmres_allowed(c) && !(h.status & kStatNonFinite)) {
         if ((rc = gmres_refine(c, V, st, wbest, &nl))) return rc;
         steps += c->gmres_iters;
     }
@@ -2025,8 +2136,8 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
         if (e != cudaSuccess) return to_err(e);
         c->status_acc |= h.status;
         if (c->graph_solved) {
-            out->refine_steps = h.steps;
-            out->gmres_iters = 0;
+            out->refine_steps = h.steps + h.gmres_iters;
+            out->gmres_iters = h.gmres_iters;
             out->omega = h.omega_best;
             for (int i = 0; i < 16; i++) out->omega_hist[i] = i <= h.steps ? h.omega_hist[i] : 0.0;
         }
@@ -2125,6 +2236,12 @@ int ipm_graph_capture(ipm_ctx *c, const double *theta_dev, double rho, double de
         }
     }
     cudaStream_t st = c->cap_stream;
+    if (nsolves > 0 && gmres_allowed(c)) {
+        // the graph-resident GMRES refinement needs its work space before the capture
+        if ((rc = gmres_alloc(c, st))) return rc;
+        cudaError_t e0 = cudaStreamSynchronize(st);
+        if (e0 != cudaSuccess) return to_err(e0);
+    }
     const bool prof = c->prof_on;
     c->prof_on = false;
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);

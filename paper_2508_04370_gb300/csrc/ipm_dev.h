@@ -51,6 +51,7 @@ struct DevCtl {
     int32_t steps;
     int32_t improved;      // the last step improved omega_best
     double omega_hist[16];
+    int32_t gmres_iters;   // GMRES iterations of a graph-resident refinement
 };
 
 // Read-only plan arrays on the device (all indices in factorisation order).
@@ -272,11 +273,38 @@ void launch_backward_persistent(const SolveSched &S, const double *fronts, doubl
                                 DevCtl *ctl, cudaStream_t st, const int32_t *skip = nullptr);
 // GMRES refinement vectors (kernels_krylov.cu)
 constexpr int kMaxDots = 16;  // vectors per dot-product launch (restart length + 1 at most)
+constexpr int kGmresM = 8;    // GMRES restart length
+
+// Device-side state of the GMRES refinement inside a captured graph: the
+// Hessenberg matrix and its Givens rotations, and the flags the kernels of the
+// section test at entry.
+struct GmDev {
+    double H[(kGmresM + 1) * kGmresM];  // H(i, j) at i * kGmresM + j
+    double cs[kGmresM], sn[kGmresM], g[kGmresM + 1], y[kGmresM];
+    double h[kMaxDots];                 // output of the dot products
+    double beta, inv, eta, wbest;
+    int32_t stop;        // GMRES finished: every kernel of the section returns at entry
+    int32_t skip_inner;  // stop, or the current cycle has converged
+    int32_t improved;    // the last cycle improved the best iterate
+    int32_t jdone, iters;
+};
 struct GmresCoef {
     double c[kMaxDots];
 };
 void launch_dots(const double *w, const double *V, int64_t N, int32_t cnt, double *part, double *out,
-                 cudaStream_t st);
+                 cudaStream_t st, const int32_t *skip = nullptr);
+// graph-resident GMRES (control kernels and device-parameter vector kernels)
+void launch_gm_begin(DevCtl *ctl, GmDev *gm, double target, unsigned long long cond_handle, cudaStream_t st);
+void launch_gm_cycle(DevCtl *ctl, GmDev *gm, double target, int32_t cycle, int32_t last, cudaStream_t st);
+void launch_gm_init(DevCtl *ctl, GmDev *gm, double target, cudaStream_t st);
+void launch_gm_hacc(GmDev *gm, int32_t j, cudaStream_t st);
+void launch_gm_arnoldi(GmDev *gm, int32_t j, cudaStream_t st);
+void launch_gm_ls(GmDev *gm, cudaStream_t st);
+void launch_gm_end(DevCtl *ctl, GmDev *gm, cudaStream_t st);
+void launch_gs_update_dev(double *w, const double *V, const GmDev *gm, int64_t N, int32_t cnt, cudaStream_t st);
+void launch_scale_dev(double *dst, const double *src, const GmDev *gm, double factor, int64_t N,
+                      const int32_t *skip, cudaStream_t st);
+void launch_combine_dev(double *x, const double *Z, const GmDev *gm, int64_t N, cudaStream_t st);
 void launch_gs_update(double *w, const double *V, const double *h, int64_t N, int32_t cnt, cudaStream_t st);
 void launch_scale(double *dst, const double *src, double alpha, int64_t N, cudaStream_t st);
 void launch_combine(double *x, const double *Z, const GmresCoef &y, int64_t N, int32_t cnt, cudaStream_t st);

@@ -801,6 +801,7 @@ __global__ void k_refine_init(DevCtl *ctl, double target, int max_steps) {
     ctl->omega_best = w;
     ctl->omega_hist[0] = w;
     ctl->steps = 0;
+    ctl->gmres_iters = 0;
     ctl->improved = 1;
     ctl->done = (w <= target || max_steps <= 0) ? 1 : 0;
 }

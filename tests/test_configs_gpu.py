@@ -205,3 +205,46 @@ def test_block_angular_forms_against_oracle(pkg):
     print(f"block-angular chooser: form {s.info()['form']} cost AS {info['est_cost_as']:.3e} "
           f"NE {info['est_cost_ne']:.3e}")
     s.close()
+
+
+def test_staircase_schedule_end_gmres_inside_graph(pkg):
+    """The same stalled system through a captured CUDA graph: classical
+    refinement ends above 1e-12, so the conditional GMRES section of the graph
+    runs (its condition is set on the device) and the backward error on K
+    reaches 1e-12; the solution agrees with the direct path's GMRES result,
+    and a replay on a system that needs no GMRES skips the section."""
+    import torch
+
+    lp = small_staircase()
+    sched = synth.theta_schedule(lp.n, 40, 3)
+    th = sched[39]
+    r7, r1 = synth.rhs_normal(lp.n, 39), synth.rhs_normal(lp.m, 40)
+    s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_AMD)
+    s.factorise(th, RHO, DELTA)
+    ex, ey = s.solve(r7, r1)
+    direct = np.concatenate([ex.cpu().numpy(), ey.cpu().numpy()])
+    assert s.info()["gmres_iters"] > 0
+    dev = s.dev
+    theta = torch.as_tensor(th, device=dev)
+    r7d, r1d = torch.as_tensor(r7, device=dev), torch.as_tensor(r1, device=dev)
+    dx = torch.zeros(lp.n, dtype=torch.float64, device=dev)
+    dy = torch.zeros(lp.m, dtype=torch.float64, device=dev)
+    assert pkg.ipm_graph_capture(s.ctx, theta, RHO, DELTA, r7d, r1d, dx, dy, nsolves=1) == 0
+    assert pkg.ipm_graph_launch(s.ctx) == 0
+    torch.cuda.synchronize()
+    info = s.info()
+    x = np.concatenate([dx.cpu().numpy(), dy.cpu().numpy()])
+    w = Oracle.from_lp(lp).omega_K(th, RHO, DELTA, r7, r1, x[: lp.n], x[lp.n:])
+    assert info["gmres_iters"] > 0 and w <= 1e-12, (info["gmres_iters"], w)
+    assert info["omega"] == pytest.approx(w, rel=1e-6, abs=1e-300)
+    assert np.abs(x - direct).max() <= 1e-8 * np.abs(direct).max()
+    # an early schedule point: classical refinement suffices, the section is skipped
+    theta.copy_(torch.as_tensor(sched[5], device=dev))
+    assert pkg.ipm_graph_launch(s.ctx) == 0
+    torch.cuda.synchronize()
+    info = s.info()
+    x = np.concatenate([dx.cpu().numpy(), dy.cpu().numpy()])
+    w = Oracle.from_lp(lp).omega_K(sched[5], RHO, DELTA, r7, r1, x[: lp.n], x[lp.n:])
+    assert info["gmres_iters"] == 0 and w <= 1e-12
+    print(f"graph GMRES: {info['refine_steps']} steps at iteration 5; stalled case reached {w:.2e}")
+    s.close()
