@@ -104,6 +104,12 @@ typedef struct orc {
     double *theta_t; /* NE: Theta~ = 1/(1/theta + rho) */
     double rho, delta, eps_piv, normM1;
     int nb;
+    /* pivoting of Sec. 4.5 (Bunch-Kaufman variation, 1x1 and 2x2 pivots) per
+       front instead of the 1x1 pivots with the Prop. 3 bound */
+    int bk;
+    int32_t *lperm;  /* per position c0 + t of a supernode: the local index moved to t */
+    double *Doff;    /* D(p+1, p) of a 2x2 block starting at p, else 0 */
+    int32_t *bsize;  /* 1 or 2 at a block's first position, 0 at the second */
     int ndyn, npos, nneg;
     int status;
     /* refinement record */
@@ -135,6 +141,8 @@ static void free_symbolic(orc *o) {
     free(o->Lsp); free(o->Lsi); free(o->sn_start); free(o->sn_parent);
     free(o->sn_rptr); free(o->sn_rows); free(o->sn_lptr); free(o->Lval);
     free(o->D); free(o->dynreg);
+    free(o->lperm); free(o->Doff); free(o->bsize);
+    o->lperm = NULL; o->Doff = NULL; o->bsize = NULL;
     o->perm = o->iperm = o->parent = NULL; o->colcount = NULL;
     o->Lsp = NULL; o->Lsi = NULL; o->sn_start = o->sn_parent = NULL;
     o->sn_rptr = NULL; o->sn_rows = NULL; o->sn_lptr = NULL; o->Lval = NULL;
@@ -534,6 +542,9 @@ int orc_analyse(orc *o, const int32_t *perm_in, int nb, int amalg_width, double 
     o->Lval = (double *)xcalloc((size_t)o->sn_lptr[o->nsuper], sizeof(double));
     o->D = (double *)xcalloc(N ? N : 1, sizeof(double));
     o->dynreg = (double *)xcalloc(N ? N : 1, sizeof(double));
+    o->lperm = (int32_t *)xcalloc(N ? N : 1, sizeof(int32_t));
+    o->Doff = (double *)xcalloc(N ? N : 1, sizeof(double));
+    o->bsize = (int32_t *)xcalloc(N ? N : 1, sizeof(int32_t));
     return ORC_OK;
 }
 
@@ -706,6 +717,19 @@ int orc_front_factor(int f, int k, int nb, double *F, const int *sgn, const doub
 
 /* ------------------------------------------------------ multifrontal */
 
+int orc_front_ldlt_bk(int n, int k, int nb, double *A, double b1, double alpha, int32_t *perm, double *D,
+                      double *Doff, int32_t *bsize, double *lift);
+
+/* Select the pivoting of a front: 0 = 1x1 pivots with static and dynamic
+ * regularisation (Sec. 4.4-4.5, Prop. 3); 1 = the Bunch-Kaufman variation of
+ * Sec. 4.5 (1x1 and 2x2 pivots chosen within each pivot block, pre-swap,
+ * lifting) through orc_front_ldlt_bk, for matrices that are not
+ * quasi-definite.  Reading: the static terms s_p sigma_p enter the diagonal
+ * of the fully-summed columns before the front is factorised (the matrix
+ * factorised is K with rho and delta, as in mode 0); the interchanges stay
+ * among the fully-summed columns, so the symbolic structure is unchanged. */
+void orc_set_pivoting(orc *o, int bk) { o->bk = bk ? 1 : 0; }
+
 int orc_factorise(orc *o, const double *theta, double rho, double delta, double eps_piv) {
     if (!o->sn_start) return ORC_ERR_ARG;
     o->rho = rho; o->delta = delta; o->eps_piv = eps_piv;
@@ -760,7 +784,30 @@ int orc_factorise(orc *o, const double *theta, double rho, double delta, double 
             sg[t] = sign_of(o, o->perm[R[t]]);
             sr[t] = static_of(o, o->perm[R[t]]);
         }
-        int frc = orc_front_factor(f, k, o->nb, F, sg, sr, b1, o->D + c0, o->dynreg + c0);
+        int frc;
+        if (!o->bk) {
+            frc = orc_front_factor(f, k, o->nb, F, sg, sr, b1, o->D + c0, o->dynreg + c0);
+        } else {
+            /* static terms on the fully-summed diagonal, both triangles for the
+               symmetric interchanges, then the pivoted partial factorisation */
+            for (int t = 0; t < k; t++) F[(int64_t)t * f + t] += sg[t] * sr[t];
+            for (int j = 0; j < f; j++)
+                for (int i = j + 1; i < f; i++) F[(int64_t)i * f + j] = F[(int64_t)j * f + i];
+            int32_t *lp = (int32_t *)xmalloc(sizeof(int32_t) * NZ(f));
+            double *Df = (double *)xmalloc(sizeof(double) * NZ(f));
+            double *Of = (double *)xmalloc(sizeof(double) * NZ(f));
+            int32_t *Bf = (int32_t *)xmalloc(sizeof(int32_t) * NZ(f));
+            double *lf = (double *)xmalloc(sizeof(double) * NZ(f));
+            frc = orc_front_ldlt_bk(f, k, o->nb, F, b1, 1.0 / 8.0 + sqrt(17.0) / 8.0, lp, Df, Of, Bf, lf);
+            for (int t = 0; t < k; t++) {
+                o->lperm[c0 + t] = lp[t];
+                o->D[c0 + t] = Df[t];
+                o->Doff[c0 + t] = Of[t];
+                o->bsize[c0 + t] = Bf[t];
+                o->dynreg[c0 + t] = lf[t];
+            }
+            free(lp); free(Df); free(Of); free(Bf); free(lf);
+        }
         if (frc && !status) status = frc;
         free(sg); free(sr);
         /* store L and keep the contribution block for the parent */
@@ -781,6 +828,16 @@ int orc_factorise(orc *o, const double *theta, double rho, double delta, double 
     free(cb); free(loc); free(chead); free(cnext); free(bp); free(bi); free(bsrc);
     for (int j = 0; j < N; j++) {
         if (o->dynreg[j] != 0.0) o->ndyn++;
+        if (o->bk && o->bsize[j] == 2) {
+            /* a 2x2 block: one positive and one negative eigenvalue when its
+               determinant is negative, else both of the sign of its trace */
+            const double det = o->D[j] * o->D[j + 1] - o->Doff[j] * o->Doff[j];
+            if (det < 0) { o->npos++; o->nneg++; }
+            else if (det > 0) { if (o->D[j] + o->D[j + 1] > 0) o->npos += 2; else o->nneg += 2; }
+            if (o->dynreg[j + 1] != 0.0) o->ndyn++;
+            j++;
+            continue;
+        }
         if (o->D[j] > 0) o->npos++;
         else if (o->D[j] < 0) o->nneg++;
     }
@@ -793,6 +850,12 @@ void orc_get_factor(const orc *o, double *Lval, double *D, double *dynreg, int64
     if (D) memcpy(D, o->D, sizeof(double) * o->N);
     if (dynreg) memcpy(dynreg, o->dynreg, sizeof(double) * o->N);
     if (sn_lptr) memcpy(sn_lptr, o->sn_lptr, sizeof(int64_t) * (o->nsuper + 1));
+}
+
+void orc_get_pivots(const orc *o, int32_t *lperm, double *Doff, int32_t *bsize) {
+    if (lperm) memcpy(lperm, o->lperm, sizeof(int32_t) * o->N);
+    if (Doff) memcpy(Doff, o->Doff, sizeof(double) * o->N);
+    if (bsize) memcpy(bsize, o->bsize, sizeof(int32_t) * o->N);
 }
 
 void orc_get_stats(const orc *o, int *ndyn, int *npos, int *nneg, double *normM1) {
@@ -810,17 +873,35 @@ static void ldlt_solve(const orc *o, double *x) {
     int N = o->N;
     double *y = (double *)xmalloc(sizeof(double) * NZ(N));
     for (int i = 0; i < N; i++) y[i] = x[o->perm[i]];
+    double *tmp = (double *)xmalloc(sizeof(double) * NZ(N));
     for (int s = 0; s < o->nsuper; s++) {
         int c0 = o->sn_start[s], k = o->sn_start[s + 1] - c0;
         int f = (int)(o->sn_rptr[s + 1] - o->sn_rptr[s]);
         const int32_t *R = o->sn_rows + o->sn_rptr[s];
         const double *L = o->Lval + o->sn_lptr[s];
+        if (o->bk) {
+            /* the front's interchanges: position t holds local index lperm[t] */
+            for (int t = 0; t < k; t++) tmp[t] = y[c0 + o->lperm[c0 + t]];
+            for (int t = 0; t < k; t++) y[c0 + t] = tmp[t];
+        }
         for (int jj = 0; jj < k; jj++) {
             double yj = y[c0 + jj];
             for (int ii = jj + 1; ii < f; ii++) y[R[ii]] -= L[(int64_t)jj * f + ii] * yj;
         }
     }
-    for (int i = 0; i < N; i++) y[i] /= o->D[i];
+    for (int i = 0; i < N; i++) {
+        if (o->bk && o->bsize[i] == 2) {
+            /* 2x2 block of D: the inverse of [e11 e21; e21 e22] */
+            const double e11 = o->D[i], e21 = o->Doff[i], e22 = o->D[i + 1];
+            const double det = e11 * e22 - e21 * e21;
+            const double y0 = y[i], y1 = y[i + 1];
+            y[i] = (e22 * y0 - e21 * y1) / det;
+            y[i + 1] = (e11 * y1 - e21 * y0) / det;
+            i++;
+            continue;
+        }
+        y[i] /= o->D[i];
+    }
     for (int s = o->nsuper - 1; s >= 0; s--) {
         int c0 = o->sn_start[s], k = o->sn_start[s + 1] - c0;
         int f = (int)(o->sn_rptr[s + 1] - o->sn_rptr[s]);
@@ -831,9 +912,14 @@ static void ldlt_solve(const orc *o, double *x) {
             for (int ii = jj + 1; ii < f; ii++) t -= L[(int64_t)jj * f + ii] * y[R[ii]];
             y[c0 + jj] = t;
         }
+        if (o->bk) {
+            for (int t = 0; t < k; t++) tmp[t] = y[c0 + t];
+            for (int t = 0; t < k; t++) y[c0 + o->lperm[c0 + t]] = tmp[t];
+        }
     }
     for (int i = 0; i < N; i++) x[o->perm[i]] = y[i];
     free(y);
+    free(tmp);
 }
 
 /* ---------------------------------------------------- residual, error */

@@ -66,6 +66,8 @@ def _load():
     lib.orc_front_ldlt_bk.restype = ct.c_int
     lib.orc_dense_solve_bk.argtypes = [ct.c_int, f64p, f64p, f64p, i32p, i32p, f64p, f64p]
     lib.orc_dense_solve_bk.restype = ct.c_int
+    lib.orc_set_pivoting.argtypes = [P, ct.c_int]
+    lib.orc_get_pivots.argtypes = [P, i32p, f64p, i32p]
     lib.orc_get_stats.argtypes = [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
                                   ct.POINTER(ct.c_double)]
     lib.orc_solve.argtypes = [P, f64p, f64p, f64p, f64p, f64p, ct.c_double, ct.c_int]
@@ -132,6 +134,22 @@ class Oracle:
         self.lib.orc_get_symbolic(self.h, out["perm"], out["parent"], out["colcount"], out["sn_start"],
                                   out["sn_parent"], out["sn_rptr"], out["sn_rows"])
         return out
+
+    def set_pivoting(self, bk):
+        """True: factorise every front with the Bunch-Kaufman variation of
+        Sec. 4.5 (1x1 and 2x2 pivots, interchanges among its fully-summed
+        columns); False: 1x1 pivots with the Prop. 3 bound."""
+        self.lib.orc_set_pivoting(self.h, 1 if bk else 0)
+
+    def pivots(self):
+        """Per factorisation position: the local index the front moved there
+        (lperm), D(p+1, p) of a 2x2 block starting at p (Doff) and the block
+        size at a block's first position (bsize: 1, 2, or 0 at a 2x2 block's
+        second position)."""
+        N = self.N
+        lp, do, bs = np.empty(N, np.int32), np.empty(N, np.float64), np.empty(N, np.int32)
+        self.lib.orc_get_pivots(self.h, lp, do, bs)
+        return dict(lperm=lp, Doff=do, bsize=bs)
 
     def factorise(self, theta, rho, delta, eps_piv=2.220446049250313e-16):
         rc = self.lib.orc_factorise(self.h, _c(theta, np.float64), float(rho), float(delta), float(eps_piv))

@@ -725,3 +725,114 @@ def test_chooser_abandons_dense_normal_equations():
     form, cas, cne, nne = choose_form(lp, perm, np.arange(m, dtype=np.int32))
     assert nne == m * (m + 1) // 2
     assert form == FORM_AS and cne == -1.0 and cas > 0
+
+
+# ---------------------------------------- multifrontal Bunch-Kaufman (Sec. 4.5)
+
+def _bk_dense_factor(o, sym):
+    """The multifrontal BK factor as dense matrices in the final order (the
+    factorisation order composed with every front's interchanges): returns
+    (q, L, Dblk) with K[perm][:, perm][q][:, q] + diag(lift) = L Dblk L^T."""
+    N = o.N
+    fac = o.factor()
+    pv = o.pivots()
+    q = np.arange(N)
+    for s in range(len(sym["sn_parent"])):
+        c0, c1 = sym["sn_start"][s], sym["sn_start"][s + 1]
+        q[c0:c1] = c0 + pv["lperm"][c0:c1]
+    qinv = np.empty(N, np.int64)
+    qinv[q] = np.arange(N)
+    L = np.zeros((N, N))
+    for s in range(len(sym["sn_parent"])):
+        c0, c1 = sym["sn_start"][s], sym["sn_start"][s + 1]
+        k = c1 - c0
+        R = sym["sn_rows"][sym["sn_rptr"][s]:sym["sn_rptr"][s + 1]]
+        f = len(R)
+        blk = fac["L"][fac["lptr"][s]:fac["lptr"][s + 1]].reshape(k, f).T
+        rows = np.concatenate([np.arange(c0, c1), qinv[R[k:]]])
+        L[np.ix_(rows, np.arange(c0, c1))] = blk
+    Dblk = np.diag(fac["D"])
+    for p in np.flatnonzero(pv["bsize"] == 2):
+        Dblk[p + 1, p] = Dblk[p, p + 1] = pv["Doff"][p]
+    return q, L, Dblk, fac, pv
+
+
+def _bk_case(seed):
+    """A (m x n): row i has one large entry a_i in its matched column
+    cols[i] and random entries only in the other (unmatched) columns, so the
+    pairs (y_i, x_cols[i]) are independent subtrees; the order is y_0,
+    x_cols[0], y_1, x_cols[1], ..., then the unmatched columns.  Each pair is
+    one front whose pivot block [[0, a_i], [a_i, -1/theta]] needs a 2x2 pivot
+    when 1/theta < alpha |a_i|; eliminating it adds A_ir^T A_ir / (theta a_i^2)
+    to the unmatched columns' block, which stays negative definite."""
+    rng = np.random.default_rng(seed)
+    m, n = 12 + 3 * seed, 30 + 5 * seed
+    cols = rng.permutation(n)[:m]
+    rest = np.setdiff1d(np.arange(n), cols)
+    A = np.zeros((m, n))
+    A[np.arange(m), cols] = rng.standard_normal(m) + 3.0
+    R = rng.standard_normal((m, rest.size)) * (rng.random((m, rest.size)) < 0.25)
+    R[rng.integers(m, size=rest.size), np.arange(rest.size)] += rng.standard_normal(rest.size)
+    A[:, rest] = R
+    perm = np.concatenate([np.ravel(np.column_stack([n + np.arange(m), cols])), rest]).astype(np.int32)
+    return rng, A, perm
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_multifrontal_bk_without_regularisation(seed):
+    """rho = delta = 0: K = [[-Theta^-1, A^T], [A, 0]] is not quasi-definite
+    (zero dual diagonal).  The multifrontal factorisation with the
+    Bunch-Kaufman variation of Sec. 4.5 must reproduce the permuted matrix
+    (dense reconstruction to 1e-13 of the entries' scale), take 2x2 pivots
+    (Theta of 1e2..1e4 makes -1/theta_j small against the off-diagonal a:
+    |M_pp| < alpha gamma_p and |M_rr| = 0), give exactly n negative and m
+    positive eigenvalues (Sylvester: A has full row rank), and solve K x = f
+    like LAPACK."""
+    rng, A, perm = _bk_case(seed)
+    m, n = A.shape
+    theta = 10.0 ** rng.uniform(2, 4, n)
+    o = Oracle(*lp_from_dense(A), form=FORM_AS)
+    # every dual row with its matched column as one 2-column front (no wider
+    # amalgamation): the pivoting of Sec. 4.5 searches only a front's
+    # fully-summed columns, so a front whose own block is singular at
+    # rho = delta = 0 would need a lift (and grow) instead of a delayed pivot
+    sym = o.analyse(perm, amalg_width=2, amalg_zero_frac=0.0)
+    assert np.all(np.diff(sym["sn_start"])[:m] == 2)
+    o.set_pivoting(True)
+    assert o.factorise(theta, 0.0, 0.0) == 0
+    q, L, Dblk, fac, pv = _bk_dense_factor(o, sym)
+    K = K_dense(A, theta, 0.0, 0.0)
+    Kq = K[np.ix_(sym["perm"], sym["perm"])][np.ix_(q, q)] + np.diag(fac["dynreg"])
+    err = np.abs(L @ Dblk @ L.T - Kq).max()
+    assert err <= 1e-13 * np.abs(L).max() ** 2 * np.abs(Dblk).max(), err
+    assert np.count_nonzero(pv["bsize"] == 2) == m and np.all(fac["dynreg"] == 0.0)
+    st = o.stats()
+    assert st["nneg"] == n and st["npos"] == m
+    b = rng.standard_normal(n + m)
+    dx, dy, info = o.solve(b[:n], b[n:], omega_target=1e-14, max_steps=5)
+    ref = np.linalg.solve(K, b)
+    x = np.concatenate([dx, dy])
+    assert np.abs(x - ref).max() <= 1e-9 * np.abs(ref).max()
+    # the same matrix without pivoting needs a lift at every zero pivot
+    o.set_pivoting(False)
+    o.factorise(theta, 0.0, 0.0)
+    assert o.stats()["ndyn"] > 0
+
+
+def test_multifrontal_bk_equals_plain_solution_when_quasi_definite():
+    """With rho, delta > 0 both pivoting modes factorise the same regularised
+    K (possibly with different pivot orders): the refined solutions agree."""
+    rng = np.random.default_rng(7)
+    lp = synth.random_lp(40, 100, 4, seed=7)
+    theta = synth.theta_loguniform(lp.n, 7, -3.0, 3.0)
+    r7, r1 = rng.standard_normal(lp.n), rng.standard_normal(lp.m)
+    out = []
+    for bk in (False, True):
+        o = Oracle.from_lp(lp)
+        o.analyse(None)
+        o.set_pivoting(bk)
+        o.factorise(theta, 1e-6, 1e-6)
+        dx, dy, info = o.solve(r7, r1, omega_target=1e-14, max_steps=10)
+        out.append(np.concatenate([dx, dy]))
+        assert o.stats()["nneg"] == lp.n and o.stats()["npos"] == lp.m
+    assert np.abs(out[0] - out[1]).max() <= 1e-10 * np.abs(out[0]).max()
