@@ -115,6 +115,16 @@ typedef struct ipm_options {
     int32_t level_kernel;     /* FP64 large fronts: 1 = one persistent, dependency-driven launch per tree
                                  level (diagonal blocks, triangular solves and trailing updates of all the
                                  level's large fronts); 0 = one launch per kernel and pivot block; 1 */
+    int32_t pivoting;         /* 0 = 1x1 pivots with static and dynamic regularisation (Sec. 4.4-4.5, Prop. 3),
+                                 for the quasi-definite regularised K; 1 = the Bunch-Kaufman variation of
+                                 Sec. 4.5 for matrices that are not quasi-definite (e.g. rho = delta = 0): 1x1
+                                 and 2x2 pivots chosen inside each 32-column pivot block of a front (pre-swap of
+                                 the largest remaining diagonal, the alpha = (1 + sqrt 17)/8 tests, a pivot below
+                                 eps_piv ||K||_1 lifted to that size with its sign), interchanges only among the
+                                 front's fully-summed columns, no delayed pivots.  One CTA per front (a
+                                 correctness path, not tuned for speed); augmented system and IPM_PREC_FP64
+                                 only; fronts up to 12,800 rows; no ipm_graph_capture or ipm_solve_noalloc
+                                 (IPM_ERR_INVALID_ARG); the factor's blocks come from ipm_get_pivots; 0 */
 } ipm_options;
 
 typedef struct ipm_info {
@@ -264,6 +274,17 @@ int ipm_get_sizes(const ipm_ctx *ctx, int32_t *N, int32_t *nsuper, int64_t *nrow
  * order, unit diagonal stored as 1, entries above it 0); D_host and
  * dynreg_host have N entries in the factorisation order.  Synchronises. */
 int ipm_get_factor(ipm_ctx *ctx, double *L_host, double *D_host, double *dynreg_host);
+
+/* The pivoting mode's factor (opt.pivoting = 1, after a factorisation; host
+ * arrays of N entries in the factorisation order, any may be NULL): lperm[p]
+ * is the local index, within its supernode's fully-summed columns, of the
+ * unknown the front's interchanges moved to position p (the supernode's
+ * columns c0 .. c0+k-1 hold c0 + lperm[c0 .. c0+k-1]; ipm_get_factor's L and D
+ * are in this interchanged order); Doff[p] = D(p+1, p) of a 2x2 block
+ * starting at p, else 0; bsize[p] = 1 or 2 at a block's first position, 0 at
+ * a 2x2 block's second.  Synchronises.  Errors: IPM_ERR_INVALID_ARG without
+ * the pivoting mode, IPM_ERR_NOT_FACTORISED. */
+int ipm_get_pivots(ipm_ctx *ctx, int32_t *lperm_host, double *Doff_host, int32_t *bsize_host);
 
 /* Capture one IPM iteration's linear algebra into one CUDA graph owned by the
  * context (Sec. 4.2: the pattern and the symbolic analysis are reused by

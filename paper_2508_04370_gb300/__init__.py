@@ -62,6 +62,7 @@ class ipm_options(ct.Structure):
         ("spin_limit_log2", ct.c_int32),
         ("verbose", ct.c_int32),
         ("level_kernel", ct.c_int32),
+        ("pivoting", ct.c_int32),
     ]
 
 
@@ -133,6 +134,7 @@ def _load():
     lib.ipm_launch_counts.argtypes = [P, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]
     lib.ipm_solve_noalloc.argtypes = [P, P, P, P, P, P]
     lib.ipm_test_recip_pivot.argtypes = [P, P, P, ct.c_int64, P]
+    lib.ipm_get_pivots.argtypes = [P, P, P, P]
     lib.ipm_measure_fp64_peak.argtypes = [ct.c_int32, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
     lib.ipm_set_profiling.argtypes = [P, ct.c_int32]
     lib.ipm_kernel_stats.argtypes = [P, P, ct.c_int32]
@@ -140,7 +142,7 @@ def _load():
                  "ipm_solve", "ipm_iterate_host", "ipm_sync_status", "ipm_get_info", "ipm_get_symbolic",
                  "ipm_get_sizes", "ipm_get_factor", "ipm_graph_capture", "ipm_graph_launch", "ipm_launch_counts",
                  "ipm_set_profiling", "ipm_kernel_stats", "ipm_solve_noalloc", "ipm_test_recip_pivot",
-                 "ipm_measure_fp64_peak"):
+                 "ipm_measure_fp64_peak", "ipm_get_pivots"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -332,6 +334,16 @@ def ipm_launch_counts(ctx):
 def ipm_test_recip_pivot(x_dev, rcp_dev, quo_dev, stream=None) -> int:
     return _load().ipm_test_recip_pivot(_dptr(x_dev), _dptr(rcp_dev), _dptr(quo_dev), int(x_dev.numel()),
                                         _stream(stream))
+
+
+def ipm_get_pivots(ctx):
+    """(lperm, Doff, bsize) of a factorisation in the pivoting mode."""
+    N = ipm_get_sizes(ctx)[0]
+    lp, do, bs = np.empty(N, np.int32), np.empty(N, np.float64), np.empty(N, np.int32)
+    rc = _load().ipm_get_pivots(ctx, lp.ctypes.data, do.ctypes.data, bs.ctypes.data)
+    if rc:
+        raise RuntimeError(f"ipm_get_pivots failed ({rc})")
+    return dict(lperm=lp, Doff=do, bsize=bs)
 
 
 def ipm_measure_fp64_peak(device=0):

@@ -94,6 +94,9 @@ struct ipm_ctx {
     DevPlan dp{};
     DevCtl *ctl = nullptr;
     double *fronts = nullptr, *D = nullptr, *Dinv = nullptr, *dyn = nullptr;
+    double *Doff = nullptr;      // pivoting mode: D(p+1, p) of 2x2 blocks
+    int32_t *bsz = nullptr;      // pivoting mode: block sizes (1, 2, 0 at a 2x2 block's second position)
+    int32_t *lperm = nullptr;    // pivoting mode: each front's interchanges (local index at each position)
     double *Ax = nullptr;
     double *theta = nullptr;  // owned copy for host entry points
     double *vf = nullptr, *vx = nullptr, *vbest = nullptr, *vr = nullptr, *vad = nullptr, *vae = nullptr,
@@ -1013,6 +1016,9 @@ int setup_device(ipm_ctx *c) {
         (rc = dalloc(c, &c->vr, N)) || (rc = dalloc(c, &c->vad, N)) || (rc = dalloc(c, &c->vae, N)) ||
         (rc = dalloc(c, &c->vc, N)) || (rc = dalloc(c, &c->upd, (size_t)std::max<int64_t>(P.upd_total, 1))))
         return rc;
+    if (c->opt.pivoting &&
+        ((rc = dalloc(c, &c->Doff, N)) || (rc = dalloc(c, &c->bsz, N)) || (rc = dalloc(c, &c->lperm, N))))
+        return rc;
     if (P.form == 2) {
         const int32_t n = P.n, m = P.m;
         std::vector<int64_t> arp(m + 1, 0);
@@ -1087,6 +1093,23 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         launch_norm1(c->dp, V, c->ctl, c->opt.eps_piv, st);
     }
     nl += 2;
+    if (c->opt.pivoting) {
+        // Sec. 4.5 pivoting: one CTA per front, the tree's levels in order
+        for (int32_t l = 0; l < P.nlevels; l++) {
+            const LevelWork &W = c->levels[l];
+            Prof pr(c, IPM_K_LARGE_PANEL, W.lvl_w, st);
+            launch_front_bk(c->dp, V, c->fronts, c->D, c->Doff, c->bsz, c->lperm, c->dyn, c->ctl,
+                            c->lvl_all + W.all_off, W.all_cnt, c->opt.nb, st);
+            nl++;
+        }
+        {
+            Prof pr(c, IPM_K_OTHER, Work(), st);
+            launch_factor_stats_bk(c->D, c->Doff, c->bsz, c->dyn, P.N, c->opt.large_reg, c->ctl, st);
+        }
+        nl++;
+        c->nl_factor = nl;
+        return to_err(cudaGetLastError());
+    }
     // Small fronts run on the caller's stream and the large fronts of the
     // same level on a second stream: fronts of one level are independent
     // (Sec. 4.3, tree-level parallelism), so a level costs the longer of the
@@ -1303,6 +1326,23 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
 // x <- (L D L^T)^-1 x in the factorisation order: one persistent launch per
 // sweep (dependency-driven, see kernels_solve.cu).
 int solve_inplace(ipm_ctx *c, double *x, cudaStream_t st, int *nl) {
+    const Plan &P = c->plan;
+    if (c->opt.pivoting) {
+        // per-level sweeps with the fronts' interchanges and 1x1 / 2x2 blocks of D
+        for (int32_t l = 0; l < P.nlevels; l++) {
+            const LevelWork &W = c->levels[l];
+            Prof pr(c, IPM_K_FORWARD, W.fwd_w, st);
+            launch_forward_bk(c->dp, c->fronts, c->D, c->Doff, c->bsz, c->lperm, x, c->upd,
+                              c->lvl_all + W.all_off, W.all_cnt, W.all_maxf, st);
+        }
+        for (int32_t l = P.nlevels - 1; l >= 0; l--) {
+            const LevelWork &W = c->levels[l];
+            Prof pr(c, IPM_K_BACKWARD, W.bwd_w, st);
+            launch_backward_bk(c->dp, c->fronts, c->lperm, x, c->lvl_all + W.all_off, W.all_cnt, W.all_maxf, st);
+        }
+        *nl += 2 * P.nlevels;
+        return to_err(cudaGetLastError());
+    }
     Work fw, bw;
     for (const LevelWork &W : c->levels) {
         fw.flops += W.fwd_w.flops;
@@ -1491,6 +1531,7 @@ void ipm_default_options(ipm_options *o) {
     o->device = 0;
     o->spin_limit_log2 = 24;
     o->level_kernel = 1;
+    o->pivoting = 0;
     o->verbose = 0;
 }
 
@@ -1506,7 +1547,8 @@ int ipm_create(ipm_ctx **out, const ipm_options *opt) {
         c->opt.level_kernel < 0 || c->opt.level_kernel > 1 ||
         (c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED &&
          c->opt.precision != IPM_PREC_SLICED) ||
-        c->opt.mixed_min_front < 1) {
+        c->opt.mixed_min_front < 1 || c->opt.pivoting < 0 || c->opt.pivoting > 1 ||
+        (c->opt.pivoting && c->opt.precision != IPM_PREC_FP64)) {
         delete c;
         return IPM_ERR_INVALID_ARG;
     }
@@ -1530,6 +1572,10 @@ int ipm_analyse(ipm_ctx *c, int32_t m, int32_t n, const int64_t *colptr, const i
     if (!c) return IPM_ERR_INVALID_ARG;
     if (form != IPM_FORM_AUTO && form != IPM_FORM_AUGMENTED && form != IPM_FORM_NORMAL) return IPM_ERR_INVALID_ARG;
     if (form == IPM_FORM_AUTO && ordering == IPM_ORD_USER) return IPM_ERR_INVALID_ARG;  // order size depends on the form
+    if (c->opt.pivoting) {
+        if (form == IPM_FORM_NORMAL) return IPM_ERR_INVALID_ARG;  // pivoting is for the indefinite K only
+        form = IPM_FORM_AUGMENTED;
+    }
     AnalyseOptions ao;
     ao.nb = c->opt.nb;
     ao.amalg_width = c->opt.amalg_width;
@@ -1697,6 +1743,10 @@ int ipm_factorise(ipm_ctx *c, const double *theta_dev, double rho, double delta,
     if (!c->values_set) return IPM_ERR_NOT_ANALYSED;
     if (!theta_dev && c->plan.n > 0) return IPM_ERR_INVALID_ARG;
     if (!(rho >= 0.0) || !(delta >= 0.0) || !std::isfinite(rho) || !std::isfinite(delta)) return IPM_ERR_INVALID_ARG;
+    // the pivoting mode: augmented system, fronts within the sweeps' shared memory (f + k doubles)
+    if (c->opt.pivoting &&
+        (c->plan.form != 1 || 2 * (int64_t)c->plan.max_f * (int64_t)sizeof(double) > kSweepSmemLimit))
+        return IPM_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (c->plan.n > 0 && theta_dev != c->theta) {
         cudaError_t e = cudaMemcpyAsync(c->theta, theta_dev, c->plan.n * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -2221,6 +2271,7 @@ int ipm_graph_capture(ipm_ctx *c, const double *theta_dev, double rho, double de
         (nsolves > 0 && ((P.n > 0 && (!r7_dev || !dx_dev)) || (P.m > 0 && (!r1_dev || !dy_dev)))))
         return IPM_ERR_INVALID_ARG;
     (void)stream;
+    if (c->opt.pivoting) return IPM_ERR_INVALID_ARG;  // the pivoting mode runs host-driven sweeps
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     c->graph_exec = nullptr;
@@ -2292,6 +2343,20 @@ int ipm_graph_capture(ipm_ctx *c, const double *theta_dev, double rho, double de
     }
     c->graph = g;
     return IPM_OK;
+}
+
+int ipm_get_pivots(ipm_ctx *c, int32_t *lperm_host, double *Doff_host, int32_t *bsize_host) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->opt.pivoting) return IPM_ERR_INVALID_ARG;
+    if (!c->factorised) return IPM_ERR_NOT_FACTORISED;
+    cudaSetDevice(c->opt.device);
+    cudaError_t e = cudaDeviceSynchronize();
+    const size_t N = (size_t)c->plan.N;
+    if (e == cudaSuccess && lperm_host) e = cudaMemcpy(lperm_host, c->lperm, N * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && Doff_host) e = cudaMemcpy(Doff_host, c->Doff, N * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && bsize_host) e = cudaMemcpy(bsize_host, c->bsz, N * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    return to_err(e);
 }
 
 int ipm_graph_launch(ipm_ctx *c, void *stream) {
@@ -2445,7 +2510,7 @@ int ipm_solve_noalloc(ipm_ctx *c, const double *r7, const double *r1, double *dx
         return IPM_ERR_SCRATCH_TOO_SMALL;
     }
     if (!c->factorised) return IPM_ERR_NOT_FACTORISED;
-    if (P.form != 1) return IPM_ERR_INVALID_ARG;  // augmented system only
+    if (P.form != 1 || c->opt.pivoting) return IPM_ERR_INVALID_ARG;  // augmented system, 1x1 pivots only
     if ((P.n > 0 && (!r7 || !dx)) || (P.m > 0 && (!r1 || !dy))) return IPM_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(c->opt.device);
     if (e != cudaSuccess) return to_err(e);

@@ -257,6 +257,16 @@ void launch_update_sliced(const DevPlan &P, double *fronts, const SlicedTile *it
                           const uint8_t *ws, const int32_t *ws_exp, DevCtl *ctl, cudaStream_t st);
 int measure_fp64_peaks(double *out, int blocks, int iters, int reps, cudaStream_t st, double *dfma_tflops,
                        double *dmma_tflops);
+void launch_front_bk(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Doff, int32_t *bsz,
+                     int32_t *lperm, double *dyn, DevCtl *ctl, const int32_t *list, int32_t count, int32_t nb,
+                     cudaStream_t st);
+void launch_factor_stats_bk(const double *D, const double *Doff, const int32_t *bsz, const double *dyn, int N,
+                            double large_reg, DevCtl *ctl, cudaStream_t st);
+void launch_forward_bk(const DevPlan &P, const double *fronts, const double *D, const double *Doff,
+                       const int32_t *bsz, const int32_t *lperm, double *x, double *upd, const int32_t *list,
+                       int32_t count, int32_t maxf, cudaStream_t st);
+void launch_backward_bk(const DevPlan &P, const double *fronts, const int32_t *lperm, double *x,
+                        const int32_t *list, int32_t count, int32_t maxf, cudaStream_t st);
 void launch_test_recip(const double *x, double *rcp, double *quo, int64_t n, cudaStream_t st);
 void launch_factor_stats(const double *D, const double *dyn, int N, double large_reg, DevCtl *ctl, cudaStream_t st);
 // solves and refinement (kernels_solve.cu)

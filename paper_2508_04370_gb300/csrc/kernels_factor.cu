@@ -906,6 +906,260 @@ __global__ void k_factor_stats(const double *__restrict__ D, const double *__res
     }
 }
 
+// ---------------------------------------------------------------------------
+// Pivoting of Sec. 4.5 (the Bunch-Kaufman variation) for matrices that are not
+// quasi-definite: one CTA per front assembles it (original entries, then the
+// children's contribution blocks in ascending order), adds the static terms
+// to its fully-summed diagonal and factorises its k fully-summed columns in
+// pivot blocks of nb columns, with 1x1 and 2x2 pivots chosen inside the
+// block: pre-swap of the largest remaining block diagonal, gamma_p = the
+// largest magnitude below the pivot in the block (row r), a lift of the pivot
+// to sign(M_pp) eps_piv ||K||_1 when max(|M_pp|, gamma_p) is not above it,
+// else a 1x1 pivot at p when |M_pp| >= alpha gamma_p or
+// |M_pp| gamma_r >= alpha gamma_p^2, a 1x1 pivot at r when
+// |M_rr| >= alpha gamma_r, otherwise the 2x2 pivot (p, r).  Interchanges stay
+// among the fully-summed columns, so the structure of the front is unchanged;
+// every pivot updates the whole trailing part of the front (the contribution
+// block included).  Each product and sum is rounded as written (no fused
+// multiply-add), so the arithmetic is that of a plain evaluation of the rule.
+// The front lives in its slab (lower triangle); a symmetric interchange of
+// positions a < b moves entries of the lower triangle only.
+constexpr int kBkThreads = 256;
+
+__device__ void bk_swap(double *F, int ld, int f, int a, int b, int32_t *lperm) {
+    if (a == b) return;
+#define FE(i, j) F[(int64_t)(j) * ld + (i)]
+    for (int i = threadIdx.x; i < f; i += kBkThreads) {
+        if (i < a) {
+            const double t = FE(a, i);
+            FE(a, i) = FE(b, i);
+            FE(b, i) = t;
+        } else if (i == a) {
+            const double t = FE(a, a);
+            FE(a, a) = FE(b, b);
+            FE(b, b) = t;
+        } else if (i < b) {
+            const double t = FE(i, a);
+            FE(i, a) = FE(b, i);
+            FE(b, i) = t;
+        } else if (i > b) {
+            const double t = FE(i, a);
+            FE(i, a) = FE(i, b);
+            FE(i, b) = t;
+        }
+    }
+    if (threadIdx.x == 0) {
+        const int32_t t = lperm[a];
+        lperm[a] = lperm[b];
+        lperm[b] = t;
+    }
+#undef FE
+}
+
+// argmax over lanes of v (first index on ties, -1 when every v is 0 and zero_is_none)
+__device__ __forceinline__ int warp_argmax_first(double v, int idx) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > v || (ov == v && oi < idx)) {
+            v = ov;
+            idx = oi;
+        }
+    }
+    return idx;
+}
+
+__global__ void __launch_bounds__(kBkThreads) k_front_bk(DevPlan P, DevVals V, double *__restrict__ fronts,
+                                                         double *__restrict__ D, double *__restrict__ Doff,
+                                                         int32_t *__restrict__ bsz, int32_t *__restrict__ lperm,
+                                                         double *__restrict__ dyn, DevCtl *ctl,
+                                                         const int32_t *__restrict__ list, int nb, double alpha) {
+    __shared__ int sh_q, sh_r, sh_two, sh_swap_a, sh_swap_b;
+    __shared__ double sh_d;
+    const int s = list[blockIdx.x];
+    const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
+    double *F = fronts + P.sn_off[s];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+#define FE(i, j) F[(int64_t)(j) * ld + (i)]
+    // assembly, in the order of the plain multifrontal method
+    for (int64_t t = tid; t < (int64_t)f * ld; t += kBkThreads) F[t] = 0.0;
+    __syncthreads();
+    for (int64_t q = P.orig_ptr[s] + tid; q < P.orig_ptr[s + 1]; q += kBkThreads)
+        F[P.orig_dst[q]] = orig_value(P, V, P.orig_src[q]);
+    __syncthreads();
+    for (int q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
+        const int c = P.child_list[q];
+        const int kc = P.sn_k[c], ldc = P.sn_ld[c], cc = P.sn_f[c] - kc;
+        const double *CB = fronts + P.sn_off[c] + (int64_t)kc * ldc + kc;
+        const int32_t *map = P.relmap + P.map_off[c];
+        for (int jj = warp; jj < cc; jj += kBkThreads / 32)
+            for (int ii = jj + lane; ii < cc; ii += 32)
+                F[(int64_t)map[jj] * ld + map[ii]] += CB[(int64_t)jj * ldc + ii];
+        __syncthreads();
+    }
+    // static terms on the fully-summed diagonal; interchanges start from the identity
+    for (int t = tid; t < k; t += kBkThreads) {
+        const int sg = P.sign[c0 + t];
+        const double sigma = sg < 0 ? V.rho : V.delta;
+        FE(t, t) = __dadd_rn(FE(t, t), (double)sg * sigma);
+        lperm[c0 + t] = t;
+        Doff[c0 + t] = 0.0;
+        dyn[c0 + t] = 0.0;
+    }
+    __syncthreads();
+    const double b1 = ctl->b1;
+    int32_t *lp = lperm + c0;
+    for (int b0 = 0; b0 < k; b0 += nb) {
+        const int b1c = min(b0 + nb, k);
+        int p = b0;
+        while (p < b1c) {
+            // pre-swap: the largest remaining block diagonal to position p
+            if (warp == 0) {
+                const int t = p + lane;
+                const double v = t < b1c ? fabs(FE(t, t)) : -1.0;
+                const int q = warp_argmax_first(v, t < b1c ? t : 0x7fffffff);
+                if (lane == 0) sh_q = q;
+            }
+            __syncthreads();
+            bk_swap(F, ld, f, p, sh_q, lp);
+            __syncthreads();
+            // gamma_p and r within the block; the pivot decision
+            if (warp == 0) {
+                const int i = p + 1 + lane;
+                const double v = i < b1c ? fabs(FE(i, p)) : -1.0;
+                const int r0 = warp_argmax_first(v, i < b1c ? i : 0x7fffffff);
+                const double gp_all = __shfl_sync(0xffffffffu, v, (r0 - p - 1) & 31);
+                if (lane == 0) {
+                    const double gp = (r0 < b1c && gp_all > 0.0) ? gp_all : 0.0;
+                    const int r = gp > 0.0 ? r0 : -1;
+                    const double app = FE(p, p);
+                    int two = 0, sa = -1, sb = -1;
+                    if ((fabs(app) > gp ? fabs(app) : gp) <= b1) {
+                        const double dn = app < 0.0 ? -b1 : b1;
+                        dyn[c0 + p] = __dsub_rn(dn, app);
+                        FE(p, p) = dn;
+                    } else if (fabs(app) < __dmul_rn(alpha, gp)) {
+                        double gr = 0.0;
+                        for (int t = p; t < b1c; t++) {
+                            if (t == r) continue;
+                            const double a = t < r ? fabs(FE(r, t)) : fabs(FE(t, r));
+                            if (a > gr) gr = a;
+                        }
+                        if (__dmul_rn(fabs(app), gr) >= __dmul_rn(__dmul_rn(alpha, gp), gp)) {
+                            // 1x1 at p
+                        } else if (fabs(FE(r, r)) >= __dmul_rn(alpha, gr)) {
+                            sa = p;
+                            sb = r;
+                        } else {
+                            sa = p + 1;
+                            sb = r;
+                            two = 1;
+                        }
+                    }
+                    sh_two = two;
+                    sh_swap_a = sa;
+                    sh_swap_b = sb;
+                }
+            }
+            __syncthreads();
+            if (sh_swap_a >= 0) {
+                bk_swap(F, ld, f, sh_swap_a, sh_swap_b, lp);
+                __syncthreads();
+            }
+            if (!sh_two) {
+                const double d = FE(p, p);
+                if (tid == 0) {
+                    D[c0 + p] = d;
+                    bsz[c0 + p] = 1;
+                    if (!isfinite(d) || d == 0.0) atomicOr(&ctl->status, kStatNonFinite);
+                }
+                for (int i = p + 1 + tid; i < f; i += kBkThreads) FE(i, p) = __ddiv_rn(FE(i, p), d);
+                __syncthreads();
+                for (int j = p + 1 + warp; j < f; j += kBkThreads / 32) {
+                    const double ljp = FE(j, p);
+                    for (int i = j + lane; i < f; i += 32)
+                        FE(i, j) = __dsub_rn(FE(i, j), __dmul_rn(__dmul_rn(FE(i, p), d), ljp));
+                }
+                __syncthreads();
+                p += 1;
+            } else {
+                const double e11 = FE(p, p), e21 = FE(p + 1, p), e22 = FE(p + 1, p + 1);
+                const double det = __dsub_rn(__dmul_rn(e11, e22), __dmul_rn(e21, e21));
+                if (tid == 0) {
+                    D[c0 + p] = e11;
+                    D[c0 + p + 1] = e22;
+                    Doff[c0 + p] = e21;
+                    bsz[c0 + p] = 2;
+                    bsz[c0 + p + 1] = 0;
+                    if (!isfinite(det) || det == 0.0) atomicOr(&ctl->status, kStatNonFinite);
+                }
+                for (int i = p + 2 + tid; i < f; i += kBkThreads) {
+                    const double x = FE(i, p), y = FE(i, p + 1);
+                    FE(i, p) = __ddiv_rn(__dsub_rn(__dmul_rn(x, e22), __dmul_rn(y, e21)), det);
+                    FE(i, p + 1) = __ddiv_rn(__dsub_rn(__dmul_rn(y, e11), __dmul_rn(x, e21)), det);
+                }
+                __syncthreads();
+                for (int j = p + 2 + warp; j < f; j += kBkThreads / 32) {
+                    const double l0 = FE(j, p), l1 = FE(j, p + 1);
+                    const double w0 = __dadd_rn(__dmul_rn(e11, l0), __dmul_rn(e21, l1));
+                    const double w1 = __dadd_rn(__dmul_rn(e21, l0), __dmul_rn(e22, l1));
+                    for (int i = j + lane; i < f; i += 32)
+                        FE(i, j) = __dsub_rn(FE(i, j), __dadd_rn(__dmul_rn(FE(i, p), w0), __dmul_rn(FE(i, p + 1), w1)));
+                }
+                __syncthreads();
+                if (tid == 0) FE(p + 1, p) = 0.0;  // L is unit lower triangular: the 2x2 block lives in D
+                __syncthreads();
+                p += 2;
+            }
+        }
+    }
+#undef FE
+}
+
+// Inertia and lift statistics of a factorisation with 1x1 and 2x2 blocks: a
+// 2x2 block holds one positive and one negative eigenvalue when its
+// determinant is negative, else two of the sign of its trace.
+__global__ void k_factor_stats_bk(const double *__restrict__ D, const double *__restrict__ Doff,
+                                  const int32_t *__restrict__ bsz, const double *__restrict__ dyn, int N,
+                                  double large_reg, DevCtl *ctl) {
+    int npos = 0, nneg = 0, ndyn = 0;
+    double mx = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+        const double a = fabs(dyn[j]);
+        ndyn += a != 0.0;
+        mx = fmax(mx, a);
+        if (bsz[j] == 2) {
+            const double det = __dsub_rn(__dmul_rn(D[j], D[j + 1]), __dmul_rn(Doff[j], Doff[j]));
+            if (det < 0.0) {
+                npos++;
+                nneg++;
+            } else if (det > 0.0) {
+                if (__dadd_rn(D[j], D[j + 1]) > 0.0) npos += 2;
+                else nneg += 2;
+            }
+        } else if (bsz[j] == 1) {
+            npos += D[j] > 0.0;
+            nneg += D[j] < 0.0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        npos += __shfl_xor_sync(0xffffffffu, npos, o);
+        nneg += __shfl_xor_sync(0xffffffffu, nneg, o);
+        ndyn += __shfl_xor_sync(0xffffffffu, ndyn, o);
+    }
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&ctl->npos, npos);
+        atomicAdd(&ctl->nneg, nneg);
+        atomicAdd(&ctl->ndyn, ndyn);
+        atomicMax((unsigned long long *)&ctl->max_dyn, (unsigned long long)__double_as_longlong(mx));
+        if (ndyn) atomicOr(&ctl->status, kStatDynReg);
+        if (mx > large_reg) atomicOr(&ctl->status, kStatLargeReg);
+    }
+}
+
 }  // namespace
 
 void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
@@ -986,6 +1240,19 @@ __global__ void k_test_recip(const double *__restrict__ x, double *__restrict__ 
         rcp[i] = recip_pivot(v);
         quo[i] = 1.0 / v;
     }
+}
+
+void launch_front_bk(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Doff, int32_t *bsz,
+                     int32_t *lperm, double *dyn, DevCtl *ctl, const int32_t *list, int32_t count, int32_t nb,
+                     cudaStream_t st) {
+    if (count <= 0) return;
+    k_front_bk<<<count, kBkThreads, 0, st>>>(P, V, fronts, D, Doff, bsz, lperm, dyn, ctl, list, nb,
+                                            0.125 + 0.125 * sqrt(17.0));
+}
+
+void launch_factor_stats_bk(const double *D, const double *Doff, const int32_t *bsz, const double *dyn, int N,
+                            double large_reg, DevCtl *ctl, cudaStream_t st) {
+    k_factor_stats_bk<<<152, 256, 0, st>>>(D, Doff, bsz, dyn, N, large_reg, ctl);
 }
 
 void launch_test_recip(const double *x, double *rcp, double *quo, int64_t n, cudaStream_t st) {

@@ -127,6 +127,122 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward(DevPlan P, const dou
     for (int t = tid; t < k; t += kSolveThreads) x[c0 + t] = z[t];
 }
 
+// Sweeps of a factorisation with the pivoting of Sec. 4.5 (1x1 and 2x2
+// blocks of D, interchanges among each front's fully-summed columns): as
+// k_forward / k_backward, with the front's interchanges applied to its
+// fully-summed entries before the forward substitution (position t takes the
+// entry of local index lperm[t]) and undone after the backward one; D is
+// applied block by block, a 2x2 block [e11 e21; e21 e22] by its inverse.
+// Dynamic shared memory: f + k doubles.
+__global__ void __launch_bounds__(kSolveThreads) k_forward_bk(DevPlan P, const double *__restrict__ fronts,
+                                                               const double *__restrict__ D,
+                                                               const double *__restrict__ Doff,
+                                                               const int32_t *__restrict__ bsz,
+                                                               const int32_t *__restrict__ lperm,
+                                                               double *__restrict__ x, double *__restrict__ upd,
+                                                               const int32_t *__restrict__ list) {
+    extern __shared__ double v[];
+    __shared__ double Lb[32 * 33];
+    const int s = list[blockIdx.x];
+    const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
+    double *tmp = v + f;
+    const double *L = fronts + P.sn_off[s];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int t = tid; t < f; t += kSolveThreads) v[t] = t < k ? x[c0 + t] : 0.0;
+    __syncthreads();
+    for (int q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
+        const int c = P.child_list[q];
+        const int cc = P.sn_f[c] - P.sn_k[c];
+        const double *u = upd + P.upd_off[c];
+        const int32_t *map = P.relmap + P.map_off[c];
+        for (int t = tid; t < cc; t += kSolveThreads) v[map[t]] += u[t];
+        __syncthreads();
+    }
+    for (int t = tid; t < k; t += kSolveThreads) tmp[t] = v[lperm[c0 + t]];
+    __syncthreads();
+    for (int t = tid; t < k; t += kSolveThreads) v[t] = tmp[t];
+    __syncthreads();
+    for (int b0 = 0; b0 < k; b0 += 32) {
+        const int b1 = min(b0 + 32, k), w = b1 - b0;
+        for (int t = tid; t < w * w; t += kSolveThreads) {
+            const int jj = t / w, ii = t - jj * w;
+            if (ii > jj) Lb[jj * 33 + ii] = L[(int64_t)(b0 + jj) * ld + (b0 + ii)];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double vi = lane < w ? v[b0 + lane] : 0.0;
+            for (int j = 0; j < w; j++) {
+                const double yj = __shfl_sync(0xffffffffu, vi, j);
+                if (lane > j && lane < w) vi -= Lb[j * 33 + lane] * yj;
+            }
+            if (lane < w) v[b0 + lane] = vi;
+        }
+        __syncthreads();
+        for (int i = b1 + tid; i < f; i += kSolveThreads) {
+            double acc = 0.0;
+            for (int j = 0; j < w; j++) acc += L[(int64_t)(b0 + j) * ld + i] * v[b0 + j];
+            v[i] -= acc;
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < f; t += kSolveThreads) {
+        if (t < k) {
+            const int b = bsz[c0 + t];
+            if (b == 1) {
+                x[c0 + t] = v[t] / D[c0 + t];
+            } else if (b == 2) {
+                const double e11 = D[c0 + t], e21 = Doff[c0 + t], e22 = D[c0 + t + 1];
+                const double det = e11 * e22 - e21 * e21;
+                const double y0 = v[t], y1 = v[t + 1];
+                x[c0 + t] = (e22 * y0 - e21 * y1) / det;
+                x[c0 + t + 1] = (e11 * y1 - e21 * y0) / det;
+            }
+        } else {
+            upd[P.upd_off[s] + (t - k)] = v[t];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSolveThreads) k_backward_bk(DevPlan P, const double *__restrict__ fronts,
+                                                                const int32_t *__restrict__ lperm,
+                                                                double *__restrict__ x,
+                                                                const int32_t *__restrict__ list) {
+    extern __shared__ double z[];
+    __shared__ double Lb[32 * 33];
+    const int s = list[blockIdx.x];
+    const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
+    const double *L = fronts + P.sn_off[s];
+    const int32_t *rows = P.sn_rows + P.sn_rptr[s];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int t = tid; t < f; t += kSolveThreads) z[t] = t < k ? x[c0 + t] : x[rows[t]];
+    __syncthreads();
+    const int nblk = (k + 31) / 32;
+    for (int bb = nblk - 1; bb >= 0; bb--) {
+        const int b0 = bb * 32, b1 = min(b0 + 32, k), w = b1 - b0;
+        for (int t = tid; t < w * w; t += kSolveThreads) {
+            const int jj = t / w, ii = t - jj * w;
+            if (ii > jj) Lb[jj * 33 + ii] = L[(int64_t)(b0 + jj) * ld + (b0 + ii)];
+        }
+        for (int j = b0 + warp; j < b1; j += kSolveThreads / 32) {
+            double acc = 0.0;
+            for (int i = b1 + lane; i < f; i += 32) acc += L[(int64_t)j * ld + i] * z[i];
+            acc = warp_sum(acc);
+            if (lane == 0) z[j] -= acc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double zi = lane < w ? z[b0 + lane] : 0.0;
+            for (int j = w - 1; j > 0; j--) {
+                const double zj = __shfl_sync(0xffffffffu, zi, j);
+                if (lane < j) zi -= Lb[lane * 33 + j] * zj;
+            }
+            if (lane < w) z[b0 + lane] = zi;
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < k; t += kSolveThreads) x[c0 + lperm[c0 + t]] = z[t];
+}
+
 // --------------------------------------------------------------------------
 // Persistent dependency-driven sweeps: one launch per forward or backward
 // pass instead of one per tree level.  CTAs take work items from an atomic
@@ -863,6 +979,25 @@ void launch_diag_inverse(const SolveSched &S, const double *fronts, double *Linv
     if (count <= 0) return;
     k_diag_inverse<<<(count + kInvWarps - 1) / kInvWarps, 32 * kInvWarps, 0, st>>>(S, fronts, Linv, items, count);
     if (npairs > 0) k_pair_products<<<npairs, 256, 0, st>>>(S, fronts, Linv, pairs, npairs);
+}
+
+void launch_forward_bk(const DevPlan &P, const double *fronts, const double *D, const double *Doff,
+                       const int32_t *bsz, const int32_t *lperm, double *x, double *upd, const int32_t *list,
+                       int32_t count, int32_t maxf, cudaStream_t st) {
+    if (count <= 0) return;
+    static uint64_t attr = 0;
+    if (first_on_device(attr)) {
+        cudaFuncSetAttribute(k_forward_bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemLimit);
+        cudaFuncSetAttribute(k_backward_bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemLimit);
+    }
+    k_forward_bk<<<count, kSolveThreads, 2 * (size_t)maxf * sizeof(double), st>>>(P, fronts, D, Doff, bsz, lperm, x,
+                                                                                  upd, list);
+}
+
+void launch_backward_bk(const DevPlan &P, const double *fronts, const int32_t *lperm, double *x,
+                        const int32_t *list, int32_t count, int32_t maxf, cudaStream_t st) {
+    if (count <= 0) return;
+    k_backward_bk<<<count, kSolveThreads, (size_t)maxf * sizeof(double), st>>>(P, fronts, lperm, x, list);
 }
 
 void launch_forward_persistent(const SolveSched &S, const double *fronts, const double *Dinv, double *x, double *upd,
