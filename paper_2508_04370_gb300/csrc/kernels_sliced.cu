@@ -194,9 +194,12 @@ __device__ __forceinline__ int acc_int(uint32_t bits) {
 
 constexpr int kSlicedSmem = 4 * (int)kSlicePairBytes + 4 * 4096 + 1024;  // A (128 rows), B (32 rows), alignment
 
-// One CTA (4 warps) per 128 x 32 output tile of the lower trailing part:
+// One CTA (8 warps) per 128 x 32 output tile of the lower trailing part:
 //     C(i, j) -= sum_q L(i, q) d_q L(j, q),   i >= j,  over the panel's columns q.
-__global__ void __launch_bounds__(128) k_update_sliced(DevPlan P, double *__restrict__ fronts,
+// Warps w and w + 4 read the same 32 TMEM lanes (rows) and split the tile's
+// columns, 16 each, so the epilogue runs on twice the threads.
+constexpr int kSlicedThreads = 256;
+__global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, double *__restrict__ fronts,
                                                        const SlicedTile *__restrict__ items,
                                                        const uint8_t *__restrict__ ws,
                                                        const int32_t *__restrict__ ws_exp, DevCtl *ctl) {
@@ -254,15 +257,18 @@ __global__ void __launch_bounds__(128) k_update_sliced(DevPlan P, double *__rest
             }
         tc::commit_to(&bar_mma);
     }
-    // the tile's FP64 entries of this thread's row, fetched while the copies
-    // and the MMAs run (independent loads; lower part of the front only)
-    const int r = warp * 32 + lane;
+    // the tile's FP64 entries of this thread's row and column half, fetched
+    // while the copies and the MMAs run (independent loads; lower part only)
+    constexpr int kHalf = kSliceCols / 2;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;
     const int row = it.i0 + r;
-    double cv[kSliceCols];
-    uint32_t live = 0;  // bit c: entry (row, j0 + c) exists and is updated
+    const int cbase = half * kHalf;
+    double cv[kHalf];
+    uint32_t live = 0;  // bit c: entry (row, j0 + cbase + c) exists and is updated
 #pragma unroll
-    for (int c = 0; c < kSliceCols; c++) {
-        const int col = it.j0 + c;
+    for (int c = 0; c < kHalf; c++) {
+        const int col = it.j0 + cbase + c;
         const bool v = row < f && col < f && row >= col;
         live |= (uint32_t)v << c;
         cv[c] = v ? F[(int64_t)col * ld + row] : 0.0;
@@ -277,31 +283,39 @@ __global__ void __launch_bounds__(128) k_update_sliced(DevPlan P, double *__rest
     tc::fence_after_sync();
     if (ok) {
         const int Ea = ws_exp[((int64_t)it.blk_a * kSliceRows + r) * 2 + 0];
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
-        for (int c8 = 0; c8 < kSliceCols / 8; c8++) {
-            uint32_t v[kSlices][8];
+        for (int c8 = 0; c8 < kHalf / 8; c8++) {
+            // S_0..S_3 first (hi), then S_4..S_7 (lo), to keep the registers low
+            uint32_t v[4][8];
+            long long hi[8];
 #pragma unroll
-            for (int d = 0; d < kSlices; d++) tc::tmem_ld8(lane_base + (uint32_t)(d * kSliceCols + c8 * 8), v[d]);
+            for (int d = 0; d < 4; d++)
+                tc::tmem_ld8(lane_base + (uint32_t)(d * kSliceCols + cbase + c8 * 8), v[d]);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 8; c++)
+                // hi = S0 2^21 + S1 2^14 + S2 2^7 + S3 (|hi| < 2^41)
+                hi[c] = ((long long)(acc_int(v[0][c]) * 128 + acc_int(v[1][c])) << 14) +
+                        (acc_int(v[2][c]) * 128 + acc_int(v[3][c]));
+#pragma unroll
+            for (int d = 0; d < 4; d++)
+                tc::tmem_ld8(lane_base + (uint32_t)((d + 4) * kSliceCols + cbase + c8 * 8), v[d]);
             tc::tmem_wait_ld();
 #pragma unroll
             for (int c = 0; c < 8; c++) {
-                int sd[kSlices];
-#pragma unroll
-                for (int d = 0; d < kSlices; d++) sd[d] = acc_int(v[d][c]);
-                // hi = S0 2^21 + S1 2^14 + S2 2^7 + S3 (|hi| < 2^41), lo likewise from S4..S7
-                const long long hi = ((long long)(sd[0] * 128 + sd[1]) << 14) + (sd[2] * 128 + sd[3]);
-                const long long lo = ((long long)(sd[4] * 128 + sd[5]) << 14) + (sd[6] * 128 + sd[7]);
+                const long long lo = ((long long)(acc_int(v[0][c]) * 128 + acc_int(v[1][c])) << 14) +
+                                     (acc_int(v[2][c]) * 128 + acc_int(v[3][c]));
                 // T = hi 2^28 + lo, kept as T 2^-8 (|.| < 2^61): the bits dropped
                 // are far below the truncation of the digit products with t + u >= 8
-                const long long tq = (hi << 20) + (lo >> 8);
+                const long long tq = (hi[c] << 20) + (lo >> 8);
                 if (tq != 0 && ((live >> (c8 * 8 + c)) & 1u))
-                    cv[c8 * 8 + c] -= int_scaled(tq, Ea + eb_col[c8 * 8 + c] - 55);
+                    cv[c8 * 8 + c] -= int_scaled(tq, Ea + eb_col[cbase + c8 * 8 + c] - 55);
             }
         }
 #pragma unroll
-        for (int c = 0; c < kSliceCols; c++)
-            if ((live >> c) & 1u) F[(int64_t)(it.j0 + c) * ld + row] = cv[c];
+        for (int c = 0; c < kHalf; c++)
+            if ((live >> c) & 1u) F[(int64_t)(it.j0 + cbase + c) * ld + row] = cv[c];
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -323,7 +337,7 @@ void launch_update_sliced(const DevPlan &P, double *fronts, const SlicedTile *it
     static uint64_t attr = 0;
     if (first_on_device(attr))
         cudaFuncSetAttribute(k_update_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlicedSmem);
-    k_update_sliced<<<count, 128, kSlicedSmem, st>>>(P, fronts, items, ws, ws_exp, ctl);
+    k_update_sliced<<<count, kSlicedThreads, kSlicedSmem, st>>>(P, fronts, items, ws, ws_exp, ctl);
 }
 
 }  // namespace ipm
