@@ -417,7 +417,8 @@ int ipm_measure_fp64_peak(int32_t device, double *dfma_tflops, double *dmma_tflo
 #define IPM_K_RESIDUAL 7       /* residual, |K||x|, |K|e and backward error */
 #define IPM_K_OTHER 8          /* norms, statistics, permutations, vector updates, diagonal-block
                                   inverses for the solves */
-#define IPM_K_SLICE 9          /* IPM_PREC_SLICED: splitting the panel operands into digit slices */
+#define IPM_K_SLICE 9          /* reserved (0 launches): the sliced path's digit slices are written by the
+                                  panel's triangular solve, counted in IPM_K_LARGE_PANEL */
 #define IPM_K_PIVOT_BLOCK 10   /* pivot blocks of a 32-column step, launched per step (the level kernel's
                                   are counted in IPM_K_LARGE_PANEL) */
 #define IPM_K_COUNT 11

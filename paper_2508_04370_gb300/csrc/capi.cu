@@ -39,12 +39,10 @@ struct StepWork {
     int64_t alt_off;  // FP64 tiles of the same fronts, used after a precision fallback
     int32_t alt_cnt;
     int32_t alt_cnt1;  // lookahead tiles among them
-    int64_t sl_off;   // sliced path: slice blocks of the panel operands (one per 128 trailing rows)
-    int32_t sl_cnt;
     int64_t st_off;   // sliced path: 128 x 32 output tiles; the first st_cnt1 cover the next panel's
     int32_t st_cnt;   // columns (critical path), the rest run beside the next panel
     int32_t st_cnt1;
-    Work panel_w, trsm_w, tile_w, tile_w1, tc_w, alt_w, alt_w1, sl_w, st_w1, st_w2;
+    Work panel_w, trsm_w, tile_w, tile_w1, tc_w, alt_w, alt_w1, st_w1, st_w2;
 };
 struct SmallClass {
     int64_t off;
@@ -110,10 +108,10 @@ struct ipm_ctx {
     AsmItem *asm_info = nullptr;
     int32_t *asm_cr = nullptr;
     int32_t *trsm_slots = nullptr;
+    int32_t *trsm_sbase = nullptr;     // sliced path: first slice block of each TRSM item's front (-1: none)
     double *panel_ws = nullptr;
     TileItem *tile_items = nullptr, *tc_items = nullptr, *alt_items = nullptr;
-    SliceItem *slice_items = nullptr;  // sliced tensor-core path: slice blocks and output tiles per step
-    SlicedTile *sliced_tiles = nullptr;
+    SlicedTile *sliced_tiles = nullptr;  // sliced tensor-core path: output tiles per step
     uint8_t *slice_ws = nullptr;       // digit images of a step: two halves, used by alternate steps
     int32_t *slice_exp = nullptr;      // their row scales (two halves)
     int64_t slice_half_blocks = 0;     // slice blocks per half
@@ -699,12 +697,11 @@ int setup_device(ipm_ctx *c) {
     std::vector<PanelItem> asm_items, panel_items, trsm_items;
     std::vector<AsmItem> asm_info;
     std::vector<int32_t> asm_cr;
-    std::vector<int32_t> trsm_slots, slot_of(P.nsuper, -1);
+    std::vector<int32_t> trsm_slots, trsm_sbase, slot_of(P.nsuper, -1);
     int32_t nslots = 0;
     for (int32_t s = 0; s < P.nsuper; s++)
         if (P.sn_large[s]) slot_of[s] = nslots++;
     std::vector<TileItem> tile_items, tc_items, alt_items;
-    std::vector<SliceItem> slice_items;
     std::vector<SlicedTile> sliced_tiles;
     int64_t max_slice_blocks = 0;
     const bool sliced = c->opt.precision == IPM_PREC_SLICED;
@@ -806,7 +803,6 @@ int setup_device(ipm_ctx *c) {
             S.tile_off = (int64_t)tile_items.size();
             S.tc_off = (int64_t)tc_items.size();
             S.alt_off = (int64_t)alt_items.size();
-            S.sl_off = (int64_t)slice_items.size();
             S.st_off = (int64_t)sliced_tiles.size();
             int32_t nblk = 0;  // slice blocks of this step
             std::vector<SlicedTile> t1, t2;  // sliced tiles: next panel's columns / the rest
@@ -826,19 +822,23 @@ int setup_device(ipm_ctx *c) {
                 if (S.p0 >= k) continue;
                 const int32_t p1 = std::min(S.p0 + c->opt.nb, k);
                 panel_items.push_back({s, 0, slot_of[s]});
+                const bool tc = c->opt.precision != IPM_PREC_FP64 && f >= c->opt.mixed_min_front;
+                // sliced fronts: the triangular solve writes the digit slices of the rows it finishes
+                const int32_t sbase = (tc && sliced && p1 < f) ? nblk : -1;
                 for (int32_t r = p1; r < f; r += kTrsmRowsHost) {
                     trsm_items.push_back({s, r, std::min(r + kTrsmRowsHost, f)});
                     trsm_slots.push_back(slot_of[s]);
+                    trsm_sbase.push_back(sbase);
                 }
-                const bool tc = c->opt.precision != IPM_PREC_FP64 && f >= c->opt.mixed_min_front;
                 const double w = p1 - S.p0, rest = f - p1;
                 // tiles of the next panel's columns (when the front has one) go first
                 const bool next_panel = p1 < k;
                 if (tc && sliced && p1 < f) {
-                    // slice blocks of rows p1.., then every 128 x 32 tile of the
-                    // lower trailing part, row blocks aligned with the slice blocks
+                    // slice blocks of rows p1.. (written by the triangular solve),
+                    // then every 128 x 32 tile of the lower trailing part, row
+                    // blocks aligned with the slice blocks
                     const int32_t base = nblk;
-                    for (int32_t r0 = p1; r0 < f; r0 += kSliceRows) slice_items.push_back({s, r0, nblk++});
+                    nblk += (f - p1 + kSliceRows - 1) / kSliceRows;
                     for (int32_t j0 = p1; j0 < f; j0 += kSliceCols)
                         for (int32_t b = (j0 - p1) / kSliceRows; p1 + b * kSliceRows < f; b++) {
                             const int32_t i0 = p1 + b * kSliceRows;
@@ -853,7 +853,7 @@ int setup_device(ipm_ctx *c) {
                             tw.flops += 2.0 * w * e;
                             tw.bytes += 16.0 * e + 2.0 * kSlices * 2.0 * w * (kSliceRows + kSliceCols);
                         }
-                    S.sl_w.bytes += 8.0 * 2.0 * rest * w + 2.0 * kSlices * 2.0 * rest * w;
+                    S.trsm_w.bytes += 2.0 * kSlices * 2.0 * rest * w;  // the slices the solve writes
                 } else if (tc) {
                     for (int32_t j0 = p1; j0 < f; j0 += kTcTile)
                         for (int32_t i0 = j0; i0 < f; i0 += kTcTile) tc_items.push_back({s, i0, j0});
@@ -899,7 +899,6 @@ int setup_device(ipm_ctx *c) {
             S.alt_cnt = (int32_t)(alt_items.size() - S.alt_off);
             sliced_tiles.insert(sliced_tiles.end(), t1.begin(), t1.end());
             sliced_tiles.insert(sliced_tiles.end(), t2.begin(), t2.end());
-            S.sl_cnt = (int32_t)(slice_items.size() - S.sl_off);
             S.st_cnt = (int32_t)(sliced_tiles.size() - S.st_off);
             S.st_cnt1 = (int32_t)t1.size();
             max_slice_blocks = std::max<int64_t>(max_slice_blocks, nblk);
@@ -944,7 +943,7 @@ int setup_device(ipm_ctx *c) {
         (rc = dalloc(c, &c->panel_ws, (size_t)std::max(nslots, 1) * kPanelWsHost)) ||
         (rc = dupload(c, &c->tile_items, tile_items)) || (rc = dupload(c, &c->tc_items, tc_items)) ||
         (rc = dupload(c, &c->alt_items, alt_items)) || (rc = dupload(c, &c->bwd_order, bwd_order)) ||
-        (rc = dupload(c, &c->slice_items, slice_items)) || (rc = dupload(c, &c->sliced_tiles, sliced_tiles)) ||
+        (rc = dupload(c, &c->trsm_sbase, trsm_sbase)) || (rc = dupload(c, &c->sliced_tiles, sliced_tiles)) ||
         (rc = dalloc(c, &c->slice_ws, 2 * (size_t)max_slice_blocks * (size_t)kSliceBlockBytes)) ||
         (rc = dalloc(c, &c->slice_exp, 2 * (size_t)std::max<int64_t>(max_slice_blocks, 1) * kSliceRows * 2)) ||
         (rc = dupload(c, &c->lvl_items, lvl_items)) || (rc = dalloc(c, &c->lvl_sync, (size_t)max_ncnt + 1)) ||
@@ -1224,12 +1223,6 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                                   S.panel_cnt, S.p0, c->opt.nb, c->panel_ws, sd);
             }
             nl++;
-            if (S.trsm_cnt > 0) {
-                Prof pr(c, IPM_K_LARGE_PANEL, S.trsm_w, sd);
-                launch_panel_trsm(c->dp, c->fronts, c->trsm_items + S.trsm_off, c->trsm_slots + S.trsm_off,
-                                  S.trsm_cnt, S.p0, c->opt.nb, c->panel_ws, sd);
-                nl++;
-            }
             const bool use_tc = (S.tc_cnt > 0 || S.st_cnt > 0) && c->mixed_active;
             const bool use_sliced = use_tc && S.st_cnt > 0;
             // sliced path: the digit images of this step (alternate halves of the
@@ -1238,10 +1231,12 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
             // which waits for the rest of step s-1)
             uint8_t *ws = c->slice_ws + (sidx & 1) * c->slice_half_blocks * kSliceBlockBytes;
             int32_t *wexp = c->slice_exp + (sidx & 1) * c->slice_half_blocks * kSliceRows * 2;
-            if (use_sliced) {
-                Prof pr(c, IPM_K_SLICE, S.sl_w, sd);
-                launch_slice_panel(c->dp, c->fronts, c->D, c->slice_items + S.sl_off, S.sl_cnt, S.p0, c->opt.nb, ws,
-                                   wexp, c->ctl, sd);
+            if (S.trsm_cnt > 0) {
+                // on the sliced path the solve also writes the slices of the rows it finishes
+                Prof pr(c, IPM_K_LARGE_PANEL, S.trsm_w, sd);
+                launch_panel_trsm(c->dp, c->fronts, c->trsm_items + S.trsm_off, c->trsm_slots + S.trsm_off,
+                                  S.trsm_cnt, S.p0, c->opt.nb, c->panel_ws, sd, c->trsm_sbase + S.trsm_off,
+                                  use_sliced ? ws : nullptr, wexp, c->D, c->ctl);
                 nl++;
             }
             const int32_t rest_tiles = S.tile_cnt - S.tile_cnt1;

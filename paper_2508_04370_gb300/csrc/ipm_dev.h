@@ -193,12 +193,6 @@ constexpr int64_t kSlicePairBytes = 128 * 128;       // two slices of 128 rows x
 constexpr int64_t kSliceOperandBytes = 4 * kSlicePairBytes;
 constexpr int64_t kSliceBlockBytes = 2 * kSliceOperandBytes;  // operand A (L), then operand B (L d)
 
-struct SliceItem {
-    int32_t s;
-    int32_t r0;   // first local row of the block (rows r0 .. r0+127; rows >= f are zero)
-    int32_t blk;  // slice block in the step's work space
-};
-
 struct SlicedTile {
     int32_t s;
     int32_t i0, j0;     // output rows i0 .. i0+127, columns j0 .. j0+31 (lower part only)
@@ -235,8 +229,12 @@ void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, doubl
                        DevCtl *ctl,
                        const PanelItem *items, int32_t count, int32_t p0, int32_t nb, double *pws, cudaStream_t st);
 // panel step 2 (rows below, kTrsmRowsHost rows per item; slots[i] = workspace slot of item i)
+// sbase[i] >= 0 (with sws non-null): item i also writes the digit slices of
+// its rows into the sliced update's work space (slice blocks from sbase[i])
 void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,
-                       int32_t p0, int32_t nb, const double *pws, cudaStream_t st);
+                       int32_t p0, int32_t nb, const double *pws, cudaStream_t st, const int32_t *sbase = nullptr,
+                       uint8_t *sws = nullptr, int32_t *sexp = nullptr, const double *D = nullptr,
+                       DevCtl *ctl = nullptr);
 constexpr int kTrsmRowsHost = 8;
 constexpr int kPanelWsHost = 32 * 33 + 32;
 void launch_large_update_strip(const DevPlan &P, double *fronts, const double *D, const TileItem *items,
@@ -250,9 +248,6 @@ void launch_large_update(const DevPlan &P, double *fronts, const double *D, cons
                          int32_t p0, int32_t w, cudaStream_t st);
 void launch_large_update_tc(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
                             int32_t p0, int32_t w, DevCtl *ctl, cudaStream_t st);
-void launch_slice_panel(const DevPlan &P, const double *fronts, const double *D, const SliceItem *items,
-                        int32_t count, int32_t p0, int32_t w, uint8_t *ws, int32_t *ws_exp, DevCtl *ctl,
-                        cudaStream_t st);
 void launch_update_sliced(const DevPlan &P, double *fronts, const SlicedTile *items, int32_t count,
                           const uint8_t *ws, const int32_t *ws_exp, DevCtl *ctl, cudaStream_t st);
 int measure_fp64_peaks(double *out, int blocks, int iters, int reps, cudaStream_t st, double *dfma_tflops,

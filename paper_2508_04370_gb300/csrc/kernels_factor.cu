@@ -29,6 +29,7 @@
 #include <cstdint>
 
 #include "ipm_dev.h"
+#include "sliced_common.cuh"
 
 namespace ipm {
 
@@ -560,8 +561,21 @@ constexpr int kTrsmRows = 8;
 static_assert(kTrsmRows == kTrsmRowsHost, "host and device row chunks differ");
 static_assert(32 * kTrsmRows == kBodyThreads, "one warp per row");
 
+// Where the triangular solve of a sliced front writes the digit slices of the
+// rows it finishes (ws == nullptr: no slicing): block base + (row - p1) / 128,
+// row (row - p1) % 128 of the step's work space.
+struct SliceOut {
+    uint8_t *ws;
+    int32_t *exps;
+    int32_t base;
+    int32_t p1;
+    const double *D;
+    DevCtl *ctl;
+};
+
 __device__ __forceinline__ void body_trsm(const DevPlan &P, double *__restrict__ fronts, int s, int r0, int r1,
-                                          int p0, int nb, const double *__restrict__ ws, double *pool) {
+                                          int p0, int nb, const double *__restrict__ ws, double *pool,
+                                          const SliceOut so = SliceOut{nullptr, nullptr, 0, 0, nullptr, nullptr}) {
     double *Wd = pool;                                                     // 32 x 33 + 32
     double(*T)[kTrsmRows + 1] = reinterpret_cast<double(*)[kTrsmRows + 1]>(pool + 32 * 33 + 32);  // [32][9]
     const int k = P.sn_k[s], ld = P.sn_ld[s];
@@ -598,7 +612,18 @@ __device__ __forceinline__ void body_trsm(const DevPlan &P, double *__restrict__
             const double u = __shfl_sync(0xffffffffu, t, q);
             if (lane > q) t -= u * Lr[q];
         }
-        T[lane][warp] = t * Wd[32 * 33 + lane];
+        const double lv = t * Wd[32 * 33 + lane];
+        T[lane][warp] = lv;
+        if (so.ws) {
+            // the finished row, sliced for the tensor-core update
+            const int row = r0 + warp;
+            const int c0 = P.sn_c0[s];
+            const double dq = lane < w ? so.D[c0 + p0 + lane] : 0.0;
+            const int blk = so.base + (row - so.p1) / kSliceRows;
+            const bool bad = sliced::slice_row_warp(lane < w ? lv : 0.0, dq, so.ws + (int64_t)blk * kSliceBlockBytes,
+                                                    so.exps + (int64_t)blk * kSliceRows * 2, (row - so.p1) % kSliceRows);
+            if (bad && lane == 0) atomicOr(&so.ctl->status, kStatNonFinite);
+        }
     }
     __syncthreads();
     {
@@ -742,10 +767,16 @@ __global__ void __launch_bounds__(kBodyThreads) k_panel_diag(DevPlan P, DevVals 
 __global__ void __launch_bounds__(kBodyThreads) k_panel_trsm(DevPlan P, double *__restrict__ fronts,
                                                               const PanelItem *__restrict__ items,
                                                               const int32_t *slots, int p0, int nb,
-                                                              const double *__restrict__ pws) {
+                                                              const double *__restrict__ pws,
+                                                              const int32_t *__restrict__ sbase, uint8_t *sws,
+                                                              int32_t *sexp, const double *__restrict__ Dg,
+                                                              DevCtl *ctl) {
     __shared__ double pool[kPoolDoubles];
     const PanelItem it = items[blockIdx.x];
-    body_trsm(P, fronts, it.s, it.r0, it.r1, p0, nb, pws + (int64_t)slots[blockIdx.x] * kPanelWs, pool);
+    SliceOut so{nullptr, nullptr, 0, 0, nullptr, nullptr};
+    if (sws && sbase[blockIdx.x] >= 0)
+        so = SliceOut{sws, sexp, sbase[blockIdx.x], min(p0 + nb, P.sn_k[it.s]), Dg, ctl};
+    body_trsm(P, fronts, it.s, it.r0, it.r1, p0, nb, pws + (int64_t)slots[blockIdx.x] * kPanelWs, pool, so);
 }
 
 __global__ void __launch_bounds__(kBodyThreads) k_large_update(DevPlan P, double *__restrict__ fronts,
@@ -1201,9 +1232,10 @@ void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, doubl
 }
 
 void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,
-                       int32_t p0, int32_t nb, const double *pws, cudaStream_t st) {
+                       int32_t p0, int32_t nb, const double *pws, cudaStream_t st, const int32_t *sbase,
+                       uint8_t *sws, int32_t *sexp, const double *D, DevCtl *ctl) {
     if (count <= 0) return;
-    k_panel_trsm<<<count, kBodyThreads, 0, st>>>(P, fronts, items, slots, p0, nb, pws);
+    k_panel_trsm<<<count, kBodyThreads, 0, st>>>(P, fronts, items, slots, p0, nb, pws, sbase, sws, sexp, D, ctl);
 }
 
 void launch_large_update(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,

@@ -10,7 +10,8 @@
 // integer arithmetic on the tensor cores (the splitting idea of Ozaki et
 // al.):
 //
-//  1. k_slice_panel: after a 32-column panel [p0, p1), every trailing row r
+//  1. slicing, in the panel's triangular solve (k_panel_trsm holds each
+//     finished row of L in one warp): after a 32-column panel [p0, p1), every trailing row r
 //     of the two panel operands a_rq = L(r, q) 2^h_q and
 //     b_rq = L(r, q) d_q 2^-h_q (h_q = floor(log2 |d_q| / 2): an exact
 //     balancing of each column, so that a_rq^2 and b_rq^2 are both within a
@@ -44,130 +45,15 @@
 
 #include "ipm_dev.h"
 #include "tc_common.cuh"
+#include "sliced_common.cuh"
 
 namespace ipm {
+
+using namespace sliced;
 
 namespace {
 
 constexpr long long kSlicePolls = 1ll << 24;  // bounded waits on copies and MMAs (~1 s)
-constexpr int kNoScale = -1100;                // row scale of an all-zero row: every digit is 0
-
-// Byte offset of the 16-byte chunk c (0..7) of row r in a 128-byte-swizzled
-// K-major image (eight rows form a 1024-byte atom).
-__device__ __forceinline__ uint32_t swz_chunk(int r, int c) {
-    return (uint32_t)r * 128u + ((((uint32_t)c) ^ ((uint32_t)r & 7u)) << 4);
-}
-
-// Biased exponent field of a double given as bits.
-__device__ __forceinline__ int biased_exp(long long b) { return (int)((b >> 52) & 0x7ff); }
-
-// rint(v 2^h 2^(56 - E)) for |v 2^h| < 2^E, from the bits of v (subnormal
-// v give 0).
-__device__ __forceinline__ long long fixed56(double v, int h, int E) {
-    const long long b = __double_as_longlong(v);
-    const int eb = biased_exp(b);
-    if (eb == 0 || eb == 0x7ff) return 0;
-    const long long m = (b & 0x000fffffffffffffll) | 0x0010000000000000ll;
-    // v 2^h = m 2^(eb + h - 1075); sh <= 3 because eb + h <= E + 1022
-    const int sh = eb + h - 1019 - E;
-    long long x;
-    if (sh >= 0) x = m << sh;
-    else if (sh >= -62) x = (m + (1ll << (-sh - 1))) >> (-sh);
-    else x = 0;
-    return b < 0 ? -x : x;
-}
-
-// Eight balanced base-2^7 digits of x (|x| <= 2^56): x = sum_t d[t] 2^(7 (7 - t)).
-// In 32-bit arithmetic: the low 28 bits give digits 7..4 and a carry of 0 or
-// 1 into the high part, which gives digits 3..0.
-__device__ __forceinline__ void digits8(long long x, int *d) {
-    int lo = (int)(x & 0x0fffffff);
-    int hi = (int)(x >> 28);
-#pragma unroll
-    for (int t = 7; t >= 4; t--) {
-        const int dg = ((lo + 64) & 127) - 64;
-        d[t] = dg;
-        lo = (lo - dg) >> 7;
-    }
-    hi += lo;
-#pragma unroll
-    for (int t = 3; t >= 1; t--) {
-        const int dg = ((hi + 64) & 127) - 64;
-        d[t] = dg;
-        hi = (hi - dg) >> 7;
-    }
-    d[0] = hi;
-}
-
-__device__ __forceinline__ uint32_t bf16_bits(int v) {
-    // every |v| <= 256 is exact in bf16: the high half of the float
-    return __float_as_uint((float)v) >> 16;
-}
-
-// One 128-row slice block per CTA: thread (r, op) takes row r of operand op
-// (op 0: a_rq = L(r, q) 2^h_q, op 1: b_rq = L(r, q) d_q 2^-h_q) and writes its
-// digit images and row scale.
-__global__ void __launch_bounds__(256) k_slice_panel(DevPlan P, const double *__restrict__ fronts,
-                                                     const double *__restrict__ Dg,
-                                                     const SliceItem *__restrict__ items, int p0, int w,
-                                                     uint8_t *__restrict__ ws, int32_t *__restrict__ ws_exp,
-                                                     DevCtl *ctl) {
-    const SliceItem it = items[blockIdx.x];
-    const int s = it.s;
-    const int f = P.sn_f[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
-    w = min(w, P.sn_k[s] - p0);
-    const double *F = fronts + P.sn_off[s];
-    const int r = threadIdx.x, op = threadIdx.y;
-    const int row = it.r0 + r;
-    const bool valid = row < f;
-    double v[kSliceCols];
-    int sh[kSliceCols];
-    // largest biased exponent of a nonzero normal entry after the column
-    // shifts; kNoExp: none
-    constexpr int kNoExp = -100000;
-    int emax = kNoExp;
-    bool bad = false;
-#pragma unroll
-    for (int q = 0; q < kSliceCols; q++) {
-        const double dq = q < w ? Dg[c0 + p0 + q] : 0.0;
-        const int ed = biased_exp(__double_as_longlong(dq));
-        const int h = ed == 0 ? 0 : ((ed - 1023) >> 1);  // floor(log2 |d_q| / 2)
-        const double l = (valid && q < w) ? F[(int64_t)(p0 + q) * ld + row] : 0.0;
-        v[q] = op == 0 ? l : l * dq;
-        sh[q] = op == 0 ? h : -h;
-        const int e = biased_exp(__double_as_longlong(v[q]));
-        bad |= e == 0x7ff;
-        if (e != 0) emax = max(emax, e + sh[q]);
-    }
-    if (bad) atomicOr(&ctl->status, kStatNonFinite);
-    // |v 2^shift| < 2^E with E = (largest shifted biased exponent) - 1022
-    const int E = (emax == kNoExp || bad) ? kNoScale : emax - 1022;
-    ws_exp[((int64_t)it.blk * kSliceRows + r) * 2 + op] = E;
-    uint8_t *img = ws + (int64_t)it.blk * kSliceBlockBytes + op * kSliceOperandBytes;
-#pragma unroll
-    for (int qg = 0; qg < kSliceCols / 8; qg++) {
-        // 8 columns x 8 slices: one 16-byte chunk per slice
-        uint32_t pk[kSlices][4];
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            int d[kSlices];
-            digits8(E == kNoScale ? 0 : fixed56(v[qg * 8 + j], sh[qg * 8 + j], E), d);
-#pragma unroll
-            for (int t = 0; t < kSlices; t++) {
-                const uint32_t hb = bf16_bits(d[t]);
-                if (j & 1) pk[t][j >> 1] |= hb << 16;
-                else pk[t][j >> 1] = hb;
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < kSlices; t++) {
-            // slice t sits in pair image t/2, K bytes (t%2)*64 .. +63 of each row
-            const int chunk = (t & 1) * 4 + qg;
-            uint4 *dst = (uint4 *)(img + (t >> 1) * kSlicePairBytes + swz_chunk(r, chunk));
-            *dst = make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
-        }
-    }
-}
 
 // t 2^e as a double (round half up to 53 bits), built with integer
 // operations; t != 0.  Leaves the normal range only through ldexp.
@@ -323,13 +209,6 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
 }
 
 }  // namespace
-
-void launch_slice_panel(const DevPlan &P, const double *fronts, const double *D, const SliceItem *items,
-                        int32_t count, int32_t p0, int32_t w, uint8_t *ws, int32_t *ws_exp, DevCtl *ctl,
-                        cudaStream_t st) {
-    if (count <= 0) return;
-    k_slice_panel<<<count, dim3(kSliceRows, 2), 0, st>>>(P, fronts, D, items, p0, w, ws, ws_exp, ctl);
-}
 
 void launch_update_sliced(const DevPlan &P, double *fronts, const SlicedTile *items, int32_t count,
                           const uint8_t *ws, const int32_t *ws_exp, DevCtl *ctl, cudaStream_t st) {

@@ -41,7 +41,9 @@ def _sliced_pair(pkg, lp, theta, seed, ordering, min_front, target=1e-12, level_
                  level_kernel=level_kernel)
     info = r["s"].info()
     assert info["flops_tensor"] > 0
-    assert r["kstats"]["large_update_tc"]["launches"] > 0 and r["kstats"]["slice"]["launches"] > 0
+    # the digit slices are written by the panel's triangular solve, so the
+    # separate slicing class stays empty
+    assert r["kstats"]["large_update_tc"]["launches"] > 0 and r["kstats"]["slice"]["launches"] == 0
     assert info["precision_fallbacks"] == 0 and info["mixed_active"] == 1
     return r, info
 
