@@ -85,6 +85,17 @@ extern "C" {
                               again, and later factorisations stay in FP64 (an IPM's Theta spread only
                               widens); ipm_info counts these fallbacks. */
 
+/* order of the large fronts' 32-column steps (Sec. 4.3 tree-level parallelism) */
+#define IPM_SCHED_AUTO 0        /* the dependency order where it takes at most 4/5 of the level order's
+                                   steps and levels for the level kernel hold under 1/10 of them; else
+                                   the level order */
+#define IPM_SCHED_LEVELS 1      /* level by level: the large fronts of a tree level step through their
+                                   panels together, the next level starts when the level is done */
+#define IPM_SCHED_DEPENDENCY 2  /* each large front starts two steps after its last large child's last
+                                   panel (and after the small-front levels of its small children), so
+                                   the steps follow the longest chain of panels in the tree instead of
+                                   the sum over levels of each level's widest front; no level kernel */
+
 typedef struct ipm_ctx ipm_ctx;
 
 typedef struct ipm_options {
@@ -125,6 +136,9 @@ typedef struct ipm_options {
                                  correctness path, not tuned for speed); augmented system and IPM_PREC_FP64
                                  only; fronts up to 12,800 rows; no ipm_graph_capture or ipm_solve_noalloc
                                  (IPM_ERR_INVALID_ARG); the factor's blocks come from ipm_get_pivots; 0 */
+    int32_t schedule;         /* IPM_SCHED_AUTO, IPM_SCHED_LEVELS or IPM_SCHED_DEPENDENCY; AUTO.  Both
+                                 orders give the same factor bit for bit (every entry receives the
+                                 same updates in the same order) */
 } ipm_options;
 
 typedef struct ipm_info {
@@ -156,6 +170,10 @@ typedef struct ipm_info {
     double amalg_zero_frac;                 /* amalgamation threshold the analysis used */
     int32_t tune_level_ctas_per_sm;         /* CTAs per SM of the level kernel (0 before the first factorisation) */
     int32_t graph_kernels;                  /* kernel nodes of the graph ipm_graph_capture built (0: none) */
+    int32_t schedule;                       /* order of the large fronts' steps in use: IPM_SCHED_LEVELS or
+                                               IPM_SCHED_DEPENDENCY */
+    int32_t steps_levels;                   /* 32-column steps of the large fronts in the level order */
+    int32_t steps_dependency;               /* ... in the dependency order */
 } ipm_info;
 
 /* Fill *opt with the defaults listed above. */

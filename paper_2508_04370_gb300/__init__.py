@@ -42,6 +42,9 @@ IPM_ORD_NATURAL = 3
 IPM_PREC_FP64 = 0
 IPM_PREC_MIXED = 1
 IPM_PREC_SLICED = 2
+IPM_SCHED_AUTO = 0
+IPM_SCHED_LEVELS = 1
+IPM_SCHED_DEPENDENCY = 2
 
 
 class ipm_options(ct.Structure):
@@ -63,6 +66,7 @@ class ipm_options(ct.Structure):
         ("verbose", ct.c_int32),
         ("level_kernel", ct.c_int32),
         ("pivoting", ct.c_int32),
+        ("schedule", ct.c_int32),
     ]
 
 
@@ -80,6 +84,7 @@ class ipm_info(ct.Structure):
         ("nnz_ne_seen", ct.c_int64), ("precision_fallbacks", ct.c_int32), ("mixed_active", ct.c_int32),
         ("tune_small_threads", ct.c_int32 * 3), ("tune_level_ratio", ct.c_double), ("tune_ms", ct.c_double),
         ("amalg_zero_frac", ct.c_double), ("tune_level_ctas_per_sm", ct.c_int32), ("graph_kernels", ct.c_int32),
+        ("schedule", ct.c_int32), ("steps_levels", ct.c_int32), ("steps_dependency", ct.c_int32),
     ]
 
     def as_dict(self):

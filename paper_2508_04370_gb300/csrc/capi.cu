@@ -26,7 +26,9 @@ struct Work {
     double flops = 0.0, bytes = 0.0;
 };
 struct StepWork {
-    int32_t p0;
+    int64_t asm_off;    // dependency order: assembly items of the fronts starting at this step
+    int32_t asm_cnt;
+    int32_t small_wait;  // dependency order: small-front level whose launch the assembly waits for (-1: none)
     int64_t panel_off;  // diagonal-block items (one per front)
     int32_t panel_cnt;
     int64_t trsm_off;   // row-chunk items below the diagonal blocks
@@ -42,7 +44,7 @@ struct StepWork {
     int64_t st_off;   // sliced path: 128 x 32 output tiles; the first st_cnt1 cover the next panel's
     int32_t st_cnt;   // columns (critical path), the rest run beside the next panel
     int32_t st_cnt1;
-    Work panel_w, trsm_w, tile_w, tile_w1, tc_w, alt_w, alt_w1, st_w1, st_w2;
+    Work panel_w, trsm_w, tile_w, tile_w1, tc_w, alt_w, alt_w1, st_w1, st_w2, asm_w;
 };
 struct SmallClass {
     int64_t off;
@@ -136,6 +138,11 @@ struct ipm_ctx {
     int32_t fallbacks = 0;
     double flops_tensor = 0.0;
     std::vector<LevelWork> levels;
+    bool dep_sched = false;              // large fronts in the dependency order (else level by level)
+    std::vector<StepWork> dsteps;        // its steps
+    std::vector<int32_t> small_dep;      // per level: step whose completion its small fronts wait for (-1: none)
+    int32_t steps_levels = 0, steps_dependency = 0;
+    std::vector<cudaEvent_t> done_ev;    // dependency order: end of each step on the critical stream
     // numeric state of the last factorisation
     double rho = 0.0, delta = 0.0;
     const double *theta_used = nullptr;
@@ -707,6 +714,7 @@ int setup_device(ipm_ctx *c) {
     const bool sliced = c->opt.precision == IPM_PREC_SLICED;
     std::vector<FactorItem> lvl_items;
     std::vector<int32_t> cbase(P.nsuper, -1);
+    std::vector<int64_t> front_asm(P.nsuper + 1, -1);  // first assembly item of each large front
     int32_t max_ncnt = 0;
     c->levels.assign(P.nlevels, LevelWork());
     c->flops_tensor = 0.0;
@@ -722,6 +730,117 @@ int setup_device(ipm_ctx *c) {
             fr.flops += cc * (cc + 1) / 2;
         }
         return fr;
+    };
+    // One step of the large-front path: for each (front s, panel start p0)
+    // of fp, the diagonal block of the panel, the triangular solve of the rows
+    // below it and the update tiles of the front's trailing part.
+    auto add_step = [&](const std::vector<std::pair<int32_t, int32_t>> &fp) {
+        StepWork S{};
+        S.small_wait = -1;
+        S.panel_off = (int64_t)panel_items.size();
+        S.trsm_off = (int64_t)trsm_items.size();
+        S.tile_off = (int64_t)tile_items.size();
+        S.tc_off = (int64_t)tc_items.size();
+        S.alt_off = (int64_t)alt_items.size();
+        S.st_off = (int64_t)sliced_tiles.size();
+        int32_t nblk = 0;  // slice blocks of this step
+        std::vector<SlicedTile> t1, t2;  // sliced tiles: next panel's columns / the rest
+        std::vector<TileItem> u1, u2, a1, a2;  // lookahead / remaining tiles of this step
+        Work w1, w2, wa1, wa2;
+        // lower entries of a kUpdTile tile times 2 w flops (and its bytes)
+        auto tile_work = [](Work &acc, int32_t f, int32_t i0, int32_t j0, double w) {
+            double e = 0.0;
+            for (int32_t j = j0; j < std::min(j0 + kUpdTile, f); j++)
+                e += std::max(0, std::min(i0 + kUpdTile, f) - std::max(i0, j));
+            acc.flops += 2.0 * w * e;
+            acc.bytes += 16.0 * e + 8.0 * w * (2.0 * kUpdTile);
+        };
+        for (const auto &e : fp) {
+            const int32_t s = e.first, p0 = e.second;
+            const int32_t k = P.sn_k[s], f = P.sn_f[s];
+            const int32_t p1 = std::min(p0 + c->opt.nb, k);
+            panel_items.push_back({s, 0, slot_of[s], p0});
+            const bool tc = c->opt.precision != IPM_PREC_FP64 && f >= c->opt.mixed_min_front;
+            // sliced fronts: the triangular solve writes the digit slices of the rows it finishes
+            const int32_t sbase = (tc && sliced && p1 < f) ? nblk : -1;
+            for (int32_t r = p1; r < f; r += kTrsmRowsHost) {
+                trsm_items.push_back({s, r, std::min(r + kTrsmRowsHost, f), p0});
+                trsm_slots.push_back(slot_of[s]);
+                trsm_sbase.push_back(sbase);
+            }
+            const double w = p1 - p0, rest = f - p1;
+            // tiles of the next panel's columns (when the front has one) go first
+            const bool next_panel = p1 < k;
+            if (tc && sliced && p1 < f) {
+                // slice blocks of rows p1.. (written by the triangular solve),
+                // then every 128 x 32 tile of the lower trailing part, row
+                // blocks aligned with the slice blocks
+                const int32_t base = nblk;
+                nblk += (f - p1 + kSliceRows - 1) / kSliceRows;
+                for (int32_t j0 = p1; j0 < f; j0 += kSliceCols)
+                    for (int32_t b = (j0 - p1) / kSliceRows; p1 + b * kSliceRows < f; b++) {
+                        const int32_t i0 = p1 + b * kSliceRows;
+                        const bool la = next_panel && j0 == p1;
+                        (la ? t1 : t2).push_back({s, i0, j0, base + b, base + (j0 - p1) / kSliceRows,
+                                                  (j0 - p1) % kSliceRows});
+                        // lower entries of the tile times 2 w flops; its C read and write
+                        double e = 0.0;
+                        for (int32_t j = j0; j < std::min(j0 + kSliceCols, f); j++)
+                            e += std::max(0, std::min(i0 + kSliceRows, f) - std::max(i0, j));
+                        Work &tw = la ? S.st_w1 : S.st_w2;
+                        tw.flops += 2.0 * w * e;
+                        tw.bytes += 16.0 * e + 2.0 * kSlices * 2.0 * w * (kSliceRows + kSliceCols);
+                    }
+                S.trsm_w.bytes += 2.0 * kSlices * 2.0 * rest * w;  // the slices the solve writes
+            } else if (tc) {
+                for (int32_t j0 = p1; j0 < f; j0 += kTcTile)
+                    for (int32_t i0 = j0; i0 < f; i0 += kTcTile) tc_items.push_back({s, i0, j0, p0});
+            }
+            for (int32_t j0 = p1; j0 < f; j0 += kUpdTile)
+                for (int32_t i0 = j0; i0 < f; i0 += kUpdTile) {
+                    // lookahead tiles become strips of kStripCols columns
+                    const bool la = next_panel && j0 == p1;
+                    std::vector<TileItem> &dst = tc ? (la ? a1 : a2) : (la ? u1 : u2);
+                    if (la) {
+                        for (int32_t jj = j0; jj < std::min(j0 + kUpdTile, f); jj += kStripCols)
+                            dst.push_back({s, i0, jj, p0});
+                    } else {
+                        dst.push_back({s, i0, j0, p0});
+                    }
+                    tile_work(tc ? (la ? wa1 : wa2) : (la ? w1 : w2), f, i0, j0, w);
+                }
+            // pivot block (w^3/3) + triangular solve of the rows below; update of the lower trailing part
+            S.panel_w.flops += w * w * w / 3.0;
+            S.panel_w.bytes += 16.0 * w * w;
+            S.trsm_w.flops += rest * w * w;
+            S.trsm_w.bytes += 16.0 * rest * w;
+            if (tc) {
+                S.tc_w.flops += 2.0 * w * rest * (rest + 1) / 2;
+                S.tc_w.bytes += 16.0 * rest * (rest + 1) / 2 + 8.0 * rest * w;
+                c->flops_tensor += 2.0 * w * rest * (rest + 1) / 2;
+            }
+        }
+        tile_items.insert(tile_items.end(), u1.begin(), u1.end());
+        tile_items.insert(tile_items.end(), u2.begin(), u2.end());
+        alt_items.insert(alt_items.end(), a1.begin(), a1.end());
+        alt_items.insert(alt_items.end(), a2.begin(), a2.end());
+        S.tile_cnt1 = (int32_t)u1.size();
+        S.alt_cnt1 = (int32_t)a1.size();
+        S.tile_w1 = w1;
+        S.tile_w = w2;
+        S.alt_w1 = wa1;
+        S.alt_w = wa2;
+        S.panel_cnt = (int32_t)(panel_items.size() - S.panel_off);
+        S.trsm_cnt = (int32_t)(trsm_items.size() - S.trsm_off);
+        S.tile_cnt = (int32_t)(tile_items.size() - S.tile_off);
+        S.tc_cnt = (int32_t)(tc_items.size() - S.tc_off);
+        S.alt_cnt = (int32_t)(alt_items.size() - S.alt_off);
+        sliced_tiles.insert(sliced_tiles.end(), t1.begin(), t1.end());
+        sliced_tiles.insert(sliced_tiles.end(), t2.begin(), t2.end());
+        S.st_cnt = (int32_t)(sliced_tiles.size() - S.st_off);
+        S.st_cnt1 = (int32_t)t1.size();
+        max_slice_blocks = std::max<int64_t>(max_slice_blocks, nblk);
+        return S;
     };
     for (int32_t l = 0; l < P.nlevels; l++) {
         LevelWork &W = c->levels[l];
@@ -774,6 +893,7 @@ int setup_device(ipm_ctx *c) {
         for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
             int32_t s = P.lvl_large[t];
             const int32_t ld = P.sn_ld[s];
+            front_asm[s] = (int64_t)asm_items.size();
             for (int32_t cl = 0; cl < P.sn_f[s]; cl += 32) {
                 const int32_t ce = std::min(cl + 32, P.sn_f[s]);
                 asm_items.push_back({s, cl, ce});
@@ -795,113 +915,12 @@ int setup_device(ipm_ctx *c) {
             maxsteps = std::max(maxsteps, (P.sn_k[s] + c->opt.nb - 1) / c->opt.nb);
         }
         W.asm_cnt = (int32_t)(asm_items.size() - W.asm_off);
+        std::vector<std::pair<int32_t, int32_t>> fp;
         for (int32_t st = 0; st < maxsteps; st++) {
-            StepWork S;
-            S.p0 = st * c->opt.nb;
-            S.panel_off = (int64_t)panel_items.size();
-            S.trsm_off = (int64_t)trsm_items.size();
-            S.tile_off = (int64_t)tile_items.size();
-            S.tc_off = (int64_t)tc_items.size();
-            S.alt_off = (int64_t)alt_items.size();
-            S.st_off = (int64_t)sliced_tiles.size();
-            int32_t nblk = 0;  // slice blocks of this step
-            std::vector<SlicedTile> t1, t2;  // sliced tiles: next panel's columns / the rest
-            std::vector<TileItem> u1, u2, a1, a2;  // lookahead / remaining tiles of this step
-            Work w1, w2, wa1, wa2;
-            // lower entries of a kUpdTile tile times 2 w flops (and its bytes)
-            auto tile_work = [](Work &acc, int32_t f, int32_t i0, int32_t j0, double w) {
-                double e = 0.0;
-                for (int32_t j = j0; j < std::min(j0 + kUpdTile, f); j++)
-                    e += std::max(0, std::min(i0 + kUpdTile, f) - std::max(i0, j));
-                acc.flops += 2.0 * w * e;
-                acc.bytes += 16.0 * e + 8.0 * w * (2.0 * kUpdTile);
-            };
-            for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
-                int32_t s = P.lvl_large[t];
-                const int32_t k = P.sn_k[s], f = P.sn_f[s];
-                if (S.p0 >= k) continue;
-                const int32_t p1 = std::min(S.p0 + c->opt.nb, k);
-                panel_items.push_back({s, 0, slot_of[s]});
-                const bool tc = c->opt.precision != IPM_PREC_FP64 && f >= c->opt.mixed_min_front;
-                // sliced fronts: the triangular solve writes the digit slices of the rows it finishes
-                const int32_t sbase = (tc && sliced && p1 < f) ? nblk : -1;
-                for (int32_t r = p1; r < f; r += kTrsmRowsHost) {
-                    trsm_items.push_back({s, r, std::min(r + kTrsmRowsHost, f)});
-                    trsm_slots.push_back(slot_of[s]);
-                    trsm_sbase.push_back(sbase);
-                }
-                const double w = p1 - S.p0, rest = f - p1;
-                // tiles of the next panel's columns (when the front has one) go first
-                const bool next_panel = p1 < k;
-                if (tc && sliced && p1 < f) {
-                    // slice blocks of rows p1.. (written by the triangular solve),
-                    // then every 128 x 32 tile of the lower trailing part, row
-                    // blocks aligned with the slice blocks
-                    const int32_t base = nblk;
-                    nblk += (f - p1 + kSliceRows - 1) / kSliceRows;
-                    for (int32_t j0 = p1; j0 < f; j0 += kSliceCols)
-                        for (int32_t b = (j0 - p1) / kSliceRows; p1 + b * kSliceRows < f; b++) {
-                            const int32_t i0 = p1 + b * kSliceRows;
-                            const bool la = next_panel && j0 == p1;
-                            (la ? t1 : t2).push_back({s, i0, j0, base + b, base + (j0 - p1) / kSliceRows,
-                                                      (j0 - p1) % kSliceRows});
-                            // lower entries of the tile times 2 w flops; its C read and write
-                            double e = 0.0;
-                            for (int32_t j = j0; j < std::min(j0 + kSliceCols, f); j++)
-                                e += std::max(0, std::min(i0 + kSliceRows, f) - std::max(i0, j));
-                            Work &tw = la ? S.st_w1 : S.st_w2;
-                            tw.flops += 2.0 * w * e;
-                            tw.bytes += 16.0 * e + 2.0 * kSlices * 2.0 * w * (kSliceRows + kSliceCols);
-                        }
-                    S.trsm_w.bytes += 2.0 * kSlices * 2.0 * rest * w;  // the slices the solve writes
-                } else if (tc) {
-                    for (int32_t j0 = p1; j0 < f; j0 += kTcTile)
-                        for (int32_t i0 = j0; i0 < f; i0 += kTcTile) tc_items.push_back({s, i0, j0});
-                }
-                for (int32_t j0 = p1; j0 < f; j0 += kUpdTile)
-                    for (int32_t i0 = j0; i0 < f; i0 += kUpdTile) {
-                        // lookahead tiles become strips of kStripCols columns
-                        const bool la = next_panel && j0 == p1;
-                        std::vector<TileItem> &dst = tc ? (la ? a1 : a2) : (la ? u1 : u2);
-                        if (la) {
-                            for (int32_t jj = j0; jj < std::min(j0 + kUpdTile, f); jj += kStripCols)
-                                dst.push_back({s, i0, jj});
-                        } else {
-                            dst.push_back({s, i0, j0});
-                        }
-                        tile_work(tc ? (la ? wa1 : wa2) : (la ? w1 : w2), f, i0, j0, w);
-                    }
-                // pivot block (w^3/3) + triangular solve of the rows below; update of the lower trailing part
-                S.panel_w.flops += w * w * w / 3.0;
-                S.panel_w.bytes += 16.0 * w * w;
-                S.trsm_w.flops += rest * w * w;
-                S.trsm_w.bytes += 16.0 * rest * w;
-                if (tc) {
-                    S.tc_w.flops += 2.0 * w * rest * (rest + 1) / 2;
-                    S.tc_w.bytes += 16.0 * rest * (rest + 1) / 2 + 8.0 * rest * w;
-                    c->flops_tensor += 2.0 * w * rest * (rest + 1) / 2;
-                }
-            }
-            tile_items.insert(tile_items.end(), u1.begin(), u1.end());
-            tile_items.insert(tile_items.end(), u2.begin(), u2.end());
-            alt_items.insert(alt_items.end(), a1.begin(), a1.end());
-            alt_items.insert(alt_items.end(), a2.begin(), a2.end());
-            S.tile_cnt1 = (int32_t)u1.size();
-            S.alt_cnt1 = (int32_t)a1.size();
-            S.tile_w1 = w1;
-            S.tile_w = w2;
-            S.alt_w1 = wa1;
-            S.alt_w = wa2;
-            S.panel_cnt = (int32_t)(panel_items.size() - S.panel_off);
-            S.trsm_cnt = (int32_t)(trsm_items.size() - S.trsm_off);
-            S.tile_cnt = (int32_t)(tile_items.size() - S.tile_off);
-            S.tc_cnt = (int32_t)(tc_items.size() - S.tc_off);
-            S.alt_cnt = (int32_t)(alt_items.size() - S.alt_off);
-            sliced_tiles.insert(sliced_tiles.end(), t1.begin(), t1.end());
-            sliced_tiles.insert(sliced_tiles.end(), t2.begin(), t2.end());
-            S.st_cnt = (int32_t)(sliced_tiles.size() - S.st_off);
-            S.st_cnt1 = (int32_t)t1.size();
-            max_slice_blocks = std::max<int64_t>(max_slice_blocks, nblk);
+            fp.clear();
+            for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++)
+                if (st * c->opt.nb < P.sn_k[P.lvl_large[t]]) fp.push_back({P.lvl_large[t], st * c->opt.nb});
+            const StepWork S = add_step(fp);
             W.steps.push_back(S);
             if (S.tc_cnt > 0 || S.st_cnt > 0) W.has_tc = true;
         }
@@ -919,6 +938,98 @@ int setup_device(ipm_ctx *c) {
         }
         max_ncnt = std::max(max_ncnt, W.lvl_ncnt);
     }
+    // Dependency order of the large fronts' steps.  Front s starts at step
+    // g0[s], two steps after the last panel of its last large child (the
+    // child's trailing tiles of that step finish before the lookahead tiles
+    // of the next step, which every later step of the critical stream
+    // follows) and not before the small-front levels holding its small
+    // children were issued.  Small-front level l is issued (on the caller's
+    // stream) once the steps up to small_dep[l] are done, small_dep[l] being
+    // one past the last panel of the last large child of its fronts.
+    c->dsteps.clear();
+    c->small_dep.assign(P.nlevels, -1);
+    int32_t steps_levels = 0;
+    for (const LevelWork &W : c->levels) steps_levels += (int32_t)W.steps.size();
+    {
+        const int32_t nb = c->opt.nb;
+        std::vector<int32_t> g0(ns, 0), gend(ns, -1), small_em(P.nlevels, 0), nsmall_child(ns, -1);
+        int32_t T = 0;
+        for (int32_t l = 0; l < P.nlevels; l++) {
+            for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
+                const int32_t s = P.lvl_large[t];
+                int32_t g = 0;
+                for (int32_t q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
+                    const int32_t ch = P.child_list[q];
+                    if (P.sn_large[ch]) {
+                        g = std::max(g, gend[ch] + 2);
+                    } else {
+                        g = std::max(g, small_em[P.sn_level[ch]]);
+                        nsmall_child[s] = std::max(nsmall_child[s], P.sn_level[ch]);
+                    }
+                }
+                g0[s] = g;
+                gend[s] = g + (P.sn_k[s] + nb - 1) / nb - 1;
+                T = std::max(T, gend[s] + 1);
+            }
+            int32_t dep = -1;
+            for (int32_t t = P.lvl_small_ptr[l]; t < P.lvl_small_ptr[l + 1]; t++) {
+                const int32_t s = P.lvl_small[t];
+                for (int32_t q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++)
+                    if (P.sn_large[P.child_list[q]]) dep = std::max(dep, gend[P.child_list[q]] + 1);
+            }
+            c->small_dep[l] = dep;
+            small_em[l] = std::max(l > 0 ? small_em[l - 1] : 0, dep + 1);
+        }
+        c->steps_dependency = T;
+        // the order in use
+        int32_t lk_steps = 0;
+        for (const LevelWork &W : c->levels)
+            if (c->opt.level_kernel && W.lvl_cnt > 0 &&
+                W.lvl_w.flops / 1.0e12 < c->tune_ratio * W.lvl_chain * 35e-6)
+                lk_steps += (int32_t)W.steps.size();
+        c->dep_sched = !c->opt.pivoting && P.nlarge > 0 &&
+                       (c->opt.schedule == IPM_SCHED_DEPENDENCY ||
+                        (c->opt.schedule == IPM_SCHED_AUTO && 5 * (int64_t)T <= 4 * (int64_t)steps_levels &&
+                         10 * lk_steps < steps_levels));
+        if (c->dep_sched) {
+            // fronts by start step; the active set advances one panel per step
+            std::vector<std::vector<int32_t>> starting(T);
+            for (int32_t s = 0; s < ns; s++)
+                if (P.sn_large[s]) starting[g0[s]].push_back(s);
+            std::vector<int32_t> active;
+            std::vector<std::pair<int32_t, int32_t>> fp;
+            for (int32_t g = 0; g < T; g++) {
+                // assembly copies of the starting fronts (same ranges as their level items)
+                const int64_t aoff = (int64_t)asm_items.size();
+                Work aw;
+                int32_t swait = -1;
+                for (int32_t s : starting[g]) {
+                    const int64_t a0 = front_asm[s];
+                    const int64_t a1 = a0 + (P.sn_f[s] + 31) / 32;
+                    for (int64_t a = a0; a < a1; a++) {
+                        const PanelItem pi = asm_items[a];
+                        const AsmItem ai = asm_info[a];
+                        asm_items.push_back(pi);
+                        asm_info.push_back(ai);
+                    }
+                    aw.bytes += front_work(s).bytes;
+                    swait = std::max(swait, nsmall_child[s]);
+                    active.push_back(s);
+                }
+                fp.clear();
+                for (int32_t s : active) fp.push_back({s, (g - g0[s]) * nb});
+                StepWork S = add_step(fp);
+                S.asm_off = aoff;
+                S.asm_cnt = (int32_t)((int64_t)asm_items.size() - aoff);
+                S.asm_w = aw;
+                S.small_wait = swait;
+                c->dsteps.push_back(S);
+                active.erase(std::remove_if(active.begin(), active.end(), [&](int32_t s) { return gend[s] == g; }),
+                             active.end());
+            }
+        }
+    }
+    c->steps_levels = steps_levels;
     std::vector<int64_t> upd_off(P.upd_off.begin(), P.upd_off.end());
     std::vector<int32_t> bwd_order(lvl_all.rbegin(), lvl_all.rend());
     c->solve_maxf = P.max_f;
@@ -1144,7 +1255,7 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
             return IPM_ERR_CUDA;
         }
     }
-    size_t nsteps = 0;
+    size_t nsteps = c->dsteps.size();
     for (const LevelWork &W : c->levels) nsteps += W.steps.size();
     while (c->step_ev.size() < 2 * nsteps) {
         cudaEvent_t e;
@@ -1154,151 +1265,204 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
         }
         c->step_ev.push_back(e);
     }
+    while (c->done_ev.size() < c->dsteps.size() + 1) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return IPM_ERR_CUDA;
+        }
+        c->done_ev.push_back(e);
+    }
     cudaStream_t sd = c->side, sd2 = c->side2;
     size_t sidx = 0;
     cudaEventRecord(c->dep_ev[0], st);
     cudaStreamWaitEvent(sd, c->dep_ev[0], 0);
     cudaEvent_t last_small = nullptr, last_large = nullptr;
-    for (int32_t l = 0; l < P.nlevels; l++) {
+    // the small fronts of level l on the caller's stream, one stream per size
+    // class (the classes of a level are independent); records last_small
+    auto emit_small = [&](int32_t l) {
         const LevelWork &W = c->levels[l];
-        cudaEvent_t small_before = last_small, large_before = last_large;
-        if (!W.small.empty()) {
-            // the size classes of a level are independent: each on its own stream
-            if (large_before) cudaStreamWaitEvent(st, large_before, 0);
-            cudaEvent_t fork = c->dep_ev[1 + 5 * l];
-            if (W.small.size() > 1) cudaEventRecord(fork, st);
-            for (size_t q = 0; q < W.small.size(); q++) {
-                const SmallClass &C = W.small[q];
-                cudaStream_t sq = q == 0 ? st : c->cls[(q - 1) & 1];
-                if (q > 0) cudaStreamWaitEvent(sq, fork, 0);
-                Prof pr(c, IPM_K_SMALL_FRONTS, C.w, sq);
-                launch_small_fronts(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_small + C.off, C.cnt,
-                                    c->opt.nb, C.maxf, c->tune_threads[C.cls], sq);
-                nl++;
-                if (q > 0) {
-                    cudaEvent_t join = c->dep_ev[2 + 5 * l + (q - 1)];
-                    cudaEventRecord(join, sq);
-                    cudaStreamWaitEvent(st, join, 0);
-                }
-            }
-            last_small = c->dep_ev[4 + 5 * l];
-            cudaEventRecord(last_small, st);
-        }
-        if (W.asm_cnt == 0 && W.steps.empty()) continue;
-        if (small_before) cudaStreamWaitEvent(sd, small_before, 0);
-        const bool latency_bound = W.lvl_w.flops / 1.0e12 < c->tune_ratio * W.lvl_chain * 35e-6;
-        // (a latency-bound level keeps the FP64 level kernel in the tensor-core
-        // modes too: its work is too small for the tensor cores to matter)
-        if (c->opt.level_kernel && W.lvl_cnt > 0 && latency_bound) {
-            // FP64: all large-front work of the level in one dependency-driven launch
-            {
-                Prof pr(c, IPM_K_LARGE_PANEL, W.lvl_w, sd);
-                launch_large_level(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_items + W.lvl_off,
-                                   W.lvl_cnt, c->lvl_sync, W.lvl_ncnt, c->asm_info, c->asm_cr, c->panel_ws,
-                                   c->opt.nb, level_grid(c),
-                                   c->opt.spin_limit_log2 < 0 ? 0 : (1ll << c->opt.spin_limit_log2), sd);
-            }
+        cudaEvent_t fork = c->dep_ev[1 + 5 * l];
+        if (W.small.size() > 1) cudaEventRecord(fork, st);
+        for (size_t q = 0; q < W.small.size(); q++) {
+            const SmallClass &C = W.small[q];
+            cudaStream_t sq = q == 0 ? st : c->cls[(q - 1) & 1];
+            if (q > 0) cudaStreamWaitEvent(sq, fork, 0);
+            Prof pr(c, IPM_K_SMALL_FRONTS, C.w, sq);
+            launch_small_fronts(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_small + C.off, C.cnt,
+                                c->opt.nb, C.maxf, c->tune_threads[C.cls], sq);
             nl++;
-            last_large = c->dep_ev[5 + 5 * l];
-            cudaEventRecord(last_large, sd);
-            continue;
+            if (q > 0) {
+                cudaEvent_t join = c->dep_ev[2 + 5 * l + (q - 1)];
+                cudaEventRecord(join, sq);
+                cudaStreamWaitEvent(st, join, 0);
+            }
         }
-        if (W.asm_cnt > 0) {
-            Prof pr(c, IPM_K_LARGE_ASSEMBLE, W.asm_w, sd);
-            launch_large_assemble(c->dp, V, c->fronts, c->asm_items + W.asm_off, c->asm_info + W.asm_off, c->asm_cr,
-                                  W.asm_cnt, sd);
+        last_small = c->dep_ev[4 + 5 * l];
+        cudaEventRecord(last_small, st);
+    };
+    // Per 32-column step: diagonal blocks and triangular solves, then the
+    // update split in two.  The tiles of the next panel's columns (lookahead)
+    // stay on the critical path; the remaining trailing tiles run on a third
+    // stream beside the next step's diagonal blocks.  Every entry still
+    // receives the panels' updates in panel order: the lookahead tiles of
+    // step s wait for the remaining tiles of step s-1.
+    cudaEvent_t prev_rest = nullptr;
+    auto emit_step = [&](const StepWork &S) {
+        {
+            Prof pr(c, IPM_K_PIVOT_BLOCK, S.panel_w, sd);
+            launch_panel_diag(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->panel_items + S.panel_off,
+                              S.panel_cnt, c->opt.nb, c->panel_ws, sd);
+        }
+        nl++;
+        const bool use_tc = (S.tc_cnt > 0 || S.st_cnt > 0) && c->mixed_active;
+        const bool use_sliced = use_tc && S.st_cnt > 0;
+        // sliced path: the digit images of this step (alternate halves of the
+        // work space: the rest of step s-1 may still read its half while
+        // step s slices; step s+1 slices only after step s's lookahead,
+        // which waits for the rest of step s-1)
+        uint8_t *ws = c->slice_ws + (sidx & 1) * c->slice_half_blocks * kSliceBlockBytes;
+        int32_t *wexp = c->slice_exp + (sidx & 1) * c->slice_half_blocks * kSliceRows * 2;
+        if (S.trsm_cnt > 0) {
+            // on the sliced path the solve also writes the slices of the rows it finishes
+            Prof pr(c, IPM_K_LARGE_PANEL, S.trsm_w, sd);
+            launch_panel_trsm(c->dp, c->fronts, c->trsm_items + S.trsm_off, c->trsm_slots + S.trsm_off, S.trsm_cnt,
+                              c->opt.nb, c->panel_ws, sd, c->trsm_sbase + S.trsm_off, use_sliced ? ws : nullptr,
+                              wexp, c->D, c->ctl);
             nl++;
         }
-        // Per 32-column step: diagonal block and TRSM, then the update split
-        // in two.  The tiles of the next panel's columns (lookahead) stay on
-        // the critical path; the remaining trailing tiles run on a third
-        // stream beside the next step's diagonal block.  Every entry still
-        // receives the panels' updates in panel order: the lookahead tiles of
-        // step s wait for the remaining tiles of step s-1.
-        cudaEvent_t prev_rest = nullptr;
-        for (const StepWork &S : W.steps) {
-            {
-                Prof pr(c, IPM_K_PIVOT_BLOCK, S.panel_w, sd);
-                launch_panel_diag(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->panel_items + S.panel_off,
-                                  S.panel_cnt, S.p0, c->opt.nb, c->panel_ws, sd);
+        const int32_t rest_tiles = S.tile_cnt - S.tile_cnt1;
+        const int32_t rest_alt = ((S.tc_cnt > 0 || S.st_cnt > 0) && !c->mixed_active) ? S.alt_cnt - S.alt_cnt1 : 0;
+        const int32_t rest_sliced = use_sliced ? S.st_cnt - S.st_cnt1 : 0;
+        cudaEvent_t this_rest = nullptr;
+        if (rest_tiles > 0 || rest_alt > 0 || rest_sliced > 0) {
+            cudaEvent_t ev_in = c->step_ev[2 * sidx], ev_out = c->step_ev[2 * sidx + 1];
+            cudaEventRecord(ev_in, sd);
+            cudaStreamWaitEvent(sd2, ev_in, 0);
+            if (rest_tiles > 0) {
+                Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w, sd2);
+                launch_large_update(c->dp, c->fronts, c->D, c->tile_items + S.tile_off + S.tile_cnt1, rest_tiles,
+                                    c->opt.nb, sd2);
+                nl++;
             }
+            if (rest_alt > 0) {
+                Prof pr(c, IPM_K_LARGE_UPDATE, S.alt_w, sd2);
+                launch_large_update(c->dp, c->fronts, c->D, c->alt_items + S.alt_off + S.alt_cnt1, rest_alt,
+                                    c->opt.nb, sd2);
+                nl++;
+            }
+            if (rest_sliced > 0) {
+                Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.st_w2, sd2);
+                launch_update_sliced(c->dp, c->fronts, c->sliced_tiles + S.st_off + S.st_cnt1, rest_sliced, ws, wexp,
+                                     c->ctl, sd2);
+                nl++;
+            }
+            cudaEventRecord(ev_out, sd2);
+            this_rest = ev_out;
+        }
+        sidx++;
+        if (prev_rest) cudaStreamWaitEvent(sd, prev_rest, 0);
+        if (S.tile_cnt1 > 0) {
+            Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w1, sd);
+            launch_large_update_strip(c->dp, c->fronts, c->D, c->tile_items + S.tile_off, S.tile_cnt1, c->opt.nb,
+                                      sd);
             nl++;
-            const bool use_tc = (S.tc_cnt > 0 || S.st_cnt > 0) && c->mixed_active;
-            const bool use_sliced = use_tc && S.st_cnt > 0;
-            // sliced path: the digit images of this step (alternate halves of the
-            // work space: the rest of step s-1 may still read its half while
-            // step s slices; step s+1 slices only after step s's lookahead,
-            // which waits for the rest of step s-1)
-            uint8_t *ws = c->slice_ws + (sidx & 1) * c->slice_half_blocks * kSliceBlockBytes;
-            int32_t *wexp = c->slice_exp + (sidx & 1) * c->slice_half_blocks * kSliceRows * 2;
-            if (S.trsm_cnt > 0) {
-                // on the sliced path the solve also writes the slices of the rows it finishes
-                Prof pr(c, IPM_K_LARGE_PANEL, S.trsm_w, sd);
-                launch_panel_trsm(c->dp, c->fronts, c->trsm_items + S.trsm_off, c->trsm_slots + S.trsm_off,
-                                  S.trsm_cnt, S.p0, c->opt.nb, c->panel_ws, sd, c->trsm_sbase + S.trsm_off,
-                                  use_sliced ? ws : nullptr, wexp, c->D, c->ctl);
+        }
+        if ((S.tc_cnt > 0 || S.st_cnt > 0) && !c->mixed_active && S.alt_cnt1 > 0) {
+            Prof pr(c, IPM_K_LARGE_UPDATE, S.alt_w1, sd);
+            launch_large_update_strip(c->dp, c->fronts, c->D, c->alt_items + S.alt_off, S.alt_cnt1, c->opt.nb, sd);
+            nl++;
+        } else if (use_sliced) {
+            if (S.st_cnt1 > 0) {
+                Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.st_w1, sd);
+                launch_update_sliced(c->dp, c->fronts, c->sliced_tiles + S.st_off, S.st_cnt1, ws, wexp, c->ctl, sd);
                 nl++;
             }
-            const int32_t rest_tiles = S.tile_cnt - S.tile_cnt1;
-            const int32_t rest_alt = ((S.tc_cnt > 0 || S.st_cnt > 0) && !c->mixed_active) ? S.alt_cnt - S.alt_cnt1 : 0;
-            const int32_t rest_sliced = use_sliced ? S.st_cnt - S.st_cnt1 : 0;
-            cudaEvent_t this_rest = nullptr;
-            if (rest_tiles > 0 || rest_alt > 0 || rest_sliced > 0) {
-                cudaEvent_t ev_in = c->step_ev[2 * sidx], ev_out = c->step_ev[2 * sidx + 1];
-                cudaEventRecord(ev_in, sd);
-                cudaStreamWaitEvent(sd2, ev_in, 0);
-                if (rest_tiles > 0) {
-                    Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w, sd2);
-                    launch_large_update(c->dp, c->fronts, c->D, c->tile_items + S.tile_off + S.tile_cnt1, rest_tiles,
-                                        S.p0, c->opt.nb, sd2);
-                    nl++;
+        } else if (use_tc) {
+            Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.tc_w, sd);
+            launch_large_update_tc(c->dp, c->fronts, c->D, c->tc_items + S.tc_off, S.tc_cnt, c->opt.nb, c->ctl, sd);
+            nl++;
+        }
+        prev_rest = this_rest;
+    };
+    if (c->dep_sched) {
+        // Dependency order: the steps of all large fronts in one sequence on
+        // the critical stream; each small-front level is issued on the
+        // caller's stream as soon as the steps its large children need are
+        // done, and a front's assembly waits for the level of its small
+        // children.  Every wait refers to an event recorded earlier in issue
+        // order, so a capture keeps them as edges.
+        const int32_t T = (int32_t)c->dsteps.size();
+        int32_t next = 0;  // next small-front level to issue
+        auto issue_small = [&](int32_t g) {
+            while (next < P.nlevels && c->small_dep[next] < g) {
+                if (!c->levels[next].small.empty()) {
+                    if (c->small_dep[next] >= 0) cudaStreamWaitEvent(st, c->done_ev[c->small_dep[next]], 0);
+                    emit_small(next);
                 }
-                if (rest_alt > 0) {
-                    Prof pr(c, IPM_K_LARGE_UPDATE, S.alt_w, sd2);
-                    launch_large_update(c->dp, c->fronts, c->D, c->alt_items + S.alt_off + S.alt_cnt1, rest_alt, S.p0,
-                                        c->opt.nb, sd2);
-                    nl++;
-                }
-                if (rest_sliced > 0) {
-                    Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.st_w2, sd2);
-                    launch_update_sliced(c->dp, c->fronts, c->sliced_tiles + S.st_off + S.st_cnt1, rest_sliced, ws,
-                                         wexp, c->ctl, sd2);
-                    nl++;
-                }
-                cudaEventRecord(ev_out, sd2);
-                this_rest = ev_out;
+                next++;
             }
-            sidx++;
-            if (prev_rest) cudaStreamWaitEvent(sd, prev_rest, 0);
-            if (S.tile_cnt1 > 0) {
-                Prof pr(c, IPM_K_LARGE_UPDATE, S.tile_w1, sd);
-                launch_large_update_strip(c->dp, c->fronts, c->D, c->tile_items + S.tile_off, S.tile_cnt1, S.p0,
-                                          c->opt.nb, sd);
+        };
+        for (int32_t g = 0; g < T; g++) {
+            issue_small(g);
+            const StepWork &S = c->dsteps[g];
+            if (S.small_wait >= 0) cudaStreamWaitEvent(sd, c->dep_ev[4 + 5 * S.small_wait], 0);
+            if (S.asm_cnt > 0) {
+                Prof pr(c, IPM_K_LARGE_ASSEMBLE, S.asm_w, sd);
+                launch_large_assemble(c->dp, V, c->fronts, c->asm_items + S.asm_off, c->asm_info + S.asm_off,
+                                      c->asm_cr, S.asm_cnt, sd);
                 nl++;
             }
-            if ((S.tc_cnt > 0 || S.st_cnt > 0) && !c->mixed_active && S.alt_cnt1 > 0) {
-                Prof pr(c, IPM_K_LARGE_UPDATE, S.alt_w1, sd);
-                launch_large_update_strip(c->dp, c->fronts, c->D, c->alt_items + S.alt_off, S.alt_cnt1, S.p0,
-                                          c->opt.nb, sd);
-                nl++;
-            } else if (use_sliced) {
-                if (S.st_cnt1 > 0) {
-                    Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.st_w1, sd);
-                    launch_update_sliced(c->dp, c->fronts, c->sliced_tiles + S.st_off, S.st_cnt1, ws, wexp, c->ctl,
-                                         sd);
-                    nl++;
-                }
-            } else if (use_tc) {
-                Prof pr(c, IPM_K_LARGE_UPDATE_TC, S.tc_w, sd);
-                launch_large_update_tc(c->dp, c->fronts, c->D, c->tc_items + S.tc_off, S.tc_cnt, S.p0, c->opt.nb,
-                                       c->ctl, sd);
-                nl++;
-            }
-            prev_rest = this_rest;
+            emit_step(S);
+            cudaEventRecord(c->done_ev[g], sd);
         }
         if (prev_rest) cudaStreamWaitEvent(sd, prev_rest, 0);
-        last_large = c->dep_ev[5 + 5 * l];
-        cudaEventRecord(last_large, sd);
+        cudaEventRecord(c->done_ev[T], sd);
+        issue_small(INT32_MAX);
+    } else {
+        // Level order: small fronts on the caller's stream and the large
+        // fronts of the same level on a second stream (fronts of one level
+        // are independent, Sec. 4.3), so a level costs the longer of the two
+        // instead of their sum.  Level l's small fronts wait for the large
+        // fronts of level l-1 and vice versa.
+        for (int32_t l = 0; l < P.nlevels; l++) {
+            const LevelWork &W = c->levels[l];
+            cudaEvent_t small_before = last_small, large_before = last_large;
+            if (!W.small.empty()) {
+                if (large_before) cudaStreamWaitEvent(st, large_before, 0);
+                emit_small(l);
+            }
+            if (W.asm_cnt == 0 && W.steps.empty()) continue;
+            if (small_before) cudaStreamWaitEvent(sd, small_before, 0);
+            const bool latency_bound = W.lvl_w.flops / 1.0e12 < c->tune_ratio * W.lvl_chain * 35e-6;
+            // (a latency-bound level keeps the FP64 level kernel in the tensor-core
+            // modes too: its work is too small for the tensor cores to matter)
+            if (c->opt.level_kernel && W.lvl_cnt > 0 && latency_bound) {
+                // FP64: all large-front work of the level in one dependency-driven launch
+                {
+                    Prof pr(c, IPM_K_LARGE_PANEL, W.lvl_w, sd);
+                    launch_large_level(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->lvl_items + W.lvl_off,
+                                       W.lvl_cnt, c->lvl_sync, W.lvl_ncnt, c->asm_info, c->asm_cr, c->panel_ws,
+                                       c->opt.nb, level_grid(c),
+                                       c->opt.spin_limit_log2 < 0 ? 0 : (1ll << c->opt.spin_limit_log2), sd);
+                }
+                nl++;
+                last_large = c->dep_ev[5 + 5 * l];
+                cudaEventRecord(last_large, sd);
+                continue;
+            }
+            if (W.asm_cnt > 0) {
+                Prof pr(c, IPM_K_LARGE_ASSEMBLE, W.asm_w, sd);
+                launch_large_assemble(c->dp, V, c->fronts, c->asm_items + W.asm_off, c->asm_info + W.asm_off,
+                                      c->asm_cr, W.asm_cnt, sd);
+                nl++;
+            }
+            prev_rest = nullptr;
+            for (const StepWork &S : W.steps) emit_step(S);
+            if (prev_rest) cudaStreamWaitEvent(sd, prev_rest, 0);
+            last_large = c->dep_ev[5 + 5 * l];
+            cudaEventRecord(last_large, sd);
+        }
     }
     // join: the second stream always rejoins the caller's stream (a capture
     // needs every forked stream joined back)
@@ -1527,6 +1691,7 @@ void ipm_default_options(ipm_options *o) {
     o->spin_limit_log2 = 24;
     o->level_kernel = 1;
     o->pivoting = 0;
+    o->schedule = IPM_SCHED_AUTO;
     o->verbose = 0;
 }
 
@@ -1542,7 +1707,8 @@ int ipm_create(ipm_ctx **out, const ipm_options *opt) {
         c->opt.level_kernel < 0 || c->opt.level_kernel > 1 ||
         (c->opt.precision != IPM_PREC_FP64 && c->opt.precision != IPM_PREC_MIXED &&
          c->opt.precision != IPM_PREC_SLICED) ||
-        c->opt.mixed_min_front < 1 || c->opt.pivoting < 0 || c->opt.pivoting > 1 ||
+        c->opt.mixed_min_front < 1 || c->opt.pivoting < 0 || c->opt.pivoting > 1 || c->opt.schedule < 0 ||
+        c->opt.schedule > IPM_SCHED_DEPENDENCY ||
         (c->opt.pivoting && c->opt.precision != IPM_PREC_FP64)) {
         delete c;
         return IPM_ERR_INVALID_ARG;
@@ -2167,6 +2333,9 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
     out->tune_level_ratio = c->tune_ratio;
     out->tune_level_ctas_per_sm = c->dev_ready ? level_grid(c) / c->sms : 0;
     out->graph_kernels = c->graph_kernels;
+    out->schedule = c->dep_sched ? IPM_SCHED_DEPENDENCY : IPM_SCHED_LEVELS;
+    out->steps_levels = c->steps_levels;
+    out->steps_dependency = c->steps_dependency;
     out->tune_ms = c->tune_ms;
     out->omega = c->omega;
     for (int i = 0; i < 16; i++) out->omega_hist[i] = c->omega_hist[i];

@@ -168,6 +168,7 @@ constexpr int64_t kRectSplit = 8192;  // split when k (f - k) reaches this
 struct PanelItem {
     int32_t s;       // supernode
     int32_t r0, r1;  // row range (local) handled by this block
+    int32_t p0;      // first column of the item's panel (diagonal blocks, triangular solves)
 };
 // Precomputed ranges of an assembly item (front columns [r0, r1) of a large
 // front): its original entries [o0, o1) and, at acr[2 * cr ...], one
@@ -179,6 +180,7 @@ struct TileItem {
     int32_t s;
     int32_t i0, j0;  // first local row / column of a kUpdTile x kUpdTile output tile
                      // (kUpdTile x kStripCols for the lookahead strips)
+    int32_t p0;      // first column of the panel whose update the tile applies
 };
 
 // Sliced tensor-core update (FP64-accurate Schur complement on bf16 tensor
@@ -224,30 +226,30 @@ void launch_small_fronts(const DevPlan &P, const DevVals &V, double *fronts, dou
                          cudaStream_t st);
 void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, const PanelItem *items,
                            const AsmItem *ainfo, const int32_t *acr, int32_t count, cudaStream_t st);
-// panel step 1 (diagonal block, one item per front; item.r1 = workspace slot)
+// panel step 1 (diagonal block of the panel [item.p0, item.p0 + nb), one item
+// per front; item.r1 = workspace slot)
 void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
-                       DevCtl *ctl,
-                       const PanelItem *items, int32_t count, int32_t p0, int32_t nb, double *pws, cudaStream_t st);
+                       DevCtl *ctl, const PanelItem *items, int32_t count, int32_t nb, double *pws, cudaStream_t st);
 // panel step 2 (rows below, kTrsmRowsHost rows per item; slots[i] = workspace slot of item i)
 // sbase[i] >= 0 (with sws non-null): item i also writes the digit slices of
 // its rows into the sliced update's work space (slice blocks from sbase[i])
 void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,
-                       int32_t p0, int32_t nb, const double *pws, cudaStream_t st, const int32_t *sbase = nullptr,
+                       int32_t nb, const double *pws, cudaStream_t st, const int32_t *sbase = nullptr,
                        uint8_t *sws = nullptr, int32_t *sexp = nullptr, const double *D = nullptr,
                        DevCtl *ctl = nullptr);
 constexpr int kTrsmRowsHost = 8;
 constexpr int kPanelWsHost = 32 * 33 + 32;
 void launch_large_update_strip(const DevPlan &P, double *fronts, const double *D, const TileItem *items,
-                               int32_t count, int32_t p0, int32_t w, cudaStream_t st);
+                               int32_t count, int32_t w, cudaStream_t st);
 void launch_large_level(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
                         DevCtl *ctl, const FactorItem *items, int32_t count, int32_t *sync, int32_t ncounters,
                         const AsmItem *ainfo, const int32_t *acr, double *pws, int32_t nb, int32_t grid,
                         long long spin_limit, cudaStream_t st);
 const void *large_level_kernel();
 void launch_large_update(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
-                         int32_t p0, int32_t w, cudaStream_t st);
+                         int32_t w, cudaStream_t st);
 void launch_large_update_tc(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
-                            int32_t p0, int32_t w, DevCtl *ctl, cudaStream_t st);
+                            int32_t w, DevCtl *ctl, cudaStream_t st);
 void launch_update_sliced(const DevPlan &P, double *fronts, const SlicedTile *items, int32_t count,
                           const uint8_t *ws, const int32_t *ws_exp, DevCtl *ctl, cudaStream_t st);
 int measure_fp64_peaks(double *out, int blocks, int iters, int reps, cudaStream_t st, double *dfma_tflops,

@@ -757,16 +757,16 @@ __global__ void __launch_bounds__(kBodyThreads) k_large_assemble(DevPlan P, DevV
 __global__ void __launch_bounds__(kBodyThreads) k_panel_diag(DevPlan P, DevVals V, double *__restrict__ fronts,
                                                               double *__restrict__ Dg, double *__restrict__ Dig,
                                                               double *__restrict__ dyng, DevCtl *ctl,
-                                                              const PanelItem *__restrict__ items, int p0, int nb,
+                                                              const PanelItem *__restrict__ items, int nb,
                                                               double *__restrict__ pws) {
     __shared__ double pool[kPoolDoubles];
     const PanelItem it = items[blockIdx.x];
-    body_diag(P, V, fronts, Dg, Dig, dyng, ctl, it.s, p0, nb, pws + (int64_t)it.r1 * kPanelWs, pool);
+    body_diag(P, V, fronts, Dg, Dig, dyng, ctl, it.s, it.p0, nb, pws + (int64_t)it.r1 * kPanelWs, pool);
 }
 
 __global__ void __launch_bounds__(kBodyThreads) k_panel_trsm(DevPlan P, double *__restrict__ fronts,
                                                               const PanelItem *__restrict__ items,
-                                                              const int32_t *slots, int p0, int nb,
+                                                              const int32_t *slots, int nb,
                                                               const double *__restrict__ pws,
                                                               const int32_t *__restrict__ sbase, uint8_t *sws,
                                                               int32_t *sexp, const double *__restrict__ Dg,
@@ -775,25 +775,24 @@ __global__ void __launch_bounds__(kBodyThreads) k_panel_trsm(DevPlan P, double *
     const PanelItem it = items[blockIdx.x];
     SliceOut so{nullptr, nullptr, 0, 0, nullptr, nullptr};
     if (sws && sbase[blockIdx.x] >= 0)
-        so = SliceOut{sws, sexp, sbase[blockIdx.x], min(p0 + nb, P.sn_k[it.s]), Dg, ctl};
-    body_trsm(P, fronts, it.s, it.r0, it.r1, p0, nb, pws + (int64_t)slots[blockIdx.x] * kPanelWs, pool, so);
+        so = SliceOut{sws, sexp, sbase[blockIdx.x], min(it.p0 + nb, P.sn_k[it.s]), Dg, ctl};
+    body_trsm(P, fronts, it.s, it.r0, it.r1, it.p0, nb, pws + (int64_t)slots[blockIdx.x] * kPanelWs, pool, so);
 }
 
 __global__ void __launch_bounds__(kBodyThreads) k_large_update(DevPlan P, double *__restrict__ fronts,
                                                                 const double *__restrict__ Dg,
-                                                                const TileItem *__restrict__ items, int p0, int w) {
+                                                                const TileItem *__restrict__ items, int w) {
     __shared__ double pool[kPoolDoubles];
     const TileItem it = items[blockIdx.x];
-    body_tile(P, fronts, Dg, it.s, it.i0, it.j0, p0, w, pool);
+    body_tile(P, fronts, Dg, it.s, it.i0, it.j0, it.p0, w, pool);
 }
 
 __global__ void __launch_bounds__(kBodyThreads) k_large_update_strip(DevPlan P, double *__restrict__ fronts,
                                                                         const double *__restrict__ Dg,
-                                                                        const TileItem *__restrict__ items, int p0,
-                                                                        int w) {
+                                                                        const TileItem *__restrict__ items, int w) {
     __shared__ double pool[kPoolDoubles];
     const TileItem it = items[blockIdx.x];
-    body_strip(P, fronts, Dg, it.s, it.i0, it.j0, p0, w, pool);
+    body_strip(P, fronts, Dg, it.s, it.i0, it.j0, it.p0, w, pool);
 }
 
 // Persistent level kernel: all large-front items of one tree level in one
@@ -1006,8 +1005,7 @@ __global__ void __launch_bounds__(kBkThreads) k_front_bk(DevPlan P, DevVals V, d
                                                          int32_t *__restrict__ bsz, int32_t *__restrict__ lperm,
                                                          double *__restrict__ dyn, DevCtl *ctl,
                                                          const int32_t *__restrict__ list, int nb, double alpha) {
-    __shared__ int sh_q, sh_r, sh_two, sh_swap_a, sh_swap_b;
-    __shared__ double sh_d;
+    __shared__ int sh_q, sh_two, sh_swap_a, sh_swap_b;
     const int s = list[blockIdx.x];
     const int f = P.sn_f[s], k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
     double *F = fronts + P.sn_off[s];
@@ -1226,28 +1224,28 @@ void launch_large_assemble(const DevPlan &P, const DevVals &V, double *fronts, c
 
 void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
                        DevCtl *ctl,
-                       const PanelItem *items, int32_t count, int32_t p0, int32_t nb, double *pws, cudaStream_t st) {
+                       const PanelItem *items, int32_t count, int32_t nb, double *pws, cudaStream_t st) {
     if (count <= 0) return;
-    k_panel_diag<<<count, kBodyThreads, 0, st>>>(P, V, fronts, D, Dinv, dyn, ctl, items, p0, nb, pws);
+    k_panel_diag<<<count, kBodyThreads, 0, st>>>(P, V, fronts, D, Dinv, dyn, ctl, items, nb, pws);
 }
 
 void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,
-                       int32_t p0, int32_t nb, const double *pws, cudaStream_t st, const int32_t *sbase,
+                       int32_t nb, const double *pws, cudaStream_t st, const int32_t *sbase,
                        uint8_t *sws, int32_t *sexp, const double *D, DevCtl *ctl) {
     if (count <= 0) return;
-    k_panel_trsm<<<count, kBodyThreads, 0, st>>>(P, fronts, items, slots, p0, nb, pws, sbase, sws, sexp, D, ctl);
+    k_panel_trsm<<<count, kBodyThreads, 0, st>>>(P, fronts, items, slots, nb, pws, sbase, sws, sexp, D, ctl);
 }
 
 void launch_large_update(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
-                         int32_t p0, int32_t w, cudaStream_t st) {
+                         int32_t w, cudaStream_t st) {
     if (count <= 0) return;
-    k_large_update<<<count, kBodyThreads, 0, st>>>(P, fronts, D, items, p0, w);
+    k_large_update<<<count, kBodyThreads, 0, st>>>(P, fronts, D, items, w);
 }
 
 void launch_large_update_strip(const DevPlan &P, double *fronts, const double *D, const TileItem *items,
-                               int32_t count, int32_t p0, int32_t w, cudaStream_t st) {
+                               int32_t count, int32_t w, cudaStream_t st) {
     if (count <= 0) return;
-    k_large_update_strip<<<count, kBodyThreads, 0, st>>>(P, fronts, D, items, p0, w);
+    k_large_update_strip<<<count, kBodyThreads, 0, st>>>(P, fronts, D, items, w);
 }
 
 void launch_large_level(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,

@@ -27,7 +27,7 @@ constexpr int kTcSmem = 4 * 16384 + 1024;    // four 128 x 32 fp32 tiles + align
 
 __global__ void __launch_bounds__(128) k_large_update_tc(DevPlan P, double *__restrict__ fronts,
                                                          const double *__restrict__ Dg,
-                                                         const TileItem *__restrict__ items, int p0, int w,
+                                                         const TileItem *__restrict__ items, int w,
                                                          DevCtl *ctl) {
     extern __shared__ uint8_t tc_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(128) k_large_update_tc(DevPlan P, double *__re
     __shared__ uint64_t mbar;
     __shared__ uint32_t tbase;
     const TileItem it = items[blockIdx.x];
-    const int s = it.s;
+    const int s = it.s, p0 = it.p0;
     const int f = P.sn_f[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
     w = min(w, P.sn_k[s] - p0);
     double *F = fronts + P.sn_off[s];
@@ -102,13 +102,13 @@ __global__ void __launch_bounds__(128) k_large_update_tc(DevPlan P, double *__re
 }  // namespace
 
 void launch_large_update_tc(const DevPlan &P, double *fronts, const double *D, const TileItem *items, int32_t count,
-                            int32_t p0, int32_t w, DevCtl *ctl, cudaStream_t st) {
+                            int32_t w, DevCtl *ctl, cudaStream_t st) {
     if (count <= 0) return;
     static uint64_t attr = 0;
     if (first_on_device(attr)) {
         cudaFuncSetAttribute(k_large_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     }
-    k_large_update_tc<<<count, 128, kTcSmem, st>>>(P, fronts, D, items, p0, w, ctl);
+    k_large_update_tc<<<count, 128, kTcSmem, st>>>(P, fronts, D, items, w, ctl);
 }
 
 }  // namespace ipm
