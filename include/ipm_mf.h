@@ -456,6 +456,18 @@ int ipm_set_profiling(ipm_ctx *ctx, int32_t enable);
  * IPM_K_COUNT entries to out (host array); reset != 0 clears the totals. */
 int ipm_kernel_stats(ipm_ctx *ctx, ipm_kernel_stat *out, int32_t reset);
 
+/* Launch trace of the profiled launches folded since the last call (the
+ * folding happens here and in ipm_kernel_stats): synchronises, then writes
+ * up to cap records in issue order (host arrays of cap entries): kernel
+ * class, stream index (streams numbered in order of first appearance),
+ * start and end in ms measured from the first launch folded in the same
+ * batch (the events of one batch are those recorded between two folds).
+ * *count receives the number of records (which may exceed cap); the trace
+ * is then cleared.  For timelines: which launches overlap, where the
+ * critical stream waits. */
+int ipm_kernel_trace(ipm_ctx *ctx, int32_t *cls, int32_t *stream, double *start_ms, double *end_ms, int32_t cap,
+                     int32_t *count);
+
 #ifdef __cplusplus
 }
 #endif

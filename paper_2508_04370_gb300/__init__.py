@@ -143,11 +143,12 @@ def _load():
     lib.ipm_measure_fp64_peak.argtypes = [ct.c_int32, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
     lib.ipm_set_profiling.argtypes = [P, ct.c_int32]
     lib.ipm_kernel_stats.argtypes = [P, P, ct.c_int32]
+    lib.ipm_kernel_trace.argtypes = [P, P, P, P, P, ct.c_int32, P]
     for name in ("ipm_create", "ipm_destroy", "ipm_analyse", "ipm_analyse_batch", "ipm_set_values", "ipm_factorise",
                  "ipm_solve", "ipm_iterate_host", "ipm_sync_status", "ipm_get_info", "ipm_get_symbolic",
                  "ipm_get_sizes", "ipm_get_factor", "ipm_graph_capture", "ipm_graph_launch", "ipm_launch_counts",
                  "ipm_set_profiling", "ipm_kernel_stats", "ipm_solve_noalloc", "ipm_test_recip_pivot",
-                 "ipm_measure_fp64_peak", "ipm_get_pivots"):
+                 "ipm_measure_fp64_peak", "ipm_get_pivots", "ipm_kernel_trace"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -372,6 +373,22 @@ def ipm_kernel_stats(ctx, reset=False):
         raise RuntimeError(f"ipm_kernel_stats failed ({rc})")
     return {name: dict(launches=a.launches, ms=a.ms, flops=a.flops, bytes=a.bytes)
             for name, a in zip(KERNEL_CLASSES, arr)}
+
+
+def ipm_kernel_trace(ctx, cap=1 << 20):
+    """Profiled launches since the last trace, in issue order: dict of numpy
+    arrays cls, stream, start_ms, end_ms (times from the batch's first launch)."""
+    cls = np.zeros(cap, np.int32)
+    stream = np.zeros(cap, np.int32)
+    t0 = np.zeros(cap, np.float64)
+    t1 = np.zeros(cap, np.float64)
+    n = ct.c_int32(0)
+    rc = _load().ipm_kernel_trace(ctx, _hptr(cls, np.int32), _hptr(stream, np.int32), _hptr(t0, np.float64),
+                                  _hptr(t1, np.float64), cap, ct.addressof(n))
+    if rc:
+        raise RuntimeError(f"ipm_kernel_trace failed ({rc})")
+    k = min(cap, n.value)
+    return dict(cls=cls[:k], stream=stream[:k], start_ms=t0[:k], end_ms=t1[:k], count=n.value)
 
 
 def declared_symbols():

@@ -77,6 +77,13 @@ struct ProfRec {
     int cls;
     cudaEvent_t e0, e1;
     double flops, bytes;
+    cudaStream_t st;
+};
+// One profiled launch in issue order: class, stream index (in order of first
+// use), start and end in ms from the first launch folded with it.
+struct TraceRec {
+    int32_t cls, stream;
+    double t0, t1;
 };
 
 
@@ -178,6 +185,8 @@ struct ipm_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<ProfRec> prof_pending;
+    std::vector<TraceRec> trace;              // launches folded since the last ipm_kernel_trace
+    std::vector<cudaStream_t> trace_streams;  // stream indices of the trace
     ipm_kernel_stat prof_tot[IPM_K_COUNT] = {};
     Work resid_w;
 };
@@ -212,14 +221,15 @@ struct Prof {
         if (c->prof_on) {
             cudaEvent_t e1 = next_event(c);
             cudaEventRecord(e1, st);
-            c->prof_pending.push_back({cls, e0, e1, flops, bytes});
+            c->prof_pending.push_back({cls, e0, e1, flops, bytes, st});
         }
     }
 };
 
 void fold_profile(ipm_ctx *c) {
+    const cudaEvent_t base = c->prof_pending.empty() ? nullptr : c->prof_pending.front().e0;
     for (const ProfRec &r : c->prof_pending) {
-        float ms = 0.f;
+        float ms = 0.f, a = 0.f, b = 0.f;
         if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) {
             cudaGetLastError();
             continue;
@@ -229,6 +239,14 @@ void fold_profile(ipm_ctx *c) {
         t.ms += ms;
         t.flops += r.flops;
         t.bytes += r.bytes;
+        if (cudaEventElapsedTime(&a, base, r.e0) != cudaSuccess || cudaEventElapsedTime(&b, base, r.e1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int32_t sid = 0;
+        while (sid < (int32_t)c->trace_streams.size() && c->trace_streams[sid] != r.st) sid++;
+        if (sid == (int32_t)c->trace_streams.size()) c->trace_streams.push_back(r.st);
+        c->trace.push_back({r.cls, sid, (double)a, (double)b});
     }
     c->prof_pending.clear();
     c->ev_used = 0;
@@ -761,10 +779,17 @@ int setup_device(ipm_ctx *c) {
             const int32_t p1 = std::min(p0 + c->opt.nb, k);
             panel_items.push_back({s, 0, slot_of[s], p0});
             const bool tc = c->opt.precision != IPM_PREC_FP64 && f >= c->opt.mixed_min_front;
+            // Sliced fronts take their full panels in pairs: the first panel of a
+            // pair updates only the second's columns, the second updates the
+            // whole trailing part with both (two chunks, K = 64).  A ragged last
+            // panel, and a full panel left over before it, stand alone.
+            const int32_t tpan = p0 / c->opt.nb, npair = 2 * ((k / c->opt.nb) / 2);
+            const bool pair_first = tpan < npair && tpan % 2 == 0;
+            const bool pair_second = tpan < npair && tpan % 2 == 1;
             // sliced fronts: the triangular solve writes the digit slices of the rows it finishes
-            const int32_t sbase = (tc && sliced && p1 < f) ? nblk : -1;
-            for (int32_t r = p1; r < f; r += kTrsmRowsHost) {
-                trsm_items.push_back({s, r, std::min(r + kTrsmRowsHost, f), p0});
+            const int32_t sbase = (tc && sliced && p1 < f) ? (nblk << 1) | (pair_second ? 1 : 0) : -1;
+            for (int32_t r = p1; r < f; r += kTrsmItemRowsHost) {
+                trsm_items.push_back({s, r, std::min(r + kTrsmItemRowsHost, f), p0});
                 trsm_slots.push_back(slot_of[s]);
                 trsm_sbase.push_back(sbase);
             }
@@ -773,25 +798,30 @@ int setup_device(ipm_ctx *c) {
             const bool next_panel = p1 < k;
             if (tc && sliced && p1 < f) {
                 // slice blocks of rows p1.. (written by the triangular solve),
-                // then every 128 x 32 tile of the lower trailing part, row
+                // then the 128 x 32 tiles of the lower trailing part (only the
+                // next panel's columns after the first panel of a pair), row
                 // blocks aligned with the slice blocks
                 const int32_t base = nblk;
+                const int32_t kc = pair_second ? 2 : 1;
+                const double wk = pair_second ? w + c->opt.nb : w;  // columns of the product
+                const int32_t jend = pair_first ? p1 + kSliceCols : f;
                 nblk += (f - p1 + kSliceRows - 1) / kSliceRows;
-                for (int32_t j0 = p1; j0 < f; j0 += kSliceCols)
+                for (int32_t j0 = p1; j0 < jend; j0 += kSliceCols)
                     for (int32_t b = (j0 - p1) / kSliceRows; p1 + b * kSliceRows < f; b++) {
                         const int32_t i0 = p1 + b * kSliceRows;
                         const bool la = next_panel && j0 == p1;
                         (la ? t1 : t2).push_back({s, i0, j0, base + b, base + (j0 - p1) / kSliceRows,
-                                                  (j0 - p1) % kSliceRows});
-                        // lower entries of the tile times 2 w flops; its C read and write
+                                                  (j0 - p1) % kSliceRows, kc});
+                        // lower entries of the tile times 2 wk flops; its C read and write
                         double e = 0.0;
                         for (int32_t j = j0; j < std::min(j0 + kSliceCols, f); j++)
                             e += std::max(0, std::min(i0 + kSliceRows, f) - std::max(i0, j));
                         Work &tw = la ? S.st_w1 : S.st_w2;
-                        tw.flops += 2.0 * w * e;
-                        tw.bytes += 16.0 * e + 2.0 * kSlices * 2.0 * w * (kSliceRows + kSliceCols);
+                        tw.flops += 2.0 * wk * e;
+                        tw.bytes += 16.0 * e + 2.0 * kSlices * 2.0 * wk * (kSliceRows + kSliceCols);
                     }
-                S.trsm_w.bytes += 2.0 * kSlices * 2.0 * rest * w;  // the slices the solve writes
+                S.trsm_w.bytes += 2.0 * kSlices * 2.0 * rest * wk;  // the slices the solve writes
+                if (pair_second) S.trsm_w.bytes += 8.0 * rest * c->opt.nb;  // the first panel's rows it re-reads
             } else if (tc) {
                 for (int32_t j0 = p1; j0 < f; j0 += kTcTile)
                     for (int32_t i0 = j0; i0 < f; i0 += kTcTile) tc_items.push_back({s, i0, j0, p0});
@@ -2585,6 +2615,28 @@ int ipm_kernel_stats(ipm_ctx *c, ipm_kernel_stat *out, int32_t reset) {
     fold_profile(c);
     if (out) std::memcpy(out, c->prof_tot, sizeof(c->prof_tot));
     if (reset) std::memset(c->prof_tot, 0, sizeof(c->prof_tot));
+    return IPM_OK;
+}
+
+int ipm_kernel_trace(ipm_ctx *c, int32_t *cls, int32_t *stream, double *start_ms, double *end_ms, int32_t cap,
+                     int32_t *count) {
+    if (!c || cap < 0 || !count || (cap > 0 && (!cls || !stream || !start_ms || !end_ms)))
+        return IPM_ERR_INVALID_ARG;
+    if (c->dev_ready) {
+        cudaSetDevice(c->opt.device);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return to_err(e);
+    }
+    fold_profile(c);
+    *count = (int32_t)c->trace.size();
+    const int32_t n = std::min(cap, *count);
+    for (int32_t i = 0; i < n; i++) {
+        cls[i] = c->trace[i].cls;
+        stream[i] = c->trace[i].stream;
+        start_ms[i] = c->trace[i].t0;
+        end_ms[i] = c->trace[i].t1;
+    }
+    c->trace.clear();
     return IPM_OK;
 }
 

@@ -184,16 +184,21 @@ struct TileItem {
 };
 
 // Sliced tensor-core update (FP64-accurate Schur complement on bf16 tensor
-// cores).  After a panel [p0, p1) of a large front, every trailing row r >= p1
-// of both panel operands, L(r, q) and L(r, q) d_q, is scaled by a power of two
-// per row and split into kSlices balanced 7-bit digits; one slice block holds
-// 128 rows.
+// cores).  Panels of a large front are taken in pairs: after the first panel
+// of a pair only the second panel's columns are updated; after the second,
+// every trailing row r >= p1 of both panel operands over both panels' 64
+// columns, L(r, q) and L(r, q) d_q, is scaled by one power of two per row
+// and split into kSlices balanced 7-bit digits, and the whole trailing part
+// receives the two panels' update at once (K = 64).  One slice block holds
+// 128 rows: one chunk of digit images per 32 columns.
 constexpr int kSlices = 8;                           // 8 x 7 = 56 bits per operand
 constexpr int kSliceRows = 128;                      // rows per slice block (the MMA's M)
-constexpr int kSliceCols = 32;                       // output columns per tile (the MMA's N)
+constexpr int kSliceCols = 32;                       // output columns per tile (the MMA's N), columns per chunk
+constexpr int kSliceChunks = 2;                      // chunks of 32 columns per slice block (K <= 64)
 constexpr int64_t kSlicePairBytes = 128 * 128;       // two slices of 128 rows x 32 bf16, one swizzled image
 constexpr int64_t kSliceOperandBytes = 4 * kSlicePairBytes;
-constexpr int64_t kSliceBlockBytes = 2 * kSliceOperandBytes;  // operand A (L), then operand B (L d)
+constexpr int64_t kSliceChunkBytes = 2 * kSliceOperandBytes;  // operand A (L), then operand B (L d)
+constexpr int64_t kSliceBlockBytes = kSliceChunks * kSliceChunkBytes;
 
 struct SlicedTile {
     int32_t s;
@@ -201,6 +206,7 @@ struct SlicedTile {
     int32_t blk_a;      // slice block of rows i0 ..
     int32_t blk_b;      // slice block holding columns j0 .. j0+31 as rows,
     int32_t roff_b;     // at row offset roff_b (a multiple of 32) inside it
+    int32_t kc;         // chunks of the product: 1 (one panel, K <= 32) or 2 (a pair of panels, K <= 64)
 };
 
 // One item of the persistent level kernel (large fronts of one tree level):
@@ -232,12 +238,14 @@ void launch_panel_diag(const DevPlan &P, const DevVals &V, double *fronts, doubl
                        DevCtl *ctl, const PanelItem *items, int32_t count, int32_t nb, double *pws, cudaStream_t st);
 // panel step 2 (rows below, kTrsmRowsHost rows per item; slots[i] = workspace slot of item i)
 // sbase[i] >= 0 (with sws non-null): item i also writes the digit slices of
-// its rows into the sliced update's work space (slice blocks from sbase[i])
+// its rows into the sliced update's work space (slice blocks from
+// sbase[i] >> 1; bit 0 set: the second panel of a pair, two chunks)
 void launch_panel_trsm(const DevPlan &P, double *fronts, const PanelItem *items, const int32_t *slots, int32_t count,
                        int32_t nb, const double *pws, cudaStream_t st, const int32_t *sbase = nullptr,
                        uint8_t *sws = nullptr, int32_t *sexp = nullptr, const double *D = nullptr,
                        DevCtl *ctl = nullptr);
-constexpr int kTrsmRowsHost = 8;
+constexpr int kTrsmRowsHost = 8;       // rows of a triangular-solve chunk of the level kernel
+constexpr int kTrsmItemRowsHost = 32;  // rows of a triangular-solve item of the one-launch-per-step kernel
 constexpr int kPanelWsHost = 32 * 33 + 32;
 void launch_large_update_strip(const DevPlan &P, double *fronts, const double *D, const TileItem *items,
                                int32_t count, int32_t w, cudaStream_t st);

@@ -340,13 +340,15 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
 // because in the persistent kernel other CTAs of the same launch wrote
 // them.  All bodies share one shared-memory pool sized for the largest.
 constexpr int kBodyThreads = 256;
-constexpr int kPoolDoubles = 2 * 32 * 33;  // a 32 x 32 update tile's two operands
+constexpr int kPoolDoubles = 2 * 32 * 33 + 32;  // a 32 x 32 update tile's two operands; L_11, 1/d and a 32 x 33 tile
 
 // Assembly of columns [c_lo, c_hi) of front s into its slab in global memory:
 // zero the columns, place the original entries (a precomputed contiguous
 // range), then add the children's contribution-block columns that land in
 // the range (precomputed per child), children in ascending order.  Child
 // descriptors are staged in shared memory 64 at a time.
+constexpr int kAsmBatch = 8;  // contribution-block rows per lane per round of the extend-add
+
 __device__ __forceinline__ void body_assemble(const DevPlan &P, const DevVals &V, double *__restrict__ fronts, int s,
                                               int c_lo, int c_hi, const AsmItem &ai, const int32_t *__restrict__ acr,
                                               double *pool) {
@@ -382,8 +384,28 @@ __device__ __forceinline__ void body_assemble(const DevPlan &P, const DevVals &V
             const double *CB = fronts + ch_cb[u];
             const int32_t *map = P.relmap + ch_map[u];
             for (int jj = a + warp; jj < b; jj += NT / 32) {
-                const int pj = map[jj];
-                for (int ii = jj + lane; ii < cc; ii += 32) F[(int64_t)pj * ld + map[ii]] += CB[(int64_t)jj * ldc + ii];
+                double *Fj = F + (int64_t)map[jj] * ld;
+                const double *CBj = CB + (int64_t)jj * ldc;
+                // kAsmBatch rows per lane per round, every load issued before
+                // any store: the entries one child adds to are distinct, so
+                // the batch's loads are independent of its stores (the child
+                // block and the front never overlap), and each entry still
+                // receives its children's terms in ascending child order
+                for (int i0 = jj + lane; i0 < cc; i0 += 32 * kAsmBatch) {
+                    int32_t mi[kAsmBatch];
+                    double cv[kAsmBatch], fv[kAsmBatch];
+#pragma unroll
+                    for (int t = 0; t < kAsmBatch; t++) {
+                        const int ii = i0 + 32 * t;
+                        mi[t] = ii < cc ? __ldg(map + ii) : -1;
+                        cv[t] = ii < cc ? __ldcg(CBj + ii) : 0.0;
+                    }
+#pragma unroll
+                    for (int t = 0; t < kAsmBatch; t++) fv[t] = mi[t] >= 0 ? Fj[mi[t]] : 0.0;
+#pragma unroll
+                    for (int t = 0; t < kAsmBatch; t++)
+                        if (mi[t] >= 0) Fj[mi[t]] = fv[t] + cv[t];
+                }
             }
             __syncthreads();
         }
@@ -556,78 +578,120 @@ __device__ __forceinline__ void body_diag(const DevPlan &P, const DevVals &V, do
 //   u_iq = F_iq - sum_{q' < q} u_iq' L_qq',   l_iq = u_iq / d_q,
 // so step q' broadcasts the finished u_iq' and every lane q > q' applies one
 // FMA: 32 dependent steps per row instead of 528 per thread when a thread
-// owns a whole row.
+// owns a whole row.  An item holds up to kTrsmItemRows rows (chunks of the
+// level kernel hold kTrsmRows); warp w solves rows w, w + 8, w + 16 and
+// w + 24 together, four independent chains on the same L_11, so a CTA costs
+// about one chain's latency.
 constexpr int kTrsmRows = 8;
-static_assert(kTrsmRows == kTrsmRowsHost, "host and device row chunks differ");
+constexpr int kTrsmItemRows = 32;
+static_assert(kTrsmRows == kTrsmRowsHost && kTrsmItemRows == kTrsmItemRowsHost, "host and device row chunks differ");
 static_assert(32 * kTrsmRows == kBodyThreads, "one warp per row");
 
 // Where the triangular solve of a sliced front writes the digit slices of the
 // rows it finishes (ws == nullptr: no slicing): block base + (row - p1) / 128,
-// row (row - p1) % 128 of the step's work space.
+// row (row - p1) % 128 of the step's work space.  pair = 0: one chunk, this
+// panel's columns; pair = 1 (the second panel of a pair): two chunks with one
+// row scale, the previous panel's 32 columns (final since the last step)
+// and this panel's.
 struct SliceOut {
     uint8_t *ws;
     int32_t *exps;
     int32_t base;
+    int32_t pair;
     int32_t p1;
     const double *D;
     DevCtl *ctl;
 };
 
+template <int RW>  // rows per warp, solved together: items of up to 8 RW rows
 __device__ __forceinline__ void body_trsm(const DevPlan &P, double *__restrict__ fronts, int s, int r0, int r1,
                                           int p0, int nb, const double *__restrict__ ws, double *pool,
-                                          const SliceOut so = SliceOut{nullptr, nullptr, 0, 0, nullptr, nullptr}) {
-    double *Wd = pool;                                                     // 32 x 33 + 32
-    double(*T)[kTrsmRows + 1] = reinterpret_cast<double(*)[kTrsmRows + 1]>(pool + 32 * 33 + 32);  // [32][9]
+                                          const SliceOut so = SliceOut{nullptr, nullptr, 0, 0, 0, nullptr, nullptr}) {
+    constexpr int kRows = kTrsmRows * RW;
+    constexpr int TP = kRows + 1;  // padded row count of the tile
+    double *Wd = pool;                             // 32 x 33 + 32
+    double(*T)[TP] = reinterpret_cast<double(*)[TP]>(pool + 32 * 33 + 32);  // [32 columns][rows]
     const int k = P.sn_k[s], ld = P.sn_ld[s];
     const int w = min(p0 + nb, k) - p0;
-    const int nr = r1 - r0;
+    const int nr = r1 - r0;  // <= kRows
     double *F = fronts + P.sn_off[s];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     {
         // all loads in flight before the shared-memory stores
         constexpr int U = (32 * 33 + 32 + kBodyThreads - 1) / kBodyThreads;
-        double v[U];
+        constexpr int V = 32 * kRows / kBodyThreads;
+        double v[U], tv[V];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const int t = tid + u * kBodyThreads;
             v[u] = t < 32 * 33 + 32 ? __ldcg(ws + t) : 0.0;
         }
-        const int q = tid / kTrsmRows, r = tid % kTrsmRows;
-        const double tv = (q < w && r < nr) ? __ldcg(F + (int64_t)(p0 + q) * ld + r0 + r) : 0.0;
+#pragma unroll
+        for (int u = 0; u < V; u++) {
+            const int t = tid + u * kBodyThreads, q = t / kRows, r = t % kRows;
+            tv[u] = (q < w && r < nr) ? __ldcg(F + (int64_t)(p0 + q) * ld + r0 + r) : 0.0;
+        }
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const int t = tid + u * kBodyThreads;
             if (t < 32 * 33 + 32) Wd[t] = v[u];
         }
-        T[q][r] = tv;
+#pragma unroll
+        for (int u = 0; u < V; u++) {
+            const int t = tid + u * kBodyThreads;
+            T[t / kRows][t % kRows] = tv[u];
+        }
     }
     __syncthreads();
     if (warp < nr) {
+        // rows warp, warp + 8, ... : RW independent chains share L_11 in registers
         double Lr[32];
 #pragma unroll
-        for (int q = 0; q < 32; q++) Lr[q] = Wd[lane * 33 + q];
-        double t = T[lane][warp];
+        for (int c = 0; c < 32; c++) Lr[c] = Wd[lane * 33 + c];
+        double t[RW];
 #pragma unroll
-        for (int q = 0; q < 31; q++) {
-            const double u = __shfl_sync(0xffffffffu, t, q);
-            if (lane > q) t -= u * Lr[q];
+        for (int j = 0; j < RW; j++) t[j] = T[lane][warp + kTrsmRows * j];
+#pragma unroll
+        for (int c = 0; c < 31; c++) {
+#pragma unroll
+            for (int j = 0; j < RW; j++) {
+                const double u = __shfl_sync(0xffffffffu, t[j], c);
+                if (lane > c) t[j] -= u * Lr[c];
+            }
         }
-        const double lv = t * Wd[32 * 33 + lane];
-        T[lane][warp] = lv;
-        if (so.ws) {
-            // the finished row, sliced for the tensor-core update
-            const int row = r0 + warp;
-            const int c0 = P.sn_c0[s];
-            const double dq = lane < w ? so.D[c0 + p0 + lane] : 0.0;
-            const int blk = so.base + (row - so.p1) / kSliceRows;
-            const bool bad = sliced::slice_row_warp(lane < w ? lv : 0.0, dq, so.ws + (int64_t)blk * kSliceBlockBytes,
-                                                    so.exps + (int64_t)blk * kSliceRows * 2, (row - so.p1) % kSliceRows);
-            if (bad && lane == 0) atomicOr(&so.ctl->status, kStatNonFinite);
+        const double dinv = Wd[32 * 33 + lane];
+#pragma unroll
+        for (int j = 0; j < RW; j++) {
+            const int rr = warp + kTrsmRows * j;
+            if (rr >= nr) break;  // uniform over the warp
+            const double lv = t[j] * dinv;
+            T[lane][rr] = lv;
+            if (so.ws) {
+                // the finished row, sliced for the tensor-core update
+                const int row = r0 + rr;
+                const int c0 = P.sn_c0[s];
+                const double dq = lane < w ? so.D[c0 + p0 + lane] : 0.0;
+                const double lq = lane < w ? lv : 0.0;
+                const int blk = so.base + (row - so.p1) / kSliceRows;
+                uint8_t *bp = so.ws + (int64_t)blk * kSliceBlockBytes;
+                int32_t *ep = so.exps + (int64_t)blk * kSliceRows * 2;
+                bool bad;
+                if (so.pair) {
+                    // the previous panel (always 32 columns) as chunk 0, this one as chunk 1
+                    const double l2[2] = {__ldcg(F + (int64_t)(p0 - 32 + lane) * ld + row), lq};
+                    const double d2[2] = {so.D[c0 + p0 - 32 + lane], dq};
+                    bad = sliced::slice_row_warp<2>(l2, d2, bp, ep, (row - so.p1) % kSliceRows);
+                } else {
+                    const double l1[1] = {lq}, d1[1] = {dq};
+                    bad = sliced::slice_row_warp<1>(l1, d1, bp, ep, (row - so.p1) % kSliceRows);
+                }
+                if (bad && lane == 0) atomicOr(&so.ctl->status, kStatNonFinite);
+            }
         }
     }
     __syncthreads();
-    {
-        const int q = tid / kTrsmRows, r = tid % kTrsmRows;
+    for (int t = tid; t < 32 * kRows; t += kBodyThreads) {
+        const int q = t / kRows, r = t % kRows;
         if (q < w && r < nr) F[(int64_t)(p0 + q) * ld + r0 + r] = T[q][r];
     }
 }
@@ -773,10 +837,12 @@ __global__ void __launch_bounds__(kBodyThreads) k_panel_trsm(DevPlan P, double *
                                                               DevCtl *ctl) {
     __shared__ double pool[kPoolDoubles];
     const PanelItem it = items[blockIdx.x];
-    SliceOut so{nullptr, nullptr, 0, 0, nullptr, nullptr};
+    SliceOut so{nullptr, nullptr, 0, 0, 0, nullptr, nullptr};
     if (sws && sbase[blockIdx.x] >= 0)
-        so = SliceOut{sws, sexp, sbase[blockIdx.x], min(it.p0 + nb, P.sn_k[it.s]), Dg, ctl};
-    body_trsm(P, fronts, it.s, it.r0, it.r1, it.p0, nb, pws + (int64_t)slots[blockIdx.x] * kPanelWs, pool, so);
+        so = SliceOut{sws, sexp, sbase[blockIdx.x] >> 1, sbase[blockIdx.x] & 1, min(it.p0 + nb, P.sn_k[it.s]), Dg,
+                      ctl};
+    body_trsm<kTrsmItemRows / kTrsmRows>(P, fronts, it.s, it.r0, it.r1, it.p0, nb,
+                                         pws + (int64_t)slots[blockIdx.x] * kPanelWs, pool, so);
 }
 
 __global__ void __launch_bounds__(kBodyThreads) k_large_update(DevPlan P, double *__restrict__ fronts,
@@ -859,7 +925,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_large_level(DevPlan P, DevVals
                           pool);
                 break;
             case kItemTrsm:
-                body_trsm(P, fronts, it.s, it.a, it.b, it.t * nb, nb, pws + (int64_t)it.aux * kPanelWs, pool);
+                body_trsm<1>(P, fronts, it.s, it.a, it.b, it.t * nb, nb, pws + (int64_t)it.aux * kPanelWs, pool);
                 break;
             case kItemStrip: body_strip(P, fronts, Dg, it.s, it.a, it.b, it.t * nb, nb, pool); break;
             default: body_tile(P, fronts, Dg, it.s, it.a, it.b, it.t * nb, nb, pool); break;

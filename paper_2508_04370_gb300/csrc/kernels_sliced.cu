@@ -11,22 +11,29 @@
 // al.):
 //
 //  1. slicing, in the panel's triangular solve (k_panel_trsm holds each
-//     finished row of L in one warp): after a 32-column panel [p0, p1), every trailing row r
-//     of the two panel operands a_rq = L(r, q) 2^h_q and
-//     b_rq = L(r, q) d_q 2^-h_q (h_q = floor(log2 |d_q| / 2): an exact
-//     balancing of each column, so that a_rq^2 and b_rq^2 are both within a
-//     factor 4 of L(r, q)^2 |d_q|, whatever the spread of the pivots) gets a
+//     finished row of L in one warp).  Panels are taken in pairs: after the
+//     first panel of a pair only the second panel's 32 columns are updated
+//     (one chunk); after the second panel the whole trailing part receives
+//     both panels' update at once (two chunks, K = 64), which halves the
+//     read-modify-write passes over the trailing part and the epilogue work
+//     per panel.  Every trailing row r of the two panel operands
+//     a_rq = L(r, q) 2^h_q and b_rq = L(r, q) d_q 2^-h_q over the chunks'
+//     columns (h_q = floor(log2 |d_q| / 2): an exact balancing of each
+//     column, so that a_rq^2 and b_rq^2 are both within a factor 4 of
+//     L(r, q)^2 |d_q|, whatever the spread of the pivots) gets one
 //     power-of-two scale 2^E_r with |entries| < 2^E_r and is rounded to the
 //     56-bit integers X_rq = rint(a_rq 2^(56 - E_r)), written as eight
 //     balanced base-2^7 digits X = sum_t x_t 2^(7 (7 - t)), |x_t| <= 64
 //     (|x_0| <= 128), each exactly a bf16.  The digits go to a work space in
-//     the 128-byte-swizzled K-major image the tensor cores read.
-//  2. k_update_sliced: one CTA per 128 x 32 output tile; the digit images
-//     arrive by bulk copies (TMA), one thread issues the 36 digit products
-//     with t + u <= 7 (72 tcgen05.mma.kind::f16, K = 16) into eight TMEM
-//     accumulators S_d, d = t + u.  Digit products are at most 2^14 and a
-//     panel has at most 32 columns, so every S_d is an integer below 2^22
-//     and FP32 accumulation is exact.  The epilogue forms
+//     the 128-byte-swizzled K-major image the tensor cores read, one image
+//     set per chunk.
+//  2. k_update_sliced: one CTA per 128 x 32 output tile; per chunk the digit
+//     images arrive by bulk copies (TMA) and one thread issues the 36 digit
+//     products with t + u <= 7 (72 tcgen05.mma.kind::f16, K = 16) into eight
+//     TMEM accumulators S_d, d = t + u, kept across the chunks.  For a
+//     given d at most two products involve x_0 or y_0 (up to 128 x 64) and
+//     the others are at most 64 x 64, so |S_d| <= 40960 K <= 2^21.4 for
+//     K <= 64 and FP32 accumulation is exact.  The epilogue forms
 //     hi = sum_{d<4} S_d 2^(7 (3 - d)) and lo = sum_{d>=4} S_d 2^(7 (7 - d))
 //     exactly in integers, the product
 //     sum_q a_iq b_jq ~= 2^(E_i + E_j - 63) (hi 2^28 + lo)
@@ -34,7 +41,7 @@
 //     subtracts it from the FP64 entry: one FP64 instruction per entry.
 // Error per entry: operand rounding 2^-57 and the dropped digit products
 // (t + u >= 8) below 2^-55, relative to 2^(E_i + E_j) per column of the
-// panel, that is about 2^-52 sqrt(max_q L_iq^2 |d_q| max_q L_jq^2 |d_q|);
+// chunks, that is about 2^-52 sqrt(max_q L_iq^2 |d_q| max_q L_jq^2 |d_q|);
 // FP64 GEMM's is 2^-53 of each |L_iq d_q L_jq|, summed.  Without the
 // balancing a panel mixing pivots of size delta and of size 1/delta pairs
 // the largest a of one column with the largest b of another, and the
@@ -92,7 +99,7 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
     extern __shared__ uint8_t sl_raw[];
     uint8_t *A = (uint8_t *)(((uintptr_t)sl_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *B = A + 4 * kSlicePairBytes;
-    __shared__ uint64_t bar_load, bar_mma;
+    __shared__ uint64_t bar_load, bar_mid, bar_mma;
     __shared__ uint32_t tbase;
     __shared__ int32_t eb_col[kSliceCols];
     const SlicedTile it = items[blockIdx.x];
@@ -103,6 +110,7 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
     if (warp == 0) tc::tmem_alloc(&tbase, 256);  // 8 accumulators x 32 columns
     if (tid == 0) {
         tc::mbar_init(&bar_load, 1);
+        tc::mbar_init(&bar_mid, 1);
         tc::mbar_init(&bar_mma, 1);
         tc::fence_mbar_init();
     }
@@ -111,21 +119,21 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tbase;
-    const uint8_t *srcA = ws + (int64_t)it.blk_a * kSliceBlockBytes;
-    const uint8_t *srcB = ws + (int64_t)it.blk_b * kSliceBlockBytes + kSliceOperandBytes;
-    if (tid == 0) {
+    // One thread streams the kc chunks (32 columns of the panel pair each)
+    // through the one buffer: copy, 72 MMAs into the same accumulators, wait
+    // for them before the next copy.  bar_mma completes once every MMA it
+    // issued has (also after a failed wait, so that TMEM is never freed
+    // under running MMAs).
+    auto chunk_copy = [&](int ch) {
+        const uint8_t *srcA = ws + (int64_t)it.blk_a * kSliceBlockBytes + ch * kSliceChunkBytes;
+        const uint8_t *srcB = ws + (int64_t)it.blk_b * kSliceBlockBytes + ch * kSliceChunkBytes + kSliceOperandBytes;
         tc::mbar_expect_tx(&bar_load, (uint32_t)(4 * kSlicePairBytes + 4 * 4096));
         tc::bulk_g2s(A, srcA, (uint32_t)(4 * kSlicePairBytes), &bar_load);
 #pragma unroll
         for (int pr = 0; pr < 4; pr++)
             tc::bulk_g2s(B + pr * 4096, srcB + pr * kSlicePairBytes + it.roff_b * 128, 4096, &bar_load);
-    }
-    bool ok = tc::mbar_wait(&bar_load, 0, kSlicePolls);
-    if (!ok) {
-        if (lane == 0) atomicOr(&ctl->status, kStatTimeout);
-        tc::mbar_wait(&bar_load, 0, kSlicePolls);  // let the copies in flight land before the CTA exits
-    }
-    if (ok && tid == 0) {
+    };
+    auto chunk_mma = [&](int ch) {
         tc::fence_after_sync();
         constexpr uint32_t id = tc::idesc_bf16(kSliceRows, kSliceCols);
         const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(B);
@@ -138,10 +146,21 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
                 for (int kk = 0; kk < 2; kk++) {
                     const uint64_t ad = tc::smem_desc(a0 + (t >> 1) * (uint32_t)kSlicePairBytes + (t & 1) * 64 + kk * 32);
                     const uint64_t bd = tc::smem_desc(b0 + (u >> 1) * 4096u + (u & 1) * 64 + kk * 32);
-                    tc::mma_bf16(tmem + (uint32_t)(d * kSliceCols), ad, bd, id, (t > 0 || kk > 0) ? 1u : 0u);
+                    tc::mma_bf16(tmem + (uint32_t)(d * kSliceCols), ad, bd, id, (ch > 0 || t > 0 || kk > 0) ? 1u : 0u);
                 }
             }
-        tc::commit_to(&bar_mma);
+    };
+    const int kc = it.kc;
+    bool lead_ok = true;  // thread 0: every copy and MMA of the tile issued
+    if (tid == 0) {
+        chunk_copy(0);
+        if (tc::mbar_wait(&bar_load, 0, kSlicePolls)) {
+            chunk_mma(0);
+        } else {
+            atomicOr(&ctl->status, kStatTimeout);
+            tc::mbar_wait(&bar_load, 0, kSlicePolls);  // let the copies in flight land before the CTA exits
+            lead_ok = false;
+        }
     }
     // the tile's FP64 entries of this thread's row and column half, fetched
     // while the copies and the MMAs run (independent loads; lower part only)
@@ -159,13 +178,32 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
         live |= (uint32_t)v << c;
         cv[c] = v ? F[(int64_t)col * ld + row] : 0.0;
     }
-    if (ok) {
-        ok = tc::mbar_wait(&bar_mma, 0, kSlicePolls);
-        if (!ok) {
-            if (lane == 0) atomicOr(&ctl->status, kStatTimeout);
-            tc::mbar_wait(&bar_mma, 0, kSlicePolls);  // the MMAs must finish before TMEM is freed
+    if (tid == 0) {
+        for (int ch = 1; ch < kc && lead_ok; ch++) {
+            // the buffer is free once the previous chunk's MMAs are done
+            tc::commit_to(&bar_mid);
+            if (!tc::mbar_wait(&bar_mid, (ch - 1) & 1, kSlicePolls)) {
+                atomicOr(&ctl->status, kStatTimeout);
+                lead_ok = false;
+                break;
+            }
+            chunk_copy(ch);
+            if (!tc::mbar_wait(&bar_load, ch & 1, kSlicePolls)) {
+                atomicOr(&ctl->status, kStatTimeout);
+                tc::mbar_wait(&bar_load, ch & 1, kSlicePolls);
+                lead_ok = false;
+                break;
+            }
+            chunk_mma(ch);
         }
+        tc::commit_to(&bar_mma);
     }
+    bool ok = tc::mbar_wait(&bar_mma, 0, kSlicePolls);
+    if (!ok) {
+        atomicOr(&ctl->status, kStatTimeout);
+        tc::mbar_wait(&bar_mma, 0, kSlicePolls);  // the MMAs must finish before TMEM is freed
+    }
+    ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the TMEM loads below are warp-collective
     tc::fence_after_sync();
     if (ok) {
         const int Ea = ws_exp[((int64_t)it.blk_a * kSliceRows + r) * 2 + 0];
@@ -181,7 +219,7 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
             tc::tmem_wait_ld();
 #pragma unroll
             for (int c = 0; c < 8; c++)
-                // hi = S0 2^21 + S1 2^14 + S2 2^7 + S3 (|hi| < 2^41)
+                // hi = S0 2^21 + S1 2^14 + S2 2^7 + S3 (|hi| < 2^42)
                 hi[c] = ((long long)(acc_int(v[0][c]) * 128 + acc_int(v[1][c])) << 14) +
                         (acc_int(v[2][c]) * 128 + acc_int(v[3][c]));
 #pragma unroll
@@ -192,7 +230,7 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
             for (int c = 0; c < 8; c++) {
                 const long long lo = ((long long)(acc_int(v[0][c]) * 128 + acc_int(v[1][c])) << 14) +
                                      (acc_int(v[2][c]) * 128 + acc_int(v[3][c]));
-                // T = hi 2^28 + lo, kept as T 2^-8 (|.| < 2^61): the bits dropped
+                // T = hi 2^28 + lo, kept as T 2^-8 (|.| < 2^62): the bits dropped
                 // are far below the truncation of the digit products with t + u >= 8
                 const long long tq = (hi[c] << 20) + (lo >> 8);
                 if (tq != 0 && ((live >> (c8 * 8 + c)) & 1u))

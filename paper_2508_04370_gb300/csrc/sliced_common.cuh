@@ -1,5 +1,5 @@
-// Digit slicing of the sliced tensor-core updates (shared by the slicing
-// kernel and the triangular solve that slices the rows it finishes): a row
+// Digit slicing of the sliced tensor-core updates (done by the panel's
+// triangular solve for the rows it finishes): a row
 // of an operand scaled by 2^-E (|entries| < 2^E) becomes 56-bit integers
 // written as eight balanced base-2^7 digits, each exactly a bf16, in the
 // 128-byte-swizzled K-major image the tensor cores read.
@@ -68,26 +68,39 @@ __device__ __forceinline__ uint32_t bf16_bits(int v) {
     return __float_as_uint((float)v) >> 16;
 }
 
-// One row r of both operands sliced by one warp: lane q holds L(r, q) and
-// d_q (both 0 beyond the panel).  Writes the row's digits at row rr of the
+// One row r of both operands sliced by one warp over NC chunks of 32
+// columns: lane q holds L(r, q) and d_q of chunk c in l[c], dq[c] (both 0
+// beyond the panel).  Writes the row's digits at row rr of chunk c of the
 // slice block `blk` (operand A: L 2^h_q, operand B: L d_q 2^-h_q,
-// h_q = floor(log2 |d_q| / 2)) and its two row scales at exps[2 rr + op];
-// returns true when an entry is not finite (its row is then sliced as zero).
-// The values are those the slicing kernel takes from the front, so both give
-// the same images.
-__device__ __forceinline__ bool slice_row_warp(double l, double dq, uint8_t *blk, int32_t *exps, int rr) {
+// h_q = floor(log2 |d_q| / 2)), one row scale per operand over all NC
+// chunks at exps[2 rr + op]; returns true when an entry is not finite (its
+// row is then sliced as zero).
+template <int NC>
+__device__ __forceinline__ bool slice_row_warp(const double (&l)[NC], const double (&dq)[NC], uint8_t *blk,
+                                               int32_t *exps, int rr) {
     const int lane = threadIdx.x & 31;
-    const int ed = biased_exp(__double_as_longlong(dq));
-    const int h = ed == 0 ? 0 : ((ed - 1023) >> 1);
-    const double v[2] = {l, l * dq};
-    const int sh[2] = {h, -h};
+    double v[NC][2];
+    int sh[NC][2];
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+        const int ed = biased_exp(__double_as_longlong(dq[c]));
+        const int h = ed == 0 ? 0 : ((ed - 1023) >> 1);
+        v[c][0] = l[c];
+        v[c][1] = l[c] * dq[c];
+        sh[c][0] = h;
+        sh[c][1] = -h;
+    }
     int E[2];
     bool bad = false;
 #pragma unroll
     for (int op = 0; op < 2; op++) {
-        const int e = biased_exp(__double_as_longlong(v[op]));
-        bad |= e == 0x7ff;
-        int m = e != 0 ? e + sh[op] : kNoExp;
+        int m = kNoExp;
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+            const int e = biased_exp(__double_as_longlong(v[c][op]));
+            bad |= e == 0x7ff;
+            if (e != 0) m = max(m, e + sh[c][op]);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         E[op] = m;
@@ -97,20 +110,24 @@ __device__ __forceinline__ bool slice_row_warp(double l, double dq, uint8_t *blk
     for (int op = 0; op < 2; op++) {
         E[op] = (E[op] == kNoExp || bad) ? kNoScale : E[op] - 1022;
         if (lane == 0) exps[2 * rr + op] = E[op];
-        int d[8];
-        digits8(E[op] == kNoScale ? 0 : fixed56(v[op], sh[op], E[op]), d);
-        uint8_t *img = blk + op * kSliceOperandBytes;
 #pragma unroll
-        for (int t = 0; t < 8; t++) {
-            // pack lanes 8c .. 8c+7 (columns) into one 16-byte chunk held by lane 8c
-            const uint32_t hb = bf16_bits(d[t]);
-            const uint32_t pair = hb | (__shfl_down_sync(0xffffffffu, hb, 1) << 16);
-            const uint32_t w1 = __shfl_down_sync(0xffffffffu, pair, 2);
-            const uint32_t w2 = __shfl_down_sync(0xffffffffu, pair, 4);
-            const uint32_t w3 = __shfl_down_sync(0xffffffffu, pair, 6);
-            if ((lane & 7) == 0) {
-                const int chunk = (t & 1) * 4 + (lane >> 3);
-                *(uint4 *)(img + (t >> 1) * kSlicePairBytes + swz_chunk(rr, chunk)) = make_uint4(pair, w1, w2, w3);
+        for (int c = 0; c < NC; c++) {
+            int d[8];
+            digits8(E[op] == kNoScale ? 0 : fixed56(v[c][op], sh[c][op], E[op]), d);
+            uint8_t *img = blk + c * kSliceChunkBytes + op * kSliceOperandBytes;
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                // pack lanes 8k .. 8k+7 (columns) into one 16-byte chunk held by lane 8k
+                const uint32_t hb = bf16_bits(d[t]);
+                const uint32_t pair = hb | (__shfl_down_sync(0xffffffffu, hb, 1) << 16);
+                const uint32_t w1 = __shfl_down_sync(0xffffffffu, pair, 2);
+                const uint32_t w2 = __shfl_down_sync(0xffffffffu, pair, 4);
+                const uint32_t w3 = __shfl_down_sync(0xffffffffu, pair, 6);
+                if ((lane & 7) == 0) {
+                    const int chunk = (t & 1) * 4 + (lane >> 3);
+                    *(uint4 *)(img + (t >> 1) * kSlicePairBytes + swz_chunk(rr, chunk)) =
+                        make_uint4(pair, w1, w2, w3);
+                }
             }
         }
     }

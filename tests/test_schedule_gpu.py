@@ -101,3 +101,36 @@ def test_auto_order_and_graph_replay(pkg):
         np.testing.assert_array_equal(gy[k * m:(k + 1) * m], ey.cpu().numpy())
     s.close()
     ref.close()
+
+
+def test_kernel_trace_matches_kernel_stats(pkg):
+    """ipm_kernel_trace lists every profiled launch of a factorisation in issue
+    order; its per-class durations sum to what ipm_kernel_stats reports, and
+    the critical stream's steps appear in order (no launch on a stream starts
+    before the previous one on that stream ended)."""
+    lp = synth.staircase(periods=4, seed=1)
+    th = synth.theta_loguniform(lp.n, 41)
+    s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND, precision=pkg.IPM_PREC_SLICED, mixed_min_front=64)
+    s.factorise(th, RHO, DELTA)
+    pkg.ipm_set_profiling(s.ctx, True)
+    pkg.ipm_kernel_stats(s.ctx, reset=True)
+    pkg.ipm_kernel_trace(s.ctx)
+    s.factorise(th, RHO, DELTA)
+    pkg.ipm_set_profiling(s.ctx, False)
+    tr = pkg.ipm_kernel_trace(s.ctx)
+    ks = pkg.ipm_kernel_stats(s.ctx, reset=True)
+    n = tr["count"]
+    assert n == len(tr["cls"]) and n == sum(v["launches"] for v in ks.values()) and n > 0
+    assert tr["start_ms"][0] == 0.0 and np.all(tr["end_ms"] >= tr["start_ms"])
+    assert np.all((tr["cls"] >= 0) & (tr["cls"] < len(pkg.KERNEL_CLASSES)))
+    for c, name in enumerate(pkg.KERNEL_CLASSES):
+        m = tr["cls"] == c
+        assert m.sum() == ks[name]["launches"]
+        assert abs(float((tr["end_ms"][m] - tr["start_ms"][m]).sum()) - ks[name]["ms"]) <= 1e-3 * max(1.0, ks[name]["ms"])
+    for st in np.unique(tr["stream"]):
+        m = tr["stream"] == st
+        a, b = tr["start_ms"][m], tr["end_ms"][m]
+        assert np.all(a[1:] >= b[:-1] - 1e-3)
+    # a second call returns nothing new
+    assert pkg.ipm_kernel_trace(s.ctx)["count"] == 0
+    s.close()
