@@ -818,7 +818,8 @@ int setup_device(ipm_ctx *c) {
                             e += std::max(0, std::min(i0 + kSliceRows, f) - std::max(i0, j));
                         Work &tw = la ? S.st_w1 : S.st_w2;
                         tw.flops += 2.0 * wk * e;
-                        tw.bytes += 16.0 * e + 2.0 * kSlices * 2.0 * wk * (kSliceRows + kSliceCols);
+                        // C read and written; the digit images of its 128 A rows and 32 B rows (bf16)
+                        tw.bytes += 16.0 * e + 2.0 * kSlices * wk * (kSliceRows + kSliceCols);
                     }
                 S.trsm_w.bytes += 2.0 * kSlices * 2.0 * rest * wk;  // the slices the solve writes
                 if (pair_second) S.trsm_w.bytes += 8.0 * rest * c->opt.nb;  // the first panel's rows it re-reads
