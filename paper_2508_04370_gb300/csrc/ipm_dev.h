@@ -14,6 +14,8 @@ enum : int32_t {
     kStatLargeReg = 4,     // a lift exceeded opt.large_reg
     kStatTimeout = 8,      // a bounded wait expired
     kStatRefineFail = 16,  // refinement did not reach the target
+    kStatWaitCopy = 32,    // with kStatTimeout: a tensor-core kernel's wait for its bulk copies gave up
+    kStatWaitMma = 64,     // with kStatTimeout: a wait for the completion of MMAs gave up
 };
 
 // Dynamic shared memory the per-level solve sweeps may use (one front's

@@ -60,7 +60,6 @@ using namespace sliced;
 
 namespace {
 
-constexpr long long kSlicePolls = 1ll << 24;  // bounded waits on copies and MMAs (~1 s)
 
 // t 2^e as a double (round half up to 53 bits), built with integer
 // operations; t != 0.  Leaves the normal range only through ldexp.
@@ -154,11 +153,11 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
     bool lead_ok = true;  // thread 0: every copy and MMA of the tile issued
     if (tid == 0) {
         chunk_copy(0);
-        if (tc::mbar_wait(&bar_load, 0, kSlicePolls)) {
+        if (tc::mbar_wait(&bar_load, 0)) {
             chunk_mma(0);
         } else {
-            atomicOr(&ctl->status, kStatTimeout);
-            tc::mbar_wait(&bar_load, 0, kSlicePolls);  // let the copies in flight land before the CTA exits
+            atomicOr(&ctl->status, kStatTimeout | kStatWaitCopy);
+            tc::mbar_wait(&bar_load, 0);  // let the copies in flight land before the CTA exits
             lead_ok = false;
         }
     }
@@ -182,15 +181,15 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
         for (int ch = 1; ch < kc && lead_ok; ch++) {
             // the buffer is free once the previous chunk's MMAs are done
             tc::commit_to(&bar_mid);
-            if (!tc::mbar_wait(&bar_mid, (ch - 1) & 1, kSlicePolls)) {
-                atomicOr(&ctl->status, kStatTimeout);
+            if (!tc::mbar_wait(&bar_mid, (ch - 1) & 1)) {
+                atomicOr(&ctl->status, kStatTimeout | kStatWaitMma);
                 lead_ok = false;
                 break;
             }
             chunk_copy(ch);
-            if (!tc::mbar_wait(&bar_load, ch & 1, kSlicePolls)) {
-                atomicOr(&ctl->status, kStatTimeout);
-                tc::mbar_wait(&bar_load, ch & 1, kSlicePolls);
+            if (!tc::mbar_wait(&bar_load, ch & 1)) {
+                atomicOr(&ctl->status, kStatTimeout | kStatWaitCopy);
+                tc::mbar_wait(&bar_load, ch & 1);
                 lead_ok = false;
                 break;
             }
@@ -198,10 +197,10 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
         }
         tc::commit_to(&bar_mma);
     }
-    bool ok = tc::mbar_wait(&bar_mma, 0, kSlicePolls);
+    bool ok = tc::mbar_wait(&bar_mma, 0);
     if (!ok) {
-        atomicOr(&ctl->status, kStatTimeout);
-        tc::mbar_wait(&bar_mma, 0, kSlicePolls);  // the MMAs must finish before TMEM is freed
+        atomicOr(&ctl->status, kStatTimeout | kStatWaitMma);
+        tc::mbar_wait(&bar_mma, 0);  // the MMAs must finish before TMEM is freed
     }
     ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the TMEM loads below are warp-collective
     tc::fence_after_sync();
@@ -256,5 +255,6 @@ void launch_update_sliced(const DevPlan &P, double *fronts, const SlicedTile *it
         cudaFuncSetAttribute(k_update_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlicedSmem);
     k_update_sliced<<<count, kSlicedThreads, kSlicedSmem, st>>>(P, fronts, items, ws, ws_exp, ctl);
 }
+
 
 }  // namespace ipm

@@ -22,7 +22,6 @@ namespace ipm {
 
 namespace {
 
-constexpr long long kMbarPolls = 1ll << 24;  // bounded wait for the MMAs (~1 s)
 constexpr int kTcSmem = 4 * 16384 + 1024;    // four 128 x 32 fp32 tiles + alignment
 
 __global__ void __launch_bounds__(128) k_large_update_tc(DevPlan P, double *__restrict__ fronts,
@@ -76,8 +75,12 @@ __global__ void __launch_bounds__(128) k_large_update_tc(DevPlan P, double *__re
         }
         tc::commit_to(&mbar);
     }
-    const bool ok = tc::mbar_wait(&mbar, 0, kMbarPolls);
-    if (!ok && lane == 0) atomicOr(&ctl->status, kStatTimeout);
+    bool ok = tc::mbar_wait(&mbar, 0);
+    if (!ok) {
+        atomicOr(&ctl->status, kStatTimeout | kStatWaitMma);
+        tc::mbar_wait(&mbar, 0);  // the MMAs must finish before TMEM is freed
+    }
+    ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the TMEM loads below are warp-collective
     tc::fence_after_sync();
     if (ok) {
         const int row = it.i0 + warp * 32 + lane;

@@ -69,10 +69,21 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
 }
 
-// Bounded wait for the given phase parity; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, long long max_polls) {
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the given phase parity, bounded in time (a healthy wait takes
+// microseconds; each try_wait may suspend the thread for a while, so a bound
+// on the number of polls alone would not bound the time); returns false on
+// timeout.
+constexpr unsigned long long kWaitNs = 50ull * 1000ull * 1000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, unsigned long long limit_ns = kWaitNs) {
     const uint32_t a = smem_u32(mbar);
-    for (long long i = 0; i < max_polls; i++) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -82,8 +93,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, long 
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if (global_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
