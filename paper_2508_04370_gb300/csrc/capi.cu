@@ -732,7 +732,6 @@ int setup_device(ipm_ctx *c) {
     const bool sliced = c->opt.precision == IPM_PREC_SLICED;
     std::vector<FactorItem> lvl_items;
     std::vector<int32_t> cbase(P.nsuper, -1);
-    std::vector<int64_t> front_asm(P.nsuper + 1, -1);  // first assembly item of each large front
     int32_t max_ncnt = 0;
     c->levels.assign(P.nlevels, LevelWork());
     c->flops_tensor = 0.0;
@@ -748,6 +747,29 @@ int setup_device(ipm_ctx *c) {
             fr.flops += cc * (cc + 1) / 2;
         }
         return fr;
+    };
+    // One assembly item: columns [cl, ce), rows [rlo, rhi) of large front s;
+    // its original entries (those of the columns) and, per child, the
+    // contribution-block columns and rows that land in it.
+    auto add_asm = [&](int32_t s, int32_t cl, int32_t ce, int32_t rlo, int32_t rhi) {
+        const int32_t ld = P.sn_ld[s];
+        asm_items.push_back({s, cl, ce, 0});
+        const int32_t *d0 = P.orig_dst.data() + P.orig_ptr[s], *d1 = P.orig_dst.data() + P.orig_ptr[s + 1];
+        AsmItem ai;
+        ai.o0 = std::lower_bound(d0, d1, (int64_t)cl * ld) - P.orig_dst.data();
+        ai.o1 = std::lower_bound(d0, d1, (int64_t)ce * ld) - P.orig_dst.data();
+        ai.cr = (int64_t)(asm_cr.size() / 4);
+        ai.r_lo = rlo;
+        ai.r_hi = rhi;
+        for (int32_t q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
+            const int32_t ch = P.child_list[q];
+            const int32_t *m0 = P.relmap.data() + P.map_off[ch], *m1 = m0 + (P.sn_f[ch] - P.sn_k[ch]);
+            asm_cr.push_back((int32_t)(std::lower_bound(m0, m1, cl) - m0));
+            asm_cr.push_back((int32_t)(std::lower_bound(m0, m1, ce) - m0));
+            asm_cr.push_back((int32_t)(std::lower_bound(m0, m1, rlo) - m0));
+            asm_cr.push_back((int32_t)(std::lower_bound(m0, m1, rhi) - m0));
+        }
+        asm_info.push_back(ai);
     };
     // One step of the large-front path: for each (front s, panel start p0)
     // of fp, the diagonal block of the panel, the triangular solve of the rows
@@ -922,27 +944,8 @@ int setup_device(ipm_ctx *c) {
         W.asm_off = (int64_t)asm_items.size();
         int32_t maxsteps = 0;
         for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
-            int32_t s = P.lvl_large[t];
-            const int32_t ld = P.sn_ld[s];
-            front_asm[s] = (int64_t)asm_items.size();
-            for (int32_t cl = 0; cl < P.sn_f[s]; cl += 32) {
-                const int32_t ce = std::min(cl + 32, P.sn_f[s]);
-                asm_items.push_back({s, cl, ce});
-                // original entries of columns [cl, ce) and, per child, the
-                // contribution-block columns mapping into them
-                const int32_t *d0 = P.orig_dst.data() + P.orig_ptr[s], *d1 = P.orig_dst.data() + P.orig_ptr[s + 1];
-                AsmItem ai;
-                ai.o0 = std::lower_bound(d0, d1, (int64_t)cl * ld) - P.orig_dst.data();
-                ai.o1 = std::lower_bound(d0, d1, (int64_t)ce * ld) - P.orig_dst.data();
-                ai.cr = (int64_t)(asm_cr.size() / 2);
-                for (int32_t q = P.child_ptr[s]; q < P.child_ptr[s + 1]; q++) {
-                    const int32_t ch = P.child_list[q];
-                    const int32_t *m0 = P.relmap.data() + P.map_off[ch], *m1 = m0 + (P.sn_f[ch] - P.sn_k[ch]);
-                    asm_cr.push_back((int32_t)(std::lower_bound(m0, m1, cl) - m0));
-                    asm_cr.push_back((int32_t)(std::lower_bound(m0, m1, ce) - m0));
-                }
-                asm_info.push_back(ai);
-            }
+            const int32_t s = P.lvl_large[t];
+            for (int32_t cl = 0; cl < P.sn_f[s]; cl += 32) add_asm(s, cl, std::min(cl + 32, P.sn_f[s]), cl, P.sn_f[s]);
             maxsteps = std::max(maxsteps, (P.sn_k[s] + c->opt.nb - 1) / c->opt.nb);
         }
         W.asm_cnt = (int32_t)(asm_items.size() - W.asm_off);
@@ -1035,14 +1038,11 @@ int setup_device(ipm_ctx *c) {
                 Work aw;
                 int32_t swait = -1;
                 for (int32_t s : starting[g]) {
-                    const int64_t a0 = front_asm[s];
-                    const int64_t a1 = a0 + (P.sn_f[s] + 31) / 32;
-                    for (int64_t a = a0; a < a1; a++) {
-                        const PanelItem pi = asm_items[a];
-                        const AsmItem ai = asm_info[a];
-                        asm_items.push_back(pi);
-                        asm_info.push_back(ai);
-                    }
+                    // one item per 32 columns (splitting the rows too made more,
+                    // shorter CTAs that slowed the trailing tiles beside them more
+                    // than they sped up the assembly)
+                    const int32_t f = P.sn_f[s];
+                    for (int32_t cl = 0; cl < f; cl += 32) add_asm(s, cl, std::min(cl + 32, f), cl, f);
                     aw.bytes += front_work(s).bytes;
                     swait = std::max(swait, nsmall_child[s]);
                     active.push_back(s);

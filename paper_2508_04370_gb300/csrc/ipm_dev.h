@@ -173,10 +173,13 @@ struct PanelItem {
     int32_t p0;      // first column of the item's panel (diagonal blocks, triangular solves)
 };
 // Precomputed ranges of an assembly item (front columns [r0, r1) of a large
-// front): its original entries [o0, o1) and, at acr[2 * cr ...], one
-// [a, b) range of contribution-block columns per child (children ascending).
+// front, rows [r_lo, r_hi)): its original entries [o0, o1) (those of the
+// columns; the item keeps the ones in its rows) and, at acr[4 * cr ...], per
+// child (children ascending) the range [a, b) of contribution-block columns
+// and the range [ilo, ihi) of contribution-block rows that land in the item.
 struct AsmItem {
     int64_t o0, o1, cr;
+    int32_t r_lo, r_hi;  // front rows [r_lo, r_hi) handled (rows below the columns' first: the upper part is never read)
 };
 struct TileItem {
     int32_t s;

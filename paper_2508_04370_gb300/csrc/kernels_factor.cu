@@ -342,35 +342,46 @@ __global__ void __launch_bounds__(NT) k_small_fronts(DevPlan P, DevVals V, doubl
 constexpr int kBodyThreads = 256;
 constexpr int kPoolDoubles = 2 * 32 * 33 + 32;  // a 32 x 32 update tile's two operands; L_11, 1/d and a 32 x 33 tile
 
-// Assembly of columns [c_lo, c_hi) of front s into its slab in global memory:
-// zero the columns, place the original entries (a precomputed contiguous
-// range), then add the children's contribution-block columns that land in
-// the range (precomputed per child), children in ascending order.  Child
-// descriptors are staged in shared memory 64 at a time.
+// Assembly of columns [c_lo, c_hi), rows [ai.r_lo, ai.r_hi) of front s into
+// its slab in global memory: zero the block, place the original entries (a
+// precomputed contiguous range of the columns' entries, filtered by row),
+// then add the children's contribution-block entries that land in the block
+// (column and row ranges precomputed per child), children in ascending order.
+// Rows above the block's first column (the upper part) are never read and
+// are not written.  Child descriptors are staged in shared memory 64 at a
+// time.
 constexpr int kAsmBatch = 8;  // contribution-block rows per lane per round of the extend-add
 
 __device__ __forceinline__ void body_assemble(const DevPlan &P, const DevVals &V, double *__restrict__ fronts, int s,
                                               int c_lo, int c_hi, const AsmItem &ai, const int32_t *__restrict__ acr,
                                               double *pool) {
     constexpr int NT = kBodyThreads;
-    int32_t *ch_a = reinterpret_cast<int32_t *>(pool), *ch_b = ch_a + 64, *ch_cc = ch_b + 64, *ch_ldc = ch_cc + 64;
-    int64_t *ch_cb = reinterpret_cast<int64_t *>(ch_ldc + 64), *ch_map = ch_cb + 64;
+    int32_t *ch_a = reinterpret_cast<int32_t *>(pool), *ch_b = ch_a + 64, *ch_ldc = ch_b + 64;
+    int32_t *ch_ilo = ch_ldc + 64, *ch_ihi = ch_ilo + 64;
+    int64_t *ch_cb = reinterpret_cast<int64_t *>(ch_ihi + 64), *ch_map = ch_cb + 64;
     const int ld = P.sn_ld[s];
     double *F = fronts + P.sn_off[s];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ncol = c_hi - c_lo;
-    for (int t = tid; t < ncol * ld; t += NT) F[(int64_t)c_lo * ld + t] = 0.0;
+    const int ncol = c_hi - c_lo, r_lo = ai.r_lo, r_hi = ai.r_hi;
+    for (int c = 0; c < ncol; c++)
+        for (int r = r_lo + tid; r < r_hi; r += NT) F[(int64_t)(c_lo + c) * ld + r] = 0.0;
     __syncthreads();
-    for (int64_t q = ai.o0 + tid; q < ai.o1; q += NT) F[P.orig_dst[q]] = orig_value(P, V, P.orig_src[q]);
+    for (int64_t q = ai.o0 + tid; q < ai.o1; q += NT) {
+        const int32_t d = P.orig_dst[q];
+        const int r = d % ld;
+        if (r >= r_lo && r < r_hi) F[d] = orig_value(P, V, P.orig_src[q]);
+    }
     const int q0 = P.child_ptr[s], nch = P.child_ptr[s + 1] - q0;
     for (int base = 0; base < nch; base += 64) {
         __syncthreads();
         if (tid < 64 && base + tid < nch) {
             const int c = P.child_list[q0 + base + tid];
             const int kc = P.sn_k[c], ldc = P.sn_ld[c];
-            ch_a[tid] = acr[2 * (ai.cr + base + tid)];
-            ch_b[tid] = acr[2 * (ai.cr + base + tid) + 1];
-            ch_cc[tid] = P.sn_f[c] - kc;
+            const int32_t *e = acr + 4 * (ai.cr + base + tid);
+            ch_a[tid] = e[0];
+            ch_b[tid] = e[1];
+            ch_ilo[tid] = e[2];
+            ch_ihi[tid] = e[3];
             ch_ldc[tid] = ldc;
             ch_cb[tid] = P.sn_off[c] + (int64_t)kc * ldc + kc;
             ch_map[tid] = P.map_off[c];
@@ -378,9 +389,9 @@ __device__ __forceinline__ void body_assemble(const DevPlan &P, const DevVals &V
         __syncthreads();
         const int nu = min(64, nch - base);
         for (int u = 0; u < nu; u++) {
-            const int a = ch_a[u], b = ch_b[u];
-            if (a >= b) continue;  // uniform over the CTA
-            const int cc = ch_cc[u], ldc = ch_ldc[u];
+            const int a = ch_a[u], b = ch_b[u], ilo = ch_ilo[u], ihi = ch_ihi[u];
+            if (a >= b || ilo >= ihi) continue;  // uniform over the CTA
+            const int ldc = ch_ldc[u];
             const double *CB = fronts + ch_cb[u];
             const int32_t *map = P.relmap + ch_map[u];
             for (int jj = a + warp; jj < b; jj += NT / 32) {
@@ -391,14 +402,14 @@ __device__ __forceinline__ void body_assemble(const DevPlan &P, const DevVals &V
                 // the batch's loads are independent of its stores (the child
                 // block and the front never overlap), and each entry still
                 // receives its children's terms in ascending child order
-                for (int i0 = jj + lane; i0 < cc; i0 += 32 * kAsmBatch) {
+                for (int i0 = max(jj, ilo) + lane; i0 < ihi; i0 += 32 * kAsmBatch) {
                     int32_t mi[kAsmBatch];
                     double cv[kAsmBatch], fv[kAsmBatch];
 #pragma unroll
                     for (int t = 0; t < kAsmBatch; t++) {
                         const int ii = i0 + 32 * t;
-                        mi[t] = ii < cc ? __ldg(map + ii) : -1;
-                        cv[t] = ii < cc ? __ldcg(CBj + ii) : 0.0;
+                        mi[t] = ii < ihi ? __ldg(map + ii) : -1;
+                        cv[t] = ii < ihi ? __ldcg(CBj + ii) : 0.0;
                     }
 #pragma unroll
                     for (int t = 0; t < kAsmBatch; t++) fv[t] = mi[t] >= 0 ? Fj[mi[t]] : 0.0;
