@@ -469,9 +469,11 @@ __device__ __forceinline__ void leaf_forward(const SolveSched &S, int s, const d
     }
     if (lane < k) x[c0 + lane] = v * dinv;
     else if (lane < f) __stcg(upd + nd.upd + (lane - k), v - acc);
-    __threadfence();
     __syncwarp();
-    if (lane == 0 && nd.parent >= 0) atomicAdd(&cnt[nd.parent], 1);
+    if (lane == 0 && nd.parent >= 0) {
+        __threadfence();
+        atomicAdd(&cnt[nd.parent], 1);
+    }
 }
 
 __device__ __forceinline__ void leaf_backward(const SolveSched &S, int s, const double *__restrict__ fronts,
@@ -688,9 +690,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
                     __stcg(upd + nd.upd + (q - k), v[q]);
                 }
             }
-            __threadfence();
+            // publish: the CTA barrier orders every thread's stores before
+            // thread 0's fence, which makes them visible device-wide before its
+            // counter updates (cumulativity)
             __syncthreads();
             if (tid == 0) {
+                __threadfence();
                 if (!single) atomicAdd(&tcnt[s], 1);
                 finish_forward(nd, s, done, cnt);
             }
@@ -727,9 +732,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
                 for (int q = 1; q < kSolveThreads / 32; q++) sum += part[q][lane];
                 __stcg(upd + nd.upd + (i - k), u0 - sum);
             }
-            __threadfence();
             __syncthreads();
-            if (tid == 0) finish_forward(nd, s, done, cnt);
+            if (tid == 0) {
+                __threadfence();
+                finish_forward(nd, s, done, cnt);
+            }
         }
     }
 }
@@ -818,9 +825,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
             __syncthreads();
         }
         for (int q = tid; q < w; q += kSolveThreads) __stcg(x + c0 + b0 + q, z[q]);
-        __threadfence();
         __syncthreads();
         if (tid == 0) {
+            __threadfence();
             if (nd.nblk > 1) atomicAdd(&tcnt[s], 1);
             if (b == 0) atomicExch(&flag[s], 1);
         }
