@@ -174,6 +174,8 @@ typedef struct ipm_info {
                                                IPM_SCHED_DEPENDENCY */
     int32_t steps_levels;                   /* 32-column steps of the large fronts in the level order */
     int32_t steps_dependency;               /* ... in the dependency order */
+    int32_t nfronts_thin;                   /* large fronts of one pivot block (k <= 32, f <= 512, FP64 updates)
+                                               that a level outside the level kernel runs whole, one CTA each */
 } ipm_info;
 
 /* Fill *opt with the defaults listed above. */

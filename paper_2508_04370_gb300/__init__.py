@@ -85,6 +85,7 @@ class ipm_info(ct.Structure):
         ("tune_small_threads", ct.c_int32 * 3), ("tune_level_ratio", ct.c_double), ("tune_ms", ct.c_double),
         ("amalg_zero_frac", ct.c_double), ("tune_level_ctas_per_sm", ct.c_int32), ("graph_kernels", ct.c_int32),
         ("schedule", ct.c_int32), ("steps_levels", ct.c_int32), ("steps_dependency", ct.c_int32),
+        ("nfronts_thin", ct.c_int32),
     ]
 
     def as_dict(self):

@@ -56,8 +56,13 @@ struct LevelWork {
     std::vector<SmallClass> small;  // small fronts of the level by size class
     int64_t all_off;
     int32_t all_cnt, all_maxf;
-    int64_t asm_off;
+    int64_t asm_off;   // assembly items of the level's large fronts (the level kernel takes them all)
     int32_t asm_cnt;
+    int64_t asm_off2;  // those of the fronts that go through the steps
+    int32_t asm_cnt2;
+    int64_t thin_off = 0;  // thin fronts, whole in one CTA each (k_thin_fronts)
+    int32_t thin_cnt = 0;
+    Work thin_w;
     std::vector<StepWork> steps;
     Work asm_w, fwd_w, bwd_w;
     int64_t lvl_off = 0;   // items of the persistent level kernel (FP64 large fronts)
@@ -118,6 +123,7 @@ struct ipm_ctx {
     int32_t *asm_cr = nullptr;
     int32_t *trsm_slots = nullptr;
     int32_t *trsm_sbase = nullptr;     // sliced path: first slice block of each TRSM item's front (-1: none)
+    int32_t *thin_list = nullptr, *thin_asm = nullptr, *thin_slot = nullptr;  // thin fronts by level
     double *panel_ws = nullptr;
     TileItem *tile_items = nullptr, *tc_items = nullptr, *alt_items = nullptr;
     SlicedTile *sliced_tiles = nullptr;  // sliced tensor-core path: output tiles per step
@@ -149,6 +155,7 @@ struct ipm_ctx {
     std::vector<StepWork> dsteps;        // its steps
     std::vector<int32_t> small_dep;      // per level: step whose completion its small fronts wait for (-1: none)
     int32_t steps_levels = 0, steps_dependency = 0;
+    int32_t nfronts_thin = 0;
     std::vector<cudaEvent_t> done_ev;    // dependency order: end of each step on the critical stream
     // numeric state of the last factorisation
     double rho = 0.0, delta = 0.0;
@@ -723,6 +730,7 @@ int setup_device(ipm_ctx *c) {
     std::vector<AsmItem> asm_info;
     std::vector<int32_t> asm_cr;
     std::vector<int32_t> trsm_slots, trsm_sbase, slot_of(P.nsuper, -1);
+    std::vector<int32_t> thin_list, thin_asm, thin_slot;
     int32_t nslots = 0;
     for (int32_t s = 0; s < P.nsuper; s++)
         if (P.sn_large[s]) slot_of[s] = nslots++;
@@ -940,20 +948,55 @@ int setup_device(ipm_ctx *c) {
             W.bwd_w.flops += 2.0 * (lnz - f);
             W.bwd_w.bytes += 8.0 * lnz + 8.0 * (f + k);
         }
-        // large fronts
+        // large fronts; the thin ones (one pivot block, f <= kThinMaxF, FP64
+        // updates) of a level that does not take the level kernel run whole,
+        // one CTA each, instead of through the steps
         W.asm_off = (int64_t)asm_items.size();
         int32_t maxsteps = 0;
+        std::vector<int32_t> main_fronts;
+        std::vector<int64_t> main_first;
+        W.thin_off = (int64_t)thin_list.size();
         for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++) {
             const int32_t s = P.lvl_large[t];
+            const int64_t first = (int64_t)asm_items.size();
             for (int32_t cl = 0; cl < P.sn_f[s]; cl += 32) add_asm(s, cl, std::min(cl + 32, P.sn_f[s]), cl, P.sn_f[s]);
-            maxsteps = std::max(maxsteps, (P.sn_k[s] + c->opt.nb - 1) / c->opt.nb);
+            const bool thin = P.sn_k[s] <= c->opt.nb && P.sn_f[s] <= kThinMaxF &&
+                              !(c->opt.precision != IPM_PREC_FP64 && P.sn_f[s] >= c->opt.mixed_min_front);
+            if (thin) {
+                thin_list.push_back(s);
+                thin_asm.push_back((int32_t)first);
+                thin_slot.push_back(slot_of[s]);
+                const Work fr = front_work(s);
+                W.thin_w.flops += fr.flops;
+                W.thin_w.bytes += fr.bytes;
+            } else {
+                main_fronts.push_back(s);
+                main_first.push_back(first);
+                maxsteps = std::max(maxsteps, (P.sn_k[s] + c->opt.nb - 1) / c->opt.nb);
+            }
         }
         W.asm_cnt = (int32_t)(asm_items.size() - W.asm_off);
+        W.thin_cnt = (int32_t)((int64_t)thin_list.size() - W.thin_off);
+        if (W.thin_cnt > 0) {
+            // the per-step assembly launch takes the other fronts' items (copies)
+            W.asm_off2 = (int64_t)asm_items.size();
+            for (size_t q = 0; q < main_fronts.size(); q++)
+                for (int64_t a = main_first[q]; a < main_first[q] + (P.sn_f[main_fronts[q]] + 31) / 32; a++) {
+                    const PanelItem pi = asm_items[a];
+                    const AsmItem ai = asm_info[a];
+                    asm_items.push_back(pi);
+                    asm_info.push_back(ai);
+                }
+            W.asm_cnt2 = (int32_t)((int64_t)asm_items.size() - W.asm_off2);
+        } else {
+            W.asm_off2 = W.asm_off;
+            W.asm_cnt2 = W.asm_cnt;
+        }
         std::vector<std::pair<int32_t, int32_t>> fp;
         for (int32_t st = 0; st < maxsteps; st++) {
             fp.clear();
-            for (int32_t t = P.lvl_large_ptr[l]; t < P.lvl_large_ptr[l + 1]; t++)
-                if (st * c->opt.nb < P.sn_k[P.lvl_large[t]]) fp.push_back({P.lvl_large[t], st * c->opt.nb});
+            for (int32_t s : main_fronts)
+                if (st * c->opt.nb < P.sn_k[s]) fp.push_back({s, st * c->opt.nb});
             const StepWork S = add_step(fp);
             W.steps.push_back(S);
             if (S.tc_cnt > 0 || S.st_cnt > 0) W.has_tc = true;
@@ -1061,6 +1104,7 @@ int setup_device(ipm_ctx *c) {
         }
     }
     c->steps_levels = steps_levels;
+    c->nfronts_thin = (int32_t)thin_list.size();
     std::vector<int64_t> upd_off(P.upd_off.begin(), P.upd_off.end());
     std::vector<int32_t> bwd_order(lvl_all.rbegin(), lvl_all.rend());
     c->solve_maxf = P.max_f;
@@ -1086,14 +1130,20 @@ int setup_device(ipm_ctx *c) {
         (rc = dupload(c, &c->tile_items, tile_items)) || (rc = dupload(c, &c->tc_items, tc_items)) ||
         (rc = dupload(c, &c->alt_items, alt_items)) || (rc = dupload(c, &c->bwd_order, bwd_order)) ||
         (rc = dupload(c, &c->trsm_sbase, trsm_sbase)) || (rc = dupload(c, &c->sliced_tiles, sliced_tiles)) ||
+        (rc = dupload(c, &c->thin_list, thin_list)) || (rc = dupload(c, &c->thin_asm, thin_asm)) ||
+        (rc = dupload(c, &c->thin_slot, thin_slot)) ||
         (rc = dalloc(c, &c->slice_ws, 2 * (size_t)max_slice_blocks * (size_t)kSliceBlockBytes)) ||
         (rc = dalloc(c, &c->slice_exp, 2 * (size_t)std::max<int64_t>(max_slice_blocks, 1) * kSliceRows * 2)) ||
         (rc = dupload(c, &c->lvl_items, lvl_items)) || (rc = dalloc(c, &c->lvl_sync, (size_t)max_ncnt + 1)) ||
         (rc = dalloc(c, &c->solve_sync, (size_t)3 * ns + 1)))
         return rc;
     c->slice_half_blocks = max_slice_blocks;
-    int32_t *d_sparent;
+    int32_t *d_sparent, *d_long;
     if ((rc = dupload(c, &d_sparent, P.sn_parent))) return rc;
+    std::vector<int32_t> long_cols;  // columns of K summed by a CTA each in the norm
+    for (int32_t i = 0; i < N; i++)
+        if (kp[i + 1] - kp[i] > kLongColumn) long_cols.push_back(i);
+    if ((rc = dupload(c, &d_long, long_cols))) return rc;
     {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
@@ -1133,6 +1183,8 @@ int setup_device(ipm_ctx *c) {
     dp.kp = d_kp;
     dp.kj = d_kj;
     dp.ksrc = d_ksrc;
+    dp.long_cols = d_long;
+    dp.nlong = (int32_t)long_cols.size();
     dp.batch_count = 0;
     dp.inst = nullptr;
     dp.inst_norm1 = dp.inst_b1 = nullptr;
@@ -1463,7 +1515,7 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                 if (large_before) cudaStreamWaitEvent(st, large_before, 0);
                 emit_small(l);
             }
-            if (W.asm_cnt == 0 && W.steps.empty()) continue;
+            if (W.asm_cnt == 0 && W.steps.empty() && W.thin_cnt == 0) continue;
             if (small_before) cudaStreamWaitEvent(sd, small_before, 0);
             const bool latency_bound = W.lvl_w.flops / 1.0e12 < c->tune_ratio * W.lvl_chain * 35e-6;
             // (a latency-bound level keeps the FP64 level kernel in the tensor-core
@@ -1482,10 +1534,17 @@ int factorise_enqueue(ipm_ctx *c, const double *theta, double rho, double delta,
                 cudaEventRecord(last_large, sd);
                 continue;
             }
-            if (W.asm_cnt > 0) {
+            if (W.asm_cnt2 > 0) {
                 Prof pr(c, IPM_K_LARGE_ASSEMBLE, W.asm_w, sd);
-                launch_large_assemble(c->dp, V, c->fronts, c->asm_items + W.asm_off, c->asm_info + W.asm_off,
-                                      c->asm_cr, W.asm_cnt, sd);
+                launch_large_assemble(c->dp, V, c->fronts, c->asm_items + W.asm_off2, c->asm_info + W.asm_off2,
+                                      c->asm_cr, W.asm_cnt2, sd);
+                nl++;
+            }
+            if (W.thin_cnt > 0) {
+                Prof pr(c, IPM_K_LARGE_PANEL, W.thin_w, sd);
+                launch_thin_fronts(c->dp, V, c->fronts, c->D, c->Dinv, c->dyn, c->ctl, c->thin_list + W.thin_off,
+                                   c->thin_asm + W.thin_off, c->thin_slot + W.thin_off, c->asm_info, c->asm_cr,
+                                   c->panel_ws, W.thin_cnt, c->opt.nb, sd);
                 nl++;
             }
             prev_rest = nullptr;
@@ -2367,6 +2426,7 @@ int ipm_get_info(ipm_ctx *c, ipm_info *out) {
     out->schedule = c->dep_sched ? IPM_SCHED_DEPENDENCY : IPM_SCHED_LEVELS;
     out->steps_levels = c->steps_levels;
     out->steps_dependency = c->steps_dependency;
+    out->nfronts_thin = c->nfronts_thin;
     out->tune_ms = c->tune_ms;
     out->omega = c->omega;
     for (int i = 0; i < 16; i++) out->omega_hist[i] = c->omega_hist[i];

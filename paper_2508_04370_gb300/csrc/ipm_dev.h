@@ -79,6 +79,10 @@ struct DevPlan {
     const int64_t *kp;
     const int32_t *kj;
     const int64_t *ksrc;
+    // columns of K with more than kLongColumn stored entries (dense rows of A):
+    // summed by a whole CTA each in the norm
+    const int32_t *long_cols;
+    int32_t nlong;
     // batches of independent problems: instance of each unknown (factorisation
     // order) and, per instance, ||K_b||_1 and eps_piv ||K_b||_1; null otherwise
     int32_t batch_count;
@@ -254,6 +258,15 @@ constexpr int kTrsmItemRowsHost = 32;  // rows of a triangular-solve item of the
 constexpr int kPanelWsHost = 32 * 33 + 32;
 void launch_large_update_strip(const DevPlan &P, double *fronts, const double *D, const TileItem *items,
                                int32_t count, int32_t w, cudaStream_t st);
+constexpr int64_t kLongColumn = 4096;
+// thin fronts (k <= nb, f <= kThinMaxF), one CTA per front: list[i] the front,
+// first_asm[i] its first assembly item (one per 32 columns, rows from the
+// block's first column), slots[i] its panel workspace slot
+constexpr int kThinMaxF = 512;
+void launch_thin_fronts(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
+                        DevCtl *ctl, const int32_t *list, const int32_t *first_asm, const int32_t *slots,
+                        const AsmItem *ainfo, const int32_t *acr, double *pws, int32_t count, int32_t nb,
+                        cudaStream_t st);
 void launch_large_level(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
                         DevCtl *ctl, const FactorItem *items, int32_t count, int32_t *sync, int32_t ncounters,
                         const AsmItem *ainfo, const int32_t *acr, double *pws, int32_t nb, int32_t grid,

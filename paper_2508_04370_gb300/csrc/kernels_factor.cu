@@ -723,6 +723,20 @@ __device__ __forceinline__ void body_tile(const DevPlan &P, double *__restrict__
     w = min(w, P.sn_k[s] - p0);  // ragged last panel
     double *F = fronts + P.sn_off[s];
     const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    // this thread's 2 x 2 outputs of the tile (lower part, columns from the
+    // panel's end), fetched with the operands: their latency overlaps the
+    // operand loads instead of following the products
+    double cv[2][2];
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        const int j = j0 + ty + 16 * b;
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+            const int i = i0 + tx + 16 * a;
+            cv[a][b] = (j < f && j >= p0 + w && i < f && i >= j) ? __ldcg(F + (int64_t)j * ld + i) : 0.0;
+        }
+    }
     {
         // all loads in flight before the shared-memory stores
         constexpr int U = 32 * T / kBodyThreads;
@@ -744,7 +758,6 @@ __device__ __forceinline__ void body_tile(const DevPlan &P, double *__restrict__
         }
     }
     __syncthreads();
-    const int tx = tid & 15, ty = tid >> 4;
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
     for (int q = 0; q < w; q++) {
         const double a0 = As[q][tx], a1 = As[q][tx + 16];
@@ -761,10 +774,7 @@ __device__ __forceinline__ void body_tile(const DevPlan &P, double *__restrict__
 #pragma unroll
         for (int a = 0; a < 2; a++) {
             const int i = i0 + tx + 16 * a;
-            if (i < f && i >= j) {
-                double *e = F + (int64_t)j * ld + i;
-                *e = __ldcg(e) - acc[a][b];
-            }
+            if (i < f && i >= j) F[(int64_t)j * ld + i] = cv[a][b] - acc[a][b];
         }
     }
 }
@@ -872,6 +882,43 @@ __global__ void __launch_bounds__(kBodyThreads) k_large_update_strip(DevPlan P, 
     body_strip(P, fronts, Dg, it.s, it.i0, it.j0, it.p0, w, pool);
 }
 
+// A thin front (one pivot block, k <= nb, f <= kThinMaxF) whole in one CTA:
+// the same bodies as the one-launch-per-step kernels, called in sequence
+// (assembly by 32-column blocks, the diagonal block, the triangular solve in
+// 32-row items, the trailing 32 x 32 tiles), so the front's values are
+// those of the per-step path bit for bit; a level of many such fronts costs
+// one launch instead of one per body and item.
+__global__ void __launch_bounds__(kBodyThreads) k_thin_fronts(DevPlan P, DevVals V, double *__restrict__ fronts,
+                                                               double *__restrict__ Dg, double *__restrict__ Dig,
+                                                               double *__restrict__ dyng, DevCtl *ctl,
+                                                               const int32_t *__restrict__ list,
+                                                               const int32_t *__restrict__ first_asm,
+                                                               const int32_t *__restrict__ slots,
+                                                               const AsmItem *__restrict__ ainfo,
+                                                               const int32_t *__restrict__ acr, double *__restrict__ pws,
+                                                               int nb) {
+    __shared__ double pool[kPoolDoubles];
+    const int s = list[blockIdx.x];
+    const int f = P.sn_f[s], k = P.sn_k[s];
+    const int64_t a0 = first_asm[blockIdx.x];
+    for (int cl = 0, a = 0; cl < f; cl += 32, a++) {
+        body_assemble(P, V, fronts, s, cl, min(cl + 32, f), ainfo[a0 + a], acr, pool);
+        __syncthreads();
+    }
+    double *ws = pws + (int64_t)slots[blockIdx.x] * kPanelWs;
+    body_diag(P, V, fronts, Dg, Dig, dyng, ctl, s, 0, nb, ws, pool);
+    __syncthreads();
+    for (int r0 = k; r0 < f; r0 += kTrsmItemRows) {
+        body_trsm<kTrsmItemRows / kTrsmRows>(P, fronts, s, r0, min(r0 + kTrsmItemRows, f), 0, nb, ws, pool);
+        __syncthreads();
+    }
+    for (int j0 = k; j0 < f; j0 += kUpdTile)
+        for (int i0 = j0; i0 < f; i0 += kUpdTile) {
+            body_tile(P, fronts, Dg, s, i0, j0, 0, nb, pool);
+            __syncthreads();
+        }
+}
+
 // Persistent level kernel: all large-front items of one tree level in one
 // launch.  CTAs take tickets in the host's order, wait (thread 0, bounded
 // spin on acquire loads) until the item's counters reach their thresholds,
@@ -950,29 +997,62 @@ __global__ void __launch_bounds__(kBodyThreads) k_large_level(DevPlan P, DevVals
 // ||K||_1 of the regularised augmented matrix (maximum absolute row sum of
 // the symmetric matrix, fixed summation order per row); also checks that
 // Theta is positive and finite.
+// |K_pi| of stored entry p of column i (with the static terms)
+__device__ __forceinline__ double kabs(const DevPlan &P, const DevVals &V, int i, int64_t p, bool &bad) {
+    const int64_t src = P.ksrc[p];
+    double val;
+    if (P.form == 2) val = V.nev[src] + (P.kj[p] == i ? V.delta : 0.0);
+    else if (src >= 0) val = V.Ax[src];
+    else if (src == kDualDiag) val = V.delta;
+    else {
+        const double th = V.theta[-1 - src];
+        if (!(th > 0.0) || !isfinite(th)) bad = true;
+        val = 1.0 / th + V.rho;
+    }
+    return fabs(val);
+}
+
+// ||K||_1: column sums in entry order, one thread per column; columns longer
+// than kLongColumn are left to k_norm1_long (a thread alone on a dense row of
+// A would take milliseconds)
 __global__ void k_norm1(DevPlan P, DevVals V, DevCtl *ctl) {
     double mx = 0.0;
     bool bad = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+        if (P.kp[i + 1] - P.kp[i] > kLongColumn) continue;
         double sum = 0.0;
-        for (int64_t p = P.kp[i]; p < P.kp[i + 1]; p++) {
-            const int64_t src = P.ksrc[p];
-            double val;
-            if (P.form == 2) val = V.nev[src] + (P.kj[p] == i ? V.delta : 0.0);
-            else if (src >= 0) val = V.Ax[src];
-            else if (src == kDualDiag) val = V.delta;
-            else {
-                const double th = V.theta[-1 - src];
-                if (!(th > 0.0) || !isfinite(th)) bad = true;
-                val = 1.0 / th + V.rho;
-            }
-            sum += fabs(val);
-        }
+        for (int64_t p = P.kp[i]; p < P.kp[i + 1]; p++) sum += kabs(P, V, i, p, bad);
         mx = fmax(mx, sum);
         if (P.inst) atomicMax((unsigned long long *)&P.inst_norm1[P.inst[i]], (unsigned long long)__double_as_longlong(sum));
     }
     mx = warp_max(mx);
     if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long *)&ctl->norm1, (unsigned long long)__double_as_longlong(mx));
+    if (bad) atomicOr(&ctl->status, kStatNonFinite);
+}
+
+// One long column per CTA: thread t sums the t-th of 256 contiguous runs in
+// entry order, then the runs' sums are added pairwise in a fixed tree (a
+// deterministic order, not the sequential one).
+__global__ void __launch_bounds__(256) k_norm1_long(DevPlan P, DevVals V, DevCtl *ctl) {
+    __shared__ double part[256];
+    const int i = P.long_cols[blockIdx.x];
+    const int64_t p0 = P.kp[i], n = P.kp[i + 1] - p0;
+    const int64_t run = (n + 255) / 256;
+    const int64_t a = p0 + run * threadIdx.x, b = min(a + run, p0 + n);
+    bool bad = false;
+    double sum = 0.0;
+    for (int64_t p = a; p < b; p++) sum += kabs(P, V, i, p, bad);
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicMax((unsigned long long *)&ctl->norm1, (unsigned long long)__double_as_longlong(part[0]));
+        if (P.inst)
+            atomicMax((unsigned long long *)&P.inst_norm1[P.inst[i]], (unsigned long long)__double_as_longlong(part[0]));
+    }
     if (bad) atomicOr(&ctl->status, kStatNonFinite);
 }
 
@@ -1325,6 +1405,15 @@ void launch_large_update_strip(const DevPlan &P, double *fronts, const double *D
     k_large_update_strip<<<count, kBodyThreads, 0, st>>>(P, fronts, D, items, w);
 }
 
+void launch_thin_fronts(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
+                        DevCtl *ctl, const int32_t *list, const int32_t *first_asm, const int32_t *slots,
+                        const AsmItem *ainfo, const int32_t *acr, double *pws, int32_t count, int32_t nb,
+                        cudaStream_t st) {
+    if (count <= 0) return;
+    k_thin_fronts<<<count, kBodyThreads, 0, st>>>(P, V, fronts, D, Dinv, dyn, ctl, list, first_asm, slots, ainfo, acr,
+                                                   pws, nb);
+}
+
 void launch_large_level(const DevPlan &P, const DevVals &V, double *fronts, double *D, double *Dinv, double *dyn,
                         DevCtl *ctl, const FactorItem *items, int32_t count, int32_t *sync, int32_t ncounters,
                         const AsmItem *ainfo, const int32_t *acr, double *pws, int32_t nb, int32_t grid,
@@ -1372,6 +1461,7 @@ void launch_norm1(const DevPlan &P, const DevVals &V, DevCtl *ctl, double eps_pi
     const int grid = (P.N + 255) / 256 < 608 ? (P.N + 255) / 256 : 608;
     if (P.inst) cudaMemsetAsync(P.inst_norm1, 0, sizeof(double) * P.batch_count, st);
     k_norm1<<<grid > 0 ? grid : 1, 256, 0, st>>>(P, V, ctl);
+    if (P.nlong > 0) k_norm1_long<<<P.nlong, 256, 0, st>>>(P, V, ctl);
     k_set_b1<<<P.inst ? (P.batch_count + 255) / 256 : 1, 256, 0, st>>>(P, ctl, eps_piv);
 }
 

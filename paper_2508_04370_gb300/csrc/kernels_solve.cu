@@ -861,6 +861,8 @@ __global__ void k_residual(DevPlan P, DevVals V, const double *__restrict__ f, c
     double xm = 0.0;
     bool bad = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+        xm = fmax(xm, fabs(x[i]));
+        if (P.kp[i + 1] - P.kp[i] > kLongColumn) continue;  // k_residual_long
         double s = 0.0, sa = 0.0, se = 0.0;
         for (int64_t p = P.kp[i]; p < P.kp[i + 1]; p++) {
             const int64_t src = P.ksrc[p];
@@ -879,11 +881,57 @@ __global__ void k_residual(DevPlan P, DevVals V, const double *__restrict__ f, c
         r[i] = ri;
         ad[i] = sa;
         ae[i] = se;
-        xm = fmax(xm, fabs(x[i]));
     }
     xm = warp_max(xm);
     if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long *)&ctl->dinf, (unsigned long long)__double_as_longlong(xm));
     if (bad) atomicOr(&ctl->status, kStatNonFinite);
+}
+
+// The rows of K longer than kLongColumn (dense rows of A), one CTA each:
+// thread t sums the t-th of 256 contiguous runs of the row in entry order,
+// the runs' sums are added pairwise in a fixed tree.
+__global__ void __launch_bounds__(256) k_residual_long(DevPlan P, DevVals V, const double *__restrict__ f,
+                                                       const double *__restrict__ x, double *__restrict__ r,
+                                                       double *__restrict__ ad, double *__restrict__ ae, DevCtl *ctl,
+                                                       const int32_t *skip) {
+    if (skip && *skip) return;
+    __shared__ double ps[256], pa[256], pe[256];
+    const int i = P.long_cols[blockIdx.x];
+    const int64_t p0 = P.kp[i], n = P.kp[i + 1] - p0;
+    const int64_t run = (n + 255) / 256;
+    const int64_t a = p0 + run * threadIdx.x, b = min(a + run, p0 + n);
+    double s = 0.0, sa = 0.0, se = 0.0;
+    for (int64_t p = a; p < b; p++) {
+        const int64_t src = P.ksrc[p];
+        double val;
+        if (P.form == 2) val = V.nev[src] + (P.kj[p] == i ? V.delta : 0.0);
+        else if (src >= 0) val = V.Ax[src];
+        else if (src == kDualDiag) val = V.delta;
+        else val = -(1.0 / V.theta[-1 - src] + V.rho);
+        const double xj = x[P.kj[p]];
+        s += val * xj;
+        sa += fabs(val) * fabs(xj);
+        se += fabs(val);
+    }
+    ps[threadIdx.x] = s;
+    pa[threadIdx.x] = sa;
+    pe[threadIdx.x] = se;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            ps[threadIdx.x] += ps[threadIdx.x + h];
+            pa[threadIdx.x] += pa[threadIdx.x + h];
+            pe[threadIdx.x] += pe[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double ri = f[i] - ps[0];
+        if (!isfinite(ri)) atomicOr(&ctl->status, kStatNonFinite);
+        r[i] = ri;
+        ad[i] = pa[0];
+        ae[i] = pe[0];
+    }
 }
 
 // omega = max_i |r_i| / den_i, den_i = (|K||x| + |f|)_i, replaced by
@@ -1046,6 +1094,7 @@ void launch_residual_omega(const DevPlan &P, const DevVals &V, const double *f, 
         k_clear_norms<<<1, 1, 0, st>>>(ctl, skip);
     }
     k_residual<<<grid, 256, 0, st>>>(P, V, f, x, r, ad, ae, ctl, skip);
+    if (P.nlong > 0) k_residual_long<<<P.nlong, 256, 0, st>>>(P, V, f, x, r, ad, ae, ctl, skip);
     k_omega<<<grid, 256, 0, st>>>(P.N, r, ad, ae, f, ctl, skip);
 }
 

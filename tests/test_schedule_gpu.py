@@ -134,3 +134,27 @@ def test_kernel_trace_matches_kernel_stats(pkg):
     # a second call returns nothing new
     assert pkg.ipm_kernel_trace(s.ctx)["count"] == 0
     s.close()
+
+
+def test_thin_fronts_block_angular(pkg):
+    """A block-angular LP whose fronts are one column plus the dense linking
+    rows (k = 1, f ~ 150): the levels outside the level kernel run these
+    thin fronts whole, one CTA each, with the per-step bodies in sequence.
+    The factor must equal the per-step path's (the dependency order) bit for
+    bit and the oracle's to the parity bar."""
+    from test_parity_gpu import check_pair, run_pair
+
+    lp = synth.block_angular(blocks=20, bm=60, bn=160, density=0.05, linking=150, seed=5)
+    th = synth.theta_loguniform(lp.n, 51)
+    s1, f1, i1 = _factor(pkg, lp, th, pkg.IPM_SCHED_LEVELS)
+    s2, f2, i2 = _factor(pkg, lp, th, pkg.IPM_SCHED_DEPENDENCY)
+    assert i1["nfronts_thin"] > 100, i1["nfronts_thin"]
+    assert i1["status"] & ~2 == 0 and i2["status"] == i1["status"]
+    for a, b in zip(f1, f2):
+        assert np.array_equal(a, b)
+    s1.close()
+    s2.close()
+    r = run_pair(pkg, lp, th, synth.rhs_normal(lp.n, 52), synth.rhs_normal(lp.m, 53), ordering=pkg.IPM_ORD_ND,
+                 level_kernel=0, schedule=pkg.IPM_SCHED_LEVELS)
+    err = check_pair(r, lp)
+    print(f"block-angular thin fronts {i1['nfronts_thin']}: omega {r['w_gpu']:.2e} rel err {err:.2e}")
