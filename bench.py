@@ -92,6 +92,7 @@ class Workload:
                 lp = synth.by_name(name, 1)
             self.lp = lp
             n, m = lp.n, lp.m
+            self.form_auto = name == "block_angular"
             if name == "grid64_q4":
                 self.ordering_name = "nested-dissection"
                 self.desc = ("grid multicommodity LP grid64_q4: 64x64 4-neighbour grid, 4 commodities, m=24444, "
@@ -101,6 +102,14 @@ class Workload:
                 self.ordering_name = "AMD"
                 self.desc = ("random sparse LP m=300, n=800, 6 nonzeros per column, N(0,1); Theta 10^U[-8,8]; "
                              "rho=delta=1e-8; AMD ordering; factorise + 2 refined solves")
+            elif name == "block_angular":
+                self.ordering_name = "AMD"
+                self.fp64_target = 1e-10  # matched residual on every path
+                self.desc = ("block-angular LP: 200 diagonal blocks of 150 x 400, Bernoulli(0.02) N(0,1), plus 300 dense "
+                             f"N(0,1) linking rows (m={m}, n={n}, nnz(A)={len(lp.rowidx)}); Theta 10^U[-8,8]; "
+                             "rho=delta=1e-8; AMD ordering, augmented system or normal equations by the library's "
+                             "chooser; one IPM iteration = factorise + 2 solves refined to omega <= 1e-10 on K on every "
+                             "path")
             elif name in ("staircase", "staircase10"):
                 per = 50 if name == "staircase" else 10
                 self.ordering_name = "nested-dissection"
@@ -137,6 +146,8 @@ class Workload:
     def solver(self, pkg, **opts):
         if self.lps is not None:
             return pkg.BatchSolver(self.lps, ordering=self.ordering(pkg), **opts)
+        if getattr(self, "form_auto", False):
+            opts = dict(opts, form=pkg.IPM_FORM_AUTO)
         return pkg.Solver.from_lp(self.lp, ordering=self.ordering(pkg), **opts)
 
 
@@ -512,6 +523,20 @@ class OracleArm:
                            f"one IPM iteration (factorise + 2 solves refined to 1e-10) at schedule iterations spread "
                            f"like the timed steps, time x {self.scale:.1f} (the full problem's front flops over the "
                            f"sample's)")
+        elif W.name == "block_angular":
+            # the same generator with 20 blocks, scaled by the front flops
+            lp = synth.block_angular(blocks=20, seed=1)
+            self.o, flops = oracle_problem(lp, pkg, W.ordering(pkg))
+            full = pkg.ipm_create(pkg.ipm_default_options())
+            pkg.ipm_analyse(full, W.lp.m, W.lp.n, W.lp.colptr, W.lp.rowidx, pkg.IPM_FORM_AUGMENTED, W.ordering(pkg))
+            _, finfo = pkg.ipm_get_info(full)
+            pkg.ipm_destroy(full)
+            self.scale = finfo.flops_factor / flops
+            self.thetas = [synth.theta_loguniform(lp.n, 1 + t) for t in range(3)]
+            self.rhs = [(synth.rhs_normal(lp.n, 10 + 2 * t), synth.rhs_normal(lp.m, 11 + 2 * t)) for t in range(2)]
+            self.sample = (f"the same block-angular generator with 20 blocks (m={lp.m}, n={lp.n}, {flops:.3e} front "
+                           f"flops), one IPM iteration (factorise + 2 refined solves), time x {self.scale:.1f} (the "
+                           f"full problem's front flops over the sample's)")
         elif W.lps is None:
             self.o, _ = oracle_problem(W.lp, pkg, W.ordering(pkg))
             self.scale = 1.0
@@ -571,7 +596,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="staircase",
-                    choices=["staircase", "grid64_q4", "random_300x800", "staircase10", "batch512"])
+                    choices=["staircase", "grid64_q4", "random_300x800", "staircase10", "batch512", "block_angular"])
     ap.add_argument("--paths", default="fp64,sliced,mixed", help="comma-separated subset of fp64,sliced,mixed")
     ap.add_argument("--autotune-reps", type=int, default=None,
                     help="repetitions per autotuner candidate (0: keep the library's default launch shapes)")
