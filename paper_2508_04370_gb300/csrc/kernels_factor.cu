@@ -173,57 +173,17 @@ __device__ __forceinline__ void pivot_warp(const double *Fd, int LDD, int p, int
     }
 }
 
-// The same decision with the pivot column held one row per lane: lane j
-// holds c = F_jp and g = F_jj (rows j > p of the block [0, w) take part),
-// sl = s_j; d is the pivot after the static term.  Returns the pivot in
-// every lane and its reciprocal through *rinv; lane 0 records D, the
-// statically regularised pivot d (the lift D - d is formed later, off the
-// pivot chain) and the status.
-__device__ __forceinline__ double pivot_lanes(double c, double g, int sl, int p, int w, int sp, double d,
-                                              double b1floor, double *rinv) {
-    const int lane = threadIdx.x & 31;
-    const long long db = dbits(d);
-    const long long sdb = sp < 0 ? db ^ kSignBit : db;
-    const long long b1b = dbits(b1floor);
-    const long long tb = gt_nonneg(sdb, b1b) ? sdb : b1b;
-    const bool t_ok = tb > 0x000fffffffffffffll && tb < kInfBits;
-    const bool take = lane > p && lane < w && sl == sp;
-    bool maybe = false, screenable = false;
-    if (take) {
-        const long long jb = dbits(g);
-        const long long ja = jb & kAbsMask;
-        const bool cand = ja != 0 && ja <= kInfBits && ((jb < 0) == (sp < 0));
-        if (cand) {
-            const long long ab = dbits(c) & kAbsMask;
-            if (ab != 0) {
-                screenable = t_ok && ab >= kTiny && ab < kHuge && ja > 0x000fffffffffffffll && ja < kInfBits;
-                maybe = !screenable || 2 * (ab - kBias) >= (ja - kBias) + (tb - kBias) - kScreen;
-            }
-        }
-    }
-    const long long dnb_fast = sp < 0 ? tb ^ kSignBit : tb;
-    double r = recip_pivot(__longlong_as_double(dnb_fast));
-    long long dnb = dnb_fast;
-    if (__any_sync(0xffffffffu, maybe)) {
-        dnb = pivot_exact_bits(maybe, screenable, c, g, tb, sdb, b1b, sp);
-        if (dnb != dnb_fast) r = recip_pivot(__longlong_as_double(dnb));
-    }
-    const double dn = __longlong_as_double(dnb);
-    *rinv = r;
-    return dn;
-}
-
-// Named barriers 1-4 of a 128-thread CTA, the id chosen by parity so that it
-// stays an immediate: sync/arrive on barrier base + (parity & 1).
-template <int kBase>
+// Named barriers, the id chosen by parity so that it stays an immediate:
+// sync/arrive on barrier base + (parity & 1) with kCount threads.
+template <int kBase, int kCount = 128>
 __device__ __forceinline__ void bar_sync_parity(int parity) {
-    if (parity & 1) asm volatile("bar.sync %0, 128;" ::"n"(kBase + 1) : "memory");
-    else asm volatile("bar.sync %0, 128;" ::"n"(kBase) : "memory");
+    if (parity & 1) asm volatile("bar.sync %0, %1;" ::"n"(kBase + 1), "n"(kCount) : "memory");
+    else asm volatile("bar.sync %0, %1;" ::"n"(kBase), "n"(kCount) : "memory");
 }
-template <int kBase>
+template <int kBase, int kCount = 128>
 __device__ __forceinline__ void bar_arrive_parity(int parity) {
-    if (parity & 1) asm volatile("bar.arrive %0, 128;" ::"n"(kBase + 1) : "memory");
-    else asm volatile("bar.arrive %0, 128;" ::"n"(kBase) : "memory");
+    if (parity & 1) asm volatile("bar.arrive %0, %1;" ::"n"(kBase + 1), "n"(kCount) : "memory");
+    else asm volatile("bar.arrive %0, %1;" ::"n"(kBase), "n"(kCount) : "memory");
 }
 
 // ------------------------------------------------------------ small fronts
@@ -424,20 +384,26 @@ __device__ __forceinline__ void body_assemble(const DevPlan &P, const DevVals &V
 }
 
 // The nb x nb diagonal block of panel [p0, p0 + nb) of front s as a
-// two-stage pipeline over the pivots, on threads 0-127.  Warp 0 owns the
-// pivot chain: lane j keeps c = F_jp of the current pivot column, g = F_jj
-// and gs = F_jj + s_j sigma_j (the static term) up to date; per pivot it
-// decides (pivot_lanes), scales the column (l_jp = F_jp / d_p, keeping the
-// unscaled w_jp = F_jp), publishes p, and brings c, g and gs to pivot p + 1
-// with three independent FMAs.  Warps 1-3 apply pivot p to the strictly
-// lower entries of columns >= p + 2 while warp 0 already works on pivot
-// p + 1, which needs only column p + 1 and the diagonal; each of their
-// threads holds up to five of these entries in registers for the whole
-// block and stores one when its column has received its last update here.
-// Named barriers 1-2 (pivot published) and 3-4 (columns updated) alternate
-// by pivot parity, so neither side runs more than one pivot ahead.  Every
-// entry receives the updates of all earlier pivots in pivot order, as in the
-// sequential elimination.  The factorised block goes back to the slab (L
+// pipeline over the pivots spread over the SM's four sub-partitions (each
+// FP64 instruction holds its sub-partition's FP64 pipe for tens of cycles,
+// so the pivot chain is kept to as few FP64 instructions as possible on one
+// of them).  Warp 0 owns the pivot chain: lane j keeps c = F_jp of the
+// current pivot column, g = F_jj and gs = F_jj + s_j sigma_j (the static
+// term) up to date; per pivot it screens the Prop. 3 candidates, scales the
+// column (l_jp = F_jp / d_p, keeping the unscaled w_jp = F_jp), publishes p,
+// and brings gs (first, for the next pivot), c and g to pivot p + 1.  Warp 5
+// forms the reciprocal of each pivot's common case (the pivot or the lift
+// floor, whichever is larger) from d, handed over through shared memory, while
+// warp 0 screens; warp 0 recomputes it only when the exact rule moves the
+// pivot.  Warps 2, 3, 6 and 7 apply pivot p to the strictly lower entries
+// of columns >= p + 2 while warp 0 already works on pivot p + 1, which needs
+// only column p + 1 and the diagonal; each of their threads holds up to four
+// of these entries in registers for the whole block and stores one when its
+// column has received its last update here.  Named barriers alternate by
+// pivot parity (1-2 pivot published, 3-4 columns updated, 5-6 d ready, 7-8
+// reciprocal ready), so no side runs more than one pivot ahead.  Every value
+// is formed by the same operations as in a single warp, so the factor does
+// not depend on the split.  The factorised block goes back to the slab (L
 // strictly below the diagonal, D on it) together with D, 1/D and the lifts,
 // and the panel workspace ws receives the rows of L_11 (row-major,
 // ws[q * 33 + q'] = L_qq') and 1 / d_q for the triangular solve below.
@@ -447,12 +413,17 @@ __device__ __forceinline__ void body_diag(const DevPlan &P, const DevVals &V, do
                                           double *__restrict__ Dg, double *__restrict__ Dig,
                                           double *__restrict__ dyng, DevCtl *ctl, int s, int p0, int nb,
                                           double *__restrict__ ws, double *pool) {
-    constexpr int LDD = 33, NT = 128, NU = NT - 32, kOwn = 5;  // 5 x 96 >= 435 entries
-    constexpr int kBarPub = 1, kBarUpd = 3;
+    // warp 0 (SM sub-partition 0) carries the chain, warp 5 (sub-partition 1)
+    // forms each pivot's reciprocal, warps 2, 3, 6 and 7 (sub-partitions 2
+    // and 3) apply the pivots to the later columns
+    constexpr int LDD = 33, NU = 128, kOwn = 4;  // 4 x 128 >= 435 entries
+    constexpr int kBarPub = 1, kBarUpd = 3, kBarD = 5, kBarR = 7;
+    constexpr int kPubCount = 32 + NU;  // warp 0 and the update warps
     double *Fd = pool;                          // 32 x 33, column-major
     double(*wsv)[32] = reinterpret_cast<double(*)[32]>(pool + 32 * 33);  // [2][32]
     double *Dtmp = pool + 32 * 33 + 64, *dstat = Dtmp + 32, *rtmp = dstat + 32;
     int8_t *sg = reinterpret_cast<int8_t *>(rtmp + 32);
+    double *shd = rtmp + 32 + 4, *shr = shd + 2;  // pivot d and its reciprocal, by pivot parity
     const int k = P.sn_k[s], ld = P.sn_ld[s], c0 = P.sn_c0[s];
     const int w = min(p0 + nb, k) - p0;
     if (w <= 0) return;  // uniform over the CTA
@@ -477,16 +448,47 @@ __device__ __forceinline__ void body_diag(const DevPlan &P, const DevVals &V, do
     __syncthreads();
     if (warp == 0) {
         const double b1floor = pivot_floor(P, ctl, c0);
+        const long long b1b = dbits(b1floor);
         const int sl = sg[lane];
         double g = lane < w ? Fd[lane * LDD + lane] : 0.0;   // F_jj of row j = lane
         double gs = g + (sl < 0 ? -V.rho : V.delta);
         double c = (lane > 0 && lane < w) ? Fd[lane] : 0.0;  // column 0
         double my_dn = 0.0, my_d = 0.0, my_r = 0.0;          // lane p keeps pivot p's values
+        double d = __shfl_sync(0xffffffffu, gs, 0);
+        if (lane == 0) shd[0] = d;
+        __syncwarp();
+        bar_arrive_parity<kBarD, 64>(0);
         for (int p = 0; p < w; p++) {
             const int sp = __shfl_sync(0xffffffffu, sl, p);
-            const double d = __shfl_sync(0xffffffffu, gs, p);
-            double rinv;
-            const double dn = pivot_lanes(c, g, sl, p, w, sp, d, b1floor, &rinv);
+            // the Prop. 3 screen (as in pivot_lanes) while warp 5 forms the
+            // reciprocal of the common-case pivot
+            const long long db = dbits(d);
+            const long long sdb = sp < 0 ? db ^ kSignBit : db;
+            const long long tb = gt_nonneg(sdb, b1b) ? sdb : b1b;
+            const bool t_ok = tb > 0x000fffffffffffffll && tb < kInfBits;
+            bool maybe = false, screenable = false;
+            if (lane > p && lane < w && sl == sp) {
+                const long long jb = dbits(g);
+                const long long ja = jb & kAbsMask;
+                const bool cand = ja != 0 && ja <= kInfBits && ((jb < 0) == (sp < 0));
+                if (cand) {
+                    const long long ab = dbits(c) & kAbsMask;
+                    if (ab != 0) {
+                        screenable = t_ok && ab >= kTiny && ab < kHuge && ja > 0x000fffffffffffffll && ja < kInfBits;
+                        maybe = !screenable || 2 * (ab - kBias) >= (ja - kBias) + (tb - kBias) - kScreen;
+                    }
+                }
+            }
+            const long long dnb_fast = sp < 0 ? tb ^ kSignBit : tb;
+            const bool any = __any_sync(0xffffffffu, maybe);
+            bar_sync_parity<kBarR, 64>(p);
+            double rinv = shr[p & 1];
+            long long dnb = dnb_fast;
+            if (any) {
+                dnb = pivot_exact_bits(maybe, screenable, c, g, tb, sdb, b1b, sp);
+                if (dnb != dnb_fast) rinv = recip_pivot(__longlong_as_double(dnb));
+            }
+            const double dn = __longlong_as_double(dnb);
             if (lane == p) {
                 my_dn = dn;
                 my_d = d;
@@ -499,14 +501,19 @@ __device__ __forceinline__ void body_diag(const DevPlan &P, const DevVals &V, do
                 wsv[p & 1][lane] = c;
             }
             __syncwarp();
-            bar_arrive_parity<kBarPub>(p);
+            bar_arrive_parity<kBarPub, kPubCount>(p);
             if (p + 1 < w) {
-                if (p >= 1) bar_sync_parity<kBarUpd>(p + 1);  // pivot p-1 applied to columns >= p+1
+                if (p >= 1) bar_sync_parity<kBarUpd, kPubCount>(p + 1);  // pivot p-1 applied to columns >= p+1
                 const double wn = __shfl_sync(0xffffffffu, c, p + 1);  // w_{p+1,p}, unscaled
                 const double fv = (lane > p + 1 && lane < w) ? Fd[(p + 1) * LDD + lane] : 0.0;
+                // the next pivot first, so that its reciprocal starts early
+                gs -= l * c;
+                d = __shfl_sync(0xffffffffu, gs, p + 1);
+                if (lane == 0) shd[(p + 1) & 1] = d;
+                __syncwarp();
+                bar_arrive_parity<kBarD, 64>(p + 1);
                 const double cn = fv - l * wn;
                 g -= l * c;
-                gs -= l * c;
                 c = lane > p + 1 ? cn : 0.0;
             }
         }
@@ -520,11 +527,26 @@ __device__ __forceinline__ void body_diag(const DevPlan &P, const DevVals &V, do
             const bool fin = (db & kAbsMask) < kInfBits && (dnb & kAbsMask) < kInfBits && (dnb & kAbsMask) != 0;
             if (!fin) atomicOr(&ctl->status, kStatNonFinite);
         }
-    } else if (warp < NT / 32) {
-        // this thread owns the strictly lower entries e = ut + 96 t of columns
+    } else if (warp == 5) {
+        // the reciprocal of each pivot's common case: the larger (as bit
+        // patterns) of s_p d and the lift floor, with the sign s_p
+        const long long b1b = dbits(pivot_floor(P, ctl, c0));
+        for (int p = 0; p < w; p++) {
+            const int sp = sg[p];
+            bar_sync_parity<kBarD, 64>(p);
+            const long long db = dbits(shd[p & 1]);
+            const long long sdb = sp < 0 ? db ^ kSignBit : db;
+            const long long tb = gt_nonneg(sdb, b1b) ? sdb : b1b;
+            const double r = recip_pivot(__longlong_as_double(sp < 0 ? tb ^ kSignBit : tb));
+            if (lane == 0) shr[p & 1] = r;
+            __syncwarp();
+            bar_arrive_parity<kBarR, 64>(p);
+        }
+    } else if (warp == 2 || warp == 3 || warp == 6 || warp == 7) {
+        // this thread owns the strictly lower entries e = ut + 128 t of columns
         // >= 2, enumerated last column first: e = r (r + 1) / 2 + c  ->
         // column w-2-r, row w-1-r+c (0 <= c <= r)
-        const int ut = tid - 32;
+        const int ut = ((warp & 3) - 2 + 2 * (warp >> 2)) * 32 + lane;
         const int nall = w >= 3 ? (w - 3) * (w - 2) / 2 : 0;
         int jo[kOwn], io[kOwn];
         double vo[kOwn];
@@ -544,7 +566,7 @@ __device__ __forceinline__ void body_diag(const DevPlan &P, const DevVals &V, do
             }
         }
         for (int q = 0; q < w; q++) {
-            bar_sync_parity<kBarPub>(q);
+            bar_sync_parity<kBarPub, kPubCount>(q);
             const int m = w - 3 - q;  // columns >= q + 2 have m (m + 1) / 2 such entries
             const int ne = m > 0 ? m * (m + 1) / 2 : 0;
             double lq[kOwn], wq[kOwn];
@@ -561,7 +583,7 @@ __device__ __forceinline__ void body_diag(const DevPlan &P, const DevVals &V, do
                     if (jo[t] == q + 2) Fd[jo[t] * LDD + io[t]] = vo[t];
                 }
             }
-            if (q <= w - 3) bar_arrive_parity<kBarUpd>(q);
+            if (q <= w - 3) bar_arrive_parity<kBarUpd, kPubCount>(q);
         }
     }
     __syncthreads();
