@@ -460,7 +460,7 @@ __device__ __forceinline__ void body_diag(const DevPlan &P, const DevVals &V, do
         bar_arrive_parity<kBarD, 64>(0);
         for (int p = 0; p < w; p++) {
             const int sp = __shfl_sync(0xffffffffu, sl, p);
-            // the Prop. 3 screen (as in pivot_lanes) while warp 5 forms the
+            // the Prop. 3 screen (on IEEE bit patterns) while warp 5 forms the
             // reciprocal of the common-case pivot
             const long long db = dbits(d);
             const long long sdb = sp < 0 ? db ^ kSignBit : db;
@@ -910,7 +910,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_large_update_strip(DevPlan P, 
 // 32-row items, the trailing 32 x 32 tiles), so the front's values are
 // those of the per-step path bit for bit; a level of many such fronts costs
 // one launch instead of one per body and item.
-__global__ void __launch_bounds__(kBodyThreads) k_thin_fronts(DevPlan P, DevVals V, double *__restrict__ fronts,
+__global__ void __launch_bounds__(kBodyThreads, 3) k_thin_fronts(DevPlan P, DevVals V, double *__restrict__ fronts,
                                                                double *__restrict__ Dg, double *__restrict__ Dig,
                                                                double *__restrict__ dyng, DevCtl *ctl,
                                                                const int32_t *__restrict__ list,
@@ -930,8 +930,10 @@ __global__ void __launch_bounds__(kBodyThreads) k_thin_fronts(DevPlan P, DevVals
     double *ws = pws + (int64_t)slots[blockIdx.x] * kPanelWs;
     body_diag(P, V, fronts, Dg, Dig, dyng, ctl, s, 0, nb, ws, pool);
     __syncthreads();
-    for (int r0 = k; r0 < f; r0 += kTrsmItemRows) {
-        body_trsm<kTrsmItemRows / kTrsmRows>(P, fronts, s, r0, min(r0 + kTrsmItemRows, f), 0, nb, ws, pool);
+    // (one row per warp: the light variant keeps three CTAs per SM; these
+    // fronts' solves are short, k <= 32 columns)
+    for (int r0 = k; r0 < f; r0 += kTrsmRows) {
+        body_trsm<1>(P, fronts, s, r0, min(r0 + kTrsmRows, f), 0, nb, ws, pool);
         __syncthreads();
     }
     for (int j0 = k; j0 < f; j0 += kUpdTile)
