@@ -106,18 +106,6 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
     const int f = P.sn_f[s], ld = P.sn_ld[s];
     double *F = fronts + P.sn_off[s];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) tc::tmem_alloc(&tbase, 256);  // 8 accumulators x 32 columns
-    if (tid == 0) {
-        tc::mbar_init(&bar_load, 1);
-        tc::mbar_init(&bar_mid, 1);
-        tc::mbar_init(&bar_mma, 1);
-        tc::fence_mbar_init();
-    }
-    if (tid < kSliceCols) eb_col[tid] = ws_exp[((int64_t)it.blk_b * kSliceRows + it.roff_b + tid) * 2 + 1];
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tmem = tbase;
     // One thread streams the kc chunks (32 columns of the panel pair each)
     // through the one buffer: copy, 72 MMAs into the same accumulators, wait
     // for them before the next copy.  bar_mma completes once every MMA it
@@ -132,7 +120,7 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
         for (int pr = 0; pr < 4; pr++)
             tc::bulk_g2s(B + pr * 4096, srcB + pr * kSlicePairBytes + it.roff_b * 128, 4096, &bar_load);
     };
-    auto chunk_mma = [&](int ch) {
+    auto chunk_mma = [&](int ch, uint32_t acc) {
         tc::fence_after_sync();
         constexpr uint32_t id = tc::idesc_bf16(kSliceRows, kSliceCols);
         const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(B);
@@ -145,22 +133,26 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
                 for (int kk = 0; kk < 2; kk++) {
                     const uint64_t ad = tc::smem_desc(a0 + (t >> 1) * (uint32_t)kSlicePairBytes + (t & 1) * 64 + kk * 32);
                     const uint64_t bd = tc::smem_desc(b0 + (u >> 1) * 4096u + (u & 1) * 64 + kk * 32);
-                    tc::mma_bf16(tmem + (uint32_t)(d * kSliceCols), ad, bd, id, (ch > 0 || t > 0 || kk > 0) ? 1u : 0u);
+                    tc::mma_bf16(acc + (uint32_t)(d * kSliceCols), ad, bd, id, (ch > 0 || t > 0 || kk > 0) ? 1u : 0u);
                 }
             }
     };
     const int kc = it.kc;
-    bool lead_ok = true;  // thread 0: every copy and MMA of the tile issued
+    // the first chunk's copy goes out before anything else the tile waits
+    // for (TMEM, the column scales)
     if (tid == 0) {
+        tc::mbar_init(&bar_load, 1);
+        tc::mbar_init(&bar_mid, 1);
+        tc::mbar_init(&bar_mma, 1);
+        tc::fence_mbar_init();
         chunk_copy(0);
-        if (tc::mbar_wait(&bar_load, 0)) {
-            chunk_mma(0);
-        } else {
-            atomicOr(&ctl->status, kStatTimeout | kStatWaitCopy);
-            tc::mbar_wait(&bar_load, 0);  // let the copies in flight land before the CTA exits
-            lead_ok = false;
-        }
     }
+    if (warp == 0) tc::tmem_alloc(&tbase, 256);  // 8 accumulators x 32 columns
+    if (tid < kSliceCols) eb_col[tid] = ws_exp[((int64_t)it.blk_b * kSliceRows + it.roff_b + tid) * 2 + 1];
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tbase;
     // the tile's FP64 entries of this thread's row and column half, fetched
     // while the copies and the MMAs run (independent loads; lower part only)
     constexpr int kHalf = kSliceCols / 2;
@@ -177,7 +169,16 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
         live |= (uint32_t)v << c;
         cv[c] = v ? F[(int64_t)col * ld + row] : 0.0;
     }
+    const int Ea = ws_exp[((int64_t)it.blk_a * kSliceRows + r) * 2 + 0];  // the row's scale
     if (tid == 0) {
+        bool lead_ok = true;  // every copy and MMA of the tile issued
+        if (tc::mbar_wait(&bar_load, 0)) {
+            chunk_mma(0, tmem);
+        } else {
+            atomicOr(&ctl->status, kStatTimeout | kStatWaitCopy);
+            tc::mbar_wait(&bar_load, 0);  // let the copies in flight land before the CTA exits
+            lead_ok = false;
+        }
         for (int ch = 1; ch < kc && lead_ok; ch++) {
             // the buffer is free once the previous chunk's MMAs are done
             tc::commit_to(&bar_mid);
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
                 lead_ok = false;
                 break;
             }
-            chunk_mma(ch);
+            chunk_mma(ch, tmem);
         }
         tc::commit_to(&bar_mma);
     }
@@ -205,7 +206,6 @@ __global__ void __launch_bounds__(kSlicedThreads, 2) k_update_sliced(DevPlan P, 
     ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the TMEM loads below are warp-collective
     tc::fence_after_sync();
     if (ok) {
-        const int Ea = ws_exp[((int64_t)it.blk_a * kSliceRows + r) * 2 + 0];
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
         for (int c8 = 0; c8 < kHalf / 8; c8++) {
