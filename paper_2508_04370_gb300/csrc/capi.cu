@@ -644,6 +644,7 @@ int build_solve_schedule(ipm_ctx *c, const std::vector<int32_t> &fwd_order, cons
     S.nsuper = ns;
     S.sync = c->solve_sync;
     S.yv = d_yv;
+    S.nyv = P.N;
     S.fwd_leaf = d_fleaf;
     S.bwd_leaf = d_bleaf;
     S.Linv = c->linv;

@@ -155,7 +155,9 @@ struct SolveSched {
     int32_t nfwd, nbwd, nsuper;
     long long spin_limit;    // polls before a dependency wait gives up (kStatTimeout)
     int32_t *sync;           // ticket + 3 x nsuper counters (forward), ticket + 2 x nsuper (backward)
-    double *yv;              // forward: y of split supernodes (before D^-1)
+    double *yv;              // the values split supernodes' blocks pass along their chain (y forward,
+                             // z backward), reset to an unset pattern before each sweep
+    int32_t nyv;
     const int32_t *fwd_leaf, *bwd_leaf;  // leaf groups: 8 childless single-item supernodes with f <= 32
                                          // per ticket (-1 pads), one warp each
     const double *Linv;                  // inverse unit-lower diagonal blocks, column-major 32 x 32

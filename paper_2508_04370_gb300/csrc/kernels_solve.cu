@@ -283,6 +283,46 @@ __device__ __forceinline__ void wait_count(const int32_t *cnt, int need, DevCtl 
     }
 }
 
+// The blocks of a split supernode pass their 32 values (y forward, z
+// backward) to the next block of the chain through S.yv, filled before the
+// sweep with a signalling-NaN pattern that no arithmetic result has: each
+// value is stored once per sweep (relaxed, gpu scope), so a relaxed load that
+// returns anything else has the final value, and the waiting block reads the
+// data itself instead of a counter and then the data.
+constexpr unsigned long long kUnset = 0x7FF4DEAD7FF4DEADull;
+
+__device__ __forceinline__ void st_relaxed(double *p, double v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
+}
+
+__device__ __forceinline__ double ld_relaxed(const double *p) {
+    long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return __longlong_as_double(v);
+}
+
+// One warp: lane q < wp returns p[q] once it is set (0 beyond wp); gives up
+// after `limit` rounds like wait_count.
+__device__ __forceinline__ double poll_block(const double *p, int wp, DevCtl *ctl, long long limit) {
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    bool pending = lane < wp;
+    long long spins = 0;
+    while (true) {
+        if (pending) {
+            v = ld_relaxed(p + lane);
+            pending = (unsigned long long)__double_as_longlong(v) == kUnset;
+        }
+        if (!__any_sync(0xffffffffu, pending)) break;
+        if (++spins > limit) {
+            if (lane == 0) atomicOr(&ctl->status, kStatTimeout);
+            break;
+        }
+        __nanosleep(64);
+    }
+    return lane < wp ? v : 0.0;
+}
+
 // Take the next ticket (thread 0) and publish its item and node to the CTA.
 __device__ __forceinline__ bool next_item(const SolveSched &S, const SolveItem *items, int nitems, SolveItem &it,
                                           SolveNode &nd, SolveItem *sh_it, SolveNode *sh_nd) {
@@ -587,7 +627,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
     __shared__ SolveNode sh_nd;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (skip && *skip) return;
-    int32_t *cnt = S.sync + 1, *done = cnt + S.nsuper, *tcnt = done + S.nsuper;
+    int32_t *cnt = S.sync + 1, *done = cnt + S.nsuper;
     SolveItem it;
     SolveNode nd;
     while (next_item(S, S.fwd, S.nfwd, it, nd, &sh_it, &sh_nd)) {
@@ -639,9 +679,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
                 // applies columns 4w..4w+3 of each
                 double acc = 0.0;
                 for (int bp = 0; bp < b - (pair ? 1 : 0); bp++) {
-                    if (tid == 0) wait_count(&tcnt[s], bp + 1, ctl, S.spin_limit);
-                    __syncthreads();
-                    if (tid < 32) ys[bp & 1][tid] = __ldcg(S.yv + c0 + 32 * bp + tid);
+                    // (ys alternates: a round writes the buffer the round
+                    // before last read, which every warp left at the last barrier)
+                    if (warp == 0) ys[bp & 1][lane] = poll_block(S.yv + c0 + 32 * bp, 32, ctl, S.spin_limit);
                     __syncthreads();
                     if (lane < w) {
 #pragma unroll
@@ -666,9 +706,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
             __syncthreads();
             if (pair) {
                 // y_b = X_b v' - W_b y_{b-1}, y_{b-1} being the last block to finish
-                if (tid == 0) wait_count(&tcnt[s], b, ctl, S.spin_limit);
-                __syncthreads();
-                if (tid < 32) ys[0][tid] = __ldcg(S.yv + c0 + 32 * (b - 1) + tid);  // block b - 1 is full
+                if (warp == 0) ys[0][lane] = poll_block(S.yv + c0 + 32 * (b - 1), 32, ctl, S.spin_limit);  // full block
                 __syncthreads();
                 apply_pair(Wb, v, ys[0], part, w, false);
                 __syncthreads();
@@ -684,7 +722,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
             for (int q = tid; q < nr; q += kSolveThreads) {
                 if (q < w) {
                     const double y = v[q];
-                    if (!single) __stcg(S.yv + c0 + b0 + q, y);
+                    if (!single) st_relaxed(S.yv + c0 + b0 + q, y);
                     x[c0 + b0 + q] = y * dinv;  // q == tid here
                 } else {
                     __stcg(upd + nd.upd + (q - k), v[q]);
@@ -696,7 +734,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
-                if (!single) atomicAdd(&tcnt[s], 1);
                 finish_forward(nd, s, done, cnt);
             }
         } else {
@@ -711,10 +748,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
             if (warp == 0 && ok) u0 = gather_row(S, nd, x, upd, i);
             double acc = 0.0;
             for (int bp = 0; bp < nd.nblk; bp++) {
-                if (tid == 0) wait_count(&tcnt[s], bp + 1, ctl, S.spin_limit);
-                __syncthreads();
                 const int wp = min(32, k - 32 * bp);
-                if (tid < 32) ys[bp & 1][tid] = tid < wp ? __ldcg(S.yv + c0 + 32 * bp + tid) : 0.0;
+                if (warp == 0) ys[bp & 1][lane] = poll_block(S.yv + c0 + 32 * bp, wp, ctl, S.spin_limit);
                 __syncthreads();
                 if (ok) {
 #pragma unroll
@@ -741,7 +776,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
     }
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSched S, const double *__restrict__ fronts,
+__global__ void __launch_bounds__(kSolveThreads, 5) k_backward_persistent(SolveSched S, const double *__restrict__ fronts,
                                                                         double *x, DevCtl *ctl, const int32_t *skip) {
     extern __shared__ double z[];  // [0, 32): the block; [32, 32 + f - k): x of the rows below
     __shared__ double Lb[32 * 33];
@@ -790,10 +825,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
             for (int t = t0; t < t1; t++) acc += Lc[t] * z[32 + t];
         }
         for (int bp = nd.nblk - 1; bp > b + (pair ? 1 : 0); bp--) {
-            if (tid == 0) wait_count(&tcnt[s], nd.nblk - bp, ctl, S.spin_limit);
-            __syncthreads();
             const int wp = min(32, k - 32 * bp);
-            if (tid < 32) zs[bp & 1][tid] = tid < wp ? __ldcg(x + c0 + 32 * bp + tid) : 0.0;
+            if (warp == 0) zs[bp & 1][lane] = poll_block(S.yv + c0 + 32 * bp, wp, ctl, S.spin_limit);
             __syncthreads();
             if (lane < w) {
                 const double *Lc = L + (int64_t)(b0 + lane) * ld + 32 * bp + 4 * warp;
@@ -816,21 +849,41 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_persistent(SolveSche
         __syncthreads();
         if (pair) {
             // z_b = X_b^T z'' - V_b^T z_{b+1}, z_{b+1} being the last block to finish
-            if (tid == 0) wait_count(&tcnt[s], nd.nblk - (b + 1), ctl, S.spin_limit);
-            __syncthreads();
             const int wn = min(32, k - 32 * (b + 1));  // block b + 1 may be the last, partial one
-            if (tid < 32) zs[0][tid] = tid < wn ? __ldcg(x + c0 + 32 * (b + 1) + tid) : 0.0;
+            if (warp == 0) zs[0][lane] = poll_block(S.yv + c0 + 32 * (b + 1), wn, ctl, S.spin_limit);
             __syncthreads();
             apply_pair(Wb, z, zs[0], part, w, true);
             __syncthreads();
         }
-        for (int q = tid; q < w; q += kSolveThreads) __stcg(x + c0 + b0 + q, z[q]);
+        for (int q = tid; q < w; q += kSolveThreads) {
+            __stcg(x + c0 + b0 + q, z[q]);
+            if (nd.nblk > 1) st_relaxed(S.yv + c0 + b0 + q, z[q]);
+        }
+        // publish: the blocks of a split supernode count themselves done
+        // (release); block 0, the last of the chain, acquires all of them
+        // before it flags the supernode, so the children that read x rows of
+        // any block after the flag see them
         __syncthreads();
         if (tid == 0) {
-            __threadfence();
-            if (nd.nblk > 1) atomicAdd(&tcnt[s], 1);
-            if (b == 0) atomicExch(&flag[s], 1);
+            if (nd.nblk > 1 && b > 0) {
+                __threadfence();
+                atomicAdd(&tcnt[s], 1);
+            }
+            if (b == 0) {
+                wait_count(&tcnt[s], nd.nblk - 1, ctl, S.spin_limit);
+                __threadfence();
+                atomicExch(&flag[s], 1);
+            }
         }
+    }
+}
+
+// Before a persistent sweep: the ticket and the counters to zero, the block
+// values of the chains to the unset pattern.
+__global__ void k_sweep_reset(int32_t *__restrict__ sync, int32_t ncnt, double *__restrict__ yv, int32_t nyv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncnt || i < nyv; i += gridDim.x * blockDim.x) {
+        if (i < ncnt) sync[i] = 0;
+        if (i < nyv) yv[i] = __longlong_as_double((long long)kUnset);
     }
 }
 
@@ -1055,6 +1108,11 @@ void launch_backward_bk(const DevPlan &P, const double *fronts, const int32_t *l
     k_backward_bk<<<count, kSolveThreads, (size_t)maxf * sizeof(double), st>>>(P, fronts, lperm, x, list);
 }
 
+void launch_sweep_reset(const SolveSched &S, int32_t ncnt, cudaStream_t st) {
+    const int grid = (S.nyv + 255) / 256 < 304 ? (S.nyv + 255) / 256 : 304;
+    k_sweep_reset<<<grid > 0 ? grid : 1, 256, 0, st>>>(S.sync, ncnt, S.yv, S.nyv);
+}
+
 void launch_forward_persistent(const SolveSched &S, const double *fronts, const double *Dinv, double *x, double *upd,
                                int32_t maxf, int32_t grid, DevCtl *ctl, cudaStream_t st, const int32_t *skip) {
     static uint64_t attr = 0;
@@ -1062,8 +1120,8 @@ void launch_forward_persistent(const SolveSched &S, const double *fronts, const 
         cudaFuncSetAttribute(k_forward_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemLimit);
         cudaFuncSetAttribute(k_backward_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemLimit);
     }
-    // sync[0] = ticket; then per supernode: finished children, finished items, finished blocks
-    cudaMemsetAsync(S.sync, 0, (size_t)(3 * S.nsuper + 1) * sizeof(int32_t), st);
+    // sync[0] = ticket; then per supernode: finished children, finished items
+    launch_sweep_reset(S, 2 * S.nsuper + 1, st);
     const size_t smem = (size_t)(maxf > kRectRows ? maxf : kRectRows) * sizeof(double);
     k_forward_persistent<<<grid, kSolveThreads, smem, st>>>(S, fronts, Dinv, x, upd, ctl, skip);
 }
@@ -1071,7 +1129,7 @@ void launch_forward_persistent(const SolveSched &S, const double *fronts, const 
 void launch_backward_persistent(const SolveSched &S, const double *fronts, double *x, int32_t maxf, int32_t grid,
                                 DevCtl *ctl, cudaStream_t st, const int32_t *skip) {
     // sync[0] = ticket; then per supernode: done flag, finished blocks
-    cudaMemsetAsync(S.sync, 0, (size_t)(2 * S.nsuper + 1) * sizeof(int32_t), st);
+    launch_sweep_reset(S, 2 * S.nsuper + 1, st);
     const size_t smem = (size_t)(maxf + 32) * sizeof(double);
     k_backward_persistent<<<grid, kSolveThreads, smem, st>>>(S, fronts, x, ctl, skip);
 }
