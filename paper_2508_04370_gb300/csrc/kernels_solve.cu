@@ -614,7 +614,7 @@ __device__ __forceinline__ void apply_pair(const double *Mb, double *t, const do
     if (warp == 0 && lane < w) t[lane] -= ((part[0][lane] + part[1][lane]) + part[2][lane]) + part[3][lane];
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched S, const double *__restrict__ fronts,
+__global__ void __launch_bounds__(kSolveThreads, 5) k_forward_persistent(SolveSched S, const double *__restrict__ fronts,
                                                                        const double *__restrict__ Dinv,
                                                                        double *__restrict__ x, double *upd,
                                                                        DevCtl *ctl, const int32_t *skip) {
@@ -681,14 +681,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
                 for (int bp = 0; bp < b - (pair ? 1 : 0); bp++) {
                     // (ys alternates: a round writes the buffer the round
                     // before last read, which every warp left at the last barrier)
+                    double lv[4];  // independent of the wait: issued before it
+#pragma unroll
+                    for (int c = 0; c < 4; c++)
+                        lv[c] = lane < w ? L[(int64_t)(32 * bp + 4 * warp + c) * ld + b0 + lane] : 0.0;
                     if (warp == 0) ys[bp & 1][lane] = poll_block(S.yv + c0 + 32 * bp, 32, ctl, S.spin_limit);
                     __syncthreads();
                     if (lane < w) {
 #pragma unroll
-                        for (int c = 0; c < 4; c++) {
-                            const int j = 4 * warp + c;
-                            acc += L[(int64_t)(32 * bp + j) * ld + b0 + lane] * ys[bp & 1][j];
-                        }
+                        for (int c = 0; c < 4; c++) acc += lv[c] * ys[bp & 1][4 * warp + c];
                     }
                 }
                 part[warp][lane] = acc;
@@ -749,14 +750,16 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward_persistent(SolveSched
             double acc = 0.0;
             for (int bp = 0; bp < nd.nblk; bp++) {
                 const int wp = min(32, k - 32 * bp);
+                double lv[4];  // independent of the wait: issued before it
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    lv[c] = (ok && 4 * warp + c < wp) ? L[(int64_t)(32 * bp + 4 * warp + c) * ld + i] : 0.0;
                 if (warp == 0) ys[bp & 1][lane] = poll_block(S.yv + c0 + 32 * bp, wp, ctl, S.spin_limit);
                 __syncthreads();
                 if (ok) {
 #pragma unroll
-                    for (int c = 0; c < 4; c++) {
-                        const int j = 4 * warp + c;
-                        if (j < wp) acc += L[(int64_t)(32 * bp + j) * ld + i] * ys[bp & 1][j];
-                    }
+                    for (int c = 0; c < 4; c++)
+                        if (4 * warp + c < wp) acc += lv[c] * ys[bp & 1][4 * warp + c];
                 }
             }
             part[warp][lane] = acc;
@@ -826,13 +829,16 @@ __global__ void __launch_bounds__(kSolveThreads, 5) k_backward_persistent(SolveS
         }
         for (int bp = nd.nblk - 1; bp > b + (pair ? 1 : 0); bp--) {
             const int wp = min(32, k - 32 * bp);
+            double lv[4];  // independent of the wait: issued before it
+            const double *Lc = L + (int64_t)(b0 + lane) * ld + 32 * bp + 4 * warp;
+#pragma unroll
+            for (int c = 0; c < 4; c++) lv[c] = (lane < w && 4 * warp + c < wp) ? Lc[c] : 0.0;
             if (warp == 0) zs[bp & 1][lane] = poll_block(S.yv + c0 + 32 * bp, wp, ctl, S.spin_limit);
             __syncthreads();
             if (lane < w) {
-                const double *Lc = L + (int64_t)(b0 + lane) * ld + 32 * bp + 4 * warp;
 #pragma unroll
                 for (int c = 0; c < 4; c++)
-                    if (4 * warp + c < wp) acc += Lc[c] * zs[bp & 1][4 * warp + c];
+                    if (4 * warp + c < wp) acc += lv[c] * zs[bp & 1][4 * warp + c];
             }
         }
         part[warp][lane] = acc;
