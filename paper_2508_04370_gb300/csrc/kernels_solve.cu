@@ -291,8 +291,14 @@ __device__ __forceinline__ void wait_count(const int32_t *cnt, int need, DevCtl 
 // data itself instead of a counter and then the data.
 constexpr unsigned long long kUnset = 0x7FF4DEAD7FF4DEADull;
 
-__device__ __forceinline__ void st_relaxed(double *p, double v) {
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
+// Publishes one value for the chain.  The unset pattern itself can only
+// come from an input copied through without arithmetic (a signalling NaN in
+// a right-hand side); it goes out as the default NaN, so a waiting block
+// never takes a written value for one still pending.
+__device__ __forceinline__ void publish_value(double *p, double v) {
+    long long b = __double_as_longlong(v);
+    if ((unsigned long long)b == kUnset) b = 0x7FF8000000000000ll;
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(b) : "memory");
 }
 
 __device__ __forceinline__ double ld_relaxed(const double *p) {
@@ -723,7 +729,7 @@ __global__ void __launch_bounds__(kSolveThreads, 5) k_forward_persistent(SolveSc
             for (int q = tid; q < nr; q += kSolveThreads) {
                 if (q < w) {
                     const double y = v[q];
-                    if (!single) st_relaxed(S.yv + c0 + b0 + q, y);
+                    if (!single) publish_value(S.yv + c0 + b0 + q, y);
                     x[c0 + b0 + q] = y * dinv;  // q == tid here
                 } else {
                     __stcg(upd + nd.upd + (q - k), v[q]);
@@ -863,7 +869,7 @@ __global__ void __launch_bounds__(kSolveThreads, 5) k_backward_persistent(SolveS
         }
         for (int q = tid; q < w; q += kSolveThreads) {
             __stcg(x + c0 + b0 + q, z[q]);
-            if (nd.nblk > 1) st_relaxed(S.yv + c0 + b0 + q, z[q]);
+            if (nd.nblk > 1) publish_value(S.yv + c0 + b0 + q, z[q]);
         }
         // publish: the blocks of a split supernode count themselves done
         // (release); block 0, the last of the chain, acquires all of them

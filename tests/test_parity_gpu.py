@@ -643,3 +643,23 @@ def test_launch_shapes_give_identical_factors(pkg, order):
         for a, b in zip(ref, s.factor()):
             assert np.array_equal(a, b), ("level CTAs per SM", per_sm)
     s.close()
+
+
+def test_unset_pattern_in_rhs_reports_nonfinite(pkg):
+    """The blocks of a split supernode pass their values along the sweep's
+    chain through a buffer reset to a signalling-NaN pattern; a right-hand
+    side made of exactly that pattern (a non-finite input) must end with the
+    non-finite error, not with waits that take its values for pending ones
+    and run out."""
+    lp = synth.grid_multicommodity(16, 4)
+    s = pkg.Solver.from_lp(lp, ordering=pkg.IPM_ORD_ND)
+    sym = s.symbolic()
+    sym_k = np.diff(np.asarray(sym["snode_ptr"]))
+    assert sym_k.max() > 32  # supernodes of several 32-column blocks
+    unset = np.array([0x7FF4DEAD7FF4DEAD], dtype=np.uint64).view(np.float64)[0]
+    s.factorise(synth.theta_loguniform(lp.n, 81), RHO, DELTA)
+    assert s.status() >= 0
+    s.solve(np.full(lp.n, unset), np.full(lp.m, unset))
+    assert not (s.info()["status"] & 8), "a chain wait ran out"
+    assert s.status() == pkg.IPM_ERR_NONFINITE
+    s.close()
