@@ -154,7 +154,8 @@ struct SolveSched {
     const SolveItem *fwd, *bwd;
     int32_t nfwd, nbwd, nsuper;
     long long spin_limit;    // polls before a dependency wait gives up (kStatTimeout)
-    int32_t *sync;           // ticket + 3 x nsuper counters (forward), ticket + 2 x nsuper (backward)
+    int32_t *sync;           // ticket + 2 x nsuper counters (forward: children done, items done;
+                             // backward: done flag, blocks done)
     double *yv;              // the values split supernodes' blocks pass along their chain (y forward,
                              // z backward), reset to an unset pattern before each sweep
     int32_t nyv;
