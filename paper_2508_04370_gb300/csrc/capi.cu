@@ -1608,7 +1608,7 @@ int solve_inplace(ipm_ctx *c, double *x, cudaStream_t st, int *nl) {
         Prof pr(c, IPM_K_BACKWARD, bw, st);
         launch_backward_persistent(c->sched, c->fronts, x, c->solve_maxf, c->solve_grid, c->ctl, st);
     }
-    *nl += 2;
+    *nl += 4;  // per sweep: the reset of its counters and chain values, then the sweep
     return to_err(cudaGetLastError());
 }
 
